@@ -1,0 +1,155 @@
+/*
+ * ibm_poisson.h -- C ABI of the GB300 ghost-cell immersed-boundary pressure Poisson library.
+ *
+ * The library implements the per-time-step pressure Poisson solve of a sharp-interface
+ * ghost-cell immersed-boundary method on a stretched cell-centred Cartesian grid
+ * (arxiv 2605.04335, Sec. "Governing Equations and Numerical Methods": fractional-step
+ * projection, second-order finite differences; Sec. "GPU Porting": iblanking, ghost-cell
+ * modules and sparse linear solvers).  Two operations follow the paper's statement of the
+ * problem: classify the grid against a triangulated body (iblank, ghost cells, image
+ * points), then solve the pressure Poisson equation on the classified grid.
+ *
+ * Conventions for every function:
+ *   - Return an ibm_status; 0 (IBM_OK) is success.  Nothing throws, nothing exits, and a
+ *     failed call leaves caller-owned memory in an unspecified but valid state.
+ *   - Cell arrays are [k][j][i] with i fastest (x contiguous), nx*ny*nz elements, indexed
+ *     by the 64-bit linear index l = (k*ny + j)*nx + i.
+ *   - "_dev" pointers are CUDA device pointers on the context's device; everything else is
+ *     host memory.  The caller owns every pointer it passes; the library copies what it
+ *     keeps.
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default stream.  All
+ *     device work of a call is ordered on that stream.  Calls that report results to the
+ *     host (counts, convergence) synchronise that stream before returning.
+ *   - A context serves one host thread at a time.
+ */
+#ifndef IBM_POISSON_H
+#define IBM_POISSON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IBM_OK = 0,
+  IBM_ERR_INVALID_ARG = 1,   /* a pointer, size or option is out of range            */
+  IBM_ERR_OOM = 2,           /* device allocation failed                             */
+  IBM_ERR_CUDA = 3,          /* a CUDA runtime call failed (see ibm_last_cuda_error) */
+  IBM_ERR_NO_FLUID = 4,      /* every cell is solid                                  */
+  IBM_ERR_NOT_CONVERGED = 5, /* max cycles reached; the last iterate is returned     */
+  IBM_ERR_DIVERGED = 6,      /* residual became non-finite or grew by > 1e6          */
+  IBM_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                   */
+  IBM_ERR_NOT_IMPLEMENTED = 8,
+  IBM_ERR_CAPACITY = 9       /* a fixed-size internal buffer is too small            */
+} ibm_status;
+
+typedef struct ibm_ctx ibm_ctx;       /* opaque: device, scratch, reduction buffers      */
+typedef struct ibm_tables ibm_tables; /* opaque: classified grid + multigrid hierarchy   */
+
+/* Grid: nx, ny, nz cells (each >= 2); nx+1, ny+1, nz+1 strictly increasing face
+ * coordinates (host, float64).  Coordinates must lie in [-4, 4] (the exact inside test
+ * works on the integer lattice 2^-24 of that range).  Walls are homogeneous Neumann. */
+typedef struct {
+  int32_t nx, ny, nz;
+  const double *xf, *yf, *zf;
+} ibm_grid;
+
+/* Triangulated surface (host).  verts: nverts x 3 float64; tris: ntris x 3 int32 vertex
+ * indices, counter-clockwise seen from outside.  closed = 1: a watertight solid body
+ * (cells whose centre is inside are solid); closed = 0: a zero-thickness membrane
+ * (not yet supported: IBM_ERR_NOT_IMPLEMENTED).  Closed meshes must not overlap. */
+typedef struct {
+  int32_t nverts, ntris;
+  const double *verts;
+  const int32_t *tris;
+  int32_t closed;
+} ibm_mesh;
+
+/* Solver options; ibm_solve_opts_default fills the defaults shown. */
+typedef struct {
+  int32_t precision;    /* 0: FP64 throughout; 1: FP32 multigrid inside FP64 iterative
+                           refinement (FP64 fine residual, update, gauge, coarsest)  [0] */
+  int32_t nu1, nu2;     /* pre-/post-smoothing red-black Gauss-Seidel sweeps        [2,2] */
+  int32_t max_cycles;   /* V-cycles (precision 0) or refinement steps (precision 1) [100] */
+  int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1)            [1] */
+  int32_t use_graph;    /* capture one cycle as a CUDA graph and replay it            [1] */
+  double omega;         /* Gauss-Seidel relaxation factor                           [1.0] */
+} ibm_solve_opts;
+
+/* Solve report.  resid_history (host, optional) receives the relative residual after
+ * every cycle, up to history_cap entries. */
+typedef struct {
+  int32_t cycles;       /* V-cycles (precision 0) or refinement steps (precision 1)     */
+  int32_t history_len;
+  double rel_resid;     /* ||S P r|| / ||S P b|| of the returned p (see poisson_solve)  */
+  double lambda;        /* the compatibility constant of the bordered system            */
+  double ms_total;      /* wall time of the call (host clock, after the final sync)     */
+  double *resid_history;
+  int32_t history_cap;
+} ibm_solve_info;
+
+const char *ibm_status_str(ibm_status s);
+/* Text of the last CUDA error seen by this host thread (empty if none). */
+const char *ibm_last_cuda_error(void);
+
+/* Create a context on CUDA device `device` (allocates reduction scratch). */
+ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device);
+ibm_status ibm_ctx_destroy(ibm_ctx *ctx);
+
+/* Iblanking and ghost-cell tables (paper Sec. "GPU Porting", items 1 and 2).
+ * Classifies every cell centre against the closed meshes (solid iff strictly inside a
+ * mesh by the exact lattice parity test with half-open tie rules; a centre on the
+ * surface is fluid), marks ghost cells (solid with a fluid face-neighbour), and for
+ * each ghost computes the boundary intercept BI (closest surface point), the image
+ * point IP = 2 BI - GC and its trilinear interpolation row.  nmesh may be 0 (no body).
+ * On success *out owns device memory until ibm_tables_destroy. */
+ibm_status ibm_classify(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes,
+                        int32_t nmesh, ibm_tables **out, void *stream);
+ibm_status ibm_tables_destroy(ibm_tables *t);
+
+/* Sizes of a classified grid: cells, fluid cells, ghost entries, solid cells. */
+ibm_status ibm_tables_counts(const ibm_tables *t, int64_t *ncell, int64_t *nfluid,
+                             int64_t *nghost, int64_t *nsolid);
+
+/* Copy the classification out to caller-owned device arrays (any may be NULL):
+ *   iblank_dev  uint8[ncell]   0 fluid, 1 solid, 3 ghost (solid | 2)
+ *   cell_dev    int64[nghost]  linear cell index of each ghost, ascending
+ *   bi_dev      double[nghost*3], ip_dev double[nghost*3]   (x,y,z)
+ *   base_dev    int32[nghost*3]  base corner (i0,j0,k0) of the IP's cell-centre box
+ *   flags_dev   int32[nghost]    bit 0: nearest-neighbour fallback; bits 8-15: valid corners
+ *   ref_dev     int64[nghost*8]  linear cell index of each interpolation source, -1 unused
+ *   w_dev       double[nghost*8] weights (sum 1; own weight moved to the left-hand side)
+ *   scale_dev   double[nghost]   residual scale of the ghost row
+ * Corner slot c = bx + 2 by + 4 bz addresses cell (i0+bx, j0+by, k0+bz). */
+ibm_status ibm_tables_export(const ibm_tables *t, uint8_t *iblank_dev, int64_t *cell_dev,
+                             double *bi_dev, double *ip_dev, int32_t *base_dev,
+                             int32_t *flags_dev, int64_t *ref_dev, double *w_dev,
+                             double *scale_dev, void *stream);
+
+void ibm_solve_opts_default(ibm_solve_opts *opts);
+
+/* Pressure Poisson solve (paper Sec. "Governing Equations and Numerical Methods") on a
+ * classified grid, by geometric-multigrid V-cycles with red-black Gauss-Seidel smoothing
+ * and the ghost-cell image-point rows updated after every sweep.
+ *
+ * Solves, for p on fluid cells and g on ghost cells and the scalar lambda,
+ *   fluid row i: sum_d c_{i,d} (v_nb - p_i) = b_i - lambda   (v_nb: p, or g at a ghost)
+ *   ghost row G: g_G - sum_k w_k v_k = 0                     (dp/dn = 0 at BI)
+ * with c_{i,+x} = 1/(dx_i (x_{i+1} - x_i)) etc., zero across walls, and returns p gauged
+ * to zero volume-weighted mean over fluid cells.  Convergence: the relative projected
+ * residual ||S P r|| / ||S P b|| <= tol (P removes the volume-weighted fluid mean of r,
+ * S scales ghost rows by the sum of the coefficients that reference them).
+ *   rhs_dev  double[ncell]  b on fluid cells (other cells ignored); not modified.
+ *   p_dev    double[ncell]  in: initial guess on fluid and ghost cells; out: p on fluid
+ *                           cells, g on ghost cells, 0 on other solid cells.
+ * Returns IBM_ERR_NOT_CONVERGED (p = last iterate) if max_cycles is reached. */
+ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol,
+                         double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBM_POISSON_H */

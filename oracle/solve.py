@@ -140,7 +140,13 @@ def solve_gmres(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray,
     rhs = np.concatenate([_rhs(b, cells, is_fluid), [0.0]])
     M = spl.LinearOperator((n + 1, n + 1), msolve)
     x, info = spl.gmres(Bm, rhs, M=M, rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter)
-    if info != 0:
-        raise RuntimeError("oracle GMRES did not converge (info=%d)" % info)
     p = gauge(grid, iblank, _scatter(grid.shape, cells, x[:n]))
+    if info != 0:
+        # GMRES's own stopping test can stall just above rtol at the FP64 floor (it depends on
+        # the platform's BLAS rounding); accept the iterate when the defining residual is at
+        # the floor, judged by the plain operator itself.
+        from .system import relative_residual
+        rr = relative_residual(grid, iblank, G, b, p)
+        if not rr <= 1e-12:
+            raise RuntimeError("oracle GMRES did not converge (info=%d, relative residual %g)" % (info, rr))
     return p, float(x[n])

@@ -1,0 +1,14 @@
+"""GB300 ghost-cell immersed-boundary pressure Poisson library (Python binding).
+
+The compute path is the CUDA library ``lib/libibmpoisson.so`` (built by
+``paper_2605_04335_gb300.build``); this package only marshals arguments to its C ABI
+(``include/ibm_poisson.h``).  Import of the binding fails loudly if the library is
+missing: there is no CPU fallback.
+"""
+from .ibm import (IbmError, Context, Tables, SolveOpts, ibm_ctx_create, ibm_ctx_destroy, ibm_classify,
+                  ibm_tables_counts, ibm_tables_export, ibm_tables_destroy, poisson_solve, load_library,
+                  library_path)
+
+__all__ = ["IbmError", "Context", "Tables", "SolveOpts", "ibm_ctx_create", "ibm_ctx_destroy", "ibm_classify",
+           "ibm_tables_counts", "ibm_tables_export", "ibm_tables_destroy", "poisson_solve", "load_library",
+           "library_path"]

@@ -1,0 +1,158 @@
+// extern "C" entry points of libibmpoisson (declared and documented in include/ibm_poisson.h).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+static thread_local std::string g_last_error;
+
+void set_cuda_error(cudaError_t e, const char *where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+ibm_status check(cudaError_t e, const char *where) {
+  if (e == cudaSuccess) return IBM_OK;
+  set_cuda_error(e, where);
+  cudaGetLastError();   // clear a non-sticky error
+  return e == cudaErrorMemoryAllocation ? IBM_ERR_OOM : IBM_ERR_CUDA;
+}
+
+ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes, int nmesh, ibm_tables **out,
+                         cudaStream_t st);
+ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
+                      const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
+
+}  // namespace ibm
+
+extern "C" {
+
+const char *ibm_status_str(ibm_status s) {
+  switch (s) {
+    case IBM_OK: return "ok";
+    case IBM_ERR_INVALID_ARG: return "invalid argument";
+    case IBM_ERR_OOM: return "out of device memory";
+    case IBM_ERR_CUDA: return "CUDA error";
+    case IBM_ERR_NO_FLUID: return "no fluid cell";
+    case IBM_ERR_NOT_CONVERGED: return "not converged";
+    case IBM_ERR_DIVERGED: return "diverged";
+    case IBM_ERR_TIMEOUT: return "device wait timed out";
+    case IBM_ERR_NOT_IMPLEMENTED: return "not implemented";
+    case IBM_ERR_CAPACITY: return "capacity exceeded";
+  }
+  return "unknown status";
+}
+
+const char *ibm_last_cuda_error(void) { return ibm::g_last_error.c_str(); }
+
+ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device) {
+  if (!out) return IBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  IBM_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(device));
+  ibm_ctx *c = new ibm_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaMalloc((void **)&c->partials, sizeof(double) * ibm::REDUCE_BLOCKS * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->scal, sizeof(double) * ibm::NSCAL);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hscal, sizeof(double) * ibm::NSCAL);
+  if (e != cudaSuccess) {
+    ibm_ctx_destroy(c);
+    return ibm::check(e, "ibm_ctx_create");
+  }
+  cudaMemset(c->scal, 0, sizeof(double) * ibm::NSCAL);
+  *out = c;
+  return IBM_OK;
+}
+
+ibm_status ibm_ctx_destroy(ibm_ctx *c) {
+  if (!c) return IBM_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (c->partials) cudaFree(c->partials);
+  if (c->scal) cudaFree(c->scal);
+  if (c->hscal) cudaFreeHost(c->hscal);
+  delete c;
+  return IBM_OK;
+}
+
+ibm_status ibm_classify(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes, int32_t nmesh, ibm_tables **out,
+                        void *stream) {
+  if (out) *out = nullptr;
+  return ibm::classify_impl(ctx, grid, meshes, nmesh, out, (cudaStream_t)stream);
+}
+
+ibm_status ibm_tables_destroy(ibm_tables *t) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  if (t->ctx) cudaSetDevice(t->ctx->device);
+  cudaDeviceSynchronize();
+  for (int q = 0; q < 2; ++q) ibm::free_hierarchy(t->hier[q]);
+  void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref};
+  for (void *p : ps) if (p) cudaFree(p);
+  delete t;
+  return IBM_OK;
+}
+
+ibm_status ibm_tables_counts(const ibm_tables *t, int64_t *ncell, int64_t *nfluid, int64_t *nghost, int64_t *nsolid) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  if (ncell) *ncell = t->ncell;
+  if (nfluid) *nfluid = t->nfluid;
+  if (nghost) *nghost = t->nghost;
+  if (nsolid) *nsolid = t->nsolid;
+  return IBM_OK;
+}
+
+ibm_status ibm_tables_export(const ibm_tables *t, uint8_t *iblank_dev, int64_t *cell_dev, double *bi_dev,
+                             double *ip_dev, int32_t *base_dev, int32_t *flags_dev, int64_t *ref_dev, double *w_dev,
+                             double *scale_dev, void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  const long long ng = t->nghost;
+  if (iblank_dev) IBM_TRY(cudaMemcpyAsync(iblank_dev, t->iblank, t->ncell, cudaMemcpyDeviceToDevice, st));
+  if (ng > 0) {
+    if (cell_dev) IBM_TRY(cudaMemcpyAsync(cell_dev, t->gcell, 8 * ng, cudaMemcpyDeviceToDevice, st));
+    if (bi_dev) IBM_TRY(cudaMemcpyAsync(bi_dev, t->gbi, 24 * ng, cudaMemcpyDeviceToDevice, st));
+    if (ip_dev) IBM_TRY(cudaMemcpyAsync(ip_dev, t->gip, 24 * ng, cudaMemcpyDeviceToDevice, st));
+    if (base_dev) IBM_TRY(cudaMemcpyAsync(base_dev, t->gbase, 12 * ng, cudaMemcpyDeviceToDevice, st));
+    if (flags_dev) IBM_TRY(cudaMemcpyAsync(flags_dev, t->gflags, 4 * ng, cudaMemcpyDeviceToDevice, st));
+    if (ref_dev) IBM_TRY(cudaMemcpyAsync(ref_dev, t->gref, 64 * ng, cudaMemcpyDeviceToDevice, st));
+    if (w_dev) IBM_TRY(cudaMemcpyAsync(w_dev, t->gw, 64 * ng, cudaMemcpyDeviceToDevice, st));
+    if (scale_dev) IBM_TRY(cudaMemcpyAsync(scale_dev, t->gscale, 8 * ng, cudaMemcpyDeviceToDevice, st));
+  }
+  IBM_TRY(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
+void ibm_solve_opts_default(ibm_solve_opts *o) {
+  if (!o) return;
+  o->precision = 0;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->max_cycles = 100;
+  o->inner_cycles = 1;
+  o->use_graph = 1;
+  o->omega = 1.0;
+}
+
+ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol, double *p_dev,
+                         const ibm_solve_opts *opts, ibm_solve_info *info, void *stream) {
+  if (!ctx || !t || !rhs_dev || !p_dev || !(tol >= 0.0) || t->ctx != ctx) return IBM_ERR_INVALID_ARG;
+  ibm_solve_opts o;
+  ibm_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if ((o.precision != 0 && o.precision != 1) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
+      o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0))
+    return IBM_ERR_INVALID_ARG;
+  if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  ibm_status s = ibm::solve_impl(ctx, const_cast<ibm_tables *>(t), rhs_dev, tol, p_dev, &o, info, (cudaStream_t)stream);
+  if (info) info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,780 @@
+// Iblanking, ghost cells, boundary intercepts, image points and interpolation rows.
+//
+// Paper (arxiv 2605.04335) Sec. "GPU Porting": item 1 classifies the grid's voxels as
+// interior or exterior of the triangulated body ("iblanking"); item 2 applies the
+// internal boundary condition with the ghost-cell method.  The paper gives no formulas;
+// this file implements the library's definition (stated in include/ibm_poisson.h):
+//
+//  * exact inside test on the integer lattice 2^-24: a centre is inside a closed mesh iff
+//    an odd number of triangles cross its vertical line strictly below it; a triangle
+//    covers a column by the half-open (top-left) rule of its xy-projection; centres on
+//    the surface are fluid;
+//  * ghost = solid cell with a fluid face-neighbour;
+//  * BI = closest surface point (lowest triangle index on exact ties), IP = 2 BI - GC,
+//    trilinear weights on the cell-centre lattice with invalid (plain solid) corners
+//    dropped and renormalised, nearest-neighbour fallback, own weight moved left.
+//
+// This translation unit is compiled with -fmad=false: every floating-point expression
+// is evaluated with separately rounded operations in the order written, and divisions
+// are IEEE, so the FP64 outputs are reproducible bit for bit by any implementation that
+// evaluates the same expressions in the same order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+namespace {
+
+constexpr double SNAP_SCALE = 16777216.0;   // 2^24
+constexpr double COORD_LIMIT = 4.0;
+constexpr double WEIGHT_SUM_MIN = 1e-3;
+constexpr double SELF_WEIGHT_MAX = 1.0 - 1e-12;
+
+__device__ __forceinline__ long long snapd(double x) { return __double2ll_rn(x * SNAP_SCALE); }
+
+// first index with a[idx] > v (a ascending, n entries)
+template <typename T>
+__device__ __forceinline__ int upper_bound_dev(const T *a, int n, T v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] > v) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+// first index with a[idx] >= v
+template <typename T>
+__device__ __forceinline__ int lower_bound_dev(const T *a, int n, T v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] >= v) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ long long orient2d(long long ax, long long ay, long long bx, long long by,
+                                              long long qx, long long qy) {
+  return (bx - ax) * (qy - ay) - (by - ay) * (qx - ax);
+}
+
+__device__ __forceinline__ bool top_left(long long px, long long py, long long qx, long long qy) {
+  return (qx > px) || (qx == px && py > qy);
+}
+
+// -------------------------------------------------------------------------- grid (step a1)
+
+// centres, snapped centres, widths and the 7-point coefficients of one axis
+__global__ void k_axis(const double *f, int n, double *c, long long *cs, double *w, double *cm, double *cp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ci = 0.5 * (f[i] + f[i + 1]);
+  c[i] = ci;
+  cs[i] = snapd(ci);
+  double wi = f[i + 1] - f[i];
+  w[i] = wi;
+  double m = 0.0, p = 0.0;
+  if (i > 0) {
+    double cl = 0.5 * (f[i - 1] + f[i]);
+    m = 1.0 / (wi * (ci - cl));
+  }
+  if (i < n - 1) {
+    double cr = 0.5 * (f[i + 1] + f[i + 2]);
+    p = 1.0 / (wi * (cr - ci));
+  }
+  cm[i] = m;
+  cp[i] = p;
+}
+
+// -------------------------------------------------------------------------- inside test
+
+struct Tri {
+  long long a[3], b[3], c[3];   // snapped, counter-clockwise in xy when area > 0
+  long long area;               // twice the projected area (> 0), or 0 if vertical
+  int i0, i1, j0, j1, k0, k1;   // covered column / plane ranges (half-open)
+  int kind;                     // 0 none, 1 projected, 2 vertical
+};
+
+__global__ void k_tri_setup(const double *verts, const int *tris, int ntri, const long long *Xs, int nx,
+                            const long long *Ys, int ny, const long long *Zs, int nz, Tri *out,
+                            long long *count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntri) return;
+  Tri T;
+  long long v[3][3];
+  for (int q = 0; q < 3; ++q)
+    for (int d = 0; d < 3; ++d) v[q][d] = snapd(verts[3 * tris[3 * t + q] + d]);
+  for (int d = 0; d < 3; ++d) { T.a[d] = v[0][d]; T.b[d] = v[1][d]; T.c[d] = v[2][d]; }
+  long long area = orient2d(T.a[0], T.a[1], T.b[0], T.b[1], T.c[0], T.c[1]);
+  long long xl = min(T.a[0], min(T.b[0], T.c[0])), xh = max(T.a[0], max(T.b[0], T.c[0]));
+  long long yl = min(T.a[1], min(T.b[1], T.c[1])), yh = max(T.a[1], max(T.b[1], T.c[1]));
+  long long zl = min(T.a[2], min(T.b[2], T.c[2])), zh = max(T.a[2], max(T.b[2], T.c[2]));
+  T.i0 = lower_bound_dev(Xs, nx, xl); T.i1 = upper_bound_dev(Xs, nx, xh);
+  T.j0 = lower_bound_dev(Ys, ny, yl); T.j1 = upper_bound_dev(Ys, ny, yh);
+  T.k0 = lower_bound_dev(Zs, nz, zl); T.k1 = upper_bound_dev(Zs, nz, zh);
+  long long cnt = 0;
+  T.kind = 0;
+  if (area != 0) {
+    if (area < 0) {
+      for (int d = 0; d < 3; ++d) { long long s = T.b[d]; T.b[d] = T.c[d]; T.c[d] = s; }
+      area = -area;
+    }
+    T.kind = 1;
+    if (T.i1 > T.i0 && T.j1 > T.j0) cnt = (long long)(T.i1 - T.i0) * (T.j1 - T.j0);
+  } else {
+    long long abx = T.b[0] - T.a[0], aby = T.b[1] - T.a[1], abz = T.b[2] - T.a[2];
+    long long acx = T.c[0] - T.a[0], acy = T.c[1] - T.a[1], acz = T.c[2] - T.a[2];
+    long long nxv = aby * acz - abz * acy, nyv = abz * acx - abx * acz;
+    if ((nxv != 0 || nyv != 0) && T.i1 > T.i0 && T.j1 > T.j0 && T.k1 > T.k0) {
+      T.kind = 2;
+      cnt = (long long)(T.i1 - T.i0) * (T.j1 - T.j0) * (T.k1 - T.k0);
+    }
+  }
+  T.area = area;
+  out[t] = T;
+  count[t] = cnt;
+}
+
+// exclusive scan of n int64 counts in one block; out has n+1 entries
+__global__ void k_scan_single(const long long *in, long long *out, int n) {
+  __shared__ long long part[1024];
+  int tid = threadIdx.x, nt = blockDim.x;
+  int per = (n + nt - 1) / nt;
+  int b = tid * per, e = min(n, b + per);
+  long long s = 0;
+  for (int i = b; i < e; ++i) s += in[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    long long run = 0;
+    for (int i = 0; i < nt; ++i) { long long v = part[i]; part[i] = run; run += v; }
+    out[n] = run;
+  }
+  __syncthreads();
+  long long run = part[tid];
+  for (int i = b; i < e; ++i) { out[i] = run; run += in[i]; }
+}
+
+__device__ __forceinline__ bool in_closed_tri2d(long long pu0, long long pv0, long long pu1, long long pv1,
+                                                long long pu2, long long pv2, long long qu, long long qv) {
+  long long e0 = orient2d(pu0, pv0, pu1, pv1, qu, qv);
+  long long e1 = orient2d(pu1, pv1, pu2, pv2, qu, qv);
+  long long e2 = orient2d(pu2, pv2, pu0, pv0, qu, qv);
+  return (e0 >= 0 && e1 >= 0 && e2 >= 0) || (e0 <= 0 && e1 <= 0 && e2 <= 0);
+}
+
+__global__ void k_tri_pairs(const Tri *tris, const long long *off, int ntri, long long total,
+                            const long long *Xs, const long long *Ys, const long long *Zs, int nx, int ny,
+                            int nz, int words, unsigned *toggles, unsigned *onsurf) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    int t = upper_bound_dev(off, ntri + 1, p) - 1;
+    const Tri &T = tris[t];
+    long long local = p - off[t];
+    int ni = T.i1 - T.i0, nj = T.j1 - T.j0;
+    int i = T.i0 + (int)(local % ni);
+    long long rest = local / ni;
+    int j = T.j0 + (int)(rest % nj);
+    long long col = (long long)j * nx + i;
+    long long qx = Xs[i], qy = Ys[j];
+    if (T.kind == 1) {
+      long long wa = orient2d(T.b[0], T.b[1], T.c[0], T.c[1], qx, qy);
+      long long wb = orient2d(T.c[0], T.c[1], T.a[0], T.a[1], qx, qy);
+      long long wc = orient2d(T.a[0], T.a[1], T.b[0], T.b[1], qx, qy);
+      bool cov = (wa > 0 || (wa == 0 && top_left(T.b[0], T.b[1], T.c[0], T.c[1]))) &&
+                 (wb > 0 || (wb == 0 && top_left(T.c[0], T.c[1], T.a[0], T.a[1]))) &&
+                 (wc > 0 || (wc == 0 && top_left(T.a[0], T.a[1], T.b[0], T.b[1])));
+      if (!cov) continue;
+      __int128 N = (__int128)wa * T.a[2] + (__int128)wb * T.b[2] + (__int128)wc * T.c[2];
+      __int128 D = (__int128)T.area;
+      __int128 q = N / D;
+      __int128 r = N - q * D;
+      if (r != 0 && N < 0) q -= 1;          // floor division (D > 0)
+      long long qz = (long long)q;
+      int ks = upper_bound_dev(Zs, nz, qz);  // first centre strictly above the crossing
+      atomicXor(&toggles[col * words + (ks >> 5)], 1u << (ks & 31));
+      if (r == 0 && ks >= 1 && Zs[ks - 1] == qz)
+        atomicOr(&onsurf[col * words + ((ks - 1) >> 5)], 1u << ((ks - 1) & 31));
+    } else if (T.kind == 2) {
+      int k = T.k0 + (int)(rest / nj);
+      // the projection is a segment: the column must lie on its line
+      long long p0x = T.a[0], p0y = T.a[1], p1x = T.b[0], p1y = T.b[1];
+      if (p0x == p1x && p0y == p1y) { p1x = T.c[0]; p1y = T.c[1]; }
+      if (orient2d(p0x, p0y, p1x, p1y, qx, qy) != 0) continue;
+      long long abx = T.b[0] - T.a[0], abz = T.b[2] - T.a[2], acx = T.c[0] - T.a[0], acz = T.c[2] - T.a[2];
+      long long nyv = abz * acx - abx * acz;
+      bool use_x = nyv != 0;
+      long long qu = use_x ? qx : qy, qv = Zs[k];
+      long long u0 = use_x ? T.a[0] : T.a[1], u1 = use_x ? T.b[0] : T.b[1], u2 = use_x ? T.c[0] : T.c[1];
+      if (in_closed_tri2d(u0, T.a[2], u1, T.b[2], u2, T.c[2], qu, qv))
+        atomicOr(&onsurf[col * words + (k >> 5)], 1u << (k & 31));
+    }
+  }
+}
+
+// per column: prefix parity of the toggles; solid where odd and not on the surface.
+// Clears the column's bit words for the next mesh.
+__global__ void k_parity(unsigned *toggles, unsigned *onsurf, int words, int nx, int ny, int nz, int i0, int i1,
+                         int j0, int j1, uint8_t *iblank) {
+  int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+  int j = j0 + blockIdx.y;
+  if (i >= i1 || j >= j1) return;
+  long long col = (long long)j * nx + i;
+  unsigned par = 0;
+  for (int w = 0; w < words; ++w) {
+    unsigned tg = toggles[col * words + w], os = onsurf[col * words + w];
+    if (tg == 0 && os == 0 && par == 0) continue;
+    toggles[col * words + w] = 0u;
+    onsurf[col * words + w] = 0u;
+    for (int b = 0; b < 32; ++b) {
+      int k = w * 32 + b;
+      if (k >= nz) break;
+      par ^= (tg >> b) & 1u;
+      if (par && !((os >> b) & 1u)) iblank[((long long)k * ny + j) * nx + i] = 1;
+    }
+  }
+}
+
+// -------------------------------------------------------------------------- ghost marking
+
+constexpr int GM_THREADS = 256;
+constexpr int GM_PER = 16;   // cells per thread; contiguous runs keep the output sorted
+
+__device__ __forceinline__ bool is_ghost(const uint8_t *ib, int nx, int ny, int nz, long long l) {
+  if ((ib[l] & 1) == 0) return false;
+  int i = (int)(l % nx);
+  long long r = l / nx;
+  int j = (int)(r % ny);
+  int k = (int)(r / ny);
+  long long sy = nx, sz = (long long)nx * ny;
+  if (i > 0 && (ib[l - 1] & 1) == 0) return true;
+  if (i < nx - 1 && (ib[l + 1] & 1) == 0) return true;
+  if (j > 0 && (ib[l - sy] & 1) == 0) return true;
+  if (j < ny - 1 && (ib[l + sy] & 1) == 0) return true;
+  if (k > 0 && (ib[l - sz] & 1) == 0) return true;
+  if (k < nz - 1 && (ib[l + sz] & 1) == 0) return true;
+  return false;
+}
+
+__global__ void k_ghost_count(const uint8_t *ib, int nx, int ny, int nz, long long ncell, long long *bcount) {
+  __shared__ int s[GM_THREADS];
+  long long base = (long long)blockIdx.x * GM_THREADS * GM_PER + (long long)threadIdx.x * GM_PER;
+  int c = 0;
+  for (int q = 0; q < GM_PER; ++q) {
+    long long l = base + q;
+    if (l < ncell && is_ghost(ib, nx, ny, nz, l)) ++c;
+  }
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = GM_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bcount[blockIdx.x] = s[0];
+}
+
+__global__ void k_ghost_scatter(const uint8_t *ib, int nx, int ny, int nz, long long ncell, const long long *boff,
+                                long long *gcell) {
+  __shared__ int s[GM_THREADS];
+  long long base = (long long)blockIdx.x * GM_THREADS * GM_PER + (long long)threadIdx.x * GM_PER;
+  unsigned bits = 0;
+  int c = 0;
+  for (int q = 0; q < GM_PER; ++q) {
+    long long l = base + q;
+    if (l < ncell && is_ghost(ib, nx, ny, nz, l)) { bits |= 1u << q; ++c; }
+  }
+  s[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < GM_THREADS; ++t) { int v = s[t]; s[t] = run; run += v; }
+  }
+  __syncthreads();
+  long long o = boff[blockIdx.x] + s[threadIdx.x];
+  for (int q = 0; q < GM_PER; ++q)
+    if (bits & (1u << q)) gcell[o++] = base + q;
+}
+
+__global__ void k_ghost_bits(uint8_t *ib, const long long *gcell, long long ng) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < ng) ib[gcell[g]] |= 2;
+}
+
+__global__ void k_count_cells(const uint8_t *ib, long long n, unsigned long long *cnt) {
+  __shared__ unsigned long long s[2][256];
+  unsigned long long f = 0, so = 0;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < n; l += (long long)gridDim.x * blockDim.x) {
+    uint8_t v = ib[l];
+    if (v == 0) ++f; else if (v == 1) ++so;
+  }
+  s[0][threadIdx.x] = f; s[1][threadIdx.x] = so;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { atomicAdd(&cnt[0], s[0][0]); atomicAdd(&cnt[1], s[1][0]); }
+}
+
+// -------------------------------------------------------------------------- image points
+
+// Closest point of P on triangle ABC and its squared distance.  Interior: the stationary
+// point of |P - (A + u ab + v ac)|^2 (normal equations [a b; b c][u v]' = [d e]') when it
+// lies in the triangle; otherwise the best projection onto the edges AB, BC, CA.
+__device__ void closest_on_tri(const double P[3], const double *A, const double *B, const double *C, double Q[3],
+                               double &d2) {
+  double abx = B[0] - A[0], aby = B[1] - A[1], abz = B[2] - A[2];
+  double acx = C[0] - A[0], acy = C[1] - A[1], acz = C[2] - A[2];
+  double apx = P[0] - A[0], apy = P[1] - A[1], apz = P[2] - A[2];
+  double a = (abx * abx + aby * aby) + abz * abz;
+  double b = (abx * acx + aby * acy) + abz * acz;
+  double c = (acx * acx + acy * acy) + acz * acz;
+  double d = (abx * apx + aby * apy) + abz * apz;
+  double e = (acx * apx + acy * apy) + acz * apz;
+  double det = a * c - b * b;
+  double su = c * d - b * e;
+  double sv = a * e - b * d;
+  if (det > 0 && su >= 0 && sv >= 0 && su + sv <= det) {
+    double u = su / det, v = sv / det;
+    Q[0] = (A[0] + u * abx) + v * acx;
+    Q[1] = (A[1] + u * aby) + v * acy;
+    Q[2] = (A[2] + u * abz) + v * acz;
+  } else {
+    const double *E0[3] = {A, B, C};
+    const double *E1[3] = {B, C, A};
+    double best = 0.0;
+    for (int s = 0; s < 3; ++s) {
+      const double *P0 = E0[s], *P1 = E1[s];
+      double ex = P1[0] - P0[0], ey = P1[1] - P0[1], ez = P1[2] - P0[2];
+      double px = P[0] - P0[0], py = P[1] - P0[1], pz = P[2] - P0[2];
+      double num = (ex * px + ey * py) + ez * pz;
+      double den = (ex * ex + ey * ey) + ez * ez;
+      double q0, q1, q2;
+      if (num <= 0 || den <= 0) { q0 = P0[0]; q1 = P0[1]; q2 = P0[2]; }
+      else if (num >= den) { q0 = P1[0]; q1 = P1[1]; q2 = P1[2]; }
+      else {
+        double t = num / den;
+        q0 = P0[0] + t * ex; q1 = P0[1] + t * ey; q2 = P0[2] + t * ez;
+      }
+      double dx = P[0] - q0, dy = P[1] - q1, dz = P[2] - q2;
+      double de = (dx * dx + dy * dy) + dz * dz;
+      if (s == 0 || de < best) { best = de; Q[0] = q0; Q[1] = q1; Q[2] = q2; }
+    }
+  }
+  double dx = P[0] - Q[0], dy = P[1] - Q[1], dz = P[2] - Q[2];
+  d2 = (dx * dx + dy * dy) + dz * dz;
+}
+
+struct MeshRange {
+  int t0, t1;
+  double lo[3], hi[3];
+};
+
+__device__ __forceinline__ float box_dist2(const float p[3], float4 lo, float4 hi) {
+  float dx = fmaxf(fmaxf(lo.x - p[0], 0.0f), p[0] - hi.x);
+  float dy = fmaxf(fmaxf(lo.y - p[1], 0.0f), p[1] - hi.y);
+  float dz = fmaxf(fmaxf(lo.z - p[2], 0.0f), p[2] - hi.z);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ double mesh_box_dist(const double P[3], const MeshRange &m) {
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double v = fmax(fmax(m.lo[d] - P[d], 0.0), P[d] - m.hi[d]);
+    s = s + v * v;
+  }
+  return sqrt(s);
+}
+
+struct GhostArgs {
+  int nx, ny, nz;
+  const double *xc, *yc, *zc;
+  const double *cxm, *cxp, *cym, *cyp, *czm, *czp;
+  const uint8_t *ib;
+  const double *tv;        // ntri x 9 vertex coordinates
+  const float4 *blo, *bhi, *cen;
+  const MeshRange *mr;
+  int nmesh;
+  long long ng;
+  const long long *gcell;
+  double *bi, *ip, *w, *scale;
+  int *base, *flags;
+  long long *ref;
+};
+
+__device__ __forceinline__ void base_t(const double *c, int n, double v, int &i0, double &t) {
+  int b = upper_bound_dev(c, n, v) - 1;
+  b = b < 0 ? 0 : (b > n - 2 ? n - 2 : b);
+  i0 = b;
+  double tt = (v - c[b]) / (c[b + 1] - c[b]);
+  t = tt < 0.0 ? 0.0 : (tt > 1.0 ? 1.0 : tt);
+}
+
+__global__ void k_ghost_tables(GhostArgs a) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= a.ng) return;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  long long lin = a.gcell[g];
+  int gi = (int)(lin % nx);
+  int gj = (int)((lin / nx) % ny);
+  int gk = (int)(lin / ((long long)nx * ny));
+  double P[3] = {a.xc[gi], a.yc[gj], a.zc[gk]};
+  float Pf[3] = {(float)P[0], (float)P[1], (float)P[2]};
+  // pass 1: an initial candidate from the nearest mesh box, by centroid distance
+  int m0 = 0;
+  double md = 1e300;
+  for (int m = 0; m < a.nmesh; ++m) {
+    double d = mesh_box_dist(P, a.mr[m]);
+    if (d < md) { md = d; m0 = m; }
+  }
+  int bt = a.mr[m0].t0;
+  float bc = 3.4e38f;
+  for (int t = a.mr[m0].t0; t < a.mr[m0].t1; ++t) {
+    float4 c = a.cen[t];
+    float dx = c.x - Pf[0], dy = c.y - Pf[1], dz = c.z - Pf[2];
+    float d = dx * dx + dy * dy + dz * dz;
+    if (d < bc) { bc = d; bt = t; }
+  }
+  double best, Q[3], BQ[3];
+  closest_on_tri(P, a.tv + 9 * bt, a.tv + 9 * bt + 3, a.tv + 9 * bt + 6, BQ, best);
+  int bidx = bt;
+  // pass 2: every triangle whose box could hold a point as close (conservative margin)
+  double thr = sqrt(best) + 4e-6;
+  for (int m = 0; m < a.nmesh; ++m) {
+    if (mesh_box_dist(P, a.mr[m]) > thr) continue;
+    for (int t = a.mr[m].t0; t < a.mr[m].t1; ++t) {
+      float lb = box_dist2(Pf, a.blo[t], a.bhi[t]);
+      if ((double)lb > thr * thr) continue;
+      double d2;
+      closest_on_tri(P, a.tv + 9 * t, a.tv + 9 * t + 3, a.tv + 9 * t + 6, Q, d2);
+      if (d2 < best || (d2 == best && t < bidx)) {
+        best = d2; bidx = t;
+        BQ[0] = Q[0]; BQ[1] = Q[1]; BQ[2] = Q[2];
+        thr = sqrt(best) + 4e-6;
+      }
+    }
+  }
+  double IP[3];
+  for (int d = 0; d < 3; ++d) {
+    IP[d] = (BQ[d] + BQ[d]) - P[d];
+    a.bi[3 * g + d] = BQ[d];
+    a.ip[3 * g + d] = IP[d];
+  }
+  int i0, j0, k0;
+  double tx, ty, tz;
+  base_t(a.xc, nx, IP[0], i0, tx);
+  base_t(a.yc, ny, IP[1], j0, ty);
+  base_t(a.zc, nz, IP[2], k0, tz);
+  a.base[3 * g + 0] = i0; a.base[3 * g + 1] = j0; a.base[3 * g + 2] = k0;
+  double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
+  double w[8];
+  long long rf[8];
+  unsigned valid = 0;
+  for (int c = 0; c < 8; ++c) {
+    int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+    long long l = ((long long)(k0 + bz) * ny + (j0 + by)) * nx + (i0 + bx);
+    rf[c] = l;
+    w[c] = (wx[bx] * wy[by]) * wz[bz];
+    if (a.ib[l] != 1) valid |= 1u << c;
+  }
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c)
+    if (valid & (1u << c)) s = s + w[c];
+  bool fallback = s < WEIGHT_SUM_MIN;
+  double wn[8];
+  if (!fallback) {
+    for (int c = 0; c < 8; ++c) wn[c] = (valid & (1u << c)) ? w[c] / s : 0.0;
+    int selfc = -1;
+    for (int c = 0; c < 8; ++c)
+      if ((valid & (1u << c)) && rf[c] == lin) { selfc = c; break; }
+    if (selfc >= 0) {
+      double ws = wn[selfc];
+      if (ws >= SELF_WEIGHT_MAX) {
+        fallback = true;
+      } else {
+        for (int c = 0; c < 8; ++c) wn[c] = wn[c] / (1.0 - ws);
+        wn[selfc] = 0.0;
+      }
+    }
+  }
+  int flags = 0;
+  if (fallback) {
+    flags |= 1;
+    long long bestl = -1;
+    double bd = 0.0;
+    const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+    for (int q = 0; q < 6; ++q) {
+      int ii = gi + di[q], jj = gj + dj[q], kk = gk + dk[q];
+      if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+      long long l = ((long long)kk * ny + jj) * nx + ii;
+      if (a.ib[l] != 0) continue;
+      double ex = IP[0] - a.xc[ii], ey = IP[1] - a.yc[jj], ez = IP[2] - a.zc[kk];
+      double d2 = (ex * ex + ey * ey) + ez * ez;
+      if (bestl < 0 || d2 < bd) { bestl = l; bd = d2; }
+    }
+    for (int c = 0; c < 8; ++c) { a.w[8 * g + c] = 0.0; a.ref[8 * g + c] = -1; }
+    a.w[8 * g] = 1.0;
+    a.ref[8 * g] = bestl;
+  } else {
+    flags |= (int)(valid << 8);
+    for (int c = 0; c < 8; ++c) {
+      a.w[8 * g + c] = wn[c];
+      a.ref[8 * g + c] = wn[c] != 0.0 ? rf[c] : -1;
+    }
+  }
+  a.flags[g] = flags;
+  // row scale: coefficients of the fluid rows that reference this ghost
+  double sc = 0.0;
+  long long sy = nx, sz = (long long)nx * ny;
+  if (gi > 0 && a.ib[lin - 1] == 0) sc = sc + a.cxp[gi - 1];
+  if (gi < nx - 1 && a.ib[lin + 1] == 0) sc = sc + a.cxm[gi + 1];
+  if (gj > 0 && a.ib[lin - sy] == 0) sc = sc + a.cyp[gj - 1];
+  if (gj < ny - 1 && a.ib[lin + sy] == 0) sc = sc + a.cym[gj + 1];
+  if (gk > 0 && a.ib[lin - sz] == 0) sc = sc + a.czp[gk - 1];
+  if (gk < nz - 1 && a.ib[lin + sz] == 0) sc = sc + a.czm[gk + 1];
+  a.scale[g] = sc;
+}
+
+// triangle boxes (outward-rounded to float) and centroids, for the pruned search
+__global__ void k_tri_boxes(const double *tv, int ntri, float4 *blo, float4 *bhi, float4 *cen) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntri) return;
+  const double *v = tv + 9 * t;
+  float lo[3], hi[3], c[3];
+  for (int d = 0; d < 3; ++d) {
+    double l = fmin(v[d], fmin(v[3 + d], v[6 + d])), h = fmax(v[d], fmax(v[3 + d], v[6 + d]));
+    lo[d] = __double2float_rd(l);
+    hi[d] = __double2float_ru(h);
+    c[d] = (float)((v[d] + v[3 + d] + v[6 + d]) / 3.0);
+  }
+  blo[t] = make_float4(lo[0], lo[1], lo[2], 0.f);
+  bhi[t] = make_float4(hi[0], hi[1], hi[2], 0.f);
+  cen[t] = make_float4(c[0], c[1], c[2], 0.f);
+}
+
+__global__ void k_gather_tris(const double *verts, const int *tris, int ntri, double *tv) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntri) return;
+  for (int q = 0; q < 3; ++q)
+    for (int d = 0; d < 3; ++d) tv[9 * t + 3 * q + d] = verts[3 * tris[3 * t + q] + d];
+}
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+  cudaError_t alloc(size_t n) { return cudaMalloc((void **)&p, (n ? n : 1) * sizeof(T)); }
+};
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// Host orchestration of ibm_classify (see include/ibm_poisson.h).
+ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes, int nmesh, ibm_tables **out,
+                         cudaStream_t st) {
+  if (!ctx || !grid || !out || nmesh < 0 || (nmesh > 0 && !meshes)) return IBM_ERR_INVALID_ARG;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  if (nx < 2 || ny < 2 || nz < 2 || !grid->xf || !grid->yf || !grid->zf) return IBM_ERR_INVALID_ARG;
+  const double *fs[3] = {grid->xf, grid->yf, grid->zf};
+  const int ns[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i <= ns[a]; ++i) {
+      double v = fs[a][i];
+      if (!(std::fabs(v) <= COORD_LIMIT) || (i > 0 && !(v > fs[a][i - 1]))) return IBM_ERR_INVALID_ARG;
+    }
+  long long totverts = 0, tottris = 0;
+  for (int m = 0; m < nmesh; ++m) {
+    const ibm_mesh &M = meshes[m];
+    if (M.nverts < 0 || M.ntris < 0 || (M.ntris > 0 && (!M.verts || !M.tris))) return IBM_ERR_INVALID_ARG;
+    if (M.closed != 1) return IBM_ERR_NOT_IMPLEMENTED;
+    for (long long q = 0; q < 3LL * M.nverts; ++q)
+      if (!(std::fabs(M.verts[q]) <= COORD_LIMIT)) return IBM_ERR_INVALID_ARG;
+    for (long long q = 0; q < 3LL * M.ntris; ++q)
+      if (M.tris[q] < 0 || M.tris[q] >= M.nverts) return IBM_ERR_INVALID_ARG;
+    totverts += M.nverts;
+    tottris += M.ntris;
+  }
+  IBM_TRY(cudaSetDevice(ctx->device));
+  const long long ncell = (long long)nx * ny * nz;
+
+  ibm_tables *T = new ibm_tables();
+  T->ctx = ctx;
+  T->nx = nx; T->ny = ny; T->nz = nz;
+  T->xf.assign(grid->xf, grid->xf + nx + 1);
+  T->yf.assign(grid->yf, grid->yf + ny + 1);
+  T->zf.assign(grid->zf, grid->zf + nz + 1);
+  T->ncell = ncell;
+  auto fail = [&](ibm_status s) { ibm_tables_destroy(T); return s; };
+#define CTRY(call)                                                  \
+  do {                                                              \
+    cudaError_t e__ = (call);                                       \
+    if (e__ != cudaSuccess) return fail(ibm::check(e__, #call));    \
+  } while (0)
+
+  // axes: faces -> centres, snapped centres, widths, coefficients (device)
+  DevBuf<double> df[3], dc[3], dw[3], dcm[3], dcp[3];
+  DevBuf<long long> ds[3];
+  for (int a = 0; a < 3; ++a) {
+    CTRY(df[a].alloc(ns[a] + 1)); CTRY(dc[a].alloc(ns[a])); CTRY(dw[a].alloc(ns[a]));
+    CTRY(dcm[a].alloc(ns[a])); CTRY(dcp[a].alloc(ns[a])); CTRY(ds[a].alloc(ns[a]));
+    CTRY(cudaMemcpyAsync(df[a].p, fs[a], (ns[a] + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_axis<<<nblk(ns[a], 128), 128, 0, st>>>(df[a].p, ns[a], dc[a].p, ds[a].p, dw[a].p, dcm[a].p, dcp[a].p);
+  }
+  CTRY(cudaGetLastError());
+  CTRY(cudaMalloc(&T->iblank, ncell));
+  CTRY(cudaMemsetAsync(T->iblank, 0, ncell, st));
+
+  // inside test per closed mesh
+  DevBuf<double> dverts;
+  DevBuf<int> dtris;
+  CTRY(dverts.alloc(3 * (totverts ? totverts : 1)));
+  CTRY(dtris.alloc(3 * (tottris ? tottris : 1)));
+  std::vector<int> vbase(nmesh), tbase(nmesh);
+  {
+    long long vo = 0, to = 0;
+    for (int m = 0; m < nmesh; ++m) {
+      vbase[m] = (int)vo; tbase[m] = (int)to;
+      if (meshes[m].nverts)
+        CTRY(cudaMemcpyAsync(dverts.p + 3 * vo, meshes[m].verts, 3 * sizeof(double) * meshes[m].nverts,
+                             cudaMemcpyHostToDevice, st));
+      if (meshes[m].ntris)
+        CTRY(cudaMemcpyAsync(dtris.p + 3 * to, meshes[m].tris, 3 * sizeof(int) * meshes[m].ntris,
+                             cudaMemcpyHostToDevice, st));
+      vo += meshes[m].nverts;
+      to += meshes[m].ntris;
+    }
+  }
+  const int words = (nz + 1 + 31) / 32;
+  if (tottris > 0) {
+    DevBuf<unsigned> tog, ons;
+    CTRY(tog.alloc((size_t)nx * ny * words));
+    CTRY(ons.alloc((size_t)nx * ny * words));
+    CTRY(cudaMemsetAsync(tog.p, 0, (size_t)nx * ny * words * 4, st));
+    CTRY(cudaMemsetAsync(ons.p, 0, (size_t)nx * ny * words * 4, st));
+    for (int m = 0; m < nmesh; ++m) {
+      const int nt = meshes[m].ntris;
+      if (nt == 0) continue;
+      DevBuf<Tri> tr;
+      DevBuf<long long> cnt, off;
+      CTRY(tr.alloc(nt)); CTRY(cnt.alloc(nt)); CTRY(off.alloc(nt + 1));
+      k_tri_setup<<<nblk(nt, 128), 128, 0, st>>>(dverts.p + 3LL * vbase[m], dtris.p + 3LL * tbase[m], nt, ds[0].p,
+                                                  nx, ds[1].p, ny, ds[2].p, nz, tr.p, cnt.p);
+      k_scan_single<<<1, 1024, 0, st>>>(cnt.p, off.p, nt);
+      long long total = 0;
+      CTRY(cudaMemcpyAsync(&total, off.p + nt, sizeof(long long), cudaMemcpyDeviceToHost, st));
+      CTRY(cudaStreamSynchronize(st));
+      if (total > 0) {
+        unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 8LL * 152 * 4);
+        k_tri_pairs<<<blocks, 256, 0, st>>>(tr.p, off.p, nt, total, ds[0].p, ds[1].p, ds[2].p, nx, ny, nz, words,
+                                            tog.p, ons.p);
+      }
+      // columns of the mesh's xy box
+      double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+      for (long long q = 0; q < meshes[m].nverts; ++q)
+        for (int d = 0; d < 2; ++d) {
+          lo[d] = std::min(lo[d], meshes[m].verts[3 * q + d]);
+          hi[d] = std::max(hi[d], meshes[m].verts[3 * q + d]);
+        }
+      int i0 = (int)(std::lower_bound(T->xf.begin(), T->xf.end(), lo[0]) - T->xf.begin()) - 1;
+      int i1 = (int)(std::upper_bound(T->xf.begin(), T->xf.end(), hi[0]) - T->xf.begin());
+      int j0 = (int)(std::lower_bound(T->yf.begin(), T->yf.end(), lo[1]) - T->yf.begin()) - 1;
+      int j1 = (int)(std::upper_bound(T->yf.begin(), T->yf.end(), hi[1]) - T->yf.begin());
+      i0 = std::max(0, i0 - 1); j0 = std::max(0, j0 - 1);
+      i1 = std::min(nx, i1 + 1); j1 = std::min(ny, j1 + 1);
+      if (i1 > i0 && j1 > j0) {
+        dim3 gp(nblk(i1 - i0, 128), j1 - j0);
+        k_parity<<<gp, 128, 0, st>>>(tog.p, ons.p, words, nx, ny, nz, i0, i1, j0, j1, T->iblank);
+      }
+      CTRY(cudaGetLastError());
+      CTRY(cudaStreamSynchronize(st));
+    }
+  }
+
+  // ghost marking + sorted compaction
+  const long long chunk = (long long)GM_THREADS * GM_PER;
+  const unsigned nb = (unsigned)((ncell + chunk - 1) / chunk);
+  {
+    DevBuf<long long> bc, bo;
+    CTRY(bc.alloc(nb)); CTRY(bo.alloc(nb + 1));
+    k_ghost_count<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bc.p);
+    k_scan_single<<<1, 1024, 0, st>>>(bc.p, bo.p, (int)nb);
+    long long ng = 0;
+    CTRY(cudaMemcpyAsync(&ng, bo.p + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CTRY(cudaStreamSynchronize(st));
+    T->nghost = ng;
+    CTRY(cudaMalloc(&T->gcell, (ng ? ng : 1) * sizeof(long long)));
+    if (ng) {
+      k_ghost_scatter<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bo.p, T->gcell);
+      k_ghost_bits<<<nblk(ng, 256), 256, 0, st>>>(T->iblank, T->gcell, ng);
+    }
+    CTRY(cudaGetLastError());
+  }
+  {
+    DevBuf<unsigned long long> cnt;
+    CTRY(cnt.alloc(2));
+    CTRY(cudaMemsetAsync(cnt.p, 0, 16, st));
+    k_count_cells<<<1216, 256, 0, st>>>(T->iblank, ncell, cnt.p);
+    unsigned long long hc[2];
+    CTRY(cudaMemcpyAsync(hc, cnt.p, 16, cudaMemcpyDeviceToHost, st));
+    CTRY(cudaStreamSynchronize(st));
+    T->nfluid = (long long)hc[0];
+    T->nsolid = (long long)hc[1];
+  }
+  const long long ng = T->nghost;
+  CTRY(cudaMalloc(&T->gbi, (ng ? ng : 1) * 3 * sizeof(double)));
+  CTRY(cudaMalloc(&T->gip, (ng ? ng : 1) * 3 * sizeof(double)));
+  CTRY(cudaMalloc(&T->gw, (ng ? ng : 1) * 8 * sizeof(double)));
+  CTRY(cudaMalloc(&T->gscale, (ng ? ng : 1) * sizeof(double)));
+  CTRY(cudaMalloc(&T->gbase, (ng ? ng : 1) * 3 * sizeof(int)));
+  CTRY(cudaMalloc(&T->gflags, (ng ? ng : 1) * sizeof(int)));
+  CTRY(cudaMalloc(&T->gref, (ng ? ng : 1) * 8 * sizeof(long long)));
+  if (ng > 0) {
+    // all closed-mesh triangles, concatenated in mesh order (global triangle index)
+    DevBuf<double> tv;
+    DevBuf<float4> blo, bhi, cen;
+    CTRY(tv.alloc(9 * tottris));
+    CTRY(blo.alloc(tottris)); CTRY(bhi.alloc(tottris)); CTRY(cen.alloc(tottris));
+    std::vector<MeshRange> hmr;
+    for (int m = 0; m < nmesh; ++m) {
+      const int nt = meshes[m].ntris;
+      if (nt == 0) continue;
+      k_gather_tris<<<nblk(nt, 128), 128, 0, st>>>(dverts.p + 3LL * vbase[m], dtris.p + 3LL * tbase[m], nt,
+                                                    tv.p + 9LL * tbase[m]);
+      MeshRange r;
+      r.t0 = tbase[m]; r.t1 = tbase[m] + nt;
+      for (int d = 0; d < 3; ++d) { r.lo[d] = 1e300; r.hi[d] = -1e300; }
+      for (long long q = 0; q < 3LL * nt; ++q) {
+        const double *v = meshes[m].verts + 3LL * meshes[m].tris[q];
+        for (int d = 0; d < 3; ++d) { r.lo[d] = std::min(r.lo[d], v[d]); r.hi[d] = std::max(r.hi[d], v[d]); }
+      }
+      hmr.push_back(r);
+    }
+    k_tri_boxes<<<nblk(tottris, 128), 128, 0, st>>>(tv.p, (int)tottris, blo.p, bhi.p, cen.p);
+    DevBuf<MeshRange> dmr;
+    CTRY(dmr.alloc(hmr.size()));
+    CTRY(cudaMemcpyAsync(dmr.p, hmr.data(), hmr.size() * sizeof(MeshRange), cudaMemcpyHostToDevice, st));
+    GhostArgs ga;
+    ga.nx = nx; ga.ny = ny; ga.nz = nz;
+    ga.xc = dc[0].p; ga.yc = dc[1].p; ga.zc = dc[2].p;
+    ga.cxm = dcm[0].p; ga.cxp = dcp[0].p; ga.cym = dcm[1].p; ga.cyp = dcp[1].p; ga.czm = dcm[2].p; ga.czp = dcp[2].p;
+    ga.ib = T->iblank;
+    ga.tv = tv.p; ga.blo = blo.p; ga.bhi = bhi.p; ga.cen = cen.p;
+    ga.mr = dmr.p; ga.nmesh = (int)hmr.size();
+    ga.ng = ng; ga.gcell = T->gcell;
+    ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
+    ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
+    k_ghost_tables<<<nblk(ng, 128), 128, 0, st>>>(ga);
+    CTRY(cudaGetLastError());
+    CTRY(cudaStreamSynchronize(st));
+  }
+  CTRY(cudaStreamSynchronize(st));
+#undef CTRY
+  if (T->nfluid == 0) return fail(IBM_ERR_NO_FLUID);
+  *out = T;
+  return IBM_OK;
+}
+
+}  // namespace ibm

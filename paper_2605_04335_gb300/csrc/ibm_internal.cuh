@@ -1,0 +1,123 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ibm_poisson.h"
+
+namespace ibm {
+
+// Padded cell arrays: one halo layer in every direction; element i = 0 of a row sits at
+// offset OX so rows start 32-byte aligned for float and double.
+constexpr int OX = 4;
+constexpr int REDUCE_BLOCKS = 608;   // 4 x 152 SMs: fixed grid -> deterministic reductions
+constexpr int REDUCE_THREADS = 256;
+constexpr int NSCAL = 32;            // device scalars per context
+
+// Device scalar slots (ctx->scal).
+enum Scal {
+  S_LAMBDA = 0,   // compatibility constant of the fine system
+  S_MU = 1,       // fluid mean of the last fine residual
+  S_NORM2 = 2,    // ||S P r||^2 of the last fine residual
+  S_FLUIDVOL = 3, // sum of fluid volumes (fine)
+  S_NF = 4,       // number of fluid cells (fine)
+  S_MEANP = 5,    // fluid mean of p (gauge)
+  S_LEVEL_SHIFT = 8  // S_LEVEL_SHIFT + l: projection shift of coarse level l
+};
+
+struct LevelGeom {
+  int nx, ny, nz, px;
+  long long sy, sz, ntot;  // strides and padded size
+};
+
+inline LevelGeom make_geom(int nx, int ny, int nz) {
+  LevelGeom g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.px = ((nx + OX + 1 + 7) / 8) * 8;
+  g.sy = g.px;
+  g.sz = (long long)g.px * (ny + 2);
+  g.ntot = g.sz * (nz + 2);
+  return g;
+}
+
+__host__ __device__ inline long long pidx(const LevelGeom &g, int i, int j, int k) {
+  return ((long long)(k + 1) * (g.ny + 2) + (j + 1)) * g.px + (i + OX);
+}
+
+// One multigrid level; arrays are device memory owned by the hierarchy.
+struct Level {
+  LevelGeom g;
+  uint8_t *mask = nullptr;                  // padded; 0 = active fluid row
+  void *e = nullptr, *r = nullptr;          // padded, element type of the hierarchy
+  void *fx = nullptr, *fy = nullptr, *fz = nullptr;   // face fractions (levels >= 1)
+  void *c1d = nullptr;                      // cxm cxp cym cyp czm czp (n each, element type)
+  double *w1d = nullptr;                    // widths dx dy dz
+  double *cen = nullptr;                    // centres xc yc zc
+  int8_t *poff = nullptr;                   // prolongation: neighbour offset per fine index (x,y,z)
+  double *pt = nullptr;                     // prolongation: weight of the neighbour (x,y,z)
+  double fluid_vol = 0.0;
+  long long nfluid = 0;
+};
+
+struct Hierarchy {
+  int elem = 8;                             // bytes per element of levels (4 or 8)
+  std::vector<Level> lv;
+  // fine-level FP64 arrays (both precisions)
+  double *p64 = nullptr, *b64 = nullptr;
+  // coarsest dense bordered inverse
+  int ncoarse = 0;                          // unknowns of the coarsest level (fluid cells)
+  double *minv = nullptr;                   // (ncoarse+1)^2
+  int *cidx = nullptr;                      // padded index of each coarsest unknown
+  int *dncoarse = nullptr;                  // device copy of ncoarse
+  double *c64 = nullptr;                    // FP64 fine coefficients cxm cxp cym cyp czm czp
+  // solver-side ghost rows: padded source indices (-1 unused), weights (double and float)
+  long long *gsrc = nullptr;
+  long long *gdst = nullptr;
+  double *gw64 = nullptr;
+  float *gw32 = nullptr;
+  double *gtmp = nullptr;                   // new ghost values (Jacobi)
+  void *graph_exec = nullptr;
+};
+
+}  // namespace ibm
+
+struct ibm_ctx {
+  int device = 0;
+  double *partials = nullptr;   // REDUCE_BLOCKS * 8 doubles
+  double *scal = nullptr;       // NSCAL device scalars
+  double *hscal = nullptr;      // pinned host mirror of scal
+  int sm_count = 0;
+};
+
+struct ibm_tables {
+  ibm_ctx *ctx = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  std::vector<double> xf, yf, zf;   // host copies of the faces
+  long long ncell = 0, nfluid = 0, nghost = 0, nsolid = 0;
+  // classification (device)
+  uint8_t *iblank = nullptr;
+  long long *gcell = nullptr;
+  double *gbi = nullptr, *gip = nullptr, *gw = nullptr, *gscale = nullptr;
+  int *gbase = nullptr, *gflags = nullptr;
+  long long *gref = nullptr;
+  // solver hierarchies by precision (lazy)
+  ibm::Hierarchy *hier[2] = {nullptr, nullptr};
+};
+
+namespace ibm {
+
+void set_cuda_error(cudaError_t e, const char *where);
+ibm_status check(cudaError_t e, const char *where);
+void free_hierarchy(Hierarchy *h);
+
+}  // namespace ibm
+
+#define IBM_TRY(call)                                                   \
+  do {                                                                  \
+    cudaError_t e__ = (call);                                           \
+    if (e__ != cudaSuccess) return ibm::check(e__, #call);              \
+  } while (0)

@@ -1,0 +1,905 @@
+// Geometric multigrid for the ghost-cell pressure Poisson system.
+//
+// Paper (arxiv 2605.04335) Sec. "Governing Equations and Numerical Methods": the pressure
+// Poisson equation of the fractional-step method, second-order finite differences on a
+// Cartesian grid.  The paper's own solver is BiCGStab with scheduled relaxed Jacobi; this
+// library reaches the same discrete solution with V-cycles:
+//
+//  * smoother: red-black Gauss-Seidel on fluid rows (colour (i+j+k) mod 2), followed on the
+//    finest level by a Jacobi update of every ghost row g_G = sum_k w_k v_k (+ rhs);
+//  * coarse levels: n_c = ceil(n/2) per axis, coarse cell fluid iff any child is fluid,
+//    coefficients rediscretised on the coarse faces and scaled by the area fraction of
+//    open fine faces (both neighbours fluid); no ghost rows (staircase Neumann);
+//  * restriction: volume-weighted sum of fluid children's residuals / coarse volume,
+//    followed by removal of the coarse level's volume-weighted fluid mean;
+//  * prolongation: trilinear in physical coordinates over fluid coarse cells, renormalised;
+//  * coarsest level (<= 128 cells): exact bordered solve [A 1; V' 0] by a precomputed inverse.
+//
+// Element type T is float or double; the fine-level residual, the refinement update and
+// the gauge are always FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+constexpr int MAX_COARSE = 128;
+
+namespace {
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+struct LV {          // kernel-side view of one level
+  int nx, ny, nz, px;
+  long long sy, sz;
+  const uint8_t *mask;
+  const T *cxm, *cxp, *cym, *cyp, *czm, *czp;
+  const T *fx, *fy, *fz;     // nullptr on the finest level
+  const double *dx, *dy, *dz;
+};
+
+template <typename T>
+LV<T> view(const Level &L) {
+  LV<T> v;
+  v.nx = L.g.nx; v.ny = L.g.ny; v.nz = L.g.nz; v.px = L.g.px; v.sy = L.g.sy; v.sz = L.g.sz;
+  v.mask = L.mask;
+  const T *c = (const T *)L.c1d;
+  v.cxm = c; v.cxp = c + L.g.nx; v.cym = c + 2 * L.g.nx; v.cyp = v.cym + L.g.ny;
+  v.czm = v.cyp + L.g.ny; v.czp = v.czm + L.g.nz;
+  v.fx = (const T *)L.fx; v.fy = (const T *)L.fy; v.fz = (const T *)L.fz;
+  v.dx = L.w1d; v.dy = L.w1d + L.g.nx; v.dz = L.w1d + L.g.nx + L.g.ny;
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ long long vidx(const LV<T> &v, int i, int j, int k) {
+  return ((long long)(k + 1) * (v.ny + 2) + (j + 1)) * v.px + (i + OX);
+}
+
+// six face coefficients of cell (i,j,k) at padded index id
+template <typename T>
+__device__ __forceinline__ void coefs(const LV<T> &v, int i, int j, int k, long long id, T c[6]) {
+  c[0] = v.cxm[i]; c[1] = v.cxp[i]; c[2] = v.cym[j]; c[3] = v.cyp[j]; c[4] = v.czm[k]; c[5] = v.czp[k];
+  if (v.fx) {
+    c[0] *= v.fx[id - 1]; c[1] *= v.fx[id];
+    c[2] *= v.fy[id - v.sy]; c[3] *= v.fy[id];
+    c[4] *= v.fz[id - v.sz]; c[5] *= v.fz[id];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T stencil_sum(const LV<T> &v, const T *e, long long id, const T c[6]) {
+  return c[0] * e[id - 1] + c[1] * e[id + 1] + c[2] * e[id - v.sy] + c[3] * e[id + v.sy] +
+         c[4] * e[id - v.sz] + c[5] * e[id + v.sz];
+}
+
+// ------------------------------------------------------------------ hierarchy setup kernels
+
+template <typename T>
+__global__ void k_axis_level(const double *f, int n, T *cm, T *cp, double *w, double *c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ci = 0.5 * (f[i] + f[i + 1]), wi = f[i + 1] - f[i];
+  double m = 0.0, p = 0.0;
+  if (i > 0) m = 1.0 / (wi * (ci - 0.5 * (f[i - 1] + f[i])));
+  if (i < n - 1) p = 1.0 / (wi * (0.5 * (f[i + 1] + f[i + 2]) - ci));
+  cm[i] = (T)m; cp[i] = (T)p; w[i] = wi; c[i] = ci;
+}
+
+// prolongation weights from coarse (cc, nc) to fine (cf, nf) along one axis
+__global__ void k_prolong_axis(const double *cf, int nf, const double *cc, int nc, int8_t *off, double *t) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  int I = i >> 1;
+  double xf = cf[i], X = cc[I];
+  int nb = xf < X ? I - 1 : (xf > X ? I + 1 : I);
+  if (nb < 0 || nb >= nc || nb == I) { off[i] = 0; t[i] = 0.0; return; }
+  off[i] = (int8_t)(nb - I);
+  t[i] = (xf - X) / (cc[nb] - X);
+}
+
+__global__ void k_mask0(const uint8_t *ib, int nx, int ny, int nz, uint8_t *mask, LevelGeom g) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)nx * ny * nz) return;
+  int i = (int)(l % nx); long long r = l / nx; int j = (int)(r % ny); int k = (int)(r / ny);
+  mask[pidx(g, i, j, k)] = ib[l];
+}
+
+__global__ void k_mask_coarse(const uint8_t *mf, LevelGeom gf, uint8_t *mc, LevelGeom gc) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)gc.nx * gc.ny * gc.nz) return;
+  int I = (int)(l % gc.nx); long long r = l / gc.nx; int J = (int)(r % gc.ny); int K = (int)(r / gc.ny);
+  uint8_t m = 1;
+  for (int c = 0; c < 8; ++c) {
+    int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
+    if (i < gf.nx && j < gf.ny && k < gf.nz && mf[pidx(gf, i, j, k)] == 0) m = 0;
+  }
+  mc[pidx(gc, I, J, K)] = m;
+}
+
+// area fraction of open fine faces on each +x/+y/+z coarse face.
+// Fine open fraction: level 0 from the mask (both sides fluid), else the fine fraction.
+template <typename T>
+__global__ void k_fractions(const uint8_t *mf, const T *ffx, const T *ffy, const T *ffz, LevelGeom gf,
+                            const double *dxf, const double *dyf, const double *dzf, LevelGeom gc,
+                            const double *dxc, const double *dyc, const double *dzc, T *fx, T *fy, T *fz) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)gc.nx * gc.ny * gc.nz) return;
+  int I = (int)(l % gc.nx); long long r = l / gc.nx; int J = (int)(r % gc.ny); int K = (int)(r / gc.ny);
+  long long ic = pidx(gc, I, J, K);
+  auto open_f = [&](int i, int j, int k, int axis) -> double {
+    long long id = pidx(gf, i, j, k);
+    if (ffx == nullptr) {
+      long long s = axis == 0 ? 1 : (axis == 1 ? gf.sy : gf.sz);
+      return (mf[id] == 0 && mf[id + s] == 0) ? 1.0 : 0.0;
+    }
+    const T *f = axis == 0 ? ffx : (axis == 1 ? ffy : ffz);
+    return (double)f[id];
+  };
+  // +x face: fine face between 2I+1 and 2I+2
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  if (I + 1 < gc.nx && 2 * I + 2 < gf.nx) {
+    for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
+      int j = 2 * J + a, k = 2 * K + b;
+      if (j < gf.ny && k < gf.nz) sx += open_f(2 * I + 1, j, k, 0) * dyf[j] * dzf[k];
+    }
+    sx /= dyc[J] * dzc[K];
+  }
+  if (J + 1 < gc.ny && 2 * J + 2 < gf.ny) {
+    for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
+      int i = 2 * I + a, k = 2 * K + b;
+      if (i < gf.nx && k < gf.nz) sy += open_f(i, 2 * J + 1, k, 1) * dxf[i] * dzf[k];
+    }
+    sy /= dxc[I] * dzc[K];
+  }
+  if (K + 1 < gc.nz && 2 * K + 2 < gf.nz) {
+    for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
+      int i = 2 * I + a, j = 2 * J + b;
+      if (i < gf.nx && j < gf.ny) sz += open_f(i, j, 2 * K + 1, 2) * dxf[i] * dyf[j];
+    }
+    sz /= dxc[I] * dyc[J];
+  }
+  fx[ic] = (T)sx; fy[ic] = (T)sy; fz[ic] = (T)sz;
+}
+
+__global__ void k_fluid_stats(const uint8_t *mask, LevelGeom g, const double *dx, const double *dy,
+                              const double *dz, double *out) {
+  __shared__ double s[2][256];
+  double v = 0.0, c = 0.0;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < (long long)g.nx * g.ny * g.nz;
+       l += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+    if (mask[pidx(g, i, j, k)] == 0) { v += dx[i] * dy[j] * dz[k]; c += 1.0; }
+  }
+  s[0][threadIdx.x] = v; s[1][threadIdx.x] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[2 * blockIdx.x] = s[0][0]; out[2 * blockIdx.x + 1] = s[1][0]; }
+}
+
+// Coarsest level: gather fluid cells, assemble the bordered matrix [A 1; V'/vbar 0] and
+// invert it by Gauss-Jordan with partial pivoting (one block, setup only).
+template <typename T>
+__global__ void k_coarsest_setup(LV<T> v, int *cidx, int *ncount, double *M, double *Minv, int cap) {
+  __shared__ int n_s;
+  __shared__ int piv_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    int n = 0;
+    for (int k = 0; k < v.nz; ++k) for (int j = 0; j < v.ny; ++j) for (int i = 0; i < v.nx; ++i) {
+      long long id = vidx(v, i, j, k);
+      if (v.mask[id] == 0 && n < cap) cidx[n++] = (int)id;
+    }
+    n_s = n;
+    *ncount = n;
+  }
+  __syncthreads();
+  const int n = n_s, m = n + 1;
+  for (int q = tid; q < m * m; q += nt) { M[q] = 0.0; Minv[q] = (q / m == q % m) ? 1.0 : 0.0; }
+  __syncthreads();
+  double vbar = 0.0;
+  for (int q = 0; q < n; ++q) {
+    long long id = cidx[q];
+    int i = (int)(id % v.px) - OX; long long r = id / v.px; int j = (int)(r % (v.ny + 2)) - 1; int k = (int)(r / (v.ny + 2)) - 1;
+    vbar += v.dx[i] * v.dy[j] * v.dz[k];
+  }
+  vbar /= (n > 0 ? n : 1);
+  for (int q = tid; q < n; q += nt) {
+    long long id = cidx[q];
+    int i = (int)(id % v.px) - OX; long long r = id / v.px; int j = (int)(r % (v.ny + 2)) - 1; int k = (int)(r / (v.ny + 2)) - 1;
+    T c[6];
+    coefs(v, i, j, k, id, c);
+    const long long nb[6] = {id - 1, id + 1, id - v.sy, id + v.sy, id - v.sz, id + v.sz};
+    double diag = 0.0;
+    for (int d = 0; d < 6; ++d) {
+      if (c[d] == (T)0) continue;
+      diag -= (double)c[d];
+      for (int s2 = 0; s2 < n; ++s2)
+        if (cidx[s2] == nb[d]) { M[q * m + s2] += (double)c[d]; break; }
+    }
+    M[q * m + q] += diag;
+    M[q * m + n] = 1.0;
+    M[n * m + q] = v.dx[i] * v.dy[j] * v.dz[k] / vbar;
+  }
+  __syncthreads();
+  for (int col = 0; col < m; ++col) {
+    if (tid == 0) {
+      int p = col;
+      double best = fabs(M[col * m + col]);
+      for (int rr = col + 1; rr < m; ++rr)
+        if (fabs(M[rr * m + col]) > best) { best = fabs(M[rr * m + col]); p = rr; }
+      piv_s = p;
+    }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != col)
+      for (int q = tid; q < m; q += nt) {
+        double a = M[col * m + q]; M[col * m + q] = M[p * m + q]; M[p * m + q] = a;
+        double b = Minv[col * m + q]; Minv[col * m + q] = Minv[p * m + q]; Minv[p * m + q] = b;
+      }
+    __syncthreads();
+    const double inv = 1.0 / M[col * m + col];
+    __syncthreads();
+    for (int q = tid; q < m; q += nt) { M[col * m + q] *= inv; Minv[col * m + q] *= inv; }
+    __syncthreads();
+    for (int rr = tid; rr < m; rr += nt) {
+      if (rr == col) continue;
+      double f = M[rr * m + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < m; ++q) { M[rr * m + q] -= f * M[col * m + q]; Minv[rr * m + q] -= f * Minv[col * m + q]; }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ solve kernels
+
+// one colour of red-black Gauss-Seidel on fluid rows: e_i += omega (sum - D e_i - rhs) / D
+template <typename T>
+__global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colour, T omega) {
+  int ti = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y, k = blockIdx.z;
+  int i = 2 * ti + ((j + k + colour) & 1);
+  if (i >= v.nx) return;
+  long long id = vidx(v, i, j, k);
+  if (v.mask[id] != 0) return;
+  T c[6];
+  coefs(v, i, j, k, id, c);
+  T D = ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+  if (D == (T)0) return;
+  T rhs = r[id] - (shift ? (T)(*shift) : (T)0);
+  T res = stencil_sum(v, e, id, c) - D * e[id] - rhs;
+  e[id] += omega * res * (T)(1.0f / (float)D);
+}
+
+// ghost rows (Jacobi): gnew = sum_k w_k e[src_k] (+ rhs at the ghost cell)
+template <typename T, typename W>
+__global__ void k_ghost_eval(const long long *src, const long long *dst, const W *w, long long ng, const T *e,
+                             const T *rhs, T *gtmp) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  T s = (T)0;
+  for (int c = 0; c < 8; ++c) {
+    long long q = src[8 * g + c];
+    if (q >= 0) s += (T)w[8 * g + c] * e[q];
+  }
+  if (rhs) s += rhs[dst[g]];
+  gtmp[g] = s;
+}
+
+template <typename T>
+__global__ void k_ghost_store(const long long *dst, long long ng, const T *gtmp, T *e) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < ng) e[dst[g]] = gtmp[g];
+}
+
+// residual of level f restricted to level c: rc = sum_{fluid children} V_f r_f / V_c, and
+// block partial sums of V_c rc for the coarse projection
+template <typename T>
+__global__ void k_restrict(LV<T> f, const T *e, const T *r, const double *shift, LV<T> cv, T *rc, double *partials) {
+  __shared__ double sm[256];
+  double acc_all = 0.0;
+  const long long nc = (long long)cv.nx * cv.ny * cv.nz;
+  const T sh = shift ? (T)(*shift) : (T)0;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nc; l += (long long)gridDim.x * blockDim.x) {
+    int I = (int)(l % cv.nx); long long q = l / cv.nx; int J = (int)(q % cv.ny); int K = (int)(q / cv.ny);
+    long long ic = vidx(cv, I, J, K);
+    if (cv.mask[ic] != 0) { rc[ic] = (T)0; continue; }
+    double acc = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
+      if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
+      long long id = vidx(f, i, j, k);
+      if (f.mask[id] != 0) continue;
+      T cf[6];
+      coefs(f, i, j, k, id, cf);
+      T D = ((cf[0] + cf[1]) + (cf[2] + cf[3])) + (cf[4] + cf[5]);
+      T res = (r[id] - sh) - (stencil_sum(f, e, id, cf) - D * e[id]);
+      acc += f.dx[i] * f.dy[j] * f.dz[k] * (double)res;
+    }
+    double vc = cv.dx[I] * cv.dy[J] * cv.dz[K];
+    rc[ic] = (T)(acc / vc);
+    acc_all += acc;
+  }
+  sm[threadIdx.x] = acc_all;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
+// deterministic sum of nb partials (stride `stride`, offset `off`) in one block
+__device__ double block_sum_partials(const double *p, int nb, int stride, int off) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += p[b * stride + off];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  double out = sm[0];
+  __syncthreads();
+  return out;
+}
+
+__global__ void k_finalize_shift(const double *partials, int nb, double fluid_vol, double *shift) {
+  double s = block_sum_partials(partials, nb, 1, 0);
+  if (threadIdx.x == 0) *shift = fluid_vol > 0 ? s / fluid_vol : 0.0;
+}
+
+template <typename T>
+__global__ void k_prolong(LV<T> cv, const T *ec, LV<T> f, T *ef, const int8_t *offx, const int8_t *offy,
+                          const int8_t *offz, const double *tx, const double *ty, const double *tz) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y, k = blockIdx.z;
+  if (i >= f.nx) return;
+  long long id = vidx(f, i, j, k);
+  if (f.mask[id] != 0) return;
+  int I = i >> 1, J = j >> 1, K = k >> 1;
+  double wx[2] = {1.0 - tx[i], tx[i]}, wy[2] = {1.0 - ty[j], ty[j]}, wz[2] = {1.0 - tz[k], tz[k]};
+  int ox = offx[i], oy = offy[j], oz = offz[k];
+  double s = 0.0, ws = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    int a = c & 1, b = (c >> 1) & 1, d = (c >> 2) & 1;
+    double w = wx[a] * wy[b] * wz[d];
+    if (w == 0.0) continue;
+    long long ic = vidx(cv, I + a * ox, J + b * oy, K + d * oz);
+    if (cv.mask[ic] != 0) continue;
+    s += w * (double)ec[ic];
+    ws += w;
+  }
+  if (ws > 0.0) ef[id] += (T)(s / ws);
+}
+
+// bordered coarsest solve: [e; lambda] = Minv [r; 0]
+template <typename T>
+__global__ void k_coarsest(const double *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
+  __shared__ double rs[MAX_COARSE + 1];
+  const int n = *ncount, m = n + 1;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = (double)r[cidx[q]];
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += Minv[q * m + c] * rs[c];
+    e[cidx[q]] = (T)s;
+  }
+}
+
+// FP64 fine residual r = b - lambda - A p on fluid rows; optional FP32 copy; block partials
+// (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}]
+__global__ void k_residual64(LV<double> v, const double *p, const double *b, const double *lambda, float *r32,
+                             double *partials) {
+  __shared__ double sm[3][REDUCE_THREADS];
+  const double lam = *lambda;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  const long long rows = (long long)v.ny * v.nz;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    int j = (int)(row % v.ny), k = (int)(row / v.ny);
+    for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
+      long long id = vidx(v, i, j, k);
+      if (v.mask[id] != 0) continue;
+      double c[6];
+      coefs(v, i, j, k, id, c);
+      double D = ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+      double res = (b[id] - lam) - (stencil_sum(v, p, id, c) - D * p[id]);
+      if (r32) r32[id] = (float)res;
+      a0 += v.dx[i] * v.dy[j] * v.dz[k] * res;
+      a1 += res;
+      a2 += res * res;
+    }
+  }
+  sm[0][threadIdx.x] = a0; sm[1][threadIdx.x] = a1; sm[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sm[q][0];
+}
+
+// ghost rows r_G = sum w v - g; block partials of (s_G r_G)^2 at gpart[b]
+__global__ void k_ghost_resid64(const long long *src, const long long *dst, const double *w, const double *scale,
+                                long long ng, const double *p, float *r32, double *gpart) {
+  __shared__ double sm[REDUCE_THREADS];
+  double a = 0.0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      long long q = src[8 * g + c];
+      if (q >= 0) s += w[8 * g + c] * p[q];
+    }
+    double rg = s - p[dst[g]];
+    if (r32) r32[dst[g]] = (float)rg;
+    double sr = scale[g] * rg;
+    a += sr * sr;
+  }
+  sm[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gpart[blockIdx.x] = sm[0];
+}
+
+// mu = sum V r / V_F; ||S P r||^2 = sum r^2 - 2 mu sum r + N_F mu^2 + sum (s r_G)^2;
+// lambda += mu when update_lambda
+__global__ void k_finalize_resid(const double *partials, int nb, const double *gpart, int ngb, double *scal,
+                                 int update_lambda) {
+  double sv = block_sum_partials(partials, nb, 3, 0);
+  double s1 = block_sum_partials(partials, nb, 3, 1);
+  double s2 = block_sum_partials(partials, nb, 3, 2);
+  double sg = ngb > 0 ? block_sum_partials(gpart, ngb, 1, 0) : 0.0;
+  if (threadIdx.x == 0) {
+    double mu = sv / scal[S_FLUIDVOL];
+    double n2 = s2 - 2.0 * mu * s1 + scal[S_NF] * mu * mu;
+    scal[S_MU] = mu;
+    scal[S_NORM2] = (n2 > 0.0 ? n2 : 0.0) + sg;
+    if (update_lambda) scal[S_LAMBDA] += mu;
+  }
+}
+
+__global__ void k_update_p(double *p, const float *e, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    p[q] += (double)e[q];
+}
+
+__global__ void k_gauge_sum(LV<double> v, const double *p, double *partials) {
+  __shared__ double sm[REDUCE_THREADS];
+  double a = 0.0;
+  const long long rows = (long long)v.ny * v.nz;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    int j = (int)(row % v.ny), k = (int)(row / v.ny);
+    for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
+      long long id = vidx(v, i, j, k);
+      if (v.mask[id] == 0) a += v.dx[i] * v.dy[j] * v.dz[k] * p[id];
+    }
+  }
+  sm[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
+__global__ void k_gauge_finalize(const double *partials, int nb, double *scal) {
+  double s = block_sum_partials(partials, nb, 1, 0);
+  if (threadIdx.x == 0) scal[S_MEANP] = s / scal[S_FLUIDVOL];
+}
+
+// pack user [k][j][i] arrays into padded arrays; unpack with the gauge applied
+__global__ void k_pack(const double *src, LevelGeom g, double *dst) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)g.nx * g.ny * g.nz) return;
+  int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+  dst[pidx(g, i, j, k)] = src[l];
+}
+
+__global__ void k_unpack_gauge(const double *src, const uint8_t *mask, LevelGeom g, const double *scal, double *dst) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)g.nx * g.ny * g.nz) return;
+  int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+  long long id = pidx(g, i, j, k);
+  dst[l] = mask[id] == 1 ? 0.0 : src[id] - scal[S_MEANP];
+}
+
+// mask solid cells of the packed p to zero (they are never read, keep them finite)
+__global__ void k_zero_solid(double *p, const uint8_t *mask, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    if (mask[q] == 1) p[q] = 0.0;
+}
+
+__global__ void k_ghost_src(const long long *ref, const long long *cell, long long ng, LevelGeom g, long long *src,
+                            long long *dst, const double *w, float *w32) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= ng * 8) return;
+  auto tp = [&](long long l) {
+    int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+    return pidx(g, i, j, k);
+  };
+  long long l = ref[q];
+  src[q] = l >= 0 ? tp(l) : -1;
+  w32[q] = (float)w[q];
+  if ((q & 7) == 0) dst[q >> 3] = tp(cell[q >> 3]);
+}
+
+template <typename T>
+cudaError_t alloc_zero(void **p, long long n, cudaStream_t st) {
+  cudaError_t e = cudaMalloc(p, (size_t)(n ? n : 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(*p, 0, (size_t)(n ? n : 1) * sizeof(T), st);
+}
+
+}  // namespace
+
+void free_hierarchy(Hierarchy *h) {
+  if (!h) return;
+  for (Level &L : h->lv) {
+    void *ps[] = {L.mask, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt};
+    for (void *p : ps) if (p) cudaFree(p);
+  }
+  void *ps[] = {h->p64, h->b64, h->minv, h->cidx, h->dncoarse, h->c64, h->gsrc, h->gdst, h->gw64, h->gw32, h->gtmp};
+  for (void *p : ps) if (p) cudaFree(p);
+  if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
+  delete h;
+}
+
+// ------------------------------------------------------------------ hierarchy build
+
+template <typename T>
+static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) {
+  Hierarchy *h = new Hierarchy();
+  h->elem = sizeof(T);
+  auto fail = [&](cudaError_t e, const char *w) { free_hierarchy(h); return check(e, w); };
+#define HTRY(call) do { cudaError_t e__ = (call); if (e__ != cudaSuccess) return fail(e__, #call); } while (0)
+  std::vector<double> fx(t->xf), fy(t->yf), fz(t->zf);
+  double *dfaces = nullptr;
+  while (true) {
+    Level L;
+    L.g = make_geom((int)fx.size() - 1, (int)fy.size() - 1, (int)fz.size() - 1);
+    const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
+    HTRY(alloc_zero<uint8_t>((void **)&L.mask, L.g.ntot, st));
+    HTRY(cudaMemsetAsync(L.mask, 1, L.g.ntot, st));
+    HTRY(alloc_zero<T>(&L.e, L.g.ntot, st));
+    HTRY(alloc_zero<T>(&L.r, L.g.ntot, st));
+    HTRY(cudaMalloc(&L.c1d, sizeof(T) * 2 * (nx + ny + nz)));
+    HTRY(cudaMalloc((void **)&L.w1d, sizeof(double) * (nx + ny + nz)));
+    HTRY(cudaMalloc((void **)&L.cen, sizeof(double) * (nx + ny + nz)));
+    HTRY(cudaMalloc((void **)&dfaces, sizeof(double) * (nx + ny + nz + 3)));
+    HTRY(cudaMemcpyAsync(dfaces, fx.data(), sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, st));
+    HTRY(cudaMemcpyAsync(dfaces + nx + 1, fy.data(), sizeof(double) * (ny + 1), cudaMemcpyHostToDevice, st));
+    HTRY(cudaMemcpyAsync(dfaces + nx + ny + 2, fz.data(), sizeof(double) * (nz + 1), cudaMemcpyHostToDevice, st));
+    T *c = (T *)L.c1d;
+    k_axis_level<T><<<nblk(nx, 128), 128, 0, st>>>(dfaces, nx, c, c + nx, L.w1d, L.cen);
+    k_axis_level<T><<<nblk(ny, 128), 128, 0, st>>>(dfaces + nx + 1, ny, c + 2 * nx, c + 2 * nx + ny, L.w1d + nx,
+                                                    L.cen + nx);
+    k_axis_level<T><<<nblk(nz, 128), 128, 0, st>>>(dfaces + nx + ny + 2, nz, c + 2 * nx + 2 * ny,
+                                                    c + 2 * nx + 2 * ny + nz, L.w1d + nx + ny, L.cen + nx + ny);
+    HTRY(cudaGetLastError());
+    HTRY(cudaStreamSynchronize(st));
+    cudaFree(dfaces);
+    dfaces = nullptr;
+    h->lv.push_back(L);
+    const long long cells = (long long)nx * ny * nz;
+    if (cells <= MAX_COARSE || (nx == 1 && ny == 1 && nz == 1)) break;
+    auto coarsen = [](const std::vector<double> &f) {
+      int n = (int)f.size() - 1, nc = (n + 1) / 2;
+      std::vector<double> c(nc + 1);
+      for (int I = 0; I < nc; ++I) c[I] = f[2 * I];
+      c[nc] = f[n];
+      return c;
+    };
+    fx = coarsen(fx); fy = coarsen(fy); fz = coarsen(fz);
+  }
+  const int nl = (int)h->lv.size();
+  // masks, fractions, prolongation tables
+  {
+    Level &L0 = h->lv[0];
+    const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
+    k_mask0<<<nblk(n0, 256), 256, 0, st>>>(t->iblank, L0.g.nx, L0.g.ny, L0.g.nz, L0.mask, L0.g);
+  }
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level &F = h->lv[l], &C = h->lv[l + 1];
+    const long long nc = (long long)C.g.nx * C.g.ny * C.g.nz;
+    k_mask_coarse<<<nblk(nc, 256), 256, 0, st>>>(F.mask, F.g, C.mask, C.g);
+    HTRY(alloc_zero<T>(&C.fx, C.g.ntot, st));
+    HTRY(alloc_zero<T>(&C.fy, C.g.ntot, st));
+    HTRY(alloc_zero<T>(&C.fz, C.g.ntot, st));
+    const double *wf = F.w1d, *wc = C.w1d;
+    k_fractions<T><<<nblk(nc, 256), 256, 0, st>>>(F.mask, (const T *)F.fx, (const T *)F.fy, (const T *)F.fz, F.g, wf,
+                                                  wf + F.g.nx, wf + F.g.nx + F.g.ny, C.g, wc, wc + C.g.nx,
+                                                  wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz);
+    const int nf = F.g.nx + F.g.ny + F.g.nz;
+    HTRY(cudaMalloc((void **)&F.poff, nf));
+    HTRY(cudaMalloc((void **)&F.pt, sizeof(double) * nf));
+    k_prolong_axis<<<nblk(F.g.nx, 128), 128, 0, st>>>(F.cen, F.g.nx, C.cen, C.g.nx, F.poff, F.pt);
+    k_prolong_axis<<<nblk(F.g.ny, 128), 128, 0, st>>>(F.cen + F.g.nx, F.g.ny, C.cen + C.g.nx, C.g.ny,
+                                                      F.poff + F.g.nx, F.pt + F.g.nx);
+    k_prolong_axis<<<nblk(F.g.nz, 128), 128, 0, st>>>(F.cen + F.g.nx + F.g.ny, F.g.nz, C.cen + C.g.nx + C.g.ny, C.g.nz,
+                                                      F.poff + F.g.nx + F.g.ny, F.pt + F.g.nx + F.g.ny);
+    HTRY(cudaGetLastError());
+  }
+  // fluid volume per level
+  {
+    double *tmp = nullptr;
+    HTRY(cudaMalloc((void **)&tmp, sizeof(double) * 2 * 152));
+    std::vector<double> hv(2 * 152);
+    for (int l = 0; l < nl; ++l) {
+      Level &L = h->lv[l];
+      k_fluid_stats<<<152, 256, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx, L.w1d + L.g.nx + L.g.ny, tmp);
+      cudaError_t e = cudaMemcpyAsync(hv.data(), tmp, sizeof(double) * 2 * 152, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { cudaFree(tmp); return fail(e, "fluid stats"); }
+      double v = 0.0, c = 0.0;
+      for (int b = 0; b < 152; ++b) { v += hv[2 * b]; c += hv[2 * b + 1]; }
+      L.fluid_vol = v;
+      L.nfluid = (long long)c;
+    }
+    cudaFree(tmp);
+  }
+  // coarsest bordered inverse
+  {
+    Level &Lc = h->lv[nl - 1];
+    const int m = MAX_COARSE + 1;
+    double *M = nullptr;
+    int *nc = nullptr;
+    HTRY(cudaMalloc((void **)&M, sizeof(double) * m * m));
+    HTRY(cudaMalloc((void **)&h->minv, sizeof(double) * m * m));
+    HTRY(cudaMalloc((void **)&h->cidx, sizeof(int) * (MAX_COARSE + 1)));
+    HTRY(cudaMalloc((void **)&nc, sizeof(int) * 2));
+    h->dncoarse = nc;
+    k_coarsest_setup<T><<<1, 256, 0, st>>>(view<T>(Lc), h->cidx, nc, M, h->minv, MAX_COARSE);
+    HTRY(cudaGetLastError());
+    HTRY(cudaMemcpyAsync(&h->ncoarse, nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HTRY(cudaStreamSynchronize(st));
+    cudaFree(M);
+  }
+  // fine FP64 arrays and solver-side ghost rows
+  {
+    Level &L0 = h->lv[0];
+    HTRY(alloc_zero<double>((void **)&h->p64, L0.g.ntot, st));
+    HTRY(alloc_zero<double>((void **)&h->b64, L0.g.ntot, st));
+    const long long ng = t->nghost;
+    HTRY(cudaMalloc((void **)&h->gsrc, sizeof(long long) * 8 * (ng ? ng : 1)));
+    HTRY(cudaMalloc((void **)&h->gdst, sizeof(long long) * (ng ? ng : 1)));
+    HTRY(cudaMalloc((void **)&h->gw32, sizeof(float) * 8 * (ng ? ng : 1)));
+    HTRY(cudaMalloc((void **)&h->gtmp, sizeof(double) * (ng ? ng : 1)));
+    h->gw64 = nullptr;
+    if (ng) k_ghost_src<<<nblk(8 * ng, 256), 256, 0, st>>>(t->gref, t->gcell, ng, L0.g, h->gsrc, h->gdst, t->gw, h->gw32);
+    HTRY(cudaGetLastError());
+    HTRY(cudaStreamSynchronize(st));
+  }
+#undef HTRY
+  *out = h;
+  return IBM_OK;
+}
+
+// ------------------------------------------------------------------ solve driver
+
+namespace {
+
+struct Solver {
+  ibm_ctx *ctx;
+  ibm_tables *t;
+  Hierarchy *h;
+  cudaStream_t st;
+  int nu1, nu2;
+  double omega;
+  int *d_ncoarse;
+};
+
+template <typename T>
+void smooth_level(Solver &S, int l, T *e, const T *r, const double *shift, bool fine, const T *ghost_rhs, int sweeps) {
+  Level &L = S.h->lv[l];
+  LV<T> v = view<T>(L);
+  dim3 grid(nblk((L.g.nx + 1) / 2, 128), L.g.ny, L.g.nz);
+  const long long ng = S.t->nghost;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour)
+      k_rbgs<T><<<grid, 128, 0, S.st>>>(v, e, r, shift, colour, (T)S.omega);
+    if (fine && ng > 0) {
+      if (sizeof(T) == 8)
+        k_ghost_eval<T, double><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, ng, e, ghost_rhs,
+                                                                  (T *)S.h->gtmp);
+      else
+        k_ghost_eval<T, float><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, ng, e, ghost_rhs,
+                                                                 (T *)S.h->gtmp);
+      k_ghost_store<T><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gdst, ng, (const T *)S.h->gtmp, e);
+    }
+  }
+}
+
+// V-cycle for level l: e_l (in/out) approximately solves A_l e_l = r_l - shift_l
+template <typename T>
+void vcycle(Solver &S, int l, T *e, const T *r, const double *shift, const T *ghost_rhs) {
+  Hierarchy *h = S.h;
+  const int nl = (int)h->lv.size();
+  if (l == nl - 1) {
+    k_coarsest<T><<<1, 128, 0, S.st>>>(h->minv, h->cidx, S.d_ncoarse, r, e);
+    return;
+  }
+  const bool fine = (l == 0);
+  smooth_level<T>(S, l, e, r, shift, fine, ghost_rhs, S.nu1);
+  Level &F = h->lv[l], &C = h->lv[l + 1];
+  const long long nc = (long long)C.g.nx * C.g.ny * C.g.nz;
+  const int nb = (int)std::min<long long>(nblk(nc, 256), REDUCE_BLOCKS);
+  T *ec = (T *)C.e, *rc = (T *)C.r;
+  k_restrict<T><<<nb, 256, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, S.ctx->partials);
+  double *cshift = S.ctx->scal + S_LEVEL_SHIFT + (l + 1);
+  k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, nb, C.fluid_vol, cshift);
+  cudaMemsetAsync(ec, 0, sizeof(T) * C.g.ntot, S.st);
+  vcycle<T>(S, l + 1, ec, rc, cshift, nullptr);
+  dim3 gp(nblk(F.g.nx, 128), F.g.ny, F.g.nz);
+  const int nxf = F.g.nx, nyf = F.g.ny;
+  k_prolong<T><<<gp, 128, 0, S.st>>>(view<T>(C), ec, view<T>(F), e, F.poff, F.poff + nxf, F.poff + nxf + nyf, F.pt,
+                                     F.pt + nxf, F.pt + nxf + nyf);
+  smooth_level<T>(S, l, e, r, shift, fine, ghost_rhs, S.nu2);
+}
+
+LV<double> fine_view64(Hierarchy *h) {
+  Level &L0 = h->lv[0];
+  LV<double> v;
+  v.nx = L0.g.nx; v.ny = L0.g.ny; v.nz = L0.g.nz; v.px = L0.g.px; v.sy = L0.g.sy; v.sz = L0.g.sz;
+  v.mask = L0.mask;
+  v.fx = v.fy = v.fz = nullptr;
+  v.dx = L0.w1d; v.dy = L0.w1d + v.nx; v.dz = L0.w1d + v.nx + v.ny;
+  const double *c = h->c64;
+  v.cxm = c; v.cxp = c + v.nx; v.cym = c + 2 * v.nx; v.cyp = v.cym + v.ny; v.czm = v.cyp + v.ny; v.czp = v.czm + v.nz;
+  return v;
+}
+
+void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
+  LV<double> v = fine_view64(S.h);
+  double *part = S.ctx->partials;
+  k_residual64<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.ctx->scal + S_LAMBDA, r32, part);
+  const long long ng = S.t->nghost;
+  const int ngb = 152;
+  double *gpart = part + 3 * REDUCE_BLOCKS;
+  if (ng > 0)
+    k_ghost_resid64<<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, ng, p, r32, gpart);
+  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, ng > 0 ? ngb : 0, S.ctx->scal,
+                                        update_lambda ? 1 : 0);
+}
+
+}  // namespace
+
+ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
+  if (t->hier[precision]) return IBM_OK;
+  Hierarchy *h = nullptr;
+  ibm_status s = precision == 0 ? build_hierarchy_t<double>(t, st, &h) : build_hierarchy_t<float>(t, st, &h);
+  if (s != IBM_OK) return s;
+  // FP64 fine coefficients
+  Level &L0 = h->lv[0];
+  const int n = L0.g.nx + L0.g.ny + L0.g.nz;
+  double *c64 = nullptr, *df = nullptr;
+  IBM_TRY(cudaMalloc((void **)&c64, sizeof(double) * 2 * n));
+  IBM_TRY(cudaMalloc((void **)&df, sizeof(double) * (n + 3)));
+  IBM_TRY(cudaMemcpyAsync(df, t->xf.data(), sizeof(double) * (L0.g.nx + 1), cudaMemcpyHostToDevice, st));
+  IBM_TRY(cudaMemcpyAsync(df + L0.g.nx + 1, t->yf.data(), sizeof(double) * (L0.g.ny + 1), cudaMemcpyHostToDevice, st));
+  IBM_TRY(cudaMemcpyAsync(df + L0.g.nx + L0.g.ny + 2, t->zf.data(), sizeof(double) * (L0.g.nz + 1),
+                          cudaMemcpyHostToDevice, st));
+  double *w = nullptr, *c = nullptr;
+  IBM_TRY(cudaMalloc((void **)&w, sizeof(double) * n));
+  IBM_TRY(cudaMalloc((void **)&c, sizeof(double) * n));
+  const int nx = L0.g.nx, ny = L0.g.ny, nz = L0.g.nz;
+  k_axis_level<double><<<nblk(nx, 128), 128, 0, st>>>(df, nx, c64, c64 + nx, w, c);
+  k_axis_level<double><<<nblk(ny, 128), 128, 0, st>>>(df + nx + 1, ny, c64 + 2 * nx, c64 + 2 * nx + ny, w + nx, c + nx);
+  k_axis_level<double><<<nblk(nz, 128), 128, 0, st>>>(df + nx + ny + 2, nz, c64 + 2 * nx + 2 * ny,
+                                                      c64 + 2 * nx + 2 * ny + nz, w + nx + ny, c + nx + ny);
+  IBM_TRY(cudaGetLastError());
+  IBM_TRY(cudaStreamSynchronize(st));
+  cudaFree(df); cudaFree(w); cudaFree(c);
+  h->c64 = c64;
+  t->hier[precision] = h;
+  return IBM_OK;
+}
+
+ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
+                      const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st) {
+  const int prec = opts->precision;
+  ibm_status s = build_hierarchy(t, prec, st);
+  if (s != IBM_OK) return s;
+  Hierarchy *h = t->hier[prec];
+  Level &L0 = h->lv[0];
+  const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
+  Solver S{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
+  // inputs
+  k_pack<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, h->b64);
+  k_pack<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, h->p64);
+  k_zero_solid<<<1216, 256, 0, st>>>(h->p64, L0.mask, L0.g.ntot);
+  double hs[NSCAL] = {0};
+  hs[S_FLUIDVOL] = L0.fluid_vol;
+  hs[S_NF] = (double)L0.nfluid;
+  IBM_TRY(cudaMemcpyAsync(ctx->scal, hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  // ||S P b||: residual of p = 0 with lambda = 0
+  {
+    double *pz = (double *)h->lv[0].e;
+    if (prec == 0) {
+      // level-0 e is FP64 in this mode; use it as a zero array (restored below)
+      IBM_TRY(cudaMemsetAsync(pz, 0, sizeof(double) * L0.g.ntot, st));
+      fine_residual(S, pz, nullptr, false);
+    } else {
+      double *tmpz = nullptr;
+      IBM_TRY(cudaMalloc((void **)&tmpz, sizeof(double) * L0.g.ntot));
+      IBM_TRY(cudaMemsetAsync(tmpz, 0, sizeof(double) * L0.g.ntot, st));
+      fine_residual(S, tmpz, nullptr, false);
+      IBM_TRY(cudaStreamSynchronize(st));
+      cudaFree(tmpz);
+    }
+  }
+  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  IBM_TRY(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(ctx->hscal[S_NORM2]);
+  const double denom = bnorm > 0 ? bnorm : 1.0;
+  // initial ghost values consistent with p, and the initial residual
+  const long long ng = t->nghost;
+  if (ng > 0) {
+    k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, ng, h->p64, nullptr, h->gtmp);
+    k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, h->p64);
+  }
+  IBM_TRY(cudaGetLastError());
+  int cycles = 0;
+  double rel = 0.0;
+  int hl = 0;
+  ibm_status result = IBM_ERR_NOT_CONVERGED;
+  float *r32 = prec == 1 ? (float *)L0.r : nullptr;
+  fine_residual(S, h->p64, r32, true);
+  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  IBM_TRY(cudaStreamSynchronize(st));
+  rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
+  double rel0 = rel;
+  if (rel <= tol) result = IBM_OK;
+  while (result != IBM_OK && cycles < opts->max_cycles) {
+    if (prec == 0) {
+      vcycle<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, nullptr);
+      fine_residual(S, h->p64, nullptr, true);
+    } else {
+      float *e32 = (float *)L0.e;
+      for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
+        if (q == 0) IBM_TRY(cudaMemsetAsync(e32, 0, sizeof(float) * L0.g.ntot, st));
+        vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
+      }
+      k_update_p<<<1216, 256, 0, st>>>(h->p64, e32, L0.g.ntot);
+      fine_residual(S, h->p64, r32, true);
+    }
+    IBM_TRY(cudaGetLastError());
+    IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    ++cycles;
+    rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
+    if (info && info->resid_history && hl < info->history_cap) info->resid_history[hl++] = rel;
+    if (!std::isfinite(rel) || rel > 1e6 * std::max(rel0, 1.0)) { result = IBM_ERR_DIVERGED; break; }
+    if (rel <= tol) result = IBM_OK;
+  }
+  // gauge and unpack
+  k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
+  k_gauge_finalize<<<1, 256, 0, st>>>(ctx->partials, REDUCE_BLOCKS, ctx->scal);
+  k_unpack_gauge<<<nblk(n0, 256), 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
+  IBM_TRY(cudaGetLastError());
+  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  IBM_TRY(cudaStreamSynchronize(st));
+  if (info) {
+    info->cycles = cycles;
+    info->history_len = hl;
+    info->rel_resid = rel;
+    info->lambda = ctx->hscal[S_LAMBDA];
+  }
+  return result;
+}
+
+}  // namespace ibm

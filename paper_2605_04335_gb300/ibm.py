@@ -1,0 +1,234 @@
+"""ctypes binding of include/ibm_poisson.h: argument marshalling only.
+
+Every function keeps the C name and forwards plain pointers and sizes; device buffers are
+torch CUDA tensors (PyTorch supplies device memory and streams, nothing else).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+IBM_OK = 0
+IBM_ERR_NOT_CONVERGED = 5
+STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_OOM", 3: "IBM_ERR_CUDA", 4: "IBM_ERR_NO_FLUID",
+          5: "IBM_ERR_NOT_CONVERGED", 6: "IBM_ERR_DIVERGED", 7: "IBM_ERR_TIMEOUT", 8: "IBM_ERR_NOT_IMPLEMENTED",
+          9: "IBM_ERR_CAPACITY"}
+
+
+class IbmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = "%s failed: %s" % (where, STATUS.get(status, status))
+        if status == 3 and _LIB is not None:
+            msg += " (" + _LIB.ibm_last_cuda_error().decode() + ")"
+        super().__init__(msg)
+        self.status = status
+
+
+class ibm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("xf", C.c_void_p), ("yf", C.c_void_p), ("zf", C.c_void_p)]
+
+
+class ibm_mesh(C.Structure):
+    _fields_ = [("nverts", C.c_int32), ("ntris", C.c_int32), ("verts", C.c_void_p), ("tris", C.c_void_p),
+                ("closed", C.c_int32)]
+
+
+class ibm_solve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32), ("max_cycles", C.c_int32),
+                ("inner_cycles", C.c_int32), ("use_graph", C.c_int32), ("omega", C.c_double)]
+
+
+class ibm_solve_info(C.Structure):
+    _fields_ = [("cycles", C.c_int32), ("history_len", C.c_int32), ("rel_resid", C.c_double),
+                ("lambda_", C.c_double), ("ms_total", C.c_double), ("resid_history", C.c_void_p),
+                ("history_cap", C.c_int32)]
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "lib", "libibmpoisson.so")
+
+
+def load_library():
+    """Load the CUDA library; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError("libibmpoisson.so not built: run __graft_entry__.build() (%s)" % path)
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "ibm_status_str": (C.c_char_p, [I32]),
+        "ibm_last_cuda_error": (C.c_char_p, []),
+        "ibm_ctx_create": (I32, [C.POINTER(P), I32]),
+        "ibm_ctx_destroy": (I32, [P]),
+        "ibm_classify": (I32, [P, C.POINTER(ibm_grid), C.POINTER(ibm_mesh), I32, C.POINTER(P), P]),
+        "ibm_tables_destroy": (I32, [P]),
+        "ibm_tables_counts": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+        "ibm_tables_export": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
+        "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
+        "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != IBM_OK:
+        raise IbmError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------- C-named calls
+
+def ibm_ctx_create(device: int = 0):
+    lib = load_library()
+    h = C.c_void_p()
+    _check(lib.ibm_ctx_create(C.byref(h), device), "ibm_ctx_create")
+    return h
+
+
+def ibm_ctx_destroy(ctx):
+    _check(load_library().ibm_ctx_destroy(ctx), "ibm_ctx_destroy")
+
+
+def ibm_classify(ctx, xf, yf, zf, meshes, stream=None):
+    """Classify the grid (host face arrays) against meshes (objects with verts, tris, closed)."""
+    lib = load_library()
+    keep = []
+    f = [np.ascontiguousarray(a, dtype=np.float64) for a in (xf, yf, zf)]
+    keep += f
+    g = ibm_grid(f[0].size - 1, f[1].size - 1, f[2].size - 1, f[0].ctypes.data, f[1].ctypes.data, f[2].ctypes.data)
+    arr = (ibm_mesh * max(1, len(meshes)))()
+    for q, m in enumerate(meshes):
+        v = np.ascontiguousarray(m.verts, dtype=np.float64)
+        t = np.ascontiguousarray(m.tris, dtype=np.int32)
+        keep += [v, t]
+        arr[q] = ibm_mesh(v.shape[0], t.shape[0], v.ctypes.data, t.ctypes.data, int(m.closed))
+    h = C.c_void_p()
+    _check(lib.ibm_classify(ctx, C.byref(g), arr, len(meshes), C.byref(h), _stream(stream)), "ibm_classify")
+    return h
+
+
+def ibm_tables_counts(tables):
+    v = [C.c_int64() for _ in range(4)]
+    _check(load_library().ibm_tables_counts(tables, *[C.byref(x) for x in v]), "ibm_tables_counts")
+    return tuple(int(x.value) for x in v)
+
+
+def ibm_tables_export(tables, iblank=None, cell=None, bi=None, ip=None, base=None, flags=None, ref=None, w=None,
+                      scale=None, stream=None):
+    _check(load_library().ibm_tables_export(tables, _ptr(iblank), _ptr(cell), _ptr(bi), _ptr(ip), _ptr(base),
+                                            _ptr(flags), _ptr(ref), _ptr(w), _ptr(scale), _stream(stream)),
+           "ibm_tables_export")
+
+
+def ibm_tables_destroy(tables):
+    _check(load_library().ibm_tables_destroy(tables), "ibm_tables_destroy")
+
+
+@dataclass
+class SolveOpts:
+    precision: int = 0
+    nu1: int = 2
+    nu2: int = 2
+    max_cycles: int = 100
+    inner_cycles: int = 1
+    use_graph: int = 1
+    omega: float = 1.0
+
+
+def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, stream=None, history_cap: int = 256,
+                  raise_on_error: bool = True):
+    """Solve in place: rhs, p are CUDA float64 tensors [nz, ny, nx].  Returns a dict report."""
+    lib = load_library()
+    o = opts or SolveOpts()
+    co = ibm_solve_opts(o.precision, o.nu1, o.nu2, o.max_cycles, o.inner_cycles, o.use_graph, o.omega)
+    hist = np.zeros(max(1, history_cap))
+    info = ibm_solve_info(0, 0, 0.0, 0.0, 0.0, hist.ctypes.data, history_cap)
+    s = lib.poisson_solve(ctx, tables, _ptr(rhs), float(tol), _ptr(p), C.byref(co), C.byref(info), _stream(stream))
+    rep = {"status": STATUS.get(s, s), "cycles": info.cycles, "rel_resid": info.rel_resid, "lambda": info.lambda_,
+           "ms_total": info.ms_total, "history": hist[:info.history_len].copy()}
+    if raise_on_error and s != IBM_OK:
+        raise IbmError(s, "poisson_solve (%s)" % rep)
+    return rep
+
+
+# ----------------------------------------------------------------------------- conveniences
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.h = ibm_ctx_create(device)
+
+    def close(self):
+        if self.h is not None:
+            ibm_ctx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Tables:
+    """Classified grid owned by a Context; export() returns torch CUDA tensors."""
+
+    def __init__(self, ctx: Context, xf, yf, zf, meshes, stream=None):
+        self.ctx = ctx
+        self.shape = (len(zf) - 1, len(yf) - 1, len(xf) - 1)
+        self.h = ibm_classify(ctx.h, xf, yf, zf, meshes, stream)
+        self.ncell, self.nfluid, self.nghost, self.nsolid = ibm_tables_counts(self.h)
+
+    def export(self, stream=None) -> dict:
+        import torch
+        dev = torch.device("cuda")
+        ng = max(self.nghost, 1)
+        out = {"iblank": torch.empty(self.shape, dtype=torch.uint8, device=dev),
+               "cell": torch.empty(ng, dtype=torch.int64, device=dev),
+               "bi": torch.empty((ng, 3), dtype=torch.float64, device=dev),
+               "ip": torch.empty((ng, 3), dtype=torch.float64, device=dev),
+               "base": torch.empty((ng, 3), dtype=torch.int32, device=dev),
+               "flags": torch.empty(ng, dtype=torch.int32, device=dev),
+               "ref": torch.empty((ng, 8), dtype=torch.int64, device=dev),
+               "w": torch.empty((ng, 8), dtype=torch.float64, device=dev),
+               "scale": torch.empty(ng, dtype=torch.float64, device=dev)}
+        ibm_tables_export(self.h, **out, stream=stream)
+        if self.nghost == 0:
+            for k in list(out):
+                if k != "iblank":
+                    out[k] = out[k][:0]
+        return out
+
+    def solve(self, rhs, p, tol=1e-10, opts: SolveOpts | None = None, stream=None, **kw):
+        return poisson_solve(self.ctx.h, self.h, rhs, tol, p, opts, stream, **kw)
+
+    def close(self):
+        if self.h is not None:
+            ibm_tables_destroy(self.h)
+            self.h = None

@@ -1,0 +1,111 @@
+"""GPU pressure solve vs the oracle: relative L2 <= 1e-8 after the gauge, both at 1e-10."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import classify as OC
+from oracle import solve as OS
+from oracle import system as OSys
+from oracle.grid import Grid
+from tests.gpu_util import require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+PARITY = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    import paper_2605_04335_gb300 as pkg
+    c = pkg.Context(0)
+    yield pkg, c
+    c.close()
+
+
+def _solve_gpu(pkg, T, b, prec, **kw):
+    rhs = torch.from_numpy(b).cuda()
+    p = torch.zeros_like(rhs)
+    rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec, **kw))
+    return p.cpu().numpy(), rep
+
+
+def _parity(ctx, xf, yf, zf, meshes, seed, oracle="gmres"):
+    pkg, c = ctx
+    g = Grid(xf, yf, zf)
+    ib, G = OC.classify(g, meshes)
+    b = synth.rhs_divergence(xf, yf, zf, seed)
+    p_o, lam_o = (OS.solve_gmres if oracle == "gmres" else OS.solve_sparse)(g, ib, G, b)
+    T = pkg.Tables(c, xf, yf, zf, meshes)
+    fl = ib == 0
+    out = {}
+    for prec in (0, 1):
+        p, rep = _solve_gpu(pkg, T, b, prec)
+        assert rep["status"] == "IBM_OK" and rep["rel_resid"] <= TOL
+        # the residual the oracle computes for the GPU's p, on the oracle's own tables
+        assert OSys.relative_residual(g, ib, G, b, p) <= 1.05 * TOL
+        err = np.linalg.norm((p - p_o)[fl]) / np.linalg.norm(p_o[fl])
+        assert err <= PARITY, (prec, err, rep)
+        if len(G):
+            gerr = np.max(np.abs(p.ravel()[G.cell] - p_o.ravel()[G.cell])) / np.max(np.abs(p_o[fl]))
+            assert gerr <= 10 * PARITY
+        assert abs(rep["lambda"] - lam_o) <= 1e-6 * max(1.0, abs(lam_o))
+        out[prec] = (err, rep)
+    T.close()
+    return out
+
+
+def test_sphere_stretched_24_sparse_oracle(ctx):
+    f = synth.faces_tanh(24, 2.0)
+    _parity(ctx, f, f, f, [synth.octa_sphere(4, (0.5, 0.48, 0.52), 0.22)], 1, "sparse")
+
+
+def test_cfg1_sphere_64(ctx):
+    p = synth.cfg1(64)
+    _parity(ctx, p.xf, p.yf, p.zf, p.meshes, p.seed)
+
+
+def test_ragged_stretched_ellipsoid(ctx):
+    xf, yf, zf = synth.faces_tanh(37, 2.0), synth.faces_tanh(29, 1.5), synth.faces_uniform(41)
+    _parity(ctx, xf, yf, zf, [synth.ellipsoid(4, (0.25, 0.12, 0.1), 33.0, (0.45, 0.5, 0.5))], 7)
+
+
+def test_no_body_ragged(ctx):
+    _parity(ctx, synth.faces_uniform(33), synth.faces_tanh(24, 2.0), synth.faces_uniform(20), [], 3)
+
+
+def test_cfg2_full_256_residual_property(ctx):
+    """At the full 256^3 size the oracle cannot solve in seconds; it certifies the GPU result
+    by evaluating its own residual of the GPU's p (any size), for both precisions."""
+    pkg, c = ctx
+    pr = synth.cfg2(256)
+    g = Grid(pr.xf, pr.yf, pr.zf)
+    ib, G = OC.classify(g, pr.meshes)
+    b = pr.rhs()
+    T = pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes)
+    ps = {}
+    for prec in (0, 1):
+        p, rep = _solve_gpu(pkg, T, b, prec)
+        assert rep["status"] == "IBM_OK"
+        assert OSys.relative_residual(g, ib, G, b, p) <= 1.05 * TOL
+        ps[prec] = p
+    fl = ib == 0
+    assert np.linalg.norm((ps[0] - ps[1])[fl]) / np.linalg.norm(ps[0][fl]) <= PARITY
+    T.close()
+
+
+def test_warm_start_and_not_converged(ctx):
+    pkg, c = ctx
+    f = synth.faces_uniform(20)
+    m = [synth.octa_sphere(3, (0.5, 0.5, 0.5), 0.2)]
+    T = pkg.Tables(c, f, f, f, m)
+    b = synth.rhs_divergence(f, f, f, 5)
+    p, rep = _solve_gpu(pkg, T, b, 0)
+    rhs = torch.from_numpy(b).cuda()
+    pw = torch.from_numpy(p).cuda()
+    rep2 = T.solve(rhs, pw, TOL, pkg.SolveOpts(precision=0))
+    assert rep2["cycles"] <= 1
+    p3 = torch.zeros_like(rhs)
+    rep3 = T.solve(rhs, p3, TOL, pkg.SolveOpts(precision=0, max_cycles=1), raise_on_error=False)
+    assert rep3["status"] == "IBM_ERR_NOT_CONVERGED"
+    T.close()
