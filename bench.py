@@ -1,0 +1,314 @@
+"""Benchmark of the ghost-cell immersed-boundary pressure Poisson hot path on GB300.
+
+One step = classify the 256^3 tanh-stretched grid (max/min spacing 2) against the prolate
+ellipsoid (0.2/0.08/0.08, 8192 triangles, 20 deg about z) + mixed-precision solve of the
+pressure Poisson system to 1e-10 relative projected residual, with the seeded N(0,1)
+divergence right-hand side (synthetic inputs standing in for the paper's wing geometries).
+Inputs are resident in HBM when the timed region starts; the working set (~0.8 GB) is
+larger than L2, so no flush is needed between steps.
+
+Printed as one JSON line (rank 0).  Also measured: FP64 and mixed time to 1e-10 (solve
+only), smoother sweep throughput (Gpts/s per sweep) with its HBM roofline fraction, the
+end-to-end time through the C ABI with host buffers, GPU clocks during the timed region,
+and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+
+--impl reference times the oracle (the CPU program the results are checked against) on a
+bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-10 residual & Gpts/s per sweep, mixed vs FP64, fraction of HBM peak"
+UNIT = "Gcell/s (cells classified and solved to 1e-10 per second)"
+TOL = 1e-10
+FP32_SWEEP_BYTES = 13.0    # read e 4 + rhs 4 + mask 1, write e 4 per cell and full sweep
+FP64_SWEEP_BYTES = 25.0    # read p 8 + b 8 + mask 1, write p 8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+                for q, nm in enumerate(names):
+                    if r[5 + q].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_sample(n: int):
+    """Oracle classify + solve of the workload's geometry on an n^3 grid (host cores)."""
+    import numpy as np
+    import synth
+    from oracle import classify as OC
+    from oracle import solve as OS
+    from oracle.grid import Grid
+    pr = synth.cfg2(n)
+    g = Grid(pr.xf, pr.yf, pr.zf)
+    b = pr.rhs()
+    t0 = time.perf_counter()
+    ib, G = OC.classify(g, pr.meshes)
+    OS.solve_gmres(g, ib, G, b)
+    dt = time.perf_counter() - t0
+    return pr.ncells, dt
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    n = args.cpu_n
+    for _ in range(args.warmup):
+        _cpu_sample(n)
+    tot_cells, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        c, dt = _cpu_sample(n)
+        tot_cells += c
+        tot_t += dt
+    val = tot_cells / tot_t / 1e9
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "FP64 CPU oracle: classify + GMRES solve of the same geometry on a %d^3 grid "
+                                       "per step" % n},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _config(args):
+    return {"workload": "ellipsoid 0.2/0.08/0.08 (8192 tris, 20 deg) in a %d^3 tanh-stretched grid (ratio 2), "
+                        "seeded N(0,1) divergence rhs, classify + mixed-precision solve to 1e-10" % args.n,
+            "grid": [args.n] * 3, "tol": TOL, "precision": "FP32 multigrid + FP64 refinement",
+            "l2": "working set > L2 (no flush)", "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2605_04335_gb300 as pkg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+
+    pr = synth.cfg2(args.n)
+    b_host = pr.rhs()
+    N = pr.ncells
+    ctx = pkg.Context(local)
+    rhs = torch.from_numpy(b_host).to(dev)
+    p = torch.zeros_like(rhs)
+    mixed = pkg.SolveOpts(precision=1)
+    fp64 = pkg.SolveOpts(precision=0)
+
+    def step():
+        T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+        p.zero_()
+        rep = T.solve(rhs, p, TOL, mixed, stream=st)
+        T.close()
+        return rep
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = pkg.ibm_ctx_launch_count(ctx.h)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        reps = [step() for _ in range(args.steps)]
+        e1.record(st)
+        barrier()
+    launches = pkg.ibm_ctx_launch_count(ctx.h) - l0
+    t_ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = ws * N / (t_ms * 1e-3) / 1e9
+
+    # solve-only time to 1e-10, mixed vs FP64 (same tables; warm)
+    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+    tts = {}
+    cyc = {}
+    for name, o in (("mixed", mixed), ("fp64", fp64)):
+        p.zero_()
+        T.solve(rhs, p, TOL, o, stream=st)
+        ts = []
+        for _ in range(max(1, args.solve_reps)):
+            p.zero_()
+            torch.cuda.synchronize()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            rep = T.solve(rhs, p, TOL, o, stream=st)
+            c.record(st)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        tts[name] = statistics.median(ts)
+        cyc[name] = rep["cycles"]
+    # smoother sweeps: Gpts/s per sweep (fine level, red + black + ghost rows)
+    sweeps = {}
+    for name, prec in (("fp32", 1), ("fp64", 0)):
+        nsw = 20
+        pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, 3, st)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, nsw, st)
+        c.record(st)
+        c.synchronize()
+        sweeps[name] = a.elapsed_time(c) / nsw
+    T.close()
+    hbm, src = _peaks()
+    gpts32 = N / (sweeps["fp32"] * 1e-3) / 1e9
+    gpts64 = N / (sweeps["fp64"] * 1e-3) / 1e9
+    ach = FP32_SWEEP_BYTES * N / (sweeps["fp32"] * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    p_pin = torch.empty_like(b_pin).pin_memory()
+    for _ in range(1):
+        rhs.copy_(b_pin, non_blocking=True)
+        step()
+        p_pin.copy_(p, non_blocking=True)
+    barrier()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(args.steps):
+        rhs.copy_(b_pin, non_blocking=True)
+        step()
+        p_pin.copy_(p, non_blocking=True)
+    c.record(st)
+    c.synchronize()
+    e2e_ms = a.elapsed_time(c) / args.steps
+    mesh_bytes = sum(m.verts.nbytes + m.tris.nbytes for m in pr.meshes) + 8 * (3 * args.n + 3)
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(args),
+            "time_to_tol_ms": {"mixed": tts["mixed"], "fp64": tts["fp64"]},
+            "cycles": cyc, "mixed_speedup_vs_fp64": tts["fp64"] / tts["mixed"],
+            "sweep_gpts": {"fp32": gpts32, "fp64": gpts64},
+            "sweep_ms": sweeps,
+            "final_rel_resid": reps[-1]["rel_resid"],
+            "roofline": {"bound": "hbm", "kernel": "FP32 red-black Gauss-Seidel sweep (fine level, + ghost rows)",
+                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                         "peak_source": src, "algorithmic_bytes_per_cell": FP32_SWEEP_BYTES},
+            "e2e": {"value": ws * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(b_host.nbytes + mesh_bytes), "d2h_bytes_per_step": int(b_host.nbytes)},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    if not args.no_cpu:
+        c_cells, c_t = _cpu_sample(args.cpu_n)
+        line["cpu_baseline"] = {"value": c_cells / c_t / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "FP64 CPU oracle: classify + GMRES solve of the same geometry on a "
+                                          "%d^3 grid (%.1f s)" % (args.cpu_n, c_t)}
+    print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--cpu-n", type=int, default=64)
+    ap.add_argument("--solve-reps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

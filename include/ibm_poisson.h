@@ -149,6 +149,16 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
                          double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
                          void *stream);
 
+/* Measurement: run `nsweeps` smoother sweeps (red, black, ghost rows) on the finest level
+ * of the hierarchy of the given precision, exactly as inside a V-cycle, on whatever the
+ * solver's work arrays hold (call after a poisson_solve of that precision).  No result;
+ * used to time the smoother in isolation.  Asynchronous on `stream`. */
+ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps,
+                               void *stream);
+
+/* Number of CUDA kernels this context has launched so far (all calls). */
+ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

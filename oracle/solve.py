@@ -149,4 +149,7 @@ def solve_gmres(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray,
         rr = relative_residual(grid, iblank, G, b, p)
         if not rr <= 1e-12:
             raise RuntimeError("oracle GMRES did not converge (info=%d, relative residual %g)" % (info, rr))
-    return p, float(x[n])
+    # lambda from its definition: every fluid row reads b_i - (A p)_i = lambda
+    from .system import residual, fluid_mean
+    rf, _ = residual(grid, iblank, G, b, p, 0.0)
+    return p, fluid_mean(grid, iblank, rf)

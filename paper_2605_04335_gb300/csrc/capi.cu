@@ -24,6 +24,7 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
                          cudaStream_t st);
 ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
+ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st);
 
 }  // namespace ibm
 
@@ -60,6 +61,8 @@ ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device) {
   cudaError_t e = cudaMalloc((void **)&c->partials, sizeof(double) * ibm::REDUCE_BLOCKS * 8);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->scal, sizeof(double) * ibm::NSCAL);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hscal, sizeof(double) * ibm::NSCAL);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->errflag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->errflag, 0, sizeof(int));
   if (e != cudaSuccess) {
     ibm_ctx_destroy(c);
     return ibm::check(e, "ibm_ctx_create");
@@ -75,6 +78,7 @@ ibm_status ibm_ctx_destroy(ibm_ctx *c) {
   if (c->partials) cudaFree(c->partials);
   if (c->scal) cudaFree(c->scal);
   if (c->hscal) cudaFreeHost(c->hscal);
+  if (c->errflag) cudaFree(c->errflag);
   delete c;
   return IBM_OK;
 }
@@ -153,6 +157,18 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
   ibm_status s = ibm::solve_impl(ctx, const_cast<ibm_tables *>(t), rhs_dev, tol, p_dev, &o, info, (cudaStream_t)stream);
   if (info) info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return s;
+}
+
+ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps, void *stream) {
+  if (!ctx || !t || t->ctx != ctx || (precision != 0 && precision != 1) || nsweeps < 0) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream);
+}
+
+ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return IBM_ERR_INVALID_ARG;
+  *count = ctx->launches;
+  return IBM_OK;
 }
 
 }  // extern "C"

@@ -771,6 +771,7 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
     CTRY(cudaStreamSynchronize(st));
   }
   CTRY(cudaStreamSynchronize(st));
+  ctx->launches += 3 + 2 * (long long)nmesh * 3 + 5 + (T->nghost > 0 ? 2 + (long long)nmesh : 0);
 #undef CTRY
   if (T->nfluid == 0) return fail(IBM_ERR_NO_FLUID);
   *out = T;

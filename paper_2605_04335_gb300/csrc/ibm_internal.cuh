@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -37,7 +38,7 @@ struct LevelGeom {
 inline LevelGeom make_geom(int nx, int ny, int nz) {
   LevelGeom g;
   g.nx = nx; g.ny = ny; g.nz = nz;
-  g.px = ((nx + OX + 1 + 7) / 8) * 8;
+  g.px = ((nx + OX + 1 + 15) / 16) * 16;   // 16-byte row pitch even for the 8-bit mask (TMA)
   g.sy = g.px;
   g.sz = (long long)g.px * (ny + 2);
   g.ntot = g.sz * (nz + 2);
@@ -58,7 +59,9 @@ struct Level {
   double *w1d = nullptr;                    // widths dx dy dz
   double *cen = nullptr;                    // centres xc yc zc
   int8_t *poff = nullptr;                   // prolongation: neighbour offset per fine index (x,y,z)
-  double *pt = nullptr;                     // prolongation: weight of the neighbour (x,y,z)
+  float *pt = nullptr;                      // prolongation: weight of the neighbour (x,y,z)
+  void *wT = nullptr;                       // widths dx dy dz in the element type
+  void *sdiag = nullptr;                    // finest level: cxm+cxp, cym+cyp, czm+czp (element type)
   double fluid_vol = 0.0;
   long long nfluid = 0;
 };
@@ -81,6 +84,12 @@ struct Hierarchy {
   float *gw32 = nullptr;
   double *gtmp = nullptr;                   // new ghost values (Jacobi)
   void *graph_exec = nullptr;
+  // finest level ping-pong for the fused z-march sweep: the second buffer of the
+  // level-0 unknown (p64 in FP64 mode, lv[0].e in mixed mode) and TMA tensor maps
+  void *e_alt = nullptr;
+  bool zmarch = false;
+  CUtensorMap tm_e[2], tm_r, tm_m;
+  void *tm_base[2] = {nullptr, nullptr};    // which buffer each tm_e describes
 };
 
 }  // namespace ibm
@@ -91,6 +100,8 @@ struct ibm_ctx {
   double *scal = nullptr;       // NSCAL device scalars
   double *hscal = nullptr;      // pinned host mirror of scal
   int sm_count = 0;
+  long long launches = 0;       // kernels launched by this context (all calls)
+  int *errflag = nullptr;       // device flag: a bounded device-side wait gave up
 };
 
 struct ibm_tables {

@@ -22,7 +22,10 @@
 #include <cstring>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "ibm_internal.cuh"
+#include "zmarch.cuh"
 
 namespace ibm {
 
@@ -32,6 +35,8 @@ namespace {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+constexpr long long GHOST_CORNER = 1LL << 62;   // flag on a ghost-row source that is itself a ghost
+
 template <typename T>
 struct LV {          // kernel-side view of one level
   int nx, ny, nz, px;
@@ -40,6 +45,8 @@ struct LV {          // kernel-side view of one level
   const T *cxm, *cxp, *cym, *cyp, *czm, *czp;
   const T *fx, *fy, *fz;     // nullptr on the finest level
   const double *dx, *dy, *dz;
+  const T *wx, *wy, *wz;     // widths in T
+  const T *sdx, *sdy, *sdz;  // finest level: separable diagonal parts (else nullptr)
 };
 
 template <typename T>
@@ -52,6 +59,10 @@ LV<T> view(const Level &L) {
   v.czm = v.cyp + L.g.ny; v.czp = v.czm + L.g.nz;
   v.fx = (const T *)L.fx; v.fy = (const T *)L.fy; v.fz = (const T *)L.fz;
   v.dx = L.w1d; v.dy = L.w1d + L.g.nx; v.dz = L.w1d + L.g.nx + L.g.ny;
+  const T *w = (const T *)L.wT;
+  v.wx = w; v.wy = w ? w + L.g.nx : nullptr; v.wz = w ? w + L.g.nx + L.g.ny : nullptr;
+  const T *d = (const T *)L.sdiag;
+  v.sdx = d; v.sdy = d ? d + L.g.nx : nullptr; v.sdz = d ? d + L.g.nx + L.g.ny : nullptr;
   return v;
 }
 
@@ -80,7 +91,8 @@ __device__ __forceinline__ T stencil_sum(const LV<T> &v, const T *e, long long i
 // ------------------------------------------------------------------ hierarchy setup kernels
 
 template <typename T>
-__global__ void k_axis_level(const double *f, int n, T *cm, T *cp, double *w, double *c) {
+__global__ void k_axis_level(const double *f, int n, T *cm, T *cp, double *w, double *c, T *wt = nullptr,
+                             T *sd = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double ci = 0.5 * (f[i] + f[i + 1]), wi = f[i + 1] - f[i];
@@ -88,18 +100,20 @@ __global__ void k_axis_level(const double *f, int n, T *cm, T *cp, double *w, do
   if (i > 0) m = 1.0 / (wi * (ci - 0.5 * (f[i - 1] + f[i])));
   if (i < n - 1) p = 1.0 / (wi * (0.5 * (f[i + 1] + f[i + 2]) - ci));
   cm[i] = (T)m; cp[i] = (T)p; w[i] = wi; c[i] = ci;
+  if (wt) wt[i] = (T)wi;
+  if (sd) sd[i] = (T)m + (T)p;
 }
 
 // prolongation weights from coarse (cc, nc) to fine (cf, nf) along one axis
-__global__ void k_prolong_axis(const double *cf, int nf, const double *cc, int nc, int8_t *off, double *t) {
+__global__ void k_prolong_axis(const double *cf, int nf, const double *cc, int nc, int8_t *off, float *t) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nf) return;
   int I = i >> 1;
   double xf = cf[i], X = cc[I];
   int nb = xf < X ? I - 1 : (xf > X ? I + 1 : I);
-  if (nb < 0 || nb >= nc || nb == I) { off[i] = 0; t[i] = 0.0; return; }
+  if (nb < 0 || nb >= nc || nb == I) { off[i] = 0; t[i] = 0.0f; return; }
   off[i] = (int8_t)(nb - I);
-  t[i] = (xf - X) / (cc[nb] - X);
+  t[i] = (float)((xf - X) / (cc[nb] - X));
 }
 
 __global__ void k_mask0(const uint8_t *ib, int nx, int ny, int nz, uint8_t *mask, LevelGeom g) {
@@ -272,7 +286,7 @@ __global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colou
   if (v.mask[id] != 0) return;
   T c[6];
   coefs(v, i, j, k, id, c);
-  T D = ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+  T D = v.sdx ? (v.sdx[i] + v.sdy[j]) + v.sdz[k] : ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
   if (D == (T)0) return;
   T rhs = r[id] - (shift ? (T)(*shift) : (T)0);
   T res = stencil_sum(v, e, id, c) - D * e[id] - rhs;
@@ -288,10 +302,29 @@ __global__ void k_ghost_eval(const long long *src, const long long *dst, const W
   T s = (T)0;
   for (int c = 0; c < 8; ++c) {
     long long q = src[8 * g + c];
-    if (q >= 0) s += (T)w[8 * g + c] * e[q];
+    if (q >= 0) s += (T)w[8 * g + c] * e[q & ~GHOST_CORNER];
   }
   if (rhs) s += rhs[dst[g]];
   gtmp[g] = s;
+}
+
+// ghost rows right after a ping-pong sweep, in one launch: fluid sources from the new
+// array, ghost sources from the previous one (whose ghost values the sweep copied
+// unchanged), so no thread reads a value another thread writes (Jacobi among ghosts)
+template <typename T, typename W>
+__global__ void k_ghost_pp(const long long *src, const long long *dst, const W *w, long long ng, T *enew,
+                           const T *eold, const T *rhs) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  T s = (T)0;
+  for (int c = 0; c < 8; ++c) {
+    long long q = src[8 * g + c];
+    if (q < 0) continue;
+    const T v = (q & GHOST_CORNER) ? eold[q & ~GHOST_CORNER] : enew[q];
+    s += (T)w[8 * g + c] * v;
+  }
+  if (rhs) s += rhs[dst[g]];
+  enew[dst[g]] = s;
 }
 
 template <typename T>
@@ -312,7 +345,7 @@ __global__ void k_restrict(LV<T> f, const T *e, const T *r, const double *shift,
     int I = (int)(l % cv.nx); long long q = l / cv.nx; int J = (int)(q % cv.ny); int K = (int)(q / cv.ny);
     long long ic = vidx(cv, I, J, K);
     if (cv.mask[ic] != 0) { rc[ic] = (T)0; continue; }
-    double acc = 0.0;
+    T acc = (T)0;
     for (int c = 0; c < 8; ++c) {
       int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
       if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
@@ -320,13 +353,13 @@ __global__ void k_restrict(LV<T> f, const T *e, const T *r, const double *shift,
       if (f.mask[id] != 0) continue;
       T cf[6];
       coefs(f, i, j, k, id, cf);
-      T D = ((cf[0] + cf[1]) + (cf[2] + cf[3])) + (cf[4] + cf[5]);
+      T D = f.sdx ? (f.sdx[i] + f.sdy[j]) + f.sdz[k] : ((cf[0] + cf[1]) + (cf[2] + cf[3])) + (cf[4] + cf[5]);
       T res = (r[id] - sh) - (stencil_sum(f, e, id, cf) - D * e[id]);
-      acc += f.dx[i] * f.dy[j] * f.dz[k] * (double)res;
+      acc += (f.wx[i] * f.wy[j]) * f.wz[k] * res;
     }
-    double vc = cv.dx[I] * cv.dy[J] * cv.dz[K];
-    rc[ic] = (T)(acc / vc);
-    acc_all += acc;
+    T vc = (cv.wx[I] * cv.wy[J]) * cv.wz[K];
+    rc[ic] = acc / vc;
+    acc_all += (double)acc;
   }
   sm[threadIdx.x] = acc_all;
   __syncthreads();
@@ -360,26 +393,27 @@ __global__ void k_finalize_shift(const double *partials, int nb, double fluid_vo
 
 template <typename T>
 __global__ void k_prolong(LV<T> cv, const T *ec, LV<T> f, T *ef, const int8_t *offx, const int8_t *offy,
-                          const int8_t *offz, const double *tx, const double *ty, const double *tz) {
+                          const int8_t *offz, const float *tx, const float *ty, const float *tz) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y, k = blockIdx.z;
   if (i >= f.nx) return;
   long long id = vidx(f, i, j, k);
   if (f.mask[id] != 0) return;
   int I = i >> 1, J = j >> 1, K = k >> 1;
-  double wx[2] = {1.0 - tx[i], tx[i]}, wy[2] = {1.0 - ty[j], ty[j]}, wz[2] = {1.0 - tz[k], tz[k]};
+  float wx[2] = {1.0f - tx[i], tx[i]}, wy[2] = {1.0f - ty[j], ty[j]}, wz[2] = {1.0f - tz[k], tz[k]};
   int ox = offx[i], oy = offy[j], oz = offz[k];
-  double s = 0.0, ws = 0.0;
+  T s = (T)0;
+  float ws = 0.0f;
   for (int c = 0; c < 8; ++c) {
     int a = c & 1, b = (c >> 1) & 1, d = (c >> 2) & 1;
-    double w = wx[a] * wy[b] * wz[d];
-    if (w == 0.0) continue;
+    float w = (wx[a] * wy[b]) * wz[d];
+    if (w == 0.0f) continue;
     long long ic = vidx(cv, I + a * ox, J + b * oy, K + d * oz);
     if (cv.mask[ic] != 0) continue;
-    s += w * (double)ec[ic];
+    s += (T)w * ec[ic];
     ws += w;
   }
-  if (ws > 0.0) ef[id] += (T)(s / ws);
+  if (ws > 0.0f) ef[id] += s * (T)(1.0f / ws);
 }
 
 // bordered coarsest solve: [e; lambda] = Minv [r; 0]
@@ -397,29 +431,52 @@ __global__ void k_coarsest(const double *Minv, const int *cidx, const int *ncoun
 }
 
 // FP64 fine residual r = b - lambda - A p on fluid rows; optional FP32 copy; block partials
-// (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}]
+// (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}].  FP64 arithmetic is kept to the
+// stencil itself (GB300 issues FP64 at 1/57 of the FP32 rate): the diagonal is separable,
+// row invariants are hoisted, and the norm/mean partial sums run in FP32 per thread.
 __global__ void k_residual64(LV<double> v, const double *p, const double *b, const double *lambda, float *r32,
                              double *partials) {
   __shared__ double sm[3][REDUCE_THREADS];
   const double lam = *lambda;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
   const long long rows = (long long)v.ny * v.nz;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    int j = (int)(row % v.ny), k = (int)(row / v.ny);
+    const int j = (int)(row % v.ny), k = (int)(row / v.ny);
+    const double cym = v.cym[j], cyp = v.cyp[j], czm = v.czm[k], czp = v.czp[k];
+    const double syz = v.sdy[j] + v.sdz[k];
+    const float dydz = (float)(v.dy[j] * v.dz[k]);
     for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
       long long id = vidx(v, i, j, k);
       if (v.mask[id] != 0) continue;
-      double c[6];
-      coefs(v, i, j, k, id, c);
-      double D = ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
-      double res = (b[id] - lam) - (stencil_sum(v, p, id, c) - D * p[id]);
-      if (r32) r32[id] = (float)res;
-      a0 += v.dx[i] * v.dy[j] * v.dz[k] * res;
-      a1 += res;
-      a2 += res * res;
+      if (p == nullptr) {            // residual of p = 0: b - lambda
+        const float rf0 = (float)(b[id] - lam);
+        if (r32) r32[id] = rf0;
+        a0 = fmaf((float)v.dx[i] * dydz, rf0, a0);
+        a1 += rf0;
+        a2 = fmaf(rf0, rf0, a2);
+        continue;
+      }
+      const double pc = p[id];
+      double s = v.cxm[i] * p[id - 1];
+      s = fma(v.cxp[i], p[id + 1], s);
+      s = fma(cym, p[id - v.sy], s);
+      s = fma(cyp, p[id + v.sy], s);
+      s = fma(czm, p[id - v.sz], s);
+      s = fma(czp, p[id + v.sz], s);
+      s = fma(-(v.sdx[i] + syz), pc, s);           // (A p)_i
+      const double res = (b[id] - lam) - s;
+      const float rf = (float)res;
+      if (r32) r32[id] = rf;
+      a0 = fmaf((float)v.dx[i] * dydz, rf, a0);
+      a1 += rf;
+      a2 = fmaf(rf, rf, a2);
     }
+    // fold the FP32 row partials into FP64 every row (bounded FP32 error)
+    A0 += a0; A1 += a1; A2 += a2;
+    a0 = a1 = a2 = 0.f;
   }
-  sm[0][threadIdx.x] = a0; sm[1][threadIdx.x] = a1; sm[2][threadIdx.x] = a2;
+  sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
   __syncthreads();
   for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st)
@@ -439,7 +496,7 @@ __global__ void k_ghost_resid64(const long long *src, const long long *dst, cons
     double s = 0.0;
     for (int c = 0; c < 8; ++c) {
       long long q = src[8 * g + c];
-      if (q >= 0) s += w[8 * g + c] * p[q];
+      if (q >= 0) s += w[8 * g + c] * p[q & ~GHOST_CORNER];
     }
     double rg = s - p[dst[g]];
     if (r32) r32[dst[g]] = (float)rg;
@@ -525,7 +582,7 @@ __global__ void k_zero_solid(double *p, const uint8_t *mask, long long n) {
 }
 
 __global__ void k_ghost_src(const long long *ref, const long long *cell, long long ng, LevelGeom g, long long *src,
-                            long long *dst, const double *w, float *w32) {
+                            long long *dst, const double *w, float *w32, const uint8_t *ib) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= ng * 8) return;
   auto tp = [&](long long l) {
@@ -533,7 +590,7 @@ __global__ void k_ghost_src(const long long *ref, const long long *cell, long lo
     return pidx(g, i, j, k);
   };
   long long l = ref[q];
-  src[q] = l >= 0 ? tp(l) : -1;
+  src[q] = l >= 0 ? (tp(l) | (ib[l] == 3 ? GHOST_CORNER : 0LL)) : -1;
   w32[q] = (float)w[q];
   if ((q & 7) == 0) dst[q >> 3] = tp(cell[q >> 3]);
 }
@@ -549,17 +606,60 @@ cudaError_t alloc_zero(void **p, long long n, cudaStream_t st) {
 
 void free_hierarchy(Hierarchy *h) {
   if (!h) return;
+  std::vector<void *> ps;
   for (Level &L : h->lv) {
-    void *ps[] = {L.mask, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt};
-    for (void *p : ps) if (p) cudaFree(p);
+    void *q[] = {L.mask, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt, L.wT, L.sdiag};
+    ps.insert(ps.end(), q, q + 13);
   }
-  void *ps[] = {h->p64, h->b64, h->minv, h->cidx, h->dncoarse, h->c64, h->gsrc, h->gdst, h->gw64, h->gw32, h->gtmp};
+  void *q[] = {h->p64, h->b64, h->minv, h->cidx, h->dncoarse, h->c64, h->gsrc, h->gdst, h->gw64, h->gw32, h->gtmp,
+               h->e_alt, h->tm_base[0], h->tm_base[1]};
+  ps.insert(ps.end(), q, q + 14);
+  std::sort(ps.begin(), ps.end());
+  ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
   for (void *p : ps) if (p) cudaFree(p);
   if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
   delete h;
 }
 
 // ------------------------------------------------------------------ hierarchy build
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+  }
+  return fn;
+}
+
+// 3-D tensor map over a padded level array; box (bx, by, 1); zero fill outside
+static bool make_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int elem, const LevelGeom &g, int bx, int by) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)(g.ny + 2), (cuuint64_t)(g.nz + 2)};
+  cuuint64_t strides[2] = {(cuuint64_t)g.px * elem, (cuuint64_t)g.px * (g.ny + 2) * elem};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
+  Level &L0 = h->lv[0];
+  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  bool ok = make_map(&h->tm_e[0], e0, dt, sizeof(T), L0.g, zm::BX, zm::EY) &&
+            make_map(&h->tm_e[1], h->e_alt, dt, sizeof(T), L0.g, zm::BX, zm::EY) &&
+            make_map(&h->tm_r, r0, dt, sizeof(T), L0.g, zm::BX, zm::RY) &&
+            make_map(&h->tm_m, L0.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, L0.g, zm::BXM, zm::RY);
+  h->tm_base[0] = e0;
+  h->tm_base[1] = h->e_alt;
+  h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(zm::Smem<T>)) == cudaSuccess;
+}
 
 template <typename T>
 static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) {
@@ -580,16 +680,20 @@ static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **
     HTRY(cudaMalloc(&L.c1d, sizeof(T) * 2 * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.w1d, sizeof(double) * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.cen, sizeof(double) * (nx + ny + nz)));
+    HTRY(cudaMalloc(&L.wT, sizeof(T) * (nx + ny + nz)));
+    const bool finest = h->lv.empty();
+    if (finest) HTRY(cudaMalloc(&L.sdiag, sizeof(T) * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&dfaces, sizeof(double) * (nx + ny + nz + 3)));
     HTRY(cudaMemcpyAsync(dfaces, fx.data(), sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, st));
     HTRY(cudaMemcpyAsync(dfaces + nx + 1, fy.data(), sizeof(double) * (ny + 1), cudaMemcpyHostToDevice, st));
     HTRY(cudaMemcpyAsync(dfaces + nx + ny + 2, fz.data(), sizeof(double) * (nz + 1), cudaMemcpyHostToDevice, st));
-    T *c = (T *)L.c1d;
-    k_axis_level<T><<<nblk(nx, 128), 128, 0, st>>>(dfaces, nx, c, c + nx, L.w1d, L.cen);
+    T *c = (T *)L.c1d, *wt = (T *)L.wT, *sd = (T *)L.sdiag;
+    k_axis_level<T><<<nblk(nx, 128), 128, 0, st>>>(dfaces, nx, c, c + nx, L.w1d, L.cen, wt, sd);
     k_axis_level<T><<<nblk(ny, 128), 128, 0, st>>>(dfaces + nx + 1, ny, c + 2 * nx, c + 2 * nx + ny, L.w1d + nx,
-                                                    L.cen + nx);
+                                                    L.cen + nx, wt + nx, sd ? sd + nx : nullptr);
     k_axis_level<T><<<nblk(nz, 128), 128, 0, st>>>(dfaces + nx + ny + 2, nz, c + 2 * nx + 2 * ny,
-                                                    c + 2 * nx + 2 * ny + nz, L.w1d + nx + ny, L.cen + nx + ny);
+                                                    c + 2 * nx + 2 * ny + nz, L.w1d + nx + ny, L.cen + nx + ny,
+                                                    wt + nx + ny, sd ? sd + nx + ny : nullptr);
     HTRY(cudaGetLastError());
     HTRY(cudaStreamSynchronize(st));
     cudaFree(dfaces);
@@ -626,7 +730,7 @@ static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **
                                                   wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz);
     const int nf = F.g.nx + F.g.ny + F.g.nz;
     HTRY(cudaMalloc((void **)&F.poff, nf));
-    HTRY(cudaMalloc((void **)&F.pt, sizeof(double) * nf));
+    HTRY(cudaMalloc((void **)&F.pt, sizeof(float) * nf));
     k_prolong_axis<<<nblk(F.g.nx, 128), 128, 0, st>>>(F.cen, F.g.nx, C.cen, C.g.nx, F.poff, F.pt);
     k_prolong_axis<<<nblk(F.g.ny, 128), 128, 0, st>>>(F.cen + F.g.nx, F.g.ny, C.cen + C.g.nx, C.g.ny,
                                                       F.poff + F.g.nx, F.pt + F.g.nx);
@@ -680,9 +784,13 @@ static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **
     HTRY(cudaMalloc((void **)&h->gw32, sizeof(float) * 8 * (ng ? ng : 1)));
     HTRY(cudaMalloc((void **)&h->gtmp, sizeof(double) * (ng ? ng : 1)));
     h->gw64 = nullptr;
-    if (ng) k_ghost_src<<<nblk(8 * ng, 256), 256, 0, st>>>(t->gref, t->gcell, ng, L0.g, h->gsrc, h->gdst, t->gw, h->gw32);
+    if (ng) k_ghost_src<<<nblk(8 * ng, 256), 256, 0, st>>>(t->gref, t->gcell, ng, L0.g, h->gsrc, h->gdst, t->gw, h->gw32,
+                                                         t->iblank);
     HTRY(cudaGetLastError());
+    HTRY(alloc_zero<T>(&h->e_alt, L0.g.ntot, st));
     HTRY(cudaStreamSynchronize(st));
+    if (sizeof(T) == 8) setup_zmarch<T>(h, h->p64, h->b64);
+    else setup_zmarch<T>(h, L0.e, L0.r);
   }
 #undef HTRY
   *out = h;
@@ -704,33 +812,82 @@ struct Solver {
 };
 
 template <typename T>
-void smooth_level(Solver &S, int l, T *e, const T *r, const double *shift, bool fine, const T *ghost_rhs, int sweeps) {
+void ghost_update(Solver &S, T *e, const T *ghost_rhs) {
+  const long long ng = S.t->nghost;
+  if (ng <= 0) return;
+  if (sizeof(T) == 8)
+    k_ghost_eval<T, double><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, ng, e, ghost_rhs,
+                                                              (T *)S.h->gtmp);
+  else
+    k_ghost_eval<T, float><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, ng, e, ghost_rhs,
+                                                             (T *)S.h->gtmp);
+  k_ghost_store<T><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gdst, ng, (const T *)S.h->gtmp, e);
+  S.ctx->launches += 2;
+}
+
+template <typename T>
+void sweep_zmarch(Solver &S, T *&e, const double *shift) {
+  Hierarchy *h = S.h;
+  Level &L0 = h->lv[0];
+  const int which = (e == (T *)h->tm_base[0]) ? 0 : 1;
+  T *other = (T *)h->tm_base[1 - which];
+  LV<T> v = view<T>(L0);
+  zm::Args<T> a;
+  a.nx = L0.g.nx; a.ny = L0.g.ny; a.nz = L0.g.nz; a.px = L0.g.px; a.sy = L0.g.sy; a.sz = L0.g.sz;
+  a.cxm = v.cxm; a.cxp = v.cxp; a.cym = v.cym; a.cyp = v.cyp; a.czm = v.czm; a.czp = v.czp;
+  a.sdx = v.sdx; a.sdy = v.sdy; a.sdz = v.sdz;
+  a.shift = shift;
+  a.omega = (float)S.omega;
+  a.out = other;
+  a.err = S.ctx->errflag;
+  const int gx = (a.nx + zm::TX - 1) / zm::TX, gy = (a.ny + zm::TY - 1) / zm::TY;
+  const int per_sm = std::max(1, (int)((227 * 1024) / (sizeof(zm::Smem<T>) + 1024)));
+  const long long target = (long long)per_sm * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152);
+  int chunks = (int)std::max<long long>(1, std::min<long long>(a.nz, (target + gx * gy - 1) / (gx * gy)));
+  a.kz = (a.nz + chunks - 1) / chunks;
+  chunks = (a.nz + a.kz - 1) / a.kz;
+  dim3 grid(gx, gy, chunks);
+  zm::k_sweep_zmarch<T><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r, h->tm_m, a);
+  S.ctx->launches += 1;
+  e = other;
+}
+
+template <typename T>
+void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool fine, const T *ghost_rhs, int sweeps) {
   Level &L = S.h->lv[l];
   LV<T> v = view<T>(L);
   dim3 grid(nblk((L.g.nx + 1) / 2, 128), L.g.ny, L.g.nz);
-  const long long ng = S.t->nghost;
   for (int s = 0; s < sweeps; ++s) {
-    for (int colour = 0; colour < 2; ++colour)
-      k_rbgs<T><<<grid, 128, 0, S.st>>>(v, e, r, shift, colour, (T)S.omega);
-    if (fine && ng > 0) {
-      if (sizeof(T) == 8)
-        k_ghost_eval<T, double><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, ng, e, ghost_rhs,
-                                                                  (T *)S.h->gtmp);
-      else
-        k_ghost_eval<T, float><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, ng, e, ghost_rhs,
-                                                                 (T *)S.h->gtmp);
-      k_ghost_store<T><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gdst, ng, (const T *)S.h->gtmp, e);
+    if (fine && S.h->zmarch) {
+      T *old = e;
+      sweep_zmarch<T>(S, e, shift);
+      const long long ng = S.t->nghost;
+      if (ng > 0) {
+        if (sizeof(T) == 8)
+          k_ghost_pp<T, double><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, ng, e, old, ghost_rhs);
+        else
+          k_ghost_pp<T, float><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, ng, e, old, ghost_rhs);
+        S.ctx->launches += 1;
+      }
+      continue;
+    } else {
+      for (int colour = 0; colour < 2; ++colour)
+        k_rbgs<T><<<grid, 128, 0, S.st>>>(v, e, r, shift, colour, (T)S.omega);
+      S.ctx->launches += 2;
     }
+    if (fine) ghost_update<T>(S, e, ghost_rhs);
   }
 }
 
-// V-cycle for level l: e_l (in/out) approximately solves A_l e_l = r_l - shift_l
+// V-cycle for level l: e_l (in/out) approximately solves A_l e_l = r_l - shift_l.  On the
+// finest level e is the hierarchy's own pointer: the fused sweep swaps it between two buffers.
 template <typename T>
-void vcycle(Solver &S, int l, T *e, const T *r, const double *shift, const T *ghost_rhs) {
+void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *ghost_rhs) {
   Hierarchy *h = S.h;
   const int nl = (int)h->lv.size();
   if (l == nl - 1) {
     k_coarsest<T><<<1, 128, 0, S.st>>>(h->minv, h->cidx, S.d_ncoarse, r, e);
+    S.ctx->launches += 1;
     return;
   }
   const bool fine = (l == 0);
@@ -748,6 +905,9 @@ void vcycle(Solver &S, int l, T *e, const T *r, const double *shift, const T *gh
   const int nxf = F.g.nx, nyf = F.g.ny;
   k_prolong<T><<<gp, 128, 0, S.st>>>(view<T>(C), ec, view<T>(F), e, F.poff, F.poff + nxf, F.poff + nxf + nyf, F.pt,
                                      F.pt + nxf, F.pt + nxf + nyf);
+  S.ctx->launches += 3;   // restrict, finalize shift, prolong
+  // the corrected fluid values make the ghost rows stale: refresh them before post-smoothing
+  if (fine) ghost_update<T>(S, e, ghost_rhs);
   smooth_level<T>(S, l, e, r, shift, fine, ghost_rhs, S.nu2);
 }
 
@@ -760,6 +920,9 @@ LV<double> fine_view64(Hierarchy *h) {
   v.dx = L0.w1d; v.dy = L0.w1d + v.nx; v.dz = L0.w1d + v.nx + v.ny;
   const double *c = h->c64;
   v.cxm = c; v.cxp = c + v.nx; v.cym = c + 2 * v.nx; v.cyp = v.cym + v.ny; v.czm = v.cyp + v.ny; v.czp = v.czm + v.nz;
+  const double *d = c + 2 * (v.nx + v.ny + v.nz);
+  v.sdx = d; v.sdy = d + v.nx; v.sdz = d + v.nx + v.ny;
+  v.wx = v.wy = v.wz = nullptr;
   return v;
 }
 
@@ -770,10 +933,12 @@ void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS;
-  if (ng > 0)
+  const bool gh = ng > 0 && p != nullptr;
+  if (gh)
     k_ghost_resid64<<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, ng, p, r32, gpart);
-  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, ng > 0 ? ngb : 0, S.ctx->scal,
+  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
                                         update_lambda ? 1 : 0);
+  S.ctx->launches += gh ? 3 : 2;
 }
 
 }  // namespace
@@ -787,7 +952,7 @@ ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
   Level &L0 = h->lv[0];
   const int n = L0.g.nx + L0.g.ny + L0.g.nz;
   double *c64 = nullptr, *df = nullptr;
-  IBM_TRY(cudaMalloc((void **)&c64, sizeof(double) * 2 * n));
+  IBM_TRY(cudaMalloc((void **)&c64, sizeof(double) * 3 * n));
   IBM_TRY(cudaMalloc((void **)&df, sizeof(double) * (n + 3)));
   IBM_TRY(cudaMemcpyAsync(df, t->xf.data(), sizeof(double) * (L0.g.nx + 1), cudaMemcpyHostToDevice, st));
   IBM_TRY(cudaMemcpyAsync(df + L0.g.nx + 1, t->yf.data(), sizeof(double) * (L0.g.ny + 1), cudaMemcpyHostToDevice, st));
@@ -797,10 +962,13 @@ ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
   IBM_TRY(cudaMalloc((void **)&w, sizeof(double) * n));
   IBM_TRY(cudaMalloc((void **)&c, sizeof(double) * n));
   const int nx = L0.g.nx, ny = L0.g.ny, nz = L0.g.nz;
-  k_axis_level<double><<<nblk(nx, 128), 128, 0, st>>>(df, nx, c64, c64 + nx, w, c);
-  k_axis_level<double><<<nblk(ny, 128), 128, 0, st>>>(df + nx + 1, ny, c64 + 2 * nx, c64 + 2 * nx + ny, w + nx, c + nx);
+  double *sd = c64 + 2 * n;
+  k_axis_level<double><<<nblk(nx, 128), 128, 0, st>>>(df, nx, c64, c64 + nx, w, c, nullptr, sd);
+  k_axis_level<double><<<nblk(ny, 128), 128, 0, st>>>(df + nx + 1, ny, c64 + 2 * nx, c64 + 2 * nx + ny, w + nx, c + nx,
+                                                      nullptr, sd + nx);
   k_axis_level<double><<<nblk(nz, 128), 128, 0, st>>>(df + nx + ny + 2, nz, c64 + 2 * nx + 2 * ny,
-                                                      c64 + 2 * nx + 2 * ny + nz, w + nx + ny, c + nx + ny);
+                                                      c64 + 2 * nx + 2 * ny + nz, w + nx + ny, c + nx + ny, nullptr,
+                                                      sd + nx + ny);
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaStreamSynchronize(st));
   cudaFree(df); cudaFree(w); cudaFree(c);
@@ -822,26 +990,13 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   k_pack<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, h->b64);
   k_pack<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, h->p64);
   k_zero_solid<<<1216, 256, 0, st>>>(h->p64, L0.mask, L0.g.ntot);
+  ctx->launches += 3;
   double hs[NSCAL] = {0};
   hs[S_FLUIDVOL] = L0.fluid_vol;
   hs[S_NF] = (double)L0.nfluid;
   IBM_TRY(cudaMemcpyAsync(ctx->scal, hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   // ||S P b||: residual of p = 0 with lambda = 0
-  {
-    double *pz = (double *)h->lv[0].e;
-    if (prec == 0) {
-      // level-0 e is FP64 in this mode; use it as a zero array (restored below)
-      IBM_TRY(cudaMemsetAsync(pz, 0, sizeof(double) * L0.g.ntot, st));
-      fine_residual(S, pz, nullptr, false);
-    } else {
-      double *tmpz = nullptr;
-      IBM_TRY(cudaMalloc((void **)&tmpz, sizeof(double) * L0.g.ntot));
-      IBM_TRY(cudaMemsetAsync(tmpz, 0, sizeof(double) * L0.g.ntot, st));
-      fine_residual(S, tmpz, nullptr, false);
-      IBM_TRY(cudaStreamSynchronize(st));
-      cudaFree(tmpz);
-    }
-  }
+  fine_residual(S, nullptr, nullptr, false);
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
   IBM_TRY(cudaStreamSynchronize(st));
   const double bnorm = std::sqrt(ctx->hscal[S_NORM2]);
@@ -851,6 +1006,7 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   if (ng > 0) {
     k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, ng, h->p64, nullptr, h->gtmp);
     k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, h->p64);
+    ctx->launches += 2;
   }
   IBM_TRY(cudaGetLastError());
   int cycles = 0;
@@ -869,12 +1025,13 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
       vcycle<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, nullptr);
       fine_residual(S, h->p64, nullptr, true);
     } else {
-      float *e32 = (float *)L0.e;
+      float *&e32 = reinterpret_cast<float *&>(L0.e);
       for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
         if (q == 0) IBM_TRY(cudaMemsetAsync(e32, 0, sizeof(float) * L0.g.ntot, st));
         vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
       }
       k_update_p<<<1216, 256, 0, st>>>(h->p64, e32, L0.g.ntot);
+      ctx->launches += 1;
       fine_residual(S, h->p64, r32, true);
     }
     IBM_TRY(cudaGetLastError());
@@ -890,9 +1047,16 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
   k_gauge_finalize<<<1, 256, 0, st>>>(ctx->partials, REDUCE_BLOCKS, ctx->scal);
   k_unpack_gauge<<<nblk(n0, 256), 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
+  ctx->launches += 3;
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  int herr = 0;
+  IBM_TRY(cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, st));
   IBM_TRY(cudaStreamSynchronize(st));
+  if (herr) {
+    IBM_TRY(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), st));
+    result = IBM_ERR_TIMEOUT;
+  }
   if (info) {
     info->cycles = cycles;
     info->history_len = hl;
@@ -900,6 +1064,21 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     info->lambda = ctx->hscal[S_LAMBDA];
   }
   return result;
+}
+
+ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st) {
+  ibm_status s = build_hierarchy(t, precision, st);
+  if (s != IBM_OK) return s;
+  Hierarchy *h = t->hier[precision];
+  Solver S{ctx, t, h, st, 1, 1, 1.0, h->dncoarse};
+  Level &L0 = h->lv[0];
+  if (precision == 0)
+    smooth_level<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, true, nullptr, nsweeps);
+  else
+    smooth_level<float>(S, 0, reinterpret_cast<float *&>(L0.e), (const float *)L0.r, ctx->scal + S_MU, true,
+                        (const float *)L0.r, nsweeps);
+  IBM_TRY(cudaGetLastError());
+  return IBM_OK;
 }
 
 }  // namespace ibm

@@ -76,6 +76,8 @@ def load_library():
         "ibm_tables_export": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
+        "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
+        "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -176,6 +178,16 @@ def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, strea
     if raise_on_error and s != IBM_OK:
         raise IbmError(s, "poisson_solve (%s)" % rep)
     return rep
+
+
+def ibm_smoother_sweeps(ctx, tables, precision: int, nsweeps: int, stream=None):
+    _check(load_library().ibm_smoother_sweeps(ctx, tables, precision, nsweeps, _stream(stream)), "ibm_smoother_sweeps")
+
+
+def ibm_ctx_launch_count(ctx) -> int:
+    v = C.c_int64()
+    _check(load_library().ibm_ctx_launch_count(ctx, C.byref(v)), "ibm_ctx_launch_count")
+    return int(v.value)
 
 
 # ----------------------------------------------------------------------------- conveniences
