@@ -209,6 +209,16 @@ def run_ours(args):
         t_ms = float(tt.item())
     value = ws * N / (t_ms * 1e-3) / 1e9
 
+    # classification alone (iblank, ghosts, image points): median of a few calls
+    tcl = []
+    for _ in range(3):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        Tc = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+        c.record(st)
+        c.synchronize()
+        tcl.append(a.elapsed_time(c))
+        Tc.close()
     # solve-only time to 1e-10, mixed vs FP64 (same tables; warm)
     T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
     tts = {}
@@ -239,6 +249,7 @@ def run_ours(args):
         c.record(st)
         c.synchronize()
         sweeps[name] = a.elapsed_time(c) / nsw
+    T_ng = T.nghost
     T.close()
     hbm, src = _peaks()
     gpts32 = N / (sweeps["fp32"] * 1e-3) / 1e9
@@ -270,6 +281,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(args),
             "time_to_tol_ms": {"mixed": tts["mixed"], "fp64": tts["fp64"]},
+            "classify_ms": statistics.median(tcl), "ghosts": T_ng,
             "cycles": cyc, "mixed_speedup_vs_fp64": tts["fp64"] / tts["mixed"],
             "sweep_gpts": {"fp32": gpts32, "fp64": gpts64},
             "sweep_ms": sweeps,

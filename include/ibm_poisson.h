@@ -73,9 +73,9 @@ typedef struct {
                            refinement (FP64 fine residual, update, gauge, coarsest)  [0] */
   int32_t nu1, nu2;     /* pre-/post-smoothing red-black Gauss-Seidel sweeps        [2,2] */
   int32_t max_cycles;   /* V-cycles (precision 0) or refinement steps (precision 1) [100] */
-  int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1)            [1] */
+  int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1)            [2] */
   int32_t use_graph;    /* capture one cycle as a CUDA graph and replay it            [1] */
-  double omega;         /* Gauss-Seidel relaxation factor                           [1.0] */
+  double omega;         /* Gauss-Seidel over-relaxation factor, in (0, 2)           [1.3] */
 } ibm_solve_opts;
 
 /* Solve report.  resid_history (host, optional) receives the relative residual after

@@ -63,6 +63,7 @@ ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device) {
   if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hscal, sizeof(double) * ibm::NSCAL);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->errflag, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->errflag, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     ibm_ctx_destroy(c);
     return ibm::check(e, "ibm_ctx_create");
@@ -79,6 +80,7 @@ ibm_status ibm_ctx_destroy(ibm_ctx *c) {
   if (c->scal) cudaFree(c->scal);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->errflag) cudaFree(c->errflag);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return IBM_OK;
 }
@@ -137,9 +139,9 @@ void ibm_solve_opts_default(ibm_solve_opts *o) {
   o->nu1 = 2;
   o->nu2 = 2;
   o->max_cycles = 100;
-  o->inner_cycles = 1;
+  o->inner_cycles = 2;
   o->use_graph = 1;
-  o->omega = 1.0;
+  o->omega = 1.3;
 }
 
 ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol, double *p_dev,

@@ -412,8 +412,21 @@ __device__ __forceinline__ void base_t(const double *c, int n, double v, int &i0
   t = tt < 0.0 ? 0.0 : (tt > 1.0 ? 1.0 : tt);
 }
 
+// one warp per ghost: the lanes split the triangle loops, then a warp reduction picks the
+// minimum squared distance (lowest triangle index on exact ties), the same result as a
+// sequential scan; lane 0 finishes the row
+__device__ __forceinline__ void warp_argmin(double &d, int &t, float &f) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double od = __shfl_xor_sync(0xffffffffu, d, o);
+    int ot = __shfl_xor_sync(0xffffffffu, t, o);
+    if (od < d || (od == d && ot < t)) { d = od; t = ot; }
+  }
+  (void)f;
+}
+
 __global__ void k_ghost_tables(GhostArgs a) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (g >= a.ng) return;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   long long lin = a.gcell[g];
@@ -429,33 +442,43 @@ __global__ void k_ghost_tables(GhostArgs a) {
     double d = mesh_box_dist(P, a.mr[m]);
     if (d < md) { md = d; m0 = m; }
   }
-  int bt = a.mr[m0].t0;
   float bc = 3.4e38f;
-  for (int t = a.mr[m0].t0; t < a.mr[m0].t1; ++t) {
+  int bt = a.mr[m0].t0;
+  for (int t = a.mr[m0].t0 + lane; t < a.mr[m0].t1; t += 32) {
     float4 c = a.cen[t];
     float dx = c.x - Pf[0], dy = c.y - Pf[1], dz = c.z - Pf[2];
     float d = dx * dx + dy * dy + dz * dz;
     if (d < bc) { bc = d; bt = t; }
   }
-  double best, Q[3], BQ[3];
-  closest_on_tri(P, a.tv + 9 * bt, a.tv + 9 * bt + 3, a.tv + 9 * bt + 6, BQ, best);
+  for (int o = 16; o > 0; o >>= 1) {
+    float ob = __shfl_xor_sync(0xffffffffu, bc, o);
+    int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+    if (ob < bc || (ob == bc && ot < bt)) { bc = ob; bt = ot; }
+  }
+  double best, Q[3];
+  closest_on_tri(P, a.tv + 9 * bt, a.tv + 9 * bt + 3, a.tv + 9 * bt + 6, Q, best);
   int bidx = bt;
-  // pass 2: every triangle whose box could hold a point as close (conservative margin)
+  // pass 2: every triangle whose box could hold a point as close (conservative margin);
+  // each lane keeps its own best, then the warp reduces
   double thr = sqrt(best) + 4e-6;
   for (int m = 0; m < a.nmesh; ++m) {
     if (mesh_box_dist(P, a.mr[m]) > thr) continue;
-    for (int t = a.mr[m].t0; t < a.mr[m].t1; ++t) {
+    for (int t = a.mr[m].t0 + lane; t < a.mr[m].t1; t += 32) {
       float lb = box_dist2(Pf, a.blo[t], a.bhi[t]);
       if ((double)lb > thr * thr) continue;
-      double d2;
-      closest_on_tri(P, a.tv + 9 * t, a.tv + 9 * t + 3, a.tv + 9 * t + 6, Q, d2);
+      double d2, Qt[3];
+      closest_on_tri(P, a.tv + 9 * t, a.tv + 9 * t + 3, a.tv + 9 * t + 6, Qt, d2);
       if (d2 < best || (d2 == best && t < bidx)) {
         best = d2; bidx = t;
-        BQ[0] = Q[0]; BQ[1] = Q[1]; BQ[2] = Q[2];
         thr = sqrt(best) + 4e-6;
       }
     }
   }
+  float unused = 0.f;
+  warp_argmin(best, bidx, unused);
+  if (lane != 0) return;
+  double BQ[3];
+  closest_on_tri(P, a.tv + 9 * bidx, a.tv + 9 * bidx + 3, a.tv + 9 * bidx + 6, BQ, best);
   double IP[3];
   for (int d = 0; d < 3; ++d) {
     IP[d] = (BQ[d] + BQ[d]) - P[d];
@@ -766,7 +789,7 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
-    k_ghost_tables<<<nblk(ng, 128), 128, 0, st>>>(ga);
+    k_ghost_tables<<<nblk(32 * ng, 128), 128, 0, st>>>(ga);
     CTRY(cudaGetLastError());
     CTRY(cudaStreamSynchronize(st));
   }

@@ -83,11 +83,14 @@ struct Hierarchy {
   double *gw64 = nullptr;
   float *gw32 = nullptr;
   double *gtmp = nullptr;                   // new ghost values (Jacobi)
-  void *graph_exec = nullptr;
+  void *graph_exec = nullptr;               // one captured cycle (see solve_impl)
+  long long graph_key = 0;
+  long long graph_launches = 0;             // kernels in the captured cycle
   // finest level ping-pong for the fused z-march sweep: the second buffer of the
   // level-0 unknown (p64 in FP64 mode, lv[0].e in mixed mode) and TMA tensor maps
   void *e_alt = nullptr;
   bool zmarch = false;
+  int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep
   CUtensorMap tm_e[2], tm_r, tm_m;
   void *tm_base[2] = {nullptr, nullptr};    // which buffer each tm_e describes
 };
@@ -102,6 +105,7 @@ struct ibm_ctx {
   int sm_count = 0;
   long long launches = 0;       // kernels launched by this context (all calls)
   int *errflag = nullptr;       // device flag: a bounded device-side wait gave up
+  cudaStream_t cap_stream = nullptr;   // private stream used only to capture CUDA graphs
 };
 
 struct ibm_tables {

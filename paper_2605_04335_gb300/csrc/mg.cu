@@ -290,7 +290,8 @@ __global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colou
   if (D == (T)0) return;
   T rhs = r[id] - (shift ? (T)(*shift) : (T)0);
   T res = stencil_sum(v, e, id, c) - D * e[id] - rhs;
-  e[id] += omega * res * (T)(1.0f / (float)D);
+  // FP32 relaxation step: the fixed point (res = 0 in T) is unchanged, FP64 work stays minimal
+  e[id] += (T)__fdividef((float)omega * (float)res, (float)D);
 }
 
 // ghost rows (Jacobi): gnew = sum_k w_k e[src_k] (+ rhs at the ghost cell)
@@ -657,8 +658,17 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
             make_map(&h->tm_m, L0.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, L0.g, zm::BXM, zm::RY);
   h->tm_base[0] = e0;
   h->tm_base[1] = h->e_alt;
-  h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(zm::Smem<T>)) == cudaSuccess;
+  // the FP64 smoother is bound by the FP64 pipe, not by memory: it keeps the two-pass kernel,
+  // whose small blocks give the occupancy that hides FP64 latency
+  h->zmarch = sizeof(T) == 4 && ok &&
+              cudaFuncSetAttribute(zm::k_sweep_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(zm::Smem<T>)) == cudaSuccess;
+  int per_sm = 0;
+  if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T>, zm::THREADS,
+                                                                 sizeof(zm::Smem<T>)) == cudaSuccess && per_sm > 0)
+    h->zm_per_sm = per_sm;
+  else
+    h->zmarch = false;
 }
 
 template <typename T>
@@ -841,9 +851,10 @@ void sweep_zmarch(Solver &S, T *&e, const double *shift) {
   a.out = other;
   a.err = S.ctx->errflag;
   const int gx = (a.nx + zm::TX - 1) / zm::TX, gy = (a.ny + zm::TY - 1) / zm::TY;
-  const int per_sm = std::max(1, (int)((227 * 1024) / (sizeof(zm::Smem<T>) + 1024)));
+  const int per_sm = std::max(1, h->zm_per_sm);
   const long long target = (long long)per_sm * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152);
-  int chunks = (int)std::max<long long>(1, std::min<long long>(a.nz, (target + gx * gy - 1) / (gx * gy)));
+  // one wave: tiles x chunks <= resident CTAs (a second, partly filled wave would idle most SMs)
+  int chunks = (int)std::max<long long>(1, std::min<long long>(a.nz, target / (gx * gy)));
   a.kz = (a.nz + chunks - 1) / chunks;
   chunks = (a.nz + a.kz - 1) / a.kz;
   dim3 grid(gx, gy, chunks);
@@ -1020,19 +1031,60 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
   double rel0 = rel;
   if (rel <= tol) result = IBM_OK;
-  while (result != IBM_OK && cycles < opts->max_cycles) {
+  // one cycle: V-cycle (FP64) or FP32 V-cycle(s) + FP64 update (mixed), then the FP64 fine
+  // residual with its norms.  Launched directly, or captured once as a CUDA graph (on the
+  // context's capture stream) and replayed; the pointer swaps of the fused sweep cancel
+  // over a cycle when its number of fine sweeps is even, so the graph stays valid.
+  auto body = [&](cudaStream_t bs) {
+    S.st = bs;
     if (prec == 0) {
       vcycle<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, nullptr);
       fine_residual(S, h->p64, nullptr, true);
     } else {
       float *&e32 = reinterpret_cast<float *&>(L0.e);
       for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
-        if (q == 0) IBM_TRY(cudaMemsetAsync(e32, 0, sizeof(float) * L0.g.ntot, st));
+        if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * L0.g.ntot, bs);
         vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
       }
-      k_update_p<<<1216, 256, 0, st>>>(h->p64, e32, L0.g.ntot);
+      k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, L0.g.ntot);
       ctx->launches += 1;
       fine_residual(S, h->p64, r32, true);
+    }
+    S.st = st;
+  };
+  const long long sweeps_per_cycle =
+      (long long)(opts->nu1 + opts->nu2) * (prec == 1 ? std::max(1, opts->inner_cycles) : 1);
+  const bool graph = opts->use_graph && ctx->cap_stream && (!h->zmarch || sweeps_per_cycle % 2 == 0);
+  long long graph_launches = 0;
+  if (graph) {
+    const long long key = ((long long)opts->nu1 << 48) ^ ((long long)opts->nu2 << 40) ^
+                          ((long long)opts->inner_cycles << 32) ^ (long long)(opts->omega * 1e6);
+    if (!h->graph_exec || h->graph_key != key) {
+      if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
+      h->graph_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      const long long l0 = ctx->launches;
+      IBM_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      body(ctx->cap_stream);
+      cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+      if (ce != cudaSuccess) return check(ce, "graph capture");
+      cudaGraphExec_t ge = nullptr;
+      ce = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return check(ce, "graph instantiate");
+      h->graph_exec = ge;
+      h->graph_key = key;
+      h->graph_launches = ctx->launches - l0;
+      ctx->launches = l0;
+    }
+    graph_launches = h->graph_launches;
+  }
+  while (result != IBM_OK && cycles < opts->max_cycles) {
+    if (graph) {
+      IBM_TRY(cudaGraphLaunch((cudaGraphExec_t)h->graph_exec, st));
+      ctx->launches += graph_launches;
+    } else {
+      body(st);
     }
     IBM_TRY(cudaGetLastError());
     IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));

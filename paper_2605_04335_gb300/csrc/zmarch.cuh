@@ -5,15 +5,20 @@
 //   1. updates the red cells of plane q on the tile plus a one-cell ring (the ring is
 //      recomputed by both neighbouring CTAs, so no inter-CTA exchange is needed),
 //   2. updates the black cells of plane q-1 on the tile (its red neighbours in planes
-//      q-2, q-1, q are all new by then),
-//   3. stores plane q-1 of the tile to the output array.
+//      q-2, q-1, q are all new by then) and stores plane q-1 of the tile from registers.
 // Every value is read from the input array and written to a separate output array, so the
 // result is exactly one red half-sweep followed by one black half-sweep (deterministic,
-// independent of the tiling).  Planes of e (halo 2 in x and y), the right-hand side and
-// the mask (halo 1) arrive by cp.async.bulk.tensor into rings of shared-memory buffers two
-// steps ahead of their use, with one mbarrier per buffer; the tensor maps zero-fill
-// everything outside the padded arrays.  Waits are bounded: a wait that gives up sets
-// the error flag, waits (bounded) for the copies still in flight and returns.
+// independent of the tiling).
+//
+// Each thread owns a fixed strip of 4 consecutive x-cells of the tile (plus, for some
+// threads, a strip of the ring): its coefficients stay in registers for the whole march
+// and every shared-memory access of a strip is a 16-byte vector access.
+//
+// Planes of e (halo 2 in x and y), the right-hand side and the mask (halo 1) arrive by
+// cp.async.bulk.tensor into rings of shared-memory buffers DP steps ahead of their use,
+// one mbarrier per buffer; the tensor maps zero-fill everything outside the padded arrays.
+// Waits are bounded: a wait that gives up sets the error flag, waits (bounded) for the
+// copies still in flight and returns.
 #pragma once
 
 #include <cuda.h>
@@ -30,13 +35,17 @@ constexpr int BX = TX + 8;      // staged width of e and rhs: x in [-4, TX + 4)
 constexpr int BXM = TX + 16;    // staged width of the mask (an 8-bit box row must be 16-byte multiple)
 constexpr int EY = TY + 4;      // e rows: y in [-2, TY + 2)
 constexpr int RY = TY + 2;      // rhs / mask rows: y in [-1, TY + 1)
-constexpr int THREADS = 256;
-// prefetch distance in planes (bytes in flight per SM hide the DRAM latency); rings hold
-// the planes in use (e: q-2 .. q+1, rhs/mask: q-1 .. q) plus the ones in flight
-template <typename T> struct Depth { static constexpr int D = sizeof(T) == 4 ? 3 : 2; };
+constexpr int THREADS = (TX / 4) * TY;       // one interior strip per thread
+constexpr int RING_ROW = TX / 4 + 2;         // strips per ring row (x from -4 to TX + 3)
+constexpr int RING = 2 * RING_ROW + 2 * TY;  // ring strips (top, bottom, left, right)
+static_assert(RING <= THREADS, "one ring strip per thread at most");
+constexpr long long WAIT_LIMIT = 1LL << 22;
+
+// prefetch distance in planes; rings hold the planes in use (e: q-2 .. q+1, rhs/mask:
+// q-1 .. q) plus the ones in flight
+template <typename T> struct Depth { static constexpr int D = sizeof(T) == 4 ? 2 : 1; };
 template <typename T> constexpr int NE = 4 + Depth<T>::D;
 template <typename T> constexpr int NR = 2 + Depth<T>::D;
-constexpr long long WAIT_LIMIT = 1LL << 22;
 
 constexpr int pad128(int bytes) { return (bytes + 127) / 128 * 128; }
 
@@ -48,7 +57,6 @@ struct Smem {
   alignas(128) uint8_t m[NR<T>][pad128(RY * BXM)];
   alignas(8) uint64_t bar_e[NE<T>];
   alignas(8) uint64_t bar_r[NR<T>];
-  T cx[2][TX + 2], cy[2][TY + 2], sx[TX + 2], sy[TY + 2];
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -100,27 +108,100 @@ struct Args {
   int *err;
 };
 
-// one colour update of cell (x, y) of plane buffer P (planes pm, pp below/above):
-// e += omega (sum_d c_d e_nb - D e - rhs) / D.  The residual is formed in T; the relaxation
-// factor 1/D and the step are FP32 (they do not move the fixed point, which is the exact
-// T-precision solution of the row), keeping FP64 work to the stencil in the FP64 variant.
+// four consecutive elements: one 16-byte (float) or two 16-byte (double) accesses
 template <typename T>
-__device__ __forceinline__ void relax(const Smem<T> &s, T *P, const T *pm, const T *pp, const T *R, const uint8_t *M,
-                                      int x, int y, T czm, T czp, T syz, T sh, float omega) {
-  const int ie = (y + 2) * BX + (x + 4);
-  const int ir = (y + 1) * BX + (x + 4);
-  if (M[(y + 1) * BXM + (x + 4)] != 0) return;
-  const T D = s.sx[x + 1] + syz;
-  T sum = s.cx[0][x + 1] * P[ie - 1];
-  sum += s.cx[1][x + 1] * P[ie + 1];
-  sum += s.cy[0][y + 1] * P[ie - BX];
-  sum += s.cy[1][y + 1] * P[ie + BX];
-  sum += czm * pm[ie];
-  sum += czp * pp[ie];
-  const T pc = P[ie];
-  const T res = (sum - D * pc) - (R[ir] - sh);
-  const float step = omega * (float)res * __frcp_rn((float)D);
-  P[ie] = pc + (T)step;
+struct Q4 {
+  T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ Q4<T> ld4(const T *p) {
+  Q4<T> q;
+  if constexpr (sizeof(T) == 4) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    q.v[0] = a.x; q.v[1] = a.y; q.v[2] = a.z; q.v[3] = a.w;
+  } else {
+    double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+  }
+  return q;
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const Q4<T> &q) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+  } else {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(q.v[0], q.v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(q.v[2], q.v[3]);
+  }
+}
+
+// a strip of 4 x-cells with its coefficients (registers for the whole march)
+template <typename T>
+struct Strip {
+  int xs, y;          // tile coordinates of the first cell
+  unsigned valid;     // bit u: cell xs+u is in the grid and in [xlo, xhi]
+  T cxm[4], cxp[4], sx[4], cym, cyp, sy;
+};
+
+template <typename T>
+__device__ __forceinline__ void make_strip(Strip<T> &S, const Args<T> &a, int x0, int y0, int xs, int y, int xlo,
+                                           int xhi) {
+  S.xs = xs; S.y = y; S.valid = 0;
+  const int gj = y0 + y;
+  const bool jok = gj >= 0 && gj < a.ny;
+  for (int u = 0; u < 4; ++u) {
+    const int x = xs + u, gi = x0 + x;
+    const bool ok = jok && gi >= 0 && gi < a.nx && x >= xlo && x <= xhi;
+    if (ok) S.valid |= 1u << u;
+    S.cxm[u] = ok ? a.cxm[gi] : (T)0;
+    S.cxp[u] = ok ? a.cxp[gi] : (T)0;
+    S.sx[u] = ok ? a.sdx[gi] : (T)0;
+  }
+  S.cym = jok ? a.cym[gj] : (T)0;
+  S.cyp = jok ? a.cyp[gj] : (T)0;
+  S.sy = jok ? a.sdy[gj] : (T)0;
+}
+
+// Relax the cells of colour par ((gi + gj + k) mod 2 == par) of strip S in plane buffer P
+// (Pm, Pp: planes k-1, k+1): e += omega (sum_d c_d e_nb - D e - rhs) / D.  The residual is
+// formed in T; the relaxation factor and step are FP32 (they do not move the fixed point,
+// the exact T-precision solution of the row), keeping FP64 work to the stencil itself.
+// C returns the strip's values after the update.
+template <typename T>
+__device__ __forceinline__ void relax_colour(const Strip<T> &S, T *P, const T *Pm, const T *Pp, const T *R,
+                                             const uint8_t *M, int par, int x0, int y0, int k, T czm, T czp, T sz,
+                                             T sh, float om, Q4<T> &C) {
+  const int ie = (S.y + 2) * BX + (S.xs + 4);
+  C = ld4(P + ie);
+  const unsigned m4 = *reinterpret_cast<const unsigned *>(M + (S.y + 1) * BXM + (S.xs + 4));
+  // cells of colour par in the strip: u = ua and ua + 2
+  const int ua = (x0 + S.xs + y0 + S.y + k + par) & 1;
+  unsigned act = 0;
+  for (int u = ua; u < 4; u += 2)
+    if (((S.valid >> u) & 1u) && ((m4 >> (8 * u)) & 0xffu) == 0u) act |= 1u << u;
+  if (!act) return;
+  const Q4<T> N = ld4(P + ie - BX), So = ld4(P + ie + BX), B = ld4(Pm + ie), U = ld4(Pp + ie);
+  const Q4<T> Rh = ld4(R + (S.y + 1) * BX + (S.xs + 4));
+  const T L = P[ie - 1], Rr = P[ie + 4];
+  const T syz = S.sy + sz;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (!((act >> u) & 1u)) continue;
+    const T west = u == 0 ? L : C.v[u - 1];
+    const T east = u == 3 ? Rr : C.v[u + 1];
+    const T D = S.sx[u] + syz;
+    T sum = S.cxm[u] * west;
+    sum += S.cxp[u] * east;
+    sum += S.cym * N.v[u];
+    sum += S.cyp * So.v[u];
+    sum += czm * B.v[u];
+    sum += czp * U.v[u];
+    const T res = (sum - D * C.v[u]) - (Rh.v[u] - sh);
+    C.v[u] += (T)__fdividef(om * (float)res, (float)D);
+  }
+  st4(P + ie, C);
 }
 
 template <typename T>
@@ -129,36 +210,38 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
                                                          const __grid_constant__ CUtensorMap tm_m, Args<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<T> &s = *reinterpret_cast<Smem<T> *>(smem_raw);
+  constexpr int NEt = NE<T>, NRt = NR<T>, DP = Depth<T>::D;
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * a.kz;
   const int k1 = min(a.nz, k0 + a.kz);
   if (k0 >= k1) return;
-  // 1-D coefficients of the tile (halo 1); zero outside the grid
-  for (int q = tid; q < TX + 2; q += THREADS) {
-    int i = x0 + q - 1;
-    bool ok = i >= 0 && i < a.nx;
-    s.cx[0][q] = ok ? a.cxm[i] : (T)0;
-    s.cx[1][q] = ok ? a.cxp[i] : (T)0;
-    s.sx[q] = ok ? a.sdx[i] : (T)0;
-  }
-  for (int q = tid; q < TY + 2; q += THREADS) {
-    int j = y0 + q - 1;
-    bool ok = j >= 0 && j < a.ny;
-    s.cy[0][q] = ok ? a.cym[j] : (T)0;
-    s.cy[1][q] = ok ? a.cyp[j] : (T)0;
-    s.sy[q] = ok ? a.sdy[j] : (T)0;
-  }
-  constexpr int NEt = NE<T>, NRt = NR<T>, DP = Depth<T>::D;
   if (tid == 0) {
     for (int b = 0; b < NEt; ++b) mbar_init(&s.bar_e[b], 1);
     for (int b = 0; b < NRt; ++b) mbar_init(&s.bar_r[b], 1);
     fence_mbar_init();
   }
+  // this thread's interior strip, and its ring strip (red updates of the one-cell ring)
+  Strip<T> Si, Sr;
+  make_strip(Si, a, x0, y0, 4 * (tid % (TX / 4)), tid / (TX / 4), 0, TX - 1);
+  const bool has_ring = tid < RING;
+  {
+    int xs = 0, y = 0;
+    if (tid < 2 * RING_ROW) {
+      y = tid < RING_ROW ? -1 : TY;
+      xs = -4 + 4 * (tid % RING_ROW);
+    } else {
+      const int r = tid - 2 * RING_ROW;
+      y = r % TY;
+      xs = r < TY ? -4 : TX;
+    }
+    make_strip(Sr, a, x0, y0, xs, y, -1, TX);
+    if (!has_ring) Sr.valid = 0;
+  }
   __syncthreads();
   const unsigned ebytes = EY * BX * sizeof(T), rbytes = RY * BX * sizeof(T) + RY * BXM;
   // padded coordinates: cell (i, j, k) at (i + OX, j + 1, k + 1); OX = 4
-  auto load_e = [&](int plane) {   // plane in [k0-2, k1+2]
+  auto load_e = [&](int plane) {
     int b = (plane + 2 * NEt) % NEt;
     mbar_expect_tx(&s.bar_e[b], ebytes);
     tma_load3(s.e[b], &tm_e, &s.bar_e[b], x0, y0 - 1, plane + 1);
@@ -169,15 +252,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
     tma_load3(s.r[b], &tm_r, &s.bar_r[b], x0, y0, plane + 1);
     tma_load3(s.m[b], &tm_m, &s.bar_r[b], x0, y0, plane + 1);
   };
-  // phase bit per buffer: number of completed loads of that buffer, mod 2
-  unsigned pe = 0, pr = 0;   // bit b = parity expected for buffer b
-  // prologue: e planes k0-2 .. k0-1+DP and rhs/mask planes k0-1 .. k0-2+DP; step q then
-  // prefetches e plane q+1+DP and rhs/mask plane q+DP and waits for e plane q+1 and
-  // rhs/mask plane q, so every load is issued once and waited for once
-  if (tid == 0) {
-    for (int pl = k0 - 2; pl <= min(k0 - 1 + DP, k1 + 1); ++pl) load_e(pl);
-    for (int pl = k0 - 1; pl <= min(k0 - 2 + DP, k1); ++pl) load_r(pl);
-  }
+  unsigned pe = 0, pr = 0;   // bit b: parity of the next completion of buffer b
   bool bad = false;
   auto wait_e = [&](int plane) {
     int b = (plane + 2 * NEt) % NEt;
@@ -189,71 +264,56 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
     if (!bad && !mbar_wait(&s.bar_r[b], (pr >> b) & 1u)) bad = true;
     pr ^= 1u << b;
   };
+  // prologue: e planes k0-2 .. k0-1+DP and rhs/mask planes k0-1 .. k0-2+DP.  Step q then
+  // waits for e plane q+1 and rhs/mask plane q and, after the step's first barrier (so no
+  // thread still reads the buffers being refilled), prefetches e plane q+1+DP (into the
+  // buffer of plane q-3) and rhs/mask plane q+DP (buffer of plane q-2).  Every load is
+  // issued once and waited for once.
+  if (tid == 0) {
+    for (int pl = k0 - 2; pl <= min(k0 - 1 + DP, k1 + 1); ++pl) load_e(pl);
+    for (int pl = k0 - 1; pl <= min(k0 - 2 + DP, k1); ++pl) load_r(pl);
+  }
   wait_e(k0 - 2);
   wait_e(k0 - 1);
   const T sh = a.shift ? (T)(*a.shift) : (T)0;
   const float om = a.omega;
   for (int q = k0 - 1; q <= k1; ++q) {
-    // prefetch: e plane q+1+DP (its buffer held plane q-3), rhs/mask plane q+DP (held q-2);
-    // both were last read in the black phase of step q-1, which ended at a barrier
+    wait_e(q + 1);
+    wait_r(q);
+    if (__syncthreads_or(bad)) break;
     if (tid == 0) {
       fence_proxy_async();
       if (q + 1 + DP <= k1 + 1) load_e(q + 1 + DP);
       if (q + DP <= k1) load_r(q + DP);
     }
-    wait_e(q + 1);
-    wait_r(q);
-    if (__syncthreads_or(bad)) break;
     T *Pm = s.e[(q - 1 + 2 * NEt) % NEt], *P = s.e[(q + 2 * NEt) % NEt], *Pp = s.e[(q + 1 + 2 * NEt) % NEt];
     // red cells of plane q on the tile plus the ring
     if (q >= 0 && q < a.nz) {
-      const T czm = a.czm[q], czp = a.czp[q], szk = a.sdz[q];
+      const T czm = a.czm[q], czp = a.czp[q], sz = a.sdz[q];
       const T *R = s.r[(q + 2 * NRt) % NRt];
       const uint8_t *M = s.m[(q + 2 * NRt) % NRt];
-      const int rowred = (TX + 2) / 2;
-      for (int c = tid; c < rowred * (TY + 2); c += THREADS) {
-        int y = c / rowred - 1;
-        int gj = y0 + y;
-        int x = ((gj + q) & 1 ? -1 : 0) + 2 * (c % rowred);
-        int gi = x0 + x;
-        if (gi < 0 || gi >= a.nx || gj < 0 || gj >= a.ny) continue;
-        relax<T>(s, P, Pm, Pp, R, M, x, y, czm, czp, s.sy[y + 1] + szk, sh, om);
-      }
+      Q4<T> C;
+      relax_colour<T>(Si, P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, C);
+      if (Sr.valid) relax_colour<T>(Sr, P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, C);
     }
     __syncthreads();
-    // black cells of plane q-1 on the tile, then store plane q-1
+    // black cells of plane q-1 on the tile; store the thread's strip from registers
     const int kb = q - 1;
     if (kb >= k0 && kb < k1) {
-      T *Bm = s.e[(kb - 1 + 2 * NEt) % NEt], *B = s.e[(kb + 2 * NEt) % NEt], *Bp = P;
-      const T czm = a.czm[kb], czp = a.czp[kb], szk = a.sdz[kb];
+      T *Bm = s.e[(kb - 1 + 2 * NEt) % NEt], *B = s.e[(kb + 2 * NEt) % NEt];
+      const T czm = a.czm[kb], czp = a.czp[kb], sz = a.sdz[kb];
       const T *R = s.r[(kb + 2 * NRt) % NRt];
       const uint8_t *M = s.m[(kb + 2 * NRt) % NRt];
-      for (int c = tid; c < (TX / 2) * TY; c += THREADS) {
-        int y = c / (TX / 2);
-        int gj = y0 + y;
-        int x = ((gj + kb + 1) & 1) + 2 * (c % (TX / 2));
-        int gi = x0 + x;
-        if (gi >= a.nx || gj >= a.ny) continue;
-        relax<T>(s, B, Bm, Bp, R, M, x, y, czm, czp, s.sy[y + 1] + szk, sh, om);
-      }
-      __syncthreads();
-      // store the tile of plane kb (every cell: updated fluid values, copied others)
-      constexpr int V = 4;
-      for (int c = tid; c < (TX / V) * TY; c += THREADS) {
-        int y = c / (TX / V), x = V * (c % (TX / V));
-        int gj = y0 + y, gi = x0 + x;
-        if (gj >= a.ny || gi >= a.nx) continue;
-        const T *src = &B[(y + 2) * BX + (x + 4)];
+      Q4<T> C;
+      relax_colour<T>(Si, B, Bm, P, R, M, 1, x0, y0, kb, czm, czp, sz, sh, om, C);
+      if (Si.valid) {
+        const int gj = y0 + Si.y, gi = x0 + Si.xs;
         T *dst = a.out + ((long long)(kb + 1) * (a.ny + 2) + (gj + 1)) * a.px + (gi + 4);
-        if (gi + V <= a.nx) {
-          if (sizeof(T) == 4) {
-            *reinterpret_cast<float4 *>(dst) = *reinterpret_cast<const float4 *>(src);
-          } else {
-            reinterpret_cast<double2 *>(dst)[0] = reinterpret_cast<const double2 *>(src)[0];
-            reinterpret_cast<double2 *>(dst)[1] = reinterpret_cast<const double2 *>(src)[1];
-          }
+        if (Si.valid == 0xfu) {
+          st4(dst, C);
         } else {
-          for (int u = 0; u < V && gi + u < a.nx; ++u) dst[u] = src[u];
+          for (int u = 0; u < 4; ++u)
+            if ((Si.valid >> u) & 1u) dst[u] = C.v[u];
         }
       }
     }

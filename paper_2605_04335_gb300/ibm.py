@@ -159,9 +159,9 @@ class SolveOpts:
     nu1: int = 2
     nu2: int = 2
     max_cycles: int = 100
-    inner_cycles: int = 1
+    inner_cycles: int = 2
     use_graph: int = 1
-    omega: float = 1.0
+    omega: float = 1.3
 
 
 def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, stream=None, history_cap: int = 256,

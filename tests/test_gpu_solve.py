@@ -109,3 +109,21 @@ def test_warm_start_and_not_converged(ctx):
     rep3 = T.solve(rhs, p3, TOL, pkg.SolveOpts(precision=0, max_cycles=1), raise_on_error=False)
     assert rep3["status"] == "IBM_ERR_NOT_CONVERGED"
     T.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_is_bit_identical_and_deterministic(ctx, prec):
+    """Replaying the captured cycle gives the same bits as direct launches, run after run
+    (fixed reduction trees, Jacobi ghost updates, ping-pong sweeps)."""
+    pkg, c = ctx
+    f = synth.faces_tanh(40, 2.0)
+    T = pkg.Tables(c, f, synth.faces_uniform(36), f, [synth.octa_sphere(4, (0.5, 0.5, 0.5), 0.2)])
+    b = synth.rhs_divergence(f, synth.faces_uniform(36), f, 11)
+    outs = []
+    for g in (0, 1, 1, 0):
+        p, rep = _solve_gpu(pkg, T, b, prec, use_graph=g)
+        outs.append((p, rep["history"].copy()))
+    for p, hst in outs[1:]:
+        assert np.array_equal(p, outs[0][0])
+        assert np.array_equal(hst, outs[0][1])
+    T.close()
