@@ -159,6 +159,29 @@ ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precis
 /* Number of CUDA kernels this context has launched so far (all calls). */
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
 
+/* Relative projected residual of a pressure field, with NO device allocation.  The paper
+ * has no counterpart: this exists for callers that cannot allocate device memory after
+ * start-up -- e.g. a flow solver that owns a fixed device arena, where cudaMalloc/cudaFree
+ * would synchronise the whole device (breaking compute/communication overlap) or could
+ * fail in the middle of a time-step loop.  It needs no context and no tables object: the
+ * caller passes the grid (host faces), the classification as exported by
+ * ibm_tables_export (iblank, ghost cells, interpolation sources, weights, row scales), the
+ * right-hand side and the pressure (user layout, ghost values at ghost cells, as
+ * poisson_solve returns it), all on the current CUDA device.
+ *   result (host, 3 doubles): ||S P r|| / ||S P b||, ||S P r||, ||S P b||, with the same
+ *   definitions as poisson_solve.
+ * Scratch: one fixed device array of about 0.2 MB inside this library, held by every GPU
+ * that loads it until the process exits.  Grids with more than 2048 cells along any axis
+ * are rejected with IBM_ERR_CAPACITY.  The first call on a device looks up that array's
+ * device address (make it before any stream capture).  Every call reuses the same array:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Synchronises `stream` before returning. */
+ibm_status ibm_residual_norm_noalloc(const ibm_grid *grid, const uint8_t *iblank_dev, int64_t nghost,
+                                     const int64_t *ghost_cell_dev, const int64_t *ghost_ref_dev,
+                                     const double *ghost_w_dev, const double *ghost_scale_dev,
+                                     const double *rhs_dev, const double *p_dev, double *result,
+                                     void *stream);
+
 #ifdef __cplusplus
 }
 #endif

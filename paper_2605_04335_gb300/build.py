@@ -17,7 +17,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path
           "-I", CSRC, "--expt-relaxed-constexpr"]
 # per-file extra flags: the classification unit keeps every FP64 operation separately rounded
 EXTRA = {"classify.cu": ["-fmad=false"]}
-SOURCES = ["capi.cu", "classify.cu", "mg.cu"]
+SOURCES = ["capi.cu", "classify.cu", "mg.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -78,6 +78,8 @@ def load_library():
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
+        "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P,
+                                            C.POINTER(C.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +190,20 @@ def ibm_ctx_launch_count(ctx) -> int:
     v = C.c_int64()
     _check(load_library().ibm_ctx_launch_count(ctx, C.byref(v)), "ibm_ctx_launch_count")
     return int(v.value)
+
+
+def ibm_residual_norm_noalloc(xf, yf, zf, iblank, cell, ref, w, scale, rhs, p, stream=None):
+    """Relative projected residual of p, computed by the library without allocating device
+    memory (for callers that cannot allocate after start-up).  Device arrays are torch CUDA
+    tensors in the layout ibm_tables_export produces.  Returns (rel, ||SPr||, ||SPb||)."""
+    f = [np.ascontiguousarray(a, dtype=np.float64) for a in (xf, yf, zf)]
+    g = ibm_grid(f[0].size - 1, f[1].size - 1, f[2].size - 1, f[0].ctypes.data, f[1].ctypes.data, f[2].ctypes.data)
+    out = (C.c_double * 3)()
+    ng = int(cell.numel()) if cell is not None else 0
+    _check(load_library().ibm_residual_norm_noalloc(C.byref(g), _ptr(iblank), ng, _ptr(cell), _ptr(ref), _ptr(w),
+                                                    _ptr(scale), _ptr(rhs), _ptr(p), out, _stream(stream)),
+           "ibm_residual_norm_noalloc")
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 # ----------------------------------------------------------------------------- conveniences
