@@ -80,46 +80,95 @@ def _closed_range(sorted_vals: np.ndarray, lo, hi):
 
 def inside_mesh(grid: Grid, verts: np.ndarray, tris: np.ndarray) -> np.ndarray:
     """Boolean [k][j][i]: cell centre strictly inside the closed mesh (exact test)."""
+    nz, ny, nx = grid.shape
+    out = np.zeros((nz, ny, nx), dtype=bool)
+    box, sub = inside_mesh_box(grid, verts, tris)
+    if box is not None:
+        (k0, j0, i0) = box
+        out[k0:, j0:j0 + sub.shape[1], i0:i0 + sub.shape[2]] = sub
+    return out
+
+
+def inside_mesh_box(grid: Grid, verts: np.ndarray, tris: np.ndarray):
+    """The inside test on the cells that can be inside: columns whose centre lies in the
+    mesh's xy box, planes from the mesh's lowest centre up to the top of the grid (cells
+    outside that region have no crossing below them, so their parity is even).  Returns
+    ((k0, j0, i0), boolean [nz-k0][nj][ni]) or (None, None).
+
+    Every (triangle, column) pair of a triangle's xy box is tested at once: integer edge
+    functions (exact in int64), the top-left rule, then the crossing height N / D.  N needs
+    up to 82 bits, so its floor is taken from a float64 estimate whose error is far below
+    one lattice unit, and pairs whose estimate lies within 1e-6 of an integer are redone
+    in exact Python integers.
+    """
     Xc, Yc, Zc = snap(grid.xc), snap(grid.yc), snap(grid.zc)
     V = snap(verts)
     nz, ny, nx = grid.shape
+    if V.size == 0:
+        return None, None
+    bi0, bi1 = _closed_range(Xc, int(V[:, 0].min()), int(V[:, 0].max()))
+    bj0, bj1 = _closed_range(Yc, int(V[:, 1].min()), int(V[:, 1].max()))
+    bk0 = int(np.searchsorted(Zc, int(V[:, 2].min()), "left"))
+    if bi0 >= bi1 or bj0 >= bj1 or bk0 >= nz:
+        return None, None
+    # local sub-box: columns [bj0, bj1) x [bi0, bi1), planes [bk0, nz)
+    Xc, Yc, Zc = Xc[bi0:bi1], Yc[bj0:bj1], Zc[bk0:]
+    nz, ny, nx = Zc.size, Yc.size, Xc.size
     toggles = np.zeros((nz + 1, ny, nx), dtype=np.uint8)
     onsurf = np.zeros((nz, ny, nx), dtype=bool)
-    for t in range(tris.shape[0]):
-        A = [int(v) for v in V[tris[t, 0]]]
-        B = [int(v) for v in V[tris[t, 1]]]
-        C = [int(v) for v in V[tris[t, 2]]]
-        area = _orient2d(A[0], A[1], B[0], B[1], C[0], C[1])
-        xs = (min(A[0], B[0], C[0]), max(A[0], B[0], C[0]))
-        ys = (min(A[1], B[1], C[1]), max(A[1], B[1], C[1]))
+    T = np.asarray(tris, dtype=np.int64)
+    A, B, Cv = V[T[:, 0]].copy(), V[T[:, 1]].copy(), V[T[:, 2]].copy()
+    area = _orient2d(A[:, 0], A[:, 1], B[:, 0], B[:, 1], Cv[:, 0], Cv[:, 1])
+    for t in np.flatnonzero(area == 0):                  # vertical (or degenerate) triangles
+        a, b, c = [[int(v) for v in X[t]] for X in (A, B, Cv)]
+        xs = (min(a[0], b[0], c[0]), max(a[0], b[0], c[0]))
+        ys = (min(a[1], b[1], c[1]), max(a[1], b[1], c[1]))
         i0, i1 = _closed_range(Xc, *xs)
         j0, j1 = _closed_range(Yc, *ys)
-        if i0 >= i1 or j0 >= j1:
-            continue
-        QX, QY = np.meshgrid(Xc[i0:i1], Yc[j0:j1], indexing="xy")   # [j][i]
-        if area == 0:
-            _mark_vertical(A, B, C, QX, QY, Zc, onsurf, i0, j0)
-            continue
-        if area < 0:
-            B, C = C, B
-            area = -area
-        wa = _orient2d(B[0], B[1], C[0], C[1], QX, QY)
-        wb = _orient2d(C[0], C[1], A[0], A[1], QX, QY)
-        wc = _orient2d(A[0], A[1], B[0], B[1], QX, QY)
-        cov = ((wa > 0) | ((wa == 0) & _top_left(B[0], B[1], C[0], C[1]))) \
-            & ((wb > 0) | ((wb == 0) & _top_left(C[0], C[1], A[0], A[1]))) \
-            & ((wc > 0) | ((wc == 0) & _top_left(A[0], A[1], B[0], B[1])))
-        jj, ii = np.nonzero(cov)
-        for a, b in zip(jj.tolist(), ii.tolist()):
-            # height of the crossing: N / D with D = 2*area > 0 (exact rationals)
-            N = int(wa[a, b]) * A[2] + int(wb[a, b]) * B[2] + int(wc[a, b]) * C[2]
-            q, rem = divmod(N, area)
-            ks = int(np.searchsorted(Zc, q, "right"))   # first centre strictly above the crossing
-            toggles[ks, j0 + a, i0 + b] ^= 1
-            if rem == 0 and ks >= 1 and int(Zc[ks - 1]) == q:
-                onsurf[ks - 1, j0 + a, i0 + b] = True
+        if i0 < i1 and j0 < j1:
+            QX, QY = np.meshgrid(Xc[i0:i1], Yc[j0:j1], indexing="xy")
+            _mark_vertical(a, b, c, QX, QY, Zc, onsurf, i0, j0)
+    sel = np.flatnonzero(area != 0)
+    A, B, Cv, area = A[sel], B[sel], Cv[sel], area[sel]
+    neg = area < 0                                       # make every projection counter-clockwise
+    B[neg], Cv[neg] = Cv[neg].copy(), B[neg].copy()
+    area = np.abs(area)
+    lo = np.minimum(np.minimum(A, B), Cv)
+    hi = np.maximum(np.maximum(A, B), Cv)
+    i0 = np.searchsorted(Xc, lo[:, 0], "left"); i1 = np.searchsorted(Xc, hi[:, 0], "right")
+    j0 = np.searchsorted(Yc, lo[:, 1], "left"); j1 = np.searchsorted(Yc, hi[:, 1], "right")
+    ni, nj = np.maximum(i1 - i0, 0), np.maximum(j1 - j0, 0)
+    cnt = ni * nj
+    tri = np.repeat(np.arange(cnt.size), cnt)
+    loc = np.arange(tri.size) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    ii = i0[tri] + loc % np.maximum(ni[tri], 1)
+    jj = j0[tri] + loc // np.maximum(ni[tri], 1)
+    qx, qy = Xc[ii], Yc[jj]
+    a, b, c = A[tri], B[tri], Cv[tri]
+    wa = _orient2d(b[:, 0], b[:, 1], c[:, 0], c[:, 1], qx, qy)
+    wb = _orient2d(c[:, 0], c[:, 1], a[:, 0], a[:, 1], qx, qy)
+    wc = _orient2d(a[:, 0], a[:, 1], b[:, 0], b[:, 1], qx, qy)
+    tl = lambda p, q: (q[:, 0] > p[:, 0]) | ((q[:, 0] == p[:, 0]) & (p[:, 1] > q[:, 1]))
+    cov = ((wa > 0) | ((wa == 0) & tl(b, c))) & ((wb > 0) | ((wb == 0) & tl(c, a))) \
+        & ((wc > 0) | ((wc == 0) & tl(a, b)))
+    k = np.flatnonzero(cov)
+    wa, wb, wc, a, b, c, ar, ii, jj = wa[k], wb[k], wc[k], a[k], b[k], c[k], area[tri[k]], ii[k], jj[k]
+    zf = (wa.astype(np.float64) * a[:, 2] + wb.astype(np.float64) * b[:, 2] + wc.astype(np.float64) * c[:, 2]) \
+        / ar.astype(np.float64)
+    q = np.floor(zf).astype(np.int64)
+    exact_hit = np.zeros(zf.size, dtype=bool)
+    for e in np.flatnonzero(np.abs(zf - np.rint(zf)) < 1e-6):   # near-integer: exact integers
+        N = int(wa[e]) * int(a[e, 2]) + int(wb[e]) * int(b[e, 2]) + int(wc[e]) * int(c[e, 2])
+        qq, rem = divmod(N, int(ar[e]))
+        q[e] = qq
+        exact_hit[e] = rem == 0
+    ks = np.searchsorted(Zc, q, "right")                 # first centre strictly above the crossing
+    np.bitwise_xor.at(toggles, (ks, jj, ii), 1)
+    on = exact_hit & (ks >= 1)
+    on &= Zc[np.maximum(ks - 1, 0)] == q
+    onsurf[ks[on] - 1, jj[on], ii[on]] = True
     parity = np.bitwise_xor.accumulate(toggles[:nz], axis=0).astype(bool)
-    return parity & ~onsurf
+    return (bk0, bj0, bi0), parity & ~onsurf
 
 
 def _mark_vertical(A, B, C, QX, QY, Zc, onsurf, i0, j0):
@@ -154,7 +203,10 @@ def iblank_closed(grid: Grid, meshes) -> np.ndarray:
     solid = np.zeros(grid.shape, dtype=bool)
     for m in meshes:
         if int(m.closed):
-            solid |= inside_mesh(grid, m.verts, m.tris)
+            box, sub = inside_mesh_box(grid, m.verts, m.tris)
+            if box is not None:
+                k0, j0, i0 = box
+                solid[k0:, j0:j0 + sub.shape[1], i0:i0 + sub.shape[2]] |= sub
     return solid.astype(np.uint8)
 
 
@@ -233,19 +285,72 @@ def closest_point_on_triangles(P: np.ndarray, A: np.ndarray, B: np.ndarray, C: n
 
 def closest_points(P: np.ndarray, meshes, chunk: int = 64):
     """Boundary intercepts: for each point, the closest surface point over all triangles
-    of all given meshes (global index order, lowest index wins exact ties)."""
-    Vs = [np.asarray(m.verts, dtype=np.float64)[np.asarray(m.tris)] for m in meshes]
-    T = np.concatenate(Vs, axis=0)                    # (ntri, 3 vertices, 3)
-    A, B, C = T[:, 0], T[:, 1], T[:, 2]
+    of all given meshes (global index order, lowest index wins exact ties).
+
+    Whole meshes are skipped for a chunk of points when the distance from every point of
+    the chunk to the mesh's bounding box exceeds an upper bound of that point's answer (the
+    exact distance to the mesh whose box is nearest): a box distance is a lower bound of
+    the distance to any triangle inside it, so no skipped triangle could be the minimum or
+    tie with it.  The remaining meshes are scanned in index order with strict improvement,
+    which keeps the lowest-index rule.
+    """
+    Ts = [np.asarray(m.verts, dtype=np.float64)[np.asarray(m.tris)] for m in meshes]
+    lo = np.array([T.reshape(-1, 3).min(axis=0) for T in Ts])
+    hi = np.array([T.reshape(-1, 3).max(axis=0) for T in Ts])
+    base = np.cumsum([0] + [T.shape[0] for T in Ts])
     out_q = np.empty((P.shape[0], 3))
     out_t = np.empty(P.shape[0], dtype=np.int64)
+
+    tlo = [T.min(axis=1) for T in Ts]
+    thi = [T.max(axis=1) for T in Ts]
+    cents = [T.mean(axis=1) for T in Ts]
+
+    def box_gap(plo, phi, qlo, qhi):
+        g = np.maximum(np.maximum(qlo - phi, 0.0), plo - qhi)
+        return np.sqrt(np.sum(g * g, axis=-1))
+
+    def scan(Pc, m, ub):
+        """Closest triangle of mesh m for each point, evaluating only triangles whose box
+        distance to the point is <= ub (no other triangle can be as close)."""
+        T = Ts[m]
+        # triangles out of reach of the whole chunk, then of each point
+        near = np.flatnonzero(box_gap(Pc.min(axis=0), Pc.max(axis=0), tlo[m], thi[m]) <= ub.max())
+        lbt = box_gap(Pc[:, None], Pc[:, None], tlo[m][near][None], thi[m][near][None])
+        pp, kk = np.nonzero(lbt <= ub[:, None])
+        tt = near[kk]
+        Q, d2 = closest_point_on_triangles(Pc[pp], T[tt, 0], T[tt, 1], T[tt, 2])
+        order = np.lexsort((tt, d2, pp))                 # per point: smallest d2, then lowest index
+        pp, tt, Q, d2 = pp[order], tt[order], Q[order], d2[order]
+        first = np.ones(pp.size, dtype=bool)
+        first[1:] = pp[1:] != pp[:-1]
+        bq = np.zeros((Pc.shape[0], 3))
+        bd = np.full(Pc.shape[0], np.inf)
+        bt = np.zeros(Pc.shape[0], dtype=np.int64)
+        bq[pp[first]], bd[pp[first]], bt[pp[first]] = Q[first], d2[first], tt[first] + base[m]
+        return bq, bd, bt
+
     for s in range(0, P.shape[0], chunk):
-        Pc = P[s:s + chunk, None, :]
-        Q, d2 = closest_point_on_triangles(np.broadcast_to(Pc, (Pc.shape[0], A.shape[0], 3)),
-                                           A[None], B[None], C[None])
-        t = np.argmin(d2, axis=1)                     # first minimum = lowest index
-        out_t[s:s + chunk] = t
-        out_q[s:s + chunk] = Q[np.arange(Q.shape[0]), t]
+        Pc = P[s:s + chunk]
+        lb = box_gap(Pc[:, None], Pc[:, None], lo[None], hi[None])      # (points, meshes)
+        m0 = int(np.argmin(lb.sum(axis=0)))
+        # an upper bound per point: exact distance to a nearby triangle of mesh m0 (the
+        # nearest centroid among the triangles closest to the chunk's box)
+        dc = box_gap(Pc.min(axis=0), Pc.max(axis=0), tlo[m0], thi[m0])
+        pool = np.argsort(dc, kind="stable")[:256]
+        cd = np.sum((cents[m0][pool][None] - Pc[:, None]) ** 2, axis=2)
+        tn = pool[np.argmin(cd, axis=1)]
+        _, d2n = closest_point_on_triangles(Pc, Ts[m0][tn, 0], Ts[m0][tn, 1], Ts[m0][tn, 2])
+        ub = np.sqrt(d2n) * (1 + 1e-12) + 1e-300
+        cand = [m for m in range(len(Ts)) if np.any(lb[:, m] <= ub)]
+        bq = np.zeros((Pc.shape[0], 3))
+        bd = np.full(Pc.shape[0], np.inf)
+        bt = np.zeros(Pc.shape[0], dtype=np.int64)
+        for m in cand:                                   # index order, strict improvement
+            q, d2, t = scan(Pc, m, ub)
+            take = d2 < bd
+            bq[take], bd[take], bt[take] = q[take], d2[take], t[take]
+        out_q[s:s + chunk] = bq
+        out_t[s:s + chunk] = bt
     return out_q, out_t
 
 
@@ -298,62 +403,64 @@ def ghost_tables(grid: Grid, iblank: np.ndarray, ghosts: np.ndarray, meshes) -> 
     wy = np.stack([1.0 - ty, ty], -1)
     wz = np.stack([1.0 - tz, tz], -1)
     flat = iblank.ravel()
+    ng = ghosts.size
     gk, gj, gi = ghosts // (nx * ny), (ghosts // nx) % ny, ghosts % nx
-    for g in range(ghosts.size):
-        w = np.zeros(8)
-        ref = np.full(8, -1, dtype=np.int64)
-        valid = np.zeros(8, dtype=bool)
-        for c in range(8):
-            bx, by, bz = c & 1, (c >> 1) & 1, (c >> 2) & 1
-            lin = ((k0[g] + bz) * ny + (j0[g] + by)) * nx + (i0[g] + bx)
-            ref[c] = lin
-            w[c] = (wx[g, bx] * wy[g, by]) * wz[g, bz]
-            valid[c] = flat[lin] != IBLANK_SOLID
-        s = 0.0
-        for c in range(8):
-            if valid[c]:
-                s = s + w[c]
-        fallback = s < WEIGHT_SUM_MIN
-        if not fallback:
-            wn = np.where(valid, w / s, 0.0)
-            selfc = np.flatnonzero(valid & (ref == ghosts[g]))
-            if selfc.size:
-                ws = wn[selfc[0]]
-                if ws >= SELF_WEIGHT_MAX:
-                    fallback = True
-                else:
-                    wn = wn / (1.0 - ws)
-                    wn[selfc[0]] = 0.0
-        if fallback:
-            G.flags[g] |= FLAG_FALLBACK
-            G.ref[g] = -1
-            G.w[g] = 0.0
-            best, bestd = -1, None
-            for (di, dj, dk) in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
-                ii, jj, kk = gi[g] + di, gj[g] + dj, gk[g] + dk
-                if not (0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz):
-                    continue
-                lin = (kk * ny + jj) * nx + ii
-                if flat[lin] != IBLANK_FLUID:
-                    continue
-                ex = IP[g, 0] - grid.xc[ii]; ey = IP[g, 1] - grid.yc[jj]; ez = IP[g, 2] - grid.zc[kk]
-                d2 = (ex * ex + ey * ey) + ez * ez
-                if bestd is None or d2 < bestd:
-                    best, bestd = lin, d2
-            G.ref[g, 0] = best
-            G.w[g, 0] = 1.0
-        else:
-            G.ref[g] = np.where(wn != 0.0, ref, -1)
-            G.w[g] = wn
-            G.flags[g] |= int(np.sum(valid.astype(np.int32) << np.arange(8))) << 8
-        # row scale: coefficients of the fluid rows that reference this ghost
-        sc = 0.0
-        for (di, dj, dk, cf) in ((-1, 0, 0, grid.cxp), (1, 0, 0, grid.cxm), (0, -1, 0, grid.cyp),
-                                 (0, 1, 0, grid.cym), (0, 0, -1, grid.czp), (0, 0, 1, grid.czm)):
-            ii, jj, kk = gi[g] + di, gj[g] + dj, gk[g] + dk
-            if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz and flat[(kk * ny + jj) * nx + ii] == IBLANK_FLUID:
-                sc = sc + cf[ii if di else (jj if dj else kk)]
-        G.scale[g] = sc
+    rows = np.arange(ng)
+    # the 8 corners: slot c = bx + 2 by + 4 bz
+    lin = np.zeros((ng, 8), dtype=np.int64)
+    w = np.zeros((ng, 8))
+    for c in range(8):
+        bx, by, bz = c & 1, (c >> 1) & 1, (c >> 2) & 1
+        lin[:, c] = ((k0 + bz) * ny + (j0 + by)) * nx + (i0 + bx)
+        w[:, c] = (wx[:, bx] * wy[:, by]) * wz[:, bz]
+    valid = flat[lin] != IBLANK_SOLID
+    s = np.zeros(ng)
+    for c in range(8):                                   # valid weights, summed in slot order
+        s = s + np.where(valid[:, c], w[:, c], 0.0)
+    fallback = s < WEIGHT_SUM_MIN
+    with np.errstate(divide="ignore", invalid="ignore"):
+        wn = np.where(valid, w / s[:, None], 0.0)
+    is_self = valid & (lin == ghosts[:, None])
+    has_self = is_self.any(axis=1)
+    selfc = np.argmax(is_self, axis=1)
+    ws = wn[rows, selfc]
+    fallback |= has_self & (ws >= SELF_WEIGHT_MAX)
+    move = has_self & ~fallback
+    with np.errstate(divide="ignore", invalid="ignore"):
+        wn = np.where(move[:, None], wn / (1.0 - ws)[:, None], wn)
+    wn[rows[move], selfc[move]] = 0.0
+    # nearest fluid face-neighbour of the ghost (to IP), for the fallback rows
+    best = np.full(ng, -1, dtype=np.int64)
+    bestd = np.full(ng, np.inf)
+    for (di, dj, dk) in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
+        ii, jj, kk = gi + di, gj + dj, gk + dk
+        ok = (ii >= 0) & (ii < nx) & (jj >= 0) & (jj < ny) & (kk >= 0) & (kk < nz)
+        l2 = np.where(ok, (kk * ny + jj) * nx + ii, 0)
+        ok &= flat[l2] == IBLANK_FLUID
+        ex = IP[:, 0] - grid.xc[np.clip(ii, 0, nx - 1)]
+        ey = IP[:, 1] - grid.yc[np.clip(jj, 0, ny - 1)]
+        ez = IP[:, 2] - grid.zc[np.clip(kk, 0, nz - 1)]
+        d2 = (ex * ex + ey * ey) + ez * ez
+        take = ok & (d2 < bestd)
+        best[take], bestd[take] = l2[take], d2[take]
+    G.flags[:] = np.where(fallback, FLAG_FALLBACK,
+                          np.sum(valid.astype(np.int32) << np.arange(8), axis=1) << 8).astype(np.int32)
+    G.w[:] = np.where(fallback[:, None], 0.0, wn)
+    G.ref[:] = np.where(fallback[:, None], -1, np.where(wn != 0.0, lin, -1))
+    G.w[fallback, 0] = 1.0
+    G.ref[fallback, 0] = best[fallback]
+    # row scale: coefficients of the fluid rows that reference this ghost, in direction order
+    sc = np.zeros(ng)
+    for (di, dj, dk, cf, idx) in ((-1, 0, 0, grid.cxp, gi - 1), (1, 0, 0, grid.cxm, gi + 1),
+                                  (0, -1, 0, grid.cyp, gj - 1), (0, 1, 0, grid.cym, gj + 1),
+                                  (0, 0, -1, grid.czp, gk - 1), (0, 0, 1, grid.czm, gk + 1)):
+        ii, jj, kk = gi + di, gj + dj, gk + dk
+        ok = (ii >= 0) & (ii < nx) & (jj >= 0) & (jj < ny) & (kk >= 0) & (kk < nz)
+        l2 = np.where(ok, (kk * ny + jj) * nx + ii, 0)
+        ok &= flat[l2] == IBLANK_FLUID
+        n_ax = cf.size
+        sc = sc + np.where(ok, cf[np.clip(idx, 0, n_ax - 1)], 0.0)
+    G.scale[:] = sc
     return G
 
 

@@ -59,11 +59,25 @@ def _shifted(p: np.ndarray, axis: int, s: int) -> np.ndarray:
     return out
 
 
-def apply_fluid(grid: Grid, p: np.ndarray) -> np.ndarray:
-    """(A p)_i = sum_d c_{i,d} (p_nb - p_i) on every cell of the full array."""
-    out = np.zeros_like(p)
-    for axis, s, c in _nb_terms(grid):
-        out += c * (_shifted(p, axis, s) - p)
+def apply_fluid(grid: Grid, p: np.ndarray, slab: int = 32) -> np.ndarray:
+    """(A p)_i = sum_d c_{i,d} (p_nb - p_i) on every cell of the full array.
+
+    Evaluated slab by slab along z (each slab with one halo plane), so large grids need
+    only a few slab-sized temporaries; every cell's arithmetic is the same.
+    """
+    nz = p.shape[0]
+    out = np.empty_like(p)
+    for k0 in range(0, nz, slab):
+        k1 = min(nz, k0 + slab)
+        a, b = max(0, k0 - 1), min(nz, k1 + 1)
+        sub = p[a:b]
+        zc = Grid.__new__(Grid)
+        zc.czm, zc.czp = grid.czm[a:b], grid.czp[a:b]
+        zc.cym, zc.cyp, zc.cxm, zc.cxp = grid.cym, grid.cyp, grid.cxm, grid.cxp
+        acc = np.zeros_like(sub)
+        for axis, s_, c in _nb_terms(zc):
+            acc += c * (_shifted(sub, axis, s_) - sub)
+        out[k0:k1] = acc[k0 - a:k0 - a + (k1 - k0)]
     return out
 
 
@@ -76,32 +90,43 @@ def ghost_values_interp(G: GhostTable, pfull: np.ndarray) -> np.ndarray:
 
 def residual(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray, pfull: np.ndarray, lam: float = 0.0):
     """(r_fluid [k][j][i] (0 off fluid rows), r_ghost per entry) for r = b - lambda - A p."""
-    fluid = iblank == IBLANK_FLUID
-    rf = np.where(fluid, (b - lam) - apply_fluid(grid, pfull), 0.0)
+    rf = apply_fluid(grid, pfull)
+    np.subtract(b - lam if lam else b, rf, out=rf)
+    rf[iblank != IBLANK_FLUID] = 0.0
     rg = ghost_values_interp(G, pfull) - pfull.ravel()[G.cell] if len(G) else np.zeros(0)
     return rf, rg
 
 
+def _slabs(n, slab=64):
+    return [(k0, min(n, k0 + slab)) for k0 in range(0, n, slab)]
+
+
 def fluid_mean(grid: Grid, iblank: np.ndarray, v: np.ndarray) -> float:
-    fluid = iblank == IBLANK_FLUID
-    V = grid.volumes()
-    return float(np.sum(np.where(fluid, V * v, 0.0)) / np.sum(np.where(fluid, V, 0.0)))
+    """Volume-weighted mean of v over fluid cells (summed slab by slab along z)."""
+    num = den = 0.0
+    for k0, k1 in _slabs(v.shape[0]):
+        fluid = iblank[k0:k1] == IBLANK_FLUID
+        V = grid.dz[k0:k1, None, None] * grid.dy[None, :, None] * grid.dx[None, None, :]
+        num += float(np.sum(np.where(fluid, V * v[k0:k1], 0.0)))
+        den += float(np.sum(np.where(fluid, V, 0.0)))
+    return num / den
 
 
 def projected_norm(grid: Grid, iblank: np.ndarray, G: GhostTable, rf: np.ndarray, rg: np.ndarray) -> float:
     """||S P r||_2 over active rows."""
-    fluid = iblank == IBLANK_FLUID
     mu = fluid_mean(grid, iblank, rf)
-    pf = np.where(fluid, rf - mu, 0.0)
+    acc = 0.0
+    for k0, k1 in _slabs(rf.shape[0]):
+        pf = np.where(iblank[k0:k1] == IBLANK_FLUID, rf[k0:k1] - mu, 0.0)
+        acc += float(np.sum(pf * pf))
     sg = G.scale * rg if len(G) else np.zeros(0)
-    return float(np.sqrt(np.sum(pf * pf) + np.sum(sg * sg)))
+    return float(np.sqrt(acc + np.sum(sg * sg)))
 
 
 def relative_residual(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray, pfull: np.ndarray) -> float:
     """||S P (b - A p)|| / ||S P b||  (lambda drops out under the projection)."""
+    den = projected_norm(grid, iblank, G, b, np.zeros(len(G)))    # fluid rows of b; ghost rows 0
     rf, rg = residual(grid, iblank, G, b, pfull)
-    bf = np.where(iblank == IBLANK_FLUID, b, 0.0)
-    den = projected_norm(grid, iblank, G, bf, np.zeros(len(G)))
     return projected_norm(grid, iblank, G, rf, rg) / den
 
 

@@ -27,6 +27,7 @@ regenerated independently and the arrays do not depend on chunking.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -200,32 +201,56 @@ def random_spheres(count: int = 12, seed: int = 4, h: float = 1.0 / 1024, level:
 
 # ----------------------------------------------------------------------------- rhs
 
-def rhs_divergence(xf: np.ndarray, yf: np.ndarray, zf: np.ndarray, seed: int) -> np.ndarray:
+def _velocity_planes(seed: int, k0: int, k1: int, nx: int, ny: int):
+    """Cell velocities (u, v, w) of planes [k0, k1), each (k1-k0, ny, nx)."""
+    idx = np.arange(k0 * nx * ny, k1 * nx * ny, dtype=np.uint64)
+    shp = (k1 - k0, ny, nx)
+    return tuple(counter_normal(seed, c, idx).reshape(shp) for c in range(3))
+
+
+def rhs_divergence(xf: np.ndarray, yf: np.ndarray, zf: np.ndarray, seed: int, threads: int = 0) -> np.ndarray:
     """Discrete divergence of a seeded N(0,1) cell-centred velocity field.
 
     Cell velocity (u, v, w) at linear index l = (k*ny + j)*nx + i is drawn from
     streams 0, 1, 2.  Face velocity is the mean of the two adjacent cells, wall
     faces carry zero.  Returns b[k, j, i] = sum over axes of (face difference)
     / (cell width), on every cell (the solver itself only reads fluid rows).
+    Planes are generated in independent slabs (in parallel threads); the values do
+    not depend on the slabbing.
     """
+    from concurrent.futures import ThreadPoolExecutor
     nx, ny, nz = len(xf) - 1, len(yf) - 1, len(zf) - 1
     dx, dy, dz = np.diff(xf), np.diff(yf), np.diff(zf)
     b = np.zeros((nz, ny, nx), dtype=np.float64)
-    plane = nx * ny
-    prev = None
-    for k in range(nz):
-        idx = np.arange(k * plane, (k + 1) * plane, dtype=np.uint64)
-        u = counter_normal(seed, 0, idx).reshape(ny, nx)
-        v = counter_normal(seed, 1, idx).reshape(ny, nx)
-        w = counter_normal(seed, 2, idx).reshape(ny, nx)
-        fu = np.zeros((ny, nx + 1)); fu[:, 1:-1] = 0.5 * (u[:, :-1] + u[:, 1:])
-        fv = np.zeros((ny + 1, nx)); fv[1:-1, :] = 0.5 * (v[:-1, :] + v[1:, :])
-        b[k] = (fu[:, 1:] - fu[:, :-1]) / dx[None, :] + (fv[1:, :] - fv[:-1, :]) / dy[:, None]
-        if prev is not None:
-            fw = 0.5 * (prev + w)                       # face k-1/2
-            b[k - 1] += fw / dz[k - 1]
-            b[k] -= fw / dz[k]
-        prev = w
+    slab = max(1, min(nz, (1 << 22) // max(1, nx * ny)))
+
+    def work(k0):
+        k1 = min(nz, k0 + slab)
+        a = max(0, k0 - 1)
+        u, v, w = _velocity_planes(seed, a, k1, nx, ny)
+        o = k0 - a                                       # offset of plane k0 in the slab
+        uu, vv = u[o:], v[o:]
+        fu = np.zeros((k1 - k0, ny, nx + 1)); fu[:, :, 1:-1] = 0.5 * (uu[:, :, :-1] + uu[:, :, 1:])
+        fv = np.zeros((k1 - k0, ny + 1, nx)); fv[:, 1:-1, :] = 0.5 * (vv[:, :-1, :] + vv[:, 1:, :])
+        out = (fu[:, :, 1:] - fu[:, :, :-1]) / dx[None, None, :] + (fv[:, 1:, :] - fv[:, :-1, :]) / dy[None, :, None]
+        # z faces k-1/2 .. k+1/2 of planes k0 .. k1-1 (wall faces 0)
+        fw = np.zeros((k1 - k0 + 1, ny, nx))
+        ww = w                                            # planes a .. k1-1
+        for q in range(k1 - k0 + 1):
+            k = k0 + q                                    # face k-1/2, between planes k-1 and k
+            if 0 < k < nz:
+                if k < k1:
+                    fw[q] = 0.5 * (ww[k - 1 - a] + ww[k - a])
+        if k1 < nz:
+            wn = _velocity_planes(seed, k1, k1 + 1, nx, ny)[2][0]
+            fw[k1 - k0] = 0.5 * (ww[k1 - 1 - a] + wn)
+        out += (fw[1:] - fw[:-1]) / dz[k0:k1, None, None]
+        b[k0:k1] = out
+
+    starts = list(range(0, nz, slab))
+    nt = threads or min(16, os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=nt) as ex:
+        list(ex.map(work, starts))
     return b
 
 

@@ -127,3 +127,40 @@ def test_graph_replay_is_bit_identical_and_deterministic(ctx, prec):
         assert np.array_equal(p, outs[0][0])
         assert np.array_equal(hst, outs[0][1])
     T.close()
+
+
+def test_cfg4_1024_twelve_spheres_single_gpu(ctx):
+    """1024^3 uniform grid, 12 random spheres: classification bit-exact (full iblank, ghost list,
+    sampled image-point rows), mixed solve to 1e-10 certified by the oracle's own residual of the
+    GPU pressure, device memory reported."""
+    pkg, c = ctx
+    pr = synth.cfg4(1024)
+    g = Grid(pr.xf, pr.yf, pr.zf)
+    ib = OC.iblank_closed(g, pr.meshes)
+    ghosts = OC.mark_ghosts(ib)
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    T = pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes)
+    ex = T.export()
+    assert np.array_equal(ex["iblank"].cpu().numpy(), ib)
+    assert np.array_equal(ex["cell"].cpu().numpy(), ghosts)
+    rng = np.random.default_rng(4)
+    sample = np.sort(rng.choice(ghosts.size, size=min(2000, ghosts.size), replace=False))
+    Gs = OC.ghost_tables(g, ib, ghosts[sample], pr.meshes)
+    for k, o in (("bi", Gs.bi), ("ip", Gs.ip), ("w", Gs.w), ("scale", Gs.scale), ("ref", Gs.ref), ("base", Gs.base)):
+        assert np.array_equal(ex[k].cpu().numpy()[sample], o), k
+    b = pr.rhs()
+    rhs = torch.from_numpy(b).cuda()
+    p = torch.zeros_like(rhs)
+    rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=1))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    used_gb = (free0 - free1) / 1e9
+    print("1024^3: ghosts %d, cycles %d, %.1f ms, device memory for tables + solver %.1f GB"
+          % (T.nghost, rep["cycles"], rep["ms_total"], used_gb))
+    assert rep["status"] == "IBM_OK"
+    G = OC.ghost_tables(g, ib, ghosts, pr.meshes)          # every ghost row, from the oracle alone
+    ph = p.cpu().numpy()
+    del p, rhs
+    assert OSys.relative_residual(g, ib, G, b, ph) <= 1.05 * TOL
+    T.close()

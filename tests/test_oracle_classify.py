@@ -275,3 +275,21 @@ def test_grid_aligned_wall_ghost_is_mirror():
     # last row/plane put it in another slot)
     assert np.all(np.sum(G.w == 1.0, axis=1) == 1) and np.all(np.sum(G.w != 0.0, axis=1) == 1)
     assert np.array_equal(G.ref[G.w == 1.0], G.cell - 1)
+
+
+def test_closest_points_mesh_pruning_equals_full_scan():
+    """The mesh-level pruning of the closest-point search changes nothing: same points, same
+    triangle indices as a scan of every triangle of every mesh (ties included)."""
+    rng = np.random.default_rng(8)
+    meshes = [synth.octa_sphere(2, tuple(c), r) for c, r in
+              (((0.3, 0.3, 0.3), 0.1), ((0.7, 0.35, 0.4), 0.12), ((0.5, 0.7, 0.6), 0.15))]
+    meshes.append(synth.box_mesh((0.2, 0.6, 0.1), (0.35, 0.9, 0.3)))
+    P = rng.uniform(0.0, 1.0, size=(700, 3))
+    P[:40] = meshes[3].verts[rng.integers(0, 8, 40)] + np.array([0.0, 0.0, -0.05])   # ties on box faces
+    q, t = C.closest_points(P, meshes, chunk=32)
+    T = np.concatenate([np.asarray(m.verts)[np.asarray(m.tris)] for m in meshes])
+    Q, d2 = C.closest_point_on_triangles(np.broadcast_to(P[:, None], (P.shape[0], T.shape[0], 3)),
+                                         T[None, :, 0], T[None, :, 1], T[None, :, 2])
+    tf = np.argmin(d2, axis=1)
+    assert np.array_equal(t, tf)
+    assert np.array_equal(q, Q[np.arange(P.shape[0]), tf])
