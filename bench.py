@@ -155,6 +155,42 @@ def _config(args):
             "l2": "working set > L2 (no flush)", "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
+def bench_batched(pkg, ctx, torch, st, reps: int = 2):
+    """48 independent uneven problems (edges U{64..192}, sphere or ellipsoid each):
+    batched mixed, batched FP64 and 48 sequential mixed solves to 1e-10 (ms, median)."""
+    import synth
+    probs = synth.cfg5(48)
+    tabs = [pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st) for pr in probs]
+    rhs = [torch.from_numpy(pr.rhs()).cuda() for pr in probs]
+    ps = [torch.zeros_like(r) for r in rhs]
+    cells = sum(pr.ncells for pr in probs)
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            for x in ps:
+                x.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            fn()
+            c.record(st)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        return statistics.median(ts[1:])
+
+    out = {"problems": len(probs), "cells": cells}
+    for name, prec in (("batched_mixed_ms", 1), ("batched_fp64_ms", 0)):
+        out[name] = timed(lambda: pkg.poisson_solve_batched(ctx.h, [t.h for t in tabs], rhs, TOL, ps,
+                                                            pkg.SolveOpts(precision=prec), stream=st))
+    out["sequential_mixed_ms"] = timed(lambda: [t.solve(r, x, TOL, pkg.SolveOpts(precision=1), stream=st)
+                                               for t, r, x in zip(tabs, rhs, ps)])
+    out["batched_mixed_gcells_per_s"] = cells / (out["batched_mixed_ms"] * 1e-3) / 1e9
+    for t in tabs:
+        t.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -292,6 +328,8 @@ def run_ours(args):
             "e2e": {"value": ws * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(b_host.nbytes + mesh_bytes), "d2h_bytes_per_step": int(b_host.nbytes)},
             "gpu_launches": launches, "clocks": clk.summary()}
+    if not args.no_batched:
+        line["batched_48"] = bench_batched(pkg, ctx, torch, st)
     if not args.no_cpu:
         c_cells, c_t = _cpu_sample(args.cpu_n)
         line["cpu_baseline"] = {"value": c_cells / c_t / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -314,6 +352,7 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=64)
     ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -149,6 +149,28 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
                          double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
                          void *stream);
 
+/* Batched pressure Poisson solves: n independent problems (each its own classified grid,
+ * of any size) advanced together, one persistent kernel launch per V-cycle stage over the
+ * work of every problem that has that stage; each batched cycle is captured once as a CUDA
+ * graph and replayed until every problem reaches tol (a converged problem's work turns
+ * into no-ops).  Same equations, options and outputs as poisson_solve, per problem:
+ *   tables[p], rhs_dev[p], p_dev[p] as in poisson_solve (p_dev[p] is in/out);
+ *   infos (optional, n entries) receives each problem's report; ms_total is the batch's.
+ * The tables must be distinct.  Returns IBM_ERR_NOT_CONVERGED if some problem did not
+ * reach tol in max_cycles (its last iterate is returned). */
+ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,
+                                 const double *const *rhs_dev, double tol, double *const *p_dev,
+                                 const ibm_solve_opts *opts, ibm_solve_info *infos, void *stream);
+
+/* Autotuner: times complete solves of the given problem (rhs_dev, tol) with candidate
+ * smoother schedules -- over-relaxation 1.2/1.3/1.4, sweeps (1,1)/(2,1)/(2,2) and, for
+ * precision 1, 1/2/3 FP32 V-cycles per refinement step -- and returns the fastest in *best
+ * (its time in *best_ms, optional).  p_work_dev (double[ncell], device) is overwritten.
+ * Use the result for poisson_solve / poisson_solve_batched of similar problems. */
+ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, const double *rhs_dev,
+                        double *p_work_dev, double tol, ibm_solve_opts *best, double *best_ms,
+                        void *stream);
+
 /* Measurement: run `nsweeps` smoother sweeps (red, black, ghost rows) on the finest level
  * of the hierarchy of the given precision, exactly as inside a V-cycle, on whatever the
  * solver's work arrays hold (call after a poisson_solve of that precision).  No result;

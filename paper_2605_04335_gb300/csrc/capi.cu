@@ -25,6 +25,9 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
 ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
 ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st);
+ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const double *const *rhs, double tol,
+                              double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
+                              cudaStream_t st);
 
 }  // namespace ibm
 
@@ -150,7 +153,7 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
   ibm_solve_opts o;
   ibm_solve_opts_default(&o);
   if (opts) o = *opts;
-  if ((o.precision != 0 && o.precision != 1) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
+  if (!(o.precision == 0 || o.precision == 1) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0))
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
@@ -165,6 +168,85 @@ ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precis
   if (!ctx || !t || t->ctx != ctx || (precision != 0 && precision != 1) || nsweeps < 0) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream);
+}
+
+static bool valid_opts(const ibm_solve_opts &o) {
+  return (o.precision == 0 || o.precision == 1) && o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 &&
+         o.max_cycles >= 0 && o.inner_cycles >= 1 && o.omega > 0.0 && o.omega < 2.0;
+}
+
+ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,
+                                 const double *const *rhs_dev, double tol, double *const *p_dev,
+                                 const ibm_solve_opts *opts, ibm_solve_info *infos, void *stream) {
+  if (!ctx || n < 0 || (n > 0 && (!tables || !rhs_dev || !p_dev)) || !(tol >= 0.0)) return IBM_ERR_INVALID_ARG;
+  for (int p = 0; p < n; ++p) {
+    if (!tables[p] || tables[p]->ctx != ctx || !rhs_dev[p] || !p_dev[p]) return IBM_ERR_INVALID_ARG;
+    for (int q = 0; q < p; ++q)
+      if (tables[q] == tables[p]) return IBM_ERR_INVALID_ARG;   // each problem owns its work arrays
+    if (infos && infos[p].history_cap > 0 && !infos[p].resid_history) return IBM_ERR_INVALID_ARG;
+  }
+  ibm_solve_opts o;
+  ibm_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_opts(o)) return IBM_ERR_INVALID_ARG;
+  if (n == 0) return IBM_OK;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  if (infos)
+    for (int p = 0; p < n; ++p) { infos[p].cycles = 0; infos[p].history_len = 0; }
+  auto t0 = std::chrono::steady_clock::now();
+  ibm_status s = ibm::solve_batched_impl(ctx, n, const_cast<ibm_tables *const *>(tables), rhs_dev, tol, p_dev, &o,
+                                         infos, (cudaStream_t)stream);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (infos)
+    for (int p = 0; p < n; ++p) infos[p].ms_total = ms;
+  return s;
+}
+
+ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, const double *rhs_dev,
+                        double *p_work_dev, double tol, ibm_solve_opts *best, double *best_ms, void *stream) {
+  if (!ctx || !t || t->ctx != ctx || !rhs_dev || !p_work_dev || !best || (precision != 0 && precision != 1) ||
+      !(tol > 0.0))
+    return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const double omegas[3] = {1.2, 1.3, 1.4};
+  const int nus[3][2] = {{1, 1}, {2, 1}, {2, 2}};
+  const int inners_mixed[3] = {1, 2, 3}, inner_fp64[1] = {1};
+  const int *inners = precision == 1 ? inners_mixed : inner_fp64;
+  const int ninner = precision == 1 ? 3 : 1;
+  const size_t bytes = sizeof(double) * (size_t)t->ncell;
+  cudaEvent_t e0, e1;
+  IBM_TRY(cudaEventCreate(&e0));
+  IBM_TRY(cudaEventCreate(&e1));
+  double best_t = 1e300;
+  ibm_solve_opts cand;
+  ibm_solve_opts_default(&cand);
+  cand.precision = precision;
+  ibm_status last = IBM_OK;
+  for (double om : omegas)
+    for (auto &nu : nus)
+      for (int q = 0; q < ninner; ++q) {
+        cand.omega = om; cand.nu1 = nu[0]; cand.nu2 = nu[1]; cand.inner_cycles = inners[q];
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {      // first run builds graphs; keep the faster
+          cudaMemsetAsync(p_work_dev, 0, bytes, st);
+          cudaEventRecord(e0, st);
+          ibm_solve_info info{};
+          ibm_status s = ibm::solve_impl(ctx, const_cast<ibm_tables *>(t), rhs_dev, tol, p_work_dev, &cand, &info, st);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          if (s != IBM_OK) { last = s; ms_best = 1e30f; break; }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms_best = std::min(ms_best, ms);
+        }
+        if (ms_best < best_t) { best_t = ms_best; *best = cand; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_t >= 1e29) return last != IBM_OK ? last : IBM_ERR_NOT_CONVERGED;
+  if (best_ms) *best_ms = best_t;
+  return IBM_OK;
 }
 
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count) {

@@ -1134,3 +1134,5 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
 }
 
 }  // namespace ibm
+
+#include "batch.cuh"

@@ -80,6 +80,8 @@ def load_library():
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
         "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P,
                                             C.POINTER(C.c_double), P]),
+        "poisson_solve_batched": (I32, [P, I32, P, P, D, P, C.POINTER(ibm_solve_opts), P, P]),
+        "ibm_autotune": (I32, [P, P, I32, P, P, D, C.POINTER(ibm_solve_opts), C.POINTER(C.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -204,6 +206,39 @@ def ibm_residual_norm_noalloc(xf, yf, zf, iblank, cell, ref, w, scale, rhs, p, s
                                                     _ptr(scale), _ptr(rhs), _ptr(p), out, _stream(stream)),
            "ibm_residual_norm_noalloc")
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def poisson_solve_batched(ctx, tables, rhs_list, tol, p_list, opts: "SolveOpts | None" = None, stream=None,
+                          history_cap: int = 64, raise_on_error: bool = True):
+    """Batched solve of independent problems (tables handles, CUDA float64 tensors).
+    Returns (status name, list of per-problem report dicts)."""
+    lib = load_library()
+    n = len(tables)
+    o = opts or SolveOpts()
+    co = ibm_solve_opts(o.precision, o.nu1, o.nu2, o.max_cycles, o.inner_cycles, o.use_graph, o.omega)
+    T = (C.c_void_p * max(1, n))(*[t.value if hasattr(t, "value") else t for t in tables])
+    R = (C.c_void_p * max(1, n))(*[r.data_ptr() for r in rhs_list])
+    Pp = (C.c_void_p * max(1, n))(*[x.data_ptr() for x in p_list])
+    hists = [np.zeros(max(1, history_cap)) for _ in range(n)]
+    infos = (ibm_solve_info * max(1, n))()
+    for q in range(n):
+        infos[q] = ibm_solve_info(0, 0, 0.0, 0.0, 0.0, hists[q].ctypes.data, history_cap)
+    s = lib.poisson_solve_batched(ctx, n, T, R, float(tol), Pp, C.byref(co), infos, _stream(stream))
+    reps = [{"cycles": infos[q].cycles, "rel_resid": infos[q].rel_resid, "lambda": infos[q].lambda_,
+             "ms_total": infos[q].ms_total, "history": hists[q][:infos[q].history_len].copy()} for q in range(n)]
+    if raise_on_error and s != IBM_OK:
+        raise IbmError(s, "poisson_solve_batched")
+    return STATUS.get(s, s), reps
+
+
+def ibm_autotune(ctx, tables, precision: int, rhs, p_work, tol: float = 1e-10, stream=None):
+    """Fastest smoother schedule for this problem: (SolveOpts, ms)."""
+    best = ibm_solve_opts()
+    ms = C.c_double()
+    _check(load_library().ibm_autotune(ctx, tables, precision, _ptr(rhs), _ptr(p_work), float(tol), C.byref(best),
+                                       C.byref(ms), _stream(stream)), "ibm_autotune")
+    return SolveOpts(best.precision, best.nu1, best.nu2, best.max_cycles, best.inner_cycles, best.use_graph,
+                     best.omega), float(ms.value)
 
 
 # ----------------------------------------------------------------------------- conveniences
