@@ -142,6 +142,8 @@ template <typename T>
 struct Strip {
   int xs, y;          // tile coordinates of the first cell
   unsigned valid;     // bit u: cell xs+u is in the grid and in [xlo, xhi]
+  int ie, ir, im;     // offsets of the first cell in an e / rhs / mask plane buffer
+  int par;            // (x0 + xs + y0 + y) mod 2
   T cxm[4], cxp[4], sx[4], cym, cyp, sy;
 };
 
@@ -149,6 +151,10 @@ template <typename T>
 __device__ __forceinline__ void make_strip(Strip<T> &S, const Args<T> &a, int x0, int y0, int xs, int y, int xlo,
                                            int xhi) {
   S.xs = xs; S.y = y; S.valid = 0;
+  S.ie = (y + 2) * BX + (xs + 4);
+  S.ir = (y + 1) * BX + (xs + 4);
+  S.im = (y + 1) * BXM + (xs + 4);
+  S.par = (x0 + xs + y0 + y) & 1;
   const int gj = y0 + y;
   const bool jok = gj >= 0 && gj < a.ny;
   for (int u = 0; u < 4; ++u) {
@@ -173,17 +179,17 @@ template <typename T>
 __device__ __forceinline__ void relax_colour(const Strip<T> &S, T *P, const T *Pm, const T *Pp, const T *R,
                                              const uint8_t *M, int par, int x0, int y0, int k, T czm, T czp, T sz,
                                              T sh, float om, Q4<T> &C) {
-  const int ie = (S.y + 2) * BX + (S.xs + 4);
+  const int ie = S.ie;
   C = ld4(P + ie);
-  const unsigned m4 = *reinterpret_cast<const unsigned *>(M + (S.y + 1) * BXM + (S.xs + 4));
+  const unsigned m4 = *reinterpret_cast<const unsigned *>(M + S.im);
   // cells of colour par in the strip: u = ua and ua + 2
-  const int ua = (x0 + S.xs + y0 + S.y + k + par) & 1;
+  const int ua = (S.par + k + par) & 1;
   unsigned act = 0;
   for (int u = ua; u < 4; u += 2)
     if (((S.valid >> u) & 1u) && ((m4 >> (8 * u)) & 0xffu) == 0u) act |= 1u << u;
   if (!act) return;
   const Q4<T> N = ld4(P + ie - BX), So = ld4(P + ie + BX), B = ld4(Pm + ie), U = ld4(Pp + ie);
-  const Q4<T> Rh = ld4(R + (S.y + 1) * BX + (S.xs + 4));
+  const Q4<T> Rh = ld4(R + S.ir);
   const T L = P[ie - 1], Rr = P[ie + 4];
   const T syz = S.sy + sz;
 #pragma unroll
@@ -202,6 +208,51 @@ __device__ __forceinline__ void relax_colour(const Strip<T> &S, T *P, const T *P
     C.v[u] += (T)__fdividef(om * (float)res, (float)D);
   }
   st4(P + ie, C);
+}
+
+// Interior strips: the warp's rows share one parity, so the colour's cells in a strip are
+// u = UA and UA + 2 with UA warp-uniform; both cases are compiled separately (no selects).
+template <int UA, typename T>
+__device__ __forceinline__ void relax_pair(const Strip<T> &S, T *P, const T *Pm, const T *Pp, const T *R,
+                                           const uint8_t *M, T czm, T czp, T sz, T sh, float om, Q4<T> &C) {
+  const int ie = S.ie;
+  C = ld4(P + ie);
+  const unsigned m4 = *reinterpret_cast<const unsigned *>(M + S.im);
+  constexpr int u0 = UA, u1 = UA + 2;
+  const bool ok0 = ((S.valid >> u0) & 1u) && ((m4 >> (8 * u0)) & 0xffu) == 0u;
+  const bool ok1 = ((S.valid >> u1) & 1u) && ((m4 >> (8 * u1)) & 0xffu) == 0u;
+  if (!(ok0 || ok1)) return;
+  const Q4<T> N = ld4(P + ie - BX), So = ld4(P + ie + BX), B = ld4(Pm + ie), U = ld4(Pp + ie);
+  const Q4<T> Rh = ld4(R + S.ir);
+  const T syz = S.sy + sz;
+  const T west0 = UA == 0 ? P[ie - 1] : C.v[0];
+  const T east1 = UA == 1 ? P[ie + 4] : C.v[3];
+  const T c0 = C.v[u0], c1 = C.v[u1];
+  const T D0 = S.sx[u0] + syz, D1 = S.sx[u1] + syz;
+  T s0 = S.cxm[u0] * west0;
+  s0 += S.cxp[u0] * C.v[u0 + 1];
+  s0 += S.cym * N.v[u0];
+  s0 += S.cyp * So.v[u0];
+  s0 += czm * B.v[u0];
+  s0 += czp * U.v[u0];
+  T s1 = S.cxm[u1] * C.v[u1 - 1];
+  s1 += S.cxp[u1] * east1;
+  s1 += S.cym * N.v[u1];
+  s1 += S.cyp * So.v[u1];
+  s1 += czm * B.v[u1];
+  s1 += czp * U.v[u1];
+  const T r0 = (s0 - D0 * c0) - (Rh.v[u0] - sh);
+  const T r1 = (s1 - D1 * c1) - (Rh.v[u1] - sh);
+  if (ok0) C.v[u0] = c0 + (T)__fdividef(om * (float)r0, (float)D0);
+  if (ok1) C.v[u1] = c1 + (T)__fdividef(om * (float)r1, (float)D1);
+  st4(P + ie, C);
+}
+
+template <typename T>
+__device__ __forceinline__ void relax_interior(const Strip<T> &S, int ua, T *P, const T *Pm, const T *Pp, const T *R,
+                                               const uint8_t *M, T czm, T czp, T sz, T sh, float om, Q4<T> &C) {
+  if (ua == 0) relax_pair<0, T>(S, P, Pm, Pp, R, M, czm, czp, sz, sh, om, C);
+  else relax_pair<1, T>(S, P, Pm, Pp, R, M, czm, czp, sz, sh, om, C);
 }
 
 template <typename T>
@@ -223,7 +274,12 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
   }
   // this thread's interior strip, and its ring strip (red updates of the one-cell ring)
   Strip<T> Si, Sr;
-  make_strip(Si, a, x0, y0, 4 * (tid % (TX / 4)), tid / (TX / 4), 0, TX - 1);
+  {
+    // warps 0..THREADS/64-1 take the even rows, the others the odd rows, two rows per warp
+    const int w = tid >> 5, l = tid & 31, half = THREADS / 64;
+    const int y = 4 * (w % half) + (w >= half ? 1 : 0) + 2 * (l >> 4);
+    make_strip(Si, a, x0, y0, 4 * (l & 15), y, 0, TX - 1);
+  }
   const bool has_ring = tid < RING;
   {
     int xs = 0, y = 0;
@@ -293,7 +349,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
       const T *R = s.r[(q + 2 * NRt) % NRt];
       const uint8_t *M = s.m[(q + 2 * NRt) % NRt];
       Q4<T> C;
-      relax_colour<T>(Si, P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, C);
+      relax_interior<T>(Si, (Si.par + q) & 1, P, Pm, Pp, R, M, czm, czp, sz, sh, om, C);
       if (Sr.valid) relax_colour<T>(Sr, P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, C);
     }
     __syncthreads();
@@ -305,7 +361,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
       const T *R = s.r[(kb + 2 * NRt) % NRt];
       const uint8_t *M = s.m[(kb + 2 * NRt) % NRt];
       Q4<T> C;
-      relax_colour<T>(Si, B, Bm, P, R, M, 1, x0, y0, kb, czm, czp, sz, sh, om, C);
+      relax_interior<T>(Si, (Si.par + kb + 1) & 1, B, Bm, P, R, M, czm, czp, sz, sh, om, C);
       if (Si.valid) {
         const int gj = y0 + Si.y, gi = x0 + Si.xs;
         T *dst = a.out + ((long long)(kb + 1) * (a.ny + 2) + (gj + 1)) * a.px + (gi + 4);
