@@ -70,10 +70,16 @@ typedef struct {
 /* Solver options; ibm_solve_opts_default fills the defaults shown. */
 typedef struct {
   int32_t precision;    /* 0: FP64 throughout; 1: FP32 multigrid inside FP64 iterative
-                           refinement (FP64 fine residual, update, gauge, coarsest)  [0] */
+                           refinement (FP64 fine residual, update, gauge, coarsest);
+                           2: as 1, but the refinement loop (accumulated p, b, the fine
+                           residual, update and gauge) in double-FP32: each value an
+                           unevaluated sum of two floats (48-bit significand), residual by
+                           error-free transformations on the FP32 pipe.  Mode 2 is this
+                           library's choice for hardware with a slow FP64 pipe; the paper
+                           states FP64 for the outer loop (mode 1).  Not batched.      [0] */
   int32_t nu1, nu2;     /* pre-/post-smoothing red-black Gauss-Seidel sweeps        [2,2] */
-  int32_t max_cycles;   /* V-cycles (precision 0) or refinement steps (precision 1) [100] */
-  int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1)            [2] */
+  int32_t max_cycles;   /* V-cycles (precision 0) or refinement steps (1, 2)        [100] */
+  int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1, 2)         [2] */
   int32_t use_graph;    /* capture one cycle as a CUDA graph and replay it            [1] */
   double omega;         /* Gauss-Seidel over-relaxation factor, in (0, 2)           [1.3] */
 } ibm_solve_opts;
@@ -81,7 +87,7 @@ typedef struct {
 /* Solve report.  resid_history (host, optional) receives the relative residual after
  * every cycle, up to history_cap entries. */
 typedef struct {
-  int32_t cycles;       /* V-cycles (precision 0) or refinement steps (precision 1)     */
+  int32_t cycles;       /* V-cycles (precision 0) or refinement steps (precision 1, 2)  */
   int32_t history_len;
   double rel_resid;     /* ||S P r|| / ||S P b|| of the returned p (see poisson_solve)  */
   double lambda;        /* the compatibility constant of the bordered system            */
@@ -164,7 +170,7 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
 
 /* Autotuner: times complete solves of the given problem (rhs_dev, tol) with candidate
  * smoother schedules -- over-relaxation 1.2/1.3/1.4, sweeps (1,1)/(2,1)/(2,2) and, for
- * precision 1, 1/2/3 FP32 V-cycles per refinement step -- and returns the fastest in *best
+ * precision 1 or 2, 1/2/3 FP32 V-cycles per refinement step -- and returns the fastest in *best
  * (its time in *best_ms, optional).  p_work_dev (double[ncell], device) is overwritten.
  * Use the result for poisson_solve / poisson_solve_batched of similar problems. */
 ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, const double *rhs_dev,

@@ -98,7 +98,7 @@ ibm_status ibm_tables_destroy(ibm_tables *t) {
   if (!t) return IBM_ERR_INVALID_ARG;
   if (t->ctx) cudaSetDevice(t->ctx->device);
   cudaDeviceSynchronize();
-  for (int q = 0; q < 2; ++q) ibm::free_hierarchy(t->hier[q]);
+  for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
   void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref};
   for (void *p : ps) if (p) cudaFree(p);
   delete t;
@@ -153,7 +153,7 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
   ibm_solve_opts o;
   ibm_solve_opts_default(&o);
   if (opts) o = *opts;
-  if (!(o.precision == 0 || o.precision == 1) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
+  if (!(o.precision >= 0 && o.precision <= 2) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0))
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
@@ -165,13 +165,13 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
 }
 
 ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps, void *stream) {
-  if (!ctx || !t || t->ctx != ctx || (precision != 0 && precision != 1) || nsweeps < 0) return IBM_ERR_INVALID_ARG;
+  if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 0) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream);
 }
 
 static bool valid_opts(const ibm_solve_opts &o) {
-  return (o.precision == 0 || o.precision == 1) && o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 &&
+  return o.precision >= 0 && o.precision <= 2 && o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 &&
          o.max_cycles >= 0 && o.inner_cycles >= 1 && o.omega > 0.0 && o.omega < 2.0;
 }
 
@@ -189,6 +189,7 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
   ibm_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!valid_opts(o)) return IBM_ERR_INVALID_ARG;
+  if (o.precision == 2) return IBM_ERR_NOT_IMPLEMENTED;   // batched double-FP32 outer loop: not built
   if (n == 0) return IBM_OK;
   IBM_TRY(cudaSetDevice(ctx->device));
   if (infos)
@@ -204,7 +205,7 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
 
 ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, const double *rhs_dev,
                         double *p_work_dev, double tol, ibm_solve_opts *best, double *best_ms, void *stream) {
-  if (!ctx || !t || t->ctx != ctx || !rhs_dev || !p_work_dev || !best || (precision != 0 && precision != 1) ||
+  if (!ctx || !t || t->ctx != ctx || !rhs_dev || !p_work_dev || !best || precision < 0 || precision > 2 ||
       !(tol > 0.0))
     return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
@@ -212,8 +213,8 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
   const double omegas[3] = {1.2, 1.3, 1.4};
   const int nus[3][2] = {{1, 1}, {2, 1}, {2, 2}};
   const int inners_mixed[3] = {1, 2, 3}, inner_fp64[1] = {1};
-  const int *inners = precision == 1 ? inners_mixed : inner_fp64;
-  const int ninner = precision == 1 ? 3 : 1;
+  const int *inners = precision != 0 ? inners_mixed : inner_fp64;
+  const int ninner = precision != 0 ? 3 : 1;
   const size_t bytes = sizeof(double) * (size_t)t->ncell;
   cudaEvent_t e0, e1;
   IBM_TRY(cudaEventCreate(&e0));

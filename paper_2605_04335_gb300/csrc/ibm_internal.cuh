@@ -69,7 +69,8 @@ struct Level {
 struct Hierarchy {
   int elem = 8;                             // bytes per element of levels (4 or 8)
   std::vector<Level> lv;
-  // fine-level FP64 arrays (both precisions)
+  // fine-level outer arrays p and b: FP64, or in double-FP32 mode the same bytes as two
+  // float arrays each (hi: first ntot floats, lo: next ntot)
   double *p64 = nullptr, *b64 = nullptr;
   // coarsest dense bordered inverse
   int ncoarse = 0;                          // unknowns of the coarsest level (fluid cells)
@@ -77,6 +78,8 @@ struct Hierarchy {
   int *cidx = nullptr;                      // padded index of each coarsest unknown
   int *dncoarse = nullptr;                  // device copy of ncoarse
   double *c64 = nullptr;                    // FP64 fine coefficients cxm cxp cym cyp czm czp
+  float *cdf = nullptr;                     // double-FP32 mode: fine coefficients, diagonal parts
+                                            // and widths split into hi (4n floats) and lo (4n)
   // solver-side ghost rows: padded source indices (-1 unused), weights (double and float)
   long long *gsrc = nullptr;
   long long *gdst = nullptr;
@@ -119,8 +122,8 @@ struct ibm_tables {
   double *gbi = nullptr, *gip = nullptr, *gw = nullptr, *gscale = nullptr;
   int *gbase = nullptr, *gflags = nullptr;
   long long *gref = nullptr;
-  // solver hierarchies by precision (lazy)
-  ibm::Hierarchy *hier[2] = {nullptr, nullptr};
+  // solver hierarchies by precision mode (lazy)
+  ibm::Hierarchy *hier[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace ibm {

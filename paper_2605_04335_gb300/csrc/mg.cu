@@ -16,7 +16,7 @@
 //  * coarsest level (<= 128 cells): exact bordered solve [A 1; V' 0] by a precomputed inverse.
 //
 // Element type T is float or double; the fine-level residual, the refinement update and
-// the gauge are always FP64.
+// the gauge are FP64, or pairs of floats in the double-FP32 outer loop (precision mode 2).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include "ibm_internal.cuh"
+#include "dfloat.cuh"
 #include "zmarch.cuh"
 
 namespace ibm {
@@ -582,6 +583,223 @@ __global__ void k_zero_solid(double *p, const uint8_t *mask, long long n) {
     if (mask[q] == 1) p[q] = 0.0;
 }
 
+// ------------------------------------------------------------------ double-FP32 outer loop
+
+// Fine-level view for the double-FP32 kernels.  h and l hold the split fine data, 4n floats
+// each (n = nx + ny + nz): cxm cxp cym cyp czm czp (2n), sdx sdy sdz (n), dx dy dz (n).
+struct DfView {
+  int nx, ny, nz, px;
+  long long sy, sz;
+  const uint8_t *mask;
+  const float *h, *l;
+};
+
+// split n doubles into hi/lo floats
+__global__ void k_split_df(const double *src, int n, float *h, float *l) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) dfl::split(src[q], h[q], l[q]);
+}
+
+// r = b - lambda - A p on fluid rows with pairs of floats (see dfloat.cuh); FP32 copy of r;
+// block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}] as k_residual64.
+// ph == nullptr: residual of p = 0.
+__global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const float *ph, const float *pl,
+                                                               const float *bh, const float *bl,
+                                                               const double *lambda, float *r32, double *partials) {
+  __shared__ double sm[3][REDUCE_THREADS];
+  float lh, ll;
+  dfl::split(*lambda, lh, ll);
+  const int nx = v.nx, ny = v.ny, nz = v.nz, n = nx + ny + nz;
+  const float *H = v.h, *L = v.l;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  int nrow = 0;
+  const long long rows = (long long)ny * nz;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = (int)(row % ny), k = (int)(row / ny);
+    const float cymh = H[2 * nx + j], cyml = L[2 * nx + j], cyph = H[2 * nx + ny + j], cypl = L[2 * nx + ny + j];
+    const float czmh = H[2 * nx + 2 * ny + k], czml = L[2 * nx + 2 * ny + k];
+    const float czph = H[2 * nx + 2 * ny + nz + k], czpl = L[2 * nx + 2 * ny + nz + k];
+    float syh, syl;   // sdy_j + sdz_k
+    dfl::two_sum(H[2 * n + nx + j], H[2 * n + nx + ny + k], syh, syl);
+    syl += L[2 * n + nx + j] + L[2 * n + nx + ny + k];
+    const float dydz = H[3 * n + nx + j] * H[3 * n + nx + ny + k];
+    const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const long long id = base + i;
+      if (v.mask[id] != 0) continue;
+      float sh, sl;
+      dfl::two_sum(bh[id], -lh, sh, sl);
+      sl += bl[id] - ll;
+      if (ph) {
+        float dh, dl;   // diagonal sdx_i + sdy_j + sdz_k
+        dfl::two_sum(H[2 * n + i], syh, dh, dl);
+        dl += L[2 * n + i] + syl;
+        dfl::acc_prod(dh, dl, ph[id], pl[id], sh, sl);
+        dfl::acc_prod(-H[i], -L[i], ph[id - 1], pl[id - 1], sh, sl);
+        dfl::acc_prod(-H[nx + i], -L[nx + i], ph[id + 1], pl[id + 1], sh, sl);
+        dfl::acc_prod(-cymh, -cyml, ph[id - v.sy], pl[id - v.sy], sh, sl);
+        dfl::acc_prod(-cyph, -cypl, ph[id + v.sy], pl[id + v.sy], sh, sl);
+        dfl::acc_prod(-czmh, -czml, ph[id - v.sz], pl[id - v.sz], sh, sl);
+        dfl::acc_prod(-czph, -czpl, ph[id + v.sz], pl[id + v.sz], sh, sl);
+      }
+      const float rf = sh + sl;
+      if (r32) r32[id] = rf;
+      a0 = fmaf(H[3 * n + i] * dydz, rf, a0);
+      a1 += rf;
+      a2 = fmaf(rf, rf, a2);
+    }
+    // fold the FP32 partials into FP64 every 8 rows (bounded FP32 error)
+    if (++nrow == 8) {
+      A0 += a0; A1 += a1; A2 += a2;
+      a0 = a1 = a2 = 0.f;
+      nrow = 0;
+    }
+  }
+  A0 += a0; A1 += a1; A2 += a2;
+  sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sm[q][0];
+}
+
+// ghost rows r_G = sum w v - g in FP64 from the split values; block partials of (s_G r_G)^2
+__global__ void k_ghost_resid_df(const long long *src, const long long *dst, const double *w, const double *scale,
+                                 long long ng, const float *ph, const float *pl, float *r32, double *gpart) {
+  __shared__ double sm[REDUCE_THREADS];
+  double a = 0.0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      long long q = src[8 * g + c];
+      if (q >= 0) {
+        q &= ~GHOST_CORNER;
+        s += w[8 * g + c] * dfl::join(ph[q], pl[q]);
+      }
+    }
+    const long long d = dst[g];
+    const double rg = s - dfl::join(ph[d], pl[d]);
+    if (r32) r32[d] = (float)rg;
+    const double sr = scale[g] * rg;
+    a += sr * sr;
+  }
+  sm[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gpart[blockIdx.x] = sm[0];
+}
+
+// ghost values g = sum w v from the split values (into gtmp), then stored split (Jacobi)
+__global__ void k_ghost_eval_df(const long long *src, const double *w, long long ng, const float *ph,
+                                const float *pl, double *gtmp) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    long long q = src[8 * g + c];
+    if (q >= 0) {
+      q &= ~GHOST_CORNER;
+      s += w[8 * g + c] * dfl::join(ph[q], pl[q]);
+    }
+  }
+  gtmp[g] = s;
+}
+
+__global__ void k_ghost_store_df(const long long *dst, long long ng, const double *gtmp, float *ph, float *pl) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < ng) dfl::split(gtmp[g], ph[dst[g]], pl[dst[g]]);
+}
+
+// p += e (FP32 correction) on every padded cell, four at a time (n4 = ntot / 4)
+__global__ void k_update_df(float4 *ph, float4 *pl, const float4 *e, long long n4) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    float4 h = ph[q], l = pl[q];
+    const float4 x = e[q];
+    float *hv = &h.x, *lv = &l.x;
+    const float *xv = &x.x;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float s, t;
+      dfl::two_sum(hv[u], xv[u], s, t);
+      t += lv[u];
+      dfl::two_sum(s, t, hv[u], lv[u]);
+    }
+    ph[q] = h;
+    pl[q] = l;
+  }
+}
+
+// pack a user [k][j][i] array into split padded arrays; cells with mask == 1 (plain solid)
+// are set to zero when mask is given
+__global__ void k_pack_df(const double *src, LevelGeom g, float *dh, float *dl, const uint8_t *mask) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= (long long)g.nx * g.ny * g.nz) return;
+  int i = (int)(q % g.nx); long long r = q / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+  const long long id = pidx(g, i, j, k);
+  float h, l;
+  dfl::split(src[q], h, l);
+  if (mask && mask[id] == 1) h = l = 0.f;
+  dh[id] = h;
+  dl[id] = l;
+}
+
+// block partials of sum V p over fluid cells; V and the products as pairs of floats
+__global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum_df(DfView v, const float *ph, const float *pl,
+                                                                double *partials) {
+  __shared__ double sm[REDUCE_THREADS];
+  const int nx = v.nx, ny = v.ny, n = nx + ny + v.nz;
+  const float *H = v.h + 3 * n, *L = v.l + 3 * n;   // widths
+  float sh = 0.f, sl = 0.f;
+  const long long rows = (long long)ny * v.nz;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = (int)(row % ny), k = (int)(row / ny);
+    float ah = 0.f, al = 0.f, yzh, yzl;   // dy_j dz_k
+    dfl::acc_prod(H[nx + j], L[nx + j], H[nx + ny + k], L[nx + ny + k], ah, al);
+    dfl::fast_two_sum(ah, al, yzh, yzl);
+    const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const long long id = base + i;
+      if (v.mask[id] != 0) continue;
+      float vh = 0.f, vl = 0.f, Vh, Vl;
+      dfl::acc_prod(H[i], L[i], yzh, yzl, vh, vl);
+      dfl::fast_two_sum(vh, vl, Vh, Vl);
+      dfl::acc_prod(Vh, Vl, ph[id], pl[id], sh, sl);
+    }
+  }
+  sm[threadIdx.x] = dfl::join(sh, sl);
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
+// (grid-stride: the mean is split once per thread)
+__global__ void k_unpack_gauge_df(const float *ph, const float *pl, const uint8_t *mask, LevelGeom g,
+                                  const double *scal, double *dst) {
+  float mh, ml;
+  dfl::split(scal[S_MEANP], mh, ml);
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(q % g.nx); long long r = q / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+    const long long id = pidx(g, i, j, k);
+    if (mask[id] == 1) { dst[q] = 0.0; continue; }
+    float s, t;
+    dfl::two_sum(ph[id], -mh, s, t);
+    t += pl[id] - ml;
+    dst[q] = dfl::join(s, t);
+  }
+}
+
 __global__ void k_ghost_src(const long long *ref, const long long *cell, long long ng, LevelGeom g, long long *src,
                             long long *dst, const double *w, float *w32, const uint8_t *ib) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -612,9 +830,9 @@ void free_hierarchy(Hierarchy *h) {
     void *q[] = {L.mask, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt, L.wT, L.sdiag};
     ps.insert(ps.end(), q, q + 13);
   }
-  void *q[] = {h->p64, h->b64, h->minv, h->cidx, h->dncoarse, h->c64, h->gsrc, h->gdst, h->gw64, h->gw32, h->gtmp,
-               h->e_alt, h->tm_base[0], h->tm_base[1]};
-  ps.insert(ps.end(), q, q + 14);
+  void *q[] = {h->p64, h->b64, h->minv, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64, h->gw32,
+               h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1]};
+  ps.insert(ps.end(), q, q + 15);
   std::sort(ps.begin(), ps.end());
   ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
   for (void *p : ps) if (p) cudaFree(p);
@@ -819,6 +1037,7 @@ struct Solver {
   int nu1, nu2;
   double omega;
   int *d_ncoarse;
+  bool dfo = false;   // double-FP32 outer loop (precision mode 2)
 };
 
 template <typename T>
@@ -937,6 +1156,44 @@ LV<double> fine_view64(Hierarchy *h) {
   return v;
 }
 
+DfView fine_view_df(Hierarchy *h) {
+  Level &L0 = h->lv[0];
+  DfView v;
+  v.nx = L0.g.nx; v.ny = L0.g.ny; v.nz = L0.g.nz; v.px = L0.g.px; v.sy = L0.g.sy; v.sz = L0.g.sz;
+  v.mask = L0.mask;
+  const int n = v.nx + v.ny + v.nz;
+  v.h = h->cdf;
+  v.l = h->cdf + 4 * n;
+  return v;
+}
+
+// split views of the outer arrays in double-FP32 mode
+inline float *hi_of(double *a) { return reinterpret_cast<float *>(a); }
+inline float *lo_of(double *a, long long ntot) { return reinterpret_cast<float *>(a) + ntot; }
+
+void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda);
+
+// the outer residual, its norms and the lambda update; with_p == false: residual of p = 0
+void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
+  if (!S.dfo) return fine_residual(S, with_p ? S.h->p64 : nullptr, r32, update_lambda);
+  Hierarchy *h = S.h;
+  const long long ntot = h->lv[0].g.ntot;
+  double *part = S.ctx->partials;
+  float *ph = with_p ? hi_of(h->p64) : nullptr, *pl = lo_of(h->p64, ntot);
+  k_residual_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(fine_view_df(h), ph, pl, hi_of(h->b64),
+                                                           lo_of(h->b64, ntot), S.ctx->scal + S_LAMBDA, r32, part);
+  const long long ng = S.t->nghost;
+  const int ngb = 152;
+  double *gpart = part + 3 * REDUCE_BLOCKS;
+  const bool gh = ng > 0 && with_p;
+  if (gh)
+    k_ghost_resid_df<<<ngb, REDUCE_THREADS, 0, S.st>>>(h->gsrc, h->gdst, S.t->gw, S.t->gscale, ng, hi_of(h->p64),
+                                                       pl, r32, gpart);
+  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
+                                        update_lambda ? 1 : 0);
+  S.ctx->launches += gh ? 3 : 2;
+}
+
 void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
   LV<double> v = fine_view64(S.h);
   double *part = S.ctx->partials;
@@ -980,10 +1237,18 @@ ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
   k_axis_level<double><<<nblk(nz, 128), 128, 0, st>>>(df + nx + ny + 2, nz, c64 + 2 * nx + 2 * ny,
                                                       c64 + 2 * nx + 2 * ny + nz, w + nx + ny, c + nx + ny, nullptr,
                                                       sd + nx + ny);
+  h->c64 = c64;
+  if (precision == 2) {
+    // split coefficients, diagonal parts (3n doubles of c64) and widths (n of w1d)
+    float *cdf = nullptr;
+    IBM_TRY(cudaMalloc((void **)&cdf, sizeof(float) * 8 * n));
+    h->cdf = cdf;
+    k_split_df<<<nblk(3 * n, 128), 128, 0, st>>>(c64, 3 * n, cdf, cdf + 4 * n);
+    k_split_df<<<nblk(n, 128), 128, 0, st>>>(L0.w1d, n, cdf + 3 * n, cdf + 7 * n);
+  }
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaStreamSynchronize(st));
   cudaFree(df); cudaFree(w); cudaFree(c);
-  h->c64 = c64;
   t->hier[precision] = h;
   return IBM_OK;
 }
@@ -997,24 +1262,36 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   Level &L0 = h->lv[0];
   const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
   Solver S{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
+  S.dfo = prec == 2;
+  const long long ntot = L0.g.ntot;
   // inputs
-  k_pack<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, h->b64);
-  k_pack<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, h->p64);
-  k_zero_solid<<<1216, 256, 0, st>>>(h->p64, L0.mask, L0.g.ntot);
-  ctx->launches += 3;
+  if (S.dfo) {
+    k_pack_df<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, ntot), nullptr);
+    k_pack_df<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, ntot), L0.mask);
+    ctx->launches += 2;
+  } else {
+    k_pack<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, h->b64);
+    k_pack<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, h->p64);
+    k_zero_solid<<<1216, 256, 0, st>>>(h->p64, L0.mask, L0.g.ntot);
+    ctx->launches += 3;
+  }
   double hs[NSCAL] = {0};
   hs[S_FLUIDVOL] = L0.fluid_vol;
   hs[S_NF] = (double)L0.nfluid;
   IBM_TRY(cudaMemcpyAsync(ctx->scal, hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   // ||S P b||: residual of p = 0 with lambda = 0
-  fine_residual(S, nullptr, nullptr, false);
+  outer_residual(S, false, nullptr, false);
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
   IBM_TRY(cudaStreamSynchronize(st));
   const double bnorm = std::sqrt(ctx->hscal[S_NORM2]);
   const double denom = bnorm > 0 ? bnorm : 1.0;
   // initial ghost values consistent with p, and the initial residual
   const long long ng = t->nghost;
-  if (ng > 0) {
+  if (ng > 0 && S.dfo) {
+    k_ghost_eval_df<<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, t->gw, ng, hi_of(h->p64), lo_of(h->p64, ntot), h->gtmp);
+    k_ghost_store_df<<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, hi_of(h->p64), lo_of(h->p64, ntot));
+    ctx->launches += 2;
+  } else if (ng > 0) {
     k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, ng, h->p64, nullptr, h->gtmp);
     k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, h->p64);
     ctx->launches += 2;
@@ -1024,8 +1301,8 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   double rel = 0.0;
   int hl = 0;
   ibm_status result = IBM_ERR_NOT_CONVERGED;
-  float *r32 = prec == 1 ? (float *)L0.r : nullptr;
-  fine_residual(S, h->p64, r32, true);
+  float *r32 = prec != 0 ? (float *)L0.r : nullptr;
+  outer_residual(S, true, r32, true);
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
   IBM_TRY(cudaStreamSynchronize(st));
   rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
@@ -1046,14 +1323,19 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
         if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * L0.g.ntot, bs);
         vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
       }
-      k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, L0.g.ntot);
+      if (S.dfo)
+        k_update_df<<<1216, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
+                                          reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
+                                          reinterpret_cast<const float4 *>(e32), ntot / 4);
+      else
+        k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, L0.g.ntot);
       ctx->launches += 1;
-      fine_residual(S, h->p64, r32, true);
+      outer_residual(S, true, r32, true);
     }
     S.st = st;
   };
   const long long sweeps_per_cycle =
-      (long long)(opts->nu1 + opts->nu2) * (prec == 1 ? std::max(1, opts->inner_cycles) : 1);
+      (long long)(opts->nu1 + opts->nu2) * (prec != 0 ? std::max(1, opts->inner_cycles) : 1);
   const bool graph = opts->use_graph && ctx->cap_stream && (!h->zmarch || sweeps_per_cycle % 2 == 0);
   long long graph_launches = 0;
   if (graph) {
@@ -1096,9 +1378,16 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     if (rel <= tol) result = IBM_OK;
   }
   // gauge and unpack
-  k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
+  if (S.dfo)
+    k_gauge_sum_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view_df(h), hi_of(h->p64), lo_of(h->p64, ntot),
+                                                             ctx->partials);
+  else
+    k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
   k_gauge_finalize<<<1, 256, 0, st>>>(ctx->partials, REDUCE_BLOCKS, ctx->scal);
-  k_unpack_gauge<<<nblk(n0, 256), 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
+  if (S.dfo)
+    k_unpack_gauge_df<<<1216, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, ctx->scal, p_user);
+  else
+    k_unpack_gauge<<<nblk(n0, 256), 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
   ctx->launches += 3;
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
