@@ -115,6 +115,19 @@ ibm_status ibm_classify(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mesh
                         int32_t nmesh, ibm_tables **out, void *stream);
 ibm_status ibm_tables_destroy(ibm_tables *t);
 
+/* Reclassify existing tables for new body positions on the same grid (a moving body, one
+ * call per time step).  Same classification as ibm_classify with these meshes, written
+ * into the tables' own device memory: its arrays are reused (the per-ghost arrays grow
+ * when the ghost count exceeds their capacity, never shrink), and the solver work arrays
+ * of every precision keep their grid-only data; their geometry-dependent parts (masks,
+ * face fractions, fluid volumes, coarsest inverse, ghost rows) are recomputed by the next
+ * solve, which replays its captured cycle when the ghost capacity did not change.
+ * Device arrays obtained earlier from ibm_tables_export are not updated.  Synchronises
+ * `stream`.  On IBM_ERR_NO_FLUID the tables hold the new (fluid-free) classification and
+ * cannot be solved; other errors leave them unusable except for ibm_tables_destroy. */
+ibm_status ibm_reclassify(ibm_ctx *ctx, ibm_tables *t, const ibm_mesh *meshes, int32_t nmesh,
+                          void *stream);
+
 /* Sizes of a classified grid: cells, fluid cells, ghost entries, solid cells. */
 ibm_status ibm_tables_counts(const ibm_tables *t, int64_t *ncell, int64_t *nfluid,
                              int64_t *nghost, int64_t *nsolid);

@@ -41,7 +41,7 @@ struct BProb {
   const double *gscale;
   double *gtmp;
   // coarsest
-  const double *minv;
+  const void *minv;   // element type of the levels
   const int *cidx, *ncoarse;
   long long ntot0;
 };
@@ -228,7 +228,8 @@ __global__ void kb_coarsest(const BLev<T> *const *Lc, const BProb *P, int np) {
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     double s = 0.0;
-    for (int c = 0; c < n; ++c) s += P[p].minv[q * m + c] * rs[c];
+    const T *Mv = static_cast<const T *>(P[p].minv);
+    for (int c = 0; c < n; ++c) s += (double)Mv[q * m + c] * rs[c];
     B.e[P[p].cidx[q]] = (T)s;
   }
 }
@@ -624,14 +625,14 @@ ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const 
     Hierarchy *h = B.hs[p];
     Level &L0 = h->lv[0];
     const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
-    k_pack<<<nblk(n0, 256), 256, 0, st>>>(rhs[p], L0.g, h->b64);
-    k_pack<<<nblk(n0, 256), 256, 0, st>>>(p_user[p], L0.g, h->p64);
-    k_zero_solid<<<1216, 256, 0, st>>>(h->p64, L0.mask, L0.g.ntot);
+    k_pack<<<PACK_BLOCKS, 256, 0, st>>>(rhs[p], L0.g, h->b64, nullptr);
+    k_pack<<<PACK_BLOCKS, 256, 0, st>>>(p_user[p], L0.g, h->p64, L0.mask);
     const long long ng = ts[p]->nghost;
     if (ng > 0) {
-      k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, ts[p]->gw, ng, h->p64, nullptr,
+      k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, ts[p]->gw, ng, nullptr, h->p64,
+                                                                  nullptr,
                                                                   h->gtmp);
-      k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, h->p64);
+      k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, nullptr, h->gtmp, h->p64);
     }
     ctx->launches += ng > 0 ? 5 : 3;
     hs[(size_t)p * NSCAL + S_FLUIDVOL] = L0.fluid_vol;
@@ -738,7 +739,7 @@ ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const 
     double *ps = B.d_scal + (size_t)p * NSCAL;
     k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
     k_gauge_finalize<<<1, 256, 0, st>>>(ctx->partials, REDUCE_BLOCKS, ps);
-    k_unpack_gauge<<<nblk(n0, 256), 256, 0, st>>>(h->p64, L0.mask, L0.g, ps, p_user[p]);
+    k_unpack_gauge<<<PACK_BLOCKS, 256, 0, st>>>(h->p64, L0.mask, L0.g, ps, p_user[p]);
     ctx->launches += 3;
   }
   IBM_TRY(cudaGetLastError());

@@ -22,6 +22,7 @@ ibm_status check(cudaError_t e, const char *where) {
 
 ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes, int nmesh, ibm_tables **out,
                          cudaStream_t st);
+ibm_status reclassify_impl(ibm_ctx *ctx, ibm_tables *t, const ibm_mesh *meshes, int nmesh, cudaStream_t st);
 ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
 ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st);
@@ -94,12 +95,17 @@ ibm_status ibm_classify(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mesh
   return ibm::classify_impl(ctx, grid, meshes, nmesh, out, (cudaStream_t)stream);
 }
 
+ibm_status ibm_reclassify(ibm_ctx *ctx, ibm_tables *t, const ibm_mesh *meshes, int32_t nmesh, void *stream) {
+  return ibm::reclassify_impl(ctx, t, meshes, nmesh, (cudaStream_t)stream);
+}
+
 ibm_status ibm_tables_destroy(ibm_tables *t) {
   if (!t) return IBM_ERR_INVALID_ARG;
   if (t->ctx) cudaSetDevice(t->ctx->device);
   cudaDeviceSynchronize();
   for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
-  void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref};
+  void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref, t->axis,
+                t->scratch};
   for (void *p : ps) if (p) cudaFree(p);
   delete t;
   return IBM_OK;

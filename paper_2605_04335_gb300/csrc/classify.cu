@@ -584,31 +584,49 @@ __global__ void k_gather_tris(const double *verts, const int *tris, int ntri, do
     for (int d = 0; d < 3; ++d) tv[9 * t + 3 * q + d] = verts[3 * tris[3 * t + q] + d];
 }
 
-template <typename T>
-struct DevBuf {
-  T *p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
-  cudaError_t alloc(size_t n) { return cudaMalloc((void **)&p, (n ? n : 1) * sizeof(T)); }
+// Device scratch of one tables object.  Allocations are bump pointers into a block the
+// tables keep between classifications; a call that needs more than the block holds takes
+// extra blocks, and when it ends the tables' block is regrown to the whole amount, so
+// repeated classifications of similar geometry allocate nothing.
+struct Scratch {
+  ibm_tables *t;
+  size_t used = 0, extra_bytes = 0;
+  std::vector<void *> extra;
+  explicit Scratch(ibm_tables *tt) : t(tt) {}
+  template <typename T>
+  cudaError_t get(T **p, size_t n) {
+    const size_t bytes = ((n ? n : 1) * sizeof(T) + 255) & ~(size_t)255;
+    if (used + bytes <= t->scratch_cap) {
+      *p = reinterpret_cast<T *>(t->scratch + used);
+      used += bytes;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) { extra.push_back(*p); extra_bytes += bytes; }
+    return e;
+  }
+  // call after the stream has drained: release the extra blocks, regrow the kept one
+  cudaError_t finish() {
+    for (void *q : extra) cudaFree(q);
+    extra.clear();
+    if (extra_bytes == 0) return cudaSuccess;
+    const size_t want = used + extra_bytes;
+    extra_bytes = 0;
+    if (t->scratch) cudaFree(t->scratch);
+    t->scratch = nullptr;
+    t->scratch_cap = 0;
+    cudaError_t e = cudaMalloc((void **)&t->scratch, want);
+    if (e == cudaSuccess) t->scratch_cap = want;
+    return e;
+  }
+  ~Scratch() { for (void *q : extra) cudaFree(q); }
 };
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-}  // namespace
-
-// Host orchestration of ibm_classify (see include/ibm_poisson.h).
-ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes, int nmesh, ibm_tables **out,
-                         cudaStream_t st) {
-  if (!ctx || !grid || !out || nmesh < 0 || (nmesh > 0 && !meshes)) return IBM_ERR_INVALID_ARG;
-  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
-  if (nx < 2 || ny < 2 || nz < 2 || !grid->xf || !grid->yf || !grid->zf) return IBM_ERR_INVALID_ARG;
-  const double *fs[3] = {grid->xf, grid->yf, grid->zf};
-  const int ns[3] = {nx, ny, nz};
-  for (int a = 0; a < 3; ++a)
-    for (int i = 0; i <= ns[a]; ++i) {
-      double v = fs[a][i];
-      if (!(std::fabs(v) <= COORD_LIMIT) || (i > 0 && !(v > fs[a][i - 1]))) return IBM_ERR_INVALID_ARG;
-    }
-  long long totverts = 0, tottris = 0;
+ibm_status check_meshes(const ibm_mesh *meshes, int nmesh, long long &totverts, long long &tottris) {
+  if (nmesh < 0 || (nmesh > 0 && !meshes)) return IBM_ERR_INVALID_ARG;
+  totverts = tottris = 0;
   for (int m = 0; m < nmesh; ++m) {
     const ibm_mesh &M = meshes[m];
     if (M.nverts < 0 || M.ntris < 0 || (M.ntris > 0 && (!M.verts || !M.tris))) return IBM_ERR_INVALID_ARG;
@@ -620,51 +638,91 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
     totverts += M.nverts;
     tottris += M.ntris;
   }
-  IBM_TRY(cudaSetDevice(ctx->device));
-  const long long ncell = (long long)nx * ny * nz;
+  return IBM_OK;
+}
 
-  ibm_tables *T = new ibm_tables();
-  T->ctx = ctx;
-  T->nx = nx; T->ny = ny; T->nz = nz;
-  T->xf.assign(grid->xf, grid->xf + nx + 1);
-  T->yf.assign(grid->yf, grid->yf + ny + 1);
-  T->zf.assign(grid->zf, grid->zf + nz + 1);
-  T->ncell = ncell;
-  auto fail = [&](ibm_status s) { ibm_tables_destroy(T); return s; };
+// grow the per-ghost arrays of the tables to hold ng entries (contents are rewritten)
+cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
+  if (ng <= T->gcap && T->gcell) return cudaSuccess;
+  const long long cap = std::max<long long>(std::max<long long>(ng + ng / 4, 1024), T->gcap);
+  void *ps[] = {T->gcell, T->gbi, T->gip, T->gw, T->gscale, T->gbase, T->gflags, T->gref};
+  for (void *q : ps) if (q) cudaFree(q);
+  T->gcell = nullptr; T->gbi = T->gip = T->gw = T->gscale = nullptr; T->gbase = T->gflags = nullptr; T->gref = nullptr;
+  T->gcap = 0;
+  cudaError_t e = cudaMalloc(&T->gcell, cap * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gbi, cap * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gip, cap * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gw, cap * 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gscale, cap * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gbase, cap * 3 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gflags, cap * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gref, cap * 8 * sizeof(long long));
+  if (e == cudaSuccess) T->gcap = cap;
+  return e;
+}
+
+// Classification of the meshes on the tables' grid, into the tables' own arrays.
+ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long long totverts, long long tottris,
+                         cudaStream_t st) {
+  const int nx = T->nx, ny = T->ny, nz = T->nz;
+  const long long ncell = T->ncell;
+  ibm_ctx *ctx = T->ctx;
+  Scratch S(T);
 #define CTRY(call)                                                  \
   do {                                                              \
     cudaError_t e__ = (call);                                       \
-    if (e__ != cudaSuccess) return fail(ibm::check(e__, #call));    \
+    if (e__ != cudaSuccess) return ibm::check(e__, #call);          \
   } while (0)
-
-  // axes: faces -> centres, snapped centres, widths, coefficients (device)
-  DevBuf<double> df[3], dc[3], dw[3], dcm[3], dcp[3];
-  DevBuf<long long> ds[3];
-  for (int a = 0; a < 3; ++a) {
-    CTRY(df[a].alloc(ns[a] + 1)); CTRY(dc[a].alloc(ns[a])); CTRY(dw[a].alloc(ns[a]));
-    CTRY(dcm[a].alloc(ns[a])); CTRY(dcp[a].alloc(ns[a])); CTRY(ds[a].alloc(ns[a]));
-    CTRY(cudaMemcpyAsync(df[a].p, fs[a], (ns[a] + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_axis<<<nblk(ns[a], 128), 128, 0, st>>>(df[a].p, ns[a], dc[a].p, ds[a].p, dw[a].p, dcm[a].p, dcp[a].p);
+  // axes (grid only, once per tables): faces, centres, snapped centres, widths, coefficients
+  const int ns[3] = {nx, ny, nz};
+  const std::vector<double> *fs[3] = {&T->xf, &T->yf, &T->zf};
+  if (!T->axis) {
+    size_t words = 0;
+    for (int a = 0; a < 3; ++a) words += 6 * (size_t)ns[a] + 1;
+    CTRY(cudaMalloc((void **)&T->axis, words * sizeof(double)));
+    size_t o = 0;
+    for (int a = 0; a < 3; ++a) {
+      double *base = T->axis + o;
+      double *df = base, *dc = df + ns[a] + 1, *dw = dc + ns[a], *dcm = dw + ns[a], *dcp = dcm + ns[a];
+      long long *ds = reinterpret_cast<long long *>(dcp + ns[a]);
+      CTRY(cudaMemcpyAsync(df, fs[a]->data(), (ns[a] + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+      k_axis<<<nblk(ns[a], 128), 128, 0, st>>>(df, ns[a], dc, ds, dw, dcm, dcp);
+      o += 6 * (size_t)ns[a] + 1;
+    }
+    CTRY(cudaGetLastError());
+    ctx->launches += 3;
   }
-  CTRY(cudaGetLastError());
-  CTRY(cudaMalloc(&T->iblank, ncell));
+  double *dc[3], *dcm[3], *dcp[3];
+  long long *ds[3];
+  {
+    size_t o = 0;
+    for (int a = 0; a < 3; ++a) {
+      double *base = T->axis + o;
+      dc[a] = base + ns[a] + 1;
+      dcm[a] = dc[a] + 2 * ns[a];
+      dcp[a] = dcm[a] + ns[a];
+      ds[a] = reinterpret_cast<long long *>(dcp[a] + ns[a]);
+      o += 6 * (size_t)ns[a] + 1;
+    }
+  }
+  if (!T->iblank) CTRY(cudaMalloc(&T->iblank, ncell));
   CTRY(cudaMemsetAsync(T->iblank, 0, ncell, st));
 
   // inside test per closed mesh
-  DevBuf<double> dverts;
-  DevBuf<int> dtris;
-  CTRY(dverts.alloc(3 * (totverts ? totverts : 1)));
-  CTRY(dtris.alloc(3 * (tottris ? tottris : 1)));
+  double *dverts = nullptr;
+  int *dtris = nullptr;
+  CTRY(S.get(&dverts, 3 * totverts));
+  CTRY(S.get(&dtris, 3 * tottris));
   std::vector<int> vbase(nmesh), tbase(nmesh);
   {
     long long vo = 0, to = 0;
     for (int m = 0; m < nmesh; ++m) {
       vbase[m] = (int)vo; tbase[m] = (int)to;
       if (meshes[m].nverts)
-        CTRY(cudaMemcpyAsync(dverts.p + 3 * vo, meshes[m].verts, 3 * sizeof(double) * meshes[m].nverts,
+        CTRY(cudaMemcpyAsync(dverts + 3 * vo, meshes[m].verts, 3 * sizeof(double) * meshes[m].nverts,
                              cudaMemcpyHostToDevice, st));
       if (meshes[m].ntris)
-        CTRY(cudaMemcpyAsync(dtris.p + 3 * to, meshes[m].tris, 3 * sizeof(int) * meshes[m].ntris,
+        CTRY(cudaMemcpyAsync(dtris + 3 * to, meshes[m].tris, 3 * sizeof(int) * meshes[m].ntris,
                              cudaMemcpyHostToDevice, st));
       vo += meshes[m].nverts;
       to += meshes[m].ntris;
@@ -672,27 +730,26 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
   }
   const int words = (nz + 1 + 31) / 32;
   if (tottris > 0) {
-    DevBuf<unsigned> tog, ons;
-    CTRY(tog.alloc((size_t)nx * ny * words));
-    CTRY(ons.alloc((size_t)nx * ny * words));
-    CTRY(cudaMemsetAsync(tog.p, 0, (size_t)nx * ny * words * 4, st));
-    CTRY(cudaMemsetAsync(ons.p, 0, (size_t)nx * ny * words * 4, st));
+    unsigned *tog = nullptr, *ons = nullptr;
+    CTRY(S.get(&tog, (size_t)nx * ny * words));
+    CTRY(S.get(&ons, (size_t)nx * ny * words));
+    CTRY(cudaMemsetAsync(tog, 0, (size_t)nx * ny * words * 4, st));
+    CTRY(cudaMemsetAsync(ons, 0, (size_t)nx * ny * words * 4, st));
     for (int m = 0; m < nmesh; ++m) {
       const int nt = meshes[m].ntris;
       if (nt == 0) continue;
-      DevBuf<Tri> tr;
-      DevBuf<long long> cnt, off;
-      CTRY(tr.alloc(nt)); CTRY(cnt.alloc(nt)); CTRY(off.alloc(nt + 1));
-      k_tri_setup<<<nblk(nt, 128), 128, 0, st>>>(dverts.p + 3LL * vbase[m], dtris.p + 3LL * tbase[m], nt, ds[0].p,
-                                                  nx, ds[1].p, ny, ds[2].p, nz, tr.p, cnt.p);
-      k_scan_single<<<1, 1024, 0, st>>>(cnt.p, off.p, nt);
+      Tri *tr = nullptr;
+      long long *cnt = nullptr, *off = nullptr;
+      CTRY(S.get(&tr, nt)); CTRY(S.get(&cnt, nt)); CTRY(S.get(&off, nt + 1));
+      k_tri_setup<<<nblk(nt, 128), 128, 0, st>>>(dverts + 3LL * vbase[m], dtris + 3LL * tbase[m], nt, ds[0], nx,
+                                                  ds[1], ny, ds[2], nz, tr, cnt);
+      k_scan_single<<<1, 1024, 0, st>>>(cnt, off, nt);
       long long total = 0;
-      CTRY(cudaMemcpyAsync(&total, off.p + nt, sizeof(long long), cudaMemcpyDeviceToHost, st));
+      CTRY(cudaMemcpyAsync(&total, off + nt, sizeof(long long), cudaMemcpyDeviceToHost, st));
       CTRY(cudaStreamSynchronize(st));
       if (total > 0) {
         unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 8LL * 152 * 4);
-        k_tri_pairs<<<blocks, 256, 0, st>>>(tr.p, off.p, nt, total, ds[0].p, ds[1].p, ds[2].p, nx, ny, nz, words,
-                                            tog.p, ons.p);
+        k_tri_pairs<<<blocks, 256, 0, st>>>(tr, off, nt, total, ds[0], ds[1], ds[2], nx, ny, nz, words, tog, ons);
       }
       // columns of the mesh's xy box
       double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
@@ -709,63 +766,48 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
       i1 = std::min(nx, i1 + 1); j1 = std::min(ny, j1 + 1);
       if (i1 > i0 && j1 > j0) {
         dim3 gp(nblk(i1 - i0, 128), j1 - j0);
-        k_parity<<<gp, 128, 0, st>>>(tog.p, ons.p, words, nx, ny, nz, i0, i1, j0, j1, T->iblank);
+        k_parity<<<gp, 128, 0, st>>>(tog, ons, words, nx, ny, nz, i0, i1, j0, j1, T->iblank);
       }
       CTRY(cudaGetLastError());
-      CTRY(cudaStreamSynchronize(st));
     }
   }
 
   // ghost marking + sorted compaction
   const long long chunk = (long long)GM_THREADS * GM_PER;
   const unsigned nb = (unsigned)((ncell + chunk - 1) / chunk);
+  unsigned long long *cellcnt = nullptr;
   {
-    DevBuf<long long> bc, bo;
-    CTRY(bc.alloc(nb)); CTRY(bo.alloc(nb + 1));
-    k_ghost_count<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bc.p);
-    k_scan_single<<<1, 1024, 0, st>>>(bc.p, bo.p, (int)nb);
+    long long *bc = nullptr, *bo = nullptr;
+    CTRY(S.get(&bc, nb)); CTRY(S.get(&bo, nb + 1));
+    CTRY(S.get(&cellcnt, 2));
+    CTRY(cudaMemsetAsync(cellcnt, 0, 16, st));
+    k_ghost_count<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bc);
+    k_scan_single<<<1, 1024, 0, st>>>(bc, bo, (int)nb);
     long long ng = 0;
-    CTRY(cudaMemcpyAsync(&ng, bo.p + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CTRY(cudaMemcpyAsync(&ng, bo + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CTRY(cudaStreamSynchronize(st));
     T->nghost = ng;
-    CTRY(cudaMalloc(&T->gcell, (ng ? ng : 1) * sizeof(long long)));
+    CTRY(ensure_ghost_capacity(T, ng));
     if (ng) {
-      k_ghost_scatter<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bo.p, T->gcell);
+      k_ghost_scatter<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bo, T->gcell);
       k_ghost_bits<<<nblk(ng, 256), 256, 0, st>>>(T->iblank, T->gcell, ng);
     }
+    k_count_cells<<<1216, 256, 0, st>>>(T->iblank, ncell, cellcnt);
     CTRY(cudaGetLastError());
   }
-  {
-    DevBuf<unsigned long long> cnt;
-    CTRY(cnt.alloc(2));
-    CTRY(cudaMemsetAsync(cnt.p, 0, 16, st));
-    k_count_cells<<<1216, 256, 0, st>>>(T->iblank, ncell, cnt.p);
-    unsigned long long hc[2];
-    CTRY(cudaMemcpyAsync(hc, cnt.p, 16, cudaMemcpyDeviceToHost, st));
-    CTRY(cudaStreamSynchronize(st));
-    T->nfluid = (long long)hc[0];
-    T->nsolid = (long long)hc[1];
-  }
   const long long ng = T->nghost;
-  CTRY(cudaMalloc(&T->gbi, (ng ? ng : 1) * 3 * sizeof(double)));
-  CTRY(cudaMalloc(&T->gip, (ng ? ng : 1) * 3 * sizeof(double)));
-  CTRY(cudaMalloc(&T->gw, (ng ? ng : 1) * 8 * sizeof(double)));
-  CTRY(cudaMalloc(&T->gscale, (ng ? ng : 1) * sizeof(double)));
-  CTRY(cudaMalloc(&T->gbase, (ng ? ng : 1) * 3 * sizeof(int)));
-  CTRY(cudaMalloc(&T->gflags, (ng ? ng : 1) * sizeof(int)));
-  CTRY(cudaMalloc(&T->gref, (ng ? ng : 1) * 8 * sizeof(long long)));
   if (ng > 0) {
     // all closed-mesh triangles, concatenated in mesh order (global triangle index)
-    DevBuf<double> tv;
-    DevBuf<float4> blo, bhi, cen;
-    CTRY(tv.alloc(9 * tottris));
-    CTRY(blo.alloc(tottris)); CTRY(bhi.alloc(tottris)); CTRY(cen.alloc(tottris));
+    double *tv = nullptr;
+    float4 *blo = nullptr, *bhi = nullptr, *cen = nullptr;
+    CTRY(S.get(&tv, 9 * tottris));
+    CTRY(S.get(&blo, tottris)); CTRY(S.get(&bhi, tottris)); CTRY(S.get(&cen, tottris));
     std::vector<MeshRange> hmr;
     for (int m = 0; m < nmesh; ++m) {
       const int nt = meshes[m].ntris;
       if (nt == 0) continue;
-      k_gather_tris<<<nblk(nt, 128), 128, 0, st>>>(dverts.p + 3LL * vbase[m], dtris.p + 3LL * tbase[m], nt,
-                                                    tv.p + 9LL * tbase[m]);
+      k_gather_tris<<<nblk(nt, 128), 128, 0, st>>>(dverts + 3LL * vbase[m], dtris + 3LL * tbase[m], nt,
+                                                    tv + 9LL * tbase[m]);
       MeshRange r;
       r.t0 = tbase[m]; r.t1 = tbase[m] + nt;
       for (int d = 0; d < 3; ++d) { r.lo[d] = 1e300; r.hi[d] = -1e300; }
@@ -775,30 +817,78 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
       }
       hmr.push_back(r);
     }
-    k_tri_boxes<<<nblk(tottris, 128), 128, 0, st>>>(tv.p, (int)tottris, blo.p, bhi.p, cen.p);
-    DevBuf<MeshRange> dmr;
-    CTRY(dmr.alloc(hmr.size()));
-    CTRY(cudaMemcpyAsync(dmr.p, hmr.data(), hmr.size() * sizeof(MeshRange), cudaMemcpyHostToDevice, st));
+    k_tri_boxes<<<nblk(tottris, 128), 128, 0, st>>>(tv, (int)tottris, blo, bhi, cen);
+    MeshRange *dmr = nullptr;
+    CTRY(S.get(&dmr, hmr.size()));
+    CTRY(cudaMemcpyAsync(dmr, hmr.data(), hmr.size() * sizeof(MeshRange), cudaMemcpyHostToDevice, st));
     GhostArgs ga;
     ga.nx = nx; ga.ny = ny; ga.nz = nz;
-    ga.xc = dc[0].p; ga.yc = dc[1].p; ga.zc = dc[2].p;
-    ga.cxm = dcm[0].p; ga.cxp = dcp[0].p; ga.cym = dcm[1].p; ga.cyp = dcp[1].p; ga.czm = dcm[2].p; ga.czp = dcp[2].p;
+    ga.xc = dc[0]; ga.yc = dc[1]; ga.zc = dc[2];
+    ga.cxm = dcm[0]; ga.cxp = dcp[0]; ga.cym = dcm[1]; ga.cyp = dcp[1]; ga.czm = dcm[2]; ga.czp = dcp[2];
     ga.ib = T->iblank;
-    ga.tv = tv.p; ga.blo = blo.p; ga.bhi = bhi.p; ga.cen = cen.p;
-    ga.mr = dmr.p; ga.nmesh = (int)hmr.size();
+    ga.tv = tv; ga.blo = blo; ga.bhi = bhi; ga.cen = cen;
+    ga.mr = dmr; ga.nmesh = (int)hmr.size();
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
     k_ghost_tables<<<nblk(32 * ng, 128), 128, 0, st>>>(ga);
     CTRY(cudaGetLastError());
-    CTRY(cudaStreamSynchronize(st));
   }
+  unsigned long long hc[2];
+  CTRY(cudaMemcpyAsync(hc, cellcnt, 16, cudaMemcpyDeviceToHost, st));
   CTRY(cudaStreamSynchronize(st));
-  ctx->launches += 3 + 2 * (long long)nmesh * 3 + 5 + (T->nghost > 0 ? 2 + (long long)nmesh : 0);
+  T->nfluid = (long long)hc[0];
+  T->nsolid = (long long)hc[1];
+  CTRY(S.finish());
+  T->geom_version += 1;
+  ctx->launches += 2 + 2 * (long long)nmesh * 3 + 5 + (T->nghost > 0 ? 2 + (long long)nmesh : 0);
 #undef CTRY
-  if (T->nfluid == 0) return fail(IBM_ERR_NO_FLUID);
+  return T->nfluid == 0 ? IBM_ERR_NO_FLUID : IBM_OK;
+}
+
+}  // namespace
+
+// Host orchestration of ibm_classify (see include/ibm_poisson.h).
+ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes, int nmesh, ibm_tables **out,
+                         cudaStream_t st) {
+  if (!ctx || !grid || !out) return IBM_ERR_INVALID_ARG;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  if (nx < 2 || ny < 2 || nz < 2 || !grid->xf || !grid->yf || !grid->zf) return IBM_ERR_INVALID_ARG;
+  const double *fs[3] = {grid->xf, grid->yf, grid->zf};
+  const int ns[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i <= ns[a]; ++i) {
+      double v = fs[a][i];
+      if (!(std::fabs(v) <= COORD_LIMIT) || (i > 0 && !(v > fs[a][i - 1]))) return IBM_ERR_INVALID_ARG;
+    }
+  long long totverts = 0, tottris = 0;
+  ibm_status s = check_meshes(meshes, nmesh, totverts, tottris);
+  if (s != IBM_OK) return s;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  ibm_tables *T = new ibm_tables();
+  T->ctx = ctx;
+  T->nx = nx; T->ny = ny; T->nz = nz;
+  T->xf.assign(grid->xf, grid->xf + nx + 1);
+  T->yf.assign(grid->yf, grid->yf + ny + 1);
+  T->zf.assign(grid->zf, grid->zf + nz + 1);
+  T->ncell = (long long)nx * ny * nz;
+  s = classify_into(T, meshes, nmesh, totverts, tottris, st);
+  if (s != IBM_OK) {
+    ibm_tables_destroy(T);
+    return s;
+  }
   *out = T;
   return IBM_OK;
+}
+
+// Host orchestration of ibm_reclassify: same grid, new body positions, the tables' memory.
+ibm_status reclassify_impl(ibm_ctx *ctx, ibm_tables *T, const ibm_mesh *meshes, int nmesh, cudaStream_t st) {
+  if (!ctx || !T || T->ctx != ctx) return IBM_ERR_INVALID_ARG;
+  long long totverts = 0, tottris = 0;
+  ibm_status s = check_meshes(meshes, nmesh, totverts, tottris);
+  if (s != IBM_OK) return s;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return classify_into(T, meshes, nmesh, totverts, tottris, st);
 }
 
 }  // namespace ibm

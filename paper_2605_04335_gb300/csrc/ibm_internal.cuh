@@ -53,6 +53,8 @@ __host__ __device__ inline long long pidx(const LevelGeom &g, int i, int j, int 
 struct Level {
   LevelGeom g;
   uint8_t *mask = nullptr;                  // padded; 0 = active fluid row
+  uint8_t *inner = nullptr;                 // levels >= 1, padded: 1 where the cell and its 26
+                                            // neighbours are all fluid
   void *e = nullptr, *r = nullptr;          // padded, element type of the hierarchy
   void *fx = nullptr, *fy = nullptr, *fz = nullptr;   // face fractions (levels >= 1)
   void *c1d = nullptr;                      // cxm cxp cym cyp czm czp (n each, element type)
@@ -74,18 +76,23 @@ struct Hierarchy {
   double *p64 = nullptr, *b64 = nullptr;
   // coarsest dense bordered inverse
   int ncoarse = 0;                          // unknowns of the coarsest level (fluid cells)
-  double *minv = nullptr;                   // (ncoarse+1)^2
+  void *minv = nullptr;                     // (MAX_COARSE+1)^2, element type of the levels
+  void *gj = nullptr;                       // Gauss-Jordan work matrix (global fallback)
   int *cidx = nullptr;                      // padded index of each coarsest unknown
   int *dncoarse = nullptr;                  // device copy of ncoarse
   double *c64 = nullptr;                    // FP64 fine coefficients cxm cxp cym cyp czm czp
-  float *cdf = nullptr;                     // double-FP32 mode: fine coefficients, diagonal parts
-                                            // and widths split into hi (4n floats) and lo (4n)
+  float *cdf = nullptr;                     // fine coefficients, diagonal parts and widths split
+                                            // into hi (4n floats) and lo (4n) parts
   // solver-side ghost rows: padded source indices (-1 unused), weights (double and float)
   long long *gsrc = nullptr;
   long long *gdst = nullptr;
   double *gw64 = nullptr;
   float *gw32 = nullptr;
   double *gtmp = nullptr;                   // new ghost values (Jacobi)
+  long long geom_version = -1;              // classification the geometry-dependent parts match
+  long long gcap = 0;                       // capacity of the solver-side ghost arrays
+  double *d_fvol = nullptr;                 // fluid volume per level (device)
+  long long *d_ng = nullptr;                // ghost count (device)
   void *graph_exec = nullptr;               // one captured cycle (see solve_impl)
   long long graph_key = 0;
   long long graph_launches = 0;             // kernels in the captured cycle
@@ -122,6 +129,11 @@ struct ibm_tables {
   double *gbi = nullptr, *gip = nullptr, *gw = nullptr, *gscale = nullptr;
   int *gbase = nullptr, *gflags = nullptr;
   long long *gref = nullptr;
+  long long gcap = 0;                // capacity of the per-ghost arrays (entries)
+  long long geom_version = 0;        // incremented by every classification of these tables
+  double *axis = nullptr;            // per-axis faces, centres, widths, coefficients, snapped centres
+  char *scratch = nullptr;           // classification scratch kept between classifications
+  size_t scratch_cap = 0;
   // solver hierarchies by precision mode (lazy)
   ibm::Hierarchy *hier[3] = {nullptr, nullptr, nullptr};
 };

@@ -31,6 +31,9 @@
 namespace ibm {
 
 constexpr int MAX_COARSE = 128;
+constexpr int PACK_BLOCKS = 1216;   // 8 x 152 SMs: grid of the row-group copy kernels
+constexpr int RESTRICT_BLOCKS = 1216;   // restriction blocks (at most; one partial sum each)
+constexpr size_t GJ_SMEM_MAX = 160 * 1024;   // coarsest Gauss-Jordan in shared memory up to this size
 
 namespace {
 
@@ -136,6 +139,20 @@ __global__ void k_mask_coarse(const uint8_t *mf, LevelGeom gf, uint8_t *mc, Leve
   mc[pidx(gc, I, J, K)] = m;
 }
 
+// inner[c] = 1 where cell c and its 26 neighbours (halo included) are all fluid
+__global__ void k_inner(const uint8_t *m, LevelGeom g, uint8_t *inner) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)g.nx * g.ny * g.nz) return;
+  int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
+  const long long c = pidx(g, i, j, k);
+  uint8_t ok = 1;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if (m[c + dz * g.sz + dy * g.sy + dx] != 0) ok = 0;
+  inner[c] = ok;
+}
+
 // area fraction of open fine faces on each +x/+y/+z coarse face.
 // Fine open fraction: level 0 from the mask (both sides fluid), else the fine fraction.
 template <typename T>
@@ -181,51 +198,39 @@ __global__ void k_fractions(const uint8_t *mf, const T *ffx, const T *ffy, const
   fx[ic] = (T)sx; fy[ic] = (T)sy; fz[ic] = (T)sz;
 }
 
-__global__ void k_fluid_stats(const uint8_t *mask, LevelGeom g, const double *dx, const double *dy,
-                              const double *dz, double *out) {
-  __shared__ double s[2][256];
-  double v = 0.0, c = 0.0;
-  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < (long long)g.nx * g.ny * g.nz;
-       l += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
-    if (mask[pidx(g, i, j, k)] == 0) { v += dx[i] * dy[j] * dz[k]; c += 1.0; }
-  }
-  s[0][threadIdx.x] = v; s[1][threadIdx.x] = c;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) { out[2 * blockIdx.x] = s[0][0]; out[2 * blockIdx.x + 1] = s[1][0]; }
-}
-
 // Coarsest level: gather fluid cells, assemble the bordered matrix [A 1; V'/vbar 0] and
-// invert it by Gauss-Jordan with partial pivoting (one block, setup only).
+// invert it by Gauss-Jordan with partial pivoting on [M | I] (one block; setup only).  The
+// elimination runs in the element type T of the hierarchy (the coarsest correction is an
+// inner-precision quantity), over all entries of the augmented matrix in parallel, in
+// shared memory when `gj` is null (else in the global work matrix gj).  Pivot ties go to
+// the lowest row, so the result is deterministic.
 template <typename T>
-__global__ void k_coarsest_setup(LV<T> v, int *cidx, int *ncount, double *M, double *Minv, int cap) {
-  __shared__ int n_s;
-  __shared__ int piv_s;
+__global__ void __launch_bounds__(1024) k_coarsest_setup(LV<T> v, int *cidx, int *ncount, T *Minv, T *gj, int cap) {
+  extern __shared__ __align__(16) unsigned char gj_smem[];
+  __shared__ int n_s, piv_s;
+  __shared__ T fac[MAX_COARSE + 1];
+  __shared__ double vbar_s;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
     int n = 0;
+    double vs = 0.0;
     for (int k = 0; k < v.nz; ++k) for (int j = 0; j < v.ny; ++j) for (int i = 0; i < v.nx; ++i) {
       long long id = vidx(v, i, j, k);
-      if (v.mask[id] == 0 && n < cap) cidx[n++] = (int)id;
+      if (v.mask[id] == 0 && n < cap) { cidx[n++] = (int)id; vs += v.dx[i] * v.dy[j] * v.dz[k]; }
     }
     n_s = n;
     *ncount = n;
+    vbar_s = vs / (n > 0 ? n : 1);
   }
   __syncthreads();
-  const int n = n_s, m = n + 1;
-  for (int q = tid; q < m * m; q += nt) { M[q] = 0.0; Minv[q] = (q / m == q % m) ? 1.0 : 0.0; }
-  __syncthreads();
-  double vbar = 0.0;
-  for (int q = 0; q < n; ++q) {
-    long long id = cidx[q];
-    int i = (int)(id % v.px) - OX; long long r = id / v.px; int j = (int)(r % (v.ny + 2)) - 1; int k = (int)(r / (v.ny + 2)) - 1;
-    vbar += v.dx[i] * v.dy[j] * v.dz[k];
+  const int n = n_s, m = n + 1, w = 2 * m;
+  T *A = gj ? gj : reinterpret_cast<T *>(gj_smem);
+  for (int q = tid; q < m * w; q += nt) {
+    const int r = q / w, c = q % w;
+    A[q] = (c - m == r) ? (T)1 : (T)0;
   }
-  vbar /= (n > 0 ? n : 1);
+  __syncthreads();
+  const double vbar = vbar_s;
   for (int q = tid; q < n; q += nt) {
     long long id = cidx[q];
     int i = (int)(id % v.px) - OX; long long r = id / v.px; int j = (int)(r % (v.ny + 2)) - 1; int k = (int)(r / (v.ny + 2)) - 1;
@@ -237,41 +242,75 @@ __global__ void k_coarsest_setup(LV<T> v, int *cidx, int *ncount, double *M, dou
       if (c[d] == (T)0) continue;
       diag -= (double)c[d];
       for (int s2 = 0; s2 < n; ++s2)
-        if (cidx[s2] == nb[d]) { M[q * m + s2] += (double)c[d]; break; }
+        if (cidx[s2] == nb[d]) { A[q * w + s2] += c[d]; break; }
     }
-    M[q * m + q] += diag;
-    M[q * m + n] = 1.0;
-    M[n * m + q] = v.dx[i] * v.dy[j] * v.dz[k] / vbar;
+    A[q * w + q] += (T)diag;
+    A[q * w + n] = (T)1;
+    A[n * w + q] = (T)(v.dx[i] * v.dy[j] * v.dz[k] / vbar);
   }
   __syncthreads();
   for (int col = 0; col < m; ++col) {
-    if (tid == 0) {
-      int p = col;
-      double best = fabs(M[col * m + col]);
-      for (int rr = col + 1; rr < m; ++rr)
-        if (fabs(M[rr * m + col]) > best) { best = fabs(M[rr * m + col]); p = rr; }
-      piv_s = p;
+    if (tid < 32) {   // pivot: largest |A[r][col]| over r >= col, lowest row on ties
+      T best = (T)-1;
+      int bi = col;
+      for (int r = col + tid; r < m; r += 32) {
+        const T a = A[r * w + col] < (T)0 ? -A[r * w + col] : A[r * w + col];
+        if (a > best) { best = a; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) piv_s = bi;
     }
     __syncthreads();
     const int p = piv_s;
     if (p != col)
-      for (int q = tid; q < m; q += nt) {
-        double a = M[col * m + q]; M[col * m + q] = M[p * m + q]; M[p * m + q] = a;
-        double b = Minv[col * m + q]; Minv[col * m + q] = Minv[p * m + q]; Minv[p * m + q] = b;
+      for (int q = tid; q < w; q += nt) {
+        const T a = A[col * w + q];
+        A[col * w + q] = A[p * w + q];
+        A[p * w + q] = a;
       }
     __syncthreads();
-    const double inv = 1.0 / M[col * m + col];
+    const T inv = (T)1 / A[col * w + col];
     __syncthreads();
-    for (int q = tid; q < m; q += nt) { M[col * m + q] *= inv; Minv[col * m + q] *= inv; }
+    for (int q = tid; q < w; q += nt) A[col * w + q] *= inv;
+    for (int r = tid; r < m; r += nt) fac[r] = r == col ? (T)0 : A[r * w + col];
     __syncthreads();
-    for (int rr = tid; rr < m; rr += nt) {
-      if (rr == col) continue;
-      double f = M[rr * m + col];
-      if (f == 0.0) continue;
-      for (int q = 0; q < m; ++q) { M[rr * m + q] -= f * M[col * m + q]; Minv[rr * m + q] -= f * Minv[col * m + q]; }
+    for (int q = tid; q < m * w; q += nt) {
+      const int r = q / w, c = q - r * w;
+      if (r != col) A[q] -= fac[r] * A[col * w + c];
     }
     __syncthreads();
   }
+  for (int q = tid; q < m * m; q += nt) Minv[q] = A[(q / m) * w + m + q % m];
+}
+
+// fluid volume and count of a level: row sums of dx over fluid cells (one FP64 add per
+// fluid cell), times dy dz per row; block partials (volume, count) at out[2 b], out[2 b + 1]
+__global__ void k_fluid_stats(const uint8_t *mask, LevelGeom g, const double *dx, const double *dy,
+                              const double *dz, double *out) {
+  __shared__ double s[2][256];
+  double v = 0.0, c = 0.0;
+  const int rows = g.ny * g.nz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % g.ny, k = row / g.ny;
+    const uint8_t *mr = mask + pidx(g, 0, j, k);
+    double sx = 0.0;
+    int cnt = 0;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
+      if (mr[i] == 0) { sx += dx[i]; ++cnt; }
+    v += sx * (dy[j] * dz[k]);
+    c += cnt;
+  }
+  s[0][threadIdx.x] = v; s[1][threadIdx.x] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[2 * blockIdx.x] = s[0][0]; out[2 * blockIdx.x + 1] = s[1][0]; }
 }
 
 // ------------------------------------------------------------------ solve kernels
@@ -297,10 +336,10 @@ __global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colou
 
 // ghost rows (Jacobi): gnew = sum_k w_k e[src_k] (+ rhs at the ghost cell)
 template <typename T, typename W>
-__global__ void k_ghost_eval(const long long *src, const long long *dst, const W *w, long long ng, const T *e,
-                             const T *rhs, T *gtmp) {
+__global__ void k_ghost_eval(const long long *src, const long long *dst, const W *w, long long ng,
+                             const long long *ngp, const T *e, const T *rhs, T *gtmp) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= ng) return;
+  if (g >= (ngp ? *ngp : ng)) return;
   T s = (T)0;
   for (int c = 0; c < 8; ++c) {
     long long q = src[8 * g + c];
@@ -314,10 +353,10 @@ __global__ void k_ghost_eval(const long long *src, const long long *dst, const W
 // array, ghost sources from the previous one (whose ghost values the sweep copied
 // unchanged), so no thread reads a value another thread writes (Jacobi among ghosts)
 template <typename T, typename W>
-__global__ void k_ghost_pp(const long long *src, const long long *dst, const W *w, long long ng, T *enew,
-                           const T *eold, const T *rhs) {
+__global__ void k_ghost_pp(const long long *src, const long long *dst, const W *w, long long ng,
+                           const long long *ngp, T *enew, const T *eold, const T *rhs) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= ng) return;
+  if (g >= (ngp ? *ngp : ng)) return;
   T s = (T)0;
   for (int c = 0; c < 8; ++c) {
     long long q = src[8 * g + c];
@@ -330,46 +369,107 @@ __global__ void k_ghost_pp(const long long *src, const long long *dst, const W *
 }
 
 template <typename T>
-__global__ void k_ghost_store(const long long *dst, long long ng, const T *gtmp, T *e) {
+__global__ void k_ghost_store(const long long *dst, long long ng, const long long *ngp, const T *gtmp, T *e) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g < ng) e[dst[g]] = gtmp[g];
+  if (g < (ngp ? *ngp : ng)) e[dst[g]] = gtmp[g];
 }
 
-// residual of level f restricted to level c: rc = sum_{fluid children} V_f r_f / V_c, and
-// block partial sums of V_c rc for the coarse projection
-template <typename T>
-__global__ void k_restrict(LV<T> f, const T *e, const T *r, const double *shift, LV<T> cv, T *rc, double *partials) {
-  __shared__ double sm[256];
-  double acc_all = 0.0;
-  const long long nc = (long long)cv.nx * cv.ny * cv.nz;
-  const T sh = shift ? (T)(*shift) : (T)0;
-  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nc; l += (long long)gridDim.x * blockDim.x) {
-    int I = (int)(l % cv.nx); long long q = l / cv.nx; int J = (int)(q % cv.ny); int K = (int)(q / cv.ny);
-    long long ic = vidx(cv, I, J, K);
-    if (cv.mask[ic] != 0) { rc[ic] = (T)0; continue; }
-    T acc = (T)0;
-    for (int c = 0; c < 8; ++c) {
-      int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
-      if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
-      long long id = vidx(f, i, j, k);
-      if (f.mask[id] != 0) continue;
-      T cf[6];
-      coefs(f, i, j, k, id, cf);
-      T D = f.sdx ? (f.sdx[i] + f.sdy[j]) + f.sdz[k] : ((cf[0] + cf[1]) + (cf[2] + cf[3])) + (cf[4] + cf[5]);
-      T res = (r[id] - sh) - (stencil_sum(f, e, id, cf) - D * e[id]);
-      acc += (f.wx[i] * f.wy[j]) * f.wz[k] * res;
-    }
-    T vc = (cv.wx[I] * cv.wy[J]) * cv.wz[K];
-    rc[ic] = acc / vc;
-    acc_all += (double)acc;
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  static __device__ __forceinline__ void ld(const float *p, float v[2]) {
+    const float2 a = *reinterpret_cast<const float2 *>(p);
+    v[0] = a.x; v[1] = a.y;
   }
+};
+template <> struct Pair<double> {
+  static __device__ __forceinline__ void ld(const double *p, double v[2]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    v[0] = a.x; v[1] = a.y;
+  }
+};
+
+// Restriction of the level-f residual to level c, one thread per coarse cell (I,J,K) with
+// coarse rows strided over blockIdx.y: rc = sum over the fluid children of V_f r_f / V_c,
+// with r_f = r - shift - (A e)_f; ec = 0 (the coarse correction starts from zero); block
+// partials of sum V_c rc at partials[blockIdx.y * gridDim.x + blockIdx.x].  Every load of a
+// coarse cell (the 2x2x2 children of e, r and mask and their 24 face neighbours) is issued
+// before the arithmetic; children past an odd fine extent are halo cells (mask 1) whose
+// outward neighbours are not read.
+template <typename T>
+__global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const T *e, const T *r, const double *shift, LV<T> cv,
+                                                   T *rc, T *ec, double *partials) {
+  __shared__ double sm[128];
+  double acc_all = 0.0;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const T sh = shift ? (T)(*shift) : (T)0;
+  const int crows = cv.ny * cv.nz;
+  if (I < cv.nx)
+    for (int row = blockIdx.y; row < crows; row += gridDim.y) {
+      const int J = row % cv.ny, K = row / cv.ny;
+      const long long ic = vidx(cv, I, J, K);
+      const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+      const bool vx1 = i0 + 1 < f.nx, vy1 = j0 + 1 < f.ny, vz1 = k0 + 1 < f.nz;
+      const long long fb = vidx(f, i0, j0, k0);
+      T E[2][2][2], R[2][2][2], XM[2][2], XP[2][2], YM[2][2], YP[2][2], ZM[2][2], ZP[2][2];
+      uchar2 M[2][2];
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const long long q = fb + d * f.sz + b * f.sy;
+          Pair<T>::ld(e + q, E[d][b]);
+          Pair<T>::ld(r + q, R[d][b]);
+          M[d][b] = *reinterpret_cast<const uchar2 *>(f.mask + q);
+          XM[d][b] = e[q - 1];
+          XP[d][b] = vx1 ? e[q + 2] : (T)0;
+        }
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          YM[d][a] = e[fb + d * f.sz - f.sy + a];
+          YP[d][a] = vy1 ? e[fb + d * f.sz + 2 * f.sy + a] : (T)0;
+        }
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          ZM[b][a] = e[fb - f.sz + b * f.sy + a];
+          ZP[b][a] = vz1 ? e[fb + 2 * f.sz + b * f.sy + a] : (T)0;
+        }
+      const bool cfl = cv.mask[ic] == 0;
+      T acc = (T)0;
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const uint8_t m = a ? M[d][b].y : M[d][b].x;
+            const int i = min(i0 + a, f.nx - 1), j = min(j0 + b, f.ny - 1), k = min(k0 + d, f.nz - 1);
+            const long long id = fb + d * f.sz + b * f.sy + a;
+            T c[6];
+            coefs(f, i, j, k, id, c);
+            const T D = f.sdx ? (f.sdx[i] + f.sdy[j]) + f.sdz[k] : ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+            const T xm = a ? E[d][b][0] : XM[d][b], xp = a ? XP[d][b] : E[d][b][1];
+            const T ym = b ? E[d][0][a] : YM[d][a], yp = b ? YP[d][a] : E[d][1][a];
+            const T zm = d ? E[0][b][a] : ZM[b][a], zp = d ? ZP[b][a] : E[1][b][a];
+            const T s = c[0] * xm + c[1] * xp + c[2] * ym + c[3] * yp + c[4] * zm + c[5] * zp;
+            const T res = (R[d][b][a] - sh) - (s - D * E[d][b][a]);
+            if (m == 0) acc += (f.wx[i] * f.wy[j]) * f.wz[k] * res;
+          }
+      const T vc = (cv.wx[I] * cv.wy[J]) * cv.wz[K];
+      rc[ic] = cfl ? acc / vc : (T)0;
+      ec[ic] = (T)0;
+      if (cfl) acc_all += (double)acc;
+    }
   sm[threadIdx.x] = acc_all;
   __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
+  for (int st = 64; st > 0; st >>= 1) {
     if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sm[0];
 }
 
 // deterministic sum of nb partials (stride `stride`, offset `off`) in one block
@@ -388,96 +488,183 @@ __device__ double block_sum_partials(const double *p, int nb, int stride, int of
   return out;
 }
 
-__global__ void k_finalize_shift(const double *partials, int nb, double fluid_vol, double *shift) {
+__global__ void k_finalize_shift(const double *partials, int nb, const double *fluid_vol, double *shift) {
   double s = block_sum_partials(partials, nb, 1, 0);
-  if (threadIdx.x == 0) *shift = fluid_vol > 0 ? s / fluid_vol : 0.0;
+  if (threadIdx.x == 0) *shift = *fluid_vol > 0 ? s / *fluid_vol : 0.0;
 }
 
+// Prolongation e_f += P e_c, one thread per coarse cell (I,J,K) and its 2x2x2 children.
+// Along each axis a child takes weight 1-t on its parent and t on the parent's neighbour
+// on the child's side (off = -1 or +1; t = 0 without one), so each child reads the 3x3x3
+// coarse block around (I,J,K).  Coarse e is zero on every non-fluid coarse cell (cleared
+// before the coarse cycle, written only on fluid rows), so the weighted sum needs no mask
+// and is contracted axis by axis; the renormalising denominator (sum of the weights of the
+// fluid corners) is 1 where the whole block is fluid (inner flag), else summed the same way
+// over the fluid indicator.  Children that are not fluid rows are left unchanged.
 template <typename T>
-__global__ void k_prolong(LV<T> cv, const T *ec, LV<T> f, T *ef, const int8_t *offx, const int8_t *offy,
-                          const int8_t *offz, const float *tx, const float *ty, const float *tz) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y, k = blockIdx.z;
-  if (i >= f.nx) return;
-  long long id = vidx(f, i, j, k);
-  if (f.mask[id] != 0) return;
-  int I = i >> 1, J = j >> 1, K = k >> 1;
-  float wx[2] = {1.0f - tx[i], tx[i]}, wy[2] = {1.0f - ty[j], ty[j]}, wz[2] = {1.0f - tz[k], tz[k]};
-  int ox = offx[i], oy = offy[j], oz = offz[k];
-  T s = (T)0;
-  float ws = 0.0f;
-  for (int c = 0; c < 8; ++c) {
-    int a = c & 1, b = (c >> 1) & 1, d = (c >> 2) & 1;
-    float w = (wx[a] * wy[b]) * wz[d];
-    if (w == 0.0f) continue;
-    long long ic = vidx(cv, I + a * ox, J + b * oy, K + d * oz);
-    if (cv.mask[ic] != 0) continue;
-    s += (T)w * ec[ic];
-    ws += w;
+__global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const uint8_t *inner, LV<T> f, T *ef,
+                                                  const int8_t *offx, const int8_t *offy, const int8_t *offz,
+                                                  const float *tx, const float *ty, const float *tz) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+  if (I >= cv.nx) return;
+  float wx[2][3], wy[2][3], wz[2][3];
+  auto axis = [](int c0, int nf, const int8_t *off, const float *t, float w[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const bool v = c0 + a < nf;
+      const int o = v ? off[c0 + a] : 0;
+      const float tt = v ? t[c0 + a] : 0.f;
+      w[a][0] = o < 0 ? tt : 0.f;
+      w[a][1] = 1.f - tt;
+      w[a][2] = o > 0 ? tt : 0.f;
+    }
+  };
+  axis(2 * I, f.nx, offx, tx, wx);
+  axis(2 * J, f.ny, offy, ty, wy);
+  axis(2 * K, f.nz, offz, tz, wz);
+  // children rows (d = z child, b = y child): padded index of child x = 2I; masks of the pair
+  long long fr[2][2];
+  uchar2 fm[2][2];
+  bool any = false;
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      fr[d][b] = vidx(f, 2 * I, 2 * J + b, 2 * K + d);
+      // rows past the fine extent (odd sizes) are halo rows: mask 1, never updated
+      fm[d][b] = *reinterpret_cast<const uchar2 *>(f.mask + fr[d][b]);
+      any |= fm[d][b].x == 0 || fm[d][b].y == 0;
+    }
+  if (!any) return;
+  const long long c0 = vidx(cv, I, J, K);
+  T e[3][3][3];
+#pragma unroll
+  for (int z = 0; z < 3; ++z)
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) e[z][y][x] = ec[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)];
+  // contract x, then y, then z
+  auto contract = [&](const T (&v)[3][3][3], T (&out)[2][2][2]) {
+    T vx[2][3][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y)
+          vx[a][z][y] = (T)wx[a][0] * v[z][y][0] + (T)wx[a][1] * v[z][y][1] + (T)wx[a][2] * v[z][y][2];
+    T vxy[2][2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int z = 0; z < 3; ++z)
+          vxy[a][b][z] = (T)wy[b][0] * vx[a][z][0] + (T)wy[b][1] * vx[a][z][1] + (T)wy[b][2] * vx[a][z][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int d = 0; d < 2; ++d)
+          out[d][b][a] = (T)wz[d][0] * vxy[a][b][0] + (T)wz[d][1] * vxy[a][b][1] + (T)wz[d][2] * vxy[a][b][2];
+  };
+  T num[2][2][2], den[2][2][2];
+  contract(e, num);
+  if (inner[c0]) {
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) den[d][b][a] = (T)1;
+  } else {
+    T m[3][3][3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+      for (int y = 0; y < 3; ++y)
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          m[z][y][x] = cv.mask[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)] == 0 ? (T)1 : (T)0;
+    contract(m, den);
   }
-  if (ws > 0.0f) ef[id] += s * (T)(1.0f / ws);
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      T *row = ef + fr[d][b];
+      T v0 = row[0], v1 = row[1];
+      if (fm[d][b].x == 0 && den[d][b][0] > (T)0) v0 += num[d][b][0] / den[d][b][0];
+      if (fm[d][b].y == 0 && den[d][b][1] > (T)0) v1 += num[d][b][1] / den[d][b][1];
+      if (fm[d][b].x == 0 || fm[d][b].y == 0) {
+        row[0] = v0;
+        row[1] = v1;
+      }
+    }
 }
 
 // bordered coarsest solve: [e; lambda] = Minv [r; 0]
 template <typename T>
-__global__ void k_coarsest(const double *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
-  __shared__ double rs[MAX_COARSE + 1];
+__global__ void k_coarsest(const T *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
+  __shared__ T rs[MAX_COARSE + 1];
   const int n = *ncount, m = n + 1;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = (double)r[cidx[q]];
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = r[cidx[q]];
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    double s = 0.0;
+    T s = (T)0;
     for (int c = 0; c < n; ++c) s += Minv[q * m + c] * rs[c];
-    e[cidx[q]] = (T)s;
+    e[cidx[q]] = s;
   }
 }
 
-// FP64 fine residual r = b - lambda - A p on fluid rows; optional FP32 copy; block partials
-// (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}].  FP64 arithmetic is kept to the
-// stencil itself (GB300 issues FP64 at 1/57 of the FP32 rate): the diagonal is separable,
-// row invariants are hoisted, and the norm/mean partial sums run in FP32 per thread.
-__global__ void k_residual64(LV<double> v, const double *p, const double *b, const double *lambda, float *r32,
-                             double *partials) {
-  __shared__ double sm[3][REDUCE_THREADS];
-  const double lam = *lambda;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
-  const long long rows = (long long)v.ny * v.nz;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int j = (int)(row % v.ny), k = (int)(row / v.ny);
-    const double cym = v.cym[j], cyp = v.cyp[j], czm = v.czm[k], czp = v.czp[k];
-    const double syz = v.sdy[j] + v.sdz[k];
-    const float dydz = (float)(v.dy[j] * v.dz[k]);
-    for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
-      long long id = vidx(v, i, j, k);
-      if (v.mask[id] != 0) continue;
-      if (p == nullptr) {            // residual of p = 0: b - lambda
-        const float rf0 = (float)(b[id] - lam);
-        if (r32) r32[id] = rf0;
-        a0 = fmaf((float)v.dx[i] * dydz, rf0, a0);
-        a1 += rf0;
-        a2 = fmaf(rf0, rf0, a2);
-        continue;
-      }
-      const double pc = p[id];
-      double s = v.cxm[i] * p[id - 1];
-      s = fma(v.cxp[i], p[id + 1], s);
-      s = fma(cym, p[id - v.sy], s);
-      s = fma(cyp, p[id + v.sy], s);
-      s = fma(czm, p[id - v.sz], s);
-      s = fma(czp, p[id + v.sz], s);
-      s = fma(-(v.sdx[i] + syz), pc, s);           // (A p)_i
-      const double res = (b[id] - lam) - s;
-      const float rf = (float)res;
-      if (r32) r32[id] = rf;
-      a0 = fmaf((float)v.dx[i] * dydz, rf, a0);
-      a1 += rf;
-      a2 = fmaf(rf, rf, a2);
-    }
-    // fold the FP32 row partials into FP64 every row (bounded FP32 error)
-    A0 += a0; A1 += a1; A2 += a2;
-    a0 = a1 = a2 = 0.f;
+// Fine-level cell kernels work on groups of four consecutive x-cells of a row (j,k): every
+// load of a group is issued before any result is needed (16-byte vector loads of the padded
+// arrays, aligned since rows start at OX = 4), so a thread keeps several cells' worth of
+// memory traffic in flight.  Cells past nx in the last group are halo or padding (mask 1).
+struct RowGroups {
+  int G, rpi, rsub, g0, gstep;   // groups per row, rows per block pass, this thread's row/group
+  __device__ explicit RowGroups(int nx) {
+    G = (nx + 3) >> 2;
+    const int bd = blockDim.x;
+    if (G >= bd) { rpi = 1; rsub = 0; g0 = threadIdx.x; gstep = bd; }
+    else { rpi = bd / G; rsub = threadIdx.x / G; g0 = threadIdx.x - rsub * G; gstep = G; }
   }
+  __device__ bool active() const { return rsub < rpi; }
+  __device__ int first_row() const { return blockIdx.x * rpi + rsub; }
+  __device__ int row_step() const { return gridDim.x * rpi; }
+};
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  static __device__ __forceinline__ void ld(const float *p, float v[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  static __device__ __forceinline__ void st(float *p, const float v[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Vec4<double> {
+  static __device__ __forceinline__ void ld(const double *p, double v[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  static __device__ __forceinline__ void st(double *p, const double v[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+__device__ __forceinline__ void ld_mask4(const uint8_t *m, bool fl[4]) {
+  const uchar4 q = *reinterpret_cast<const uchar4 *>(m);
+  fl[0] = q.x == 0; fl[1] = q.y == 0; fl[2] = q.z == 0; fl[3] = q.w == 0;
+}
+
+// block reduction of three doubles into partials[3 b + q]
+__device__ __forceinline__ void block_partials3(double A0, double A1, double A2, double *partials) {
+  __shared__ double sm[3][REDUCE_THREADS];
   sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
   __syncthreads();
   for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
@@ -489,11 +676,82 @@ __global__ void k_residual64(LV<double> v, const double *p, const double *b, con
     for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sm[q][0];
 }
 
+// FP64 fine residual r = b - lambda - A p on fluid rows; FP32 copy (0 on other cells);
+// block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}].  FP64 arithmetic is
+// kept to the stencil itself (GB300 issues FP64 at about 1/64 of the FP32 rate): the
+// diagonal is separable, row invariants are hoisted, the volume weights (wf: float widths
+// dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64 every 8 rows.
+__global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
+                                                              const double *lambda, const float *wf, float *r32,
+                                                              double *partials) {
+  const double lam = *lambda;
+  const int nx = v.nx, ny = v.ny;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  int nrow = 0;
+  const RowGroups rg(nx);
+  const int rows = ny * v.nz;
+  if (rg.active())
+    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+      const int j = row % ny, k = row / ny;
+      const double cym = v.cym[j], cyp = v.cyp[j], czm = v.czm[k], czp = v.czp[k];
+      const double syz = v.sdy[j] + v.sdz[k];
+      const float dydz = wf[nx + j] * wf[nx + ny + k];
+      const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      for (int g = rg.g0; g < rg.G; g += rg.gstep) {
+        const long long id = base + 4 * g;
+        bool fl[4];
+        ld_mask4(v.mask + id, fl);
+        double B[4], P[4], YM[4], YP[4], ZM[4], ZP[4], xl = 0.0, xr = 0.0;
+        Vec4<double>::ld(b + id, B);
+        if (p) {
+          Vec4<double>::ld(p + id, P);
+          Vec4<double>::ld(p + id - v.sy, YM);
+          Vec4<double>::ld(p + id + v.sy, YP);
+          Vec4<double>::ld(p + id - v.sz, ZM);
+          Vec4<double>::ld(p + id + v.sz, ZP);
+          xl = p[id - 1];
+          xr = p[id + 4];
+        }
+        float rf[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = min(4 * g + u, nx - 1);   // coefficients of cells past nx: any valid index
+          double res = B[u] - lam;
+          if (p) {
+            const double left = u == 0 ? xl : P[u - 1], right = u == 3 ? xr : P[u + 1];
+            double s = v.cxm[i] * left;
+            s = fma(v.cxp[i], right, s);
+            s = fma(cym, YM[u], s);
+            s = fma(cyp, YP[u], s);
+            s = fma(czm, ZM[u], s);
+            s = fma(czp, ZP[u], s);
+            s = fma(-(v.sdx[i] + syz), P[u], s);   // (A p)_i
+            res -= s;
+          }
+          rf[u] = fl[u] ? (float)res : 0.f;
+          a0 = fmaf(wf[i] * dydz, rf[u], a0);
+          a1 += rf[u];
+          a2 = fmaf(rf[u], rf[u], a2);
+        }
+        if (r32) Vec4<float>::st(r32 + id, rf);
+      }
+      if (++nrow == 8) {
+        A0 += a0; A1 += a1; A2 += a2;
+        a0 = a1 = a2 = 0.f;
+        nrow = 0;
+      }
+    }
+  A0 += a0; A1 += a1; A2 += a2;
+  block_partials3(A0, A1, A2, partials);
+}
+
 // ghost rows r_G = sum w v - g; block partials of (s_G r_G)^2 at gpart[b]
 __global__ void k_ghost_resid64(const long long *src, const long long *dst, const double *w, const double *scale,
-                                long long ng, const double *p, float *r32, double *gpart) {
+                                const long long *ngp, const double *p, float *r32, double *gpart) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
+  const long long ng = *ngp;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < 8; ++c) {
@@ -536,17 +794,28 @@ __global__ void k_update_p(double *p, const float *e, long long n) {
     p[q] += (double)e[q];
 }
 
-__global__ void k_gauge_sum(LV<double> v, const double *p, double *partials) {
+__global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum(LV<double> v, const double *p, double *partials) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
-  const long long rows = (long long)v.ny * v.nz;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    int j = (int)(row % v.ny), k = (int)(row / v.ny);
-    for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
-      long long id = vidx(v, i, j, k);
-      if (v.mask[id] == 0) a += v.dx[i] * v.dy[j] * v.dz[k] * p[id];
+  const int nx = v.nx, ny = v.ny;
+  const RowGroups rg(nx);
+  const int rows = ny * v.nz;
+  if (rg.active())
+    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+      const int j = row % ny, k = row / ny;
+      const double dydz = v.dy[j] * v.dz[k];
+      const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      for (int g = rg.g0; g < rg.G; g += rg.gstep) {
+        const long long id = base + 4 * g;
+        bool fl[4];
+        ld_mask4(v.mask + id, fl);
+        double P[4];
+        Vec4<double>::ld(p + id, P);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (fl[u]) a = fma(v.dx[min(4 * g + u, nx - 1)] * dydz, P[u], a);
+      }
     }
-  }
   sm[threadIdx.x] = a;
   __syncthreads();
   for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
@@ -561,27 +830,54 @@ __global__ void k_gauge_finalize(const double *partials, int nb, double *scal) {
   if (threadIdx.x == 0) scal[S_MEANP] = s / scal[S_FLUIDVOL];
 }
 
-// pack user [k][j][i] arrays into padded arrays; unpack with the gauge applied
-__global__ void k_pack(const double *src, LevelGeom g, double *dst) {
-  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= (long long)g.nx * g.ny * g.nz) return;
-  int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
-  dst[pidx(g, i, j, k)] = src[l];
+// pack a user [k][j][i] array into a padded array (cells past nx in the last group get 0);
+// cells with mask == 1 (plain solid) are set to zero when mask is given
+__global__ void k_pack(const double *src, LevelGeom g, double *dst, const uint8_t *mask) {
+  const RowGroups rg(g.nx);
+  const int rows = g.ny * g.nz;
+  if (!rg.active()) return;
+  for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+    const int j = row % g.ny, k = row / g.ny;
+    const long long q0 = (long long)row * g.nx;
+    const long long base = (long long)(k + 1) * g.sz + (long long)(j + 1) * g.sy + OX;
+    for (int gr = rg.g0; gr < rg.G; gr += rg.gstep) {
+      const long long id = base + 4 * gr;
+      bool fl[4] = {true, true, true, true};
+      if (mask) {
+        const uchar4 m = *reinterpret_cast<const uchar4 *>(mask + id);
+        fl[0] = m.x != 1; fl[1] = m.y != 1; fl[2] = m.z != 1; fl[3] = m.w != 1;
+      }
+      double V[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) V[u] = (4 * gr + u < g.nx && fl[u]) ? src[q0 + 4 * gr + u] : 0.0;
+      Vec4<double>::st(dst + id, V);
+    }
+  }
 }
 
+// unpack with the gauge applied: dst = p - mean on active cells, 0 on plain solid cells
 __global__ void k_unpack_gauge(const double *src, const uint8_t *mask, LevelGeom g, const double *scal, double *dst) {
-  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= (long long)g.nx * g.ny * g.nz) return;
-  int i = (int)(l % g.nx); long long r = l / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
-  long long id = pidx(g, i, j, k);
-  dst[l] = mask[id] == 1 ? 0.0 : src[id] - scal[S_MEANP];
+  const RowGroups rg(g.nx);
+  const int rows = g.ny * g.nz;
+  if (!rg.active()) return;
+  const double mean = scal[S_MEANP];
+  for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+    const int j = row % g.ny, k = row / g.ny;
+    const long long q0 = (long long)row * g.nx;
+    const long long base = (long long)(k + 1) * g.sz + (long long)(j + 1) * g.sy + OX;
+    for (int gr = rg.g0; gr < rg.G; gr += rg.gstep) {
+      const long long id = base + 4 * gr;
+      const uchar4 m = *reinterpret_cast<const uchar4 *>(mask + id);
+      const uint8_t mv[4] = {m.x, m.y, m.z, m.w};
+      double P[4];
+      Vec4<double>::ld(src + id, P);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * gr + u < g.nx) dst[q0 + 4 * gr + u] = mv[u] == 1 ? 0.0 : P[u] - mean;
+    }
+  }
 }
 
-// mask solid cells of the packed p to zero (they are never read, keep them finite)
-__global__ void k_zero_solid(double *p, const uint8_t *mask, long long n) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-    if (mask[q] == 1) p[q] = 0.0;
-}
 
 // ------------------------------------------------------------------ double-FP32 outer loop
 
@@ -600,13 +896,12 @@ __global__ void k_split_df(const double *src, int n, float *h, float *l) {
   if (q < n) dfl::split(src[q], h[q], l[q]);
 }
 
-// r = b - lambda - A p on fluid rows with pairs of floats (see dfloat.cuh); FP32 copy of r;
-// block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}] as k_residual64.
-// ph == nullptr: residual of p = 0.
+// r = b - lambda - A p on fluid rows with pairs of floats (see dfloat.cuh); FP32 copy of r
+// (0 on other cells); block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}] as
+// k_residual64.  ph == nullptr: residual of p = 0.
 __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const float *ph, const float *pl,
                                                                const float *bh, const float *bl,
                                                                const double *lambda, float *r32, double *partials) {
-  __shared__ double sm[3][REDUCE_THREADS];
   float lh, ll;
   dfl::split(*lambda, lh, ll);
   const int nx = v.nx, ny = v.ny, nz = v.nz, n = nx + ny + nz;
@@ -614,65 +909,81 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const 
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   double A0 = 0.0, A1 = 0.0, A2 = 0.0;
   int nrow = 0;
-  const long long rows = (long long)ny * nz;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int j = (int)(row % ny), k = (int)(row / ny);
-    const float cymh = H[2 * nx + j], cyml = L[2 * nx + j], cyph = H[2 * nx + ny + j], cypl = L[2 * nx + ny + j];
-    const float czmh = H[2 * nx + 2 * ny + k], czml = L[2 * nx + 2 * ny + k];
-    const float czph = H[2 * nx + 2 * ny + nz + k], czpl = L[2 * nx + 2 * ny + nz + k];
-    float syh, syl;   // sdy_j + sdz_k
-    dfl::two_sum(H[2 * n + nx + j], H[2 * n + nx + ny + k], syh, syl);
-    syl += L[2 * n + nx + j] + L[2 * n + nx + ny + k];
-    const float dydz = H[3 * n + nx + j] * H[3 * n + nx + ny + k];
-    const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const long long id = base + i;
-      if (v.mask[id] != 0) continue;
-      float sh, sl;
-      dfl::two_sum(bh[id], -lh, sh, sl);
-      sl += bl[id] - ll;
-      if (ph) {
-        float dh, dl;   // diagonal sdx_i + sdy_j + sdz_k
-        dfl::two_sum(H[2 * n + i], syh, dh, dl);
-        dl += L[2 * n + i] + syl;
-        dfl::acc_prod(dh, dl, ph[id], pl[id], sh, sl);
-        dfl::acc_prod(-H[i], -L[i], ph[id - 1], pl[id - 1], sh, sl);
-        dfl::acc_prod(-H[nx + i], -L[nx + i], ph[id + 1], pl[id + 1], sh, sl);
-        dfl::acc_prod(-cymh, -cyml, ph[id - v.sy], pl[id - v.sy], sh, sl);
-        dfl::acc_prod(-cyph, -cypl, ph[id + v.sy], pl[id + v.sy], sh, sl);
-        dfl::acc_prod(-czmh, -czml, ph[id - v.sz], pl[id - v.sz], sh, sl);
-        dfl::acc_prod(-czph, -czpl, ph[id + v.sz], pl[id + v.sz], sh, sl);
+  const RowGroups rg(nx);
+  const int rows = ny * nz;
+  if (rg.active())
+    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+      const int j = row % ny, k = row / ny;
+      const float cymh = H[2 * nx + j], cyml = L[2 * nx + j], cyph = H[2 * nx + ny + j], cypl = L[2 * nx + ny + j];
+      const float czmh = H[2 * nx + 2 * ny + k], czml = L[2 * nx + 2 * ny + k];
+      const float czph = H[2 * nx + 2 * ny + nz + k], czpl = L[2 * nx + 2 * ny + nz + k];
+      float syh, syl;   // sdy_j + sdz_k
+      dfl::two_sum(H[2 * n + nx + j], H[2 * n + nx + ny + k], syh, syl);
+      syl += L[2 * n + nx + j] + L[2 * n + nx + ny + k];
+      const float dydz = H[3 * n + nx + j] * H[3 * n + nx + ny + k];
+      const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      for (int g = rg.g0; g < rg.G; g += rg.gstep) {
+        const long long id = base + 4 * g;
+        bool fl[4];
+        ld_mask4(v.mask + id, fl);
+        float BH[4], BL[4];
+        Vec4<float>::ld(bh + id, BH);
+        Vec4<float>::ld(bl + id, BL);
+        float PH[4], PL[4], YMH[4], YML[4], YPH[4], YPL[4], ZMH[4], ZML[4], ZPH[4], ZPL[4];
+        float xlh = 0.f, xll = 0.f, xrh = 0.f, xrl = 0.f;
+        if (ph) {
+          Vec4<float>::ld(ph + id, PH);          Vec4<float>::ld(pl + id, PL);
+          Vec4<float>::ld(ph + id - v.sy, YMH);  Vec4<float>::ld(pl + id - v.sy, YML);
+          Vec4<float>::ld(ph + id + v.sy, YPH);  Vec4<float>::ld(pl + id + v.sy, YPL);
+          Vec4<float>::ld(ph + id - v.sz, ZMH);  Vec4<float>::ld(pl + id - v.sz, ZML);
+          Vec4<float>::ld(ph + id + v.sz, ZPH);  Vec4<float>::ld(pl + id + v.sz, ZPL);
+          xlh = ph[id - 1]; xll = pl[id - 1]; xrh = ph[id + 4]; xrl = pl[id + 4];
+        }
+        float rf[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = min(4 * g + u, nx - 1);   // coefficients of cells past nx: any valid index
+          float sh, sl;
+          dfl::two_sum(BH[u], -lh, sh, sl);
+          sl += BL[u] - ll;
+          if (ph) {
+            float dh, dl;   // diagonal sdx_i + sdy_j + sdz_k
+            dfl::two_sum(H[2 * n + i], syh, dh, dl);
+            dl += L[2 * n + i] + syl;
+            dfl::acc_prod(dh, dl, PH[u], PL[u], sh, sl);
+            const float lfh = u == 0 ? xlh : PH[u - 1], lfl = u == 0 ? xll : PL[u - 1];
+            const float rgh = u == 3 ? xrh : PH[u + 1], rgl = u == 3 ? xrl : PL[u + 1];
+            dfl::acc_prod(-H[i], -L[i], lfh, lfl, sh, sl);
+            dfl::acc_prod(-H[nx + i], -L[nx + i], rgh, rgl, sh, sl);
+            dfl::acc_prod(-cymh, -cyml, YMH[u], YML[u], sh, sl);
+            dfl::acc_prod(-cyph, -cypl, YPH[u], YPL[u], sh, sl);
+            dfl::acc_prod(-czmh, -czml, ZMH[u], ZML[u], sh, sl);
+            dfl::acc_prod(-czph, -czpl, ZPH[u], ZPL[u], sh, sl);
+          }
+          rf[u] = fl[u] ? sh + sl : 0.f;
+          a0 = fmaf(H[3 * n + i] * dydz, rf[u], a0);
+          a1 += rf[u];
+          a2 = fmaf(rf[u], rf[u], a2);
+        }
+        if (r32) Vec4<float>::st(r32 + id, rf);
       }
-      const float rf = sh + sl;
-      if (r32) r32[id] = rf;
-      a0 = fmaf(H[3 * n + i] * dydz, rf, a0);
-      a1 += rf;
-      a2 = fmaf(rf, rf, a2);
+      // fold the FP32 partials into FP64 every 8 rows (bounded FP32 error)
+      if (++nrow == 8) {
+        A0 += a0; A1 += a1; A2 += a2;
+        a0 = a1 = a2 = 0.f;
+        nrow = 0;
+      }
     }
-    // fold the FP32 partials into FP64 every 8 rows (bounded FP32 error)
-    if (++nrow == 8) {
-      A0 += a0; A1 += a1; A2 += a2;
-      a0 = a1 = a2 = 0.f;
-      nrow = 0;
-    }
-  }
   A0 += a0; A1 += a1; A2 += a2;
-  sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
-  __syncthreads();
-  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st)
-      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + st];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sm[q][0];
+  block_partials3(A0, A1, A2, partials);
 }
 
 // ghost rows r_G = sum w v - g in FP64 from the split values; block partials of (s_G r_G)^2
 __global__ void k_ghost_resid_df(const long long *src, const long long *dst, const double *w, const double *scale,
-                                 long long ng, const float *ph, const float *pl, float *r32, double *gpart) {
+                                 const long long *ngp, const float *ph, const float *pl, float *r32, double *gpart) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
+  const long long ng = *ngp;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < 8; ++c) {
@@ -737,18 +1048,33 @@ __global__ void k_update_df(float4 *ph, float4 *pl, const float4 *e, long long n
   }
 }
 
-// pack a user [k][j][i] array into split padded arrays; cells with mask == 1 (plain solid)
-// are set to zero when mask is given
+// pack a user [k][j][i] array into split padded arrays (cells past nx in the last group
+// get 0); cells with mask == 1 (plain solid) are set to zero when mask is given
 __global__ void k_pack_df(const double *src, LevelGeom g, float *dh, float *dl, const uint8_t *mask) {
-  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)g.nx * g.ny * g.nz) return;
-  int i = (int)(q % g.nx); long long r = q / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
-  const long long id = pidx(g, i, j, k);
-  float h, l;
-  dfl::split(src[q], h, l);
-  if (mask && mask[id] == 1) h = l = 0.f;
-  dh[id] = h;
-  dl[id] = l;
+  const RowGroups rg(g.nx);
+  const int rows = g.ny * g.nz;
+  if (!rg.active()) return;
+  for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+    const int j = row % g.ny, k = row / g.ny;
+    const long long q0 = (long long)row * g.nx;
+    const long long base = (long long)(k + 1) * g.sz + (long long)(j + 1) * g.sy + OX;
+    for (int gr = rg.g0; gr < rg.G; gr += rg.gstep) {
+      const long long id = base + 4 * gr;
+      bool fl[4] = {true, true, true, true};
+      if (mask) {
+        const uchar4 m = *reinterpret_cast<const uchar4 *>(mask + id);
+        fl[0] = m.x != 1; fl[1] = m.y != 1; fl[2] = m.z != 1; fl[3] = m.w != 1;
+      }
+      double V[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) V[u] = (4 * gr + u < g.nx && fl[u]) ? src[q0 + 4 * gr + u] : 0.0;
+      float H[4], L[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dfl::split(V[u], H[u], L[u]);
+      Vec4<float>::st(dh + id, H);
+      Vec4<float>::st(dl + id, L);
+    }
+  }
 }
 
 // block partials of sum V p over fluid cells; V and the products as pairs of floats
@@ -758,22 +1084,32 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum_df(DfView v, const
   const int nx = v.nx, ny = v.ny, n = nx + ny + v.nz;
   const float *H = v.h + 3 * n, *L = v.l + 3 * n;   // widths
   float sh = 0.f, sl = 0.f;
-  const long long rows = (long long)ny * v.nz;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int j = (int)(row % ny), k = (int)(row / ny);
-    float ah = 0.f, al = 0.f, yzh, yzl;   // dy_j dz_k
-    dfl::acc_prod(H[nx + j], L[nx + j], H[nx + ny + k], L[nx + ny + k], ah, al);
-    dfl::fast_two_sum(ah, al, yzh, yzl);
-    const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const long long id = base + i;
-      if (v.mask[id] != 0) continue;
-      float vh = 0.f, vl = 0.f, Vh, Vl;
-      dfl::acc_prod(H[i], L[i], yzh, yzl, vh, vl);
-      dfl::fast_two_sum(vh, vl, Vh, Vl);
-      dfl::acc_prod(Vh, Vl, ph[id], pl[id], sh, sl);
+  const RowGroups rg(nx);
+  const int rows = ny * v.nz;
+  if (rg.active())
+    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+      const int j = row % ny, k = row / ny;
+      float ah = 0.f, al = 0.f, yzh, yzl;   // dy_j dz_k
+      dfl::acc_prod(H[nx + j], L[nx + j], H[nx + ny + k], L[nx + ny + k], ah, al);
+      dfl::fast_two_sum(ah, al, yzh, yzl);
+      const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      for (int g = rg.g0; g < rg.G; g += rg.gstep) {
+        const long long id = base + 4 * g;
+        bool fl[4];
+        ld_mask4(v.mask + id, fl);
+        float PH[4], PL[4];
+        Vec4<float>::ld(ph + id, PH);
+        Vec4<float>::ld(pl + id, PL);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = min(4 * g + u, nx - 1);
+          float vh = 0.f, vl = 0.f, Vh, Vl;
+          dfl::acc_prod(H[i], L[i], yzh, yzl, vh, vl);
+          dfl::fast_two_sum(vh, vl, Vh, Vl);
+          if (fl[u]) dfl::acc_prod(Vh, Vl, PH[u], PL[u], sh, sl);
+        }
+      }
     }
-  }
   sm[threadIdx.x] = dfl::join(sh, sl);
   __syncthreads();
   for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
@@ -783,20 +1119,34 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum_df(DfView v, const
   if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
 }
 
-// (grid-stride: the mean is split once per thread)
+// unpack with the gauge applied (p - mean in pairs of floats, then one FP64 add per cell)
 __global__ void k_unpack_gauge_df(const float *ph, const float *pl, const uint8_t *mask, LevelGeom g,
                                   const double *scal, double *dst) {
+  const RowGroups rg(g.nx);
+  const int rows = g.ny * g.nz;
+  if (!rg.active()) return;
   float mh, ml;
   dfl::split(scal[S_MEANP], mh, ml);
-  const long long n = (long long)g.nx * g.ny * g.nz;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(q % g.nx); long long r = q / g.nx; int j = (int)(r % g.ny); int k = (int)(r / g.ny);
-    const long long id = pidx(g, i, j, k);
-    if (mask[id] == 1) { dst[q] = 0.0; continue; }
-    float s, t;
-    dfl::two_sum(ph[id], -mh, s, t);
-    t += pl[id] - ml;
-    dst[q] = dfl::join(s, t);
+  for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+    const int j = row % g.ny, k = row / g.ny;
+    const long long q0 = (long long)row * g.nx;
+    const long long base = (long long)(k + 1) * g.sz + (long long)(j + 1) * g.sy + OX;
+    for (int gr = rg.g0; gr < rg.G; gr += rg.gstep) {
+      const long long id = base + 4 * gr;
+      const uchar4 m = *reinterpret_cast<const uchar4 *>(mask + id);
+      const uint8_t mv[4] = {m.x, m.y, m.z, m.w};
+      float PH[4], PL[4];
+      Vec4<float>::ld(ph + id, PH);
+      Vec4<float>::ld(pl + id, PL);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (4 * gr + u >= g.nx) continue;
+        float s, t;
+        dfl::two_sum(PH[u], -mh, s, t);
+        t += PL[u] - ml;
+        dst[q0 + 4 * gr + u] = mv[u] == 1 ? 0.0 : dfl::join(s, t);
+      }
+    }
   }
 }
 
@@ -827,12 +1177,12 @@ void free_hierarchy(Hierarchy *h) {
   if (!h) return;
   std::vector<void *> ps;
   for (Level &L : h->lv) {
-    void *q[] = {L.mask, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt, L.wT, L.sdiag};
-    ps.insert(ps.end(), q, q + 13);
+    void *q[] = {L.mask, L.inner, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt, L.wT, L.sdiag};
+    ps.insert(ps.end(), q, q + 14);
   }
-  void *q[] = {h->p64, h->b64, h->minv, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64, h->gw32,
-               h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1]};
-  ps.insert(ps.end(), q, q + 15);
+  void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
+               h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng};
+  ps.insert(ps.end(), q, q + 18);
   std::sort(ps.begin(), ps.end());
   ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
   for (void *p : ps) if (p) cudaFree(p);
@@ -889,19 +1239,48 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
     h->zmarch = false;
 }
 
+// Grid-only part of a hierarchy: every allocation, the level geometry, coefficients,
+// prolongation tables and the fused-sweep tensor maps.  Nothing here depends on the bodies.
 template <typename T>
-static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) {
+static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) {
   Hierarchy *h = new Hierarchy();
   h->elem = sizeof(T);
   auto fail = [&](cudaError_t e, const char *w) { free_hierarchy(h); return check(e, w); };
 #define HTRY(call) do { cudaError_t e__ = (call); if (e__ != cudaSuccess) return fail(e__, #call); } while (0)
-  std::vector<double> fx(t->xf), fy(t->yf), fz(t->zf);
-  double *dfaces = nullptr;
+  // level faces on the host, then one device copy of all of them
+  std::vector<std::vector<double>> F[3];
+  F[0].push_back(t->xf); F[1].push_back(t->yf); F[2].push_back(t->zf);
+  auto coarsen = [](const std::vector<double> &f) {
+    int n = (int)f.size() - 1, nc = (n + 1) / 2;
+    std::vector<double> c(nc + 1);
+    for (int I = 0; I < nc; ++I) c[I] = f[2 * I];
+    c[nc] = f[n];
+    return c;
+  };
   while (true) {
+    const std::vector<double> &fx = F[0].back(), &fy = F[1].back(), &fz = F[2].back();
+    const long long cells = (long long)(fx.size() - 1) * (fy.size() - 1) * (fz.size() - 1);
+    if (cells <= MAX_COARSE || (fx.size() == 2 && fy.size() == 2 && fz.size() == 2)) break;
+    F[0].push_back(coarsen(fx)); F[1].push_back(coarsen(fy)); F[2].push_back(coarsen(fz));
+  }
+  const int nl = (int)F[0].size();
+  std::vector<double> hfaces;
+  std::vector<size_t> foff(nl);
+  for (int l = 0; l < nl; ++l) {
+    foff[l] = hfaces.size();
+    for (int a = 0; a < 3; ++a) hfaces.insert(hfaces.end(), F[a][l].begin(), F[a][l].end());
+  }
+  double *dfaces = nullptr;
+  HTRY(cudaMalloc((void **)&dfaces, sizeof(double) * hfaces.size()));
+  auto free_faces = [&]() { if (dfaces) { cudaStreamSynchronize(st); cudaFree(dfaces); dfaces = nullptr; } };
+#undef HTRY
+#define HTRY(call) do { cudaError_t e__ = (call); if (e__ != cudaSuccess) { free_faces(); return fail(e__, #call); } } while (0)
+  HTRY(cudaMemcpyAsync(dfaces, hfaces.data(), sizeof(double) * hfaces.size(), cudaMemcpyHostToDevice, st));
+  for (int l = 0; l < nl; ++l) {
     Level L;
-    L.g = make_geom((int)fx.size() - 1, (int)fy.size() - 1, (int)fz.size() - 1);
+    L.g = make_geom((int)F[0][l].size() - 1, (int)F[1][l].size() - 1, (int)F[2][l].size() - 1);
     const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
-    HTRY(alloc_zero<uint8_t>((void **)&L.mask, L.g.ntot, st));
+    HTRY(cudaMalloc((void **)&L.mask, L.g.ntot));
     HTRY(cudaMemsetAsync(L.mask, 1, L.g.ntot, st));
     HTRY(alloc_zero<T>(&L.e, L.g.ntot, st));
     HTRY(alloc_zero<T>(&L.r, L.g.ntot, st));
@@ -909,114 +1288,56 @@ static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **
     HTRY(cudaMalloc((void **)&L.w1d, sizeof(double) * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.cen, sizeof(double) * (nx + ny + nz)));
     HTRY(cudaMalloc(&L.wT, sizeof(T) * (nx + ny + nz)));
-    const bool finest = h->lv.empty();
-    if (finest) HTRY(cudaMalloc(&L.sdiag, sizeof(T) * (nx + ny + nz)));
-    HTRY(cudaMalloc((void **)&dfaces, sizeof(double) * (nx + ny + nz + 3)));
-    HTRY(cudaMemcpyAsync(dfaces, fx.data(), sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, st));
-    HTRY(cudaMemcpyAsync(dfaces + nx + 1, fy.data(), sizeof(double) * (ny + 1), cudaMemcpyHostToDevice, st));
-    HTRY(cudaMemcpyAsync(dfaces + nx + ny + 2, fz.data(), sizeof(double) * (nz + 1), cudaMemcpyHostToDevice, st));
-    T *c = (T *)L.c1d, *wt = (T *)L.wT, *sd = (T *)L.sdiag;
-    k_axis_level<T><<<nblk(nx, 128), 128, 0, st>>>(dfaces, nx, c, c + nx, L.w1d, L.cen, wt, sd);
-    k_axis_level<T><<<nblk(ny, 128), 128, 0, st>>>(dfaces + nx + 1, ny, c + 2 * nx, c + 2 * nx + ny, L.w1d + nx,
-                                                    L.cen + nx, wt + nx, sd ? sd + nx : nullptr);
-    k_axis_level<T><<<nblk(nz, 128), 128, 0, st>>>(dfaces + nx + ny + 2, nz, c + 2 * nx + 2 * ny,
-                                                    c + 2 * nx + 2 * ny + nz, L.w1d + nx + ny, L.cen + nx + ny,
+    if (l == 0) HTRY(cudaMalloc(&L.sdiag, sizeof(T) * (nx + ny + nz)));
+    h->lv.push_back(L);
+    Level &Lr = h->lv.back();
+    const double *df = dfaces + foff[l];
+    T *c = (T *)Lr.c1d, *wt = (T *)Lr.wT, *sd = (T *)Lr.sdiag;
+    k_axis_level<T><<<nblk(nx, 128), 128, 0, st>>>(df, nx, c, c + nx, Lr.w1d, Lr.cen, wt, sd);
+    k_axis_level<T><<<nblk(ny, 128), 128, 0, st>>>(df + nx + 1, ny, c + 2 * nx, c + 2 * nx + ny, Lr.w1d + nx,
+                                                    Lr.cen + nx, wt + nx, sd ? sd + nx : nullptr);
+    k_axis_level<T><<<nblk(nz, 128), 128, 0, st>>>(df + nx + ny + 2, nz, c + 2 * nx + 2 * ny,
+                                                    c + 2 * nx + 2 * ny + nz, Lr.w1d + nx + ny, Lr.cen + nx + ny,
                                                     wt + nx + ny, sd ? sd + nx + ny : nullptr);
     HTRY(cudaGetLastError());
-    HTRY(cudaStreamSynchronize(st));
-    cudaFree(dfaces);
-    dfaces = nullptr;
-    h->lv.push_back(L);
-    const long long cells = (long long)nx * ny * nz;
-    if (cells <= MAX_COARSE || (nx == 1 && ny == 1 && nz == 1)) break;
-    auto coarsen = [](const std::vector<double> &f) {
-      int n = (int)f.size() - 1, nc = (n + 1) / 2;
-      std::vector<double> c(nc + 1);
-      for (int I = 0; I < nc; ++I) c[I] = f[2 * I];
-      c[nc] = f[n];
-      return c;
-    };
-    fx = coarsen(fx); fy = coarsen(fy); fz = coarsen(fz);
-  }
-  const int nl = (int)h->lv.size();
-  // masks, fractions, prolongation tables
-  {
-    Level &L0 = h->lv[0];
-    const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
-    k_mask0<<<nblk(n0, 256), 256, 0, st>>>(t->iblank, L0.g.nx, L0.g.ny, L0.g.nz, L0.mask, L0.g);
   }
   for (int l = 0; l + 1 < nl; ++l) {
-    Level &F = h->lv[l], &C = h->lv[l + 1];
-    const long long nc = (long long)C.g.nx * C.g.ny * C.g.nz;
-    k_mask_coarse<<<nblk(nc, 256), 256, 0, st>>>(F.mask, F.g, C.mask, C.g);
+    Level &Fl = h->lv[l], &C = h->lv[l + 1];
+    HTRY(alloc_zero<uint8_t>((void **)&C.inner, C.g.ntot, st));
     HTRY(alloc_zero<T>(&C.fx, C.g.ntot, st));
     HTRY(alloc_zero<T>(&C.fy, C.g.ntot, st));
     HTRY(alloc_zero<T>(&C.fz, C.g.ntot, st));
-    const double *wf = F.w1d, *wc = C.w1d;
-    k_fractions<T><<<nblk(nc, 256), 256, 0, st>>>(F.mask, (const T *)F.fx, (const T *)F.fy, (const T *)F.fz, F.g, wf,
-                                                  wf + F.g.nx, wf + F.g.nx + F.g.ny, C.g, wc, wc + C.g.nx,
-                                                  wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz);
-    const int nf = F.g.nx + F.g.ny + F.g.nz;
-    HTRY(cudaMalloc((void **)&F.poff, nf));
-    HTRY(cudaMalloc((void **)&F.pt, sizeof(float) * nf));
-    k_prolong_axis<<<nblk(F.g.nx, 128), 128, 0, st>>>(F.cen, F.g.nx, C.cen, C.g.nx, F.poff, F.pt);
-    k_prolong_axis<<<nblk(F.g.ny, 128), 128, 0, st>>>(F.cen + F.g.nx, F.g.ny, C.cen + C.g.nx, C.g.ny,
-                                                      F.poff + F.g.nx, F.pt + F.g.nx);
-    k_prolong_axis<<<nblk(F.g.nz, 128), 128, 0, st>>>(F.cen + F.g.nx + F.g.ny, F.g.nz, C.cen + C.g.nx + C.g.ny, C.g.nz,
-                                                      F.poff + F.g.nx + F.g.ny, F.pt + F.g.nx + F.g.ny);
+    const int nf = Fl.g.nx + Fl.g.ny + Fl.g.nz;
+    HTRY(cudaMalloc((void **)&Fl.poff, nf));
+    HTRY(cudaMalloc((void **)&Fl.pt, sizeof(float) * nf));
+    k_prolong_axis<<<nblk(Fl.g.nx, 128), 128, 0, st>>>(Fl.cen, Fl.g.nx, C.cen, C.g.nx, Fl.poff, Fl.pt);
+    k_prolong_axis<<<nblk(Fl.g.ny, 128), 128, 0, st>>>(Fl.cen + Fl.g.nx, Fl.g.ny, C.cen + C.g.nx, C.g.ny,
+                                                       Fl.poff + Fl.g.nx, Fl.pt + Fl.g.nx);
+    k_prolong_axis<<<nblk(Fl.g.nz, 128), 128, 0, st>>>(Fl.cen + Fl.g.nx + Fl.g.ny, Fl.g.nz, C.cen + C.g.nx + C.g.ny,
+                                                       C.g.nz, Fl.poff + Fl.g.nx + Fl.g.ny, Fl.pt + Fl.g.nx + Fl.g.ny);
     HTRY(cudaGetLastError());
   }
-  // fluid volume per level
+  // coarsest inverse, per-level fluid volumes, ghost count
   {
-    double *tmp = nullptr;
-    HTRY(cudaMalloc((void **)&tmp, sizeof(double) * 2 * 152));
-    std::vector<double> hv(2 * 152);
-    for (int l = 0; l < nl; ++l) {
-      Level &L = h->lv[l];
-      k_fluid_stats<<<152, 256, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx, L.w1d + L.g.nx + L.g.ny, tmp);
-      cudaError_t e = cudaMemcpyAsync(hv.data(), tmp, sizeof(double) * 2 * 152, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) { cudaFree(tmp); return fail(e, "fluid stats"); }
-      double v = 0.0, c = 0.0;
-      for (int b = 0; b < 152; ++b) { v += hv[2 * b]; c += hv[2 * b + 1]; }
-      L.fluid_vol = v;
-      L.nfluid = (long long)c;
-    }
-    cudaFree(tmp);
-  }
-  // coarsest bordered inverse
-  {
-    Level &Lc = h->lv[nl - 1];
     const int m = MAX_COARSE + 1;
-    double *M = nullptr;
-    int *nc = nullptr;
-    HTRY(cudaMalloc((void **)&M, sizeof(double) * m * m));
-    HTRY(cudaMalloc((void **)&h->minv, sizeof(double) * m * m));
+    HTRY(cudaMalloc(&h->minv, sizeof(T) * m * m));
     HTRY(cudaMalloc((void **)&h->cidx, sizeof(int) * (MAX_COARSE + 1)));
-    HTRY(cudaMalloc((void **)&nc, sizeof(int) * 2));
-    h->dncoarse = nc;
-    k_coarsest_setup<T><<<1, 256, 0, st>>>(view<T>(Lc), h->cidx, nc, M, h->minv, MAX_COARSE);
-    HTRY(cudaGetLastError());
-    HTRY(cudaMemcpyAsync(&h->ncoarse, nc, sizeof(int), cudaMemcpyDeviceToHost, st));
-    HTRY(cudaStreamSynchronize(st));
-    cudaFree(M);
+    HTRY(cudaMalloc((void **)&h->dncoarse, sizeof(int) * 2));
+    HTRY(cudaMalloc((void **)&h->d_fvol, sizeof(double) * nl));
+    HTRY(cudaMalloc((void **)&h->d_ng, sizeof(long long)));
+    if (sizeof(T) * m * 2 * m > GJ_SMEM_MAX) HTRY(cudaMalloc(&h->gj, sizeof(T) * m * 2 * m));
   }
-  // fine FP64 arrays and solver-side ghost rows
+  // fine outer arrays and the fused sweep's second buffer
   {
     Level &L0 = h->lv[0];
     HTRY(alloc_zero<double>((void **)&h->p64, L0.g.ntot, st));
     HTRY(alloc_zero<double>((void **)&h->b64, L0.g.ntot, st));
-    const long long ng = t->nghost;
-    HTRY(cudaMalloc((void **)&h->gsrc, sizeof(long long) * 8 * (ng ? ng : 1)));
-    HTRY(cudaMalloc((void **)&h->gdst, sizeof(long long) * (ng ? ng : 1)));
-    HTRY(cudaMalloc((void **)&h->gw32, sizeof(float) * 8 * (ng ? ng : 1)));
-    HTRY(cudaMalloc((void **)&h->gtmp, sizeof(double) * (ng ? ng : 1)));
-    h->gw64 = nullptr;
-    if (ng) k_ghost_src<<<nblk(8 * ng, 256), 256, 0, st>>>(t->gref, t->gcell, ng, L0.g, h->gsrc, h->gdst, t->gw, h->gw32,
-                                                         t->iblank);
-    HTRY(cudaGetLastError());
     HTRY(alloc_zero<T>(&h->e_alt, L0.g.ntot, st));
-    HTRY(cudaStreamSynchronize(st));
+  }
+  HTRY(cudaStreamSynchronize(st));
+  free_faces();
+  {
+    Level &L0 = h->lv[0];
     if (sizeof(T) == 8) setup_zmarch<T>(h, h->p64, h->b64);
     else setup_zmarch<T>(h, L0.e, L0.r);
   }
@@ -1025,6 +1346,86 @@ static ibm_status build_hierarchy_t(ibm_tables *t, cudaStream_t st, Hierarchy **
   return IBM_OK;
 }
 
+// Geometry-dependent part of a hierarchy, for the tables' current classification: masks,
+// inner flags, face fractions, fluid volumes, coarsest inverse and the solver-side ghost
+// rows.  Writes every value it owns, so it refreshes a hierarchy built for other bodies.
+template <typename T>
+static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t st) {
+  const int nl = (int)h->lv.size();
+  Level &L0 = h->lv[0];
+  {
+    const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
+    k_mask0<<<nblk(n0, 256), 256, 0, st>>>(t->iblank, L0.g.nx, L0.g.ny, L0.g.nz, L0.mask, L0.g);
+  }
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level &Fl = h->lv[l], &C = h->lv[l + 1];
+    const long long nc = (long long)C.g.nx * C.g.ny * C.g.nz;
+    k_mask_coarse<<<nblk(nc, 256), 256, 0, st>>>(Fl.mask, Fl.g, C.mask, C.g);
+    k_inner<<<nblk(nc, 256), 256, 0, st>>>(C.mask, C.g, C.inner);
+    const double *wf = Fl.w1d, *wc = C.w1d;
+    k_fractions<T><<<nblk(nc, 256), 256, 0, st>>>(Fl.mask, (const T *)Fl.fx, (const T *)Fl.fy, (const T *)Fl.fz, Fl.g,
+                                                  wf, wf + Fl.g.nx, wf + Fl.g.nx + Fl.g.ny, C.g, wc, wc + C.g.nx,
+                                                  wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz);
+  }
+  IBM_TRY(cudaGetLastError());
+  // fluid volume and count per level (one read-back for all levels)
+  {
+    double *part = t->ctx->partials;   // 2 x 152 doubles per level fit in the context's scratch
+    static_assert(2 * 152 * 16 <= REDUCE_BLOCKS * 8, "fluid statistics scratch");
+    if (nl > 16) return IBM_ERR_CAPACITY;
+    for (int l = 0; l < nl; ++l) {
+      Level &L = h->lv[l];
+      k_fluid_stats<<<152, 256, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx, L.w1d + L.g.nx + L.g.ny,
+                                         part + 2 * 152 * l);
+    }
+    std::vector<double> hv(2 * 152 * nl), fv(nl);
+    IBM_TRY(cudaMemcpyAsync(hv.data(), part, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    for (int l = 0; l < nl; ++l) {
+      double v = 0.0, c = 0.0;
+      for (int b = 0; b < 152; ++b) { v += hv[2 * 152 * l + 2 * b]; c += hv[2 * 152 * l + 2 * b + 1]; }
+      h->lv[l].fluid_vol = v;
+      h->lv[l].nfluid = (long long)c;
+      fv[l] = v;
+    }
+    IBM_TRY(cudaMemcpyAsync(h->d_fvol, fv.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, st));
+  }
+  // coarsest bordered inverse
+  {
+    Level &Lc = h->lv[nl - 1];
+    const int m = MAX_COARSE + 1;
+    const size_t smem = h->gj ? 0 : sizeof(T) * m * 2 * m;
+    IBM_TRY(cudaFuncSetAttribute(k_coarsest_setup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_coarsest_setup<T><<<1, 1024, smem, st>>>(view<T>(Lc), h->cidx, h->dncoarse, (T *)h->minv, (T *)h->gj,
+                                               MAX_COARSE);
+    IBM_TRY(cudaGetLastError());
+    IBM_TRY(cudaMemcpyAsync(&h->ncoarse, h->dncoarse, sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
+  // solver-side ghost rows (arrays grow with the ghost count; growing changes their
+  // addresses, which the captured cycle's key records)
+  {
+    const long long ng = t->nghost;
+    if (ng > h->gcap || !h->gsrc) {
+      const long long cap = std::max<long long>(std::max<long long>(ng + ng / 4, 1024), t->gcap);
+      void *old[] = {h->gsrc, h->gdst, h->gw32, h->gtmp};
+      for (void *q : old) if (q) cudaFree(q);
+      h->gsrc = h->gdst = nullptr; h->gw32 = nullptr; h->gtmp = nullptr; h->gcap = 0;
+      IBM_TRY(cudaMalloc((void **)&h->gsrc, sizeof(long long) * 8 * cap));
+      IBM_TRY(cudaMalloc((void **)&h->gdst, sizeof(long long) * cap));
+      IBM_TRY(cudaMalloc((void **)&h->gw32, sizeof(float) * 8 * cap));
+      IBM_TRY(cudaMalloc((void **)&h->gtmp, sizeof(double) * cap));
+      h->gcap = cap;
+    }
+    h->gw64 = nullptr;
+    if (ng) k_ghost_src<<<nblk(8 * ng, 256), 256, 0, st>>>(t->gref, t->gcell, ng, L0.g, h->gsrc, h->gdst, t->gw, h->gw32,
+                                                         t->iblank);
+    IBM_TRY(cudaMemcpyAsync(h->d_ng, &t->nghost, sizeof(long long), cudaMemcpyHostToDevice, st));
+    IBM_TRY(cudaGetLastError());
+  }
+  IBM_TRY(cudaStreamSynchronize(st));
+  h->geom_version = t->geom_version;
+  return IBM_OK;
+}
 // ------------------------------------------------------------------ solve driver
 
 namespace {
@@ -1045,12 +1446,15 @@ void ghost_update(Solver &S, T *e, const T *ghost_rhs) {
   const long long ng = S.t->nghost;
   if (ng <= 0) return;
   if (sizeof(T) == 8)
-    k_ghost_eval<T, double><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, ng, e, ghost_rhs,
+    k_ghost_eval<T, double><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.h->gcap,
+                                                                     S.h->d_ng, e, ghost_rhs,
                                                               (T *)S.h->gtmp);
   else
-    k_ghost_eval<T, float><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, ng, e, ghost_rhs,
+    k_ghost_eval<T, float><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, S.h->gcap,
+                                                                    S.h->d_ng, e, ghost_rhs,
                                                              (T *)S.h->gtmp);
-  k_ghost_store<T><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gdst, ng, (const T *)S.h->gtmp, e);
+  k_ghost_store<T><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gdst, S.h->gcap, S.h->d_ng, (const T *)S.h->gtmp,
+                                                            e);
   S.ctx->launches += 2;
 }
 
@@ -1094,9 +1498,11 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
       const long long ng = S.t->nghost;
       if (ng > 0) {
         if (sizeof(T) == 8)
-          k_ghost_pp<T, double><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, ng, e, old, ghost_rhs);
+          k_ghost_pp<T, double><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.h->gcap,
+                                                                        S.h->d_ng, e, old, ghost_rhs);
         else
-          k_ghost_pp<T, float><<<nblk(ng, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, ng, e, old, ghost_rhs);
+          k_ghost_pp<T, float><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, S.h->gcap,
+                                                                       S.h->d_ng, e, old, ghost_rhs);
         S.ctx->launches += 1;
       }
       continue;
@@ -1116,25 +1522,23 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   Hierarchy *h = S.h;
   const int nl = (int)h->lv.size();
   if (l == nl - 1) {
-    k_coarsest<T><<<1, 128, 0, S.st>>>(h->minv, h->cidx, S.d_ncoarse, r, e);
+    k_coarsest<T><<<1, 128, 0, S.st>>>((const T *)h->minv, h->cidx, S.d_ncoarse, r, e);
     S.ctx->launches += 1;
     return;
   }
   const bool fine = (l == 0);
   smooth_level<T>(S, l, e, r, shift, fine, ghost_rhs, S.nu1);
   Level &F = h->lv[l], &C = h->lv[l + 1];
-  const long long nc = (long long)C.g.nx * C.g.ny * C.g.nz;
-  const int nb = (int)std::min<long long>(nblk(nc, 256), REDUCE_BLOCKS);
   T *ec = (T *)C.e, *rc = (T *)C.r;
-  k_restrict<T><<<nb, 256, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, S.ctx->partials);
+  const int gx = (int)nblk(C.g.nx, 128), gy = std::max(1, std::min(C.g.ny * C.g.nz, RESTRICT_BLOCKS / gx));
+  k_restrict8<T><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, ec, S.ctx->partials);
   double *cshift = S.ctx->scal + S_LEVEL_SHIFT + (l + 1);
-  k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, nb, C.fluid_vol, cshift);
-  cudaMemsetAsync(ec, 0, sizeof(T) * C.g.ntot, S.st);
+  k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, gx * gy, h->d_fvol + (l + 1), cshift);
   vcycle<T>(S, l + 1, ec, rc, cshift, nullptr);
-  dim3 gp(nblk(F.g.nx, 128), F.g.ny, F.g.nz);
+  dim3 gp(nblk(C.g.nx, 128), C.g.ny, C.g.nz);
   const int nxf = F.g.nx, nyf = F.g.ny;
-  k_prolong<T><<<gp, 128, 0, S.st>>>(view<T>(C), ec, view<T>(F), e, F.poff, F.poff + nxf, F.poff + nxf + nyf, F.pt,
-                                     F.pt + nxf, F.pt + nxf + nyf);
+  k_prolong8<T><<<gp, 128, 0, S.st>>>(view<T>(C), ec, C.inner, view<T>(F), e, F.poff, F.poff + nxf, F.poff + nxf + nyf,
+                                      F.pt, F.pt + nxf, F.pt + nxf + nyf);
   S.ctx->launches += 3;   // restrict, finalize shift, prolong
   // the corrected fluid values make the ghost rows stale: refresh them before post-smoothing
   if (fine) ghost_update<T>(S, e, ghost_rhs);
@@ -1187,7 +1591,7 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   double *gpart = part + 3 * REDUCE_BLOCKS;
   const bool gh = ng > 0 && with_p;
   if (gh)
-    k_ghost_resid_df<<<ngb, REDUCE_THREADS, 0, S.st>>>(h->gsrc, h->gdst, S.t->gw, S.t->gscale, ng, hi_of(h->p64),
+    k_ghost_resid_df<<<ngb, REDUCE_THREADS, 0, S.st>>>(h->gsrc, h->gdst, S.t->gw, S.t->gscale, h->d_ng, hi_of(h->p64),
                                                        pl, r32, gpart);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
                                         update_lambda ? 1 : 0);
@@ -1197,13 +1601,16 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
 void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
   LV<double> v = fine_view64(S.h);
   double *part = S.ctx->partials;
-  k_residual64<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.ctx->scal + S_LAMBDA, r32, part);
+  const int n = v.nx + v.ny + v.nz;
+  k_residual64<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n,
+                                                          r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS;
   const bool gh = ng > 0 && p != nullptr;
   if (gh)
-    k_ghost_resid64<<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, ng, p, r32, gpart);
+    k_ghost_resid64<<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, S.h->d_ng, p, r32,
+                                                      gpart);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
                                         update_lambda ? 1 : 0);
   S.ctx->launches += gh ? 3 : 2;
@@ -1212,23 +1619,26 @@ void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
 }  // namespace
 
 ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
-  if (t->hier[precision]) return IBM_OK;
-  Hierarchy *h = nullptr;
-  ibm_status s = precision == 0 ? build_hierarchy_t<double>(t, st, &h) : build_hierarchy_t<float>(t, st, &h);
+  Hierarchy *h = t->hier[precision];
+  if (h && h->geom_version == t->geom_version) return IBM_OK;
+  if (h) return precision == 0 ? refresh_geometry_t<double>(t, h, st) : refresh_geometry_t<float>(t, h, st);
+  ibm_status s = precision == 0 ? build_grid_t<double>(t, st, &h) : build_grid_t<float>(t, st, &h);
   if (s != IBM_OK) return s;
   // FP64 fine coefficients
   Level &L0 = h->lv[0];
   const int n = L0.g.nx + L0.g.ny + L0.g.nz;
   double *c64 = nullptr, *df = nullptr;
-  IBM_TRY(cudaMalloc((void **)&c64, sizeof(double) * 3 * n));
-  IBM_TRY(cudaMalloc((void **)&df, sizeof(double) * (n + 3)));
-  IBM_TRY(cudaMemcpyAsync(df, t->xf.data(), sizeof(double) * (L0.g.nx + 1), cudaMemcpyHostToDevice, st));
-  IBM_TRY(cudaMemcpyAsync(df + L0.g.nx + 1, t->yf.data(), sizeof(double) * (L0.g.ny + 1), cudaMemcpyHostToDevice, st));
-  IBM_TRY(cudaMemcpyAsync(df + L0.g.nx + L0.g.ny + 2, t->zf.data(), sizeof(double) * (L0.g.nz + 1),
-                          cudaMemcpyHostToDevice, st));
+  auto bail = [&](cudaError_t e, const char *w) { cudaFree(df); cudaFree(c64); free_hierarchy(h); return check(e, w); };
+#define BTRY(call) do { cudaError_t e__ = (call); if (e__ != cudaSuccess) return bail(e__, #call); } while (0)
+  BTRY(cudaMalloc((void **)&c64, sizeof(double) * 3 * n));
+  BTRY(cudaMalloc((void **)&df, sizeof(double) * (n + 3)));
+  BTRY(cudaMemcpyAsync(df, t->xf.data(), sizeof(double) * (L0.g.nx + 1), cudaMemcpyHostToDevice, st));
+  BTRY(cudaMemcpyAsync(df + L0.g.nx + 1, t->yf.data(), sizeof(double) * (L0.g.ny + 1), cudaMemcpyHostToDevice, st));
+  BTRY(cudaMemcpyAsync(df + L0.g.nx + L0.g.ny + 2, t->zf.data(), sizeof(double) * (L0.g.nz + 1),
+                       cudaMemcpyHostToDevice, st));
   double *w = nullptr, *c = nullptr;
-  IBM_TRY(cudaMalloc((void **)&w, sizeof(double) * n));
-  IBM_TRY(cudaMalloc((void **)&c, sizeof(double) * n));
+  BTRY(cudaMalloc((void **)&w, sizeof(double) * 2 * n));
+  c = w + n;
   const int nx = L0.g.nx, ny = L0.g.ny, nz = L0.g.nz;
   double *sd = c64 + 2 * n;
   k_axis_level<double><<<nblk(nx, 128), 128, 0, st>>>(df, nx, c64, c64 + nx, w, c, nullptr, sd);
@@ -1238,17 +1648,26 @@ ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
                                                       c64 + 2 * nx + 2 * ny + nz, w + nx + ny, c + nx + ny, nullptr,
                                                       sd + nx + ny);
   h->c64 = c64;
-  if (precision == 2) {
-    // split coefficients, diagonal parts (3n doubles of c64) and widths (n of w1d)
+  c64 = nullptr;   // owned by the hierarchy from here on
+  {
+    // split coefficients, diagonal parts (3n doubles of c64) and widths (n of w1d); the FP64
+    // residual uses the high parts of the widths as FP32 volume weights
     float *cdf = nullptr;
-    IBM_TRY(cudaMalloc((void **)&cdf, sizeof(float) * 8 * n));
+    BTRY(cudaMalloc((void **)&cdf, sizeof(float) * 8 * n));
     h->cdf = cdf;
-    k_split_df<<<nblk(3 * n, 128), 128, 0, st>>>(c64, 3 * n, cdf, cdf + 4 * n);
+    k_split_df<<<nblk(3 * n, 128), 128, 0, st>>>(h->c64, 3 * n, cdf, cdf + 4 * n);
     k_split_df<<<nblk(n, 128), 128, 0, st>>>(L0.w1d, n, cdf + 3 * n, cdf + 7 * n);
   }
-  IBM_TRY(cudaGetLastError());
-  IBM_TRY(cudaStreamSynchronize(st));
-  cudaFree(df); cudaFree(w); cudaFree(c);
+  BTRY(cudaGetLastError());
+  BTRY(cudaStreamSynchronize(st));
+  cudaFree(df); cudaFree(w);
+  df = nullptr;
+#undef BTRY
+  s = precision == 0 ? refresh_geometry_t<double>(t, h, st) : refresh_geometry_t<float>(t, h, st);
+  if (s != IBM_OK) {
+    free_hierarchy(h);
+    return s;
+  }
   t->hier[precision] = h;
   return IBM_OK;
 }
@@ -1266,15 +1685,13 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   const long long ntot = L0.g.ntot;
   // inputs
   if (S.dfo) {
-    k_pack_df<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, ntot), nullptr);
-    k_pack_df<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, ntot), L0.mask);
-    ctx->launches += 2;
+    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, ntot), nullptr);
+    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, ntot), L0.mask);
   } else {
-    k_pack<<<nblk(n0, 256), 256, 0, st>>>(rhs, L0.g, h->b64);
-    k_pack<<<nblk(n0, 256), 256, 0, st>>>(p_user, L0.g, h->p64);
-    k_zero_solid<<<1216, 256, 0, st>>>(h->p64, L0.mask, L0.g.ntot);
-    ctx->launches += 3;
+    k_pack<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, h->b64, nullptr);
+    k_pack<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask);
   }
+  ctx->launches += 2;
   double hs[NSCAL] = {0};
   hs[S_FLUIDVOL] = L0.fluid_vol;
   hs[S_NF] = (double)L0.nfluid;
@@ -1292,8 +1709,9 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     k_ghost_store_df<<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, hi_of(h->p64), lo_of(h->p64, ntot));
     ctx->launches += 2;
   } else if (ng > 0) {
-    k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, ng, h->p64, nullptr, h->gtmp);
-    k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, h->p64);
+    k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, ng, nullptr, h->p64, nullptr,
+                                                                h->gtmp);
+    k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, nullptr, h->gtmp, h->p64);
     ctx->launches += 2;
   }
   IBM_TRY(cudaGetLastError());
@@ -1339,9 +1757,16 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   const bool graph = opts->use_graph && ctx->cap_stream && (!h->zmarch || sweeps_per_cycle % 2 == 0);
   long long graph_launches = 0;
   if (graph) {
-    const long long key = ((long long)opts->nu1 << 48) ^ ((long long)opts->nu2 << 40) ^
-                          ((long long)opts->inner_cycles << 32) ^ (long long)(opts->omega * 1e6);
-    if (!h->graph_exec || h->graph_key != key) {
+    // the captured cycle depends on the schedule, on whether ghost rows exist and on the
+    // addresses of the per-ghost arrays (which move when they grow); everything else it
+    // reads from device memory or from grid-only data
+    unsigned long long key = ((unsigned long long)opts->nu1 << 48) ^ ((unsigned long long)opts->nu2 << 40) ^
+                             ((unsigned long long)opts->inner_cycles << 32) ^
+                             (unsigned long long)(long long)(opts->omega * 1e6) ^ (ng > 0 ? 1ULL << 62 : 0ULL);
+    const unsigned long long ptrs[4] = {(unsigned long long)(uintptr_t)t->gw, (unsigned long long)(uintptr_t)t->gscale,
+                                        (unsigned long long)(uintptr_t)h->gsrc, (unsigned long long)h->gcap};
+    for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
+    if (!h->graph_exec || h->graph_key != (long long)key) {
       if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
       h->graph_exec = nullptr;
       cudaGraph_t g = nullptr;
@@ -1355,7 +1780,7 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
       cudaGraphDestroy(g);
       if (ce != cudaSuccess) return check(ce, "graph instantiate");
       h->graph_exec = ge;
-      h->graph_key = key;
+      h->graph_key = (long long)key;
       h->graph_launches = ctx->launches - l0;
       ctx->launches = l0;
     }
@@ -1385,9 +1810,10 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
   k_gauge_finalize<<<1, 256, 0, st>>>(ctx->partials, REDUCE_BLOCKS, ctx->scal);
   if (S.dfo)
-    k_unpack_gauge_df<<<1216, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, ctx->scal, p_user);
+    k_unpack_gauge_df<<<PACK_BLOCKS, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, ctx->scal,
+                                                   p_user);
   else
-    k_unpack_gauge<<<nblk(n0, 256), 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
+    k_unpack_gauge<<<PACK_BLOCKS, 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
   ctx->launches += 3;
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));

@@ -71,6 +71,7 @@ def load_library():
         "ibm_ctx_create": (I32, [C.POINTER(P), I32]),
         "ibm_ctx_destroy": (I32, [P]),
         "ibm_classify": (I32, [P, C.POINTER(ibm_grid), C.POINTER(ibm_mesh), I32, C.POINTER(P), P]),
+        "ibm_reclassify": (I32, [P, P, C.POINTER(ibm_mesh), I32, P]),
         "ibm_tables_destroy": (I32, [P]),
         "ibm_tables_counts": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
         "ibm_tables_export": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
@@ -122,6 +123,16 @@ def ibm_ctx_destroy(ctx):
     _check(load_library().ibm_ctx_destroy(ctx), "ibm_ctx_destroy")
 
 
+def _mesh_array(meshes, keep):
+    arr = (ibm_mesh * max(1, len(meshes)))()
+    for q, m in enumerate(meshes):
+        v = np.ascontiguousarray(m.verts, dtype=np.float64)
+        t = np.ascontiguousarray(m.tris, dtype=np.int32)
+        keep += [v, t]
+        arr[q] = ibm_mesh(v.shape[0], t.shape[0], v.ctypes.data, t.ctypes.data, int(m.closed))
+    return arr
+
+
 def ibm_classify(ctx, xf, yf, zf, meshes, stream=None):
     """Classify the grid (host face arrays) against meshes (objects with verts, tris, closed)."""
     lib = load_library()
@@ -129,15 +140,17 @@ def ibm_classify(ctx, xf, yf, zf, meshes, stream=None):
     f = [np.ascontiguousarray(a, dtype=np.float64) for a in (xf, yf, zf)]
     keep += f
     g = ibm_grid(f[0].size - 1, f[1].size - 1, f[2].size - 1, f[0].ctypes.data, f[1].ctypes.data, f[2].ctypes.data)
-    arr = (ibm_mesh * max(1, len(meshes)))()
-    for q, m in enumerate(meshes):
-        v = np.ascontiguousarray(m.verts, dtype=np.float64)
-        t = np.ascontiguousarray(m.tris, dtype=np.int32)
-        keep += [v, t]
-        arr[q] = ibm_mesh(v.shape[0], t.shape[0], v.ctypes.data, t.ctypes.data, int(m.closed))
+    arr = _mesh_array(meshes, keep)
     h = C.c_void_p()
     _check(lib.ibm_classify(ctx, C.byref(g), arr, len(meshes), C.byref(h), _stream(stream)), "ibm_classify")
     return h
+
+
+def ibm_reclassify(ctx, tables, meshes, stream=None):
+    """Reclassify existing tables for new meshes on the same grid (reuses their memory)."""
+    keep = []
+    arr = _mesh_array(meshes, keep)
+    _check(load_library().ibm_reclassify(ctx, tables, arr, len(meshes), _stream(stream)), "ibm_reclassify")
 
 
 def ibm_tables_counts(tables):
@@ -287,6 +300,11 @@ class Tables:
                 if k != "iblank":
                     out[k] = out[k][:0]
         return out
+
+    def reclassify(self, meshes, stream=None):
+        """New body positions on the same grid, in the tables' own memory."""
+        ibm_reclassify(self.ctx.h, self.h, meshes, stream)
+        self.ncell, self.nfluid, self.nghost, self.nsolid = ibm_tables_counts(self.h)
 
     def solve(self, rhs, p, tol=1e-10, opts: SolveOpts | None = None, stream=None, **kw):
         return poisson_solve(self.ctx.h, self.h, rhs, tol, p, opts, stream, **kw)
