@@ -1228,15 +1228,17 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
   h->tm_base[1] = h->e_alt;
   // the FP64 smoother is bound by the FP64 pipe, not by memory: it keeps the two-pass kernel,
   // whose small blocks give the occupancy that hides FP64 latency
-  h->zmarch = sizeof(T) == 4 && ok &&
-              cudaFuncSetAttribute(zm::k_sweep_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(zm::Smem<T>)) == cudaSuccess;
-  int per_sm = 0;
-  if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T>, zm::THREADS,
-                                                                 sizeof(zm::Smem<T>)) == cudaSuccess && per_sm > 0)
-    h->zm_per_sm = per_sm;
-  else
-    h->zmarch = false;
+  h->zmarch = false;
+  if constexpr (sizeof(T) == 4) {
+    h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(zm::Smem<T>)) == cudaSuccess;
+    int per_sm = 0;
+    if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T>, zm::THREADS,
+                                                                   sizeof(zm::Smem<T>)) == cudaSuccess && per_sm > 0)
+      h->zm_per_sm = per_sm;
+    else
+      h->zmarch = false;
+  }
 }
 
 // Grid-only part of a hierarchy: every allocation, the level geometry, coefficients,
@@ -1481,7 +1483,8 @@ void sweep_zmarch(Solver &S, T *&e, const double *shift) {
   a.kz = (a.nz + chunks - 1) / chunks;
   chunks = (a.nz + a.kz - 1) / a.kz;
   dim3 grid(gx, gy, chunks);
-  zm::k_sweep_zmarch<T><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r, h->tm_m, a);
+  if constexpr (sizeof(T) == 4)   // FP32 only (setup_zmarch enables it for FP32 hierarchies)
+    zm::k_sweep_zmarch<T><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r, h->tm_m, a);
   S.ctx->launches += 1;
   e = other;
 }
@@ -1492,7 +1495,7 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
   LV<T> v = view<T>(L);
   dim3 grid(nblk((L.g.nx + 1) / 2, 128), L.g.ny, L.g.nz);
   for (int s = 0; s < sweeps; ++s) {
-    if (fine && S.h->zmarch) {
+    if (sizeof(T) == 4 && fine && S.h->zmarch) {
       T *old = e;
       sweep_zmarch<T>(S, e, shift);
       const long long ng = S.t->nghost;

@@ -3,16 +3,22 @@
 //
 // One CTA owns an x-y tile (TX x TY) and a z-range [k0, k1).  Step q of the march
 //   1. updates the red cells of plane q on the tile plus a one-cell ring (the ring is
-//      recomputed by both neighbouring CTAs, so no inter-CTA exchange is needed),
-//   2. updates the black cells of plane q-1 on the tile (its red neighbours in planes
-//      q-2, q-1, q are all new by then) and stores plane q-1 of the tile from registers.
+//      recomputed by both neighbouring CTAs, so no inter-CTA exchange is needed), in place
+//      in plane q's shared buffer;
+//   2. updates the black cells of plane q-1 on the tile and stores plane q-1 of the tile.
 // Every value is read from the input array and written to a separate output array, so the
 // result is exactly one red half-sweep followed by one black half-sweep (deterministic,
 // independent of the tiling).
 //
-// Each thread owns a fixed strip of 4 consecutive x-cells of the tile (plus, for some
-// threads, a strip of the ring): its coefficients stay in registers for the whole march
-// and every shared-memory access of a strip is a 16-byte vector access.
+// Each thread owns a fixed strip of 4 consecutive x-cells of the tile and keeps that strip's
+// values in planes q-1 .. q+1 in registers.  Red results go back to the plane's buffer
+// (their y-neighbours in other warps read them in the next step, and the strip's black
+// update two steps later reads its z-1 neighbours there); black results go only to
+// registers and global memory, since nothing in the march reads a black value after its
+// update.  x-neighbours across strips move by warp
+// shuffle; only the tile edges read the ring from shared memory.  A red update reads only
+// black cells and a black update only red ones, so the in-place writes never change a value
+// another thread reads in the same step: one barrier per step suffices.
 //
 // Planes of e (halo 2 in x and y), the right-hand side and the mask (halo 1) arrive by
 // cp.async.bulk.tensor into rings of shared-memory buffers DP steps ahead of their use,
@@ -41,8 +47,8 @@ constexpr int RING = 2 * RING_ROW + 2 * TY;  // ring strips (top, bottom, left, 
 static_assert(RING <= THREADS, "one ring strip per thread at most");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
-// prefetch distance in planes; rings hold the planes in use (e: q-2 .. q+1, rhs/mask:
-// q-1 .. q) plus the ones in flight
+// prefetch distance in planes; rings hold the planes in use at step q (e: q-2 .. q+1,
+// rhs/mask: q-1 .. q) plus the ones in flight
 template <typename T> struct Depth { static constexpr int D = sizeof(T) == 4 ? 2 : 1; };
 template <typename T> constexpr int NE = 4 + Depth<T>::D;
 template <typename T> constexpr int NR = 2 + Depth<T>::D;
@@ -58,6 +64,8 @@ struct Smem {
   alignas(8) uint64_t bar_e[NE<T>];
   alignas(8) uint64_t bar_r[NR<T>];
 };
+
+template <typename T> struct Strip;
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -210,49 +218,35 @@ __device__ __forceinline__ void relax_colour(const Strip<T> &S, T *P, const T *P
   st4(P + ie, C);
 }
 
-// Interior strips: the warp's rows share one parity, so the colour's cells in a strip are
-// u = UA and UA + 2 with UA warp-uniform; both cases are compiled separately (no selects).
+// Interior strip update from registers: cells u = UA and UA + 2 of C (UA warp-uniform: a
+// warp's rows share one parity), neighbours N/So (rows y -1 / +1 of the same plane), Zm/Zp
+// (the strip in planes k -1 / +1), west/east (the cells left of u = 0 and right of u = 3).
 template <int UA, typename T>
-__device__ __forceinline__ void relax_pair(const Strip<T> &S, T *P, const T *Pm, const T *Pp, const T *R,
-                                           const uint8_t *M, T czm, T czp, T sz, T sh, float om, Q4<T> &C) {
-  const int ie = S.ie;
-  C = ld4(P + ie);
-  const unsigned m4 = *reinterpret_cast<const unsigned *>(M + S.im);
+__device__ __forceinline__ void relax_reg(const Strip<T> &S, Q4<T> &C, const Q4<T> &N, const Q4<T> &So,
+                                          const Q4<T> &Zm, const Q4<T> &Zp, const Q4<T> &Rh, unsigned m4, T west,
+                                          T east, T czm, T czp, T sz, T sh, float om) {
   constexpr int u0 = UA, u1 = UA + 2;
   const bool ok0 = ((S.valid >> u0) & 1u) && ((m4 >> (8 * u0)) & 0xffu) == 0u;
   const bool ok1 = ((S.valid >> u1) & 1u) && ((m4 >> (8 * u1)) & 0xffu) == 0u;
-  if (!(ok0 || ok1)) return;
-  const Q4<T> N = ld4(P + ie - BX), So = ld4(P + ie + BX), B = ld4(Pm + ie), U = ld4(Pp + ie);
-  const Q4<T> Rh = ld4(R + S.ir);
   const T syz = S.sy + sz;
-  const T west0 = UA == 0 ? P[ie - 1] : C.v[0];
-  const T east1 = UA == 1 ? P[ie + 4] : C.v[3];
   const T c0 = C.v[u0], c1 = C.v[u1];
   const T D0 = S.sx[u0] + syz, D1 = S.sx[u1] + syz;
-  T s0 = S.cxm[u0] * west0;
+  T s0 = S.cxm[u0] * (UA == 0 ? west : C.v[0]);
   s0 += S.cxp[u0] * C.v[u0 + 1];
   s0 += S.cym * N.v[u0];
   s0 += S.cyp * So.v[u0];
-  s0 += czm * B.v[u0];
-  s0 += czp * U.v[u0];
+  s0 += czm * Zm.v[u0];
+  s0 += czp * Zp.v[u0];
   T s1 = S.cxm[u1] * C.v[u1 - 1];
-  s1 += S.cxp[u1] * east1;
+  s1 += S.cxp[u1] * (UA == 1 ? east : C.v[3]);
   s1 += S.cym * N.v[u1];
   s1 += S.cyp * So.v[u1];
-  s1 += czm * B.v[u1];
-  s1 += czp * U.v[u1];
+  s1 += czm * Zm.v[u1];
+  s1 += czp * Zp.v[u1];
   const T r0 = (s0 - D0 * c0) - (Rh.v[u0] - sh);
   const T r1 = (s1 - D1 * c1) - (Rh.v[u1] - sh);
   if (ok0) C.v[u0] = c0 + (T)__fdividef(om * (float)r0, (float)D0);
   if (ok1) C.v[u1] = c1 + (T)__fdividef(om * (float)r1, (float)D1);
-  st4(P + ie, C);
-}
-
-template <typename T>
-__device__ __forceinline__ void relax_interior(const Strip<T> &S, int ua, T *P, const T *Pm, const T *Pp, const T *R,
-                                               const uint8_t *M, T czm, T czp, T sz, T sh, float om, Q4<T> &C) {
-  if (ua == 0) relax_pair<0, T>(S, P, Pm, Pp, R, M, czm, czp, sz, sh, om, C);
-  else relax_pair<1, T>(S, P, Pm, Pp, R, M, czm, czp, sz, sh, om, C);
 }
 
 template <typename T>
@@ -272,16 +266,20 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
     for (int b = 0; b < NRt; ++b) mbar_init(&s.bar_r[b], 1);
     fence_mbar_init();
   }
-  // this thread's interior strip, and its ring strip (red updates of the one-cell ring)
-  Strip<T> Si, Sr;
+  // this thread's interior strip (registers), and the ring strips (red updates of the
+  // one-cell ring; shared memory, read only by their owners, once per step)
+  __shared__ Strip<T> ring[RING];
+  Strip<T> Si;
+  const int l16 = tid & 15;
   {
     // warps 0..THREADS/64-1 take the even rows, the others the odd rows, two rows per warp
+    // (lanes 0-15 and 16-31), so a warp's strips share one colour parity
     const int w = tid >> 5, l = tid & 31, half = THREADS / 64;
     const int y = 4 * (w % half) + (w >= half ? 1 : 0) + 2 * (l >> 4);
-    make_strip(Si, a, x0, y0, 4 * (l & 15), y, 0, TX - 1);
+    make_strip(Si, a, x0, y0, 4 * l16, y, 0, TX - 1);
   }
   const bool has_ring = tid < RING;
-  {
+  if (has_ring) {
     int xs = 0, y = 0;
     if (tid < 2 * RING_ROW) {
       y = tid < RING_ROW ? -1 : TY;
@@ -291,8 +289,7 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
       y = r % TY;
       xs = r < TY ? -4 : TX;
     }
-    make_strip(Sr, a, x0, y0, xs, y, -1, TX);
-    if (!has_ring) Sr.valid = 0;
+    make_strip(ring[tid], a, x0, y0, xs, y, -1, TX);
   }
   __syncthreads();
   const unsigned ebytes = EY * BX * sizeof(T), rbytes = RY * BX * sizeof(T) + RY * BXM;
@@ -320,17 +317,20 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
     if (!bad && !mbar_wait(&s.bar_r[b], (pr >> b) & 1u)) bad = true;
     pr ^= 1u << b;
   };
-  // prologue: e planes k0-2 .. k0-1+DP and rhs/mask planes k0-1 .. k0-2+DP.  Step q then
-  // waits for e plane q+1 and rhs/mask plane q and, after the step's first barrier (so no
-  // thread still reads the buffers being refilled), prefetches e plane q+1+DP (into the
-  // buffer of plane q-3) and rhs/mask plane q+DP (buffer of plane q-2).  Every load is
-  // issued once and waited for once.
+  auto ebuf = [&](int plane) { return s.e[(plane + 2 * NEt) % NEt]; };
+  // prologue: e planes k0-2 .. k0-1+DP and rhs/mask planes k0-1 .. k0-2+DP.  Step q waits
+  // for e plane q+1 and rhs/mask plane q and, after the step's barrier (so no thread still
+  // reads the buffers being refilled), prefetches e plane q+1+DP (into the buffer of plane
+  // q-3) and rhs/mask plane q+DP (buffer of plane q-2).  Every load is issued once and
+  // waited for once.
   if (tid == 0) {
     for (int pl = k0 - 2; pl <= min(k0 - 1 + DP, k1 + 1); ++pl) load_e(pl);
     for (int pl = k0 - 1; pl <= min(k0 - 2 + DP, k1); ++pl) load_r(pl);
   }
   wait_e(k0 - 2);
   wait_e(k0 - 1);
+  // registers: the strip in planes q-1 (Cm1) and q (C0)
+  Q4<T> Cm1 = ld4(ebuf(k0 - 2) + Si.ie), C0 = ld4(ebuf(k0 - 1) + Si.ie);
   const T sh = a.shift ? (T)(*a.shift) : (T)0;
   const float om = a.omega;
   for (int q = k0 - 1; q <= k1; ++q) {
@@ -342,37 +342,60 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
       if (q + 1 + DP <= k1 + 1) load_e(q + 1 + DP);
       if (q + DP <= k1) load_r(q + DP);
     }
-    T *Pm = s.e[(q - 1 + 2 * NEt) % NEt], *P = s.e[(q + 2 * NEt) % NEt], *Pp = s.e[(q + 1 + 2 * NEt) % NEt];
-    // red cells of plane q on the tile plus the ring
+    T *P = ebuf(q), *Pm = ebuf(q - 1);
+    const T *Pp = ebuf(q + 1);
+    const T *R = s.r[(q + 2 * NRt) % NRt];
+    const uint8_t *M = s.m[(q + 2 * NRt) % NRt];
+    const Q4<T> U = ld4(Pp + Si.ie);
+    // x-edges: the cell west of u = 0 and east of u = 3, from the adjacent lanes (same row),
+    // or from the ring in shared memory at the tile edges; all lanes take part
+    T wr = __shfl_up_sync(0xffffffffu, C0.v[3], 1, 16), er = __shfl_down_sync(0xffffffffu, C0.v[0], 1, 16);
+    T wb = __shfl_up_sync(0xffffffffu, Cm1.v[3], 1, 16), eb = __shfl_down_sync(0xffffffffu, Cm1.v[0], 1, 16);
+    if (l16 == 0) { wr = P[Si.ie - 1]; wb = Pm[Si.ie - 1]; }
+    if (l16 == 15) { er = P[Si.ie + 4]; eb = Pm[Si.ie + 4]; }
+    // red cells of plane q on the tile (from registers) and the ring (from shared memory)
     if (q >= 0 && q < a.nz) {
       const T czm = a.czm[q], czp = a.czp[q], sz = a.sdz[q];
-      const T *R = s.r[(q + 2 * NRt) % NRt];
-      const uint8_t *M = s.m[(q + 2 * NRt) % NRt];
-      Q4<T> C;
-      relax_interior<T>(Si, (Si.par + q) & 1, P, Pm, Pp, R, M, czm, czp, sz, sh, om, C);
-      if (Sr.valid) relax_colour<T>(Sr, P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, C);
+      const Q4<T> N = ld4(P + Si.ie - BX), So = ld4(P + Si.ie + BX);
+      const Q4<T> R0 = ld4(R + Si.ir);
+      const unsigned M0 = *reinterpret_cast<const unsigned *>(M + Si.im);
+      if (((Si.par + q) & 1) == 0)
+        relax_reg<0, T>(Si, C0, N, So, Cm1, U, R0, M0, wr, er, czm, czp, sz, sh, om);
+      else
+        relax_reg<1, T>(Si, C0, N, So, Cm1, U, R0, M0, wr, er, czm, czp, sz, sh, om);
+      st4(P + Si.ie, C0);
+      if (has_ring && ring[tid].valid) {
+        Q4<T> Cr;
+        relax_colour<T>(ring[tid], P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, Cr);
+      }
     }
-    __syncthreads();
-    // black cells of plane q-1 on the tile; store the thread's strip from registers
+    // black cells of plane q-1 on the tile: neighbours all red, updated by now; store the
+    // strip from registers
     const int kb = q - 1;
     if (kb >= k0 && kb < k1) {
-      T *Bm = s.e[(kb - 1 + 2 * NEt) % NEt], *B = s.e[(kb + 2 * NEt) % NEt];
       const T czm = a.czm[kb], czp = a.czp[kb], sz = a.sdz[kb];
-      const T *R = s.r[(kb + 2 * NRt) % NRt];
-      const uint8_t *M = s.m[(kb + 2 * NRt) % NRt];
-      Q4<T> C;
-      relax_interior<T>(Si, (Si.par + kb + 1) & 1, B, Bm, P, R, M, czm, czp, sz, sh, om, C);
+      const Q4<T> N = ld4(Pm + Si.ie - BX), So = ld4(Pm + Si.ie + BX);
+      const Q4<T> Zm = ld4(ebuf(kb - 1) + Si.ie);   // red values of plane q-2, in place
+      const T *Rb = s.r[(kb + 2 * NRt) % NRt];
+      const Q4<T> Rm1 = ld4(Rb + Si.ir);
+      const unsigned Mm1 = *reinterpret_cast<const unsigned *>(s.m[(kb + 2 * NRt) % NRt] + Si.im);
+      if (((Si.par + kb + 1) & 1) == 0)
+        relax_reg<0, T>(Si, Cm1, N, So, Zm, C0, Rm1, Mm1, wb, eb, czm, czp, sz, sh, om);
+      else
+        relax_reg<1, T>(Si, Cm1, N, So, Zm, C0, Rm1, Mm1, wb, eb, czm, czp, sz, sh, om);
       if (Si.valid) {
         const int gj = y0 + Si.y, gi = x0 + Si.xs;
         T *dst = a.out + ((long long)(kb + 1) * (a.ny + 2) + (gj + 1)) * a.px + (gi + 4);
         if (Si.valid == 0xfu) {
-          st4(dst, C);
+          st4(dst, Cm1);
         } else {
           for (int u = 0; u < 4; ++u)
-            if ((Si.valid >> u) & 1u) dst[u] = C.v[u];
+            if ((Si.valid >> u) & 1u) dst[u] = Cm1.v[u];
         }
       }
     }
+    Cm1 = C0;
+    C0 = U;
   }
   if (bad) {
     if (tid == 0) {
