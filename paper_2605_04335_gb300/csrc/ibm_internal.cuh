@@ -99,6 +99,7 @@ struct Hierarchy {
   // finest level ping-pong for the fused z-march sweep: the second buffer of the
   // level-0 unknown (p64 in FP64 mode, lv[0].e in mixed mode) and TMA tensor maps
   void *e_alt = nullptr;
+  int grid_blocks[2] = {1216, 1216};        // resident blocks of the restriction / prolongation
   bool zmarch = false;
   int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep
   CUtensorMap tm_e[2], tm_r, tm_m;

@@ -403,12 +403,30 @@ __global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const T *e, const T 
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const T sh = shift ? (T)(*shift) : (T)0;
   const int crows = cv.ny * cv.nz;
+  // the children's 1D coefficients: x parts fixed per thread, y and z parts per row
+  const int i0 = 2 * I;
+  T cxm[2], cxp[2], sdx[2], wxf[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int i = min(i0 + a, f.nx - 1);
+    cxm[a] = f.cxm[i]; cxp[a] = f.cxp[i]; wxf[a] = f.wx[i];
+    sdx[a] = f.sdx ? f.sdx[i] : (T)0;
+  }
   if (I < cv.nx)
     for (int row = blockIdx.y; row < crows; row += gridDim.y) {
       const int J = row % cv.ny, K = row / cv.ny;
       const long long ic = vidx(cv, I, J, K);
-      const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+      const int j0 = 2 * J, k0 = 2 * K;
       const bool vx1 = i0 + 1 < f.nx, vy1 = j0 + 1 < f.ny, vz1 = k0 + 1 < f.nz;
+      T cym[2], cyp[2], sdy[2], wyf[2], czm[2], czp[2], sdz[2], wzf[2];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int j = min(j0 + b, f.ny - 1), k = min(k0 + b, f.nz - 1);
+        cym[b] = f.cym[j]; cyp[b] = f.cyp[j]; wyf[b] = f.wy[j];
+        czm[b] = f.czm[k]; czp[b] = f.czp[k]; wzf[b] = f.wz[k];
+        sdy[b] = f.sdx ? f.sdy[j] : (T)0;
+        sdz[b] = f.sdx ? f.sdz[k] : (T)0;
+      }
       const long long fb = vidx(f, i0, j0, k0);
       T E[2][2][2], R[2][2][2], XM[2][2], XP[2][2], YM[2][2], YP[2][2], ZM[2][2], ZP[2][2];
       uchar2 M[2][2];
@@ -446,17 +464,20 @@ __global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const T *e, const T 
 #pragma unroll
           for (int a = 0; a < 2; ++a) {
             const uint8_t m = a ? M[d][b].y : M[d][b].x;
-            const int i = min(i0 + a, f.nx - 1), j = min(j0 + b, f.ny - 1), k = min(k0 + d, f.nz - 1);
             const long long id = fb + d * f.sz + b * f.sy + a;
-            T c[6];
-            coefs(f, i, j, k, id, c);
-            const T D = f.sdx ? (f.sdx[i] + f.sdy[j]) + f.sdz[k] : ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+            T c[6] = {cxm[a], cxp[a], cym[b], cyp[b], czm[d], czp[d]};
+            if (f.fx) {
+              c[0] *= f.fx[id - 1]; c[1] *= f.fx[id];
+              c[2] *= f.fy[id - f.sy]; c[3] *= f.fy[id];
+              c[4] *= f.fz[id - f.sz]; c[5] *= f.fz[id];
+            }
+            const T D = f.sdx ? (sdx[a] + sdy[b]) + sdz[d] : ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
             const T xm = a ? E[d][b][0] : XM[d][b], xp = a ? XP[d][b] : E[d][b][1];
             const T ym = b ? E[d][0][a] : YM[d][a], yp = b ? YP[d][a] : E[d][1][a];
             const T zm = d ? E[0][b][a] : ZM[b][a], zp = d ? ZP[b][a] : E[1][b][a];
             const T s = c[0] * xm + c[1] * xp + c[2] * ym + c[3] * yp + c[4] * zm + c[5] * zp;
             const T res = (R[d][b][a] - sh) - (s - D * E[d][b][a]);
-            if (m == 0) acc += (f.wx[i] * f.wy[j]) * f.wz[k] * res;
+            if (m == 0) acc += (wxf[a] * wyf[b]) * wzf[d] * res;
           }
       const T vc = (cv.wx[I] * cv.wy[J]) * cv.wz[K];
       rc[ic] = cfl ? acc / vc : (T)0;
@@ -493,19 +514,21 @@ __global__ void k_finalize_shift(const double *partials, int nb, const double *f
   if (threadIdx.x == 0) *shift = *fluid_vol > 0 ? s / *fluid_vol : 0.0;
 }
 
-// Prolongation e_f += P e_c, one thread per coarse cell (I,J,K) and its 2x2x2 children.
-// Along each axis a child takes weight 1-t on its parent and t on the parent's neighbour
-// on the child's side (off = -1 or +1; t = 0 without one), so each child reads the 3x3x3
-// coarse block around (I,J,K).  Coarse e is zero on every non-fluid coarse cell (cleared
-// before the coarse cycle, written only on fluid rows), so the weighted sum needs no mask
-// and is contracted axis by axis; the renormalising denominator (sum of the weights of the
-// fluid corners) is 1 where the whole block is fluid (inner flag), else summed the same way
-// over the fluid indicator.  Children that are not fluid rows are left unchanged.
+// Prolongation e_f += P e_c, one thread per coarse cell (I,J,K) and its 2x2x2 children,
+// coarse rows strided over blockIdx.y.  Along each axis a child takes weight 1-t on its
+// parent and t on the parent's neighbour on the child's side (off = -1 or +1; t = 0 without
+// one), so each child reads the 3x3x3 coarse block around (I,J,K).  Coarse e is zero on
+// every non-fluid coarse cell (zeroed by the restriction, written only on fluid rows), so
+// the weighted sum needs no mask and is contracted axis by axis; the renormalising
+// denominator (sum of the weights of the fluid corners) is 1 where the whole block is fluid
+// (inner flag), else summed the same way over the fluid indicator.  Children that are not
+// fluid rows are left unchanged.  The children's e and masks are loaded with the coarse
+// block, before any arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const uint8_t *inner, LV<T> f, T *ef,
                                                   const int8_t *offx, const int8_t *offy, const int8_t *offz,
                                                   const float *tx, const float *ty, const float *tz) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= cv.nx) return;
   float wx[2][3], wy[2][3], wz[2][3];
   auto axis = [](int c0, int nf, const int8_t *off, const float *t, float w[2][3]) {
@@ -520,89 +543,89 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const u
     }
   };
   axis(2 * I, f.nx, offx, tx, wx);
-  axis(2 * J, f.ny, offy, ty, wy);
-  axis(2 * K, f.nz, offz, tz, wz);
-  // children rows (d = z child, b = y child): padded index of child x = 2I; masks of the pair
-  long long fr[2][2];
-  uchar2 fm[2][2];
-  bool any = false;
-#pragma unroll
-  for (int d = 0; d < 2; ++d)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      fr[d][b] = vidx(f, 2 * I, 2 * J + b, 2 * K + d);
-      // rows past the fine extent (odd sizes) are halo rows: mask 1, never updated
-      fm[d][b] = *reinterpret_cast<const uchar2 *>(f.mask + fr[d][b]);
-      any |= fm[d][b].x == 0 || fm[d][b].y == 0;
-    }
-  if (!any) return;
-  const long long c0 = vidx(cv, I, J, K);
-  T e[3][3][3];
-#pragma unroll
-  for (int z = 0; z < 3; ++z)
-#pragma unroll
-    for (int y = 0; y < 3; ++y)
-#pragma unroll
-      for (int x = 0; x < 3; ++x) e[z][y][x] = ec[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)];
-  // contract x, then y, then z
-  auto contract = [&](const T (&v)[3][3][3], T (&out)[2][2][2]) {
-    T vx[2][3][3];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int z = 0; z < 3; ++z)
-#pragma unroll
-        for (int y = 0; y < 3; ++y)
-          vx[a][z][y] = (T)wx[a][0] * v[z][y][0] + (T)wx[a][1] * v[z][y][1] + (T)wx[a][2] * v[z][y][2];
-    T vxy[2][2][3];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int z = 0; z < 3; ++z)
-          vxy[a][b][z] = (T)wy[b][0] * vx[a][z][0] + (T)wy[b][1] * vx[a][z][1] + (T)wy[b][2] * vx[a][z][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int d = 0; d < 2; ++d)
-          out[d][b][a] = (T)wz[d][0] * vxy[a][b][0] + (T)wz[d][1] * vxy[a][b][1] + (T)wz[d][2] * vxy[a][b][2];
-  };
-  T num[2][2][2], den[2][2][2];
-  contract(e, num);
-  if (inner[c0]) {
+  const int crows = cv.ny * cv.nz;
+  for (int row = blockIdx.y; row < crows; row += gridDim.y) {
+    const int J = row % cv.ny, K = row / cv.ny;
+    axis(2 * J, f.ny, offy, ty, wy);
+    axis(2 * K, f.nz, offz, tz, wz);
+    // children rows (d = z child, b = y child) at x = 2I; rows past the fine extent (odd
+    // sizes) are halo rows: mask 1, never updated
+    long long fr[2][2];
+    uchar2 fm[2][2];
+    T fe[2][2][2];
 #pragma unroll
     for (int d = 0; d < 2; ++d)
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int a = 0; a < 2; ++a) den[d][b][a] = (T)1;
-  } else {
-    T m[3][3][3];
+      for (int b = 0; b < 2; ++b) {
+        fr[d][b] = vidx(f, 2 * I, 2 * J + b, 2 * K + d);
+        fm[d][b] = *reinterpret_cast<const uchar2 *>(f.mask + fr[d][b]);
+        Pair<T>::ld(ef + fr[d][b], fe[d][b]);
+      }
+    const long long c0 = vidx(cv, I, J, K);
+    const bool inr = inner[c0] != 0;
+    T e[3][3][3];
 #pragma unroll
     for (int z = 0; z < 3; ++z)
 #pragma unroll
       for (int y = 0; y < 3; ++y)
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
-          m[z][y][x] = cv.mask[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)] == 0 ? (T)1 : (T)0;
-    contract(m, den);
-  }
+        for (int x = 0; x < 3; ++x) e[z][y][x] = ec[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)];
+    // contract x, then y, then z
+    auto contract = [&](const T (&v)[3][3][3], T (&out)[2][2][2]) {
+      T vx[2][3][3];
 #pragma unroll
-  for (int d = 0; d < 2; ++d)
+      for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      T *row = ef + fr[d][b];
-      T v0 = row[0], v1 = row[1];
-      if (fm[d][b].x == 0 && den[d][b][0] > (T)0) v0 += num[d][b][0] / den[d][b][0];
-      if (fm[d][b].y == 0 && den[d][b][1] > (T)0) v1 += num[d][b][1] / den[d][b][1];
-      if (fm[d][b].x == 0 || fm[d][b].y == 0) {
-        row[0] = v0;
-        row[1] = v1;
-      }
+        for (int z = 0; z < 3; ++z)
+#pragma unroll
+          for (int y = 0; y < 3; ++y)
+            vx[a][z][y] = (T)wx[a][0] * v[z][y][0] + (T)wx[a][1] * v[z][y][1] + (T)wx[a][2] * v[z][y][2];
+      T vxy[2][2][3];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int z = 0; z < 3; ++z)
+            vxy[a][b][z] = (T)wy[b][0] * vx[a][z][0] + (T)wy[b][1] * vx[a][z][1] + (T)wy[b][2] * vx[a][z][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int d = 0; d < 2; ++d)
+            out[d][b][a] = (T)wz[d][0] * vxy[a][b][0] + (T)wz[d][1] * vxy[a][b][1] + (T)wz[d][2] * vxy[a][b][2];
+    };
+    T num[2][2][2], den[2][2][2];
+    contract(e, num);
+    if (inr) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) den[d][b][a] = (T)1;
+    } else {
+      T m[3][3][3];
+#pragma unroll
+      for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y)
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            m[z][y][x] = cv.mask[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)] == 0 ? (T)1 : (T)0;
+      contract(m, den);
     }
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const bool u0 = fm[d][b].x == 0 && den[d][b][0] > (T)0, u1 = fm[d][b].y == 0 && den[d][b][1] > (T)0;
+        T *rowp = ef + fr[d][b];
+        if (u0) rowp[0] = fe[d][b][0] + num[d][b][0] / den[d][b][0];
+        if (u1) rowp[1] = fe[d][b][1] + num[d][b][1] / den[d][b][1];
+      }
+  }
 }
 
 // bordered coarsest solve: [e; lambda] = Minv [r; 0]
@@ -1343,6 +1366,14 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     if (sizeof(T) == 8) setup_zmarch<T>(h, h->p64, h->b64);
     else setup_zmarch<T>(h, L0.e, L0.r);
   }
+  // one wave of the row-strided restriction and prolongation kernels
+  {
+    int sms = t->ctx->sm_count > 0 ? t->ctx->sm_count : 152, pr = 0, pp = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pr, k_restrict8<T>, 128, 0) != cudaSuccess || pr < 1) pr = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pp, k_prolong8<T>, 128, 0) != cudaSuccess || pp < 1) pp = 8;
+    h->grid_blocks[0] = pr * sms;
+    h->grid_blocks[1] = pp * sms;
+  }
 #undef HTRY
   *out = h;
   return IBM_OK;
@@ -1533,12 +1564,14 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   smooth_level<T>(S, l, e, r, shift, fine, ghost_rhs, S.nu1);
   Level &F = h->lv[l], &C = h->lv[l + 1];
   T *ec = (T *)C.e, *rc = (T *)C.r;
-  const int gx = (int)nblk(C.g.nx, 128), gy = std::max(1, std::min(C.g.ny * C.g.nz, RESTRICT_BLOCKS / gx));
+  const int gx = (int)nblk(C.g.nx, 128),
+            gy = std::max(1, std::min(C.g.ny * C.g.nz, std::min(RESTRICT_BLOCKS, h->grid_blocks[0]) / gx));
   k_restrict8<T><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, ec, S.ctx->partials);
   double *cshift = S.ctx->scal + S_LEVEL_SHIFT + (l + 1);
   k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, gx * gy, h->d_fvol + (l + 1), cshift);
   vcycle<T>(S, l + 1, ec, rc, cshift, nullptr);
-  dim3 gp(nblk(C.g.nx, 128), C.g.ny, C.g.nz);
+  const int pgx = (int)nblk(C.g.nx, 128);
+  dim3 gp(pgx, std::max(1, std::min(C.g.ny * C.g.nz, h->grid_blocks[1] / pgx)));
   const int nxf = F.g.nx, nyf = F.g.ny;
   k_prolong8<T><<<gp, 128, 0, S.st>>>(view<T>(C), ec, C.inner, view<T>(F), e, F.poff, F.poff + nxf, F.poff + nxf + nyf,
                                       F.pt, F.pt + nxf, F.pt + nxf + nyf);
