@@ -35,6 +35,9 @@ UNIT = "Gcell/s (cells classified and solved to 1e-10 per second)"
 TOL = 1e-10
 FP32_SWEEP_BYTES = 13.0    # read e 4 + rhs 4 + mask 1, write e 4 per cell and full sweep
 FP64_SWEEP_BYTES = 25.0    # read p 8 + b 8 + mask 1, write p 8
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_zmarch launch on the 256^3 grid,
+# from one ncu --set full capture of the current kernel
+SWEEP_TRAFFIC_BYTES = 176443904 + 40851968
 
 
 def _peaks():
@@ -47,7 +50,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while active."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -63,7 +66,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -305,17 +308,19 @@ def run_ours(args):
             ts.append(a.elapsed_time(c))
         tts[name] = statistics.median(ts)
         cyc[name] = rep["cycles"]
-    # smoother sweeps: Gpts/s per sweep (fine level, red + black + ghost rows)
-    sweeps = {}
-    for name, prec in (("fp32", 1), ("fp64", 0)):
+    # smoother sweeps (fine level): the sweep kernel alone (CUDA events on the stream around
+    # each fused-sweep launch, 20 sweeps), and whole sweeps with the ghost-row refresh
+    sweeps, sweeps_g = {}, {}
+    for name, prec in (("fp32", 2), ("fp64", 0)):
         nsw = 20
         pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, 3, st)
+        sweeps[name] = pkg.ibm_smoother_sweeps_timed(ctx.h, T.h, prec, nsw, st)
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
         pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, nsw, st)
         c.record(st)
         c.synchronize()
-        sweeps[name] = a.elapsed_time(c) / nsw
+        sweeps_g[name] = a.elapsed_time(c) / nsw
     T_ng = T.nghost
     hbm, src = _peaks()
     gpts32 = N / (sweeps["fp32"] * 1e-3) / 1e9
@@ -350,12 +355,15 @@ def run_ours(args):
             "time_to_tol_ms": dict(tts),
             "classify_ms": statistics.median(tcl), "reclassify_ms": statistics.median(trc), "ghosts": T_ng,
             "cycles": cyc, "mixed_speedup_vs_fp64": tts["fp64"] / tts["mixed"],
+            "mixed_df_speedup_vs_fp64": tts["fp64"] / tts["mixed_df"],
             "sweep_gpts": {"fp32": gpts32, "fp64": gpts64},
-            "sweep_ms": sweeps,
+            "sweep_kernel_ms": sweeps, "sweep_with_ghost_rows_ms": sweeps_g,
             "final_rel_resid": reps[-1]["rel_resid"],
-            "roofline": {"bound": "hbm", "kernel": "FP32 red-black Gauss-Seidel sweep (fine level, + ghost rows)",
-                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                         "peak_source": src, "algorithmic_bytes_per_cell": FP32_SWEEP_BYTES},
+            "roofline": {"bound": "hbm", "kernel": "k_sweep_zmarch (fused FP32 red-black sweep, finest level)",
+                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": SWEEP_TRAFFIC_BYTES if args.n == 256 else None,
+                         "peak_source": src + " (copy bandwidth)", "algorithmic_bytes_per_cell": FP32_SWEEP_BYTES,
+                         "cells_per_launch": N},
             "e2e": {"value": ws * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(b_host.nbytes + mesh_bytes), "d2h_bytes_per_step": int(b_host.nbytes)},
             "gpu_launches": launches, "clocks": clk.summary()}
@@ -376,15 +384,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--cpu-n", type=int, default=64)
+    ap.add_argument("--cpu-n", type=int, default=96)
     ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -197,6 +197,14 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
 ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps,
                                void *stream);
 
+/* Measurement: as ibm_smoother_sweeps (nsweeps >= 1), with CUDA events recorded on `stream`
+ * immediately before and after each sweep's kernel(s) -- the fused sweep in FP32, the two
+ * colour passes in FP64 -- so the ghost-row refresh between sweeps is excluded.  Waits for
+ * the stream and returns the mean duration of one sweep's kernels in *kernel_ms.  The paper
+ * has no counterpart; it serves roofline measurements. */
+ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t precision,
+                                     int32_t nsweeps, void *stream, double *kernel_ms);
+
 /* Number of CUDA kernels this context has launched so far (all calls). */
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
 

@@ -25,7 +25,8 @@ ibm_status classify_impl(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *mes
 ibm_status reclassify_impl(ibm_ctx *ctx, ibm_tables *t, const ibm_mesh *meshes, int nmesh, cudaStream_t st);
 ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
-ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st);
+ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st,
+                       double *kernel_ms);
 ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const double *const *rhs, double tol,
                               double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
                               cudaStream_t st);
@@ -173,7 +174,15 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
 ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps, void *stream) {
   if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 0) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
-  return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream);
+  return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, nullptr);
+}
+
+ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps,
+                                     void *stream, double *kernel_ms) {
+  if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 1 || !kernel_ms)
+    return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, kernel_ms);
 }
 
 static bool valid_opts(const ibm_solve_opts &o) {

@@ -100,6 +100,7 @@ struct Hierarchy {
   // level-0 unknown (p64 in FP64 mode, lv[0].e in mixed mode) and TMA tensor maps
   void *e_alt = nullptr;
   int grid_blocks[2] = {1216, 1216};        // resident blocks of the restriction / prolongation
+  int tail_level = -1;                      // first level of the one-block coarse tail (-1: none)
   bool zmarch = false;
   int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep
   CUtensorMap tm_e[2], tm_r, tm_m;

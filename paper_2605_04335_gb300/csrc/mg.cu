@@ -628,6 +628,177 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const u
   }
 }
 
+// ------------------------------------------------------------------ coarse tail
+
+// The V-cycle below the first level of at most TAIL_CELLS cells in one block of
+// TAIL_THREADS threads: the same smoothing, restriction (with the projection shift),
+// coarsest solve and prolongation as the per-level kernels, one pass after another with
+// block barriers instead of kernel launches.  Small levels are latency-bound, so the
+// launches and grid-wide ramps they save dominate.
+constexpr int TAIL_CELLS = 512;
+constexpr int TAIL_THREADS = 1024;
+constexpr int TAIL_MAX_LEVELS = 8;
+
+template <typename T>
+struct TailLevel {
+  LV<T> v;
+  T *e, *r;
+  const int8_t *poff;    // prolongation tables of this level as the fine level (x, y, z)
+  const float *pt;
+};
+
+template <typename T>
+struct TailArgs {
+  TailLevel<T> lv[TAIL_MAX_LEVELS];
+  int nl;                 // levels in the tail (the last one is the coarsest)
+  const double *shift0;   // projection shift of the tail's first level
+  const double *fvol;     // fluid volume of each tail level
+  const T *minv;
+  const int *cidx, *ncoarse;
+  int nu1, nu2;
+  T omega;
+};
+
+// one colour of red-black relaxation of level v, all threads of the block
+template <typename T>
+__device__ void tail_relax(const LV<T> &v, T *e, const T *r, T sh, int colour, T omega) {
+  const int hx = (v.nx + 1) >> 1;
+  const int rows = v.ny * v.nz;
+  const int rstep = hx >= (int)blockDim.x ? 1 : (int)blockDim.x / hx;
+  const int r0 = hx >= (int)blockDim.x ? 0 : (int)threadIdx.x / hx;
+  const int t0 = hx >= (int)blockDim.x ? (int)threadIdx.x : (int)threadIdx.x - r0 * hx;
+  const int tstep = hx >= (int)blockDim.x ? (int)blockDim.x : hx;
+  if (r0 >= rstep) return;
+  for (int row = r0; row < rows; row += rstep) {
+    const int j = row % v.ny, k = row / v.ny;
+    for (int ti = t0; ti < hx; ti += tstep) {
+      const int i = 2 * ti + ((j + k + colour) & 1);
+      if (i >= v.nx) continue;
+      const long long id = vidx(v, i, j, k);
+      if (v.mask[id] != 0) continue;
+      T c[6];
+      coefs(v, i, j, k, id, c);
+      const T D = v.sdx ? (v.sdx[i] + v.sdy[j]) + v.sdz[k] : ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
+      if (D == (T)0) continue;
+      const T res = stencil_sum(v, e, id, c) - D * e[id] - (r[id] - sh);
+      e[id] += (T)__fdividef((float)omega * (float)res, (float)D);
+    }
+  }
+}
+
+// restriction of level f to level c (rc, ec = 0); returns sum V_c rc on thread 0
+template <typename T>
+__device__ double tail_restrict(const LV<T> &f, const T *e, const T *r, T sh, const LV<T> &cv, T *rc, T *ec) {
+  __shared__ double red[TAIL_THREADS / 32];
+  double acc_all = 0.0;
+  const int nc = cv.nx * cv.ny * cv.nz;
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+    const int I = l % cv.nx, q = l / cv.nx, J = q % cv.ny, K = q / cv.ny;
+    const long long ic = vidx(cv, I, J, K);
+    ec[ic] = (T)0;
+    if (cv.mask[ic] != 0) { rc[ic] = (T)0; continue; }
+    T acc = (T)0;
+    for (int c = 0; c < 8; ++c) {
+      const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
+      if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
+      const long long id = vidx(f, i, j, k);
+      if (f.mask[id] != 0) continue;
+      T cf[6];
+      coefs(f, i, j, k, id, cf);
+      const T D = f.sdx ? (f.sdx[i] + f.sdy[j]) + f.sdz[k] : ((cf[0] + cf[1]) + (cf[2] + cf[3])) + (cf[4] + cf[5]);
+      const T res = (r[id] - sh) - (stencil_sum(f, e, id, cf) - D * e[id]);
+      acc += (f.wx[i] * f.wy[j]) * f.wz[k] * res;
+    }
+    rc[ic] = acc / ((cv.wx[I] * cv.wy[J]) * cv.wz[K]);
+    acc_all += (double)acc;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc_all += __shfl_down_sync(0xffffffffu, acc_all, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc_all;
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+  __syncthreads();
+  return sum;
+}
+
+// prolongation e_f += P e_c on the fluid cells of level f (per fine cell)
+template <typename T>
+__device__ void tail_prolong(const LV<T> &cv, const T *ec, const LV<T> &f, T *ef, const int8_t *poff,
+                             const float *pt) {
+  const int nf = f.nx * f.ny * f.nz;
+  const int8_t *offx = poff, *offy = poff + f.nx, *offz = poff + f.nx + f.ny;
+  const float *tx = pt, *ty = pt + f.nx, *tz = pt + f.nx + f.ny;
+  for (int l = threadIdx.x; l < nf; l += blockDim.x) {
+    const int i = l % f.nx, q = l / f.nx, j = q % f.ny, k = q / f.ny;
+    const long long id = vidx(f, i, j, k);
+    if (f.mask[id] != 0) continue;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const float wx[2] = {1.0f - tx[i], tx[i]}, wy[2] = {1.0f - ty[j], ty[j]}, wz[2] = {1.0f - tz[k], tz[k]};
+    const int ox = offx[i], oy = offy[j], oz = offz[k];
+    T s = (T)0;
+    float ws = 0.0f;
+    for (int c = 0; c < 8; ++c) {
+      const int a = c & 1, b = (c >> 1) & 1, d = (c >> 2) & 1;
+      const float w = (wx[a] * wy[b]) * wz[d];
+      if (w == 0.0f) continue;
+      const long long ic = vidx(cv, I + a * ox, J + b * oy, K + d * oz);
+      if (cv.mask[ic] != 0) continue;
+      s += (T)w * ec[ic];
+      ws += w;
+    }
+    if (ws > 0.0f) ef[id] += s * (T)(1.0f / ws);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail(TailArgs<T> A) {
+  __shared__ double shift_s[TAIL_MAX_LEVELS];
+  __shared__ T rs[MAX_COARSE + 1];
+  if (threadIdx.x == 0) shift_s[0] = *A.shift0;
+  __syncthreads();
+  const int last = A.nl - 1;
+  // down: pre-smooth, restrict
+  for (int l = 0; l < last; ++l) {
+    const TailLevel<T> &F = A.lv[l];
+    const T sh = (T)shift_s[l];
+    for (int s = 0; s < A.nu1; ++s)
+      for (int colour = 0; colour < 2; ++colour) {
+        tail_relax(F.v, F.e, F.r, sh, colour, A.omega);
+        __syncthreads();
+      }
+    const TailLevel<T> &C = A.lv[l + 1];
+    const double sum = tail_restrict(F.v, F.e, F.r, sh, C.v, C.r, C.e);
+    if (threadIdx.x == 0) shift_s[l + 1] = A.fvol[l + 1] > 0 ? sum / A.fvol[l + 1] : 0.0;
+    __syncthreads();
+  }
+  // coarsest: e = Minv r (the bordered row's right-hand side is 0)
+  {
+    const TailLevel<T> &Lc = A.lv[last];
+    const int n = *A.ncoarse, m = n + 1;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = Lc.r[A.cidx[q]];
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      T acc = (T)0;
+      for (int c = 0; c < n; ++c) acc += A.minv[q * m + c] * rs[c];
+      Lc.e[A.cidx[q]] = acc;
+    }
+    __syncthreads();
+  }
+  // up: prolong, post-smooth
+  for (int l = last - 1; l >= 0; --l) {
+    const TailLevel<T> &F = A.lv[l], &C = A.lv[l + 1];
+    tail_prolong(C.v, C.e, F.v, F.e, F.poff, F.pt);
+    __syncthreads();
+    const T sh = (T)shift_s[l];
+    for (int s = 0; s < A.nu2; ++s)
+      for (int colour = 0; colour < 2; ++colour) {
+        tail_relax(F.v, F.e, F.r, sh, colour, A.omega);
+        __syncthreads();
+      }
+  }
+}
+
 // bordered coarsest solve: [e; lambda] = Minv [r; 0]
 template <typename T>
 __global__ void k_coarsest(const T *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
@@ -1366,6 +1537,12 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     if (sizeof(T) == 8) setup_zmarch<T>(h, h->p64, h->b64);
     else setup_zmarch<T>(h, L0.e, L0.r);
   }
+  // coarse tail: the first level (below the finest) small enough for one block
+  h->tail_level = -1;
+  for (int l = 1; l < nl; ++l) {
+    const Level &L = h->lv[l];
+    if ((long long)L.g.nx * L.g.ny * L.g.nz <= TAIL_CELLS && nl - l <= TAIL_MAX_LEVELS) { h->tail_level = l; break; }
+  }
   // one wave of the row-strided restriction and prolongation kernels
   {
     int sms = t->ctx->sm_count > 0 ? t->ctx->sm_count : 152, pr = 0, pp = 0;
@@ -1472,6 +1649,8 @@ struct Solver {
   double omega;
   int *d_ncoarse;
   bool dfo = false;   // double-FP32 outer loop (precision mode 2)
+  // measurement only: events recorded on the stream around each fine-level sweep kernel
+  std::vector<cudaEvent_t> *sweep_events = nullptr;
 };
 
 template <typename T>
@@ -1526,9 +1705,12 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
   LV<T> v = view<T>(L);
   dim3 grid(nblk((L.g.nx + 1) / 2, 128), L.g.ny, L.g.nz);
   for (int s = 0; s < sweeps; ++s) {
+    const bool timed = fine && S.sweep_events && S.sweep_events->size() >= 2 * (size_t)(s + 1);
+    if (timed) cudaEventRecord((*S.sweep_events)[2 * s], S.st);
     if (sizeof(T) == 4 && fine && S.h->zmarch) {
       T *old = e;
       sweep_zmarch<T>(S, e, shift);
+      if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
       const long long ng = S.t->nghost;
       if (ng > 0) {
         if (sizeof(T) == 8)
@@ -1543,6 +1725,7 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
     } else {
       for (int colour = 0; colour < 2; ++colour)
         k_rbgs<T><<<grid, 128, 0, S.st>>>(v, e, r, shift, colour, (T)S.omega);
+      if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
       S.ctx->launches += 2;
     }
     if (fine) ghost_update<T>(S, e, ghost_rhs);
@@ -1555,6 +1738,30 @@ template <typename T>
 void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *ghost_rhs) {
   Hierarchy *h = S.h;
   const int nl = (int)h->lv.size();
+  if (l > 0 && l == h->tail_level && nl - l >= 2) {
+    // levels l .. nl-1 in one block (e of level l was zeroed by the restriction into it)
+    TailArgs<T> A;
+    A.nl = nl - l;
+    for (int q = 0; q < A.nl; ++q) {
+      Level &L = h->lv[l + q];
+      A.lv[q].v = view<T>(L);
+      A.lv[q].e = (T *)L.e;
+      A.lv[q].r = (T *)L.r;
+      A.lv[q].poff = L.poff;
+      A.lv[q].pt = L.pt;
+    }
+    A.shift0 = shift;
+    A.fvol = h->d_fvol + l;
+    A.minv = (const T *)h->minv;
+    A.cidx = h->cidx;
+    A.ncoarse = S.d_ncoarse;
+    A.nu1 = S.nu1;
+    A.nu2 = S.nu2;
+    A.omega = (T)S.omega;
+    k_tail<T><<<1, TAIL_THREADS, 0, S.st>>>(A);
+    S.ctx->launches += 1;
+    return;
+  }
   if (l == nl - 1) {
     k_coarsest<T><<<1, 128, 0, S.st>>>((const T *)h->minv, h->cidx, S.d_ncoarse, r, e);
     S.ctx->launches += 1;
@@ -1869,18 +2076,38 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   return result;
 }
 
-ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st) {
+ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st,
+                       double *kernel_ms) {
   ibm_status s = build_hierarchy(t, precision, st);
   if (s != IBM_OK) return s;
   Hierarchy *h = t->hier[precision];
   Solver S{ctx, t, h, st, 1, 1, 1.0, h->dncoarse};
   Level &L0 = h->lv[0];
+  std::vector<cudaEvent_t> ev;
+  auto destroy = [&]() { for (cudaEvent_t x : ev) cudaEventDestroy(x); };
+  if (kernel_ms && nsweeps > 0) {
+    ev.resize(2 * (size_t)nsweeps);
+    for (cudaEvent_t &x : ev)
+      if (cudaEventCreate(&x) != cudaSuccess) { x = nullptr; destroy(); return check(cudaGetLastError(), "event"); }
+    S.sweep_events = &ev;
+  }
   if (precision == 0)
     smooth_level<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, true, nullptr, nsweeps);
   else
     smooth_level<float>(S, 0, reinterpret_cast<float *&>(L0.e), (const float *)L0.r, ctx->scal + S_MU, true,
                         (const float *)L0.r, nsweeps);
-  IBM_TRY(cudaGetLastError());
+  cudaError_t ce = cudaGetLastError();
+  if (ce == cudaSuccess && kernel_ms) {
+    *kernel_ms = 0.0;
+    ce = cudaStreamSynchronize(st);
+    for (int q = 0; q < nsweeps && ce == cudaSuccess; ++q) {
+      float ms = 0.f;
+      ce = cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
+      *kernel_ms += ms / nsweeps;
+    }
+  }
+  destroy();
+  if (ce != cudaSuccess) return check(ce, "smoother sweeps");
   return IBM_OK;
 }
 

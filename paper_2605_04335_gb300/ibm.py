@@ -78,6 +78,7 @@ def load_library():
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
+        "ibm_smoother_sweeps_timed": (I32, [P, P, I32, I32, P, C.POINTER(C.c_double)]),
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
         "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P,
                                             C.POINTER(C.c_double), P]),
@@ -199,6 +200,14 @@ def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, strea
 
 def ibm_smoother_sweeps(ctx, tables, precision: int, nsweeps: int, stream=None):
     _check(load_library().ibm_smoother_sweeps(ctx, tables, precision, nsweeps, _stream(stream)), "ibm_smoother_sweeps")
+
+
+def ibm_smoother_sweeps_timed(ctx, tables, precision: int, nsweeps: int, stream=None) -> float:
+    """Mean duration (ms) of one fine-level sweep's kernel(s), CUDA events on `stream`."""
+    ms = C.c_double()
+    _check(load_library().ibm_smoother_sweeps_timed(ctx, tables, precision, nsweeps, _stream(stream), C.byref(ms)),
+           "ibm_smoother_sweeps_timed")
+    return float(ms.value)
 
 
 def ibm_ctx_launch_count(ctx) -> int:
