@@ -17,8 +17,7 @@ surface; the readings taken here:
   the axis cuts nothing.
 * Side.  side(i) of a cut link is the sign of orient3d(A, B, C, centre i) of the crossing
   triangle (vertex order as given): 1 when positive, 0 otherwise.  When several triangles
-  cross one link, each end takes the crossing nearest to it (lowest triangle index on
-  ties).
+  cross one link, the one with the lowest index decides both ends' sides.
 * Ghost entries.  Every cut link i -> j gives the entry (j, side(i)): the value of cell j
   as seen from i's side.  Entries are unique, ordered by cell, then side.  Fluid row i uses
   g_(j, side(i)) in place of p_j across a cut link.
@@ -46,8 +45,6 @@ normal derivative of a manufactured field vanishes (second order), invariants (A
 and a planted wrong side (tests/test_oracle_membrane.py).
 """
 from __future__ import annotations
-
-from fractions import Fraction
 
 import numpy as np
 import scipy.sparse as sp
@@ -89,7 +86,7 @@ def cut_links(grid: Grid, meshes):
     T = membrane_triangles(meshes)
     cut = np.zeros((nz, ny, nx), dtype=np.uint8)
     side = np.zeros((nz, ny, nx), dtype=np.uint8)
-    # best crossing per (link end): key (axis, lower cell linear index, end) -> (distance, tri, side)
+    # crossing triangle of each link: key (axis, lower cell linear index) -> lowest triangle index
     best = {}
     for a in range(3):
         u_ax, v_ax = (a + 1) % 3, (a + 2) % 3
@@ -127,26 +124,21 @@ def cut_links(grid: Grid, meshes):
                     lo = m - 1
                     if lo < 0 or lo + 1 >= Ca.size or not int(Ca[lo + 1]) > q:
                         continue
-                    # cell indices of the two ends (i, j, k order of the grid axes)
                     ijk = [0, 0, 0]
                     ijk[a], ijk[u_ax], ijk[v_ax] = lo, iu, iv
-                    lin_lo = (ijk[2] * ny + ijk[1]) * nx + ijk[0]
-                    ijk[a] = lo + 1
-                    lin_hi = (ijk[2] * ny + ijk[1]) * nx + ijk[0]
-                    for end, lin, ca in ((0, lin_lo, int(Ca[lo])), (1, lin_hi, int(Ca[lo + 1]))):
-                        dist = Fraction(N, D) - ca if end == 0 else ca - Fraction(N, D)
-                        cc = [int(C[0][lin % nx]), int(C[1][(lin // nx) % ny]), int(C[2][lin // (nx * ny)])]
-                        s = 1 if _orient3d_exact(P[0], P[1], P[2], cc) > 0 else 0
-                        key = (a, lin_lo, end)
-                        cand = (dist, t, s, lin)
-                        if key not in best or (cand[0], cand[1]) < (best[key][0], best[key][1]):
-                            best[key] = cand
+                    key = (a, (ijk[2] * ny + ijk[1]) * nx + ijk[0])
+                    if key not in best or t < best[key]:
+                        best[key] = t
     flat_cut, flat_side = cut.reshape(-1), side.reshape(-1)
-    for (a, _lin_lo, end), (_dist, _t, s, lin) in best.items():
-        d = 2 * a + (1 if end == 0 else 0)        # the lower end looks in +a, the upper in -a
-        flat_cut[lin] |= np.uint8(1 << d)
-        if s:
-            flat_side[lin] |= np.uint8(1 << d)
+    step = (1, nx, nx * ny)
+    for (a, lin_lo), t in best.items():
+        P = [T[t, q] for q in range(3)]
+        for end, lin in ((0, lin_lo), (1, lin_lo + step[a])):
+            cc = [int(C[0][lin % nx]), int(C[1][(lin // nx) % ny]), int(C[2][lin // (nx * ny)])]
+            d = 2 * a + (1 if end == 0 else 0)    # the lower end looks in +a, the upper in -a
+            flat_cut[lin] |= np.uint8(1 << d)
+            if _orient3d_exact(P[0], P[1], P[2], cc) > 0:
+                flat_side[lin] |= np.uint8(1 << d)
     return cut, side
 
 

@@ -28,7 +28,8 @@ def _tilted_plate(nq=4, seed_angle=0.37):
 
 def _brute_cut(grid, mesh):
     """Every (link, triangle) pair in exact rationals: segment-plane crossing strictly inside
-    the triangle and strictly between the centres; side = sign of n . (P - X*)."""
+    the triangle and strictly between the centres; the lowest crossing triangle decides;
+    side = sign of n . (P - X*)."""
     nz, ny, nx = grid.shape
     C = [snap(grid.xc), snap(grid.yc), snap(grid.zc)]
     V = snap(mesh.verts)
@@ -67,14 +68,13 @@ def _brute_cut(grid, mesh):
                         assert s1 != 0 and s2 != 0 and s3 != 0, "tie: choose a more generic plate"
                         if not ((s1 > 0 and s2 > 0 and s3 > 0) or (s1 < 0 and s2 < 0 and s3 < 0)):
                             continue
-                        for end, cell, dist in ((0, tuple(lo), tt), (1, tuple(hi), Q[a] - P[a] - tt)):
+                        for end, cell in ((0, tuple(lo)), (1, tuple(hi))):
                             E = P if end == 0 else Q
                             sg = sum(n[q] * (E[q] - X[q]) for q in range(3))
                             key = (a, tuple(lo), end)
-                            cand = (dist, t, 1 if sg > 0 else 0, cell)
-                            if key not in best or cand[:2] < best[key][:2]:
-                                best[key] = cand
-    for (a, _lo, end), (_dist, _t, s, cell) in best.items():
+                            if key not in best or t < best[key][0]:
+                                best[key] = (t, 1 if sg > 0 else 0, cell)
+    for (a, _lo, end), (_t, s, cell) in best.items():
         dbit = 2 * a + (1 if end == 0 else 0)
         i, j, k = cell
         cut[k, j, i] |= 1 << dbit
