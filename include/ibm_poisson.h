@@ -58,8 +58,11 @@ typedef struct {
 
 /* Triangulated surface (host).  verts: nverts x 3 float64; tris: ntris x 3 int32 vertex
  * indices, counter-clockwise seen from outside.  closed = 1: a watertight solid body
- * (cells whose centre is inside are solid); closed = 0: a zero-thickness membrane
- * (not yet supported: IBM_ERR_NOT_IMPLEMENTED).  Closed meshes must not overlap. */
+ * (cells whose centre is inside are solid); closed = 0: a zero-thickness membrane (every
+ * cell stays fluid; links between face-neighbours that the membrane crosses are cut, and
+ * the cell across a cut link is replaced by a ghost entry of the near side).  Closed meshes
+ * must not overlap; membranes and closed bodies are not mixed in one classification
+ * (IBM_ERR_NOT_IMPLEMENTED). */
 typedef struct {
   int32_t nverts, ntris;
   const double *verts;
@@ -105,12 +108,17 @@ ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device);
 ibm_status ibm_ctx_destroy(ibm_ctx *ctx);
 
 /* Iblanking and ghost-cell tables (paper Sec. "GPU Porting", items 1 and 2).
- * Classifies every cell centre against the closed meshes (solid iff strictly inside a
- * mesh by the exact lattice parity test with half-open tie rules; a centre on the
- * surface is fluid), marks ghost cells (solid with a fluid face-neighbour), and for
- * each ghost computes the boundary intercept BI (closest surface point), the image
- * point IP = 2 BI - GC and its trilinear interpolation row.  nmesh may be 0 (no body).
- * On success *out owns device memory until ibm_tables_destroy. */
+ * Closed meshes: classifies every cell centre (solid iff strictly inside a mesh by the
+ * exact lattice parity test with half-open tie rules; a centre on the surface is fluid),
+ * marks ghost cells (solid with a fluid face-neighbour), and for each ghost computes the
+ * boundary intercept BI (closest surface point), the image point IP = 2 BI - GC and its
+ * trilinear interpolation row.  Membranes (closed = 0): every cell is fluid; a link between
+ * face-neighbours is cut when a triangle crosses it (exact lattice test, lowest crossing
+ * triangle decides), and every cut link i -> j gives the ghost entry (j, side of i), side =
+ * sign of orient3d of the crossing triangle and centre i; entries are ordered by cell, then
+ * side; the IP's corners count only on the entry's side (exact segment tests), blocked
+ * corners through the same-side entry of that cell.  nmesh may be 0 (no body).  On
+ * success *out owns device memory until ibm_tables_destroy. */
 ibm_status ibm_classify(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes,
                         int32_t nmesh, ibm_tables **out, void *stream);
 ibm_status ibm_tables_destroy(ibm_tables *t);
@@ -133,12 +141,14 @@ ibm_status ibm_tables_counts(const ibm_tables *t, int64_t *ncell, int64_t *nflui
                              int64_t *nghost, int64_t *nsolid);
 
 /* Copy the classification out to caller-owned device arrays (any may be NULL):
- *   iblank_dev  uint8[ncell]   0 fluid, 1 solid, 3 ghost (solid | 2)
- *   cell_dev    int64[nghost]  linear cell index of each ghost, ascending
+ *   iblank_dev  uint8[ncell]   0 fluid, 1 solid, 3 ghost (solid | 2); membranes: all 0
+ *   cell_dev    int64[nghost]  linear cell index of each ghost, ascending (membranes: of
+ *                              each entry, ascending, side 0 before side 1)
  *   bi_dev      double[nghost*3], ip_dev double[nghost*3]   (x,y,z)
  *   base_dev    int32[nghost*3]  base corner (i0,j0,k0) of the IP's cell-centre box
  *   flags_dev   int32[nghost]    bit 0: nearest-neighbour fallback; bits 8-15: valid corners
  *   ref_dev     int64[nghost*8]  linear cell index of each interpolation source, -1 unused
+ *                              (membranes: ncell + e refers to ghost entry e)
  *   w_dev       double[nghost*8] weights (sum 1; own weight moved to the left-hand side)
  *   scale_dev   double[nghost]   residual scale of the ghost row
  * Corner slot c = bx + 2 by + 4 bz addresses cell (i0+bx, j0+by, k0+bz). */
@@ -146,6 +156,13 @@ ibm_status ibm_tables_export(const ibm_tables *t, uint8_t *iblank_dev, int64_t *
                              double *bi_dev, double *ip_dev, int32_t *base_dev,
                              int32_t *flags_dev, int64_t *ref_dev, double *w_dev,
                              double *scale_dev, void *stream);
+
+/* Membrane tables only (IBM_ERR_INVALID_ARG otherwise): copy out, to caller-owned device
+ * arrays (any may be NULL), per cell uint8[ncell] cut_dev (bit d set: the link in direction
+ * d = -x, +x, -y, +y, -z, +z is cut) and side_dev (bit d: the cell's side of that link,
+ * 1 = positive orient3d), and per entry uint8[nghost] gside_dev.  Synchronises `stream`. */
+ibm_status ibm_tables_export_membrane(const ibm_tables *t, uint8_t *cut_dev, uint8_t *side_dev,
+                                      uint8_t *gside_dev, void *stream);
 
 void ibm_solve_opts_default(ibm_solve_opts *opts);
 

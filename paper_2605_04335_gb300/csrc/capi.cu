@@ -106,9 +106,22 @@ ibm_status ibm_tables_destroy(ibm_tables *t) {
   cudaDeviceSynchronize();
   for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
   void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref, t->axis,
-                t->scratch};
+                t->scratch, t->cut, t->cside, t->gside, t->gkeys};
   for (void *p : ps) if (p) cudaFree(p);
   delete t;
+  return IBM_OK;
+}
+
+ibm_status ibm_tables_export_membrane(const ibm_tables *t, uint8_t *cut_dev, uint8_t *side_dev, uint8_t *gside_dev,
+                                      void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  if (!t->membrane) return IBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  if (cut_dev) IBM_TRY(cudaMemcpyAsync(cut_dev, t->cut, t->ncell, cudaMemcpyDeviceToDevice, st));
+  if (side_dev) IBM_TRY(cudaMemcpyAsync(side_dev, t->cside, t->ncell, cudaMemcpyDeviceToDevice, st));
+  if (gside_dev && t->nghost > 0) IBM_TRY(cudaMemcpyAsync(gside_dev, t->gside, t->nghost, cudaMemcpyDeviceToDevice, st));
+  IBM_TRY(cudaStreamSynchronize(st));
   return IBM_OK;
 }
 
@@ -164,6 +177,7 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0))
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
+  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   ibm_status s = ibm::solve_impl(ctx, const_cast<ibm_tables *>(t), rhs_dev, tol, p_dev, &o, info, (cudaStream_t)stream);
@@ -173,6 +187,7 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
 
 ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps, void *stream) {
   if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 0) return IBM_ERR_INVALID_ARG;
+  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, nullptr);
 }
@@ -181,6 +196,7 @@ ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t 
                                      void *stream, double *kernel_ms) {
   if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 1 || !kernel_ms)
     return IBM_ERR_INVALID_ARG;
+  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, kernel_ms);
 }
@@ -196,6 +212,7 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
   if (!ctx || n < 0 || (n > 0 && (!tables || !rhs_dev || !p_dev)) || !(tol >= 0.0)) return IBM_ERR_INVALID_ARG;
   for (int p = 0; p < n; ++p) {
     if (!tables[p] || tables[p]->ctx != ctx || !rhs_dev[p] || !p_dev[p]) return IBM_ERR_INVALID_ARG;
+    if (tables[p]->membrane) return IBM_ERR_NOT_IMPLEMENTED;
     for (int q = 0; q < p; ++q)
       if (tables[q] == tables[p]) return IBM_ERR_INVALID_ARG;   // each problem owns its work arrays
     if (infos && infos[p].history_cap > 0 && !infos[p].resid_history) return IBM_ERR_INVALID_ARG;
@@ -223,6 +240,7 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
   if (!ctx || !t || t->ctx != ctx || !rhs_dev || !p_work_dev || !best || precision < 0 || precision > 2 ||
       !(tol > 0.0))
     return IBM_ERR_INVALID_ARG;
+  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   const double omegas[3] = {1.2, 1.3, 1.4};

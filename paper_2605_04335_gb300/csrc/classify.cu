@@ -424,16 +424,9 @@ __device__ __forceinline__ void warp_argmin(double &d, int &t, float &f) {
   (void)f;
 }
 
-__global__ void k_ghost_tables(GhostArgs a) {
-  const int lane = threadIdx.x & 31;
-  long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (g >= a.ng) return;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  long long lin = a.gcell[g];
-  int gi = (int)(lin % nx);
-  int gj = (int)((lin / nx) % ny);
-  int gk = (int)(lin / ((long long)nx * ny));
-  double P[3] = {a.xc[gi], a.yc[gj], a.zc[gk]};
+// closest triangle to P over all meshes of a (lowest index on exact ties): each lane of the
+// warp scans a share, the warp reduces; every lane returns the result
+__device__ void find_closest(const GhostArgs &a, const double P[3], int lane, double &best, int &bidx) {
   float Pf[3] = {(float)P[0], (float)P[1], (float)P[2]};
   // pass 1: an initial candidate from the nearest mesh box, by centroid distance
   int m0 = 0;
@@ -455,9 +448,9 @@ __global__ void k_ghost_tables(GhostArgs a) {
     int ot = __shfl_xor_sync(0xffffffffu, bt, o);
     if (ob < bc || (ob == bc && ot < bt)) { bc = ob; bt = ot; }
   }
-  double best, Q[3];
+  double Q[3];
   closest_on_tri(P, a.tv + 9 * bt, a.tv + 9 * bt + 3, a.tv + 9 * bt + 6, Q, best);
-  int bidx = bt;
+  bidx = bt;
   // pass 2: every triangle whose box could hold a point as close (conservative margin);
   // each lane keeps its own best, then the warp reduces
   double thr = sqrt(best) + 4e-6;
@@ -476,6 +469,21 @@ __global__ void k_ghost_tables(GhostArgs a) {
   }
   float unused = 0.f;
   warp_argmin(best, bidx, unused);
+}
+
+__global__ void k_ghost_tables(GhostArgs a) {
+  const int lane = threadIdx.x & 31;
+  long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (g >= a.ng) return;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  long long lin = a.gcell[g];
+  int gi = (int)(lin % nx);
+  int gj = (int)((lin / nx) % ny);
+  int gk = (int)(lin / ((long long)nx * ny));
+  double P[3] = {a.xc[gi], a.yc[gj], a.zc[gk]};
+  double best;
+  int bidx;
+  find_closest(a, P, lane, best, bidx);
   if (lane != 0) return;
   double BQ[3];
   closest_on_tri(P, a.tv + 9 * bidx, a.tv + 9 * bidx + 3, a.tv + 9 * bidx + 6, BQ, best);
@@ -584,6 +592,339 @@ __global__ void k_gather_tris(const double *verts, const int *tris, int ntri, do
     for (int d = 0; d < 3; ++d) tv[9 * t + 3 * q + d] = verts[3 * tris[3 * t + q] + d];
 }
 
+// -------------------------------------------------------------------------- membranes
+
+// Zero-thickness membranes (closed = 0): every cell is a fluid row; links between
+// face-neighbours that a membrane triangle crosses are cut, and each cut link i -> j gives
+// the ghost entry (j, side of i).  Exact predicates on the snapped lattice, as the
+// closed-body test: a link along axis a is cut when a triangle covers its line in the
+// projection onto the next two axes (cyclic order, counter-clockwise, top-left rule) and
+// the crossing coordinate N / D lies strictly between the two centres; when several
+// triangles cross a link the lowest index decides; side = sign of orient3d(A, B, C, centre)
+// with the vertices in mesh order.
+
+__device__ __forceinline__ __int128 orient3d_i128(const long long a[3], const long long b[3], const long long c[3],
+                                                  const long long d[3]) {
+  const long long abx = b[0] - a[0], aby = b[1] - a[1], abz = b[2] - a[2];
+  const long long acx = c[0] - a[0], acy = c[1] - a[1], acz = c[2] - a[2];
+  const __int128 nx = (__int128)aby * acz - (__int128)abz * acy;
+  const __int128 ny = (__int128)abz * acx - (__int128)abx * acz;
+  const __int128 nz = (__int128)abx * acy - (__int128)aby * acx;
+  return nx * (d[0] - a[0]) + ny * (d[1] - a[1]) + nz * (d[2] - a[2]);
+}
+
+__device__ __forceinline__ void snap_tri(const double *tv, int t, long long v[3][3]) {
+  for (int q = 0; q < 3; ++q)
+    for (int d = 0; d < 3; ++d) v[q][d] = snapd(tv[9 * t + 3 * q + d]);
+}
+
+// "no crossing triangle" in the per-link minimum: the value a byte memset of 0x7f leaves,
+// above every triangle index (the triangle count is below 2^31 / 8)
+constexpr int NO_TRI = 0x7f7f7f7f;
+
+// one (triangle, axis) record of the cut-link search
+struct MTri {
+  long long pu[3], pv[3], pa[3];   // projected vertices (counter-clockwise) and axis coordinates
+  long long area;                  // twice the projected area (> 0)
+  int iu0, iu1, iv0, iv1;          // covered centre lines (half-open) in u and v
+};
+
+struct Axes {
+  const long long *C[3];   // snapped centres per axis
+  int n[3];
+};
+
+__global__ void k_mem_setup(const double *tv, int ntri, Axes ax, MTri *out, long long *count) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= 3 * ntri) return;
+  const int a = p / ntri, t = p - a * ntri, u = (a + 1) % 3, w = (a + 2) % 3;
+  long long v[3][3];
+  snap_tri(tv, t, v);
+  const long long D = orient2d(v[0][u], v[0][w], v[1][u], v[1][w], v[2][u], v[2][w]);
+  MTri M;
+  long long cnt = 0;
+  const int ord[2][3] = {{0, 1, 2}, {0, 2, 1}};
+  const int *o = ord[D > 0 ? 0 : 1];
+  for (int q = 0; q < 3; ++q) { M.pu[q] = v[o[q]][u]; M.pv[q] = v[o[q]][w]; M.pa[q] = v[o[q]][a]; }
+  M.area = D > 0 ? D : -D;
+  const long long ul = min(M.pu[0], min(M.pu[1], M.pu[2])), uh = max(M.pu[0], max(M.pu[1], M.pu[2]));
+  const long long vl = min(M.pv[0], min(M.pv[1], M.pv[2])), vh = max(M.pv[0], max(M.pv[1], M.pv[2]));
+  M.iu0 = lower_bound_dev(ax.C[u], ax.n[u], ul); M.iu1 = upper_bound_dev(ax.C[u], ax.n[u], uh);
+  M.iv0 = lower_bound_dev(ax.C[w], ax.n[w], vl); M.iv1 = upper_bound_dev(ax.C[w], ax.n[w], vh);
+  if (D != 0 && M.iu1 > M.iu0 && M.iv1 > M.iv0) cnt = (long long)(M.iu1 - M.iu0) * (M.iv1 - M.iv0);
+  out[p] = M;
+  count[p] = cnt;
+}
+
+// every (record, line) pair: covering test, crossing, lowest crossing triangle per link
+// (linktri[a * ncell + lower cell])
+__global__ void k_mem_pairs(const MTri *recs, const long long *off, int nrec, long long total, int ntri, Axes ax,
+                            long long ncell, int *linktri) {
+  const int nx = ax.n[0], ny = ax.n[1];
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int r = upper_bound_dev(off, nrec + 1, p) - 1;
+    const MTri &M = recs[r];
+    const int a = r / ntri, t = r - a * ntri, u = (a + 1) % 3, w = (a + 2) % 3;
+    const long long local = p - off[r];
+    const int niu = M.iu1 - M.iu0;
+    const int iu = M.iu0 + (int)(local % niu), iv = M.iv0 + (int)(local / niu);
+    const long long qu = ax.C[u][iu], qv = ax.C[w][iv];
+    const long long wa = orient2d(M.pu[1], M.pv[1], M.pu[2], M.pv[2], qu, qv);
+    const long long wb = orient2d(M.pu[2], M.pv[2], M.pu[0], M.pv[0], qu, qv);
+    const long long wc = orient2d(M.pu[0], M.pv[0], M.pu[1], M.pv[1], qu, qv);
+    const bool cov = (wa > 0 || (wa == 0 && top_left(M.pu[1], M.pv[1], M.pu[2], M.pv[2]))) &&
+                     (wb > 0 || (wb == 0 && top_left(M.pu[2], M.pv[2], M.pu[0], M.pv[0]))) &&
+                     (wc > 0 || (wc == 0 && top_left(M.pu[0], M.pv[0], M.pu[1], M.pv[1])));
+    if (!cov) continue;
+    const __int128 N = (__int128)wa * M.pa[0] + (__int128)wb * M.pa[1] + (__int128)wc * M.pa[2];
+    const __int128 D = (__int128)M.area;
+    __int128 q = N / D;
+    const __int128 rem = N - q * D;
+    if (rem != 0 && N < 0) q -= 1;          // floor division (D > 0)
+    const long long qa = (long long)q;
+    const long long *Ca = ax.C[a];
+    const int na = ax.n[a];
+    const int m = (rem != 0) ? upper_bound_dev(Ca, na, qa) : lower_bound_dev(Ca, na, qa);   // centres < N/D
+    const int lo = m - 1;
+    if (lo < 0 || lo + 1 >= na || !(Ca[lo + 1] > qa)) continue;
+    int ijk[3];
+    ijk[a] = lo; ijk[u] = iu; ijk[w] = iv;
+    const long long lin = ((long long)ijk[2] * ny + ijk[1]) * nx + ijk[0];
+    atomicMin(&linktri[a * ncell + lin], t);
+  }
+}
+
+// cut and side bytes of every cell from its six links
+__global__ void k_mem_cut(const int *linktri, long long ncell, Axes ax, const double *tv, uint8_t *cut,
+                          uint8_t *side) {
+  const int nx = ax.n[0], ny = ax.n[1], nz = ax.n[2];
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < ncell;
+       l += (long long)gridDim.x * blockDim.x) {
+    const int idx[3] = {(int)(l % nx), (int)((l / nx) % ny), (int)(l / ((long long)nx * ny))};
+    const long long step[3] = {1, nx, (long long)nx * ny};
+    const long long P[3] = {ax.C[0][idx[0]], ax.C[1][idx[1]], ax.C[2][idx[2]]};
+    uint8_t c = 0, sd = 0;
+    for (int a = 0; a < 3; ++a) {
+      for (int dir = 0; dir < 2; ++dir) {       // dir 0: -a (link from the lower cell), 1: +a
+        int t;
+        if (dir == 1) t = idx[a] + 1 < ax.n[a] ? linktri[a * ncell + l] : NO_TRI;
+        else t = idx[a] > 0 ? linktri[a * ncell + l - step[a]] : NO_TRI;
+        if (t == NO_TRI) continue;
+        long long v[3][3];
+        snap_tri(tv, t, v);
+        const int bit = 2 * a + dir;
+        c |= (uint8_t)(1u << bit);
+        if (orient3d_i128(v[0], v[1], v[2], P) > 0) sd |= (uint8_t)(1u << bit);
+      }
+    }
+    (void)nz;
+    cut[l] = c;
+    side[l] = sd;
+  }
+}
+
+// entries of cell l: one per side from which a cut link reaches it (bit s of the result)
+__device__ __forceinline__ unsigned entry_sides(uint8_t c, uint8_t sd) {
+  unsigned e = 0;
+  for (int d = 0; d < 6; ++d)
+    if ((c >> d) & 1u) e |= 1u << (1u - ((sd >> d) & 1u));
+  return e;
+}
+
+__global__ void k_mem_count(const uint8_t *cut, const uint8_t *side, long long ncell, long long *bcount) {
+  __shared__ int s[GM_THREADS];
+  const long long base = (long long)blockIdx.x * GM_THREADS * GM_PER + (long long)threadIdx.x * GM_PER;
+  int c = 0;
+  for (int q = 0; q < GM_PER; ++q) {
+    const long long l = base + q;
+    if (l < ncell && cut[l]) c += __popc(entry_sides(cut[l], side[l]));
+  }
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = GM_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bcount[blockIdx.x] = s[0];
+}
+
+// entries in (cell, side) order: cell, side and the sort key 2 cell + side
+__global__ void k_mem_scatter(const uint8_t *cut, const uint8_t *side, long long ncell, const long long *boff,
+                              long long *gcell, uint8_t *gside, long long *keys) {
+  __shared__ int s[GM_THREADS];
+  const long long base = (long long)blockIdx.x * GM_THREADS * GM_PER + (long long)threadIdx.x * GM_PER;
+  int c = 0;
+  for (int q = 0; q < GM_PER; ++q) {
+    const long long l = base + q;
+    if (l < ncell && cut[l]) c += __popc(entry_sides(cut[l], side[l]));
+  }
+  s[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < GM_THREADS; ++t) { int v = s[t]; s[t] = run; run += v; }
+  }
+  __syncthreads();
+  long long o = boff[blockIdx.x] + s[threadIdx.x];
+  for (int q = 0; q < GM_PER; ++q) {
+    const long long l = base + q;
+    if (l >= ncell || !cut[l]) continue;
+    const unsigned e = entry_sides(cut[l], side[l]);
+    for (unsigned sd = 0; sd < 2; ++sd)
+      if ((e >> sd) & 1u) { gcell[o] = l; gside[o] = (uint8_t)sd; keys[o] = 2 * l + sd; ++o; }
+  }
+}
+
+struct MemArgs {
+  long long ncell;
+  const long long *keys;       // 2 cell + side of every entry, ascending
+  const uint8_t *gside, *cut, *side;
+  const long long *Xs, *Ys, *Zs;
+  int ntri;
+};
+
+// is the segment P-Q (snapped) cut by triangle t: endpoints strictly on opposite sides of its
+// plane, and the segment's line through the closed triangle
+__device__ __forceinline__ bool seg_cut_tri(const long long P[3], const long long Q[3], const long long v[3][3]) {
+  const __int128 sp = orient3d_i128(v[0], v[1], v[2], P), sq = orient3d_i128(v[0], v[1], v[2], Q);
+  if (sp == 0 || sq == 0 || (sp > 0) == (sq > 0)) return false;
+  const __int128 e1 = orient3d_i128(P, Q, v[0], v[1]);
+  const __int128 e2 = orient3d_i128(P, Q, v[1], v[2]);
+  const __int128 e3 = orient3d_i128(P, Q, v[2], v[0]);
+  return (e1 >= 0 && e2 >= 0 && e3 >= 0) || (e1 <= 0 && e2 <= 0 && e3 <= 0);
+}
+
+// one warp per entry: boundary intercept and image point (as for closed bodies), corners
+// blocked by the membrane (exact segment tests), same-side entries for blocked corners,
+// weights, fallback and row scale
+__global__ void k_mem_tables(GhostArgs a, MemArgs m) {
+  const int lane = threadIdx.x & 31;
+  const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (g >= a.ng) return;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long lin = a.gcell[g];
+  const unsigned gs = m.gside[g];
+  const int gi = (int)(lin % nx), gj = (int)((lin / nx) % ny), gk = (int)(lin / ((long long)nx * ny));
+  double P[3] = {a.xc[gi], a.yc[gj], a.zc[gk]};
+  double best;
+  int bidx;
+  find_closest(a, P, lane, best, bidx);
+  double BQ[3];
+  closest_on_tri(P, a.tv + 9 * bidx, a.tv + 9 * bidx + 3, a.tv + 9 * bidx + 6, BQ, best);
+  double IP[3];
+  for (int d = 0; d < 3; ++d) IP[d] = (BQ[d] + BQ[d]) - P[d];
+  int i0, j0, k0;
+  double tx, ty, tz;
+  base_t(a.xc, nx, IP[0], i0, tx);
+  base_t(a.yc, ny, IP[1], j0, ty);
+  base_t(a.zc, nz, IP[2], k0, tz);
+  // blocked corners: lanes split the (corner, triangle) pairs whose boxes overlap
+  const long long SIP[3] = {snapd(IP[0]), snapd(IP[1]), snapd(IP[2])};
+  unsigned blocked = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+    const long long Q[3] = {m.Xs[i0 + bx], m.Ys[j0 + by], m.Zs[k0 + bz]};
+    // segment box, widened past the snapping distance (2^-25) and FP32 rounding, so the box
+    // filter never drops a triangle the exact test would count
+    float lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      const double e0 = (double)min(SIP[d], Q[d]) / SNAP_SCALE, e1 = (double)max(SIP[d], Q[d]) / SNAP_SCALE;
+      lo[d] = __double2float_rd(e0 - 1e-6);
+      hi[d] = __double2float_ru(e1 + 1e-6);
+    }
+    bool hit = false;
+    for (int t = lane; t < m.ntri && !hit; t += 32) {
+      const float4 bl = a.blo[t], bh = a.bhi[t];
+      if (bl.x > hi[0] || bh.x < lo[0] || bl.y > hi[1] || bh.y < lo[1] || bl.z > hi[2] || bh.z < lo[2]) continue;
+      long long v[3][3];
+      snap_tri(a.tv, t, v);
+      if (seg_cut_tri(SIP, Q, v)) hit = true;
+    }
+    if (__any_sync(0xffffffffu, hit)) blocked |= 1u << c;
+  }
+  if (lane != 0) return;
+  for (int d = 0; d < 3; ++d) {
+    a.bi[3 * g + d] = BQ[d];
+    a.ip[3 * g + d] = IP[d];
+  }
+  a.base[3 * g + 0] = i0; a.base[3 * g + 1] = j0; a.base[3 * g + 2] = k0;
+  double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
+  double w[8];
+  long long rf[8];
+  unsigned valid = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+    const long long l = ((long long)(k0 + bz) * ny + (j0 + by)) * nx + (i0 + bx);
+    w[c] = (wx[bx] * wy[by]) * wz[bz];
+    if (!((blocked >> c) & 1u)) {
+      rf[c] = l;
+      valid |= 1u << c;
+    } else {
+      const long long key = 2 * l + gs;
+      const int e = lower_bound_dev(m.keys, (int)a.ng, key);
+      if (e < a.ng && m.keys[e] == key) {
+        rf[c] = m.ncell + e;
+        valid |= 1u << c;
+      } else {
+        rf[c] = -1;
+      }
+    }
+  }
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c)
+    if (valid & (1u << c)) s = s + w[c];
+  bool fallback = s < WEIGHT_SUM_MIN;
+  double wn[8];
+  if (!fallback) {
+    for (int c = 0; c < 8; ++c) wn[c] = (valid & (1u << c)) ? w[c] / s : 0.0;
+    int selfc = -1;
+    for (int c = 0; c < 8; ++c)
+      if ((valid & (1u << c)) && rf[c] == m.ncell + g) { selfc = c; break; }
+    if (selfc >= 0) {
+      const double ws = wn[selfc];
+      if (ws >= SELF_WEIGHT_MAX) {
+        fallback = true;
+      } else {
+        for (int c = 0; c < 8; ++c) wn[c] = wn[c] / (1.0 - ws);
+        wn[selfc] = 0.0;
+      }
+    }
+  }
+  // the cells that use the entry: face-neighbours n of the cell cut from side gs (the
+  // cell's own side bit of that link is the other side)
+  const uint8_t cc = m.cut[lin], cs = m.side[lin];
+  const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+  const double *coef[6] = {a.cxp, a.cxm, a.cyp, a.cym, a.czp, a.czm};
+  int flags = 0;
+  double sc = 0.0;
+  long long bestl = -1;
+  double bd = 0.0;
+  for (int d = 0; d < 6; ++d) {
+    if (!((cc >> d) & 1u) || ((cs >> d) & 1u) == gs) continue;
+    const int ii = gi + di[d], jj = gj + dj[d], kk = gk + dk[d];
+    const int ax_idx = d < 2 ? ii : (d < 4 ? jj : kk);
+    sc = sc + coef[d][ax_idx];
+    const double ex = IP[0] - a.xc[ii], ey = IP[1] - a.yc[jj], ez = IP[2] - a.zc[kk];
+    const double d2 = (ex * ex + ey * ey) + ez * ez;
+    if (bestl < 0 || d2 < bd) { bestl = ((long long)kk * ny + jj) * nx + ii; bd = d2; }
+  }
+  if (fallback) {
+    flags |= 1;
+    for (int c = 0; c < 8; ++c) { a.w[8 * g + c] = 0.0; a.ref[8 * g + c] = -1; }
+    a.w[8 * g] = 1.0;
+    a.ref[8 * g] = bestl;
+  } else {
+    flags |= (int)(valid << 8);
+    for (int c = 0; c < 8; ++c) {
+      a.w[8 * g + c] = wn[c];
+      a.ref[8 * g + c] = wn[c] != 0.0 ? rf[c] : -1;
+    }
+  }
+  a.flags[g] = flags;
+  a.scale[g] = sc;
+}
+
 // Device scratch of one tables object.  Allocations are bump pointers into a block the
 // tables keep between classifications; a call that needs more than the block holds takes
 // extra blocks, and when it ends the tables' block is regrown to the whole amount, so
@@ -627,10 +968,12 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 ibm_status check_meshes(const ibm_mesh *meshes, int nmesh, long long &totverts, long long &tottris) {
   if (nmesh < 0 || (nmesh > 0 && !meshes)) return IBM_ERR_INVALID_ARG;
   totverts = tottris = 0;
+  int nclosed = 0;
   for (int m = 0; m < nmesh; ++m) {
     const ibm_mesh &M = meshes[m];
     if (M.nverts < 0 || M.ntris < 0 || (M.ntris > 0 && (!M.verts || !M.tris))) return IBM_ERR_INVALID_ARG;
-    if (M.closed != 1) return IBM_ERR_NOT_IMPLEMENTED;
+    if (M.closed != 0 && M.closed != 1) return IBM_ERR_INVALID_ARG;
+    nclosed += M.closed;
     for (long long q = 0; q < 3LL * M.nverts; ++q)
       if (!(std::fabs(M.verts[q]) <= COORD_LIMIT)) return IBM_ERR_INVALID_ARG;
     for (long long q = 0; q < 3LL * M.ntris; ++q)
@@ -638,6 +981,7 @@ ibm_status check_meshes(const ibm_mesh *meshes, int nmesh, long long &totverts, 
     totverts += M.nverts;
     tottris += M.ntris;
   }
+  if (nclosed != 0 && nclosed != nmesh) return IBM_ERR_NOT_IMPLEMENTED;   // membranes with closed bodies
   return IBM_OK;
 }
 
@@ -645,9 +989,10 @@ ibm_status check_meshes(const ibm_mesh *meshes, int nmesh, long long &totverts, 
 cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
   if (ng <= T->gcap && T->gcell) return cudaSuccess;
   const long long cap = std::max<long long>(std::max<long long>(ng + ng / 4, 1024), T->gcap);
-  void *ps[] = {T->gcell, T->gbi, T->gip, T->gw, T->gscale, T->gbase, T->gflags, T->gref};
+  void *ps[] = {T->gcell, T->gbi, T->gip, T->gw, T->gscale, T->gbase, T->gflags, T->gref, T->gside, T->gkeys};
   for (void *q : ps) if (q) cudaFree(q);
   T->gcell = nullptr; T->gbi = T->gip = T->gw = T->gscale = nullptr; T->gbase = T->gflags = nullptr; T->gref = nullptr;
+  T->gside = nullptr; T->gkeys = nullptr;
   T->gcap = 0;
   cudaError_t e = cudaMalloc(&T->gcell, cap * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&T->gbi, cap * 3 * sizeof(double));
@@ -657,8 +1002,124 @@ cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
   if (e == cudaSuccess) e = cudaMalloc(&T->gbase, cap * 3 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&T->gflags, cap * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&T->gref, cap * 8 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gside, cap);
+  if (e == cudaSuccess) e = cudaMalloc(&T->gkeys, cap * sizeof(long long));
   if (e == cudaSuccess) T->gcap = cap;
   return e;
+}
+
+// Membrane classification (all meshes closed = 0): cut links, ghost entries and their rows.
+ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long long totverts, long long tottris,
+                         cudaStream_t st, Scratch &S, double *const dc[3], double *const dcm[3],
+                         double *const dcp[3], long long *const ds[3]) {
+  const int nx = T->nx, ny = T->ny, nz = T->nz;
+  const long long ncell = T->ncell;
+  ibm_ctx *ctx = T->ctx;
+#define MTRY(call)                                                  \
+  do {                                                              \
+    cudaError_t e__ = (call);                                       \
+    if (e__ != cudaSuccess) return ibm::check(e__, #call);          \
+  } while (0)
+  if (!T->cut) MTRY(cudaMalloc(&T->cut, ncell));
+  if (!T->cside) MTRY(cudaMalloc(&T->cside, ncell));
+  T->nfluid = ncell;
+  T->nsolid = 0;
+  // all membrane triangles, concatenated in mesh order (global triangle index)
+  double *dverts = nullptr, *tv = nullptr;
+  int *dtris = nullptr;
+  MTRY(S.get(&dverts, 3 * totverts));
+  MTRY(S.get(&dtris, 3 * tottris));
+  MTRY(S.get(&tv, 9 * tottris));
+  std::vector<MeshRange> hmr;
+  long long vo = 0, to = 0;
+  for (int m = 0; m < nmesh; ++m) {
+    const int nt = meshes[m].ntris;
+    if (meshes[m].nverts)
+      MTRY(cudaMemcpyAsync(dverts + 3 * vo, meshes[m].verts, 3 * sizeof(double) * meshes[m].nverts,
+                           cudaMemcpyHostToDevice, st));
+    if (nt) {
+      MTRY(cudaMemcpyAsync(dtris + 3 * to, meshes[m].tris, 3 * sizeof(int) * nt, cudaMemcpyHostToDevice, st));
+      k_gather_tris<<<nblk(nt, 128), 128, 0, st>>>(dverts + 3 * vo, dtris + 3 * to, nt, tv + 9 * to);
+      MeshRange r;
+      r.t0 = (int)to; r.t1 = (int)to + nt;
+      for (int d = 0; d < 3; ++d) { r.lo[d] = 1e300; r.hi[d] = -1e300; }
+      for (long long q = 0; q < 3LL * nt; ++q) {
+        const double *v = meshes[m].verts + 3LL * meshes[m].tris[q];
+        for (int d = 0; d < 3; ++d) { r.lo[d] = std::min(r.lo[d], v[d]); r.hi[d] = std::max(r.hi[d], v[d]); }
+      }
+      hmr.push_back(r);
+    }
+    vo += meshes[m].nverts;
+    to += nt;
+  }
+  if (tottris >= NO_TRI) return IBM_ERR_INVALID_ARG;
+  const int ntri = (int)tottris;
+  Axes ax;
+  ax.C[0] = ds[0]; ax.C[1] = ds[1]; ax.C[2] = ds[2];
+  ax.n[0] = nx; ax.n[1] = ny; ax.n[2] = nz;
+  // cut links: lowest crossing triangle per link, then the cells' cut and side bytes
+  int *linktri = nullptr;
+  MTRY(S.get(&linktri, 3 * ncell));
+  MTRY(cudaMemsetAsync(linktri, 0x7f, sizeof(int) * 3 * ncell, st));   // every link: NO_TRI
+  if (ntri > 0) {
+    MTri *recs = nullptr;
+    long long *cnt = nullptr, *off = nullptr;
+    MTRY(S.get(&recs, 3 * (size_t)ntri));
+    MTRY(S.get(&cnt, 3 * (size_t)ntri));
+    MTRY(S.get(&off, 3 * (size_t)ntri + 1));
+    k_mem_setup<<<nblk(3 * ntri, 128), 128, 0, st>>>(tv, ntri, ax, recs, cnt);
+    k_scan_single<<<1, 1024, 0, st>>>(cnt, off, 3 * ntri);
+    long long total = 0;
+    MTRY(cudaMemcpyAsync(&total, off + 3 * ntri, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    MTRY(cudaStreamSynchronize(st));
+    if (total > 0) {
+      const unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 8LL * 152 * 4);
+      k_mem_pairs<<<blocks, 256, 0, st>>>(recs, off, 3 * ntri, total, ntri, ax, ncell, linktri);
+    }
+  }
+  k_mem_cut<<<1216, 256, 0, st>>>(linktri, ncell, ax, tv, T->cut, T->cside);
+  MTRY(cudaGetLastError());
+  // ghost entries in (cell, side) order
+  const long long chunk = (long long)GM_THREADS * GM_PER;
+  const unsigned nb = (unsigned)((ncell + chunk - 1) / chunk);
+  long long *bc = nullptr, *bo = nullptr;
+  MTRY(S.get(&bc, nb));
+  MTRY(S.get(&bo, nb + 1));
+  k_mem_count<<<nb, GM_THREADS, 0, st>>>(T->cut, T->cside, ncell, bc);
+  k_scan_single<<<1, 1024, 0, st>>>(bc, bo, (int)nb);
+  long long ng = 0;
+  MTRY(cudaMemcpyAsync(&ng, bo + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  MTRY(cudaStreamSynchronize(st));
+  T->nghost = ng;
+  MTRY(ensure_ghost_capacity(T, ng));
+  if (ng > 0) {
+    k_mem_scatter<<<nb, GM_THREADS, 0, st>>>(T->cut, T->cside, ncell, bo, T->gcell, T->gside, T->gkeys);
+    float4 *blo = nullptr, *bhi = nullptr, *cen = nullptr;
+    MTRY(S.get(&blo, ntri)); MTRY(S.get(&bhi, ntri)); MTRY(S.get(&cen, ntri));
+    k_tri_boxes<<<nblk(ntri, 128), 128, 0, st>>>(tv, ntri, blo, bhi, cen);
+    MeshRange *dmr = nullptr;
+    MTRY(S.get(&dmr, hmr.size()));
+    MTRY(cudaMemcpyAsync(dmr, hmr.data(), hmr.size() * sizeof(MeshRange), cudaMemcpyHostToDevice, st));
+    GhostArgs ga;
+    ga.nx = nx; ga.ny = ny; ga.nz = nz;
+    ga.xc = dc[0]; ga.yc = dc[1]; ga.zc = dc[2];
+    ga.cxm = dcm[0]; ga.cxp = dcp[0]; ga.cym = dcm[1]; ga.cyp = dcp[1]; ga.czm = dcm[2]; ga.czp = dcp[2];
+    ga.ib = T->iblank;
+    ga.tv = tv; ga.blo = blo; ga.bhi = bhi; ga.cen = cen;
+    ga.mr = dmr; ga.nmesh = (int)hmr.size();
+    ga.ng = ng; ga.gcell = T->gcell;
+    ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
+    ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
+    MemArgs ma;
+    ma.ncell = ncell; ma.keys = T->gkeys; ma.gside = T->gside; ma.cut = T->cut; ma.side = T->cside;
+    ma.Xs = ds[0]; ma.Ys = ds[1]; ma.Zs = ds[2]; ma.ntri = ntri;
+    k_mem_tables<<<nblk(32 * ng, 128), 128, 0, st>>>(ga, ma);
+    MTRY(cudaGetLastError());
+  }
+  MTRY(cudaStreamSynchronize(st));
+  ctx->launches += 4 + (ntri > 0 ? 3 : 0) + (ng > 0 ? 3 : 0);
+#undef MTRY
+  return IBM_OK;
 }
 
 // Classification of the meshes on the tables' grid, into the tables' own arrays.
@@ -707,6 +1168,14 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
   }
   if (!T->iblank) CTRY(cudaMalloc(&T->iblank, ncell));
   CTRY(cudaMemsetAsync(T->iblank, 0, ncell, st));
+  T->membrane = nmesh > 0 && meshes[0].closed == 0;
+  if (T->membrane) {
+    ibm_status ms = membrane_into(T, meshes, nmesh, totverts, tottris, st, S, dc, dcm, dcp, ds);
+    if (ms != IBM_OK) return ms;
+    CTRY(S.finish());
+    T->geom_version += 1;
+    return IBM_OK;
+  }
 
   // inside test per closed mesh
   double *dverts = nullptr;

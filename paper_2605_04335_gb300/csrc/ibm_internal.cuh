@@ -132,6 +132,12 @@ struct ibm_tables {
   int *gbase = nullptr, *gflags = nullptr;
   long long *gref = nullptr;
   long long gcap = 0;                // capacity of the per-ghost arrays (entries)
+  bool membrane = false;             // classified against membranes (closed = 0): all cells fluid,
+                                     // ghost entries are (cell, side) pairs of cut links
+  uint8_t *cut = nullptr, *cside = nullptr;   // membranes: per cell, bit d = link in direction d
+                                              // (-x +x -y +y -z +z) cut / this cell's side of it
+  uint8_t *gside = nullptr;          // membranes: side of each ghost entry
+  long long *gkeys = nullptr;        // membranes: 2 cell + side of each entry (ascending)
   long long geom_version = 0;        // incremented by every classification of these tables
   double *axis = nullptr;            // per-axis faces, centres, widths, coefficients, snapped centres
   char *scratch = nullptr;           // classification scratch kept between classifications

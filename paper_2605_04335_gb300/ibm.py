@@ -75,6 +75,7 @@ def load_library():
         "ibm_tables_destroy": (I32, [P]),
         "ibm_tables_counts": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
         "ibm_tables_export": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
+        "ibm_tables_export_membrane": (I32, [P, P, P, P, P]),
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
@@ -288,6 +289,7 @@ class Tables:
         self.ctx = ctx
         self.shape = (len(zf) - 1, len(yf) - 1, len(xf) - 1)
         self.h = ibm_classify(ctx.h, xf, yf, zf, meshes, stream)
+        self.membrane = len(meshes) > 0 and not int(meshes[0].closed)
         self.ncell, self.nfluid, self.nghost, self.nsolid = ibm_tables_counts(self.h)
 
     def export(self, stream=None) -> dict:
@@ -304,15 +306,23 @@ class Tables:
                "w": torch.empty((ng, 8), dtype=torch.float64, device=dev),
                "scale": torch.empty(ng, dtype=torch.float64, device=dev)}
         ibm_tables_export(self.h, **out, stream=stream)
+        if self.membrane:
+            out["cut"] = torch.empty(self.shape, dtype=torch.uint8, device=dev)
+            out["cside"] = torch.empty(self.shape, dtype=torch.uint8, device=dev)
+            out["side"] = torch.empty(ng, dtype=torch.uint8, device=dev)
+            _check(load_library().ibm_tables_export_membrane(self.h, _ptr(out["cut"]), _ptr(out["cside"]),
+                                                             _ptr(out["side"]), _stream(stream)),
+                   "ibm_tables_export_membrane")
         if self.nghost == 0:
             for k in list(out):
-                if k != "iblank":
+                if k not in ("iblank", "cut", "cside"):
                     out[k] = out[k][:0]
         return out
 
     def reclassify(self, meshes, stream=None):
         """New body positions on the same grid, in the tables' own memory."""
         ibm_reclassify(self.ctx.h, self.h, meshes, stream)
+        self.membrane = len(meshes) > 0 and not int(meshes[0].closed)
         self.ncell, self.nfluid, self.nghost, self.nsolid = ibm_tables_counts(self.h)
 
     def solve(self, rhs, p, tol=1e-10, opts: SolveOpts | None = None, stream=None, **kw):

@@ -1,0 +1,85 @@
+"""GPU membrane classification vs the oracle: cut links, sides, ghost entries and their
+interpolation rows bit for bit (same lattice predicates, same FP64 evaluation order)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import membrane as OM
+from oracle.grid import Grid
+from tests.gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    import paper_2605_04335_gb300 as pkg
+    c = pkg.Context(0)
+    yield pkg, c
+    c.close()
+
+
+def _square_plate(x0, x1, y0, y1, z):
+    V = np.array([[x0, y0, z], [x1, y0, z], [x1, y1, z], [x0, y1, z]])
+    return synth.Mesh(V, np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32), 0)
+
+
+def _tilted_plate(nq=6):
+    m = synth.plate(0.13, chord=0.5, span=0.35, nq_x=nq, nq_y=nq, heave=0.05, pitch_deg=25.0,
+                    center=(0.503, 0.491, 0.517))
+    c, s = np.cos(0.11), np.sin(0.11)
+    R = np.array([[1, 0, 0], [0, c, -s], [0, s, c]])
+    return synth.Mesh((m.verts - 0.5) @ R.T + 0.5, m.tris, 0)
+
+
+def _check(pkg, T, grid, meshes):
+    ib_o, G = OM.classify(grid, meshes)
+    ex = {k: v.cpu().numpy() for k, v in T.export().items()}
+    assert T.membrane and T.nsolid == 0 and T.nfluid == grid.shape[0] * grid.shape[1] * grid.shape[2]
+    assert np.array_equal(ex["iblank"], ib_o)
+    assert np.array_equal(ex["cut"], G.cut)
+    assert np.array_equal(ex["cside"] & ex["cut"], G.cside & G.cut)
+    assert T.nghost == len(G) and len(G) > 0
+    assert np.array_equal(ex["cell"], G.cell)
+    assert np.array_equal(ex["side"], G.side)
+    for k, o in (("bi", G.bi), ("ip", G.ip), ("base", G.base), ("flags", G.flags), ("ref", G.ref), ("w", G.w),
+                 ("scale", G.scale)):
+        assert np.array_equal(ex[k], o), k
+
+
+def test_tilted_plate_ragged_stretched(ctx):
+    pkg, c = ctx
+    xf, yf, zf = synth.faces_tanh(23, 2.0), synth.faces_uniform(19), synth.faces_tanh(27, 1.5)
+    m = [_tilted_plate()]
+    T = pkg.Tables(c, xf, yf, zf, m)
+    _check(pkg, T, Grid(xf, yf, zf), m)
+    T.close()
+
+
+def test_flat_plate_with_lattice_ties(ctx):
+    pkg, c = ctx
+    f = synth.faces_uniform(32)
+    m = [_square_plate(0.25, 0.75, 0.25, 0.75, 0.5)]
+    T = pkg.Tables(c, f, f, f, m)
+    _check(pkg, T, Grid(f, f, f), m)
+    T.close()
+
+
+def test_flapping_plate_phases_and_reclassify(ctx):
+    pkg, c = ctx
+    f = synth.faces_tanh(40, 2.0)
+    grid = Grid(f, f, f)
+    phases = [[synth.plate(q / 8, nq_x=12, nq_y=8)] for q in (0, 3)]
+    T = pkg.Tables(c, f, f, f, phases[0])
+    _check(pkg, T, grid, phases[0])
+    T.reclassify(phases[1])
+    _check(pkg, T, grid, phases[1])
+    T.close()
+
+
+def test_membranes_are_not_mixed_with_closed_bodies(ctx):
+    pkg, c = ctx
+    f = synth.faces_uniform(16)
+    with pytest.raises(pkg.IbmError):
+        pkg.Tables(c, f, f, f, [_tilted_plate(), synth.octa_sphere(3, (0.5, 0.5, 0.2), 0.1)])
