@@ -185,7 +185,8 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
                          double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
                          void *stream);
 
-/* Batched pressure Poisson solves: n independent problems (each its own classified grid,
+/* Batched pressure Poisson solves (precision 0 or 1, closed bodies; membrane tables and
+ * precision 2 return IBM_ERR_NOT_IMPLEMENTED): n independent problems (each its own classified grid,
  * of any size) advanced together, one persistent kernel launch per V-cycle stage over the
  * work of every problem that has that stage; each batched cycle is captured once as a CUDA
  * graph and replayed until every problem reaches tol (a converged problem's work turns

@@ -177,7 +177,6 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0))
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
-  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   ibm_status s = ibm::solve_impl(ctx, const_cast<ibm_tables *>(t), rhs_dev, tol, p_dev, &o, info, (cudaStream_t)stream);
@@ -187,7 +186,6 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
 
 ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps, void *stream) {
   if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 0) return IBM_ERR_INVALID_ARG;
-  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, nullptr);
 }
@@ -196,7 +194,6 @@ ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t 
                                      void *stream, double *kernel_ms) {
   if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 1 || !kernel_ms)
     return IBM_ERR_INVALID_ARG;
-  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, kernel_ms);
 }
@@ -240,7 +237,6 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
   if (!ctx || !t || t->ctx != ctx || !rhs_dev || !p_work_dev || !best || precision < 0 || precision > 2 ||
       !(tol > 0.0))
     return IBM_ERR_INVALID_ARG;
-  if (t->membrane) return IBM_ERR_NOT_IMPLEMENTED;
   IBM_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   const double omegas[3] = {1.2, 1.3, 1.4};

@@ -100,6 +100,20 @@ struct Hierarchy {
   // level-0 unknown (p64 in FP64 mode, lv[0].e in mixed mode) and TMA tensor maps
   void *e_alt = nullptr;
   int grid_blocks[2] = {1216, 1216};        // resident blocks of the restriction / prolongation
+  long long slotcap = 0;                    // membranes: ghost-entry slots after the finest cells
+  long long nslot = 0;                      // elements of the finest arrays (cells + slots); in
+                                            // double-FP32 mode the hi/lo split point of p and b
+  // membranes: cut cells (fluid rows with a cut link), red ones first, each half ascending
+  long long cutcap = 0, parcap = 0;
+  long long *cut_id = nullptr;              // padded index
+  long long *cut_nb = nullptr;              // 6 per cut cell: index of the value each link reads
+  int *cut_ijk = nullptr;                   // 3 per cut cell
+  long long *par_id = nullptr;              // coarse parents of cut cells (padded index, ascending)
+  long long *d_cnt = nullptr;               // device: red cut cells, all cut cells, parents
+  long long hcnt[3] = {0, 0, 0};            // host copy
+  uint8_t *par_flag = nullptr;              // level-1 scratch flags (kept zero between uses)
+  long long *scan_buf = nullptr;            // compaction scratch: block counts and offsets
+  long long scan_cap = 0;
   int tail_level = -1;                      // first level of the one-block coarse tail (-1: none)
   bool zmarch = false;
   int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep

@@ -40,6 +40,10 @@ namespace {
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 constexpr long long GHOST_CORNER = 1LL << 62;   // flag on a ghost-row source that is itself a ghost
+// finest-level mask value of a fluid cell with a cut membrane link: a fluid row whose stencil
+// reads ghost entries, updated by the cut-cell kernels instead of the regular ones
+constexpr uint8_t MASK_CUT = 4;
+__host__ __device__ __forceinline__ bool fluid_row(uint8_t m) { return m == 0 || m == MASK_CUT; }
 
 template <typename T>
 struct LV {          // kernel-side view of one level
@@ -120,11 +124,13 @@ __global__ void k_prolong_axis(const double *cf, int nf, const double *cc, int n
   t[i] = (float)((xf - X) / (cc[nb] - X));
 }
 
-__global__ void k_mask0(const uint8_t *ib, int nx, int ny, int nz, uint8_t *mask, LevelGeom g) {
+// finest-level mask from the classification: iblank, and MASK_CUT for fluid cells with a cut
+// membrane link (cut may be null)
+__global__ void k_mask0(const uint8_t *ib, const uint8_t *cut, int nx, int ny, int nz, uint8_t *mask, LevelGeom g) {
   long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (l >= (long long)nx * ny * nz) return;
   int i = (int)(l % nx); long long r = l / nx; int j = (int)(r % ny); int k = (int)(r / ny);
-  mask[pidx(g, i, j, k)] = ib[l];
+  mask[pidx(g, i, j, k)] = (cut && cut[l] && ib[l] == 0) ? MASK_CUT : ib[l];
 }
 
 __global__ void k_mask_coarse(const uint8_t *mf, LevelGeom gf, uint8_t *mc, LevelGeom gc) {
@@ -134,7 +140,7 @@ __global__ void k_mask_coarse(const uint8_t *mf, LevelGeom gf, uint8_t *mc, Leve
   uint8_t m = 1;
   for (int c = 0; c < 8; ++c) {
     int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
-    if (i < gf.nx && j < gf.ny && k < gf.nz && mf[pidx(gf, i, j, k)] == 0) m = 0;
+    if (i < gf.nx && j < gf.ny && k < gf.nz && fluid_row(mf[pidx(gf, i, j, k)])) m = 0;
   }
   mc[pidx(gc, I, J, K)] = m;
 }
@@ -158,16 +164,18 @@ __global__ void k_inner(const uint8_t *m, LevelGeom g, uint8_t *inner) {
 template <typename T>
 __global__ void k_fractions(const uint8_t *mf, const T *ffx, const T *ffy, const T *ffz, LevelGeom gf,
                             const double *dxf, const double *dyf, const double *dzf, LevelGeom gc,
-                            const double *dxc, const double *dyc, const double *dzc, T *fx, T *fy, T *fz) {
+                            const double *dxc, const double *dyc, const double *dzc, T *fx, T *fy, T *fz,
+                            const uint8_t *cut) {
   long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (l >= (long long)gc.nx * gc.ny * gc.nz) return;
   int I = (int)(l % gc.nx); long long r = l / gc.nx; int J = (int)(r % gc.ny); int K = (int)(r / gc.ny);
   long long ic = pidx(gc, I, J, K);
   auto open_f = [&](int i, int j, int k, int axis) -> double {
     long long id = pidx(gf, i, j, k);
-    if (ffx == nullptr) {
+    if (ffx == nullptr) {   // finest level: open iff both sides are fluid rows and the link is not cut
       long long s = axis == 0 ? 1 : (axis == 1 ? gf.sy : gf.sz);
-      return (mf[id] == 0 && mf[id + s] == 0) ? 1.0 : 0.0;
+      if (cut && ((cut[((long long)k * gf.ny + j) * gf.nx + i] >> (2 * axis + 1)) & 1u)) return 0.0;
+      return (fluid_row(mf[id]) && fluid_row(mf[id + s])) ? 1.0 : 0.0;
     }
     const T *f = axis == 0 ? ffx : (axis == 1 ? ffy : ffz);
     return (double)f[id];
@@ -300,7 +308,7 @@ __global__ void k_fluid_stats(const uint8_t *mask, LevelGeom g, const double *dx
     double sx = 0.0;
     int cnt = 0;
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
-      if (mr[i] == 0) { sx += dx[i]; ++cnt; }
+      if (fluid_row(mr[i])) { sx += dx[i]; ++cnt; }
     v += sx * (dy[j] * dz[k]);
     c += cnt;
   }
@@ -620,7 +628,8 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const u
     for (int d = 0; d < 2; ++d)
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        const bool u0 = fm[d][b].x == 0 && den[d][b][0] > (T)0, u1 = fm[d][b].y == 0 && den[d][b][1] > (T)0;
+        const bool u0 = fluid_row(fm[d][b].x) && den[d][b][0] > (T)0,
+                   u1 = fluid_row(fm[d][b].y) && den[d][b][1] > (T)0;
         T *rowp = ef + fr[d][b];
         if (u0) rowp[0] = fe[d][b][0] + num[d][b][0] / den[d][b][0];
         if (u1) rowp[1] = fe[d][b][1] + num[d][b][1] / den[d][b][1];
@@ -851,9 +860,15 @@ template <> struct Vec4<double> {
   }
 };
 
+// regular fluid rows (mask 0) of four cells
 __device__ __forceinline__ void ld_mask4(const uint8_t *m, bool fl[4]) {
   const uchar4 q = *reinterpret_cast<const uchar4 *>(m);
   fl[0] = q.x == 0; fl[1] = q.y == 0; fl[2] = q.z == 0; fl[3] = q.w == 0;
+}
+// all fluid rows (mask 0 or MASK_CUT) of four cells
+__device__ __forceinline__ void ld_fluid4(const uint8_t *m, bool fl[4]) {
+  const uchar4 q = *reinterpret_cast<const uchar4 *>(m);
+  fl[0] = fluid_row(q.x); fl[1] = fluid_row(q.y); fl[2] = fluid_row(q.z); fl[3] = fluid_row(q.w);
 }
 
 // block reduction of three doubles into partials[3 b + q]
@@ -968,12 +983,18 @@ __global__ void k_ghost_resid64(const long long *src, const long long *dst, cons
 
 // mu = sum V r / V_F; ||S P r||^2 = sum r^2 - 2 mu sum r + N_F mu^2 + sum (s r_G)^2;
 // lambda += mu when update_lambda
+// (cpart, ncb: block partials of the membrane cut cells, same layout as partials; ncb may be 0)
 __global__ void k_finalize_resid(const double *partials, int nb, const double *gpart, int ngb, double *scal,
-                                 int update_lambda) {
+                                 int update_lambda, const double *cpart, int ncb) {
   double sv = block_sum_partials(partials, nb, 3, 0);
   double s1 = block_sum_partials(partials, nb, 3, 1);
   double s2 = block_sum_partials(partials, nb, 3, 2);
   double sg = ngb > 0 ? block_sum_partials(gpart, ngb, 1, 0) : 0.0;
+  if (ncb > 0) {
+    sv += block_sum_partials(cpart, ncb, 3, 0);
+    s1 += block_sum_partials(cpart, ncb, 3, 1);
+    s2 += block_sum_partials(cpart, ncb, 3, 2);
+  }
   if (threadIdx.x == 0) {
     double mu = sv / scal[S_FLUIDVOL];
     double n2 = s2 - 2.0 * mu * s1 + scal[S_NF] * mu * mu;
@@ -1002,7 +1023,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum(LV<double> v, cons
       for (int g = rg.g0; g < rg.G; g += rg.gstep) {
         const long long id = base + 4 * g;
         bool fl[4];
-        ld_mask4(v.mask + id, fl);
+        ld_fluid4(v.mask + id, fl);
         double P[4];
         Vec4<double>::ld(p + id, P);
 #pragma unroll
@@ -1290,7 +1311,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum_df(DfView v, const
       for (int g = rg.g0; g < rg.G; g += rg.gstep) {
         const long long id = base + 4 * g;
         bool fl[4];
-        ld_mask4(v.mask + id, fl);
+        ld_fluid4(v.mask + id, fl);
         float PH[4], PL[4];
         Vec4<float>::ld(ph + id, PH);
         Vec4<float>::ld(pl + id, PL);
@@ -1344,8 +1365,318 @@ __global__ void k_unpack_gauge_df(const float *ph, const float *pl, const uint8_
   }
 }
 
+// ------------------------------------------------------------------ membrane cut cells
+
+// Fluid cells with a cut membrane link (mask MASK_CUT) read a ghost entry across that link
+// instead of the neighbour.  The regular kernels leave them alone; these kernels relax them
+// after each fine sweep, form their outer residuals and add their restriction.  The cut
+// cells are listed red first, then black, each half ascending; cut_nb holds, per cell and
+// direction (-x +x -y +y -z +z), the index of the value the link reads (a padded cell, or
+// ntot + e for entry e).
+
+constexpr int CUT_THREADS = 256, CUT_PER = 16;   // compaction: cells per thread, contiguous
+constexpr int CUT_BLOCKS = 152;                  // grid of the cut-cell kernels (grid-stride)
+
+// exclusive scan of n int64 counts in one block; out has n+1 entries
+__global__ void k_scan1(const long long *in, long long *out, int n) {
+  __shared__ long long part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (n + nt - 1) / nt;
+  const int b = tid * per, e = min(n, b + per);
+  long long s = 0;
+  for (int i = b; i < e; ++i) s += in[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    long long run = 0;
+    for (int i = 0; i < nt; ++i) { long long v = part[i]; part[i] = run; run += v; }
+    out[n] = run;
+  }
+  __syncthreads();
+  long long run = part[tid];
+  for (int i = b; i < e; ++i) { out[i] = run; run += in[i]; }
+}
+
+// cells of one colour ((i + j + k) mod 2) with a cut link, per block of CUT_THREADS x CUT_PER
+__global__ void k_cut_count(const uint8_t *cut, const uint8_t *ib, int nx, int ny, long long ncell, int colour,
+                            long long *bcount) {
+  __shared__ int s[CUT_THREADS];
+  const long long base = (long long)blockIdx.x * CUT_THREADS * CUT_PER + (long long)threadIdx.x * CUT_PER;
+  int c = 0;
+  for (int q = 0; q < CUT_PER; ++q) {
+    const long long l = base + q;
+    if (l >= ncell || !cut[l] || ib[l] != 0) continue;
+    const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+    if (((i + j + k) & 1) == colour) ++c;
+  }
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = CUT_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bcount[blockIdx.x] = s[0];
+}
+
+// the cut cells of one colour in ascending order, from output offset base0; per cell its
+// padded index, (i, j, k) and the value index of each link
+__global__ void k_cut_scatter(const uint8_t *cut, const uint8_t *side, const uint8_t *ib, LevelGeom g,
+                              long long ncell, int colour, const long long *boff, long long base0,
+                              const long long *keys, long long nentry, long long *cut_id, int *cut_ijk,
+                              long long *cut_nb) {
+  __shared__ int s[CUT_THREADS];
+  const int nx = g.nx, ny = g.ny;
+  const long long base = (long long)blockIdx.x * CUT_THREADS * CUT_PER + (long long)threadIdx.x * CUT_PER;
+  int c = 0;
+  for (int q = 0; q < CUT_PER; ++q) {
+    const long long l = base + q;
+    if (l >= ncell || !cut[l] || ib[l] != 0) continue;
+    const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+    if (((i + j + k) & 1) == colour) ++c;
+  }
+  s[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < CUT_THREADS; ++t) { int v = s[t]; s[t] = run; run += v; }
+  }
+  __syncthreads();
+  long long o = base0 + boff[blockIdx.x] + s[threadIdx.x];
+  const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+  for (int q = 0; q < CUT_PER; ++q) {
+    const long long l = base + q;
+    if (l >= ncell || !cut[l] || ib[l] != 0) continue;
+    const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+    if (((i + j + k) & 1) != colour) continue;
+    cut_id[o] = pidx(g, i, j, k);
+    cut_ijk[3 * o] = i; cut_ijk[3 * o + 1] = j; cut_ijk[3 * o + 2] = k;
+    for (int d = 0; d < 6; ++d) {
+      const int ii = i + di[d], jj = j + dj[d], kk = k + dk[d];
+      long long v = pidx(g, ii, jj, kk);   // halo cells (zero, coefficient 0) stay as they are
+      if ((cut[l] >> d) & 1u) {
+        const long long nb = ((long long)kk * ny + jj) * nx + ii;
+        const long long key = 2 * nb + ((side[l] >> d) & 1u);
+        long long lo = 0, hi = nentry;    // the entry (neighbour, this cell's side) exists
+        while (lo < hi) {
+          const long long mid = (lo + hi) >> 1;
+          if (keys[mid] >= key) hi = mid; else lo = mid + 1;
+        }
+        v = g.ntot + lo;
+      }
+      cut_nb[6 * o + d] = v;
+    }
+    ++o;
+  }
+}
+
+// coarse parents of cut cells: flag, then compact in ascending order
+__global__ void k_par_flag(const long long *cut_id, const int *cut_ijk, const long long *cnt, LevelGeom gc,
+                           uint8_t *flag) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt[1];
+       q += (long long)gridDim.x * blockDim.x)
+    flag[pidx(gc, cut_ijk[3 * q] >> 1, cut_ijk[3 * q + 1] >> 1, cut_ijk[3 * q + 2] >> 1)] = 1;
+  (void)cut_id;
+}
+
+__global__ void k_par_count(const uint8_t *flag, long long n, long long *bcount) {
+  __shared__ int s[CUT_THREADS];
+  const long long base = (long long)blockIdx.x * CUT_THREADS * CUT_PER + (long long)threadIdx.x * CUT_PER;
+  int c = 0;
+  for (int q = 0; q < CUT_PER; ++q) c += (base + q < n && flag[base + q]) ? 1 : 0;
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = CUT_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bcount[blockIdx.x] = s[0];
+}
+
+__global__ void k_par_scatter(uint8_t *flag, long long n, const long long *boff, long long *par_id) {
+  __shared__ int s[CUT_THREADS];
+  const long long base = (long long)blockIdx.x * CUT_THREADS * CUT_PER + (long long)threadIdx.x * CUT_PER;
+  int c = 0;
+  for (int q = 0; q < CUT_PER; ++q) c += (base + q < n && flag[base + q]) ? 1 : 0;
+  s[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < CUT_THREADS; ++t) { int v = s[t]; s[t] = run; run += v; }
+  }
+  __syncthreads();
+  long long o = boff[blockIdx.x] + s[threadIdx.x];
+  for (int q = 0; q < CUT_PER; ++q)
+    if (base + q < n && flag[base + q]) { par_id[o++] = base + q; flag[base + q] = 0; }
+}
+
+// one colour of relaxation of the cut cells (red: list [0, cnt[0]), black: [cnt[0], cnt[1])):
+// neighbours from e, entries from eg (the buffer holding the current entry values)
+template <typename T>
+__global__ void k_cut_relax(const long long *cut_id, const long long *cut_nb, const int *cut_ijk,
+                            const long long *cnt, int colour, LV<T> v, T *e, const T *eg, const T *r,
+                            const double *shift, T omega) {
+  const long long b = colour ? cnt[0] : 0, n = colour ? cnt[1] : cnt[0];
+  const T sh = shift ? (T)(*shift) : (T)0;
+  const long long ntot = (long long)(v.nz + 2) * v.sz;
+  for (long long q = b + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long id = cut_id[q];
+    const int i = cut_ijk[3 * q], j = cut_ijk[3 * q + 1], k = cut_ijk[3 * q + 2];
+    const T c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
+    T s = (T)0;
+    for (int d = 0; d < 6; ++d) {
+      const long long x = cut_nb[6 * q + d];
+      s += c[d] * (x >= ntot ? eg[x] : e[x]);
+    }
+    const T D = (v.sdx[i] + v.sdy[j]) + v.sdz[k];
+    const T res = s - D * e[id] - (r[id] - sh);
+    e[id] += (T)__fdividef((float)omega * (float)res, (float)D);
+  }
+}
+
+// outer residual of the cut cells in FP64: r32 and block partials (V r, r, r^2) at
+// part[3 b + {0,1,2}] (p == nullptr: residual of p = 0)
+__global__ void __launch_bounds__(256) k_cut_resid64(const long long *cut_id, const long long *cut_nb,
+                                                     const int *cut_ijk, const long long *cnt, LV<double> v,
+                                                     const double *p, const double *bb, const double *lambda,
+                                                     const float *wf, float *r32, double *part) {
+  __shared__ double sm[3][256];
+  const double lam = *lambda;
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  const int nx = v.nx, ny = v.ny;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt[1];
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long id = cut_id[q];
+    const int i = cut_ijk[3 * q], j = cut_ijk[3 * q + 1], k = cut_ijk[3 * q + 2];
+    double res = bb[id] - lam;
+    if (p) {
+      const double c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
+      double s = 0.0;
+      for (int d = 0; d < 6; ++d) s = fma(c[d], p[cut_nb[6 * q + d]], s);
+      s = fma(-((v.sdx[i] + v.sdy[j]) + v.sdz[k]), p[id], s);
+      res -= s;
+    }
+    const float rf = (float)res;
+    if (r32) r32[id] = rf;
+    const double V = (double)(wf[i] * (wf[nx + j] * wf[nx + ny + k]));
+    A0 += V * rf; A1 += rf; A2 += (double)rf * rf;
+  }
+  sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int w = 0; w < 3; ++w) sm[w][threadIdx.x] += sm[w][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 3; ++w) part[3 * blockIdx.x + w] = sm[w][0];
+}
+
+// the same in double-FP32 (outer arrays split into hi and lo at offset nsplit)
+__global__ void __launch_bounds__(256) k_cut_resid_df(const long long *cut_id, const long long *cut_nb,
+                                                      const int *cut_ijk, const long long *cnt, DfView v,
+                                                      const float *ph, const float *pl, const float *bh,
+                                                      const float *bl, const double *lambda, float *r32,
+                                                      double *part) {
+  __shared__ double sm[3][256];
+  float lh, ll;
+  dfl::split(*lambda, lh, ll);
+  double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+  const int nx = v.nx, ny = v.ny, n = nx + ny + v.nz;
+  const float *H = v.h, *L = v.l;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt[1];
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long id = cut_id[q];
+    const int i = cut_ijk[3 * q], j = cut_ijk[3 * q + 1], k = cut_ijk[3 * q + 2];
+    float sh, sl;
+    dfl::two_sum(bh[id], -lh, sh, sl);
+    sl += bl[id] - ll;
+    if (ph) {
+      const int ci[6] = {i, nx + i, 2 * nx + j, 2 * nx + ny + j, 2 * nx + 2 * ny + k, 2 * nx + 2 * ny + v.nz + k};
+      float dh, dl, th, tl;   // diagonal sdx_i + sdy_j + sdz_k
+      dfl::two_sum(H[2 * n + i], H[2 * n + nx + j], dh, dl);
+      dl += L[2 * n + i] + L[2 * n + nx + j];
+      dfl::two_sum(dh, H[2 * n + nx + ny + k], th, tl);
+      tl += dl + L[2 * n + nx + ny + k];
+      dfl::acc_prod(th, tl, ph[id], pl[id], sh, sl);
+      for (int d = 0; d < 6; ++d) {
+        const long long x = cut_nb[6 * q + d];
+        dfl::acc_prod(-H[ci[d]], -L[ci[d]], ph[x], pl[x], sh, sl);
+      }
+    }
+    const float rf = sh + sl;
+    if (r32) r32[id] = rf;
+    const double V = (double)(H[3 * n + i] * (H[3 * n + nx + j] * H[3 * n + nx + ny + k]));
+    A0 += V * rf; A1 += rf; A2 += (double)rf * rf;
+  }
+  sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int w = 0; w < 3; ++w) sm[w][threadIdx.x] += sm[w][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 3; ++w) part[3 * blockIdx.x + w] = sm[w][0];
+}
+
+// restriction of the cut cells (the regular restriction skips them): per coarse parent, its
+// cut children's V_f (r - shift - (A e)_f) in child order, added to rc as / V_c; block
+// partials of those sums at part[b]
+template <typename T>
+__global__ void __launch_bounds__(256) k_cut_restrict(const long long *par_id, const long long *cnt,
+                                                      const long long *cut_id, const long long *cut_nb,
+                                                      LV<T> f, const T *e, const T *r, const double *shift,
+                                                      LV<T> cv, T *rc, double *part) {
+  __shared__ double sm[256];
+  double acc_all = 0.0;
+  const T sh = shift ? (T)(*shift) : (T)0;
+  const long long ntot = (long long)(f.nz + 2) * f.sz;
+  const long long nred = cnt[0], ncut = cnt[1];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt[2];
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long ic = par_id[q];
+    const int I = (int)(ic % cv.px) - OX, J = (int)((ic / cv.px) % (cv.ny + 2)) - 1,
+              K = (int)(ic / ((long long)cv.px * (cv.ny + 2))) - 1;
+    T acc = (T)0;
+    for (int c = 0; c < 8; ++c) {
+      const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + ((c >> 2) & 1);
+      if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
+      const long long id = vidx(f, i, j, k);
+      if (f.mask[id] != MASK_CUT) continue;
+      // the cut cell's list position: binary search in its colour's half
+      long long lo = ((i + j + k) & 1) ? nred : 0, hi = ((i + j + k) & 1) ? ncut : nred;
+      while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (cut_id[mid] >= id) hi = mid; else lo = mid + 1;
+      }
+      const T cf[6] = {f.cxm[i], f.cxp[i], f.cym[j], f.cyp[j], f.czm[k], f.czp[k]};
+      T s = (T)0;
+      for (int d = 0; d < 6; ++d) s += cf[d] * e[cut_nb[6 * lo + d]];
+      const T D = (f.sdx[i] + f.sdy[j]) + f.sdz[k];
+      const T res = (r[id] - sh) - (s - D * e[id]);
+      acc += (f.wx[i] * f.wy[j]) * f.wz[k] * res;
+    }
+    rc[ic] += acc / ((cv.wx[I] * cv.wy[J]) * cv.wz[K]);
+    acc_all += (double)acc;
+  }
+  (void)ntot;
+  sm[threadIdx.x] = acc_all;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// solver-side ghost rows: padded source and destination indices.  Closed bodies: a ghost
+// lives at its (solid) cell, a source that is itself a ghost is flagged GHOST_CORNER.
+// Membranes: entry e lives in slot ntot + e after the padded cells; a reference >= ncell is
+// an entry (flagged); every other reference is a fluid cell.
 __global__ void k_ghost_src(const long long *ref, const long long *cell, long long ng, LevelGeom g, long long *src,
-                            long long *dst, const double *w, float *w32, const uint8_t *ib) {
+                            long long *dst, const double *w, float *w32, const uint8_t *ib, int membrane,
+                            long long ncell) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= ng * 8) return;
   auto tp = [&](long long l) {
@@ -1353,9 +1684,11 @@ __global__ void k_ghost_src(const long long *ref, const long long *cell, long lo
     return pidx(g, i, j, k);
   };
   long long l = ref[q];
-  src[q] = l >= 0 ? (tp(l) | (ib[l] == 3 ? GHOST_CORNER : 0LL)) : -1;
+  if (l < 0) src[q] = -1;
+  else if (membrane) src[q] = l >= ncell ? ((g.ntot + (l - ncell)) | GHOST_CORNER) : tp(l);
+  else src[q] = tp(l) | (ib[l] == 3 ? GHOST_CORNER : 0LL);
   w32[q] = (float)w[q];
-  if ((q & 7) == 0) dst[q >> 3] = tp(cell[q >> 3]);
+  if ((q & 7) == 0) dst[q >> 3] = membrane ? g.ntot + (q >> 3) : tp(cell[q >> 3]);
 }
 
 template <typename T>
@@ -1375,8 +1708,9 @@ void free_hierarchy(Hierarchy *h) {
     ps.insert(ps.end(), q, q + 14);
   }
   void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
-               h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng};
-  ps.insert(ps.end(), q, q + 18);
+               h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng,
+               h->cut_id, h->cut_nb, h->cut_ijk, h->par_id, h->d_cnt, h->par_flag, h->scan_buf};
+  ps.insert(ps.end(), q, q + 25);
   std::sort(ps.begin(), ps.end());
   ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
   for (void *p : ps) if (p) cudaFree(p);
@@ -1441,6 +1775,10 @@ template <typename T>
 static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) {
   Hierarchy *h = new Hierarchy();
   h->elem = sizeof(T);
+  // membranes: one slot per ghost entry after the finest level's padded cells (capacity
+  // rounded to 16 elements, so the level-0 arrays stay a multiple of 16 long)
+  const long long slotcap = t->membrane ? (std::max<long long>(t->gcap, 1024) + 15) / 16 * 16 : 0;
+  h->slotcap = slotcap;
   auto fail = [&](cudaError_t e, const char *w) { free_hierarchy(h); return check(e, w); };
 #define HTRY(call) do { cudaError_t e__ = (call); if (e__ != cudaSuccess) return fail(e__, #call); } while (0)
   // level faces on the host, then one device copy of all of them
@@ -1478,8 +1816,10 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
     HTRY(cudaMalloc((void **)&L.mask, L.g.ntot));
     HTRY(cudaMemsetAsync(L.mask, 1, L.g.ntot, st));
-    HTRY(alloc_zero<T>(&L.e, L.g.ntot, st));
-    HTRY(alloc_zero<T>(&L.r, L.g.ntot, st));
+    // the finest level's arrays end with one slot per membrane ghost entry
+    const long long nel = l == 0 ? L.g.ntot + slotcap : L.g.ntot;
+    HTRY(alloc_zero<T>(&L.e, nel, st));
+    HTRY(alloc_zero<T>(&L.r, nel, st));
     HTRY(cudaMalloc(&L.c1d, sizeof(T) * 2 * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.w1d, sizeof(double) * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.cen, sizeof(double) * (nx + ny + nz)));
@@ -1497,6 +1837,7 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
                                                     wt + nx + ny, sd ? sd + nx + ny : nullptr);
     HTRY(cudaGetLastError());
   }
+  h->nslot = h->lv[0].g.ntot + slotcap;
   for (int l = 0; l + 1 < nl; ++l) {
     Level &Fl = h->lv[l], &C = h->lv[l + 1];
     HTRY(alloc_zero<uint8_t>((void **)&C.inner, C.g.ntot, st));
@@ -1521,14 +1862,15 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     HTRY(cudaMalloc((void **)&h->dncoarse, sizeof(int) * 2));
     HTRY(cudaMalloc((void **)&h->d_fvol, sizeof(double) * nl));
     HTRY(cudaMalloc((void **)&h->d_ng, sizeof(long long)));
+    HTRY(alloc_zero<long long>((void **)&h->d_cnt, 3, st));
     if (sizeof(T) * m * 2 * m > GJ_SMEM_MAX) HTRY(cudaMalloc(&h->gj, sizeof(T) * m * 2 * m));
   }
   // fine outer arrays and the fused sweep's second buffer
   {
     Level &L0 = h->lv[0];
-    HTRY(alloc_zero<double>((void **)&h->p64, L0.g.ntot, st));
-    HTRY(alloc_zero<double>((void **)&h->b64, L0.g.ntot, st));
-    HTRY(alloc_zero<T>(&h->e_alt, L0.g.ntot, st));
+    HTRY(alloc_zero<double>((void **)&h->p64, h->nslot, st));
+    HTRY(alloc_zero<double>((void **)&h->b64, h->nslot, st));
+    HTRY(alloc_zero<T>(&h->e_alt, h->nslot, st));
   }
   HTRY(cudaStreamSynchronize(st));
   free_faces();
@@ -1565,7 +1907,8 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
   Level &L0 = h->lv[0];
   {
     const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
-    k_mask0<<<nblk(n0, 256), 256, 0, st>>>(t->iblank, L0.g.nx, L0.g.ny, L0.g.nz, L0.mask, L0.g);
+    k_mask0<<<nblk(n0, 256), 256, 0, st>>>(t->iblank, t->membrane ? t->cut : nullptr, L0.g.nx, L0.g.ny, L0.g.nz,
+                                           L0.mask, L0.g);
   }
   for (int l = 0; l + 1 < nl; ++l) {
     Level &Fl = h->lv[l], &C = h->lv[l + 1];
@@ -1575,7 +1918,8 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
     const double *wf = Fl.w1d, *wc = C.w1d;
     k_fractions<T><<<nblk(nc, 256), 256, 0, st>>>(Fl.mask, (const T *)Fl.fx, (const T *)Fl.fy, (const T *)Fl.fz, Fl.g,
                                                   wf, wf + Fl.g.nx, wf + Fl.g.nx + Fl.g.ny, C.g, wc, wc + C.g.nx,
-                                                  wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz);
+                                                  wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz,
+                                                  l == 0 && t->membrane ? t->cut : nullptr);
   }
   IBM_TRY(cudaGetLastError());
   // fluid volume and count per level (one read-back for all levels)
@@ -1628,8 +1972,69 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
     }
     h->gw64 = nullptr;
     if (ng) k_ghost_src<<<nblk(8 * ng, 256), 256, 0, st>>>(t->gref, t->gcell, ng, L0.g, h->gsrc, h->gdst, t->gw, h->gw32,
-                                                         t->iblank);
+                                                         t->iblank, t->membrane ? 1 : 0, t->ncell);
     IBM_TRY(cudaMemcpyAsync(h->d_ng, &t->nghost, sizeof(long long), cudaMemcpyHostToDevice, st));
+    IBM_TRY(cudaGetLastError());
+  }
+  // membranes: the cut cells (red, then black) and their coarse parents
+  h->hcnt[0] = h->hcnt[1] = h->hcnt[2] = 0;
+  if (t->membrane && nl >= 2) {
+    const long long ncell = t->ncell;
+    const long long chunk = (long long)CUT_THREADS * CUT_PER;
+    const unsigned nb = (unsigned)((ncell + chunk - 1) / chunk);
+    Level &L1 = h->lv[1];
+    const unsigned nbp = (unsigned)((L1.g.ntot + chunk - 1) / chunk);
+    const long long need = std::max<long long>(nb, nbp) + 1;
+    if (h->scan_cap < need) {
+      if (h->scan_buf) cudaFree(h->scan_buf);
+      h->scan_buf = nullptr; h->scan_cap = 0;
+      IBM_TRY(cudaMalloc((void **)&h->scan_buf, sizeof(long long) * 4 * need));
+      h->scan_cap = need;
+    }
+    long long *bc = h->scan_buf, *bo[2] = {h->scan_buf + 2 * need, h->scan_buf + 3 * need};
+    long long counts[2];
+    for (int colour = 0; colour < 2; ++colour) {
+      k_cut_count<<<nb, CUT_THREADS, 0, st>>>(t->cut, t->iblank, L0.g.nx, L0.g.ny, ncell, colour, bc + colour * need);
+      k_scan1<<<1, 1024, 0, st>>>(bc + colour * need, bo[colour], (int)nb);
+    }
+    IBM_TRY(cudaMemcpyAsync(&counts[0], bo[0] + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaMemcpyAsync(&counts[1], bo[1] + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    const long long ncut = counts[0] + counts[1];
+    if (ncut > h->cutcap) {
+      void *old[] = {h->cut_id, h->cut_nb, h->cut_ijk};
+      for (void *q : old) if (q) cudaFree(q);
+      h->cut_id = nullptr; h->cut_nb = nullptr; h->cut_ijk = nullptr; h->cutcap = 0;
+      const long long cap = std::max<long long>(ncut + ncut / 4, 1024);
+      IBM_TRY(cudaMalloc((void **)&h->cut_id, sizeof(long long) * cap));
+      IBM_TRY(cudaMalloc((void **)&h->cut_nb, sizeof(long long) * 6 * cap));
+      IBM_TRY(cudaMalloc((void **)&h->cut_ijk, sizeof(int) * 3 * cap));
+      h->cutcap = cap;
+    }
+    for (int colour = 0; colour < 2; ++colour)
+      k_cut_scatter<<<nb, CUT_THREADS, 0, st>>>(t->cut, t->cside, t->iblank, L0.g, ncell, colour, bo[colour],
+                                                colour ? counts[0] : 0, t->gkeys, t->nghost, h->cut_id, h->cut_ijk,
+                                                h->cut_nb);
+    h->hcnt[0] = counts[0];
+    h->hcnt[1] = ncut;
+    IBM_TRY(cudaMemcpyAsync(h->d_cnt, h->hcnt, sizeof(long long) * 2, cudaMemcpyHostToDevice, st));
+    if (!h->par_flag) IBM_TRY(alloc_zero<uint8_t>((void **)&h->par_flag, L1.g.ntot, st));
+    k_par_flag<<<152, 256, 0, st>>>(h->cut_id, h->cut_ijk, h->d_cnt, L1.g, h->par_flag);
+    k_par_count<<<nbp, CUT_THREADS, 0, st>>>(h->par_flag, L1.g.ntot, bc);
+    k_scan1<<<1, 1024, 0, st>>>(bc, bo[0], (int)nbp);
+    long long npar = 0;
+    IBM_TRY(cudaMemcpyAsync(&npar, bo[0] + nbp, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    if (npar > h->parcap) {
+      if (h->par_id) cudaFree(h->par_id);
+      h->par_id = nullptr; h->parcap = 0;
+      const long long cap = std::max<long long>(npar + npar / 4, 1024);
+      IBM_TRY(cudaMalloc((void **)&h->par_id, sizeof(long long) * cap));
+      h->parcap = cap;
+    }
+    k_par_scatter<<<nbp, CUT_THREADS, 0, st>>>(h->par_flag, L1.g.ntot, bo[0], h->par_id);
+    h->hcnt[2] = npar;
+    IBM_TRY(cudaMemcpyAsync(h->d_cnt, h->hcnt, sizeof(long long) * 3, cudaMemcpyHostToDevice, st));
     IBM_TRY(cudaGetLastError());
   }
   IBM_TRY(cudaStreamSynchronize(st));
@@ -1699,6 +2104,17 @@ void sweep_zmarch(Solver &S, T *&e, const double *shift) {
   e = other;
 }
 
+// membranes: relax the finest level's cut cells, red then black (entries read from eg)
+template <typename T>
+void cut_relax(Solver &S, T *e, const T *eg, const T *r, const double *shift) {
+  if (S.h->hcnt[1] == 0) return;
+  LV<T> v = view<T>(S.h->lv[0]);
+  for (int colour = 0; colour < 2; ++colour)
+    k_cut_relax<T><<<CUT_BLOCKS, 128, 0, S.st>>>(S.h->cut_id, S.h->cut_nb, S.h->cut_ijk, S.h->d_cnt, colour, v, e, eg,
+                                                 r, shift, (T)S.omega);
+  S.ctx->launches += 2;
+}
+
 template <typename T>
 void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool fine, const T *ghost_rhs, int sweeps) {
   Level &L = S.h->lv[l];
@@ -1711,6 +2127,7 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
       T *old = e;
       sweep_zmarch<T>(S, e, shift);
       if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
+      cut_relax<T>(S, e, old, r, shift);
       const long long ng = S.t->nghost;
       if (ng > 0) {
         if (sizeof(T) == 8)
@@ -1727,6 +2144,7 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
         k_rbgs<T><<<grid, 128, 0, S.st>>>(v, e, r, shift, colour, (T)S.omega);
       if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
       S.ctx->launches += 2;
+      if (fine) cut_relax<T>(S, e, e, r, shift);
     }
     if (fine) ghost_update<T>(S, e, ghost_rhs);
   }
@@ -1774,8 +2192,15 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   const int gx = (int)nblk(C.g.nx, 128),
             gy = std::max(1, std::min(C.g.ny * C.g.nz, std::min(RESTRICT_BLOCKS, h->grid_blocks[0]) / gx));
   k_restrict8<T><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, ec, S.ctx->partials);
+  int nparts = gx * gy;
+  if (l == 0 && h->hcnt[2] > 0) {   // membranes: the cut cells' share, partials after the regular ones
+    k_cut_restrict<T><<<CUT_BLOCKS, 256, 0, S.st>>>(h->par_id, h->d_cnt, h->cut_id, h->cut_nb, view<T>(F), e, r,
+                                                    shift, view<T>(C), rc, S.ctx->partials + nparts);
+    nparts += CUT_BLOCKS;
+    S.ctx->launches += 1;
+  }
   double *cshift = S.ctx->scal + S_LEVEL_SHIFT + (l + 1);
-  k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, gx * gy, h->d_fvol + (l + 1), cshift);
+  k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, nparts, h->d_fvol + (l + 1), cshift);
   vcycle<T>(S, l + 1, ec, rc, cshift, nullptr);
   const int pgx = (int)nblk(C.g.nx, 128);
   dim3 gp(pgx, std::max(1, std::min(C.g.ny * C.g.nz, h->grid_blocks[1] / pgx)));
@@ -1824,20 +2249,27 @@ void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda);
 void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   if (!S.dfo) return fine_residual(S, with_p ? S.h->p64 : nullptr, r32, update_lambda);
   Hierarchy *h = S.h;
-  const long long ntot = h->lv[0].g.ntot;
+  const long long ntot = h->nslot;   // hi/lo split point of the outer arrays
   double *part = S.ctx->partials;
   float *ph = with_p ? hi_of(h->p64) : nullptr, *pl = lo_of(h->p64, ntot);
   k_residual_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(fine_view_df(h), ph, pl, hi_of(h->b64),
                                                            lo_of(h->b64, ntot), S.ctx->scal + S_LAMBDA, r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
-  double *gpart = part + 3 * REDUCE_BLOCKS;
+  double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
+  const bool cuts = h->hcnt[1] > 0;
+  if (cuts) {
+    k_cut_resid_df<<<CUT_BLOCKS, 256, 0, S.st>>>(h->cut_id, h->cut_nb, h->cut_ijk, h->d_cnt, fine_view_df(h), ph, pl,
+                                                 hi_of(h->b64), lo_of(h->b64, ntot), S.ctx->scal + S_LAMBDA, r32,
+                                                 cpart);
+    S.ctx->launches += 1;
+  }
   const bool gh = ng > 0 && with_p;
   if (gh)
     k_ghost_resid_df<<<ngb, REDUCE_THREADS, 0, S.st>>>(h->gsrc, h->gdst, S.t->gw, S.t->gscale, h->d_ng, hi_of(h->p64),
                                                        pl, r32, gpart);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
-                                        update_lambda ? 1 : 0);
+                                        update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
 }
 
@@ -1849,13 +2281,19 @@ void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
                                                           r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
-  double *gpart = part + 3 * REDUCE_BLOCKS;
+  double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
+  const bool cuts = S.h->hcnt[1] > 0;
+  if (cuts) {
+    k_cut_resid64<<<CUT_BLOCKS, 256, 0, S.st>>>(S.h->cut_id, S.h->cut_nb, S.h->cut_ijk, S.h->d_cnt, v, p, S.h->b64,
+                                                S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n, r32, cpart);
+    S.ctx->launches += 1;
+  }
   const bool gh = ng > 0 && p != nullptr;
   if (gh)
     k_ghost_resid64<<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, S.h->d_ng, p, r32,
                                                       gpart);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
-                                        update_lambda ? 1 : 0);
+                                        update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
 }
 
@@ -1864,6 +2302,10 @@ void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
 ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
   Hierarchy *h = t->hier[precision];
   if (h && h->geom_version == t->geom_version) return IBM_OK;
+  if (h && t->membrane && t->nghost > h->slotcap) {   // more membrane entries than slots: rebuild
+    free_hierarchy(h);
+    t->hier[precision] = h = nullptr;
+  }
   if (h) return precision == 0 ? refresh_geometry_t<double>(t, h, st) : refresh_geometry_t<float>(t, h, st);
   ibm_status s = precision == 0 ? build_grid_t<double>(t, st, &h) : build_grid_t<float>(t, st, &h);
   if (s != IBM_OK) return s;
@@ -1925,7 +2367,7 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
   Solver S{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
   S.dfo = prec == 2;
-  const long long ntot = L0.g.ntot;
+  const long long ntot = h->nslot;   // level-0 elements: padded cells and membrane entry slots
   // inputs
   if (S.dfo) {
     k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, ntot), nullptr);
@@ -1981,7 +2423,7 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     } else {
       float *&e32 = reinterpret_cast<float *&>(L0.e);
       for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
-        if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * L0.g.ntot, bs);
+        if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * ntot, bs);
         vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
       }
       if (S.dfo)
@@ -1989,7 +2431,7 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
                                           reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
                                           reinterpret_cast<const float4 *>(e32), ntot / 4);
       else
-        k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, L0.g.ntot);
+        k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, ntot);
       ctx->launches += 1;
       outer_residual(S, true, r32, true);
     }
@@ -2006,8 +2448,11 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     unsigned long long key = ((unsigned long long)opts->nu1 << 48) ^ ((unsigned long long)opts->nu2 << 40) ^
                              ((unsigned long long)opts->inner_cycles << 32) ^
                              (unsigned long long)(long long)(opts->omega * 1e6) ^ (ng > 0 ? 1ULL << 62 : 0ULL);
-    const unsigned long long ptrs[4] = {(unsigned long long)(uintptr_t)t->gw, (unsigned long long)(uintptr_t)t->gscale,
-                                        (unsigned long long)(uintptr_t)h->gsrc, (unsigned long long)h->gcap};
+    const unsigned long long ptrs[8] = {(unsigned long long)(uintptr_t)t->gw, (unsigned long long)(uintptr_t)t->gscale,
+                                        (unsigned long long)(uintptr_t)h->gsrc, (unsigned long long)h->gcap,
+                                        (unsigned long long)(uintptr_t)h->cut_id, (unsigned long long)(uintptr_t)h->par_id,
+                                        (unsigned long long)(h->hcnt[1] > 0) | ((unsigned long long)(h->hcnt[2] > 0) << 1),
+                                        (unsigned long long)h->slotcap};
     for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
     if (!h->graph_exec || h->graph_key != (long long)key) {
       if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);

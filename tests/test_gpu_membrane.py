@@ -83,3 +83,48 @@ def test_membranes_are_not_mixed_with_closed_bodies(ctx):
     f = synth.faces_uniform(16)
     with pytest.raises(pkg.IbmError):
         pkg.Tables(c, f, f, f, [_tilted_plate(), synth.octa_sphere(3, (0.5, 0.5, 0.2), 0.1)])
+
+
+# ----------------------------------------------------------------------------- solves
+
+TOL = 1e-10
+PARITY = 1e-8
+
+
+def _solve_parity(pkg, c, xf, yf, zf, meshes, seed, T=None):
+    grid = Grid(xf, yf, zf)
+    _, G = OM.classify(grid, meshes)
+    b = synth.rhs_divergence(xf, yf, zf, seed)
+    p_o, g_o, lam_o = OM.solve_sparse(grid, G, b)
+    import torch
+    own = T is None
+    if own:
+        T = pkg.Tables(c, xf, yf, zf, meshes)
+    rhs = torch.from_numpy(b).cuda()
+    for prec in (0, 1, 2):
+        p = torch.zeros_like(rhs)
+        rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec))
+        assert rep["status"] == "IBM_OK" and rep["rel_resid"] <= TOL, (prec, rep)
+        pg = p.cpu().numpy()
+        err = np.linalg.norm(pg - p_o) / np.linalg.norm(p_o)
+        assert err <= PARITY, (prec, err, rep["cycles"])
+        assert abs(rep["lambda"] - lam_o) <= 1e-6 * max(1.0, abs(lam_o))
+    if own:
+        T.close()
+
+
+def test_membrane_solve_matches_oracle(ctx):
+    pkg, c = ctx
+    xf, yf, zf = synth.faces_tanh(24, 2.0), synth.faces_uniform(20), synth.faces_tanh(28, 1.5)
+    _solve_parity(pkg, c, xf, yf, zf, [_tilted_plate()], 6)
+
+
+def test_membrane_reclassified_solves(ctx):
+    pkg, c = ctx
+    f = synth.faces_tanh(32, 2.0)
+    phases = [[synth.plate(q / 8, nq_x=12, nq_y=8)] for q in (1, 5)]
+    T = pkg.Tables(c, f, f, f, phases[0])
+    _solve_parity(pkg, c, f, f, f, phases[0], 8, T)
+    T.reclassify(phases[1])
+    _solve_parity(pkg, c, f, f, f, phases[1], 8, T)
+    T.close()
