@@ -214,6 +214,47 @@ def bench_batched(pkg, ctx, torch, st, reps: int = 2):
     return out
 
 
+def bench_membrane(pkg, ctx, torch, st, n: int = 512, nphase: int = 8):
+    """Flapping plate (20 000 triangles) on an n^3 tanh-stretched grid: per phase, reclassify
+    and solve to 1e-10 in mode 2 starting from the previous phase's pressure; one more FP64
+    solve of the last phase for the mixed/FP64 ratio (ms, medians over the phases)."""
+    import synth
+    pr = synth.cfg3(n, 0, nphase)
+    rhs = torch.from_numpy(pr.rhs()).cuda()
+    p = torch.zeros_like(rhs)
+    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+    T.solve(rhs, p, TOL, pkg.SolveOpts(precision=2), stream=st)       # builds the hierarchy and its graph
+    rec, sol, cyc, ng = [], [], [], []
+    for q in range(1, nphase + 1):
+        mesh = [synth.plate((q % nphase) / nphase)]
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(st)
+        T.reclassify(mesh, stream=st)
+        b.record(st)
+        rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=2), stream=st)
+        c.record(st)
+        c.synchronize()
+        rec.append(a.elapsed_time(b)); sol.append(b.elapsed_time(c)); cyc.append(rep["cycles"]); ng.append(T.nghost)
+    out = {"grid": [n] * 3, "phases": nphase, "triangles": int(pr.meshes[0].tris.shape[0]),
+           "reclassify_ms": statistics.median(rec), "solve_warm_ms": statistics.median(sol),
+           "step_ms": statistics.median([x + y for x, y in zip(rec, sol)]),
+           "refinement_steps": cyc, "ghost_entries": ng}
+    for name, prec in (("mixed_df", 2), ("fp64", 0)):
+        p.zero_()
+        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)
+        p.zero_()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)
+        c.record(st)
+        c.synchronize()
+        out["cold_solve_ms_" + name] = a.elapsed_time(c)
+        out["cycles_" + name] = rep["cycles"]
+    out["mixed_df_speedup_vs_fp64"] = out["cold_solve_ms_fp64"] / out["cold_solve_ms_mixed_df"]
+    T.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -369,6 +410,8 @@ def run_ours(args):
             "gpu_launches": launches, "clocks": clk.summary()}
     if not args.no_batched:
         line["batched_48"] = bench_batched(pkg, ctx, torch, st)
+    if not args.no_membrane:
+        line["membrane_plate"] = bench_membrane(pkg, ctx, torch, st, args.membrane_n)
     if not args.no_cpu:
         c_cells, c_t = _cpu_sample(args.cpu_n)
         line["cpu_baseline"] = {"value": c_cells / c_t / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -392,6 +435,8 @@ def main():
     ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-membrane", action="store_true")
+    ap.add_argument("--membrane-n", type=int, default=512)
     ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")
     args = ap.parse_args()

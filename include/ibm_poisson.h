@@ -85,6 +85,12 @@ typedef struct {
   int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1, 2)         [2] */
   int32_t use_graph;    /* capture one cycle as a CUDA graph and replay it            [1] */
   double omega;         /* Gauss-Seidel over-relaxation factor, in (0, 2)           [1.3] */
+  int32_t krylov;       /* 0: plain refinement (precision 1, 2) or V-cycle iteration
+                           (precision 0); 1..8: GCR acceleration with that many
+                           directions, restarted, each step's V-cycle correction (FP32
+                           in modes 1 and 2, FP64 in mode 0, which then runs in
+                           correction form) as preconditioner; -1 automatic: 8 for
+                           membrane tables, 0 otherwise.                            [-1] */
 } ibm_solve_opts;
 
 /* Solve report.  resid_history (host, optional) receives the relative residual after
@@ -185,8 +191,8 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
                          double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
                          void *stream);
 
-/* Batched pressure Poisson solves (precision 0 or 1, closed bodies; membrane tables and
- * precision 2 return IBM_ERR_NOT_IMPLEMENTED): n independent problems (each its own classified grid,
+/* Batched pressure Poisson solves (precision 0 or 1, closed bodies, no Krylov acceleration;
+ * membrane tables, precision 2 and krylov > 0 return IBM_ERR_NOT_IMPLEMENTED): n independent problems (each its own classified grid,
  * of any size) advanced together, one persistent kernel launch per V-cycle stage over the
  * work of every problem that has that stage; each batched cycle is captured once as a CUDA
  * graph and replayed until every problem reaches tol (a converged problem's work turns

@@ -112,6 +112,10 @@ struct Hierarchy {
   long long *d_cnt = nullptr;               // device: red cut cells, all cut cells, parents
   long long hcnt[3] = {0, 0, 0};            // host copy
   uint8_t *par_flag = nullptr;              // level-1 scratch flags (kept zero between uses)
+  int gcr_m = 0;                            // Krylov directions allocated
+  void *gcr_buf = nullptr;                  // 2 gcr_m arrays of nslot elements of T (Z then Q)
+  void *gcr_state = nullptr;                // device state of the Krylov acceleration
+  double *gcr_part = nullptr;               // its block partial sums
   long long *scan_buf = nullptr;            // compaction scratch: block counts and offsets
   long long scan_cap = 0;
   int tail_level = -1;                      // first level of the one-block coarse tail (-1: none)

@@ -885,13 +885,16 @@ __device__ __forceinline__ void block_partials3(double A0, double A1, double A2,
     for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sm[q][0];
 }
 
-// FP64 fine residual r = b - lambda - A p on fluid rows; FP32 copy (0 on other cells);
-// block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}].  FP64 arithmetic is
-// kept to the stencil itself (GB300 issues FP64 at about 1/64 of the FP32 rate): the
-// diagonal is separable, row invariants are hoisted, the volume weights (wf: float widths
-// dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64 every 8 rows.
+// FP64 fine residual r = b - lambda - A p on fluid rows, stored as R (FP32 for the mixed
+// modes' inner cycles, FP64 for the accelerated FP64 mode; 0 on other cells); block partials
+// (sum V r, sum r, sum r^2, of the FP32-rounded r) at partials[3 b + {0,1,2}].  FP64
+// arithmetic is kept to the stencil itself (GB300 issues FP64 at about 1/64 of the FP32
+// rate): the diagonal is separable, row invariants are hoisted, the volume weights (wf: float
+// widths dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64 every
+// 8 rows.
+template <typename R>
 __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
-                                                              const double *lambda, const float *wf, float *r32,
+                                                              const double *lambda, const float *wf, R *r32,
                                                               double *partials) {
   const double lam = *lambda;
   const int nx = v.nx, ny = v.ny;
@@ -923,6 +926,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
           xr = p[id + 4];
         }
         float rf[4];
+        R rs[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = min(4 * g + u, nx - 1);   // coefficients of cells past nx: any valid index
@@ -939,11 +943,12 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
             res -= s;
           }
           rf[u] = fl[u] ? (float)res : 0.f;
+          rs[u] = fl[u] ? (R)res : (R)0;
           a0 = fmaf(wf[i] * dydz, rf[u], a0);
           a1 += rf[u];
           a2 = fmaf(rf[u], rf[u], a2);
         }
-        if (r32) Vec4<float>::st(r32 + id, rf);
+        if (r32) Vec4<R>::st(r32 + id, rs);
       }
       if (++nrow == 8) {
         A0 += a0; A1 += a1; A2 += a2;
@@ -956,8 +961,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
 }
 
 // ghost rows r_G = sum w v - g; block partials of (s_G r_G)^2 at gpart[b]
+template <typename R>
 __global__ void k_ghost_resid64(const long long *src, const long long *dst, const double *w, const double *scale,
-                                const long long *ngp, const double *p, float *r32, double *gpart) {
+                                const long long *ngp, const double *p, R *r32, double *gpart) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
   const long long ng = *ngp;
@@ -968,7 +974,7 @@ __global__ void k_ghost_resid64(const long long *src, const long long *dst, cons
       if (q >= 0) s += w[8 * g + c] * p[q & ~GHOST_CORNER];
     }
     double rg = s - p[dst[g]];
-    if (r32) r32[dst[g]] = (float)rg;
+    if (r32) r32[dst[g]] = (R)rg;
     double sr = scale[g] * rg;
     a += sr * sr;
   }
@@ -1534,12 +1540,13 @@ __global__ void k_cut_relax(const long long *cut_id, const long long *cut_nb, co
   }
 }
 
-// outer residual of the cut cells in FP64: r32 and block partials (V r, r, r^2) at
-// part[3 b + {0,1,2}] (p == nullptr: residual of p = 0)
+// outer residual of the cut cells in FP64: r (stored as R) and block partials (V r, r, r^2
+// of the FP32-rounded r) at part[3 b + {0,1,2}] (p == nullptr: residual of p = 0)
+template <typename R>
 __global__ void __launch_bounds__(256) k_cut_resid64(const long long *cut_id, const long long *cut_nb,
                                                      const int *cut_ijk, const long long *cnt, LV<double> v,
                                                      const double *p, const double *bb, const double *lambda,
-                                                     const float *wf, float *r32, double *part) {
+                                                     const float *wf, R *r32, double *part) {
   __shared__ double sm[3][256];
   const double lam = *lambda;
   double A0 = 0.0, A1 = 0.0, A2 = 0.0;
@@ -1557,7 +1564,7 @@ __global__ void __launch_bounds__(256) k_cut_resid64(const long long *cut_id, co
       res -= s;
     }
     const float rf = (float)res;
-    if (r32) r32[id] = rf;
+    if (r32) r32[id] = (R)res;
     const double V = (double)(wf[i] * (wf[nx + j] * wf[nx + ny + k]));
     A0 += V * rf; A1 += rf; A2 += (double)rf * rf;
   }
@@ -1670,6 +1677,311 @@ __global__ void __launch_bounds__(256) k_cut_restrict(const long long *par_id, c
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
 
+// ------------------------------------------------------------------ Krylov acceleration
+
+// GCR(m) on the refinement loop.  Each refinement step's correction z (V-cycle(s) applied to
+// the fine residual r; FP32 in modes 1 and 2, FP64 in mode 0) becomes a search direction:
+// q = P A z (A the fine operator with its ghost rows, P the removal of the volume-weighted
+// fluid mean), orthonormalised against the cycle's previous directions in the inner product
+// <a, b> = sum_fluid V a b + sum_ghost s^2 a b, and the outer solution moves by alpha Z with
+// alpha = <r, Q>.  The direction index, the coefficients and the restart live in device
+// memory, so one captured refinement step serves every step.  Storage: m directions Z_i and
+// Q_i of nslot elements of T each (Z at zb + i nslot, Q at qb + i nslot).
+constexpr int GCR_MAX = 8;
+constexpr int GCR_BLOCKS = 608;
+constexpr int GCR_GBLOCKS = 152;
+constexpr int GCR_NV = 2 * GCR_MAX + 3;   // partial sums per block: <q,Q_i>, <r,Q_i>, <q,q>, <r,q>, sum V q
+
+struct GcrState {           // device memory
+  int j;                    // direction being built in the current cycle
+  int pad;
+  double beta[GCR_MAX];     // <q, Q_i> of the new direction against the previous ones
+  double nu;                // norm after orthogonalisation
+  double alpha;             // step length along the new normalised direction
+  double mu;                // volume-weighted fluid mean of A z
+};
+
+template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+
+// q = A z on every row of the finest level (regular fluid rows here; 0 on other cells), with
+// block partials of sum V q over regular fluid rows at part[b]
+template <typename T>
+__global__ void __launch_bounds__(REDUCE_THREADS) k_gcr_apply(LV<T> v, const float *wf, const T *z,
+                                                              const GcrState *gs, T *qb, long long nslot,
+                                                              double *part) {
+  __shared__ double sm[REDUCE_THREADS];
+  T *q = qb + (long long)gs->j * nslot;
+  const int nx = v.nx, ny = v.ny;
+  double A = 0.0;
+  const RowGroups rg(nx);
+  const int rows = ny * v.nz;
+  if (rg.active())
+    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+      const int j = row % ny, k = row / ny;
+      const T cym = v.cym[j], cyp = v.cyp[j], czm = v.czm[k], czp = v.czp[k], syz = v.sdy[j] + v.sdz[k];
+      const float dydz = wf[nx + j] * wf[nx + ny + k];
+      const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      T a = 0;
+      for (int g = rg.g0; g < rg.G; g += rg.gstep) {
+        const long long id = base + 4 * g;
+        bool fl[4];
+        ld_mask4(v.mask + id, fl);
+        T Z[4], YM[4], YP[4], ZM[4], ZP[4], Q[4];
+        Vec4<T>::ld(z + id, Z);
+        Vec4<T>::ld(z + id - v.sy, YM);
+        Vec4<T>::ld(z + id + v.sy, YP);
+        Vec4<T>::ld(z + id - v.sz, ZM);
+        Vec4<T>::ld(z + id + v.sz, ZP);
+        const T xl = z[id - 1], xr = z[id + 4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = min(4 * g + u, nx - 1);
+          const T left = u == 0 ? xl : Z[u - 1], right = u == 3 ? xr : Z[u + 1];
+          T s = v.cxm[i] * left;
+          s = fma_t<T>(v.cxp[i], right, s);
+          s = fma_t<T>(cym, YM[u], s);
+          s = fma_t<T>(cyp, YP[u], s);
+          s = fma_t<T>(czm, ZM[u], s);
+          s = fma_t<T>(czp, ZP[u], s);
+          s = fma_t<T>(-(v.sdx[i] + syz), Z[u], s);
+          Q[u] = fl[u] ? s : (T)0;
+          a = fma_t<T>((T)(wf[i] * dydz), Q[u], a);
+        }
+        Vec4<T>::st(q + id, Q);
+      }
+      A += (double)a;
+    }
+  sm[threadIdx.x] = A;
+  __syncthreads();
+  for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// q = A z at the membrane cut cells, block partials of sum V q at part[b]
+template <typename T>
+__global__ void __launch_bounds__(256) k_gcr_apply_cut(const long long *cut_id, const long long *cut_nb,
+                                                       const int *cut_ijk, const long long *cnt, LV<T> v,
+                                                       const float *wf, const T *z, const GcrState *gs, T *qb,
+                                                       long long nslot, double *part) {
+  __shared__ double sm[256];
+  T *q = qb + (long long)gs->j * nslot;
+  const int nx = v.nx, ny = v.ny;
+  double A = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt[1];
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long id = cut_id[t];
+    const int i = cut_ijk[3 * t], j = cut_ijk[3 * t + 1], k = cut_ijk[3 * t + 2];
+    const T c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
+    T s = 0;
+    for (int d = 0; d < 6; ++d) s = fma_t<T>(c[d], z[cut_nb[6 * t + d]], s);
+    s = fma_t<T>(-((v.sdx[i] + v.sdy[j]) + v.sdz[k]), z[id], s);
+    q[id] = s;
+    A += (double)(wf[i] * (wf[nx + j] * wf[nx + ny + k])) * (double)s;
+  }
+  sm[threadIdx.x] = A;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// ghost rows: q = z_G - sum w z_src (weights W: FP32 or FP64 copies of the interpolation rows)
+template <typename T, typename W>
+__global__ void k_gcr_apply_ghost(const long long *src, const long long *dst, const W *w, const long long *ngp,
+                                  const T *z, const GcrState *gs, T *qb, long long nslot) {
+  T *q = qb + (long long)gs->j * nslot;
+  const long long ng = *ngp;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    T s = 0;
+    for (int c = 0; c < 8; ++c) {
+      const long long x = src[8 * g + c];
+      if (x >= 0) s += (T)w[8 * g + c] * z[x & ~GHOST_CORNER];
+    }
+    q[dst[g]] = z[dst[g]] - s;
+  }
+}
+
+__global__ void k_gcr_mean(const double *part, int nb, const double *cpart, int ncb, const double *fluid_vol,
+                           GcrState *gs) {
+  double s = block_sum_partials(part, nb, 1, 0);
+  if (ncb > 0) s += block_sum_partials(cpart, ncb, 1, 0);
+  if (threadIdx.x == 0) gs->mu = *fluid_vol > 0 ? s / *fluid_vol : 0.0;
+}
+
+// project q (remove mu on fluid rows) and block partials over fluid rows (weights V) of
+// <q,Q_i>, <r,Q_i> (i < j), <q,q>, <r,q> at part[GCR_NV b + ...]
+template <typename T>
+__global__ void __launch_bounds__(REDUCE_THREADS) k_gcr_dots(LV<T> v, const float *wf, const T *r,
+                                                             const GcrState *gs, T *qb, long long nslot,
+                                                             double *part) {
+  __shared__ double sm[REDUCE_THREADS];
+  const int jj = gs->j;
+  T *q = qb + (long long)jj * nslot;
+  const T mu = (T)gs->mu;
+  const int nx = v.nx, ny = v.ny;
+  double acc[GCR_NV];
+  for (int t = 0; t < GCR_NV; ++t) acc[t] = 0.0;
+  const RowGroups rg(nx);
+  const int rows = ny * v.nz;
+  if (rg.active())
+    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+      const int j = row % ny, k = row / ny;
+      const float dydz = wf[nx + j] * wf[nx + ny + k];
+      const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      for (int g = rg.g0; g < rg.G; g += rg.gstep) {
+        const long long id = base + 4 * g;
+        bool fl[4];
+        ld_fluid4(v.mask + id, fl);
+        T Q[4], R[4], Wt[4];
+        Vec4<T>::ld(q + id, Q);
+        Vec4<T>::ld(r + id, R);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          Wt[u] = fl[u] ? (T)(wf[min(4 * g + u, nx - 1)] * dydz) : (T)0;
+          Q[u] = fl[u] ? Q[u] - mu : Q[u];
+        }
+        Vec4<T>::st(q + id, Q);
+        for (int i = 0; i < jj; ++i) {
+          T Qi[4];
+          Vec4<T>::ld(qb + (long long)i * nslot + id, Qi);
+          T a = 0, b = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) { a = fma_t<T>(Wt[u] * Q[u], Qi[u], a); b = fma_t<T>(Wt[u] * R[u], Qi[u], b); }
+          acc[i] += (double)a; acc[GCR_MAX + i] += (double)b;
+        }
+        T a = 0, b = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { a = fma_t<T>(Wt[u] * Q[u], Q[u], a); b = fma_t<T>(Wt[u] * R[u], Q[u], b); }
+        acc[2 * GCR_MAX] += (double)a; acc[2 * GCR_MAX + 1] += (double)b;
+      }
+    }
+  for (int t = 0; t < 2 * GCR_MAX + 2; ++t) {
+    if (t < 2 * GCR_MAX && (t % GCR_MAX) >= jj) continue;
+    sm[threadIdx.x] = acc[t];
+    __syncthreads();
+    for (int st = REDUCE_THREADS / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[GCR_NV * blockIdx.x + t] = sm[0];
+    __syncthreads();
+  }
+}
+
+// the same inner products over the ghost rows (weights s^2)
+template <typename T>
+__global__ void __launch_bounds__(256) k_gcr_dots_ghost(const long long *dst, const double *scale, const long long *ngp,
+                                                        const T *r, const GcrState *gs, const T *qb,
+                                                        long long nslot, double *part) {
+  __shared__ double sm[256];
+  const int jj = gs->j;
+  const T *q = qb + (long long)jj * nslot;
+  const long long ng = *ngp;
+  double acc[GCR_NV];
+  for (int t = 0; t < GCR_NV; ++t) acc[t] = 0.0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    const long long x = dst[g];
+    const double w = scale[g] * scale[g];
+    const double qx = q[x], rx = r[x];
+    for (int i = 0; i < jj; ++i) {
+      const double qi = qb[(long long)i * nslot + x];
+      acc[i] += w * qx * qi;
+      acc[GCR_MAX + i] += w * rx * qi;
+    }
+    acc[2 * GCR_MAX] += w * qx * qx;
+    acc[2 * GCR_MAX + 1] += w * rx * qx;
+  }
+  for (int t = 0; t < 2 * GCR_MAX + 2; ++t) {
+    if (t < 2 * GCR_MAX && (t % GCR_MAX) >= jj) continue;
+    sm[threadIdx.x] = acc[t];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+      if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[GCR_NV * blockIdx.x + t] = sm[0];
+    __syncthreads();
+  }
+}
+
+// coefficients of the new direction (one block): beta_i = <q, Q_i>, nu = |q - sum beta_i Q_i|,
+// alpha = (<r, q> - sum beta_i <r, Q_i>) / nu (0 if the direction degenerated)
+__global__ void k_gcr_coef(const double *part, int nb, const double *gpart, int ngb, GcrState *gs) {
+  const int jj = gs->j;
+  double qq = 0.0, rq = 0.0, sb = 0.0, sbr = 0.0;
+  for (int t = 0; t < 2 * GCR_MAX + 2; ++t) {
+    if (t < 2 * GCR_MAX && (t % GCR_MAX) >= jj) continue;
+    double v = block_sum_partials(part, nb, GCR_NV, t);
+    if (ngb > 0) v += block_sum_partials(gpart, ngb, GCR_NV, t);
+    if (threadIdx.x == 0) {
+      if (t < GCR_MAX) gs->beta[t] = v;
+      else if (t < 2 * GCR_MAX) sbr += gs->beta[t - GCR_MAX] * v;
+      else if (t == 2 * GCR_MAX) qq = v;
+      else rq = v;
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < jj; ++i) sb += gs->beta[i] * gs->beta[i];
+    const double n2 = qq - sb;
+    if (n2 > 1e-30 * qq && n2 > 0.0) {
+      gs->nu = sqrt(n2);
+      gs->alpha = (rq - sbr) / gs->nu;
+    } else {
+      gs->nu = 1.0;
+      gs->alpha = 0.0;
+    }
+  }
+}
+
+// finish the new direction in place (Q_j, Z_j normalised) and move the outer solution by
+// alpha Z_j: FP64 outer arrays (p64), or double-FP32 pairs (ph, pl) for FP32 directions
+template <typename T>
+__global__ void k_gcr_update(const T *z, T *zb, T *qb, long long nslot, const GcrState *gs, double *p64, float *ph,
+                             float *pl) {
+  const int jj = gs->j;
+  const T inv = (T)(1.0 / gs->nu);
+  T beta[GCR_MAX];
+  for (int i = 0; i < GCR_MAX; ++i) beta[i] = i < jj ? (T)gs->beta[i] : (T)0;
+  const double alpha = gs->alpha;
+  float ah, al;
+  dfl::split(alpha, ah, al);
+  T *Z = zb + (long long)jj * nslot, *Q = qb + (long long)jj * nslot;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nslot;
+       x += (long long)gridDim.x * blockDim.x) {
+    T zn = z[x], qn = Q[x];
+    for (int i = 0; i < jj; ++i) {
+      zn = fma_t<T>(-beta[i], zb[(long long)i * nslot + x], zn);
+      qn = fma_t<T>(-beta[i], qb[(long long)i * nslot + x], qn);
+    }
+    zn *= inv;
+    qn *= inv;
+    Z[x] = zn;
+    Q[x] = qn;
+    if constexpr (sizeof(T) == 4) {
+      if (pl) {
+        float sh = 0.f, sl = 0.f, s, t;
+        dfl::acc_prod(ah, al, zn, 0.f, sh, sl);      // alpha zn as a pair
+        dfl::two_sum(ph[x], sh, s, t);
+        t += pl[x] + sl;
+        dfl::two_sum(s, t, ph[x], pl[x]);
+        continue;
+      }
+    }
+    p64[x] = fma(alpha, (double)zn, p64[x]);
+  }
+}
+
+__global__ void k_gcr_advance(GcrState *gs, int m) {
+  if (threadIdx.x == 0) gs->j = (gs->j + 1) % m;
+}
+
 // solver-side ghost rows: padded source and destination indices.  Closed bodies: a ghost
 // lives at its (solid) cell, a source that is itself a ghost is flagged GHOST_CORNER.
 // Membranes: entry e lives in slot ntot + e after the padded cells; a reference >= ncell is
@@ -1709,8 +2021,9 @@ void free_hierarchy(Hierarchy *h) {
   }
   void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
                h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng,
-               h->cut_id, h->cut_nb, h->cut_ijk, h->par_id, h->d_cnt, h->par_flag, h->scan_buf};
-  ps.insert(ps.end(), q, q + 25);
+               h->cut_id, h->cut_nb, h->cut_ijk, h->par_id, h->d_cnt, h->par_flag, h->scan_buf, h->gcr_buf,
+               h->gcr_state, h->gcr_part};
+  ps.insert(ps.end(), q, q + 28);
   std::sort(ps.begin(), ps.end());
   ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
   for (void *p : ps) if (p) cudaFree(p);
@@ -2243,11 +2556,12 @@ DfView fine_view_df(Hierarchy *h) {
 inline float *hi_of(double *a) { return reinterpret_cast<float *>(a); }
 inline float *lo_of(double *a, long long ntot) { return reinterpret_cast<float *>(a) + ntot; }
 
-void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda);
+template <typename R>
+void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda);
 
 // the outer residual, its norms and the lambda update; with_p == false: residual of p = 0
 void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
-  if (!S.dfo) return fine_residual(S, with_p ? S.h->p64 : nullptr, r32, update_lambda);
+  if (!S.dfo) return fine_residual<float>(S, with_p ? S.h->p64 : nullptr, r32, update_lambda);
   Hierarchy *h = S.h;
   const long long ntot = h->nslot;   // hi/lo split point of the outer arrays
   double *part = S.ctx->partials;
@@ -2273,28 +2587,66 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   S.ctx->launches += gh ? 3 : 2;
 }
 
-void fine_residual(Solver &S, const double *p, float *r32, bool update_lambda) {
+template <typename R>
+void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda) {
   LV<double> v = fine_view64(S.h);
   double *part = S.ctx->partials;
   const int n = v.nx + v.ny + v.nz;
-  k_residual64<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n,
+  k_residual64<R><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n,
                                                           r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
   const bool cuts = S.h->hcnt[1] > 0;
   if (cuts) {
-    k_cut_resid64<<<CUT_BLOCKS, 256, 0, S.st>>>(S.h->cut_id, S.h->cut_nb, S.h->cut_ijk, S.h->d_cnt, v, p, S.h->b64,
+    k_cut_resid64<R><<<CUT_BLOCKS, 256, 0, S.st>>>(S.h->cut_id, S.h->cut_nb, S.h->cut_ijk, S.h->d_cnt, v, p, S.h->b64,
                                                 S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n, r32, cpart);
     S.ctx->launches += 1;
   }
   const bool gh = ng > 0 && p != nullptr;
   if (gh)
-    k_ghost_resid64<<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, S.h->d_ng, p, r32,
+    k_ghost_resid64<R><<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, S.h->d_ng, p, r32,
                                                       gpart);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
                                         update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
+}
+
+// one GCR step on the finest level: e (the refinement step's correction) becomes the
+// cycle's next orthonormal direction and the outer solution moves along it (r: the fine
+// residual the correction was computed from, ghost rows included)
+template <typename T>
+void gcr_step(Solver &S, T *e, const T *r, int m) {
+  Hierarchy *h = S.h;
+  Level &L0 = h->lv[0];
+  const long long ntot = h->nslot, ng = S.t->nghost;
+  const LV<T> v0 = view<T>(L0);
+  const float *wf = h->cdf + 3 * (L0.g.nx + L0.g.ny + L0.g.nz);
+  GcrState *gs = reinterpret_cast<GcrState *>(h->gcr_state);
+  T *Zb = reinterpret_cast<T *>(h->gcr_buf), *Qb = Zb + (long long)m * ntot;
+  double *p0 = h->gcr_part, *p1 = p0 + REDUCE_BLOCKS + CUT_BLOCKS, *p2 = p1 + GCR_NV * REDUCE_BLOCKS;
+  const bool cuts = h->hcnt[1] > 0;
+  cudaStream_t bs = S.st;
+  k_gcr_apply<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, bs>>>(v0, wf, e, gs, Qb, ntot, p0);
+  if (cuts)
+    k_gcr_apply_cut<T><<<CUT_BLOCKS, 256, 0, bs>>>(h->cut_id, h->cut_nb, h->cut_ijk, h->d_cnt, v0, wf, e, gs, Qb, ntot,
+                                                   p0 + REDUCE_BLOCKS);
+  if (ng > 0) {
+    if constexpr (sizeof(T) == 8)
+      k_gcr_apply_ghost<T, double><<<nblk(h->gcap, 128), 128, 0, bs>>>(h->gsrc, h->gdst, S.t->gw, h->d_ng, e, gs, Qb,
+                                                                       ntot);
+    else
+      k_gcr_apply_ghost<T, float><<<nblk(h->gcap, 128), 128, 0, bs>>>(h->gsrc, h->gdst, h->gw32, h->d_ng, e, gs, Qb,
+                                                                      ntot);
+  }
+  k_gcr_mean<<<1, 256, 0, bs>>>(p0, REDUCE_BLOCKS, p0 + REDUCE_BLOCKS, cuts ? CUT_BLOCKS : 0, h->d_fvol, gs);
+  k_gcr_dots<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, bs>>>(v0, wf, r, gs, Qb, ntot, p1);
+  if (ng > 0) k_gcr_dots_ghost<T><<<GCR_GBLOCKS, 256, 0, bs>>>(h->gdst, S.t->gscale, h->d_ng, r, gs, Qb, ntot, p2);
+  k_gcr_coef<<<1, 256, 0, bs>>>(p1, REDUCE_BLOCKS, p2, ng > 0 ? GCR_GBLOCKS : 0, gs);
+  k_gcr_update<T><<<1216, 256, 0, bs>>>(e, Zb, Qb, ntot, gs, S.dfo ? nullptr : h->p64,
+                                        S.dfo ? hi_of(h->p64) : nullptr, S.dfo ? lo_of(h->p64, ntot) : nullptr);
+  k_gcr_advance<<<1, 32, 0, bs>>>(gs, m);
+  S.ctx->launches += 6 + (cuts ? 1 : 0) + (ng > 0 ? 2 : 0);
 }
 
 }  // namespace
@@ -2404,8 +2756,26 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   double rel = 0.0;
   int hl = 0;
   ibm_status result = IBM_ERR_NOT_CONVERGED;
+  // Krylov acceleration of the refinement loop: directions (of the cycle's type), state,
+  // partials.  Mode 0 with it runs in correction form like the mixed modes, in FP64.
+  const int gcr_m = opts->krylov < 0 ? (t->membrane ? GCR_MAX : 0) : std::min(opts->krylov, GCR_MAX);
+  if (gcr_m > 0) {
+    if (h->gcr_m < gcr_m) {
+      if (h->gcr_buf) cudaFree(h->gcr_buf);
+      h->gcr_buf = nullptr; h->gcr_m = 0;
+      IBM_TRY(cudaMalloc(&h->gcr_buf, (size_t)h->elem * 2 * (size_t)gcr_m * ntot));
+      h->gcr_m = gcr_m;
+    }
+    if (!h->gcr_state) IBM_TRY(cudaMalloc(&h->gcr_state, sizeof(GcrState)));
+    if (!h->gcr_part)
+      IBM_TRY(cudaMalloc((void **)&h->gcr_part,
+                         sizeof(double) * (REDUCE_BLOCKS + CUT_BLOCKS + GCR_NV * (REDUCE_BLOCKS + GCR_GBLOCKS))));
+    IBM_TRY(cudaMemsetAsync(h->gcr_state, 0, sizeof(GcrState), st));
+  }
   float *r32 = prec != 0 ? (float *)L0.r : nullptr;
-  outer_residual(S, true, r32, true);
+  double *r64 = prec == 0 && gcr_m > 0 ? (double *)L0.r : nullptr;
+  if (r64) fine_residual<double>(S, h->p64, r64, true);
+  else outer_residual(S, true, r32, true);
   IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
   IBM_TRY(cudaStreamSynchronize(st));
   rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
@@ -2417,22 +2787,33 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   // over a cycle when its number of fine sweeps is even, so the graph stays valid.
   auto body = [&](cudaStream_t bs) {
     S.st = bs;
-    if (prec == 0) {
+    if (prec == 0 && gcr_m == 0) {
       vcycle<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, nullptr);
-      fine_residual(S, h->p64, nullptr, true);
+      fine_residual<float>(S, h->p64, nullptr, true);
+    } else if (prec == 0) {
+      // correction form in FP64: e = V-cycle(r - mu), a GCR step on p, the new residual
+      double *&e64 = reinterpret_cast<double *&>(L0.e);
+      cudaMemsetAsync(e64, 0, sizeof(double) * ntot, bs);
+      vcycle<double>(S, 0, e64, r64, ctx->scal + S_MU, r64);
+      gcr_step<double>(S, e64, r64, gcr_m);
+      fine_residual<double>(S, h->p64, r64, true);
     } else {
       float *&e32 = reinterpret_cast<float *&>(L0.e);
       for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
         if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * ntot, bs);
         vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
       }
-      if (S.dfo)
-        k_update_df<<<1216, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
-                                          reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
-                                          reinterpret_cast<const float4 *>(e32), ntot / 4);
-      else
-        k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, ntot);
-      ctx->launches += 1;
+      if (gcr_m > 0) {
+        gcr_step<float>(S, e32, r32, gcr_m);
+      } else {
+        if (S.dfo)
+          k_update_df<<<1216, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
+                                            reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
+                                            reinterpret_cast<const float4 *>(e32), ntot / 4);
+        else
+          k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, ntot);
+        ctx->launches += 1;
+      }
       outer_residual(S, true, r32, true);
     }
     S.st = st;
@@ -2445,7 +2826,8 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     // the captured cycle depends on the schedule, on whether ghost rows exist and on the
     // addresses of the per-ghost arrays (which move when they grow); everything else it
     // reads from device memory or from grid-only data
-    unsigned long long key = ((unsigned long long)opts->nu1 << 48) ^ ((unsigned long long)opts->nu2 << 40) ^
+    unsigned long long key = ((unsigned long long)gcr_m << 56) ^
+                             ((unsigned long long)opts->nu1 << 48) ^ ((unsigned long long)opts->nu2 << 40) ^
                              ((unsigned long long)opts->inner_cycles << 32) ^
                              (unsigned long long)(long long)(opts->omega * 1e6) ^ (ng > 0 ? 1ULL << 62 : 0ULL);
     const unsigned long long ptrs[8] = {(unsigned long long)(uintptr_t)t->gw, (unsigned long long)(uintptr_t)t->gscale,

@@ -84,3 +84,26 @@ def test_autotune_returns_a_converging_schedule(ctx):
     rep = T.solve(rhs, p, TOL, opts)
     assert rep["rel_resid"] <= TOL
     T.close()
+
+
+def test_batched_rejects_unbuilt_options(ctx):
+    """The batched path has no double-FP32 outer loop, no Krylov acceleration and no
+    membranes: those requests return IBM_ERR_NOT_IMPLEMENTED and leave p untouched."""
+    pkg, c = ctx
+    probs = _batch(2, 5, 16, 20)
+    tabs = [pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes) for pr in probs]
+    rhs = [torch.from_numpy(pr.rhs()).cuda() for pr in probs]
+    ps = [torch.zeros_like(r) for r in rhs]
+    for o in (pkg.SolveOpts(precision=2), pkg.SolveOpts(precision=1, krylov=4), pkg.SolveOpts(precision=0, krylov=2)):
+        status, _ = pkg.poisson_solve_batched(c.h, [t.h for t in tabs], rhs, TOL, ps, o, raise_on_error=False)
+        assert status == "IBM_ERR_NOT_IMPLEMENTED", o
+    assert all(float(p.abs().max()) == 0.0 for p in ps)
+    f = synth.faces_uniform(16)
+    M = pkg.Tables(c, f, f, f, [synth.plate(0.0, nq_x=6, nq_y=4)])
+    r = torch.from_numpy(synth.rhs_divergence(f, f, f, 1)).cuda()
+    status, _ = pkg.poisson_solve_batched(c.h, [M.h], [r], TOL, [torch.zeros_like(r)], pkg.SolveOpts(precision=1),
+                                          raise_on_error=False)
+    assert status == "IBM_ERR_NOT_IMPLEMENTED"
+    M.close()
+    for t in tabs:
+        t.close()

@@ -128,3 +128,42 @@ def test_membrane_reclassified_solves(ctx):
     T.reclassify(phases[1])
     _solve_parity(pkg, c, f, f, f, phases[1], 8, T)
     T.close()
+
+
+def test_krylov_acceleration_on_and_off(ctx):
+    """GCR acceleration (automatic for membranes) and plain refinement reach the same
+    solution; GCR on a closed body too."""
+    pkg, c = ctx
+    import torch
+    xf, yf, zf = synth.faces_tanh(24, 2.0), synth.faces_uniform(20), synth.faces_tanh(28, 1.5)
+    grid = Grid(xf, yf, zf)
+    m = [_tilted_plate()]
+    _, G = OM.classify(grid, m)
+    b = synth.rhs_divergence(xf, yf, zf, 6)
+    p_o, _, _ = OM.solve_sparse(grid, G, b)
+    T = pkg.Tables(c, xf, yf, zf, m)
+    rhs = torch.from_numpy(b).cuda()
+    for prec in (0, 1, 2):
+        for kr in (0, 3, 8):
+            p = torch.zeros_like(rhs)
+            rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec, krylov=kr))
+            err = np.linalg.norm(p.cpu().numpy() - p_o) / np.linalg.norm(p_o)
+            assert rep["status"] == "IBM_OK" and err <= PARITY, (prec, kr, err, rep["cycles"])
+    T.close()
+    from oracle import classify as OC
+    from oracle import solve as OS
+    f = synth.faces_tanh(30, 2.0)
+    grid = Grid(f, f, f)
+    mb = [synth.ellipsoid(4, (0.25, 0.12, 0.1), 33.0, (0.45, 0.5, 0.5))]
+    ib, Gc = OC.classify(grid, mb)
+    b = synth.rhs_divergence(f, f, f, 7)
+    p_o, _ = OS.solve_gmres(grid, ib, Gc, b)
+    fl = ib == 0
+    T = pkg.Tables(c, f, f, f, mb)
+    rhs = torch.from_numpy(b).cuda()
+    for prec in (0, 1, 2):
+        p = torch.zeros_like(rhs)
+        rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec, krylov=4))
+        err = np.linalg.norm((p.cpu().numpy() - p_o)[fl]) / np.linalg.norm(p_o[fl])
+        assert rep["status"] == "IBM_OK" and err <= PARITY, (prec, err)
+    T.close()
