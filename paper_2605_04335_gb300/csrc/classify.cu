@@ -367,11 +367,6 @@ __device__ void closest_on_tri(const double P[3], const double *A, const double 
   d2 = (dx * dx + dy * dy) + dz * dz;
 }
 
-struct MeshRange {
-  int t0, t1;
-  double lo[3], hi[3];
-};
-
 __device__ __forceinline__ float box_dist2(const float p[3], float4 lo, float4 hi) {
   float dx = fmaxf(fmaxf(lo.x - p[0], 0.0f), p[0] - hi.x);
   float dy = fmaxf(fmaxf(lo.y - p[1], 0.0f), p[1] - hi.y);
@@ -379,13 +374,77 @@ __device__ __forceinline__ float box_dist2(const float p[3], float4 lo, float4 h
   return dx * dx + dy * dy + dz * dz;
 }
 
-__device__ __forceinline__ double mesh_box_dist(const double P[3], const MeshRange &m) {
-  double s = 0.0;
+// Uniform cubic bins (edge h, origin lo, nb[d] per axis) over the triangles' bounding box:
+// each triangle is listed in every bin that its box, widened by BIN_MARGIN, meets.  A search
+// that has visited every bin within distance L of a point has therefore seen every triangle
+// within L of it.
+struct TriBins {
+  double lo[3];
+  double h, inv;
+  int nb[3];
+  const long long *off;   // nb[0] nb[1] nb[2] + 1 offsets into tri
+  const int *tri;         // triangle indices, bin by bin
+  const uint2 *range;     // per triangle: first (x) and last (y) bin per axis, one byte each
+};
+
+// does triangle t's bin range meet the box of bins [l, h] (per axis)?  first: the range's
+// first bin inside the box
+__device__ __forceinline__ bool range_meets(uint2 rg, const int l[3], const int h[3], int first[3]) {
+  bool ok = true;
   for (int d = 0; d < 3; ++d) {
-    double v = fmax(fmax(m.lo[d] - P[d], 0.0), P[d] - m.hi[d]);
-    s = s + v * v;
+    const int a = (int)((rg.x >> (8 * d)) & 0xffu), b = (int)((rg.y >> (8 * d)) & 0xffu);
+    first[d] = max(a, l[d]);
+    ok = ok && first[d] <= min(b, h[d]);
   }
-  return sqrt(s);
+  return ok;
+}
+constexpr double BIN_MARGIN = 1e-9;
+
+// bins met by the box [l, h] widened by BIN_MARGIN (clamped to the grid)
+__device__ __forceinline__ void box_bin_range(const double l[3], const double h[3], const TriBins &B, int i0[3],
+                                              int i1[3]) {
+  for (int d = 0; d < 3; ++d) {
+    const double a = floor((l[d] - B.lo[d] - BIN_MARGIN) * B.inv), b = floor((h[d] - B.lo[d] + BIN_MARGIN) * B.inv);
+    const double top = (double)(B.nb[d] - 1);
+    i0[d] = (int)fmin(fmax(a, 0.0), top);
+    i1[d] = (int)fmin(fmax(b, 0.0), top);
+  }
+}
+
+__device__ __forceinline__ void tri_bin_range(const double *v, const TriBins &B, int i0[3], int i1[3]) {
+  double l[3], h[3];
+  for (int d = 0; d < 3; ++d) {
+    l[d] = fmin(v[d], fmin(v[3 + d], v[6 + d]));
+    h[d] = fmax(v[d], fmax(v[3 + d], v[6 + d]));
+  }
+  box_bin_range(l, h, B, i0, i1);
+}
+
+__global__ void k_bin_count(const double *tv, int ntri, TriBins B, long long *cnt, uint2 *range) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntri) return;
+  int i0[3], i1[3];
+  tri_bin_range(tv + 9 * t, B, i0, i1);
+  range[t] = make_uint2((unsigned)i0[0] | ((unsigned)i0[1] << 8) | ((unsigned)i0[2] << 16),
+                        (unsigned)i1[0] | ((unsigned)i1[1] << 8) | ((unsigned)i1[2] << 16));
+  for (int k = i0[2]; k <= i1[2]; ++k)
+    for (int j = i0[1]; j <= i1[1]; ++j)
+      for (int i = i0[0]; i <= i1[0]; ++i)
+        atomicAdd(reinterpret_cast<unsigned long long *>(cnt) + ((long long)k * B.nb[1] + j) * B.nb[0] + i, 1ULL);
+}
+
+// the order inside a bin is arbitrary: the search's result does not depend on it
+__global__ void k_bin_fill(const double *tv, int ntri, TriBins B, const long long *off, long long *cur, int *tri) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntri) return;
+  int i0[3], i1[3];
+  tri_bin_range(tv + 9 * t, B, i0, i1);
+  for (int k = i0[2]; k <= i1[2]; ++k)
+    for (int j = i0[1]; j <= i1[1]; ++j)
+      for (int i = i0[0]; i <= i1[0]; ++i) {
+        const long long b = ((long long)k * B.nb[1] + j) * B.nb[0] + i;
+        tri[off[b] + (long long)atomicAdd(reinterpret_cast<unsigned long long *>(cur) + b, 1ULL)] = t;
+      }
 }
 
 struct GhostArgs {
@@ -394,9 +453,9 @@ struct GhostArgs {
   const double *cxm, *cxp, *cym, *cyp, *czm, *czp;
   const uint8_t *ib;
   const double *tv;        // ntri x 9 vertex coordinates
-  const float4 *blo, *bhi, *cen;
-  const MeshRange *mr;
-  int nmesh;
+  const float4 *blo, *bhi; // triangle boxes, outward-rounded to float
+  const float4 *cen;       // triangle centroids (float)
+  TriBins bins;
   long long ng;
   const long long *gcell;
   double *bi, *ip, *w, *scale;
@@ -424,54 +483,136 @@ __device__ __forceinline__ void warp_argmin(double &d, int &t, float &f) {
   (void)f;
 }
 
-// closest triangle to P over all meshes of a (lowest index on exact ties): each lane of the
-// warp scans a share, the warp reduces; every lane returns the result
-__device__ void find_closest(const GhostArgs &a, const double P[3], int lane, double &best, int &bidx) {
-  float Pf[3] = {(float)P[0], (float)P[1], (float)P[2]};
-  // pass 1: an initial candidate from the nearest mesh box, by centroid distance
-  int m0 = 0;
-  double md = 1e300;
-  for (int m = 0; m < a.nmesh; ++m) {
-    double d = mesh_box_dist(P, a.mr[m]);
-    if (d < md) { md = d; m0 = m; }
-  }
-  float bc = 3.4e38f;
-  int bt = a.mr[m0].t0;
-  for (int t = a.mr[m0].t0 + lane; t < a.mr[m0].t1; t += 32) {
-    float4 c = a.cen[t];
-    float dx = c.x - Pf[0], dy = c.y - Pf[1], dz = c.z - Pf[2];
-    float d = dx * dx + dy * dy + dz * dz;
-    if (d < bc) { bc = d; bt = t; }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    float ob = __shfl_xor_sync(0xffffffffu, bc, o);
-    int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-    if (ob < bc || (ob == bc && ot < bt)) { bc = ob; bt = ot; }
-  }
-  double Q[3];
-  closest_on_tri(P, a.tv + 9 * bt, a.tv + 9 * bt + 3, a.tv + 9 * bt + 6, Q, best);
-  bidx = bt;
-  // pass 2: every triangle whose box could hold a point as close (conservative margin);
-  // each lane keeps its own best, then the warp reduces
-  double thr = sqrt(best) + 4e-6;
-  for (int m = 0; m < a.nmesh; ++m) {
-    if (mesh_box_dist(P, a.mr[m]) > thr) continue;
-    for (int t = a.mr[m].t0 + lane; t < a.mr[m].t1; t += 32) {
-      float lb = box_dist2(Pf, a.blo[t], a.bhi[t]);
-      if ((double)lb > thr * thr) continue;
-      double d2, Qt[3];
-      closest_on_tri(P, a.tv + 9 * t, a.tv + 9 * t + 3, a.tv + 9 * t + 6, Qt, d2);
-      if (d2 < best || (d2 == best && t < bidx)) {
-        best = d2; bidx = t;
-        thr = sqrt(best) + 4e-6;
+// per-warp candidate list of the closest-triangle search (shared memory)
+constexpr int CAND_MAX = 64;
+constexpr int TABLE_THREADS = 128;
+
+// The closest triangle to P (minimum squared distance, lowest index on exact ties) and the
+// closest point Q on it: the warp visits the bins in Chebyshev shells around P's bin (first
+// the whole 3 x 3 x 3 block, then r = 2, 3, ...) and stops once every unvisited bin lies
+// farther than the best distance found (plus a margin covering the float boxes).  In a
+// shell a triangle is taken once, from the first bin of its range inside the visited block,
+// and only if no earlier shell met its range.  The nearest centroid bounds the distance
+// first; triangles whose box is not farther than the bound are gathered into the warp's
+// list cq and evaluated exactly, spread over the lanes.  Every triangle that could be the
+// minimum or tie with it is evaluated, so the result equals a scan over all triangles.
+// Every lane returns the result.
+__device__ void find_closest(const GhostArgs &a, const double P[3], int lane, double &best, int &bidx, double Q[3],
+                             int *cq) {
+  const TriBins &B = a.bins;
+  const float Pf[3] = {(float)P[0], (float)P[1], (float)P[2]};
+  int c[3];
+  for (int d = 0; d < 3; ++d)
+    c[d] = (int)fmin(fmax(floor((P[d] - B.lo[d]) * B.inv), 0.0), (double)(B.nb[d] - 1));
+  double lb = 1e300, lq[3] = {0.0, 0.0, 0.0};   // this lane's best
+  int lt = 0x7fffffff;
+  best = 1e300;
+  bidx = 0x7fffffff;
+  double thr = 1e300;
+  auto consider = [&](int t) {
+    double d2, Qt[3];
+    closest_on_tri(P, a.tv + 9 * t, a.tv + 9 * t + 3, a.tv + 9 * t + 6, Qt, d2);
+    if (d2 < lb || (d2 == lb && t < lt)) {
+      lb = d2; lt = t;
+      lq[0] = Qt[0]; lq[1] = Qt[1]; lq[2] = Qt[2];
+    }
+  };
+  for (int r = 1;; ++r) {
+    const int w = 2 * r + 1;
+    const long long ncube = (long long)w * w * w;
+    int vl[3], vh[3], pl[3], ph[3];   // visited block after this shell, and before it
+    for (int d = 0; d < 3; ++d) {
+      vl[d] = max(c[d] - r, 0); vh[d] = min(c[d] + r, B.nb[d] - 1);
+      pl[d] = max(c[d] - r + 1, 0); ph[d] = min(c[d] + r - 1, B.nb[d] - 1);
+    }
+    auto shell_bin = [&](long long q, int bc[3]) -> long long {   // bin of cube cell q, or -1
+      const int dx = (int)(q % w) - r, dy = (int)((q / w) % w) - r, dz = (int)(q / ((long long)w * w)) - r;
+      if (r > 1 && max(abs(dx), max(abs(dy), abs(dz))) != r) return -1;
+      bc[0] = c[0] + dx; bc[1] = c[1] + dy; bc[2] = c[2] + dz;
+      if (bc[0] < 0 || bc[1] < 0 || bc[2] < 0 || bc[0] >= B.nb[0] || bc[1] >= B.nb[1] || bc[2] >= B.nb[2]) return -1;
+      return ((long long)bc[2] * B.nb[1] + bc[1]) * B.nb[0] + bc[0];
+    };
+    // is this the triangle's own visit: the first bin of its range in the block, and its
+    // range did not meet the block of the earlier shells
+    auto own_visit = [&](int t, const int bc[3]) {
+      const uint2 rg = B.range[t];
+      int f[3], g[3];
+      range_meets(rg, vl, vh, f);
+      if (f[0] != bc[0] || f[1] != bc[1] || f[2] != bc[2]) return false;
+      return r == 1 || !range_meets(rg, pl, ph, g);
+    };
+    // the distance to a centroid bounds the distance to its triangle (relative margin for
+    // the float arithmetic)
+    float cb = 3.4e38f;
+    for (long long q = lane; q < ncube; q += 32) {
+      int bc[3];
+      const long long bin = shell_bin(q, bc);
+      if (bin < 0) continue;
+      for (long long e = B.off[bin]; e < B.off[bin + 1]; ++e) {
+        const float4 cc = a.cen[B.tri[e]];
+        const float dx = cc.x - Pf[0], dy = cc.y - Pf[1], dz = cc.z - Pf[2];
+        cb = fminf(cb, dx * dx + dy * dy + dz * dz);
       }
     }
+    for (int o = 16; o > 0; o >>= 1) cb = fminf(cb, __shfl_xor_sync(0xffffffffu, cb, o));
+    if (cb < 3.4e38f) thr = fmin(thr, sqrt((double)cb) * (1.0 + 1e-5) + 4e-6);
+    const double thr2 = thr * thr;
+    // chunks of 32 bins: candidates into the list (a lane whose share does not fit
+    // evaluates the rest itself), then the list over the lanes
+    for (long long q0 = 0; q0 < ncube; q0 += 32) {
+      const long long q = q0 + lane;
+      int bc[3];
+      const long long bin = q < ncube ? shell_bin(q, bc) : -1;
+      int n = 0;
+      if (bin >= 0)
+        for (long long e = B.off[bin]; e < B.off[bin + 1]; ++e) {
+          const int t = B.tri[e];
+          if ((double)box_dist2(Pf, a.blo[t], a.bhi[t]) <= thr2 && own_visit(t, bc)) ++n;
+        }
+      int pre = n;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, pre, 31);
+      pre -= n;
+      if (n > 0) {
+        int k = pre;
+        for (long long e = B.off[bin]; e < B.off[bin + 1]; ++e) {
+          const int t = B.tri[e];
+          if ((double)box_dist2(Pf, a.blo[t], a.bhi[t]) > thr2 || !own_visit(t, bc)) continue;
+          if (k < CAND_MAX) cq[k] = t;
+          else consider(t);
+          ++k;
+        }
+      }
+      __syncwarp();
+      for (int k = lane; k < min(total, CAND_MAX); k += 32) consider(cq[k]);
+      __syncwarp();
+    }
+    best = lb;
+    bidx = lt;
+    float unused = 0.f;
+    warp_argmin(best, bidx, unused);
+    thr = sqrt(best) + 4e-6;
+    // distance from P to the bins outside the visited cube
+    double lv = 1e300;
+    bool more = false;
+    for (int d = 0; d < 3; ++d) {
+      if (c[d] - r - 1 >= 0) { more = true; lv = fmin(lv, P[d] - (B.lo[d] + (c[d] - r) * B.h)); }
+      if (c[d] + r + 1 < B.nb[d]) { more = true; lv = fmin(lv, (B.lo[d] + (c[d] + r + 1) * B.h) - P[d]); }
+    }
+    if (!more || lv > thr) break;
   }
-  float unused = 0.f;
-  warp_argmin(best, bidx, unused);
+  // the closest point from a lane that evaluated the winning triangle (same arithmetic on
+  // every lane, so any of them)
+  const unsigned own = __ballot_sync(0xffffffffu, lt == bidx && lb == best);
+  const int src = own ? __ffs(own) - 1 : 0;
+  for (int d = 0; d < 3; ++d) Q[d] = __shfl_sync(0xffffffffu, lq[d], src);
 }
 
-__global__ void k_ghost_tables(GhostArgs a) {
+__global__ void __launch_bounds__(TABLE_THREADS) k_ghost_tables(GhostArgs a) {
+  __shared__ int cand[TABLE_THREADS / 32][CAND_MAX];
   const int lane = threadIdx.x & 31;
   long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (g >= a.ng) return;
@@ -481,12 +622,10 @@ __global__ void k_ghost_tables(GhostArgs a) {
   int gj = (int)((lin / nx) % ny);
   int gk = (int)(lin / ((long long)nx * ny));
   double P[3] = {a.xc[gi], a.yc[gj], a.zc[gk]};
-  double best;
+  double best, BQ[3];
   int bidx;
-  find_closest(a, P, lane, best, bidx);
+  find_closest(a, P, lane, best, bidx, BQ, cand[threadIdx.x >> 5]);
   if (lane != 0) return;
-  double BQ[3];
-  closest_on_tri(P, a.tv + 9 * bidx, a.tv + 9 * bidx + 3, a.tv + 9 * bidx + 6, BQ, best);
   double IP[3];
   for (int d = 0; d < 3; ++d) {
     IP[d] = (BQ[d] + BQ[d]) - P[d];
@@ -798,7 +937,8 @@ __device__ __forceinline__ bool seg_cut_tri(const long long P[3], const long lon
 // one warp per entry: boundary intercept and image point (as for closed bodies), corners
 // blocked by the membrane (exact segment tests), same-side entries for blocked corners,
 // weights, fallback and row scale
-__global__ void k_mem_tables(GhostArgs a, MemArgs m) {
+__global__ void __launch_bounds__(TABLE_THREADS) k_mem_tables(GhostArgs a, MemArgs m) {
+  __shared__ int cand[TABLE_THREADS / 32][CAND_MAX];
   const int lane = threadIdx.x & 31;
   const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (g >= a.ng) return;
@@ -807,11 +947,9 @@ __global__ void k_mem_tables(GhostArgs a, MemArgs m) {
   const unsigned gs = m.gside[g];
   const int gi = (int)(lin % nx), gj = (int)((lin / nx) % ny), gk = (int)(lin / ((long long)nx * ny));
   double P[3] = {a.xc[gi], a.yc[gj], a.zc[gk]};
-  double best;
+  double best, BQ[3];
   int bidx;
-  find_closest(a, P, lane, best, bidx);
-  double BQ[3];
-  closest_on_tri(P, a.tv + 9 * bidx, a.tv + 9 * bidx + 3, a.tv + 9 * bidx + 6, BQ, best);
+  find_closest(a, P, lane, best, bidx, BQ, cand[threadIdx.x >> 5]);
   double IP[3];
   for (int d = 0; d < 3; ++d) IP[d] = (BQ[d] + BQ[d]) - P[d];
   int i0, j0, k0;
@@ -828,19 +966,34 @@ __global__ void k_mem_tables(GhostArgs a, MemArgs m) {
     // segment box, widened past the snapping distance (2^-25) and FP32 rounding, so the box
     // filter never drops a triangle the exact test would count
     float lo[3], hi[3];
+    double dlo[3], dhi[3];
     for (int d = 0; d < 3; ++d) {
-      const double e0 = (double)min(SIP[d], Q[d]) / SNAP_SCALE, e1 = (double)max(SIP[d], Q[d]) / SNAP_SCALE;
-      lo[d] = __double2float_rd(e0 - 1e-6);
-      hi[d] = __double2float_ru(e1 + 1e-6);
+      dlo[d] = (double)min(SIP[d], Q[d]) / SNAP_SCALE - 1e-6;
+      dhi[d] = (double)max(SIP[d], Q[d]) / SNAP_SCALE + 1e-6;
+      lo[d] = __double2float_rd(dlo[d]);
+      hi[d] = __double2float_ru(dhi[d]);
     }
+    // a triangle that crosses the segment meets its box, so it is listed in a bin the box
+    // meets; lanes split each bin's list (a triangle listed in several bins is tested again)
+    int b0[3], b1[3];
+    box_bin_range(dlo, dhi, a.bins, b0, b1);
     bool hit = false;
-    for (int t = lane; t < m.ntri && !hit; t += 32) {
-      const float4 bl = a.blo[t], bh = a.bhi[t];
-      if (bl.x > hi[0] || bh.x < lo[0] || bl.y > hi[1] || bh.y < lo[1] || bl.z > hi[2] || bh.z < lo[2]) continue;
-      long long v[3][3];
-      snap_tri(a.tv, t, v);
-      if (seg_cut_tri(SIP, Q, v)) hit = true;
-    }
+    for (int bz = b0[2]; bz <= b1[2]; ++bz)
+      for (int by = b0[1]; by <= b1[1]; ++by)
+        for (int bx = b0[0]; bx <= b1[0]; ++bx) {
+          const long long bin = ((long long)bz * a.bins.nb[1] + by) * a.bins.nb[0] + bx;
+          for (long long e = a.bins.off[bin] + lane; e < a.bins.off[bin + 1] && !hit; e += 32) {
+            const int t = a.bins.tri[e];
+            int f[3];   // test each triangle once: in the first bin of its range inside the box
+            range_meets(a.bins.range[t], b0, b1, f);
+            if (f[0] != bx || f[1] != by || f[2] != bz) continue;
+            const float4 bl = a.blo[t], bh = a.bhi[t];
+            if (bl.x > hi[0] || bh.x < lo[0] || bl.y > hi[1] || bh.y < lo[1] || bl.z > hi[2] || bh.z < lo[2]) continue;
+            long long v[3][3];
+            snap_tri(a.tv, t, v);
+            if (seg_cut_tri(SIP, Q, v)) hit = true;
+          }
+        }
     if (__any_sync(0xffffffffu, hit)) blocked |= 1u << c;
   }
   if (lane != 0) return;
@@ -965,6 +1118,68 @@ struct Scratch {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// bounding box and total area of the meshes' triangles (host arrays)
+struct TriStats {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  double area = 0.0;
+  void add(const ibm_mesh &m) {
+    for (long long t = 0; t < m.ntris; ++t) {
+      const double *v[3];
+      for (int q = 0; q < 3; ++q) {
+        v[q] = m.verts + 3LL * m.tris[3 * t + q];
+        for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], v[q][d]); hi[d] = std::max(hi[d], v[q][d]); }
+      }
+      const double u[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+      const double w[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+      const double c[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+      area += 0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    }
+  }
+};
+
+// Bins for the closest-triangle search: edge twice the square root of the mean triangle
+// area (a few triangles per bin near the surface), at most 256 bins per axis (the per-
+// triangle ranges are stored as bytes) and 2^20 in total.  One readback (the number of
+// entries) sizes the index list.
+cudaError_t build_bins(Scratch &S, const double *tv, int ntri, const TriStats &ts, cudaStream_t st, TriBins &B) {
+  double ext = 0.0;
+  for (int d = 0; d < 3; ++d) ext = std::max(ext, ts.hi[d] - ts.lo[d]);
+  double h = 2.0 * std::sqrt(ts.area / std::max(1, ntri));
+  h = std::max({h, ext / 255.0, 1e-12});   // <= 256 bins per axis: bin indices fit in a byte
+  auto nbins = [&](double hh) {
+    long long n = 1;
+    for (int d = 0; d < 3; ++d) n *= (long long)std::floor((ts.hi[d] - ts.lo[d]) / hh) + 1;
+    return n;
+  };
+  while (nbins(h) > (1LL << 20)) h *= 1.25;
+  for (int d = 0; d < 3; ++d) {
+    B.lo[d] = ts.lo[d];
+    B.nb[d] = (int)std::floor((ts.hi[d] - ts.lo[d]) / h) + 1;
+  }
+  B.h = h;
+  B.inv = 1.0 / h;
+  const long long nb = (long long)B.nb[0] * B.nb[1] * B.nb[2];
+  long long *cnt = nullptr, *off = nullptr;
+  int *tri = nullptr;
+  cudaError_t e;
+  if ((e = S.get(&cnt, nb)) != cudaSuccess || (e = S.get(&off, nb + 1)) != cudaSuccess) return e;
+  uint2 *range = nullptr;
+  if ((e = S.get(&range, ntri)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(long long) * nb, st)) != cudaSuccess) return e;
+  k_bin_count<<<nblk(ntri, 128), 128, 0, st>>>(tv, ntri, B, cnt, range);
+  k_scan_single<<<1, 1024, 0, st>>>(cnt, off, (int)nb);
+  long long total = 0;
+  if ((e = cudaMemcpyAsync(&total, off + nb, sizeof(long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  if ((e = S.get(&tri, total)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(long long) * nb, st)) != cudaSuccess) return e;
+  k_bin_fill<<<nblk(ntri, 128), 128, 0, st>>>(tv, ntri, B, off, cnt, tri);
+  B.off = off;
+  B.tri = tri;
+  B.range = range;
+  return cudaGetLastError();
+}
+
 ibm_status check_meshes(const ibm_mesh *meshes, int nmesh, long long &totverts, long long &tottris) {
   if (nmesh < 0 || (nmesh > 0 && !meshes)) return IBM_ERR_INVALID_ARG;
   totverts = tottris = 0;
@@ -1030,7 +1245,7 @@ ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
   MTRY(S.get(&dverts, 3 * totverts));
   MTRY(S.get(&dtris, 3 * tottris));
   MTRY(S.get(&tv, 9 * tottris));
-  std::vector<MeshRange> hmr;
+  TriStats ts;
   long long vo = 0, to = 0;
   for (int m = 0; m < nmesh; ++m) {
     const int nt = meshes[m].ntris;
@@ -1040,14 +1255,7 @@ ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     if (nt) {
       MTRY(cudaMemcpyAsync(dtris + 3 * to, meshes[m].tris, 3 * sizeof(int) * nt, cudaMemcpyHostToDevice, st));
       k_gather_tris<<<nblk(nt, 128), 128, 0, st>>>(dverts + 3 * vo, dtris + 3 * to, nt, tv + 9 * to);
-      MeshRange r;
-      r.t0 = (int)to; r.t1 = (int)to + nt;
-      for (int d = 0; d < 3; ++d) { r.lo[d] = 1e300; r.hi[d] = -1e300; }
-      for (long long q = 0; q < 3LL * nt; ++q) {
-        const double *v = meshes[m].verts + 3LL * meshes[m].tris[q];
-        for (int d = 0; d < 3; ++d) { r.lo[d] = std::min(r.lo[d], v[d]); r.hi[d] = std::max(r.hi[d], v[d]); }
-      }
-      hmr.push_back(r);
+      ts.add(meshes[m]);
     }
     vo += meshes[m].nverts;
     to += nt;
@@ -1097,27 +1305,24 @@ ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     float4 *blo = nullptr, *bhi = nullptr, *cen = nullptr;
     MTRY(S.get(&blo, ntri)); MTRY(S.get(&bhi, ntri)); MTRY(S.get(&cen, ntri));
     k_tri_boxes<<<nblk(ntri, 128), 128, 0, st>>>(tv, ntri, blo, bhi, cen);
-    MeshRange *dmr = nullptr;
-    MTRY(S.get(&dmr, hmr.size()));
-    MTRY(cudaMemcpyAsync(dmr, hmr.data(), hmr.size() * sizeof(MeshRange), cudaMemcpyHostToDevice, st));
     GhostArgs ga;
+    MTRY(build_bins(S, tv, ntri, ts, st, ga.bins));
     ga.nx = nx; ga.ny = ny; ga.nz = nz;
     ga.xc = dc[0]; ga.yc = dc[1]; ga.zc = dc[2];
     ga.cxm = dcm[0]; ga.cxp = dcp[0]; ga.cym = dcm[1]; ga.cyp = dcp[1]; ga.czm = dcm[2]; ga.czp = dcp[2];
     ga.ib = T->iblank;
     ga.tv = tv; ga.blo = blo; ga.bhi = bhi; ga.cen = cen;
-    ga.mr = dmr; ga.nmesh = (int)hmr.size();
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
     MemArgs ma;
     ma.ncell = ncell; ma.keys = T->gkeys; ma.gside = T->gside; ma.cut = T->cut; ma.side = T->cside;
     ma.Xs = ds[0]; ma.Ys = ds[1]; ma.Zs = ds[2]; ma.ntri = ntri;
-    k_mem_tables<<<nblk(32 * ng, 128), 128, 0, st>>>(ga, ma);
+    k_mem_tables<<<nblk(32 * ng, TABLE_THREADS), TABLE_THREADS, 0, st>>>(ga, ma);
     MTRY(cudaGetLastError());
   }
   MTRY(cudaStreamSynchronize(st));
-  ctx->launches += 4 + (ntri > 0 ? 3 : 0) + (ng > 0 ? 3 : 0);
+  ctx->launches += 4 + (ntri > 0 ? 3 : 0) + (ng > 0 ? 6 : 0);   // bins: count, scan, fill
 #undef MTRY
   return IBM_OK;
 }
@@ -1271,36 +1476,26 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     float4 *blo = nullptr, *bhi = nullptr, *cen = nullptr;
     CTRY(S.get(&tv, 9 * tottris));
     CTRY(S.get(&blo, tottris)); CTRY(S.get(&bhi, tottris)); CTRY(S.get(&cen, tottris));
-    std::vector<MeshRange> hmr;
+    TriStats ts;
     for (int m = 0; m < nmesh; ++m) {
       const int nt = meshes[m].ntris;
       if (nt == 0) continue;
       k_gather_tris<<<nblk(nt, 128), 128, 0, st>>>(dverts + 3LL * vbase[m], dtris + 3LL * tbase[m], nt,
                                                     tv + 9LL * tbase[m]);
-      MeshRange r;
-      r.t0 = tbase[m]; r.t1 = tbase[m] + nt;
-      for (int d = 0; d < 3; ++d) { r.lo[d] = 1e300; r.hi[d] = -1e300; }
-      for (long long q = 0; q < 3LL * nt; ++q) {
-        const double *v = meshes[m].verts + 3LL * meshes[m].tris[q];
-        for (int d = 0; d < 3; ++d) { r.lo[d] = std::min(r.lo[d], v[d]); r.hi[d] = std::max(r.hi[d], v[d]); }
-      }
-      hmr.push_back(r);
+      ts.add(meshes[m]);
     }
     k_tri_boxes<<<nblk(tottris, 128), 128, 0, st>>>(tv, (int)tottris, blo, bhi, cen);
-    MeshRange *dmr = nullptr;
-    CTRY(S.get(&dmr, hmr.size()));
-    CTRY(cudaMemcpyAsync(dmr, hmr.data(), hmr.size() * sizeof(MeshRange), cudaMemcpyHostToDevice, st));
     GhostArgs ga;
+    CTRY(build_bins(S, tv, (int)tottris, ts, st, ga.bins));
     ga.nx = nx; ga.ny = ny; ga.nz = nz;
     ga.xc = dc[0]; ga.yc = dc[1]; ga.zc = dc[2];
     ga.cxm = dcm[0]; ga.cxp = dcp[0]; ga.cym = dcm[1]; ga.cyp = dcp[1]; ga.czm = dcm[2]; ga.czp = dcp[2];
     ga.ib = T->iblank;
     ga.tv = tv; ga.blo = blo; ga.bhi = bhi; ga.cen = cen;
-    ga.mr = dmr; ga.nmesh = (int)hmr.size();
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
-    k_ghost_tables<<<nblk(32 * ng, 128), 128, 0, st>>>(ga);
+    k_ghost_tables<<<nblk(32 * ng, TABLE_THREADS), TABLE_THREADS, 0, st>>>(ga);
     CTRY(cudaGetLastError());
   }
   unsigned long long hc[2];
@@ -1310,7 +1505,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
   T->nsolid = (long long)hc[1];
   CTRY(S.finish());
   T->geom_version += 1;
-  ctx->launches += 2 + 2 * (long long)nmesh * 3 + 5 + (T->nghost > 0 ? 2 + (long long)nmesh : 0);
+  ctx->launches += 2 + 2 * (long long)nmesh * 3 + 5 + (T->nghost > 0 ? 5 + (long long)nmesh : 0);
 #undef CTRY
   return T->nfluid == 0 ? IBM_ERR_NO_FLUID : IBM_OK;
 }
