@@ -11,11 +11,11 @@
 // independent of the tiling).
 //
 // Each thread owns a fixed strip of 4 consecutive x-cells of the tile and keeps that strip's
-// values in planes q-1 .. q+1 in registers.  Red results go back to the plane's buffer
-// (their y-neighbours in other warps read them in the next step, and the strip's black
-// update two steps later reads its z-1 neighbours there); black results go only to
-// registers and global memory, since nothing in the march reads a black value after its
-// update.  x-neighbours across strips move by warp
+// values in planes q-2 .. q+1 in registers, with the rhs, mask and z coefficients of plane
+// q-1.  Red results go back to the plane's buffer (their y-neighbours in other warps read
+// them in the next step) and stay in the registers (the strip's black update two steps
+// later reads its z-1 neighbours there); black results go only to registers and global
+// memory, since nothing in the march reads a black value after its update.  x-neighbours across strips move by warp
 // shuffle; only the tile edges read the ring from shared memory.  A red update reads only
 // black cells and a black update only red ones, so the in-place writes never change a value
 // another thread reads in the same step: one barrier per step suffices.
@@ -47,11 +47,11 @@ constexpr int RING = 2 * RING_ROW + 2 * TY;  // ring strips (top, bottom, left, 
 static_assert(RING <= THREADS, "one ring strip per thread at most");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
-// prefetch distance in planes; rings hold the planes in use at step q (e: q-2 .. q+1,
-// rhs/mask: q-1 .. q) plus the ones in flight
+// prefetch distance in planes; rings hold the planes in use at step q (e: q-1 .. q+1,
+// rhs/mask: q) plus the ones in flight
 template <typename T> struct Depth { static constexpr int D = sizeof(T) == 4 ? 2 : 1; };
-template <typename T> constexpr int NE = 4 + Depth<T>::D;
-template <typename T> constexpr int NR = 2 + Depth<T>::D;
+template <typename T> constexpr int NE = 3 + Depth<T>::D;
+template <typename T> constexpr int NR = 1 + Depth<T>::D;
 
 constexpr int pad128(int bytes) { return (bytes + 127) / 128 * 128; }
 
@@ -250,7 +250,7 @@ __device__ __forceinline__ void relax_reg(const Strip<T> &S, Q4<T> &C, const Q4<
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
+__global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
                                                          const __grid_constant__ CUtensorMap tm_r,
                                                          const __grid_constant__ CUtensorMap tm_m, Args<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -293,59 +293,66 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
   }
   __syncthreads();
   const unsigned ebytes = EY * BX * sizeof(T), rbytes = RY * BX * sizeof(T) + RY * BXM;
+  // buffer slots: plane p lives in e slot (p + 2 NE) mod NE and rhs/mask slot (p + 2 NR) mod
+  // NR; the march advances the slots by one (wrapping) per step
+  auto wrap_e = [](int x) { return x >= NEt ? x - NEt : x; };
+  auto wrap_r = [](int x) { return x >= NRt ? x - NRt : x; };
   // padded coordinates: cell (i, j, k) at (i + OX, j + 1, k + 1); OX = 4
-  auto load_e = [&](int plane) {
-    int b = (plane + 2 * NEt) % NEt;
+  auto load_e = [&](int plane, int b) {
     mbar_expect_tx(&s.bar_e[b], ebytes);
     tma_load3(s.e[b], &tm_e, &s.bar_e[b], x0, y0 - 1, plane + 1);
   };
-  auto load_r = [&](int plane) {
-    int b = (plane + 2 * NRt) % NRt;
+  auto load_r = [&](int plane, int b) {
     mbar_expect_tx(&s.bar_r[b], rbytes);
     tma_load3(s.r[b], &tm_r, &s.bar_r[b], x0, y0, plane + 1);
     tma_load3(s.m[b], &tm_m, &s.bar_r[b], x0, y0, plane + 1);
   };
   unsigned pe = 0, pr = 0;   // bit b: parity of the next completion of buffer b
   bool bad = false;
-  auto wait_e = [&](int plane) {
-    int b = (plane + 2 * NEt) % NEt;
+  auto wait_e = [&](int b) {
     if (!bad && !mbar_wait(&s.bar_e[b], (pe >> b) & 1u)) bad = true;
     pe ^= 1u << b;
   };
-  auto wait_r = [&](int plane) {
-    int b = (plane + 2 * NRt) % NRt;
+  auto wait_r = [&](int b) {
     if (!bad && !mbar_wait(&s.bar_r[b], (pr >> b) & 1u)) bad = true;
     pr ^= 1u << b;
   };
-  auto ebuf = [&](int plane) { return s.e[(plane + 2 * NEt) % NEt]; };
+  const int se0 = (k0 - 2 + 2 * NEt) % NEt, sr0 = (k0 - 1 + 2 * NRt) % NRt;   // planes k0 - 2 / k0 - 1
   // prologue: e planes k0-2 .. k0-1+DP and rhs/mask planes k0-1 .. k0-2+DP.  Step q waits
   // for e plane q+1 and rhs/mask plane q and, after the step's barrier (so no thread still
   // reads the buffers being refilled), prefetches e plane q+1+DP (into the buffer of plane
-  // q-3) and rhs/mask plane q+DP (buffer of plane q-2).  Every load is issued once and
-  // waited for once.
+  // q-2, last read in step q-1) and rhs/mask plane q+DP (buffer of plane q-1).  Every load
+  // is issued once and waited for once.
   if (tid == 0) {
-    for (int pl = k0 - 2; pl <= min(k0 - 1 + DP, k1 + 1); ++pl) load_e(pl);
-    for (int pl = k0 - 1; pl <= min(k0 - 2 + DP, k1); ++pl) load_r(pl);
+    for (int pl = k0 - 2, b = se0; pl <= min(k0 - 1 + DP, k1 + 1); ++pl, b = wrap_e(b + 1)) load_e(pl, b);
+    for (int pl = k0 - 1, b = sr0; pl <= min(k0 - 2 + DP, k1); ++pl, b = wrap_r(b + 1)) load_r(pl, b);
   }
-  wait_e(k0 - 2);
-  wait_e(k0 - 1);
-  // registers: the strip in planes q-1 (Cm1) and q (C0)
-  Q4<T> Cm1 = ld4(ebuf(k0 - 2) + Si.ie), C0 = ld4(ebuf(k0 - 1) + Si.ie);
+  int sq = wrap_e(se0 + 1), rq = sr0;   // slots of plane q (e, rhs/mask)
+  wait_e(se0);
+  wait_e(sq);
+  // registers: the strip in planes q-2 (Cm2; its red cells are final once plane q-2's red
+  // pass is done), q-1 (Cm1) and q (C0); the rhs, mask and z coefficients of plane q-1
+  Q4<T> Cm1 = ld4(s.e[se0] + Si.ie), C0 = ld4(s.e[sq] + Si.ie), Cm2 = Cm1;
+  Q4<T> Rb = Cm1;
+  unsigned Mb = 0u;
+  T czm_b = (T)0, czp_b = (T)0, sz_b = (T)0;
   const T sh = a.shift ? (T)(*a.shift) : (T)0;
   const float om = a.omega;
+  T *const dst0 = a.out + (long long)(y0 + Si.y + 1) * a.px + (x0 + Si.xs + 4);
   for (int q = k0 - 1; q <= k1; ++q) {
-    wait_e(q + 1);
-    wait_r(q);
+    const int sp1 = wrap_e(sq + 1), sm1 = sq == 0 ? NEt - 1 : sq - 1;
+    wait_e(sp1);
+    wait_r(rq);
     if (__syncthreads_or(bad)) break;
     if (tid == 0) {
       fence_proxy_async();
-      if (q + 1 + DP <= k1 + 1) load_e(q + 1 + DP);
-      if (q + DP <= k1) load_r(q + DP);
+      if (q + 1 + DP <= k1 + 1) load_e(q + 1 + DP, wrap_e(sp1 + DP));
+      if (q + DP <= k1) load_r(q + DP, wrap_r(rq + DP));
     }
-    T *P = ebuf(q), *Pm = ebuf(q - 1);
-    const T *Pp = ebuf(q + 1);
-    const T *R = s.r[(q + 2 * NRt) % NRt];
-    const uint8_t *M = s.m[(q + 2 * NRt) % NRt];
+    T *P = s.e[sq], *Pm = s.e[sm1];
+    const T *Pp = s.e[sp1];
+    const T *R = s.r[rq];
+    const uint8_t *M = s.m[rq];
     const Q4<T> U = ld4(Pp + Si.ie);
     // x-edges: the cell west of u = 0 and east of u = 3, from the adjacent lanes (same row),
     // or from the ring in shared memory at the tile edges; all lanes take part
@@ -354,11 +361,14 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
     if (l16 == 0) { wr = P[Si.ie - 1]; wb = Pm[Si.ie - 1]; }
     if (l16 == 15) { er = P[Si.ie + 4]; eb = Pm[Si.ie + 4]; }
     // red cells of plane q on the tile (from registers) and the ring (from shared memory)
+    T czm = (T)0, czp = (T)0, sz = (T)0;
+    Q4<T> R0 = Rb;
+    unsigned M0 = 0u;
     if (q >= 0 && q < a.nz) {
-      const T czm = a.czm[q], czp = a.czp[q], sz = a.sdz[q];
+      czm = a.czm[q]; czp = a.czp[q]; sz = a.sdz[q];
       const Q4<T> N = ld4(P + Si.ie - BX), So = ld4(P + Si.ie + BX);
-      const Q4<T> R0 = ld4(R + Si.ir);
-      const unsigned M0 = *reinterpret_cast<const unsigned *>(M + Si.im);
+      R0 = ld4(R + Si.ir);
+      M0 = *reinterpret_cast<const unsigned *>(M + Si.im);
       if (((Si.par + q) & 1) == 0)
         relax_reg<0, T>(Si, C0, N, So, Cm1, U, R0, M0, wr, er, czm, czp, sz, sh, om);
       else
@@ -369,23 +379,17 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
         relax_colour<T>(ring[tid], P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, Cr);
       }
     }
-    // black cells of plane q-1 on the tile: neighbours all red, updated by now; store the
-    // strip from registers
+    // black cells of plane q-1 on the tile: neighbours all red, updated by now (in-plane ones
+    // in shared memory, the z-neighbours in Cm2 and C0); store the strip from registers
     const int kb = q - 1;
     if (kb >= k0 && kb < k1) {
-      const T czm = a.czm[kb], czp = a.czp[kb], sz = a.sdz[kb];
       const Q4<T> N = ld4(Pm + Si.ie - BX), So = ld4(Pm + Si.ie + BX);
-      const Q4<T> Zm = ld4(ebuf(kb - 1) + Si.ie);   // red values of plane q-2, in place
-      const T *Rb = s.r[(kb + 2 * NRt) % NRt];
-      const Q4<T> Rm1 = ld4(Rb + Si.ir);
-      const unsigned Mm1 = *reinterpret_cast<const unsigned *>(s.m[(kb + 2 * NRt) % NRt] + Si.im);
       if (((Si.par + kb + 1) & 1) == 0)
-        relax_reg<0, T>(Si, Cm1, N, So, Zm, C0, Rm1, Mm1, wb, eb, czm, czp, sz, sh, om);
+        relax_reg<0, T>(Si, Cm1, N, So, Cm2, C0, Rb, Mb, wb, eb, czm_b, czp_b, sz_b, sh, om);
       else
-        relax_reg<1, T>(Si, Cm1, N, So, Zm, C0, Rm1, Mm1, wb, eb, czm, czp, sz, sh, om);
+        relax_reg<1, T>(Si, Cm1, N, So, Cm2, C0, Rb, Mb, wb, eb, czm_b, czp_b, sz_b, sh, om);
       if (Si.valid) {
-        const int gj = y0 + Si.y, gi = x0 + Si.xs;
-        T *dst = a.out + ((long long)(kb + 1) * (a.ny + 2) + (gj + 1)) * a.px + (gi + 4);
+        T *dst = dst0 + (long long)(kb + 1) * a.sz;
         if (Si.valid == 0xfu) {
           st4(dst, Cm1);
         } else {
@@ -394,8 +398,14 @@ __global__ void __launch_bounds__(THREADS) k_sweep_zmarch(const __grid_constant_
         }
       }
     }
+    Cm2 = Cm1;
     Cm1 = C0;
     C0 = U;
+    Rb = R0;
+    Mb = M0;
+    czm_b = czm; czp_b = czp; sz_b = sz;
+    sq = sp1;
+    rq = wrap_r(rq + 1);
   }
   if (bad) {
     if (tid == 0) {
