@@ -2,9 +2,10 @@
 // TMA-staged planes in shared memory.
 //
 // One CTA owns an x-y tile (TX x TY) and a z-range [k0, k1).  Step q of the march
-//   1. updates the red cells of plane q on the tile plus a one-cell ring (the ring is
-//      recomputed by both neighbouring CTAs, so no inter-CTA exchange is needed), in place
-//      in plane q's shared buffer;
+//   1. updates the red cells of plane q on the tile plus the one-cell ring that the tile's
+//      black cells read (rows -1 and TY over the tile's x range, columns -1 and TX over its
+//      y range; the ring is recomputed by both neighbouring CTAs, in the same operation
+//      order, so no inter-CTA exchange is needed), in place in plane q's shared buffer;
 //   2. updates the black cells of plane q-1 on the tile and stores plane q-1 of the tile.
 // Every value is read from the input array and written to a separate output array, so the
 // result is exactly one red half-sweep followed by one black half-sweep (deterministic,
@@ -42,9 +43,10 @@ constexpr int BXM = TX + 16;    // staged width of the mask (an 8-bit box row mu
 constexpr int EY = TY + 4;      // e rows: y in [-2, TY + 2)
 constexpr int RY = TY + 2;      // rhs / mask rows: y in [-1, TY + 1)
 constexpr int THREADS = (TX / 4) * TY;       // one interior strip per thread
-constexpr int RING_ROW = TX / 4 + 2;         // strips per ring row (x from -4 to TX + 3)
-constexpr int RING = 2 * RING_ROW + 2 * TY;  // ring strips (top, bottom, left, right)
-static_assert(RING <= THREADS, "one ring strip per thread at most");
+constexpr int RING = 2 * (TX / 4);           // ring row strips (rows -1 and TY, x in [0, TX)): warp 0
+constexpr int CELL_WARP = 1;                 // the warp of the ring column cells
+constexpr int CELLS = TY;                    // ring column cells per plane (the red one of each y pair)
+static_assert(RING == 32 && CELLS <= 32 && THREADS >= 64, "ring rows fill warp 0, the columns fit warp 1");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 // prefetch distance in planes; rings hold the planes in use at step q (e: q-1 .. q+1,
@@ -218,6 +220,24 @@ __device__ __forceinline__ void relax_colour(const Strip<T> &S, T *P, const T *P
   st4(P + ie, C);
 }
 
+// one cell at ie of plane buffer P, in the same operation order as relax_colour / relax_reg
+// (so a ring cell gets the bits its owner computes)
+template <typename T>
+__device__ __forceinline__ void relax_cell(T *P, const T *Pm, const T *Pp, int ie, T rh, T cxm, T cxp, T cym, T cyp,
+                                           T sx, T sy, T czm, T czp, T sz, T sh, float om) {
+  const T c = P[ie];
+  const T syz = sy + sz;
+  const T D = sx + syz;
+  T sum = cxm * P[ie - 1];
+  sum += cxp * P[ie + 1];
+  sum += cym * P[ie - BX];
+  sum += cyp * P[ie + BX];
+  sum += czm * Pm[ie];
+  sum += czp * Pp[ie];
+  const T res = (sum - D * c) - (rh - sh);
+  P[ie] = c + (T)__fdividef(om * (float)res, (float)D);
+}
+
 // Interior strip update from registers: cells u = UA and UA + 2 of C (UA warp-uniform: a
 // warp's rows share one parity), neighbours N/So (rows y -1 / +1 of the same plane), Zm/Zp
 // (the strip in planes k -1 / +1), west/east (the cells left of u = 0 and right of u = 3).
@@ -279,18 +299,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_consta
     make_strip(Si, a, x0, y0, 4 * l16, y, 0, TX - 1);
   }
   const bool has_ring = tid < RING;
-  if (has_ring) {
-    int xs = 0, y = 0;
-    if (tid < 2 * RING_ROW) {
-      y = tid < RING_ROW ? -1 : TY;
-      xs = -4 + 4 * (tid % RING_ROW);
-    } else {
-      const int r = tid - 2 * RING_ROW;
-      y = r % TY;
-      xs = r < TY ? -4 : TX;
-    }
-    make_strip(ring[tid], a, x0, y0, xs, y, -1, TX);
-  }
+  if (has_ring) make_strip(ring[tid], a, x0, y0, 4 * (tid & 15), tid < 16 ? -1 : TY, 0, TX - 1);
+  const bool has_cell = (tid >> 5) == CELL_WARP && (tid & 31) < CELLS;
   __syncthreads();
   const unsigned ebytes = EY * BX * sizeof(T), rbytes = RY * BX * sizeof(T) + RY * BXM;
   // buffer slots: plane p lives in e slot (p + 2 NE) mod NE and rhs/mask slot (p + 2 NR) mod
@@ -377,6 +387,16 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_consta
       if (has_ring && ring[tid].valid) {
         Q4<T> Cr;
         relax_colour<T>(ring[tid], P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, Cr);
+      }
+      // ring column cell of this lane (warp CELL_WARP, lanes < CELLS): x = -1 or TX, y the
+      // red one of (2i, 2i + 1)
+      const int cl = tid & 31, cx = (cl >= CELLS / 2) ? TX : -1, cya = 2 * (cl % (CELLS / 2)), cgi = x0 + cx;
+      if (has_cell && cgi >= 0 && cgi < a.nx) {
+        const int cy = cya + ((cgi + y0 + cya + q) & 1), cgj = y0 + cy;
+        const int ie = (cy + 2) * BX + (cx + 4);
+        if (cgj < a.ny && M[(cy + 1) * BXM + (cx + 4)] == 0)
+          relax_cell<T>(P, Pm, Pp, ie, R[(cy + 1) * BX + (cx + 4)], a.cxm[cgi], a.cxp[cgi], a.cym[cgj], a.cyp[cgj],
+                        a.sdx[cgi], a.sdy[cgj], czm, czp, sz, sh, om);
       }
     }
     // black cells of plane q-1 on the tile: neighbours all red, updated by now (in-plane ones
