@@ -37,16 +37,18 @@ namespace ibm {
 namespace zm {
 
 constexpr int TX = 64;          // tile width (cells); multiple of 16
-constexpr int TY = 16;          // tile height
+constexpr int NS = 2;           // interior strips per thread: rows y and y + 16
+constexpr int TY = 16 * NS;     // tile height
 constexpr int BX = TX + 8;      // staged width of e and rhs: x in [-4, TX + 4)
 constexpr int BXM = TX + 16;    // staged width of the mask (an 8-bit box row must be 16-byte multiple)
 constexpr int EY = TY + 4;      // e rows: y in [-2, TY + 2)
 constexpr int RY = TY + 2;      // rhs / mask rows: y in [-1, TY + 1)
-constexpr int THREADS = (TX / 4) * TY;       // one interior strip per thread
+constexpr int THREADS = (TX / 4) * 16;       // NS interior strips per thread
 constexpr int RING = 2 * (TX / 4);           // ring row strips (rows -1 and TY, x in [0, TX)): warp 0
 constexpr int CELL_WARP = 1;                 // the warp of the ring column cells
 constexpr int CELLS = TY;                    // ring column cells per plane (the red one of each y pair)
 static_assert(RING == 32 && CELLS <= 32 && THREADS >= 64, "ring rows fill warp 0, the columns fit warp 1");
+static_assert(NS == 1 || NS == 2, "strips at rows y and y + 16 share the colour parity");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 // prefetch distance in planes; rings hold the planes in use at step q (e: q-1 .. q+1,
@@ -242,25 +244,26 @@ __device__ __forceinline__ void relax_cell(T *P, const T *Pm, const T *Pp, int i
 // warp's rows share one parity), neighbours N/So (rows y -1 / +1 of the same plane), Zm/Zp
 // (the strip in planes k -1 / +1), west/east (the cells left of u = 0 and right of u = 3).
 template <int UA, typename T>
-__device__ __forceinline__ void relax_reg(const Strip<T> &S, Q4<T> &C, const Q4<T> &N, const Q4<T> &So,
+__device__ __forceinline__ void relax_reg(const T (&cxm)[4], const T (&cxp)[4], const T (&sx)[4], unsigned valid,
+                                          T cym, T cyp, T sy, Q4<T> &C, const Q4<T> &N, const Q4<T> &So,
                                           const Q4<T> &Zm, const Q4<T> &Zp, const Q4<T> &Rh, unsigned m4, T west,
                                           T east, T czm, T czp, T sz, T sh, float om) {
   constexpr int u0 = UA, u1 = UA + 2;
-  const bool ok0 = ((S.valid >> u0) & 1u) && ((m4 >> (8 * u0)) & 0xffu) == 0u;
-  const bool ok1 = ((S.valid >> u1) & 1u) && ((m4 >> (8 * u1)) & 0xffu) == 0u;
-  const T syz = S.sy + sz;
+  const bool ok0 = ((valid >> u0) & 1u) && ((m4 >> (8 * u0)) & 0xffu) == 0u;
+  const bool ok1 = ((valid >> u1) & 1u) && ((m4 >> (8 * u1)) & 0xffu) == 0u;
+  const T syz = sy + sz;
   const T c0 = C.v[u0], c1 = C.v[u1];
-  const T D0 = S.sx[u0] + syz, D1 = S.sx[u1] + syz;
-  T s0 = S.cxm[u0] * (UA == 0 ? west : C.v[0]);
-  s0 += S.cxp[u0] * C.v[u0 + 1];
-  s0 += S.cym * N.v[u0];
-  s0 += S.cyp * So.v[u0];
+  const T D0 = sx[u0] + syz, D1 = sx[u1] + syz;
+  T s0 = cxm[u0] * (UA == 0 ? west : C.v[0]);
+  s0 += cxp[u0] * C.v[u0 + 1];
+  s0 += cym * N.v[u0];
+  s0 += cyp * So.v[u0];
   s0 += czm * Zm.v[u0];
   s0 += czp * Zp.v[u0];
-  T s1 = S.cxm[u1] * C.v[u1 - 1];
-  s1 += S.cxp[u1] * (UA == 1 ? east : C.v[3]);
-  s1 += S.cym * N.v[u1];
-  s1 += S.cyp * So.v[u1];
+  T s1 = cxm[u1] * C.v[u1 - 1];
+  s1 += cxp[u1] * (UA == 1 ? east : C.v[3]);
+  s1 += cym * N.v[u1];
+  s1 += cyp * So.v[u1];
   s1 += czm * Zm.v[u1];
   s1 += czp * Zp.v[u1];
   const T r0 = (s0 - D0 * c0) - (Rh.v[u0] - sh);
@@ -270,7 +273,7 @@ __device__ __forceinline__ void relax_reg(const Strip<T> &S, Q4<T> &C, const Q4<
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
+__global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
                                                          const __grid_constant__ CUtensorMap tm_r,
                                                          const __grid_constant__ CUtensorMap tm_m, Args<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -286,17 +289,38 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_consta
     for (int b = 0; b < NRt; ++b) mbar_init(&s.bar_r[b], 1);
     fence_mbar_init();
   }
-  // this thread's interior strip (registers), and the ring strips (red updates of the
-  // one-cell ring; shared memory, read only by their owners, once per step)
+  // this thread's interior strips (registers: x coefficients shared, y ones per strip), and
+  // the ring strips (red updates of the one-cell ring; shared memory, read only by their
+  // owners, once per step)
   __shared__ Strip<T> ring[RING];
-  Strip<T> Si;
   const int l16 = tid & 15;
-  {
-    // warps 0..THREADS/64-1 take the even rows, the others the odd rows, two rows per warp
-    // (lanes 0-15 and 16-31), so a warp's strips share one colour parity
-    const int w = tid >> 5, l = tid & 31, half = THREADS / 64;
-    const int y = 4 * (w % half) + (w >= half ? 1 : 0) + 2 * (l >> 4);
-    make_strip(Si, a, x0, y0, 4 * l16, y, 0, TX - 1);
+  // warps 0..3 take the even rows, warps 4..7 the odd rows of each 16-row half, two rows
+  // per warp (lanes 0-15 and 16-31), so a warp's strips share one colour parity; strip s
+  // lies 16 s rows below strip 0 (same parity)
+  const int ys = 4 * ((tid >> 5) & 3) + ((tid >> 5) >= 4 ? 1 : 0) + 2 * ((tid & 31) >> 4), xs = 4 * l16;
+  const int ie0 = (ys + 2) * BX + (xs + 4), ir0 = (ys + 1) * BX + (xs + 4), im0 = (ys + 1) * BXM + (xs + 4);
+  const int par = (x0 + xs + y0 + ys) & 1;
+  T cxm[4], cxp[4], sx[4];
+  unsigned xvalid = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int gi = x0 + xs + u;
+    const bool ok = gi < a.nx;
+    if (ok) xvalid |= 1u << u;
+    cxm[u] = ok ? a.cxm[gi] : (T)0;
+    cxp[u] = ok ? a.cxp[gi] : (T)0;
+    sx[u] = ok ? a.sdx[gi] : (T)0;
+  }
+  T cym[NS], cyp[NS], sy[NS];
+  unsigned valid[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const int gj = y0 + ys + 16 * q;
+    const bool jok = gj < a.ny;
+    valid[q] = jok ? xvalid : 0u;
+    cym[q] = jok ? a.cym[gj] : (T)0;
+    cyp[q] = jok ? a.cyp[gj] : (T)0;
+    sy[q] = jok ? a.sdy[gj] : (T)0;
   }
   const bool has_ring = tid < RING;
   if (has_ring) make_strip(ring[tid], a, x0, y0, 4 * (tid & 15), tid < 16 ? -1 : TY, 0, TX - 1);
@@ -340,15 +364,23 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_consta
   int sq = wrap_e(se0 + 1), rq = sr0;   // slots of plane q (e, rhs/mask)
   wait_e(se0);
   wait_e(sq);
-  // registers: the strip in planes q-2 (Cm2; its red cells are final once plane q-2's red
-  // pass is done), q-1 (Cm1) and q (C0); the rhs, mask and z coefficients of plane q-1
-  Q4<T> Cm1 = ld4(s.e[se0] + Si.ie), C0 = ld4(s.e[sq] + Si.ie), Cm2 = Cm1;
-  Q4<T> Rb = Cm1;
-  unsigned Mb = 0u;
+  // registers: each strip in planes q-2 (Cm2; its red cells are final once plane q-2's red
+  // pass is done), q-1 (Cm1) and q (C0); its rhs and mask in plane q-1; the z coefficients
+  // of plane q-1
+  Q4<T> Cm2[NS], Cm1[NS], C0[NS], Rb[NS];
+  unsigned Mb[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    Cm1[q] = ld4(s.e[se0] + ie0 + 16 * q * BX);
+    C0[q] = ld4(s.e[sq] + ie0 + 16 * q * BX);
+    Cm2[q] = Cm1[q];
+    Rb[q] = Cm1[q];
+    Mb[q] = 0u;
+  }
   T czm_b = (T)0, czp_b = (T)0, sz_b = (T)0;
   const T sh = a.shift ? (T)(*a.shift) : (T)0;
   const float om = a.omega;
-  T *const dst0 = a.out + (long long)(y0 + Si.y + 1) * a.px + (x0 + Si.xs + 4);
+  T *const dst0 = a.out + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
   for (int q = k0 - 1; q <= k1; ++q) {
     const int sp1 = wrap_e(sq + 1), sm1 = sq == 0 ? NEt - 1 : sq - 1;
     wait_e(sp1);
@@ -363,27 +395,44 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_consta
     const T *Pp = s.e[sp1];
     const T *R = s.r[rq];
     const uint8_t *M = s.m[rq];
-    const Q4<T> U = ld4(Pp + Si.ie);
-    // x-edges: the cell west of u = 0 and east of u = 3, from the adjacent lanes (same row),
-    // or from the ring in shared memory at the tile edges; all lanes take part
-    T wr = __shfl_up_sync(0xffffffffu, C0.v[3], 1, 16), er = __shfl_down_sync(0xffffffffu, C0.v[0], 1, 16);
-    T wb = __shfl_up_sync(0xffffffffu, Cm1.v[3], 1, 16), eb = __shfl_down_sync(0xffffffffu, Cm1.v[0], 1, 16);
-    if (l16 == 0) { wr = P[Si.ie - 1]; wb = Pm[Si.ie - 1]; }
-    if (l16 == 15) { er = P[Si.ie + 4]; eb = Pm[Si.ie + 4]; }
+    Q4<T> U[NS];
+    T wr[NS], er[NS], wb[NS], eb[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int ie = ie0 + 16 * t * BX;
+      U[t] = ld4(Pp + ie);
+      // x-edges: the cell west of u = 0 and east of u = 3, from the adjacent lanes (same
+      // row), or from the ring in shared memory at the tile edges; all lanes take part
+      wr[t] = __shfl_up_sync(0xffffffffu, C0[t].v[3], 1, 16);
+      er[t] = __shfl_down_sync(0xffffffffu, C0[t].v[0], 1, 16);
+      wb[t] = __shfl_up_sync(0xffffffffu, Cm1[t].v[3], 1, 16);
+      eb[t] = __shfl_down_sync(0xffffffffu, Cm1[t].v[0], 1, 16);
+      if (l16 == 0) { wr[t] = P[ie - 1]; wb[t] = Pm[ie - 1]; }
+      if (l16 == 15) { er[t] = P[ie + 4]; eb[t] = Pm[ie + 4]; }
+    }
     // red cells of plane q on the tile (from registers) and the ring (from shared memory)
     T czm = (T)0, czp = (T)0, sz = (T)0;
-    Q4<T> R0 = Rb;
-    unsigned M0 = 0u;
+    Q4<T> R0[NS];
+    unsigned M0[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) { R0[t] = Rb[t]; M0[t] = 0u; }
     if (q >= 0 && q < a.nz) {
       czm = a.czm[q]; czp = a.czp[q]; sz = a.sdz[q];
-      const Q4<T> N = ld4(P + Si.ie - BX), So = ld4(P + Si.ie + BX);
-      R0 = ld4(R + Si.ir);
-      M0 = *reinterpret_cast<const unsigned *>(M + Si.im);
-      if (((Si.par + q) & 1) == 0)
-        relax_reg<0, T>(Si, C0, N, So, Cm1, U, R0, M0, wr, er, czm, czp, sz, sh, om);
-      else
-        relax_reg<1, T>(Si, C0, N, So, Cm1, U, R0, M0, wr, er, czm, czp, sz, sh, om);
-      st4(P + Si.ie, C0);
+      const bool ua0 = ((par + q) & 1) == 0;
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int ie = ie0 + 16 * t * BX;
+        const Q4<T> N = ld4(P + ie - BX), So = ld4(P + ie + BX);
+        R0[t] = ld4(R + ir0 + 16 * t * BX);
+        M0[t] = *reinterpret_cast<const unsigned *>(M + im0 + 16 * t * BXM);
+        if (ua0)
+          relax_reg<0, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], C0[t], N, So, Cm1[t], U[t], R0[t], M0[t],
+                          wr[t], er[t], czm, czp, sz, sh, om);
+        else
+          relax_reg<1, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], C0[t], N, So, Cm1[t], U[t], R0[t], M0[t],
+                          wr[t], er[t], czm, czp, sz, sh, om);
+        st4(P + ie, C0[t]);
+      }
       if (has_ring && ring[tid].valid) {
         Q4<T> Cr;
         relax_colour<T>(ring[tid], P, Pm, Pp, R, M, 0, x0, y0, q, czm, czp, sz, sh, om, Cr);
@@ -400,29 +449,40 @@ __global__ void __launch_bounds__(THREADS, 3) k_sweep_zmarch(const __grid_consta
       }
     }
     // black cells of plane q-1 on the tile: neighbours all red, updated by now (in-plane ones
-    // in shared memory, the z-neighbours in Cm2 and C0); store the strip from registers
+    // in shared memory, the z-neighbours in Cm2 and C0); store the strips from registers
     const int kb = q - 1;
     if (kb >= k0 && kb < k1) {
-      const Q4<T> N = ld4(Pm + Si.ie - BX), So = ld4(Pm + Si.ie + BX);
-      if (((Si.par + kb + 1) & 1) == 0)
-        relax_reg<0, T>(Si, Cm1, N, So, Cm2, C0, Rb, Mb, wb, eb, czm_b, czp_b, sz_b, sh, om);
-      else
-        relax_reg<1, T>(Si, Cm1, N, So, Cm2, C0, Rb, Mb, wb, eb, czm_b, czp_b, sz_b, sh, om);
-      if (Si.valid) {
-        T *dst = dst0 + (long long)(kb + 1) * a.sz;
-        if (Si.valid == 0xfu) {
-          st4(dst, Cm1);
-        } else {
-          for (int u = 0; u < 4; ++u)
-            if ((Si.valid >> u) & 1u) dst[u] = Cm1.v[u];
+      const bool ua0 = ((par + kb + 1) & 1) == 0;
+      T *const dk = dst0 + (long long)(kb + 1) * a.sz;
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int ie = ie0 + 16 * t * BX;
+        const Q4<T> N = ld4(Pm + ie - BX), So = ld4(Pm + ie + BX);
+        if (ua0)
+          relax_reg<0, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], Cm1[t], N, So, Cm2[t], C0[t], Rb[t], Mb[t],
+                          wb[t], eb[t], czm_b, czp_b, sz_b, sh, om);
+        else
+          relax_reg<1, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], Cm1[t], N, So, Cm2[t], C0[t], Rb[t], Mb[t],
+                          wb[t], eb[t], czm_b, czp_b, sz_b, sh, om);
+        if (valid[t]) {
+          T *dst = dk + (long long)(16 * t) * a.px;
+          if (valid[t] == 0xfu) {
+            st4(dst, Cm1[t]);
+          } else {
+            for (int u = 0; u < 4; ++u)
+              if ((valid[t] >> u) & 1u) dst[u] = Cm1[t].v[u];
+          }
         }
       }
     }
-    Cm2 = Cm1;
-    Cm1 = C0;
-    C0 = U;
-    Rb = R0;
-    Mb = M0;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      Cm2[t] = Cm1[t];
+      Cm1[t] = C0[t];
+      C0[t] = U[t];
+      Rb[t] = R0[t];
+      Mb[t] = M0[t];
+    }
     czm_b = czm; czp_b = czp; sz_b = sz;
     sq = sp1;
     rq = wrap_r(rq + 1);
