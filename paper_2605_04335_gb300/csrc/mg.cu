@@ -170,38 +170,40 @@ __global__ void k_fractions(const uint8_t *mf, const T *ffx, const T *ffy, const
   if (l >= (long long)gc.nx * gc.ny * gc.nz) return;
   int I = (int)(l % gc.nx); long long r = l / gc.nx; int J = (int)(r % gc.ny); int K = (int)(r / gc.ny);
   long long ic = pidx(gc, I, J, K);
-  auto open_f = [&](int i, int j, int k, int axis) -> double {
+  auto open_f = [&](int i, int j, int k, int axis) -> float {
     long long id = pidx(gf, i, j, k);
     if (ffx == nullptr) {   // finest level: open iff both sides are fluid rows and the link is not cut
       long long s = axis == 0 ? 1 : (axis == 1 ? gf.sy : gf.sz);
-      if (cut && ((cut[((long long)k * gf.ny + j) * gf.nx + i] >> (2 * axis + 1)) & 1u)) return 0.0;
-      return (fluid_row(mf[id]) && fluid_row(mf[id + s])) ? 1.0 : 0.0;
+      if (cut && ((cut[((long long)k * gf.ny + j) * gf.nx + i] >> (2 * axis + 1)) & 1u)) return 0.f;
+      return (fluid_row(mf[id]) && fluid_row(mf[id + s])) ? 1.f : 0.f;
     }
     const T *f = axis == 0 ? ffx : (axis == 1 ? ffy : ffz);
-    return (double)f[id];
+    return (float)f[id];
   };
+  // FP32 arithmetic: the fractions shape the coarse operators (the rate of the multigrid
+  // cycle), not the discrete solution, and FP64 runs at a small fraction of the FP32 rate
   // +x face: fine face between 2I+1 and 2I+2
-  double sx = 0.0, sy = 0.0, sz = 0.0;
+  float sx = 0.f, sy = 0.f, sz = 0.f;
   if (I + 1 < gc.nx && 2 * I + 2 < gf.nx) {
     for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
       int j = 2 * J + a, k = 2 * K + b;
-      if (j < gf.ny && k < gf.nz) sx += open_f(2 * I + 1, j, k, 0) * dyf[j] * dzf[k];
+      if (j < gf.ny && k < gf.nz) sx += open_f(2 * I + 1, j, k, 0) * ((float)dyf[j] * (float)dzf[k]);
     }
-    sx /= dyc[J] * dzc[K];
+    sx /= (float)dyc[J] * (float)dzc[K];
   }
   if (J + 1 < gc.ny && 2 * J + 2 < gf.ny) {
     for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
       int i = 2 * I + a, k = 2 * K + b;
-      if (i < gf.nx && k < gf.nz) sy += open_f(i, 2 * J + 1, k, 1) * dxf[i] * dzf[k];
+      if (i < gf.nx && k < gf.nz) sy += open_f(i, 2 * J + 1, k, 1) * ((float)dxf[i] * (float)dzf[k]);
     }
-    sy /= dxc[I] * dzc[K];
+    sy /= (float)dxc[I] * (float)dzc[K];
   }
   if (K + 1 < gc.nz && 2 * K + 2 < gf.nz) {
     for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
       int i = 2 * I + a, j = 2 * J + b;
-      if (i < gf.nx && j < gf.ny) sz += open_f(i, j, 2 * K + 1, 2) * dxf[i] * dyf[j];
+      if (i < gf.nx && j < gf.ny) sz += open_f(i, j, 2 * K + 1, 2) * ((float)dxf[i] * (float)dyf[j]);
     }
-    sz /= dxc[I] * dyc[J];
+    sz /= (float)dxc[I] * (float)dyc[J];
   }
   fx[ic] = (T)sx; fy[ic] = (T)sy; fz[ic] = (T)sz;
 }
@@ -297,28 +299,41 @@ __global__ void __launch_bounds__(1024) k_coarsest_setup(LV<T> v, int *cidx, int
 
 // fluid volume and count of a level: row sums of dx over fluid cells (one FP64 add per
 // fluid cell), times dy dz per row; block partials (volume, count) at out[2 b], out[2 b + 1]
-__global__ void k_fluid_stats(const uint8_t *mask, LevelGeom g, const double *dx, const double *dy,
-                              const double *dz, double *out) {
-  __shared__ double s[2][256];
+// fluid volume and fluid-row count of a level: block partials at out[2 b], out[2 b + 1].
+// One warp per row at a time (every warp of the grid in flight); each lane sums its cells'
+// widths in FP32 and folds the row into FP64 with dy dz once (GB300's FP64 rate is a
+// small fraction of its FP32 rate).  The volume enters the solver only through mean
+// removals, whose fixed points do not depend on it.
+constexpr int STATS_THREADS = 1024;
+__global__ void __launch_bounds__(STATS_THREADS) k_fluid_stats(const uint8_t *mask, LevelGeom g, const double *dx,
+                                                              const double *dy, const double *dz, double *out) {
+  __shared__ double s[2][STATS_THREADS / 32];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   double v = 0.0, c = 0.0;
   const int rows = g.ny * g.nz;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+  for (int row = warp; row < rows; row += nwarps) {
     const int j = row % g.ny, k = row / g.ny;
     const uint8_t *mr = mask + pidx(g, 0, j, k);
-    double sx = 0.0;
+    float sx = 0.f;
     int cnt = 0;
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
-      if (fluid_row(mr[i])) { sx += dx[i]; ++cnt; }
-    v += sx * (dy[j] * dz[k]);
+    for (int i = lane; i < g.nx; i += 32)
+      if (fluid_row(mr[i])) { sx += (float)dx[i]; ++cnt; }
+    v = fma((double)sx, dy[j] * dz[k], v);
     c += cnt;
   }
-  s[0][threadIdx.x] = v; s[1][threadIdx.x] = c;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_down_sync(0xffffffffu, v, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
   }
-  if (threadIdx.x == 0) { out[2 * blockIdx.x] = s[0][0]; out[2 * blockIdx.x + 1] = s[1][0]; }
+  if (lane == 0) { s[0][threadIdx.x >> 5] = v; s[1][threadIdx.x >> 5] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sv = 0.0, sc = 0.0;
+    for (int w = 0; w < STATS_THREADS / 32; ++w) { sv += s[0][w]; sc += s[1][w]; }
+    out[2 * blockIdx.x] = sv;
+    out[2 * blockIdx.x + 1] = sc;
+  }
 }
 
 // ------------------------------------------------------------------ solve kernels
@@ -2242,8 +2257,8 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
     if (nl > 16) return IBM_ERR_CAPACITY;
     for (int l = 0; l < nl; ++l) {
       Level &L = h->lv[l];
-      k_fluid_stats<<<152, 256, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx, L.w1d + L.g.nx + L.g.ny,
-                                         part + 2 * 152 * l);
+      k_fluid_stats<<<152, STATS_THREADS, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx, L.w1d + L.g.nx + L.g.ny,
+                                                   part + 2 * 152 * l);
     }
     std::vector<double> hv(2 * 152 * nl), fv(nl);
     IBM_TRY(cudaMemcpyAsync(hv.data(), part, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
