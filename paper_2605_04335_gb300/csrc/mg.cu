@@ -183,27 +183,43 @@ __global__ void k_fractions(const uint8_t *mf, const T *ffx, const T *ffy, const
   // FP32 arithmetic: the fractions shape the coarse operators (the rate of the multigrid
   // cycle), not the discrete solution, and FP64 runs at a small fraction of the FP32 rate
   // +x face: fine face between 2I+1 and 2I+2
+  // a face whose four fine faces are all fully open is exactly 1 (no rounding of the ratio)
   float sx = 0.f, sy = 0.f, sz = 0.f;
   if (I + 1 < gc.nx && 2 * I + 2 < gf.nx) {
+    int full = 0;
     for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
       int j = 2 * J + a, k = 2 * K + b;
-      if (j < gf.ny && k < gf.nz) sx += open_f(2 * I + 1, j, k, 0) * ((float)dyf[j] * (float)dzf[k]);
+      if (j < gf.ny && k < gf.nz) {
+        const float o = open_f(2 * I + 1, j, k, 0);
+        sx += o * ((float)dyf[j] * (float)dzf[k]);
+        full += o == 1.f;
+      }
     }
-    sx /= (float)dyc[J] * (float)dzc[K];
+    sx = full == 4 ? 1.f : sx / ((float)dyc[J] * (float)dzc[K]);
   }
   if (J + 1 < gc.ny && 2 * J + 2 < gf.ny) {
+    int full = 0;
     for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
       int i = 2 * I + a, k = 2 * K + b;
-      if (i < gf.nx && k < gf.nz) sy += open_f(i, 2 * J + 1, k, 1) * ((float)dxf[i] * (float)dzf[k]);
+      if (i < gf.nx && k < gf.nz) {
+        const float o = open_f(i, 2 * J + 1, k, 1);
+        sy += o * ((float)dxf[i] * (float)dzf[k]);
+        full += o == 1.f;
+      }
     }
-    sy /= (float)dxc[I] * (float)dzc[K];
+    sy = full == 4 ? 1.f : sy / ((float)dxc[I] * (float)dzc[K]);
   }
   if (K + 1 < gc.nz && 2 * K + 2 < gf.nz) {
+    int full = 0;
     for (int b = 0; b < 2; ++b) for (int a = 0; a < 2; ++a) {
       int i = 2 * I + a, j = 2 * J + b;
-      if (i < gf.nx && j < gf.ny) sz += open_f(i, j, 2 * K + 1, 2) * ((float)dxf[i] * (float)dyf[j]);
+      if (i < gf.nx && j < gf.ny) {
+        const float o = open_f(i, j, 2 * K + 1, 2);
+        sz += o * ((float)dxf[i] * (float)dyf[j]);
+        full += o == 1.f;
+      }
     }
-    sz /= (float)dxc[I] * (float)dyc[J];
+    sz = full == 4 ? 1.f : sz / ((float)dxc[I] * (float)dyc[J]);
   }
   fx[ic] = (T)sx; fy[ic] = (T)sy; fz[ic] = (T)sz;
 }
@@ -2366,6 +2382,9 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
     IBM_TRY(cudaGetLastError());
   }
   IBM_TRY(cudaStreamSynchronize(st));
+  // mask0, 3 per coarse level, fluid statistics per level, coarsest setup, ghost sources,
+  // membrane cut lists
+  t->ctx->launches += 1 + 3LL * (nl - 1) + nl + 1 + (t->nghost ? 1 : 0) + (t->membrane && nl >= 2 ? 10 : 0);
   h->geom_version = t->geom_version;
   return IBM_OK;
 }
