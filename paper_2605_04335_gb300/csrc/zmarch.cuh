@@ -381,6 +381,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_consta
   const T sh = a.shift ? (T)(*a.shift) : (T)0;
   const float om = a.omega;
   T *const dst0 = a.out + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
+  // unrolled by 3: the strips' register rotation (planes q-2, q-1, q) becomes renaming
+#pragma unroll 3
   for (int q = k0 - 1; q <= k1; ++q) {
     const int sp1 = wrap_e(sq + 1), sm1 = sq == 0 ? NEt - 1 : sq - 1;
     wait_e(sp1);
