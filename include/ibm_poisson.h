@@ -79,7 +79,7 @@ typedef struct {
                            unevaluated sum of two floats (48-bit significand), residual by
                            error-free transformations on the FP32 pipe.  Mode 2 is this
                            library's choice for hardware with a slow FP64 pipe; the paper
-                           states FP64 for the outer loop (mode 1).  Not batched.      [0] */
+                           states FP64 for the outer loop (mode 1).                     [0] */
   int32_t nu1, nu2;     /* pre-/post-smoothing red-black Gauss-Seidel sweeps        [2,2] */
   int32_t max_cycles;   /* V-cycles (precision 0) or refinement steps (1, 2)        [100] */
   int32_t inner_cycles; /* FP32 V-cycles per refinement step (precision 1, 2)         [2] */
@@ -191,15 +191,18 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
                          double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
                          void *stream);
 
-/* Batched pressure Poisson solves (precision 0 or 1, closed bodies, no Krylov acceleration;
- * membrane tables, precision 2 and krylov > 0 return IBM_ERR_NOT_IMPLEMENTED): n independent problems (each its own classified grid,
- * of any size) advanced together, one persistent kernel launch per V-cycle stage over the
- * work of every problem that has that stage; each batched cycle is captured once as a CUDA
- * graph and replayed until every problem reaches tol (a converged problem's work turns
- * into no-ops).  Same equations, options and outputs as poisson_solve, per problem:
+/* Batched pressure Poisson solves: n independent problems (each its own classified grid, of
+ * any size; closed bodies or membranes; every precision mode and Krylov setting) advanced
+ * together.  Each problem runs the single-problem refinement step with its own device
+ * scalars and partial sums, captured once as a CUDA graph; every step launches the graphs of
+ * the problems still iterating on a small pool of streams owned by the context (forked from
+ * and joined back into `stream`), so that the problems' kernels run concurrently, with one
+ * read-back per step for all of them.  Same equations, options and outputs as
+ * poisson_solve, per problem:
  *   tables[p], rhs_dev[p], p_dev[p] as in poisson_solve (p_dev[p] is in/out);
  *   infos (optional, n entries) receives each problem's report; ms_total is the batch's.
- * The tables must be distinct.  Returns IBM_ERR_NOT_CONVERGED if some problem did not
+ * The tables must be distinct (each problem owns its work arrays); the context's batch
+ * buffers grow to the largest n seen.  Returns IBM_ERR_NOT_CONVERGED if some problem did not
  * reach tol in max_cycles (its last iterate is returned). */
 ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,
                                  const double *const *rhs_dev, double tol, double *const *p_dev,

@@ -86,6 +86,11 @@ ibm_status ibm_ctx_destroy(ibm_ctx *c) {
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->errflag) cudaFree(c->errflag);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaStream_t q : c->bstream) if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t q : c->bevent) if (q) cudaEventDestroy(q);
+  if (c->bscal) cudaFree(c->bscal);
+  if (c->bhscal) cudaFreeHost(c->bhscal);
+  if (c->bpart) cudaFree(c->bpart);
   delete c;
   return IBM_OK;
 }
@@ -211,7 +216,6 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
   if (!ctx || n < 0 || (n > 0 && (!tables || !rhs_dev || !p_dev)) || !(tol >= 0.0)) return IBM_ERR_INVALID_ARG;
   for (int p = 0; p < n; ++p) {
     if (!tables[p] || tables[p]->ctx != ctx || !rhs_dev[p] || !p_dev[p]) return IBM_ERR_INVALID_ARG;
-    if (tables[p]->membrane) return IBM_ERR_NOT_IMPLEMENTED;
     for (int q = 0; q < p; ++q)
       if (tables[q] == tables[p]) return IBM_ERR_INVALID_ARG;   // each problem owns its work arrays
     if (infos && infos[p].history_cap > 0 && !infos[p].resid_history) return IBM_ERR_INVALID_ARG;
@@ -220,7 +224,6 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
   ibm_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!valid_opts(o)) return IBM_ERR_INVALID_ARG;
-  if (o.precision == 2 || o.krylov > 0) return IBM_ERR_NOT_IMPLEMENTED;   // batched: no df loop, no GCR
   if (n == 0) return IBM_OK;
   IBM_TRY(cudaSetDevice(ctx->device));
   if (infos)

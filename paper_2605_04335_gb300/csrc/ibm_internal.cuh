@@ -136,6 +136,13 @@ struct ibm_ctx {
   long long launches = 0;       // kernels launched by this context (all calls)
   int *errflag = nullptr;       // device flag: a bounded device-side wait gave up
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture CUDA graphs
+  // batched solves: the streams the problems' step graphs run on, fork/join events, and
+  // per-problem scalars (device and pinned host) and block partials
+  static constexpr int NBSTREAM = 8;
+  cudaStream_t bstream[NBSTREAM] = {};
+  cudaEvent_t bevent[NBSTREAM + 1] = {};
+  double *bscal = nullptr, *bhscal = nullptr, *bpart = nullptr;
+  int bcap = 0;                        // problems the batch buffers hold
 };
 
 struct ibm_tables {

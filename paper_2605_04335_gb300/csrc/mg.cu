@@ -2401,6 +2401,8 @@ struct Solver {
   double omega;
   int *d_ncoarse;
   bool dfo = false;   // double-FP32 outer loop (precision mode 2)
+  double *scal = nullptr, *part = nullptr;   // this solve's device scalars and block partials
+  bool batched = false;                      // one of several problems advancing together
   // measurement only: events recorded on the stream around each fine-level sweep kernel
   std::vector<cudaEvent_t> *sweep_events = nullptr;
 };
@@ -2440,8 +2442,11 @@ void sweep_zmarch(Solver &S, T *&e, const double *shift) {
   const int gx = (a.nx + zm::TX - 1) / zm::TX, gy = (a.ny + zm::TY - 1) / zm::TY;
   const int per_sm = std::max(1, h->zm_per_sm);
   const long long target = (long long)per_sm * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152);
-  // one wave: tiles x chunks <= resident CTAs (a second, partly filled wave would idle most SMs)
+  // one wave: tiles x chunks <= resident CTAs (a second, partly filled wave would idle most
+  // SMs); in a batch, chunks of at least 24 planes, so that several problems' sweeps share
+  // the GPU without the extra planes of short chunks
   int chunks = (int)std::max<long long>(1, std::min<long long>(a.nz, target / (gx * gy)));
+  if (S.batched) chunks = std::max(1, std::min(chunks, a.nz / 24));
   a.kz = (a.nz + chunks - 1) / chunks;
   chunks = (a.nz + a.kz - 1) / a.kz;
   dim3 grid(gx, gy, chunks);
@@ -2538,16 +2543,16 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   T *ec = (T *)C.e, *rc = (T *)C.r;
   const int gx = (int)nblk(C.g.nx, 128),
             gy = std::max(1, std::min(C.g.ny * C.g.nz, std::min(RESTRICT_BLOCKS, h->grid_blocks[0]) / gx));
-  k_restrict8<T><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, ec, S.ctx->partials);
+  k_restrict8<T><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, ec, S.part);
   int nparts = gx * gy;
   if (l == 0 && h->hcnt[2] > 0) {   // membranes: the cut cells' share, partials after the regular ones
     k_cut_restrict<T><<<CUT_BLOCKS, 256, 0, S.st>>>(h->par_id, h->d_cnt, h->cut_id, h->cut_nb, view<T>(F), e, r,
-                                                    shift, view<T>(C), rc, S.ctx->partials + nparts);
+                                                    shift, view<T>(C), rc, S.part + nparts);
     nparts += CUT_BLOCKS;
     S.ctx->launches += 1;
   }
-  double *cshift = S.ctx->scal + S_LEVEL_SHIFT + (l + 1);
-  k_finalize_shift<<<1, 256, 0, S.st>>>(S.ctx->partials, nparts, h->d_fvol + (l + 1), cshift);
+  double *cshift = S.scal + S_LEVEL_SHIFT + (l + 1);
+  k_finalize_shift<<<1, 256, 0, S.st>>>(S.part, nparts, h->d_fvol + (l + 1), cshift);
   vcycle<T>(S, l + 1, ec, rc, cshift, nullptr);
   const int pgx = (int)nblk(C.g.nx, 128);
   dim3 gp(pgx, std::max(1, std::min(C.g.ny * C.g.nz, h->grid_blocks[1] / pgx)));
@@ -2598,17 +2603,17 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   if (!S.dfo) return fine_residual<float>(S, with_p ? S.h->p64 : nullptr, r32, update_lambda);
   Hierarchy *h = S.h;
   const long long ntot = h->nslot;   // hi/lo split point of the outer arrays
-  double *part = S.ctx->partials;
+  double *part = S.part;
   float *ph = with_p ? hi_of(h->p64) : nullptr, *pl = lo_of(h->p64, ntot);
   k_residual_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(fine_view_df(h), ph, pl, hi_of(h->b64),
-                                                           lo_of(h->b64, ntot), S.ctx->scal + S_LAMBDA, r32, part);
+                                                           lo_of(h->b64, ntot), S.scal + S_LAMBDA, r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
   const bool cuts = h->hcnt[1] > 0;
   if (cuts) {
     k_cut_resid_df<<<CUT_BLOCKS, 256, 0, S.st>>>(h->cut_id, h->cut_nb, h->cut_ijk, h->d_cnt, fine_view_df(h), ph, pl,
-                                                 hi_of(h->b64), lo_of(h->b64, ntot), S.ctx->scal + S_LAMBDA, r32,
+                                                 hi_of(h->b64), lo_of(h->b64, ntot), S.scal + S_LAMBDA, r32,
                                                  cpart);
     S.ctx->launches += 1;
   }
@@ -2616,7 +2621,7 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   if (gh)
     k_ghost_resid_df<<<ngb, REDUCE_THREADS, 0, S.st>>>(h->gsrc, h->gdst, S.t->gw, S.t->gscale, h->d_ng, hi_of(h->p64),
                                                        pl, r32, gpart);
-  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
+  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.scal,
                                         update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
 }
@@ -2624,9 +2629,9 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
 template <typename R>
 void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda) {
   LV<double> v = fine_view64(S.h);
-  double *part = S.ctx->partials;
+  double *part = S.part;
   const int n = v.nx + v.ny + v.nz;
-  k_residual64<R><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n,
+  k_residual64<R><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.scal + S_LAMBDA, S.h->cdf + 3 * n,
                                                           r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
@@ -2634,14 +2639,14 @@ void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda) {
   const bool cuts = S.h->hcnt[1] > 0;
   if (cuts) {
     k_cut_resid64<R><<<CUT_BLOCKS, 256, 0, S.st>>>(S.h->cut_id, S.h->cut_nb, S.h->cut_ijk, S.h->d_cnt, v, p, S.h->b64,
-                                                S.ctx->scal + S_LAMBDA, S.h->cdf + 3 * n, r32, cpart);
+                                                S.scal + S_LAMBDA, S.h->cdf + 3 * n, r32, cpart);
     S.ctx->launches += 1;
   }
   const bool gh = ng > 0 && p != nullptr;
   if (gh)
     k_ghost_resid64<R><<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, S.h->d_ng, p, r32,
                                                       gpart);
-  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.ctx->scal,
+  k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.scal,
                                         update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
 }
@@ -2743,39 +2748,72 @@ ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
   return IBM_OK;
 }
 
-ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
-                      const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st) {
-  const int prec = opts->precision;
-  ibm_status s = build_hierarchy(t, prec, st);
+namespace {
+
+// One problem's refinement solve, in phases, so that several problems can advance together
+// (batched solves) with one read-back per phase: its own device scalars and block
+// partials, and a host copy of the scalars filled by the caller's read-backs.
+struct Run {
+  ibm_ctx *ctx = nullptr;
+  ibm_tables *t = nullptr;
+  Hierarchy *h = nullptr;
+  const ibm_solve_opts *opts = nullptr;
+  Solver S{};
+  int prec = 0, gcr_m = 0;
+  long long ntot = 0, ng = 0;
+  float *r32 = nullptr;
+  double *r64 = nullptr;
+  double *hs = nullptr;              // host copy of the scalars (NSCAL)
+  double denom = 1.0, rel = 0.0, rel0 = 0.0;
+  int cycles = 0, hl = 0;
+  bool active = true;
+  ibm_status result = IBM_ERR_NOT_CONVERGED;
+};
+
+// phase 1: hierarchy, packed inputs, and the residual of p = 0 (its norm is ||S P b||)
+ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, const double *p_user,
+                     const ibm_solve_opts *opts, double *scal, double *part, double *hs, bool batched,
+                     cudaStream_t st) {
+  R.ctx = ctx; R.t = t; R.opts = opts; R.prec = opts->precision; R.hs = hs;
+  ibm_status s = build_hierarchy(t, R.prec, st);
   if (s != IBM_OK) return s;
-  Hierarchy *h = t->hier[prec];
+  Hierarchy *h = R.h = t->hier[R.prec];
   Level &L0 = h->lv[0];
-  const long long n0 = (long long)L0.g.nx * L0.g.ny * L0.g.nz;
-  Solver S{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
-  S.dfo = prec == 2;
-  const long long ntot = h->nslot;   // level-0 elements: padded cells and membrane entry slots
-  // inputs
-  if (S.dfo) {
-    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, ntot), nullptr);
-    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, ntot), L0.mask);
+  R.S = Solver{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
+  R.S.dfo = R.prec == 2;
+  R.S.scal = scal;
+  R.S.part = part;
+  R.S.batched = batched;
+  R.ntot = h->nslot;   // level-0 elements: padded cells and membrane entry slots
+  if (R.S.dfo) {
+    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, R.ntot), nullptr);
+    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, R.ntot), L0.mask);
   } else {
     k_pack<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, h->b64, nullptr);
     k_pack<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask);
   }
   ctx->launches += 2;
-  double hs[NSCAL] = {0};
+  for (int q = 0; q < NSCAL; ++q) hs[q] = 0.0;
   hs[S_FLUIDVOL] = L0.fluid_vol;
   hs[S_NF] = (double)L0.nfluid;
-  IBM_TRY(cudaMemcpyAsync(ctx->scal, hs, sizeof(hs), cudaMemcpyHostToDevice, st));
-  // ||S P b||: residual of p = 0 with lambda = 0
-  outer_residual(S, false, nullptr, false);
-  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
-  IBM_TRY(cudaStreamSynchronize(st));
-  const double bnorm = std::sqrt(ctx->hscal[S_NORM2]);
-  const double denom = bnorm > 0 ? bnorm : 1.0;
-  // initial ghost values consistent with p, and the initial residual
-  const long long ng = t->nghost;
-  if (ng > 0 && S.dfo) {
+  IBM_TRY(cudaMemcpyAsync(scal, hs, sizeof(double) * NSCAL, cudaMemcpyHostToDevice, st));
+  outer_residual(R.S, false, nullptr, false);
+  IBM_TRY(cudaGetLastError());
+  return IBM_OK;
+}
+
+// phase 2 (hs holds the norm of b): ghost values consistent with p, the Krylov state, and
+// the initial residual
+ibm_status run_begin(Run &R, cudaStream_t st) {
+  const double bnorm = std::sqrt(R.hs[S_NORM2]);
+  R.denom = bnorm > 0 ? bnorm : 1.0;
+  Hierarchy *h = R.h;
+  ibm_tables *t = R.t;
+  ibm_ctx *ctx = R.ctx;
+  Level &L0 = h->lv[0];
+  R.S.st = st;
+  const long long ntot = R.ntot, ng = R.ng = t->nghost;
+  if (ng > 0 && R.S.dfo) {
     k_ghost_eval_df<<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, t->gw, ng, hi_of(h->p64), lo_of(h->p64, ntot), h->gtmp);
     k_ghost_store_df<<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, hi_of(h->p64), lo_of(h->p64, ntot));
     ctx->launches += 2;
@@ -2785,20 +2823,16 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
     k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, nullptr, h->gtmp, h->p64);
     ctx->launches += 2;
   }
-  IBM_TRY(cudaGetLastError());
-  int cycles = 0;
-  double rel = 0.0;
-  int hl = 0;
-  ibm_status result = IBM_ERR_NOT_CONVERGED;
   // Krylov acceleration of the refinement loop: directions (of the cycle's type), state,
   // partials.  Mode 0 with it runs in correction form like the mixed modes, in FP64.
-  const int gcr_m = opts->krylov < 0 ? (t->membrane ? GCR_MAX : 0) : std::min(opts->krylov, GCR_MAX);
-  if (gcr_m > 0) {
-    if (h->gcr_m < gcr_m) {
+  const ibm_solve_opts *opts = R.opts;
+  R.gcr_m = opts->krylov < 0 ? (t->membrane ? GCR_MAX : 0) : std::min(opts->krylov, GCR_MAX);
+  if (R.gcr_m > 0) {
+    if (h->gcr_m < R.gcr_m) {
       if (h->gcr_buf) cudaFree(h->gcr_buf);
       h->gcr_buf = nullptr; h->gcr_m = 0;
-      IBM_TRY(cudaMalloc(&h->gcr_buf, (size_t)h->elem * 2 * (size_t)gcr_m * ntot));
-      h->gcr_m = gcr_m;
+      IBM_TRY(cudaMalloc(&h->gcr_buf, (size_t)h->elem * 2 * (size_t)R.gcr_m * ntot));
+      h->gcr_m = R.gcr_m;
     }
     if (!h->gcr_state) IBM_TRY(cudaMalloc(&h->gcr_state, sizeof(GcrState)));
     if (!h->gcr_part)
@@ -2806,134 +2840,294 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
                          sizeof(double) * (REDUCE_BLOCKS + CUT_BLOCKS + GCR_NV * (REDUCE_BLOCKS + GCR_GBLOCKS))));
     IBM_TRY(cudaMemsetAsync(h->gcr_state, 0, sizeof(GcrState), st));
   }
-  float *r32 = prec != 0 ? (float *)L0.r : nullptr;
-  double *r64 = prec == 0 && gcr_m > 0 ? (double *)L0.r : nullptr;
-  if (r64) fine_residual<double>(S, h->p64, r64, true);
-  else outer_residual(S, true, r32, true);
-  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
-  IBM_TRY(cudaStreamSynchronize(st));
-  rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
-  double rel0 = rel;
-  if (rel <= tol) result = IBM_OK;
-  // one cycle: V-cycle (FP64) or FP32 V-cycle(s) + FP64 update (mixed), then the FP64 fine
-  // residual with its norms.  Launched directly, or captured once as a CUDA graph (on the
-  // context's capture stream) and replayed; the pointer swaps of the fused sweep cancel
-  // over a cycle when its number of fine sweeps is even, so the graph stays valid.
-  auto body = [&](cudaStream_t bs) {
-    S.st = bs;
-    if (prec == 0 && gcr_m == 0) {
-      vcycle<double>(S, 0, h->p64, h->b64, ctx->scal + S_LAMBDA, nullptr);
-      fine_residual<float>(S, h->p64, nullptr, true);
-    } else if (prec == 0) {
-      // correction form in FP64: e = V-cycle(r - mu), a GCR step on p, the new residual
-      double *&e64 = reinterpret_cast<double *&>(L0.e);
-      cudaMemsetAsync(e64, 0, sizeof(double) * ntot, bs);
-      vcycle<double>(S, 0, e64, r64, ctx->scal + S_MU, r64);
-      gcr_step<double>(S, e64, r64, gcr_m);
-      fine_residual<double>(S, h->p64, r64, true);
-    } else {
-      float *&e32 = reinterpret_cast<float *&>(L0.e);
-      for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
-        if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * ntot, bs);
-        vcycle<float>(S, 0, e32, r32, ctx->scal + S_MU, r32);
-      }
-      if (gcr_m > 0) {
-        gcr_step<float>(S, e32, r32, gcr_m);
-      } else {
-        if (S.dfo)
-          k_update_df<<<1216, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
-                                            reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
-                                            reinterpret_cast<const float4 *>(e32), ntot / 4);
-        else
-          k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, ntot);
-        ctx->launches += 1;
-      }
-      outer_residual(S, true, r32, true);
-    }
-    S.st = st;
-  };
-  const long long sweeps_per_cycle =
-      (long long)(opts->nu1 + opts->nu2) * (prec != 0 ? std::max(1, opts->inner_cycles) : 1);
-  const bool graph = opts->use_graph && ctx->cap_stream && (!h->zmarch || sweeps_per_cycle % 2 == 0);
-  long long graph_launches = 0;
-  if (graph) {
-    // the captured cycle depends on the schedule, on whether ghost rows exist and on the
-    // addresses of the per-ghost arrays (which move when they grow); everything else it
-    // reads from device memory or from grid-only data
-    unsigned long long key = ((unsigned long long)gcr_m << 56) ^
-                             ((unsigned long long)opts->nu1 << 48) ^ ((unsigned long long)opts->nu2 << 40) ^
-                             ((unsigned long long)opts->inner_cycles << 32) ^
-                             (unsigned long long)(long long)(opts->omega * 1e6) ^ (ng > 0 ? 1ULL << 62 : 0ULL);
-    const unsigned long long ptrs[8] = {(unsigned long long)(uintptr_t)t->gw, (unsigned long long)(uintptr_t)t->gscale,
-                                        (unsigned long long)(uintptr_t)h->gsrc, (unsigned long long)h->gcap,
-                                        (unsigned long long)(uintptr_t)h->cut_id, (unsigned long long)(uintptr_t)h->par_id,
-                                        (unsigned long long)(h->hcnt[1] > 0) | ((unsigned long long)(h->hcnt[2] > 0) << 1),
-                                        (unsigned long long)h->slotcap};
-    for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
-    if (!h->graph_exec || h->graph_key != (long long)key) {
-      if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
-      h->graph_exec = nullptr;
-      cudaGraph_t g = nullptr;
-      const long long l0 = ctx->launches;
-      IBM_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-      body(ctx->cap_stream);
-      cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
-      if (ce != cudaSuccess) return check(ce, "graph capture");
-      cudaGraphExec_t ge = nullptr;
-      ce = cudaGraphInstantiate(&ge, g, 0);
-      cudaGraphDestroy(g);
-      if (ce != cudaSuccess) return check(ce, "graph instantiate");
-      h->graph_exec = ge;
-      h->graph_key = (long long)key;
-      h->graph_launches = ctx->launches - l0;
-      ctx->launches = l0;
-    }
-    graph_launches = h->graph_launches;
-  }
-  while (result != IBM_OK && cycles < opts->max_cycles) {
-    if (graph) {
-      IBM_TRY(cudaGraphLaunch((cudaGraphExec_t)h->graph_exec, st));
-      ctx->launches += graph_launches;
-    } else {
-      body(st);
-    }
-    IBM_TRY(cudaGetLastError());
-    IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
-    IBM_TRY(cudaStreamSynchronize(st));
-    ++cycles;
-    rel = std::sqrt(ctx->hscal[S_NORM2]) / denom;
-    if (info && info->resid_history && hl < info->history_cap) info->resid_history[hl++] = rel;
-    if (!std::isfinite(rel) || rel > 1e6 * std::max(rel0, 1.0)) { result = IBM_ERR_DIVERGED; break; }
-    if (rel <= tol) result = IBM_OK;
-  }
-  // gauge and unpack
-  if (S.dfo)
-    k_gauge_sum_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view_df(h), hi_of(h->p64), lo_of(h->p64, ntot),
-                                                             ctx->partials);
-  else
-    k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, ctx->partials);
-  k_gauge_finalize<<<1, 256, 0, st>>>(ctx->partials, REDUCE_BLOCKS, ctx->scal);
-  if (S.dfo)
-    k_unpack_gauge_df<<<PACK_BLOCKS, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, ctx->scal,
-                                                   p_user);
-  else
-    k_unpack_gauge<<<PACK_BLOCKS, 256, 0, st>>>(h->p64, L0.mask, L0.g, ctx->scal, p_user);
-  ctx->launches += 3;
+  R.r32 = R.prec != 0 ? (float *)L0.r : nullptr;
+  R.r64 = R.prec == 0 && R.gcr_m > 0 ? (double *)L0.r : nullptr;
+  if (R.r64) fine_residual<double>(R.S, h->p64, R.r64, true);
+  else outer_residual(R.S, true, R.r32, true);
   IBM_TRY(cudaGetLastError());
-  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  return IBM_OK;
+}
+
+// after the initial residual's read-back
+void run_initial(Run &R, double tol) {
+  R.rel = R.rel0 = std::sqrt(R.hs[S_NORM2]) / R.denom;
+  if (R.rel <= tol) { R.result = IBM_OK; R.active = false; }
+}
+
+// one refinement step: V-cycle (FP64) or FP32 V-cycle(s) + outer update (mixed), then the
+// fine residual with its norms, on stream bs
+void run_step(Run &R, cudaStream_t bs) {
+  Solver &S = R.S;
+  Hierarchy *h = R.h;
+  Level &L0 = h->lv[0];
+  const long long ntot = R.ntot;
+  const ibm_solve_opts *opts = R.opts;
+  S.st = bs;
+  if (R.prec == 0 && R.gcr_m == 0) {
+    vcycle<double>(S, 0, h->p64, h->b64, S.scal + S_LAMBDA, nullptr);
+    fine_residual<float>(S, h->p64, nullptr, true);
+  } else if (R.prec == 0) {
+    // correction form in FP64: e = V-cycle(r - mu), a GCR step on p, the new residual
+    double *&e64 = reinterpret_cast<double *&>(L0.e);
+    cudaMemsetAsync(e64, 0, sizeof(double) * ntot, bs);
+    vcycle<double>(S, 0, e64, R.r64, S.scal + S_MU, R.r64);
+    gcr_step<double>(S, e64, R.r64, R.gcr_m);
+    fine_residual<double>(S, h->p64, R.r64, true);
+  } else {
+    float *&e32 = reinterpret_cast<float *&>(L0.e);
+    for (int q = 0; q < std::max(1, opts->inner_cycles); ++q) {
+      if (q == 0) cudaMemsetAsync(e32, 0, sizeof(float) * ntot, bs);
+      vcycle<float>(S, 0, e32, R.r32, S.scal + S_MU, R.r32);
+    }
+    if (R.gcr_m > 0) {
+      gcr_step<float>(S, e32, R.r32, R.gcr_m);
+    } else {
+      if (S.dfo)
+        k_update_df<<<1216, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
+                                          reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
+                                          reinterpret_cast<const float4 *>(e32), ntot / 4);
+      else
+        k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, ntot);
+      R.ctx->launches += 1;
+    }
+    outer_residual(S, true, R.r32, true);
+  }
+}
+
+// after a step's read-back: history and status (a problem stops when it converges or
+// diverges)
+void run_account(Run &R, double tol, ibm_solve_info *info) {
+  ++R.cycles;
+  R.rel = std::sqrt(R.hs[S_NORM2]) / R.denom;
+  if (info && info->resid_history && R.hl < info->history_cap) info->resid_history[R.hl++] = R.rel;
+  if (!std::isfinite(R.rel) || R.rel > 1e6 * std::max(R.rel0, 1.0)) {
+    R.result = IBM_ERR_DIVERGED;
+    R.active = false;
+  } else if (R.rel <= tol) {
+    R.result = IBM_OK;
+    R.active = false;
+  }
+}
+
+// gauge and unpack into the caller's p
+void run_finish(Run &R, double *p_user, cudaStream_t st) {
+  Hierarchy *h = R.h;
+  Level &L0 = h->lv[0];
+  const long long ntot = R.ntot;
+  double *scal = R.S.scal, *part = R.S.part;
+  if (R.S.dfo)
+    k_gauge_sum_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view_df(h), hi_of(h->p64), lo_of(h->p64, ntot),
+                                                             part);
+  else
+    k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, part);
+  k_gauge_finalize<<<1, 256, 0, st>>>(part, REDUCE_BLOCKS, scal);
+  if (R.S.dfo)
+    k_unpack_gauge_df<<<PACK_BLOCKS, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, scal, p_user);
+  else
+    k_unpack_gauge<<<PACK_BLOCKS, 256, 0, st>>>(h->p64, L0.mask, L0.g, scal, p_user);
+  R.ctx->launches += 3;
+}
+
+// can one step be captured and replayed: the pointer swaps of the fused sweep cancel over a
+// step when its number of fine sweeps is even
+bool run_graphable(const Run &R) {
+  const ibm_solve_opts *o = R.opts;
+  const long long sweeps = (long long)(o->nu1 + o->nu2) * (R.prec != 0 ? std::max(1, o->inner_cycles) : 1);
+  return o->use_graph && R.ctx->cap_stream && (!R.h->zmarch || sweeps % 2 == 0);
+}
+
+// what a captured step depends on: the schedule, whether ghost rows exist and the addresses
+// of the per-ghost and cut-cell arrays (which move when they grow), the scalars and
+// partials; everything else it reads from device memory or from grid-only data
+unsigned long long run_key(const Run &R) {
+  const ibm_solve_opts *o = R.opts;
+  const Hierarchy *h = R.h;
+  const ibm_tables *t = R.t;
+  unsigned long long key = ((unsigned long long)R.gcr_m << 56) ^ ((unsigned long long)o->nu1 << 48) ^
+                           ((unsigned long long)o->nu2 << 40) ^ ((unsigned long long)o->inner_cycles << 32) ^
+                           (unsigned long long)(long long)(o->omega * 1e6) ^ (R.ng > 0 ? 1ULL << 62 : 0ULL);
+  const unsigned long long ptrs[11] = {(unsigned long long)(uintptr_t)t->gw, (unsigned long long)(uintptr_t)t->gscale,
+                                       (unsigned long long)(uintptr_t)h->gsrc, (unsigned long long)h->gcap,
+                                       (unsigned long long)(uintptr_t)h->cut_id, (unsigned long long)(uintptr_t)h->par_id,
+                                       (unsigned long long)(h->hcnt[1] > 0) | ((unsigned long long)(h->hcnt[2] > 0) << 1),
+                                       (unsigned long long)h->slotcap, (unsigned long long)(uintptr_t)R.S.scal,
+                                       (unsigned long long)(uintptr_t)R.S.part, (unsigned long long)R.S.batched};
+  for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
+  return key;
+}
+
+// the step captured as the hierarchy's CUDA graph (on the context's capture stream),
+// unless the graph it holds is already this step's
+ibm_status run_capture(Run &R) {
+  Hierarchy *h = R.h;
+  ibm_ctx *ctx = R.ctx;
+  const unsigned long long key = run_key(R);
+  if (h->graph_exec && h->graph_key == (long long)key) return IBM_OK;
+  if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
+  h->graph_exec = nullptr;
+  cudaGraph_t g = nullptr;
+  const long long l0 = ctx->launches;
+  IBM_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  run_step(R, ctx->cap_stream);
+  cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (ce != cudaSuccess) return check(ce, "graph capture");
+  cudaGraphExec_t ge = nullptr;
+  ce = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return check(ce, "graph instantiate");
+  h->graph_exec = ge;
+  h->graph_key = (long long)key;
+  h->graph_launches = ctx->launches - l0;
+  ctx->launches = l0;
+  return IBM_OK;
+}
+
+// one step on stream st: the captured graph, or the launches themselves
+ibm_status run_launch(Run &R, bool graph, cudaStream_t st) {
+  if (graph) {
+    IBM_TRY(cudaGraphLaunch((cudaGraphExec_t)R.h->graph_exec, st));
+    R.ctx->launches += R.h->graph_launches;
+  } else {
+    run_step(R, st);
+  }
+  return IBM_OK;
+}
+
+// after the solve: the time-out flag of bounded device waits
+ibm_status read_errflag(ibm_ctx *ctx, ibm_status result, cudaStream_t st) {
   int herr = 0;
   IBM_TRY(cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, st));
   IBM_TRY(cudaStreamSynchronize(st));
   if (herr) {
     IBM_TRY(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), st));
-    result = IBM_ERR_TIMEOUT;
+    return IBM_ERR_TIMEOUT;
   }
+  return result;
+}
+
+}  // namespace
+
+ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
+                      const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st) {
+  Run R;
+  ibm_status s = run_start(R, ctx, t, rhs, p_user, opts, ctx->scal, ctx->partials, ctx->hscal, false, st);
+  if (s != IBM_OK) return s;
+  auto readback = [&]() -> ibm_status {
+    IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    return IBM_OK;
+  };
+  if ((s = readback()) != IBM_OK) return s;
+  if ((s = run_begin(R, st)) != IBM_OK) return s;
+  if ((s = readback()) != IBM_OK) return s;
+  run_initial(R, tol);
+  // one step launched directly, or captured once as a CUDA graph and replayed
+  const bool graph = run_graphable(R);
+  if (graph && (s = run_capture(R)) != IBM_OK) return s;
+  while (R.active && R.cycles < opts->max_cycles) {
+    if ((s = run_launch(R, graph, st)) != IBM_OK) return s;
+    IBM_TRY(cudaGetLastError());
+    if ((s = readback()) != IBM_OK) return s;
+    run_account(R, tol, info);
+  }
+  run_finish(R, p_user, st);
+  IBM_TRY(cudaGetLastError());
+  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  const ibm_status result = read_errflag(ctx, R.result, st);
   if (info) {
-    info->cycles = cycles;
-    info->history_len = hl;
-    info->rel_resid = rel;
+    info->cycles = R.cycles;
+    info->history_len = R.hl;
+    info->rel_resid = R.rel;
     info->lambda = ctx->hscal[S_LAMBDA];
   }
+  return result;
+}
+
+// Batched solves: every problem runs the single-problem refinement step with its own
+// scalars and partials, captured once as its hierarchy's CUDA graph.  Each step launches
+// the graphs of the problems still iterating on the context's pool of streams (problem p
+// on stream p mod NBSTREAM), forked from and joined back into the caller's stream, so the
+// small problems' latency-bound coarse levels overlap and their fine-level kernels share
+// the GPU; converged problems drop out.  One read-back per step serves every problem.
+ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const double *const *rhs, double tol,
+                              double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
+                              cudaStream_t st) {
+  const size_t part_n = (size_t)REDUCE_BLOCKS * 8;
+  if (ctx->bcap < n) {
+    if (ctx->bscal) cudaFree(ctx->bscal);
+    if (ctx->bhscal) cudaFreeHost(ctx->bhscal);
+    if (ctx->bpart) cudaFree(ctx->bpart);
+    ctx->bscal = ctx->bhscal = ctx->bpart = nullptr;
+    ctx->bcap = 0;
+    IBM_TRY(cudaMalloc((void **)&ctx->bscal, sizeof(double) * NSCAL * n));
+    IBM_TRY(cudaMallocHost((void **)&ctx->bhscal, sizeof(double) * NSCAL * n));
+    IBM_TRY(cudaMalloc((void **)&ctx->bpart, sizeof(double) * part_n * n));
+    ctx->bcap = n;
+  }
+  if (!ctx->bstream[0]) {
+    for (int q = 0; q < ibm_ctx::NBSTREAM; ++q)
+      IBM_TRY(cudaStreamCreateWithFlags(&ctx->bstream[q], cudaStreamNonBlocking));
+    for (int q = 0; q <= ibm_ctx::NBSTREAM; ++q)
+      IBM_TRY(cudaEventCreateWithFlags(&ctx->bevent[q], cudaEventDisableTiming));
+  }
+  std::vector<Run> R(n);
+  auto readback = [&]() -> ibm_status {
+    IBM_TRY(cudaMemcpyAsync(ctx->bhscal, ctx->bscal, sizeof(double) * NSCAL * n, cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    return IBM_OK;
+  };
+  ibm_status s;
+  for (int p = 0; p < n; ++p)
+    if ((s = run_start(R[p], ctx, ts[p], rhs[p], p_user[p], opts, ctx->bscal + (size_t)p * NSCAL,
+                       ctx->bpart + part_n * p, ctx->bhscal + (size_t)p * NSCAL, true, st)) != IBM_OK)
+      return s;
+  if ((s = readback()) != IBM_OK) return s;
+  for (int p = 0; p < n; ++p)
+    if ((s = run_begin(R[p], st)) != IBM_OK) return s;
+  if ((s = readback()) != IBM_OK) return s;
+  int active = 0;
+  std::vector<char> graph(n);
+  for (int p = 0; p < n; ++p) {
+    run_initial(R[p], tol);
+    active += R[p].active;
+    graph[p] = run_graphable(R[p]);
+    if (graph[p] && (s = run_capture(R[p])) != IBM_OK) return s;
+  }
+  const int ns = std::min(n, (int)ibm_ctx::NBSTREAM);
+  int it = 0;
+  while (active > 0 && it < opts->max_cycles) {
+    IBM_TRY(cudaEventRecord(ctx->bevent[ibm_ctx::NBSTREAM], st));
+    for (int q = 0; q < ns; ++q) IBM_TRY(cudaStreamWaitEvent(ctx->bstream[q], ctx->bevent[ibm_ctx::NBSTREAM], 0));
+    for (int p = 0; p < n; ++p)
+      if (R[p].active && (s = run_launch(R[p], graph[p], ctx->bstream[p % ns])) != IBM_OK) return s;
+    for (int q = 0; q < ns; ++q) {
+      IBM_TRY(cudaEventRecord(ctx->bevent[q], ctx->bstream[q]));
+      IBM_TRY(cudaStreamWaitEvent(st, ctx->bevent[q], 0));
+    }
+    IBM_TRY(cudaGetLastError());
+    if ((s = readback()) != IBM_OK) return s;
+    ++it;
+    active = 0;
+    for (int p = 0; p < n; ++p) {
+      if (!R[p].active) continue;
+      run_account(R[p], tol, infos ? &infos[p] : nullptr);
+      active += R[p].active;
+    }
+  }
+  for (int p = 0; p < n; ++p) run_finish(R[p], p_user[p], st);
+  IBM_TRY(cudaGetLastError());
+  IBM_TRY(cudaMemcpyAsync(ctx->bhscal, ctx->bscal, sizeof(double) * NSCAL * n, cudaMemcpyDeviceToHost, st));
+  ibm_status result = IBM_OK;
+  for (int p = 0; p < n; ++p)
+    if (R[p].result != IBM_OK && result == IBM_OK) result = R[p].result;
+  result = read_errflag(ctx, result, st);
+  if (infos)
+    for (int p = 0; p < n; ++p) {
+      infos[p].cycles = R[p].cycles;
+      infos[p].history_len = R[p].hl;
+      infos[p].rel_resid = R[p].rel;
+      infos[p].lambda = ctx->bhscal[(size_t)p * NSCAL + S_LAMBDA];
+    }
   return result;
 }
 
@@ -2943,6 +3137,8 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
   if (s != IBM_OK) return s;
   Hierarchy *h = t->hier[precision];
   Solver S{ctx, t, h, st, 1, 1, 1.0, h->dncoarse};
+  S.scal = ctx->scal;
+  S.part = ctx->partials;
   Level &L0 = h->lv[0];
   std::vector<cudaEvent_t> ev;
   auto destroy = [&]() { for (cudaEvent_t x : ev) cudaEventDestroy(x); };
@@ -2974,4 +3170,3 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
 
 }  // namespace ibm
 
-#include "batch.cuh"

@@ -272,16 +272,17 @@ __device__ __forceinline__ void relax_reg(const T (&cxm)[4], const T (&cxp)[4], 
   if (ok1) C.v[u1] = c1 + (T)__fdividef(om * (float)r1, (float)D1);
 }
 
+// one CTA's march: tile (bx, by) of the grid, planes [bz kz, min(nz, (bz + 1) kz)); the
+// tensor maps in parameter or global memory
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
-                                                         const __grid_constant__ CUtensorMap tm_r,
-                                                         const __grid_constant__ CUtensorMap tm_m, Args<T> a) {
+__device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUtensorMap *tm_r, const CUtensorMap *tm_m,
+                                            const Args<T> &a, int bx, int by, int bz) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<T> &s = *reinterpret_cast<Smem<T> *>(smem_raw);
   constexpr int NEt = NE<T>, NRt = NR<T>, DP = Depth<T>::D;
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * a.kz;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int k0 = bz * a.kz;
   const int k1 = min(a.nz, k0 + a.kz);
   if (k0 >= k1) return;
   if (tid == 0) {
@@ -334,12 +335,12 @@ __global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_consta
   // padded coordinates: cell (i, j, k) at (i + OX, j + 1, k + 1); OX = 4
   auto load_e = [&](int plane, int b) {
     mbar_expect_tx(&s.bar_e[b], ebytes);
-    tma_load3(s.e[b], &tm_e, &s.bar_e[b], x0, y0 - 1, plane + 1);
+    tma_load3(s.e[b], tm_e, &s.bar_e[b], x0, y0 - 1, plane + 1);
   };
   auto load_r = [&](int plane, int b) {
     mbar_expect_tx(&s.bar_r[b], rbytes);
-    tma_load3(s.r[b], &tm_r, &s.bar_r[b], x0, y0, plane + 1);
-    tma_load3(s.m[b], &tm_m, &s.bar_r[b], x0, y0, plane + 1);
+    tma_load3(s.r[b], tm_r, &s.bar_r[b], x0, y0, plane + 1);
+    tma_load3(s.m[b], tm_m, &s.bar_r[b], x0, y0, plane + 1);
   };
   unsigned pe = 0, pr = 0;   // bit b: parity of the next completion of buffer b
   bool bad = false;
@@ -498,6 +499,13 @@ __global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_consta
     }
     __syncthreads();
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
+                                                         const __grid_constant__ CUtensorMap tm_r,
+                                                         const __grid_constant__ CUtensorMap tm_m, Args<T> a) {
+  sweep_block<T>(&tm_e, &tm_r, &tm_m, a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace zm

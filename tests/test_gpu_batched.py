@@ -86,24 +86,25 @@ def test_autotune_returns_a_converging_schedule(ctx):
     T.close()
 
 
-def test_batched_rejects_unbuilt_options(ctx):
-    """The batched path has no double-FP32 outer loop, no Krylov acceleration and no
-    membranes: those requests return IBM_ERR_NOT_IMPLEMENTED and leave p untouched."""
+def test_batched_every_mode_membranes_and_krylov(ctx):
+    """The batched path runs each problem's single-problem step: double-FP32 refinement, GCR
+    acceleration and membrane tables batch like the rest, and every problem matches its own
+    single solve (1e-8) at a residual within tol."""
     pkg, c = ctx
-    probs = _batch(2, 5, 16, 20)
+    probs = _batch(3, 5, 16, 28)
     tabs = [pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes) for pr in probs]
+    f = synth.faces_tanh(24, 2.0)
+    tabs.append(pkg.Tables(c, f, f, f, [synth.plate(0.25, nq_x=10, nq_y=6)]))
     rhs = [torch.from_numpy(pr.rhs()).cuda() for pr in probs]
-    ps = [torch.zeros_like(r) for r in rhs]
-    for o in (pkg.SolveOpts(precision=2), pkg.SolveOpts(precision=1, krylov=4), pkg.SolveOpts(precision=0, krylov=2)):
-        status, _ = pkg.poisson_solve_batched(c.h, [t.h for t in tabs], rhs, TOL, ps, o, raise_on_error=False)
-        assert status == "IBM_ERR_NOT_IMPLEMENTED", o
-    assert all(float(p.abs().max()) == 0.0 for p in ps)
-    f = synth.faces_uniform(16)
-    M = pkg.Tables(c, f, f, f, [synth.plate(0.0, nq_x=6, nq_y=4)])
-    r = torch.from_numpy(synth.rhs_divergence(f, f, f, 1)).cuda()
-    status, _ = pkg.poisson_solve_batched(c.h, [M.h], [r], TOL, [torch.zeros_like(r)], pkg.SolveOpts(precision=1),
-                                          raise_on_error=False)
-    assert status == "IBM_ERR_NOT_IMPLEMENTED"
-    M.close()
+    rhs.append(torch.from_numpy(synth.rhs_divergence(f, f, f, 3)).cuda())
+    for o in (pkg.SolveOpts(precision=2), pkg.SolveOpts(precision=1, krylov=4), pkg.SolveOpts(precision=0)):
+        ps = [torch.zeros_like(r) for r in rhs]
+        status, reps = pkg.poisson_solve_batched(c.h, [t.h for t in tabs], rhs, TOL, ps, o)
+        assert status == "IBM_OK", o
+        for q, t in enumerate(tabs):
+            assert reps[q]["rel_resid"] <= TOL and reps[q]["cycles"] > 0
+            p1 = torch.zeros_like(rhs[q])
+            t.solve(rhs[q], p1, TOL, o)
+            assert float((p1 - ps[q]).norm() / p1.norm()) <= PARITY, (o, q)
     for t in tabs:
         t.close()
