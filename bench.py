@@ -179,8 +179,9 @@ def _config(args):
 
 
 def bench_batched(pkg, ctx, torch, st, reps: int = 2):
-    """48 independent uneven problems (edges U{64..192}, sphere or ellipsoid each):
-    batched mixed, batched FP64 and 48 sequential mixed solves to 1e-10 (ms, median)."""
+    """48 independent uneven problems (edges U{64..192}, sphere or ellipsoid each): batched
+    solves in each precision mode and 48 sequential solves in the mixed modes, to 1e-10
+    (ms, median)."""
     import synth
     probs = synth.cfg5(48)
     tabs = [pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st) for pr in probs]
@@ -203,12 +204,15 @@ def bench_batched(pkg, ctx, torch, st, reps: int = 2):
         return statistics.median(ts[1:])
 
     out = {"problems": len(probs), "cells": cells}
-    for name, prec in (("batched_mixed_ms", 1), ("batched_fp64_ms", 0)):
-        out[name] = timed(lambda: pkg.poisson_solve_batched(ctx.h, [t.h for t in tabs], rhs, TOL, ps,
-                                                            pkg.SolveOpts(precision=prec), stream=st))
-    out["sequential_mixed_ms"] = timed(lambda: [t.solve(r, x, TOL, pkg.SolveOpts(precision=1), stream=st)
-                                               for t, r, x in zip(tabs, rhs, ps)])
+    for name, prec in (("mixed", 1), ("mixed_df", 2), ("fp64", 0)):
+        out["batched_%s_ms" % name] = timed(lambda: pkg.poisson_solve_batched(
+            ctx.h, [t.h for t in tabs], rhs, TOL, ps, pkg.SolveOpts(precision=prec), stream=st))
+    for name, prec in (("mixed", 1), ("mixed_df", 2)):
+        out["sequential_%s_ms" % name] = timed(lambda: [t.solve(r, x, TOL, pkg.SolveOpts(precision=prec), stream=st)
+                                                       for t, r, x in zip(tabs, rhs, ps)])
     out["batched_mixed_gcells_per_s"] = cells / (out["batched_mixed_ms"] * 1e-3) / 1e9
+    out["batched_speedup_vs_sequential"] = {k: out["sequential_%s_ms" % k] / out["batched_%s_ms" % k]
+                                            for k in ("mixed", "mixed_df")}
     for t in tabs:
         t.close()
     return out
