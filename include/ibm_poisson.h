@@ -170,6 +170,30 @@ ibm_status ibm_tables_export(const ibm_tables *t, uint8_t *iblank_dev, int64_t *
 ibm_status ibm_tables_export_membrane(const ibm_tables *t, uint8_t *cut_dev, uint8_t *side_dev,
                                       uint8_t *gside_dev, void *stream);
 
+/* Moving-boundary Neumann datum (paper Sec. "Governing Equations and Numerical Methods": the
+ * pressure condition of the projection at a moving body, dp/dn = -rho Du_b/Dt . n).  Ghost
+ * row G reads  g_G - sum_k w_k v_k = kappa_G q_G, where q_G is the pressure's derivative
+ * along the row's unit direction: from the ghost cell's centre GC towards its image point
+ * (the body's outward normal at BI), or towards its neighbour on a nearest-neighbour
+ * fallback row.  kappa_G = -|IP - GC| (fallback: -|centre - GC|), divided by 1 - w_self
+ * when the row's own interpolation weight was moved to the left-hand side.  Every
+ * classification (ibm_classify, ibm_reclassify) clears the datum (q = 0, a fixed body).
+ *
+ * ibm_set_neumann: q_dev double[nghost] (device, in ghost order) sets the data; NULL clears
+ *   them.  Stream-ordered; q_dev may be released once `stream` has passed the call.
+ * ibm_neumann_rigid: q from rigid-body kinematics, rho = 1: for the mesh holding each ghost's
+ *   closest triangle, q = -a(BI) . n with a(x) = a0 + alpha x (x - c) + omega x (omega x
+ *   (x - c)).  motions (host) double[nmesh * 12]: per mesh in classification order a0 (3),
+ *   alpha (3), omega (3), c (3).  nmesh must equal the classification's mesh count (at most
+ *   32; IBM_ERR_CAPACITY beyond).
+ * ibm_tables_export_neumann: copy out kappa_dev double[nghost], tri_dev int32[nghost] (the
+ *   closest triangle's global index, meshes concatenated in order) and d_dev double[nghost]
+ *   (kappa q, 0 without data); any may be NULL.  Synchronises `stream`. */
+ibm_status ibm_set_neumann(ibm_tables *t, const double *q_dev, void *stream);
+ibm_status ibm_neumann_rigid(ibm_tables *t, const double *motions, int32_t nmesh, void *stream);
+ibm_status ibm_tables_export_neumann(const ibm_tables *t, double *kappa_dev, int32_t *tri_dev,
+                                     double *d_dev, void *stream);
+
 void ibm_solve_opts_default(ibm_solve_opts *opts);
 
 /* Pressure Poisson solve (paper Sec. "Governing Equations and Numerical Methods") on a
@@ -178,7 +202,8 @@ void ibm_solve_opts_default(ibm_solve_opts *opts);
  *
  * Solves, for p on fluid cells and g on ghost cells and the scalar lambda,
  *   fluid row i: sum_d c_{i,d} (v_nb - p_i) = b_i - lambda   (v_nb: p, or g at a ghost)
- *   ghost row G: g_G - sum_k w_k v_k = 0                     (dp/dn = 0 at BI)
+ *   ghost row G: g_G - sum_k w_k v_k = kappa_G q_G           (dp/dn at BI; 0 unless a
+ *                                                              datum is set, see above)
  * with c_{i,+x} = 1/(dx_i (x_{i+1} - x_i)) etc., zero across walls, and returns p gauged
  * to zero volume-weighted mean over fluid cells.  Convergence: the relative projected
  * residual ||S P r|| / ||S P b|| <= tol (P removes the volume-weighted fluid mean of r,

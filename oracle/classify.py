@@ -357,7 +357,9 @@ def closest_points(P: np.ndarray, meshes, chunk: int = 64):
 # ----------------------------------------------------------------------------- ghost tables
 
 class GhostTable:
-    """Per ghost entry: cell, BI, IP, base corner, flags, 8 (ref, weight) pairs, row scale."""
+    """Per ghost entry: cell, BI, IP, base corner, flags, 8 (ref, weight) pairs, row scale;
+    the closest triangle (global index), the Neumann coefficient kappa and the row's
+    right-hand side d (see set_neumann)."""
 
     def __init__(self, n):
         self.cell = np.zeros(n, dtype=np.int64)
@@ -368,9 +370,41 @@ class GhostTable:
         self.ref = np.full((n, 8), -1, dtype=np.int64)
         self.w = np.zeros((n, 8))
         self.scale = np.zeros(n)
+        self.tri = np.full(n, -1, dtype=np.int64)
+        self.kappa = np.zeros(n)
+        self.d = np.zeros(n)
 
     def __len__(self):
         return self.cell.size
+
+
+def row_kappa(grid: Grid, G: GhostTable, GC: np.ndarray, fallback: np.ndarray, moved: np.ndarray,
+              ws: np.ndarray, best: np.ndarray) -> np.ndarray:
+    """Neumann coefficient of each ghost row (dp/dn = q at the boundary, Sec. "Governing
+    Equations and Numerical Methods": the moving-boundary pressure condition).
+
+    The ghost value is the image-point value less the normal derivative times the distance
+    along the row: g = p(IP) - l q with l = |IP - GC|, q the derivative along (IP - GC)/l.
+    A row whose own weight w_self was moved to the left-hand side divides by 1 - w_self like
+    its weights; a nearest-neighbour fallback row takes l = |centre(nb) - GC|.  The row reads
+    g - sum w v = kappa q with kappa = -l (or -l / (1 - w_self))."""
+    nz, ny, nx = grid.shape
+    ex, ey, ez = G.ip[:, 0] - GC[:, 0], G.ip[:, 1] - GC[:, 1], G.ip[:, 2] - GC[:, 2]
+    length = np.sqrt((ex * ex + ey * ey) + ez * ez)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kap = np.where(moved, -length / (1.0 - ws), -length)
+    bb = np.where(best >= 0, best, 0)
+    bi, bj, bk = bb % nx, (bb // nx) % ny, bb // (nx * ny)
+    fx, fy, fz = grid.xc[bi] - GC[:, 0], grid.yc[bj] - GC[:, 1], grid.zc[bk] - GC[:, 2]
+    lf = np.sqrt((fx * fx + fy * fy) + fz * fz)
+    kap = np.where(fallback, np.where(best >= 0, -lf, 0.0), kap)
+    return kap
+
+
+def set_neumann(G: GhostTable, q: np.ndarray) -> None:
+    """Ghost-row right-hand sides d = kappa q for the normal derivatives q along each row's
+    direction (q = 0: the homogeneous condition of a fixed body)."""
+    G.d = G.kappa * np.asarray(q, dtype=np.float64)
 
 
 def _base_and_t(c: np.ndarray, v: np.ndarray):
@@ -391,8 +425,9 @@ def ghost_tables(grid: Grid, iblank: np.ndarray, ghosts: np.ndarray, meshes) -> 
         return G
     closed = [m for m in meshes if int(m.closed)]
     GC = grid.centre(ghosts)
-    BI, _ = closest_points(GC, closed)
+    BI, TRI = closest_points(GC, closed)
     IP = (BI + BI) - GC
+    G.tri[:] = TRI
     G.bi[:] = BI
     G.ip[:] = IP
     i0, tx = _base_and_t(grid.xc, IP[:, 0])
@@ -449,6 +484,7 @@ def ghost_tables(grid: Grid, iblank: np.ndarray, ghosts: np.ndarray, meshes) -> 
     G.ref[:] = np.where(fallback[:, None], -1, np.where(wn != 0.0, lin, -1))
     G.w[fallback, 0] = 1.0
     G.ref[fallback, 0] = best[fallback]
+    G.kappa[:] = row_kappa(grid, G, GC, fallback, move, ws, best)
     # row scale: coefficients of the fluid rows that reference this ghost, in direction order
     sc = np.zeros(ng)
     for (di, dj, dk, cf, idx) in ((-1, 0, 0, grid.cxp, gi - 1), (1, 0, 0, grid.cxm, gi + 1),

@@ -50,7 +50,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
-from .classify import (FLAG_FALLBACK, SELF_WEIGHT_MAX, WEIGHT_SUM_MIN, GhostTable, _base_and_t, closest_points,
+from .classify import (FLAG_FALLBACK, SELF_WEIGHT_MAX, WEIGHT_SUM_MIN, GhostTable, _base_and_t, closest_points, row_kappa,
                        snap)
 from .grid import Grid
 
@@ -204,7 +204,7 @@ def ghost_tables(grid: Grid, cut: np.ndarray, side: np.ndarray, meshes) -> Membr
     mem = [m for m in meshes if not int(m.closed)]
     T = membrane_triangles(mem)
     GC = grid.centre(gcell)
-    BI, _ = closest_points(GC, mem)
+    BI, TRI = closest_points(GC, mem)
     IP = (BI + BI) - GC
     G.bi[:] = BI
     G.ip[:] = IP
@@ -281,6 +281,8 @@ def ghost_tables(grid: Grid, cut: np.ndarray, side: np.ndarray, meshes) -> Membr
     G.w[fallback, 0] = 1.0
     G.ref[fallback, 0] = best[fallback]
     G.scale[:] = sc
+    G.tri[:] = TRI
+    G.kappa[:] = row_kappa(grid, G, GC, fallback, move, ws, best)
     return G
 
 
@@ -342,7 +344,7 @@ def solve_sparse(grid: Grid, G: MembraneTables, b: np.ndarray):
     At[i0, :] = 0.0
     At[i0, i0] = 1.0
     lu = spl.splu(sp.csc_matrix(At), permc_spec="COLAMD")
-    bb = np.concatenate([b.ravel(), np.zeros(len(G))])
+    bb = np.concatenate([b.ravel(), G.d])
     one = is_fluid.astype(np.float64)
     r1 = bb.copy(); r1[i0] = 0.0
     r2 = one.copy(); r2[i0] = 0.0
@@ -361,7 +363,7 @@ def residual(grid: Grid, G: MembraneTables, b: np.ndarray, p: np.ndarray, g: np.
     u = np.concatenate([p.ravel(), g])
     Au = A @ u
     rf = (b.ravel() - lam) - Au[:ncell]
-    rg = -Au[ncell:]
+    rg = G.d - Au[ncell:]
     return rf.reshape(grid.shape), rg
 
 

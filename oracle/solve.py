@@ -28,8 +28,14 @@ from .grid import Grid
 from .system import assemble, gauge
 
 
-def _rhs(b: np.ndarray, cells: np.ndarray, is_fluid: np.ndarray) -> np.ndarray:
-    return np.where(is_fluid, b.ravel()[cells], 0.0)
+def _rhs(b: np.ndarray, cells: np.ndarray, is_fluid: np.ndarray, G: GhostTable) -> np.ndarray:
+    """b on fluid rows, the ghost rows' right-hand sides d on ghost rows."""
+    out = np.where(is_fluid, b.ravel()[cells], 0.0)
+    if len(G):
+        row = np.full(b.size, -1, dtype=np.int64)
+        row[cells] = np.arange(cells.size)
+        out[row[G.cell]] = G.d
+    return out
 
 
 def _scatter(shape, cells, x) -> np.ndarray:
@@ -47,7 +53,7 @@ def solve_dense(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray):
     M[:n, :n] = A.toarray()
     M[:n, n] = is_fluid.astype(np.float64)
     M[n, :n] = np.where(is_fluid, V, 0.0)
-    rhs = np.concatenate([_rhs(b, cells, is_fluid), [0.0]])
+    rhs = np.concatenate([_rhs(b, cells, is_fluid, G), [0.0]])
     x = np.linalg.solve(M, rhs)
     return _scatter(grid.shape, cells, x[:n]), float(x[n])
 
@@ -61,7 +67,7 @@ def solve_sparse(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray):
     At[i0, :] = 0.0
     At[i0, i0] = 1.0
     lu = spl.splu(sp.csc_matrix(At), permc_spec="COLAMD")
-    bb = _rhs(b, cells, is_fluid)
+    bb = _rhs(b, cells, is_fluid, G)
     one = is_fluid.astype(np.float64)
     r1 = bb.copy(); r1[i0] = 0.0
     r2 = one.copy(); r2[i0] = 0.0
@@ -137,7 +143,7 @@ def solve_gmres(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray,
         out[n] = r[n]
         return out
 
-    rhs = np.concatenate([_rhs(b, cells, is_fluid), [0.0]])
+    rhs = np.concatenate([_rhs(b, cells, is_fluid, G), [0.0]])
     M = spl.LinearOperator((n + 1, n + 1), msolve)
     x, info = spl.gmres(Bm, rhs, M=M, rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter)
     p = gauge(grid, iblank, _scatter(grid.shape, cells, x[:n]))

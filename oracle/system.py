@@ -93,7 +93,7 @@ def residual(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray, pfull
     rf = apply_fluid(grid, pfull)
     np.subtract(b - lam if lam else b, rf, out=rf)
     rf[iblank != IBLANK_FLUID] = 0.0
-    rg = ghost_values_interp(G, pfull) - pfull.ravel()[G.cell] if len(G) else np.zeros(0)
+    rg = (ghost_values_interp(G, pfull) - pfull.ravel()[G.cell]) + G.d if len(G) else np.zeros(0)
     return rf, rg
 
 

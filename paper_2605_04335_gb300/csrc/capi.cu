@@ -27,6 +27,8 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
 ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st,
                        double *kernel_ms);
+ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st);
+ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st);
 ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const double *const *rhs, double tol,
                               double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
                               cudaStream_t st);
@@ -111,9 +113,39 @@ ibm_status ibm_tables_destroy(ibm_tables *t) {
   cudaDeviceSynchronize();
   for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
   void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref, t->axis,
-                t->scratch, t->cut, t->cside, t->gside, t->gkeys};
+                t->scratch, t->cut, t->cside, t->gside, t->gkeys, t->gkappa, t->gd, t->gtri};
   for (void *p : ps) if (p) cudaFree(p);
   delete t;
+  return IBM_OK;
+}
+
+ibm_status ibm_set_neumann(ibm_tables *t, const double *q_dev, void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  return ibm::neumann_set_impl(t, q_dev, (cudaStream_t)stream);
+}
+
+ibm_status ibm_neumann_rigid(ibm_tables *t, const double *motions, int32_t nmesh, void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  return ibm::neumann_rigid_impl(t, motions, nmesh, (cudaStream_t)stream);
+}
+
+ibm_status ibm_tables_export_neumann(const ibm_tables *t, double *kappa_dev, int32_t *tri_dev, double *d_dev,
+                                     void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ng = t->nghost;
+  if (ng > 0) {
+    if (kappa_dev) IBM_TRY(cudaMemcpyAsync(kappa_dev, t->gkappa, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st));
+    if (tri_dev) IBM_TRY(cudaMemcpyAsync(tri_dev, t->gtri, sizeof(int32_t) * ng, cudaMemcpyDeviceToDevice, st));
+    if (d_dev) {
+      if (t->has_datum) IBM_TRY(cudaMemcpyAsync(d_dev, t->gd, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st));
+      else IBM_TRY(cudaMemsetAsync(d_dev, 0, sizeof(double) * ng, st));
+    }
+  }
+  IBM_TRY(cudaStreamSynchronize(st));
   return IBM_OK;
 }
 

@@ -461,6 +461,8 @@ struct GhostArgs {
   double *bi, *ip, *w, *scale;
   int *base, *flags;
   long long *ref;
+  double *kappa;           // Neumann coefficient of each row
+  int *tri;                // closest triangle of each ghost
 };
 
 __device__ __forceinline__ void base_t(const double *c, int n, double v, int &i0, double &t) {
@@ -611,6 +613,23 @@ __device__ void find_closest(const GhostArgs &a, const double P[3], int lane, do
   for (int d = 0; d < 3; ++d) Q[d] = __shfl_sync(0xffffffffu, lq[d], src);
 }
 
+// Neumann coefficient of a row (moving-boundary datum): g = p(IP) - l q with l = |IP - GC|
+// and q the derivative along (IP - GC) / l, so g - sum w v = kappa q, kappa = -l, divided by
+// 1 - w_self when the row's own weight was moved to the left-hand side
+__device__ __forceinline__ double row_kappa(const double P[3], const double IP[3], bool moved, double wself) {
+  const double ex = IP[0] - P[0], ey = IP[1] - P[1], ez = IP[2] - P[2];
+  const double l = sqrt((ex * ex + ey * ey) + ez * ez);
+  return moved ? -l / (1.0 - wself) : -l;
+}
+
+// a nearest-neighbour fallback row: l = |centre(nb) - GC| (0 without a neighbour)
+__device__ __forceinline__ double fallback_kappa(const GhostArgs &a, const double P[3], long long nb) {
+  if (nb < 0) return 0.0;
+  const int i = (int)(nb % a.nx), j = (int)((nb / a.nx) % a.ny), k = (int)(nb / ((long long)a.nx * a.ny));
+  const double fx = a.xc[i] - P[0], fy = a.yc[j] - P[1], fz = a.zc[k] - P[2];
+  return -sqrt((fx * fx + fy * fy) + fz * fz);
+}
+
 __global__ void __launch_bounds__(TABLE_THREADS) k_ghost_tables(GhostArgs a) {
   __shared__ int cand[TABLE_THREADS / 32][CAND_MAX];
   const int lane = threadIdx.x & 31;
@@ -654,6 +673,8 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_ghost_tables(GhostArgs a) {
     if (valid & (1u << c)) s = s + w[c];
   bool fallback = s < WEIGHT_SUM_MIN;
   double wn[8];
+  bool moved = false;    // the row's own weight moved to the left-hand side
+  double wself = 0.0;
   if (!fallback) {
     for (int c = 0; c < 8; ++c) wn[c] = (valid & (1u << c)) ? w[c] / s : 0.0;
     int selfc = -1;
@@ -666,10 +687,14 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_ghost_tables(GhostArgs a) {
       } else {
         for (int c = 0; c < 8; ++c) wn[c] = wn[c] / (1.0 - ws);
         wn[selfc] = 0.0;
+        moved = true;
+        wself = ws;
       }
     }
   }
   int flags = 0;
+  a.tri[g] = bidx;
+  if (!fallback) a.kappa[g] = row_kappa(P, IP, moved, wself);
   if (fallback) {
     flags |= 1;
     long long bestl = -1;
@@ -687,6 +712,7 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_ghost_tables(GhostArgs a) {
     for (int c = 0; c < 8; ++c) { a.w[8 * g + c] = 0.0; a.ref[8 * g + c] = -1; }
     a.w[8 * g] = 1.0;
     a.ref[8 * g] = bestl;
+    a.kappa[g] = fallback_kappa(a, P, bestl);
   } else {
     flags |= (int)(valid << 8);
     for (int c = 0; c < 8; ++c) {
@@ -1029,6 +1055,8 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_mem_tables(GhostArgs a, MemAr
     if (valid & (1u << c)) s = s + w[c];
   bool fallback = s < WEIGHT_SUM_MIN;
   double wn[8];
+  bool moved = false;    // the row's own weight moved to the left-hand side
+  double wself = 0.0;
   if (!fallback) {
     for (int c = 0; c < 8; ++c) wn[c] = (valid & (1u << c)) ? w[c] / s : 0.0;
     int selfc = -1;
@@ -1041,9 +1069,12 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_mem_tables(GhostArgs a, MemAr
       } else {
         for (int c = 0; c < 8; ++c) wn[c] = wn[c] / (1.0 - ws);
         wn[selfc] = 0.0;
+        moved = true;
+        wself = ws;
       }
     }
   }
+  a.tri[g] = bidx;
   // the cells that use the entry: face-neighbours n of the cell cut from side gs (the
   // cell's own side bit of that link is the other side)
   const uint8_t cc = m.cut[lin], cs = m.side[lin];
@@ -1067,7 +1098,9 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_mem_tables(GhostArgs a, MemAr
     for (int c = 0; c < 8; ++c) { a.w[8 * g + c] = 0.0; a.ref[8 * g + c] = -1; }
     a.w[8 * g] = 1.0;
     a.ref[8 * g] = bestl;
+    a.kappa[g] = fallback_kappa(a, P, bestl);
   } else {
+    a.kappa[g] = row_kappa(P, IP, moved, wself);
     flags |= (int)(valid << 8);
     for (int c = 0; c < 8; ++c) {
       a.w[8 * g + c] = wn[c];
@@ -1204,10 +1237,11 @@ ibm_status check_meshes(const ibm_mesh *meshes, int nmesh, long long &totverts, 
 cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
   if (ng <= T->gcap && T->gcell) return cudaSuccess;
   const long long cap = std::max<long long>(std::max<long long>(ng + ng / 4, 1024), T->gcap);
-  void *ps[] = {T->gcell, T->gbi, T->gip, T->gw, T->gscale, T->gbase, T->gflags, T->gref, T->gside, T->gkeys};
+  void *ps[] = {T->gcell, T->gbi,   T->gip,  T->gw,     T->gscale, T->gbase, T->gflags,
+                T->gref,  T->gside, T->gkeys, T->gkappa, T->gd,     T->gtri};
   for (void *q : ps) if (q) cudaFree(q);
   T->gcell = nullptr; T->gbi = T->gip = T->gw = T->gscale = nullptr; T->gbase = T->gflags = nullptr; T->gref = nullptr;
-  T->gside = nullptr; T->gkeys = nullptr;
+  T->gside = nullptr; T->gkeys = nullptr; T->gkappa = T->gd = nullptr; T->gtri = nullptr;
   T->gcap = 0;
   cudaError_t e = cudaMalloc(&T->gcell, cap * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&T->gbi, cap * 3 * sizeof(double));
@@ -1219,6 +1253,9 @@ cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
   if (e == cudaSuccess) e = cudaMalloc(&T->gref, cap * 8 * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&T->gside, cap);
   if (e == cudaSuccess) e = cudaMalloc(&T->gkeys, cap * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gkappa, cap * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gd, cap * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gtri, cap * sizeof(int));
   if (e == cudaSuccess) T->gcap = cap;
   return e;
 }
@@ -1315,6 +1352,7 @@ ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
+    ga.kappa = T->gkappa; ga.tri = T->gtri;
     MemArgs ma;
     ma.ncell = ncell; ma.keys = T->gkeys; ma.gside = T->gside; ma.cut = T->cut; ma.side = T->cside;
     ma.Xs = ds[0]; ma.Ys = ds[1]; ma.Zs = ds[2]; ma.ntri = ntri;
@@ -1374,6 +1412,11 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
   if (!T->iblank) CTRY(cudaMalloc(&T->iblank, ncell));
   CTRY(cudaMemsetAsync(T->iblank, 0, ncell, st));
   T->membrane = nmesh > 0 && meshes[0].closed == 0;
+  // a new classification clears the moving-boundary datum; the meshes' triangle ranges serve
+  // ibm_neumann_rigid
+  T->has_datum = false;
+  T->mesh_tri_off.assign(1, 0);
+  for (int m = 0; m < nmesh; ++m) T->mesh_tri_off.push_back(T->mesh_tri_off.back() + meshes[m].ntris);
   if (T->membrane) {
     ibm_status ms = membrane_into(T, meshes, nmesh, totverts, tottris, st, S, dc, dcm, dcp, ds);
     if (ms != IBM_OK) return ms;
@@ -1495,6 +1538,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
+    ga.kappa = T->gkappa; ga.tri = T->gtri;
     k_ghost_tables<<<nblk(32 * ng, TABLE_THREADS), TABLE_THREADS, 0, st>>>(ga);
     CTRY(cudaGetLastError());
   }
@@ -1553,6 +1597,103 @@ ibm_status reclassify_impl(ibm_ctx *ctx, ibm_tables *T, const ibm_mesh *meshes, 
   if (s != IBM_OK) return s;
   IBM_TRY(cudaSetDevice(ctx->device));
   return classify_into(T, meshes, nmesh, totverts, tottris, st);
+}
+
+// ---------------------------------------------------------------------- Neumann datum
+//
+// The moving-boundary pressure condition dp/dn = -rho Du_b/Dt . n (the fractional-step
+// projection at a body moving with acceleration a): ghost row g - sum w v = kappa q with q
+// the derivative along the row's direction (towards IP, or towards a fallback neighbour).
+
+namespace {
+
+__global__ void k_set_datum(const double *kappa, const double *q, long long ng, double *d) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < ng) d[g] = kappa[g] * q[g];
+}
+
+constexpr int MAX_RIGID = 32;
+struct RigidMotions {
+  int n;
+  int off[MAX_RIGID + 1];   // first global triangle index of each mesh, and the total
+  double m[MAX_RIGID][12];  // per mesh: a0 (3), angular acceleration (3), angular velocity (3), centre (3)
+};
+
+// q = -a(BI) . n (rho = 1), a(x) = a0 + alpha x r + omega x (omega x r), r = x - centre, for
+// the mesh holding the ghost's closest triangle; n the unit direction of the row; d = kappa q
+__global__ void k_rigid_datum(const double *kappa, const double *bi, const double *ip, const long long *gcell,
+                              const int *flags, const long long *ref, const int *tri, long long ng, const double *xc,
+                              const double *yc, const double *zc, int nx, int ny, RigidMotions M, double *d) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  int lo = 0, hi = M.n;   // the mesh: largest m with off[m] <= tri
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (M.off[mid] <= tri[g]) lo = mid; else hi = mid;
+  }
+  const double *mm = M.m[lo];
+  const long long c = gcell[g];
+  const double G[3] = {xc[c % nx], yc[(c / nx) % ny], zc[c / ((long long)nx * ny)]};
+  double t[3];
+  if (flags[g] & 1) {
+    const long long nb = ref[8 * g];
+    t[0] = xc[nb % nx] - G[0]; t[1] = yc[(nb / nx) % ny] - G[1]; t[2] = zc[nb / ((long long)nx * ny)] - G[2];
+  } else {
+    for (int q = 0; q < 3; ++q) t[q] = ip[3 * g + q] - G[q];
+  }
+  const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  const double r[3] = {bi[3 * g] - mm[9], bi[3 * g + 1] - mm[10], bi[3 * g + 2] - mm[11]};
+  const double *al = mm + 3, *om = mm + 6;
+  const double wr[3] = {om[1] * r[2] - om[2] * r[1], om[2] * r[0] - om[0] * r[2], om[0] * r[1] - om[1] * r[0]};
+  double a[3];
+  a[0] = mm[0] + (al[1] * r[2] - al[2] * r[1]) + (om[1] * wr[2] - om[2] * wr[1]);
+  a[1] = mm[1] + (al[2] * r[0] - al[0] * r[2]) + (om[2] * wr[0] - om[0] * wr[2]);
+  a[2] = mm[2] + (al[0] * r[1] - al[1] * r[0]) + (om[0] * wr[1] - om[1] * wr[0]);
+  const double q = len > 0.0 ? -(a[0] * t[0] + a[1] * t[1] + a[2] * t[2]) / len : 0.0;
+  d[g] = kappa[g] * q;
+}
+
+// device pointers to the cell centres of each axis in the tables' axis block
+void axis_centres(const ibm_tables *T, const double *c[3]) {
+  const int ns[3] = {T->nx, T->ny, T->nz};
+  size_t o = 0;
+  for (int a = 0; a < 3; ++a) {
+    c[a] = T->axis + o + ns[a] + 1;
+    o += 6 * (size_t)ns[a] + 1;
+  }
+}
+
+}  // namespace
+
+ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st) {
+  if (!q) { T->has_datum = false; return IBM_OK; }
+  const long long ng = T->nghost;
+  if (ng > 0) k_set_datum<<<nblk(ng, 256), 256, 0, st>>>(T->gkappa, q, ng, T->gd);
+  IBM_TRY(cudaGetLastError());
+  T->has_datum = ng > 0;
+  T->ctx->launches += ng > 0 ? 1 : 0;
+  return IBM_OK;
+}
+
+ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st) {
+  if (nmesh < 1 || nmesh + 1 != (int)T->mesh_tri_off.size() || !motions) return IBM_ERR_INVALID_ARG;
+  if (nmesh > MAX_RIGID) return IBM_ERR_CAPACITY;
+  RigidMotions M;
+  M.n = nmesh;
+  for (int m = 0; m <= nmesh; ++m) M.off[m] = T->mesh_tri_off[m];
+  for (int m = 0; m < nmesh; ++m)
+    for (int q = 0; q < 12; ++q) M.m[m][q] = motions[12 * m + q];
+  const long long ng = T->nghost;
+  if (ng > 0) {
+    const double *c[3];
+    axis_centres(T, c);
+    k_rigid_datum<<<nblk(ng, 256), 256, 0, st>>>(T->gkappa, T->gbi, T->gip, T->gcell, T->gflags, T->gref, T->gtri, ng,
+                                                 c[0], c[1], c[2], T->nx, T->ny, M, T->gd);
+    T->ctx->launches += 1;
+  }
+  IBM_TRY(cudaGetLastError());
+  T->has_datum = ng > 0;
+  return IBM_OK;
 }
 
 }  // namespace ibm

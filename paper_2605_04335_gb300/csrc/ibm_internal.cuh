@@ -163,6 +163,13 @@ struct ibm_tables {
                                               // (-x +x -y +y -z +z) cut / this cell's side of it
   uint8_t *gside = nullptr;          // membranes: side of each ghost entry
   long long *gkeys = nullptr;        // membranes: 2 cell + side of each entry (ascending)
+  // moving-boundary Neumann datum: ghost row g - sum w v = kappa q (q the pressure's normal
+  // derivative along the row's direction); d = kappa q is set by ibm_set_neumann or
+  // ibm_neumann_rigid and cleared by every classification
+  double *gkappa = nullptr, *gd = nullptr;
+  int *gtri = nullptr;               // closest triangle of each ghost (global index)
+  bool has_datum = false;
+  std::vector<int> mesh_tri_off;     // first global triangle index of each mesh, and the total
   long long geom_version = 0;        // incremented by every classification of these tables
   double *axis = nullptr;            // per-axis faces, centres, widths, coefficients, snapped centres
   char *scratch = nullptr;           // classification scratch kept between classifications

@@ -376,7 +376,7 @@ __global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colou
 // ghost rows (Jacobi): gnew = sum_k w_k e[src_k] (+ rhs at the ghost cell)
 template <typename T, typename W>
 __global__ void k_ghost_eval(const long long *src, const long long *dst, const W *w, long long ng,
-                             const long long *ngp, const T *e, const T *rhs, T *gtmp) {
+                             const long long *ngp, const T *e, const T *rhs, T *gtmp, const double *gd = nullptr) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= (ngp ? *ngp : ng)) return;
   T s = (T)0;
@@ -385,6 +385,7 @@ __global__ void k_ghost_eval(const long long *src, const long long *dst, const W
     if (q >= 0) s += (T)w[8 * g + c] * e[q & ~GHOST_CORNER];
   }
   if (rhs) s += rhs[dst[g]];
+  if (gd) s += (T)gd[g];     // the row's Neumann datum
   gtmp[g] = s;
 }
 
@@ -994,7 +995,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
 // ghost rows r_G = sum w v - g; block partials of (s_G r_G)^2 at gpart[b]
 template <typename R>
 __global__ void k_ghost_resid64(const long long *src, const long long *dst, const double *w, const double *scale,
-                                const long long *ngp, const double *p, R *r32, double *gpart) {
+                                const long long *ngp, const double *p, R *r32, double *gpart, const double *gd) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
   const long long ng = *ngp;
@@ -1005,6 +1006,7 @@ __global__ void k_ghost_resid64(const long long *src, const long long *dst, cons
       if (q >= 0) s += w[8 * g + c] * p[q & ~GHOST_CORNER];
     }
     double rg = s - p[dst[g]];
+    if (gd) rg += gd[g];       // r_G = kappa q - (g - sum w v)
     if (r32) r32[dst[g]] = (R)rg;
     double sr = scale[g] * rg;
     a += sr * sr;
@@ -1232,7 +1234,8 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const 
 
 // ghost rows r_G = sum w v - g in FP64 from the split values; block partials of (s_G r_G)^2
 __global__ void k_ghost_resid_df(const long long *src, const long long *dst, const double *w, const double *scale,
-                                 const long long *ngp, const float *ph, const float *pl, float *r32, double *gpart) {
+                                 const long long *ngp, const float *ph, const float *pl, float *r32, double *gpart,
+                                 const double *gd) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
   const long long ng = *ngp;
@@ -1246,7 +1249,8 @@ __global__ void k_ghost_resid_df(const long long *src, const long long *dst, con
       }
     }
     const long long d = dst[g];
-    const double rg = s - dfl::join(ph[d], pl[d]);
+    double rg = s - dfl::join(ph[d], pl[d]);
+    if (gd) rg += gd[g];       // r_G = kappa q - (g - sum w v)
     if (r32) r32[d] = (float)rg;
     const double sr = scale[g] * rg;
     a += sr * sr;
@@ -1262,7 +1266,7 @@ __global__ void k_ghost_resid_df(const long long *src, const long long *dst, con
 
 // ghost values g = sum w v from the split values (into gtmp), then stored split (Jacobi)
 __global__ void k_ghost_eval_df(const long long *src, const double *w, long long ng, const float *ph,
-                                const float *pl, double *gtmp) {
+                                const float *pl, double *gtmp, const double *gd) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= ng) return;
   double s = 0.0;
@@ -1273,6 +1277,7 @@ __global__ void k_ghost_eval_df(const long long *src, const double *w, long long
       s += w[8 * g + c] * dfl::join(ph[q], pl[q]);
     }
   }
+  if (gd) s += gd[g];        // the row's Neumann datum
   gtmp[g] = s;
 }
 
@@ -2403,6 +2408,8 @@ struct Solver {
   bool dfo = false;   // double-FP32 outer loop (precision mode 2)
   double *scal = nullptr, *part = nullptr;   // this solve's device scalars and block partials
   bool batched = false;                      // one of several problems advancing together
+  const double *gd = nullptr;                // Neumann datum added by the level-0 ghost updates
+                                             // (the V-cycle on p itself: precision 0 without GCR)
   // measurement only: events recorded on the stream around each fine-level sweep kernel
   std::vector<cudaEvent_t> *sweep_events = nullptr;
 };
@@ -2413,12 +2420,10 @@ void ghost_update(Solver &S, T *e, const T *ghost_rhs) {
   if (ng <= 0) return;
   if (sizeof(T) == 8)
     k_ghost_eval<T, double><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.h->gcap,
-                                                                     S.h->d_ng, e, ghost_rhs,
-                                                              (T *)S.h->gtmp);
+                                                                     S.h->d_ng, e, ghost_rhs, (T *)S.h->gtmp, S.gd);
   else
     k_ghost_eval<T, float><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, S.h->gcap,
-                                                                    S.h->d_ng, e, ghost_rhs,
-                                                             (T *)S.h->gtmp);
+                                                                    S.h->d_ng, e, ghost_rhs, (T *)S.h->gtmp, S.gd);
   k_ghost_store<T><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gdst, S.h->gcap, S.h->d_ng, (const T *)S.h->gtmp,
                                                             e);
   S.ctx->launches += 2;
@@ -2620,7 +2625,7 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   const bool gh = ng > 0 && with_p;
   if (gh)
     k_ghost_resid_df<<<ngb, REDUCE_THREADS, 0, S.st>>>(h->gsrc, h->gdst, S.t->gw, S.t->gscale, h->d_ng, hi_of(h->p64),
-                                                       pl, r32, gpart);
+                                                       pl, r32, gpart, S.t->has_datum ? S.t->gd : nullptr);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.scal,
                                         update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
@@ -2645,7 +2650,7 @@ void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda) {
   const bool gh = ng > 0 && p != nullptr;
   if (gh)
     k_ghost_resid64<R><<<ngb, REDUCE_THREADS, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.t->gscale, S.h->d_ng, p, r32,
-                                                      gpart);
+                                                      gpart, S.t->has_datum ? S.t->gd : nullptr);
   k_finalize_resid<<<1, 256, 0, S.st>>>(part, REDUCE_BLOCKS, gpart, gh ? ngb : 0, S.scal,
                                         update_lambda ? 1 : 0, cpart, cuts ? CUT_BLOCKS : 0);
   S.ctx->launches += gh ? 3 : 2;
@@ -2814,12 +2819,13 @@ ibm_status run_begin(Run &R, cudaStream_t st) {
   R.S.st = st;
   const long long ntot = R.ntot, ng = R.ng = t->nghost;
   if (ng > 0 && R.S.dfo) {
-    k_ghost_eval_df<<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, t->gw, ng, hi_of(h->p64), lo_of(h->p64, ntot), h->gtmp);
+    k_ghost_eval_df<<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, t->gw, ng, hi_of(h->p64), lo_of(h->p64, ntot), h->gtmp,
+                                                   t->has_datum ? t->gd : nullptr);
     k_ghost_store_df<<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, h->gtmp, hi_of(h->p64), lo_of(h->p64, ntot));
     ctx->launches += 2;
   } else if (ng > 0) {
     k_ghost_eval<double, double><<<nblk(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, ng, nullptr, h->p64, nullptr,
-                                                                h->gtmp);
+                                                                h->gtmp, t->has_datum ? t->gd : nullptr);
     k_ghost_store<double><<<nblk(ng, 128), 128, 0, st>>>(h->gdst, ng, nullptr, h->gtmp, h->p64);
     ctx->launches += 2;
   }
@@ -2842,6 +2848,9 @@ ibm_status run_begin(Run &R, cudaStream_t st) {
   }
   R.r32 = R.prec != 0 ? (float *)L0.r : nullptr;
   R.r64 = R.prec == 0 && R.gcr_m > 0 ? (double *)L0.r : nullptr;
+  // the V-cycle on p itself (precision 0 without GCR) updates ghost rows with their datum;
+  // correction forms carry it in the residual
+  R.S.gd = R.prec == 0 && R.gcr_m == 0 && t->has_datum ? t->gd : nullptr;
   if (R.r64) fine_residual<double>(R.S, h->p64, R.r64, true);
   else outer_residual(R.S, true, R.r32, true);
   IBM_TRY(cudaGetLastError());
@@ -2951,7 +2960,8 @@ unsigned long long run_key(const Run &R) {
                                        (unsigned long long)(uintptr_t)h->cut_id, (unsigned long long)(uintptr_t)h->par_id,
                                        (unsigned long long)(h->hcnt[1] > 0) | ((unsigned long long)(h->hcnt[2] > 0) << 1),
                                        (unsigned long long)h->slotcap, (unsigned long long)(uintptr_t)R.S.scal,
-                                       (unsigned long long)(uintptr_t)R.S.part, (unsigned long long)R.S.batched};
+                                       (unsigned long long)(uintptr_t)R.S.part,
+                                       (unsigned long long)R.S.batched | ((unsigned long long)t->has_datum << 1)};
   for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
   return key;
 }

@@ -77,6 +77,9 @@ def load_library():
         "ibm_tables_counts": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
         "ibm_tables_export": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
         "ibm_tables_export_membrane": (I32, [P, P, P, P, P]),
+        "ibm_tables_export_neumann": (I32, [P, P, P, P, P]),
+        "ibm_set_neumann": (I32, [P, P, P]),
+        "ibm_neumann_rigid": (I32, [P, C.POINTER(C.c_double), I32, P]),
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
@@ -167,6 +170,20 @@ def ibm_tables_export(tables, iblank=None, cell=None, bi=None, ip=None, base=Non
     _check(load_library().ibm_tables_export(tables, _ptr(iblank), _ptr(cell), _ptr(bi), _ptr(ip), _ptr(base),
                                             _ptr(flags), _ptr(ref), _ptr(w), _ptr(scale), _stream(stream)),
            "ibm_tables_export")
+
+
+def ibm_set_neumann(tables, q=None, stream=None):
+    """Moving-boundary datum: q (CUDA float64, one per ghost row) the pressure's derivative
+    along each row's direction; None clears it."""
+    _check(load_library().ibm_set_neumann(tables, _ptr(q), _stream(stream)), "ibm_set_neumann")
+
+
+def ibm_neumann_rigid(tables, motions, stream=None):
+    """Datum from rigid-body kinematics: motions (nmesh x 12 floats per mesh: a0, angular
+    acceleration, angular velocity, centre)."""
+    m = np.ascontiguousarray(np.asarray(motions, dtype=np.float64).reshape(-1, 12))
+    _check(load_library().ibm_neumann_rigid(tables, m.ctypes.data_as(C.POINTER(C.c_double)), int(m.shape[0]),
+                                            _stream(stream)), "ibm_neumann_rigid")
 
 
 def ibm_tables_destroy(tables):
@@ -308,6 +325,11 @@ class Tables:
                "w": torch.empty((ng, 8), dtype=torch.float64, device=dev),
                "scale": torch.empty(ng, dtype=torch.float64, device=dev)}
         ibm_tables_export(self.h, **out, stream=stream)
+        out["kappa"] = torch.empty(ng, dtype=torch.float64, device=dev)
+        out["tri"] = torch.empty(ng, dtype=torch.int32, device=dev)
+        out["d"] = torch.empty(ng, dtype=torch.float64, device=dev)
+        _check(load_library().ibm_tables_export_neumann(self.h, _ptr(out["kappa"]), _ptr(out["tri"]), _ptr(out["d"]),
+                                                        _stream(stream)), "ibm_tables_export_neumann")
         if self.membrane:
             out["cut"] = torch.empty(self.shape, dtype=torch.uint8, device=dev)
             out["cside"] = torch.empty(self.shape, dtype=torch.uint8, device=dev)
@@ -320,6 +342,14 @@ class Tables:
                 if k not in ("iblank", "cut", "cside"):
                     out[k] = out[k][:0]
         return out
+
+    def set_neumann(self, q=None, stream=None):
+        """Per-ghost pressure derivative along each row's direction (None: fixed body)."""
+        ibm_set_neumann(self.h, q, stream)
+
+    def neumann_rigid(self, motions, stream=None):
+        """Datum from rigid-body kinematics per mesh (a0, alpha, omega, centre)."""
+        ibm_neumann_rigid(self.h, motions, stream)
 
     def reclassify(self, meshes, stream=None):
         """New body positions on the same grid, in the tables' own memory."""

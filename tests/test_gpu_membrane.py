@@ -44,8 +44,9 @@ def _check(pkg, T, grid, meshes):
     assert np.array_equal(ex["cell"], G.cell)
     assert np.array_equal(ex["side"], G.side)
     for k, o in (("bi", G.bi), ("ip", G.ip), ("base", G.base), ("flags", G.flags), ("ref", G.ref), ("w", G.w),
-                 ("scale", G.scale)):
+                 ("scale", G.scale), ("kappa", G.kappa)):
         assert np.array_equal(ex[k], o), k
+    assert np.array_equal(ex["tri"].astype(np.int64), G.tri)
 
 
 def test_tilted_plate_ragged_stretched(ctx):
