@@ -181,6 +181,19 @@ def plate(t: float, chord: float = 0.4, span: float = 0.2, nq_x: int = 100, nq_y
     return Mesh(V @ R.T + off, T, 0)
 
 
+def plate_motion(t: float, heave: float = 0.1, pitch_deg: float = 30.0, center=(0.5, 0.5, 0.5)) -> np.ndarray:
+    """Rigid-body kinematics of `plate` at phase t (time in periods): the acceleration of its
+    centre, its angular acceleration and angular velocity (about y), and the centre.  Twelve
+    numbers, the layout ibm_neumann_rigid takes per mesh."""
+    w = 2.0 * math.pi
+    th0 = math.radians(pitch_deg)
+    c = np.asarray(center, dtype=np.float64) + np.array([0.0, 0.0, heave * math.sin(w * t)])
+    a0 = np.array([0.0, 0.0, -heave * w * w * math.sin(w * t)])
+    alpha = np.array([0.0, -th0 * w * w * math.cos(w * t), 0.0])
+    omega = np.array([0.0, -th0 * w * math.sin(w * t), 0.0])
+    return np.concatenate([a0, alpha, omega, c])
+
+
 def random_spheres(count: int = 12, seed: int = 4, h: float = 1.0 / 1024, level: int = 4,
                    rmin: float = 0.03, rmax: float = 0.08) -> list:
     """Non-overlapping spheres by rejection sampling (surface gap >= 8 h)."""

@@ -72,3 +72,20 @@ def test_configs_build():
     assert sizes.min() >= 64 and sizes.max() <= 192
     s = synth.random_spheres(12, 4, 1.0 / 1024)
     assert len(s) == 12
+
+
+def test_plate_motion_matches_the_poses():
+    """The rigid kinematics of the flapping plate against central differences of its own
+    vertex positions in time (velocity from omega, acceleration from a0, alpha and omega)."""
+    t, h = 0.37, 1e-4
+    V = [synth.plate(t + s * h, nq_x=4, nq_y=3).verts for s in (-1, 0, 1)]
+    acc_fd = (V[2] - 2 * V[1] + V[0]) / (h * h)
+    m = synth.plate_motion(t)
+    a0, al, om, c = m[0:3], m[3:6], m[6:9], m[9:12]
+    r = V[1] - c
+    acc = a0 + np.cross(al, r) + np.cross(om, np.cross(om, r))
+    assert np.max(np.abs(acc - acc_fd)) < 1e-4 * np.max(np.abs(acc))
+    vel_fd = (V[2] - V[0]) / (2 * h)
+    vel_rot = np.cross(om, r)
+    heave_v = vel_fd - vel_rot                        # the centre's velocity, equal at every vertex
+    assert np.max(np.abs(heave_v - heave_v[0])) < 1e-6
