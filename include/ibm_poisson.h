@@ -91,6 +91,13 @@ typedef struct {
                            in modes 1 and 2, FP64 in mode 0, which then runs in
                            correction form) as preconditioner; -1 automatic: 8 for
                            membrane tables, 0 otherwise.                            [-1] */
+  int32_t method;       /* 0: geometric multigrid (this library's solver); 1: BiCGStab
+                           preconditioned with scheduled relaxed Jacobi, the paper's
+                           pressure solver (precision 0 only, not batched): each
+                           preconditioner application is srj_steps Jacobi sweeps with the
+                           relaxation factors 1 / Chebyshev nodes of [2/K^2, 2] (K =
+                           srj_steps); max_cycles counts BiCGStab iterations.            [0] */
+  int32_t srj_steps;    /* Jacobi sweeps per preconditioner application, 1..64            [8] */
 } ibm_solve_opts;
 
 /* Solve report.  resid_history (host, optional) receives the relative residual after

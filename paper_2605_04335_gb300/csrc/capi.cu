@@ -203,6 +203,8 @@ void ibm_solve_opts_default(ibm_solve_opts *o) {
   o->use_graph = 1;
   o->omega = 1.3;
   o->krylov = -1;
+  o->method = 0;
+  o->srj_steps = 8;
 }
 
 ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol, double *p_dev,
@@ -212,7 +214,8 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
   ibm_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.precision >= 0 && o.precision <= 2) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
-      o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0) || o.krylov < -1 || o.krylov > 8)
+      o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0) || o.krylov < -1 || o.krylov > 8 || o.method < 0 ||
+      o.method > 1 || o.srj_steps < 1 || o.srj_steps > 64 || (o.method == 1 && o.precision != 0))
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
@@ -239,7 +242,7 @@ ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t 
 static bool valid_opts(const ibm_solve_opts &o) {
   return o.precision >= 0 && o.precision <= 2 && o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 &&
          o.max_cycles >= 0 && o.inner_cycles >= 1 && o.omega > 0.0 && o.omega < 2.0 && o.krylov >= -1 &&
-         o.krylov <= 8;
+         o.krylov <= 8 && o.method == 0;   // batched: the multigrid solver
 }
 
 ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,

@@ -112,6 +112,8 @@ struct Hierarchy {
   long long *d_cnt = nullptr;               // device: red cut cells, all cut cells, parents
   long long hcnt[3] = {0, 0, 0};            // host copy
   uint8_t *par_flag = nullptr;              // level-1 scratch flags (kept zero between uses)
+  void *bicg_buf = nullptr;                 // workspace of the paper's solver (BiCGStab + SRJ)
+  long long bicg_n = 0;
   int gcr_m = 0;                            // Krylov directions allocated
   void *gcr_buf = nullptr;                  // 2 gcr_m arrays of nslot elements of T (Z then Q)
   void *gcr_state = nullptr;                // device state of the Krylov acceleration

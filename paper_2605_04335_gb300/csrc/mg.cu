@@ -2058,7 +2058,7 @@ void free_hierarchy(Hierarchy *h) {
   void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
                h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng,
                h->cut_id, h->cut_nb, h->cut_ijk, h->par_id, h->d_cnt, h->par_flag, h->scan_buf, h->gcr_buf,
-               h->gcr_state, h->gcr_part};
+               h->gcr_state, h->gcr_part, h->bicg_buf};
   ps.insert(ps.end(), q, q + 28);
   std::sort(ps.begin(), ps.end());
   ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
@@ -3017,8 +3017,12 @@ ibm_status read_errflag(ibm_ctx *ctx, ibm_status result, cudaStream_t st) {
 
 }  // namespace
 
+ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
+                               const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
+
 ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st) {
+  if (opts->method == 1) return solve_bicgstab_impl(ctx, t, rhs, tol, p_user, opts, info, st);
   Run R;
   ibm_status s = run_start(R, ctx, t, rhs, p_user, opts, ctx->scal, ctx->partials, ctx->hscal, false, st);
   if (s != IBM_OK) return s;
@@ -3138,6 +3142,318 @@ ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const 
       infos[p].rel_resid = R[p].rel;
       infos[p].lambda = ctx->bhscal[(size_t)p * NSCAL + S_LAMBDA];
     }
+  return result;
+}
+
+// ------------------------------------------------------------------ the paper's solver
+//
+// BiCGStab preconditioned with scheduled relaxed Jacobi (Sec. "Governing Equations and
+// Numerical Methods"), in FP64, on the same discrete system: unknowns p on fluid rows and g
+// on ghost rows of the finest level's slots.  The compatibility constant is handled by
+// projection: every residual-like vector has its volume-weighted fluid mean removed (so
+// constants, the null space, never enter the Krylov space), and lambda is that mean of the
+// final unprojected residual.  Inner products: unweighted on fluid rows, s^2 on ghost rows,
+// so |r| is the solver's ||S P r||.  The preconditioner approximates A^-1 by K Jacobi
+// sweeps from zero, y += w_k D^-1 (x - A y), with relaxation factors w_k = 1 / Chebyshev
+// nodes of [2/K^2, 2] (the spectrum of D^-1 A lies in [0, 2]).  Scalars stay on the device,
+// so one iteration is captured as a CUDA graph; the host reads |r| once per iteration.
+
+namespace {
+
+struct BicgState {
+  double rho, alpha, omega, beta;
+  double d[4];        // dot products of the current step; d[3] the projection mean
+  double vsum;        // total fluid volume (the projection's denominator, same sums)
+};
+
+// per-slot weights and inverse diagonal: aw = 1 on fluid rows, s^2 on ghost rows; vw = the
+// cell volume on fluid rows; dinv = 1 / A_ii (-1 / D on fluid rows, 1 on ghost rows)
+__global__ void k_bc_cells(LV<double> v, double *aw, double *vw, double *dinv) {
+  const long long n = (long long)v.nx * v.ny * v.nz;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < n; l += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(l % v.nx), j = (int)((l / v.nx) % v.ny), k = (int)(l / ((long long)v.nx * v.ny));
+    const long long id = vidx(v, i, j, k);
+    const bool fl = fluid_row(v.mask[id]);
+    aw[id] = fl ? 1.0 : 0.0;
+    vw[id] = fl ? (v.dx[i] * v.dy[j]) * v.dz[k] : 0.0;
+    dinv[id] = fl ? -1.0 / ((v.sdx[i] + v.sdy[j]) + v.sdz[k]) : 0.0;
+  }
+}
+
+__global__ void k_bc_ghosts(const long long *dst, const double *scale, const long long *ngp, double *aw, double *dinv,
+                            double *bt, const double *gd) {
+  const long long ng = *ngp;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    aw[dst[g]] = scale[g] * scale[g];
+    dinv[dst[g]] = 1.0;
+    bt[dst[g]] = gd ? gd[g] : 0.0;      // the ghost row's right-hand side
+  }
+}
+
+// block partials of up to three dot products sum w x_d y_d (y_d == nullptr: 1) at
+// part[3 b + d] (fixed grid: deterministic)
+__global__ void __launch_bounds__(256) k_bc_dots(const double *x0, const double *y0, const double *x1, const double *y1,
+                                                 const double *x2, const double *y2, const double *w, long long n,
+                                                 double *part) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    if (wi == 0.0) continue;
+    if (x0) a0 = fma(wi * x0[i], y0 ? y0[i] : 1.0, a0);
+    if (x1) a1 = fma(wi * x1[i], y1 ? y1[i] : 1.0, a1);
+    if (x2) a2 = fma(wi * x2[i], y2 ? y2[i] : 1.0, a2);
+  }
+  __shared__ double sm[3][256];
+  sm[0][threadIdx.x] = a0; sm[1][threadIdx.x] = a1; sm[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[3 * blockIdx.x + q] = sm[q][0];
+}
+
+// the sums of k_bc_dots into st->d[0..2], then one scalar step (what: 0 beta, 1 alpha, 2
+// omega, 3 projection mean, 4 none, 5 the total fluid volume)
+__global__ void k_bc_scalars(const double *part, int nb, BicgState *s, int what) {
+  double d[3];
+  for (int q = 0; q < 3; ++q) d[q] = block_sum_partials(part, nb, 3, q);
+  if (threadIdx.x != 0) return;
+  for (int q = 0; q < 3; ++q) s->d[q] = d[q];
+  if (what == 0) {          // d0 = (rh, r): beta = (rho_new / rho)(alpha / omega)
+    s->beta = (d[0] / s->rho) * (s->alpha / s->omega);
+    s->rho = d[0];
+  } else if (what == 1) {   // d0 = (rh, v)
+    s->alpha = s->rho / d[0];
+  } else if (what == 2) {   // d0 = (t, s), d1 = (t, t)
+    s->omega = d[1] > 0.0 ? d[0] / d[1] : 0.0;
+  } else if (what == 3) {
+    s->d[3] = s->vsum > 0.0 ? d[0] / s->vsum : 0.0;
+  } else if (what == 5) {
+    s->vsum = d[0];
+  }
+}
+
+// r = mask (bt - y) on active rows (0 elsewhere)
+__global__ void k_bc_resid(const double *bt, const double *y, const double *aw, long long n, double *r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = aw[i] != 0.0 ? bt[i] - y[i] : 0.0;
+}
+
+// remove the projection mean (st->d[3]) from fluid rows
+__global__ void k_bc_project(double *y, const double *vw, const BicgState *s, long long n) {
+  const double mu = s->d[3];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (vw[i] != 0.0) y[i] -= mu;
+}
+
+// vector steps with the device scalars: op 0 p = r + beta (p - omega v); 1 s = r - alpha v;
+// 2 x += alpha y + omega z, r = s - omega t
+__global__ void k_bc_update(int op, const BicgState *st, long long n, double *a, const double *b, const double *c,
+                            double *x, const double *y, const double *z, const double *t) {
+  const double al = st->alpha, om = st->omega, be = st->beta;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (op == 0) a[i] = b[i] + be * (a[i] - om * c[i]);
+    else if (op == 1) a[i] = b[i] - al * c[i];
+    else {
+      x[i] = fma(al, y[i], fma(om, z[i], x[i]));
+      a[i] = b[i] - om * t[i];
+    }
+  }
+}
+
+// one relaxed Jacobi sweep of the preconditioner: y += w D^-1 (x - Ay) (Ay == nullptr: y = 0)
+__global__ void k_bc_jacobi(double *y, const double *x, const double *Ay, const double *dinv, double w, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = Ay ? fma(w * dinv[i], x[i] - Ay[i], y[i]) : w * dinv[i] * x[i];
+}
+
+struct Bicg {
+  double *x, *bt, *r, *rh, *p, *v, *s, *t, *y, *z, *w, *aw, *vw, *dinv;
+  BicgState *st;
+  GcrState *gz;     // a zeroed GCR state: the operator kernels write at its direction 0
+  double *part;
+};
+
+constexpr int BC_BLOCKS = 608;
+
+void bc_apply(Solver &S, Bicg &B, const double *x, double *y, cudaStream_t bs) {
+  Hierarchy *h = S.h;
+  Level &L0 = h->lv[0];
+  const long long ntot = h->nslot;
+  const LV<double> v0 = view<double>(L0);
+  const float *wf = h->cdf + 3 * (L0.g.nx + L0.g.ny + L0.g.nz);
+  k_gcr_apply<double><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, bs>>>(v0, wf, x, B.gz, y, ntot, B.part);
+  if (h->hcnt[1] > 0)
+    k_gcr_apply_cut<double><<<CUT_BLOCKS, 256, 0, bs>>>(h->cut_id, h->cut_nb, h->cut_ijk, h->d_cnt, v0, wf, x, B.gz, y,
+                                                        ntot, B.part + REDUCE_BLOCKS);
+  if (S.t->nghost > 0)
+    k_gcr_apply_ghost<double, double><<<nblk(h->gcap, 128), 128, 0, bs>>>(h->gsrc, h->gdst, S.t->gw, h->d_ng, x, B.gz,
+                                                                         y, ntot);
+  S.ctx->launches += 1 + (h->hcnt[1] > 0 ? 1 : 0) + (S.t->nghost > 0 ? 1 : 0);
+}
+
+void bc_dots(Solver &S, Bicg &B, const double *x0, const double *y0, const double *x1, const double *y1,
+             const double *w, int what, cudaStream_t bs) {
+  const long long n = S.h->nslot;
+  k_bc_dots<<<BC_BLOCKS, 256, 0, bs>>>(x0, y0, x1, y1, nullptr, nullptr, w, n, B.part);
+  k_bc_scalars<<<1, 256, 0, bs>>>(B.part, BC_BLOCKS, B.st, what);
+  S.ctx->launches += 2;
+}
+
+// y := P y (volume-weighted fluid mean removed)
+void bc_project(Solver &S, Bicg &B, double *y, cudaStream_t bs) {
+  bc_dots(S, B, y, nullptr, nullptr, nullptr, B.vw, 3, bs);
+  k_bc_project<<<1216, 256, 0, bs>>>(y, B.vw, B.st, S.h->nslot);
+  S.ctx->launches += 1;
+}
+
+// y = K x: K relaxed Jacobi sweeps from zero
+void bc_precond(Solver &S, Bicg &B, const double *x, double *y, int K, cudaStream_t bs) {
+  const long long n = S.h->nslot;
+  for (int k = 0; k < K; ++k) {
+    const double node = std::cos(M_PI * (2.0 * k + 1.0) / (2.0 * K));
+    const double lo = 2.0 / ((double)K * K), hi = 2.0;
+    const double w = 2.0 / ((hi + lo) - (hi - lo) * node);
+    if (k == 0) {
+      k_bc_jacobi<<<1216, 256, 0, bs>>>(y, x, nullptr, B.dinv, w, n);
+    } else {
+      bc_apply(S, B, y, B.w, bs);
+      k_bc_jacobi<<<1216, 256, 0, bs>>>(y, x, B.w, B.dinv, w, n);
+    }
+    S.ctx->launches += 1;
+  }
+}
+
+}  // namespace
+
+ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol, double *p_user,
+                               const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st) {
+  Run R;
+  ibm_status s = run_start(R, ctx, t, rhs, p_user, opts, ctx->scal, ctx->partials, ctx->hscal, false, st);
+  if (s != IBM_OK) return s;
+  IBM_TRY(cudaMemcpyAsync(ctx->hscal, ctx->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  IBM_TRY(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(ctx->hscal[S_NORM2]);
+  const double denom = bnorm > 0 ? bnorm : 1.0;
+  Hierarchy *h = R.h;
+  Solver &S = R.S;
+  const long long n = h->nslot;
+  // workspace (kept in the hierarchy, grown with it)
+  const size_t nvec = 14;
+  if (!h->bicg_buf || h->bicg_n != n) {
+    if (h->bicg_buf) cudaFree(h->bicg_buf);
+    h->bicg_buf = nullptr; h->bicg_n = 0;
+    IBM_TRY(cudaMalloc(&h->bicg_buf, sizeof(double) * (nvec * (size_t)n + 3 * BC_BLOCKS + 64) + sizeof(BicgState) +
+                                          sizeof(GcrState) + 256));
+    h->bicg_n = n;
+  }
+  Bicg B;
+  double *base = (double *)h->bicg_buf;
+  double **vecs[13] = {&B.bt, &B.r, &B.rh, &B.p, &B.v, &B.s, &B.t, &B.y, &B.z, &B.w, &B.aw, &B.vw, &B.dinv};
+  for (int q = 0; q < 13; ++q) *vecs[q] = base + (size_t)q * n;
+  B.x = h->p64;
+  B.part = base + nvec * (size_t)n;
+  B.st = reinterpret_cast<BicgState *>(B.part + 3 * BC_BLOCKS + 64);
+  B.gz = reinterpret_cast<GcrState *>(reinterpret_cast<char *>(B.st) + ((sizeof(BicgState) + 127) / 128) * 128);
+  IBM_TRY(cudaMemsetAsync(base, 0, sizeof(double) * 13 * (size_t)n, st));
+  IBM_TRY(cudaMemsetAsync(B.gz, 0, sizeof(GcrState), st));
+  // weights, inverse diagonal, the right-hand side (b on fluid rows, the ghost rows' data)
+  Level &L0 = h->lv[0];
+  const LV<double> v0 = view<double>(L0);
+  IBM_TRY(cudaMemcpyAsync(B.bt, h->b64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  k_bc_cells<<<1216, 256, 0, st>>>(v0, B.aw, B.vw, B.dinv);
+  if (t->nghost > 0)
+    k_bc_ghosts<<<nblk(h->gcap, 256), 256, 0, st>>>(h->gdst, t->gscale, h->d_ng, B.aw, B.dinv, B.bt,
+                                                     t->has_datum ? t->gd : nullptr);
+  ctx->launches += 1 + (t->nghost > 0 ? 1 : 0);
+  // r0 = P (bt - A x0) (ghost values are unknowns like the rest), rh = r0
+  S.st = st;
+  const BicgState init{1.0, 1.0, 1.0, 0.0, {0.0, 0.0, 0.0, 0.0}, 0.0};
+  IBM_TRY(cudaMemcpyAsync(B.st, &init, sizeof(BicgState), cudaMemcpyHostToDevice, st));
+  bc_dots(S, B, B.aw, nullptr, nullptr, nullptr, B.vw, 5, st);             // sum of fluid volumes
+  bc_apply(S, B, B.x, B.y, st);
+  k_bc_resid<<<1216, 256, 0, st>>>(B.bt, B.y, B.aw, n, B.r);
+  ctx->launches += 1;
+  bc_project(S, B, B.r, st);
+  IBM_TRY(cudaMemcpyAsync(B.rh, B.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  // |r0|
+  bc_dots(S, B, B.r, B.r, nullptr, nullptr, B.aw, 4, st);
+  BicgState hst;
+  IBM_TRY(cudaMemcpyAsync(&hst, B.st, sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+  IBM_TRY(cudaStreamSynchronize(st));
+  double rel = std::sqrt(std::max(hst.d[0], 0.0)) / denom;
+  ibm_status result = rel <= tol ? IBM_OK : IBM_ERR_NOT_CONVERGED;
+  const int K = opts->srj_steps;
+  auto iterate = [&](cudaStream_t bs) {
+    S.st = bs;
+    bc_dots(S, B, B.rh, B.r, nullptr, nullptr, B.aw, 0, bs);                 // rho, beta
+    k_bc_update<<<1216, 256, 0, bs>>>(0, B.st, n, B.p, B.r, B.v, nullptr, nullptr, nullptr, nullptr);
+    bc_precond(S, B, B.p, B.y, K, bs);                                        // y = K p
+    bc_apply(S, B, B.y, B.v, bs);                                             // v = P A y
+    bc_project(S, B, B.v, bs);
+    bc_dots(S, B, B.rh, B.v, nullptr, nullptr, B.aw, 1, bs);                 // alpha
+    k_bc_update<<<1216, 256, 0, bs>>>(1, B.st, n, B.s, B.r, B.v, nullptr, nullptr, nullptr, nullptr);
+    bc_precond(S, B, B.s, B.z, K, bs);                                        // z = K s
+    bc_apply(S, B, B.z, B.t, bs);                                             // t = P A z
+    bc_project(S, B, B.t, bs);
+    bc_dots(S, B, B.t, B.s, B.t, B.t, B.aw, 2, bs);                          // omega
+    k_bc_update<<<1216, 256, 0, bs>>>(2, B.st, n, B.r, B.s, nullptr, B.x, B.y, B.z, B.t);
+    bc_dots(S, B, B.r, B.r, nullptr, nullptr, B.aw, 4, bs);                  // |r|^2
+    ctx->launches += 3;
+    S.st = st;
+  };
+  cudaGraphExec_t ge = nullptr;
+  long long per_it = 0;
+  if (opts->use_graph && ctx->cap_stream) {
+    cudaGraph_t g = nullptr;
+    const long long l0 = ctx->launches;
+    IBM_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    iterate(ctx->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (ce != cudaSuccess) return check(ce, "graph capture");
+    ce = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return check(ce, "graph instantiate");
+    per_it = ctx->launches - l0;
+    ctx->launches = l0;
+  }
+  int it = 0, hl = 0;
+  const double rel0 = rel;
+  while (result != IBM_OK && it < opts->max_cycles) {
+    if (ge) {
+      cudaError_t ce = cudaGraphLaunch(ge, st);
+      if (ce != cudaSuccess) { cudaGraphExecDestroy(ge); return check(ce, "graph launch"); }
+      ctx->launches += per_it;
+    } else {
+      iterate(st);
+    }
+    IBM_TRY(cudaMemcpyAsync(&hst, B.st, sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    ++it;
+    rel = std::sqrt(std::max(hst.d[0], 0.0)) / denom;
+    if (info && info->resid_history && hl < info->history_cap) info->resid_history[hl++] = rel;
+    if (!std::isfinite(rel) || rel > 1e6 * std::max(rel0, 1.0)) { result = IBM_ERR_DIVERGED; break; }
+    if (rel <= tol) result = IBM_OK;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  // lambda: the volume-weighted fluid mean of the final unprojected residual
+  bc_apply(S, B, B.x, B.y, st);
+  k_bc_resid<<<1216, 256, 0, st>>>(B.bt, B.y, B.aw, n, B.r);
+  bc_dots(S, B, B.r, nullptr, nullptr, nullptr, B.vw, 3, st);
+  ctx->launches += 1;
+  IBM_TRY(cudaMemcpyAsync(&hst, B.st, sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+  run_finish(R, p_user, st);
+  IBM_TRY(cudaGetLastError());
+  result = read_errflag(ctx, result, st);
+  if (info) {
+    info->cycles = it;
+    info->history_len = hl;
+    info->rel_resid = rel;
+    info->lambda = hst.d[3];
+  }
   return result;
 }
 
