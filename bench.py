@@ -355,6 +355,24 @@ def run_ours(args):
             ts.append(a.elapsed_time(c))
         tts[name] = statistics.median(ts)
         cyc[name] = rep["cycles"]
+    # the paper's pressure solver on the same system (BiCGStab + scheduled relaxed Jacobi, FP64)
+    paper = None
+    if not args.no_paper_solver:
+        po = pkg.SolveOpts(precision=0, method=1, max_cycles=5000)
+        p.zero_()
+        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=0, method=1, max_cycles=2), stream=st,
+                raise_on_error=False)   # workspace
+        p.zero_()
+        torch.cuda.synchronize()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rep = T.solve(rhs, p, TOL, po, stream=st)
+        c.record(st)
+        c.synchronize()
+        t_paper = a.elapsed_time(c)
+        paper = {"method": "BiCGStab preconditioned with %d relaxed Jacobi sweeps (Chebyshev schedule), FP64"
+                 % po.srj_steps, "time_to_tol_ms": t_paper, "iterations": rep["cycles"],
+                 "multigrid_speedup": {k: t_paper / tts[k] for k in tts}}
     # smoother sweeps (fine level): the sweep kernel alone (CUDA events on the stream around
     # each fused-sweep launch, 20 sweeps), and whole sweeps with the ghost-row refresh
     sweeps, sweeps_g = {}, {}
@@ -403,6 +421,7 @@ def run_ours(args):
             "classify_ms": statistics.median(tcl), "reclassify_ms": statistics.median(trc), "ghosts": T_ng,
             "cycles": cyc, "mixed_speedup_vs_fp64": tts["fp64"] / tts["mixed"],
             "mixed_df_speedup_vs_fp64": tts["fp64"] / tts["mixed_df"],
+            "paper_solver": paper,
             "sweep_gpts": {"fp32": gpts32, "fp64": gpts64},
             "sweep_kernel_ms": sweeps, "sweep_with_ghost_rows_ms": sweeps_g,
             "final_rel_resid": reps[-1]["rel_resid"],
@@ -442,6 +461,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-membrane", action="store_true")
+    ap.add_argument("--no-paper-solver", action="store_true")
     ap.add_argument("--membrane-n", type=int, default=512)
     ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")
