@@ -218,6 +218,40 @@ def bench_batched(pkg, ctx, torch, st, reps: int = 2):
     return out
 
 
+def bench_spheres_1024(pkg, ctx, torch, st):
+    """1024^3 uniform grid with 12 random spheres (1.07e9 cells): classification, and the
+    solve to 1e-10 in mode 2 and in FP64 once the hierarchy exists (ms), cycles, device
+    memory held by the tables and both hierarchies."""
+    import synth
+    pr = synth.cfg4(1024)
+    rhs = torch.from_numpy(pr.rhs()).cuda()
+    p = torch.zeros_like(rhs)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+    c.record(st)
+    c.synchronize()
+    out = {"grid": [1024] * 3, "bodies": len(pr.meshes), "ghosts": T.nghost, "classify_ms": a.elapsed_time(c)}
+    for name, prec in (("mixed_df", 2), ("fp64", 0)):
+        p.zero_()
+        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)      # builds the hierarchy
+        p.zero_()
+        a.record(st)
+        rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)
+        c.record(st)
+        c.synchronize()
+        out["solve_ms_" + name] = a.elapsed_time(c)
+        out["cycles_" + name] = rep["cycles"]
+    free1, _ = torch.cuda.mem_get_info()
+    out["device_gb"] = (free0 - free1) / 1e9
+    out["mixed_df_speedup_vs_fp64"] = out["solve_ms_fp64"] / out["solve_ms_mixed_df"]
+    out["gcells_per_s_mixed_df"] = pr.ncells / (out["solve_ms_mixed_df"] * 1e-3) / 1e9
+    T.close()
+    return out
+
+
 def bench_membrane(pkg, ctx, torch, st, n: int = 512, nphase: int = 8):
     """Flapping plate (20 000 triangles) on an n^3 tanh-stretched grid: per phase, reclassify,
     set the moving-boundary datum from the plate's rigid kinematics (dp/dn = -a.n) and solve
@@ -437,6 +471,8 @@ def run_ours(args):
         line["batched_48"] = bench_batched(pkg, ctx, torch, st)
     if not args.no_membrane:
         line["membrane_plate"] = bench_membrane(pkg, ctx, torch, st, args.membrane_n)
+    if not args.no_large:
+        line["spheres_1024"] = bench_spheres_1024(pkg, ctx, torch, st)
     if not args.no_cpu:
         c_cells, c_t = _cpu_sample(args.cpu_n)
         line["cpu_baseline"] = {"value": c_cells / c_t / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -462,6 +498,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-membrane", action="store_true")
     ap.add_argument("--no-paper-solver", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--membrane-n", type=int, default=512)
     ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")
