@@ -37,18 +37,20 @@ namespace ibm {
 namespace zm {
 
 constexpr int TX = 64;          // tile width (cells); multiple of 16
-constexpr int NS = 2;           // interior strips per thread: rows y and y + 16
-constexpr int TY = 16 * NS;     // tile height
+constexpr int SR = 16;          // rows of one strip set (a multiple of 4)
+constexpr int NS = 2;           // interior strips per thread: rows y and y + SR
+constexpr int TY = SR * NS;     // tile height
 constexpr int BX = TX + 8;      // staged width of e and rhs: x in [-4, TX + 4)
 constexpr int BXM = TX + 16;    // staged width of the mask (an 8-bit box row must be 16-byte multiple)
 constexpr int EY = TY + 4;      // e rows: y in [-2, TY + 2)
 constexpr int RY = TY + 2;      // rhs / mask rows: y in [-1, TY + 1)
-constexpr int THREADS = (TX / 4) * 16;       // NS interior strips per thread
+constexpr int THREADS = (TX / 4) * SR;       // NS interior strips per thread
+constexpr int MIN_CTAS = 65536 / (THREADS * 128);   // resident CTAs per SM at up to 128 registers
 constexpr int RING = 2 * (TX / 4);           // ring row strips (rows -1 and TY, x in [0, TX)): warp 0
 constexpr int CELL_WARP = 1;                 // the warp of the ring column cells
 constexpr int CELLS = TY;                    // ring column cells per plane (the red one of each y pair)
 static_assert(RING == 32 && CELLS <= 32 && THREADS >= 64, "ring rows fill warp 0, the columns fit warp 1");
-static_assert(NS == 1 || NS == 2, "strips at rows y and y + 16 share the colour parity");
+static_assert(SR % 4 == 0 && (NS == 1 || NS == 2), "strips at rows y and y + SR share the colour parity");
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 // prefetch distance in planes; rings hold the planes in use at step q (e: q-1 .. q+1,
@@ -295,10 +297,9 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
   // owners, once per step)
   __shared__ Strip<T> ring[RING];
   const int l16 = tid & 15;
-  // warps 0..3 take the even rows, warps 4..7 the odd rows of each 16-row half, two rows
-  // per warp (lanes 0-15 and 16-31), so a warp's strips share one colour parity; strip s
-  // lies 16 s rows below strip 0 (same parity)
-  const int ys = 4 * ((tid >> 5) & 3) + ((tid >> 5) >= 4 ? 1 : 0) + 2 * ((tid & 31) >> 4), xs = 4 * l16;
+  // warp w takes rows r and r + 2 (lanes 0-15 and 16-31), r = 4 (w / 2) + (w mod 2), so a
+  // warp's strips share one colour parity; strip s lies SR s rows below strip 0 (same parity)
+  const int ys = 4 * ((tid >> 5) >> 1) + ((tid >> 5) & 1) + 2 * ((tid & 31) >> 4), xs = 4 * l16;
   const int ie0 = (ys + 2) * BX + (xs + 4), ir0 = (ys + 1) * BX + (xs + 4), im0 = (ys + 1) * BXM + (xs + 4);
   const int par = (x0 + xs + y0 + ys) & 1;
   T cxm[4], cxp[4], sx[4];
@@ -316,7 +317,7 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
   unsigned valid[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) {
-    const int gj = y0 + ys + 16 * q;
+    const int gj = y0 + ys + SR * q;
     const bool jok = gj < a.ny;
     valid[q] = jok ? xvalid : 0u;
     cym[q] = jok ? a.cym[gj] : (T)0;
@@ -372,8 +373,8 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
   unsigned Mb[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) {
-    Cm1[q] = ld4(s.e[se0] + ie0 + 16 * q * BX);
-    C0[q] = ld4(s.e[sq] + ie0 + 16 * q * BX);
+    Cm1[q] = ld4(s.e[se0] + ie0 + SR * q * BX);
+    C0[q] = ld4(s.e[sq] + ie0 + SR * q * BX);
     Cm2[q] = Cm1[q];
     Rb[q] = Cm1[q];
     Mb[q] = 0u;
@@ -402,7 +403,7 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
     T wr[NS], er[NS], wb[NS], eb[NS];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
-      const int ie = ie0 + 16 * t * BX;
+      const int ie = ie0 + SR * t * BX;
       U[t] = ld4(Pp + ie);
       // x-edges: the cell west of u = 0 and east of u = 3, from the adjacent lanes (same
       // row), or from the ring in shared memory at the tile edges; all lanes take part
@@ -424,10 +425,10 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
       const bool ua0 = ((par + q) & 1) == 0;
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
-        const int ie = ie0 + 16 * t * BX;
+        const int ie = ie0 + SR * t * BX;
         const Q4<T> N = ld4(P + ie - BX), So = ld4(P + ie + BX);
-        R0[t] = ld4(R + ir0 + 16 * t * BX);
-        M0[t] = *reinterpret_cast<const unsigned *>(M + im0 + 16 * t * BXM);
+        R0[t] = ld4(R + ir0 + SR * t * BX);
+        M0[t] = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM);
         if (ua0)
           relax_reg<0, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], C0[t], N, So, Cm1[t], U[t], R0[t], M0[t],
                           wr[t], er[t], czm, czp, sz, sh, om);
@@ -459,7 +460,7 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
       T *const dk = dst0 + (long long)(kb + 1) * a.sz;
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
-        const int ie = ie0 + 16 * t * BX;
+        const int ie = ie0 + SR * t * BX;
         const Q4<T> N = ld4(Pm + ie - BX), So = ld4(Pm + ie + BX);
         if (ua0)
           relax_reg<0, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], Cm1[t], N, So, Cm2[t], C0[t], Rb[t], Mb[t],
@@ -468,7 +469,7 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
           relax_reg<1, T>(cxm, cxp, sx, valid[t], cym[t], cyp[t], sy[t], Cm1[t], N, So, Cm2[t], C0[t], Rb[t], Mb[t],
                           wb[t], eb[t], czm_b, czp_b, sz_b, sh, om);
         if (valid[t]) {
-          T *dst = dk + (long long)(16 * t) * a.px;
+          T *dst = dk + (long long)(SR * t) * a.px;
           if (valid[t] == 0xfu) {
             st4(dst, Cm1[t]);
           } else {
@@ -502,7 +503,7 @@ __device__ __forceinline__ void sweep_block(const CUtensorMap *tm_e, const CUten
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
+__global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
                                                          const __grid_constant__ CUtensorMap tm_r,
                                                          const __grid_constant__ CUtensorMap tm_m, Args<T> a) {
   sweep_block<T>(&tm_e, &tm_r, &tm_m, a, blockIdx.x, blockIdx.y, blockIdx.z);
