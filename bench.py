@@ -254,31 +254,38 @@ def bench_spheres_1024(pkg, ctx, torch, st):
 
 def bench_membrane(pkg, ctx, torch, st, n: int = 512, nphase: int = 8):
     """Flapping plate (20 000 triangles) on an n^3 tanh-stretched grid: per phase, reclassify,
-    set the moving-boundary datum from the plate's rigid kinematics (dp/dn = -a.n) and solve
-    to 1e-10 in mode 2 starting from the previous phase's pressure; one more FP64 solve of the
-    last phase for the mixed/FP64 ratio (ms, medians over the phases)."""
+    set the moving-boundary datum from the plate's rigid kinematics (dp/dn = -a.n), solve to
+    1e-10 in mode 2 starting from the previous phase's pressure, and take the surface pressure
+    and nodal pressure forces on the plate; one more FP64 solve of the last phase for the
+    mixed/FP64 ratio (ms, medians over the phases)."""
     import synth
     pr = synth.cfg3(n, 0, nphase)
     rhs = torch.from_numpy(pr.rhs()).cuda()
     p = torch.zeros_like(rhs)
     T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
     T.solve(rhs, p, TOL, pkg.SolveOpts(precision=2), stream=st)       # builds the hierarchy and its graph
-    rec, sol, cyc, ng = [], [], [], []
+    rec, sol, frc, cyc, ng, lift = [], [], [], [], [], []
     for q in range(1, nphase + 1):
         mesh = [synth.plate((q % nphase) / nphase)]
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        motion = [synth.plate_motion((q % nphase) / nphase)]
+        a, b, c, d = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         a.record(st)
         T.reclassify(mesh, stream=st)
-        T.neumann_rigid([synth.plate_motion((q % nphase) / nphase)], stream=st)
+        T.neumann_rigid(motion, stream=st)
         b.record(st)
         rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=2), stream=st)
         c.record(st)
-        c.synchronize()
-        rec.append(a.elapsed_time(b)); sol.append(b.elapsed_time(c)); cyc.append(rep["cycles"]); ng.append(T.nghost)
+        fo = T.surface_forces(mesh, p, motions=motion, stream=st)
+        d.record(st)
+        d.synchronize()
+        rec.append(a.elapsed_time(b)); sol.append(b.elapsed_time(c)); frc.append(c.elapsed_time(d))
+        cyc.append(rep["cycles"]); ng.append(T.nghost)
+        lift.append(float(fo["f_node"][:, 2].sum()))
     out = {"grid": [n] * 3, "phases": nphase, "triangles": int(pr.meshes[0].tris.shape[0]),
            "reclassify_ms": statistics.median(rec), "solve_warm_ms": statistics.median(sol),
-           "step_ms": statistics.median([x + y for x, y in zip(rec, sol)]),
-           "refinement_steps": cyc, "ghost_entries": ng}
+           "surface_forces_ms": statistics.median(frc),
+           "step_ms": statistics.median([x + y + z for x, y, z in zip(rec, sol, frc)]),
+           "refinement_steps": cyc, "ghost_entries": ng, "pressure_force_z": lift}
     for name, prec in (("mixed_df", 2), ("fp64", 0)):
         p.zero_()
         T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)

@@ -201,6 +201,39 @@ ibm_status ibm_neumann_rigid(ibm_tables *t, const double *motions, int32_t nmesh
 ibm_status ibm_tables_export_neumann(const ibm_tables *t, double *kappa_dev, int32_t *tri_dev,
                                      double *d_dev, void *stream);
 
+/* Surface pressure and nodal pressure forces (paper Sec. "Force Formulations": the external
+ * force on a structure node is one third of the traction times the area, summed over the
+ * node's triangles; here the pressure part, -dp n A).  The shear part is not computed.
+ *
+ * Per triangle t of the classified meshes (N = (v1 - v0) x (v2 - v0), n = N / |N|, centroid
+ * c): the pressure on side s = +1 (the side n points to) and s = -1 is read at the probe
+ * X = c + s d n, d = 1.5 x the diagonal of the cell holding c, by trilinear interpolation of
+ * the cell pressures that hold fluid on side s (closed bodies: fluid cells; membranes: cells
+ * whose centre lies strictly on side s of the triangle's plane), renormalised, minus s d q
+ * with q = dp/dn at c.  A side whose usable weights sum below 1e-3 reads 0 and sets flag bit
+ * s (bit 0 for +, bit 1 for -); a zero-area triangle sets bit 2 and has no force.  Closed
+ * bodies have no fluid on the - side (outward normals): p_- = 0.  The triangle's force
+ * f = -(p_+ - p_-) N / 2 goes in equal thirds to its three nodes; node sums run over
+ * triangles in ascending order, so results are deterministic.
+ *   meshes, nmesh   the meshes of the last classification of t, same order and triangle
+ *                   counts (vertex positions may have moved since, topology not), host.
+ *                   Vertices and triangles are numbered mesh after mesh.
+ *   p_dev           double[ncell] cell pressures (poisson_solve's output), device.
+ *   q_tri_dev       double[ntri] dp/dn per triangle (device), or NULL;
+ *   motions         or rigid kinematics per mesh as for ibm_neumann_rigid (host), q = -a(c).n;
+ *                   at most one of the two; neither means q = 0 (a fixed body).
+ *   p_side_dev      double[ntri][2] (p_+, p_-) out, device, or NULL.
+ *   flags_dev       uint8[ntri] out, device, or NULL.
+ *   f_node_dev      double[nvert][3] nodal forces out, device.
+ * Stream-ordered; the host arrays may be released when the call returns.  The tables keep a
+ * device working set that grows with the mesh (reallocation synchronises `stream`).
+ * Errors: IBM_ERR_INVALID_ARG for NULL p_dev / f_node_dev, both q_tri_dev and motions, or
+ * meshes that do not match the classification; IBM_ERR_CAPACITY beyond 2^31 - 2 vertices
+ * or 32 meshes with motions. */
+ibm_status ibm_surface_forces(ibm_tables *t, const ibm_mesh *meshes, int32_t nmesh, const double *p_dev,
+                              const double *q_tri_dev, const double *motions, double *p_side_dev,
+                              uint8_t *flags_dev, double *f_node_dev, void *stream);
+
 void ibm_solve_opts_default(ibm_solve_opts *opts);
 
 /* Pressure Poisson solve (paper Sec. "Governing Equations and Numerical Methods") on a

@@ -15,9 +15,10 @@ LIB = os.path.join(PKG, "lib", "libibmpoisson.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "-I", CSRC, "--expt-relaxed-constexpr"]
-# per-file extra flags: the classification unit keeps every FP64 operation separately rounded
-EXTRA = {"classify.cu": ["-fmad=false"]}
-SOURCES = ["capi.cu", "classify.cu", "mg.cu", "noalloc.cu"]
+# per-file extra flags: the classification and surface-force units keep every FP64 operation
+# separately rounded
+EXTRA = {"classify.cu": ["-fmad=false"], "forces.cu": ["-fmad=false"]}
+SOURCES = ["capi.cu", "classify.cu", "mg.cu", "noalloc.cu", "forces.cu"]
 
 
 def nvcc() -> str:

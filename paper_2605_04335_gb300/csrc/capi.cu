@@ -29,6 +29,9 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
                        double *kernel_ms);
 ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st);
 ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st);
+ibm_status surface_forces_impl(ibm_tables *T, const ibm_mesh *meshes, int nmesh, const double *p,
+                               const double *q_tri, const double *motions, double *p_side, uint8_t *flags,
+                               double *f_node, cudaStream_t st);
 ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const double *const *rhs, double tol,
                               double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
                               cudaStream_t st);
@@ -113,7 +116,7 @@ ibm_status ibm_tables_destroy(ibm_tables *t) {
   cudaDeviceSynchronize();
   for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
   void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref, t->axis,
-                t->scratch, t->cut, t->cside, t->gside, t->gkeys, t->gkappa, t->gd, t->gtri};
+                t->scratch, t->cut, t->cside, t->gside, t->gkeys, t->gkappa, t->gd, t->gtri, t->fbuf};
   for (void *p : ps) if (p) cudaFree(p);
   delete t;
   return IBM_OK;
@@ -129,6 +132,16 @@ ibm_status ibm_neumann_rigid(ibm_tables *t, const double *motions, int32_t nmesh
   if (!t) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(t->ctx->device));
   return ibm::neumann_rigid_impl(t, motions, nmesh, (cudaStream_t)stream);
+}
+
+ibm_status ibm_surface_forces(ibm_tables *t, const ibm_mesh *meshes, int32_t nmesh, const double *p_dev,
+                              const double *q_tri_dev, const double *motions, double *p_side_dev, uint8_t *flags_dev,
+                              double *f_node_dev, void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  if (t->nx < 2 || t->ny < 2 || t->nz < 2) return IBM_ERR_INVALID_ARG;
+  return ibm::surface_forces_impl(t, meshes, nmesh, p_dev, q_tri_dev, motions, p_side_dev, flags_dev, f_node_dev,
+                                  (cudaStream_t)stream);
 }
 
 ibm_status ibm_tables_export_neumann(const ibm_tables *t, double *kappa_dev, int32_t *tri_dev, double *d_dev,

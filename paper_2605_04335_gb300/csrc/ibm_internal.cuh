@@ -176,6 +176,8 @@ struct ibm_tables {
   double *axis = nullptr;            // per-axis faces, centres, widths, coefficients, snapped centres
   char *scratch = nullptr;           // classification scratch kept between classifications
   size_t scratch_cap = 0;
+  char *fbuf = nullptr;              // surface-force working set (meshes, incidence, shares)
+  size_t fcap = 0;
   // solver hierarchies by precision mode (lazy)
   ibm::Hierarchy *hier[3] = {nullptr, nullptr, nullptr};
 };

@@ -80,6 +80,7 @@ def load_library():
         "ibm_tables_export_neumann": (I32, [P, P, P, P, P]),
         "ibm_set_neumann": (I32, [P, P, P]),
         "ibm_neumann_rigid": (I32, [P, C.POINTER(C.c_double), I32, P]),
+        "ibm_surface_forces": (I32, [P, C.POINTER(ibm_mesh), I32, P, P, C.POINTER(C.c_double), P, P, P, P]),
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
@@ -184,6 +185,21 @@ def ibm_neumann_rigid(tables, motions, stream=None):
     m = np.ascontiguousarray(np.asarray(motions, dtype=np.float64).reshape(-1, 12))
     _check(load_library().ibm_neumann_rigid(tables, m.ctypes.data_as(C.POINTER(C.c_double)), int(m.shape[0]),
                                             _stream(stream)), "ibm_neumann_rigid")
+
+
+def ibm_surface_forces(tables, meshes, p, f_node, q=None, motions=None, p_side=None, flags=None, stream=None):
+    """Surface pressure per triangle side and nodal pressure forces (see the header): p the
+    cell pressures, f_node (nvert, 3) out; q (per triangle) or motions (per mesh, 12 floats),
+    not both; p_side (ntri, 2) and flags (ntri,) optional outputs.  All tensors CUDA."""
+    keep = []
+    arr = _mesh_array(meshes, keep)
+    mo = None
+    if motions is not None:
+        m = np.ascontiguousarray(np.asarray(motions, dtype=np.float64).reshape(-1, 12))
+        keep.append(m)
+        mo = m.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load_library().ibm_surface_forces(tables, arr, len(meshes), _ptr(p), _ptr(q), mo, _ptr(p_side),
+                                             _ptr(flags), _ptr(f_node), _stream(stream)), "ibm_surface_forces")
 
 
 def ibm_tables_destroy(tables):
@@ -352,6 +368,20 @@ class Tables:
     def neumann_rigid(self, motions, stream=None):
         """Datum from rigid-body kinematics per mesh (a0, alpha, omega, centre)."""
         ibm_neumann_rigid(self.h, motions, stream)
+
+    def surface_forces(self, meshes, p, q=None, motions=None, stream=None) -> dict:
+        """Side pressures (ntri, 2), flags (ntri,) and nodal forces (nvert, 3) of the meshes of
+        the last classification, from the cell pressures p (CUDA float64)."""
+        import torch
+        dev = p.device
+        ntri = sum(int(np.asarray(m.tris).reshape(-1, 3).shape[0]) for m in meshes)
+        nvert = sum(int(np.asarray(m.verts).reshape(-1, 3).shape[0]) for m in meshes)
+        out = {"p_side": torch.empty((ntri, 2), dtype=torch.float64, device=dev),
+               "flags": torch.empty(ntri, dtype=torch.uint8, device=dev),
+               "f_node": torch.empty((nvert, 3), dtype=torch.float64, device=dev)}
+        ibm_surface_forces(self.h, meshes, p, out["f_node"], q=q, motions=motions, p_side=out["p_side"],
+                           flags=out["flags"], stream=stream)
+        return out
 
     def reclassify(self, meshes, stream=None):
         """New body positions on the same grid, in the tables' own memory."""

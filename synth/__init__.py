@@ -221,6 +221,22 @@ def _velocity_planes(seed: int, k0: int, k1: int, nx: int, ny: int):
     return tuple(counter_normal(seed, c, idx).reshape(shp) for c in range(3))
 
 
+def smooth_field(xf: np.ndarray, yf: np.ndarray, zf: np.ndarray, seed: int, modes: int = 3) -> np.ndarray:
+    """A smooth seeded cell field [nz][ny][nx]: the product over the axes of
+    1 + sum_m a_m cos(k_m x + phi_m) at the cell centres, with a_m, k_m, phi_m drawn from
+    the counter generator (stream 10 + axis)."""
+    out = None
+    for ax, f in enumerate((xf, yf, zf)):
+        f = np.asarray(f, dtype=np.float64)
+        x = 0.5 * (f[:-1] + f[1:])
+        u = counter_uniform(seed, 10 + ax, np.arange(3 * modes))
+        g = np.ones_like(x)
+        for m in range(modes):
+            g = g + (0.5 * u[3 * m] / modes) * np.cos((1.0 + 6.0 * u[3 * m + 1]) * x + 6.283185307179586 * u[3 * m + 2])
+        out = g if out is None else np.multiply.outer(g, out)
+    return np.ascontiguousarray(out)
+
+
 def rhs_divergence(xf: np.ndarray, yf: np.ndarray, zf: np.ndarray, seed: int, threads: int = 0) -> np.ndarray:
     """Discrete divergence of a seeded N(0,1) cell-centred velocity field.
 
