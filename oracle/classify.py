@@ -359,7 +359,8 @@ def closest_points(P: np.ndarray, meshes, chunk: int = 64):
 class GhostTable:
     """Per ghost entry: cell, BI, IP, base corner, flags, 8 (ref, weight) pairs, row scale;
     the closest triangle (global index), the Neumann coefficient kappa and the row's
-    right-hand side d (see set_neumann)."""
+    right-hand side d (see set_neumann); the row's own interpolation weight wself where it
+    was moved to the left-hand side (0 otherwise), which Dirichlet rows need."""
 
     def __init__(self, n):
         self.cell = np.zeros(n, dtype=np.int64)
@@ -373,6 +374,7 @@ class GhostTable:
         self.tri = np.full(n, -1, dtype=np.int64)
         self.kappa = np.zeros(n)
         self.d = np.zeros(n)
+        self.wself = np.zeros(n)
 
     def __len__(self):
         return self.cell.size
@@ -485,6 +487,7 @@ def ghost_tables(grid: Grid, iblank: np.ndarray, ghosts: np.ndarray, meshes) -> 
     G.w[fallback, 0] = 1.0
     G.ref[fallback, 0] = best[fallback]
     G.kappa[:] = row_kappa(grid, G, GC, fallback, move, ws, best)
+    G.wself[:] = np.where(move, ws, 0.0)
     # row scale: coefficients of the fluid rows that reference this ghost, in direction order
     sc = np.zeros(ng)
     for (di, dj, dk, cf, idx) in ((-1, 0, 0, grid.cxp, gi - 1), (1, 0, 0, grid.cxm, gi + 1),

@@ -283,6 +283,7 @@ def ghost_tables(grid: Grid, cut: np.ndarray, side: np.ndarray, meshes) -> Membr
     G.scale[:] = sc
     G.tri[:] = TRI
     G.kappa[:] = row_kappa(grid, G, GC, fallback, move, ws, best)
+    G.wself[:] = np.where(move, ws, 0.0)
     return G
 
 

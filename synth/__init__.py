@@ -194,6 +194,18 @@ def plate_motion(t: float, heave: float = 0.1, pitch_deg: float = 30.0, center=(
     return np.concatenate([a0, alpha, omega, c])
 
 
+def plate_velocity(t: float, heave: float = 0.1, pitch_deg: float = 30.0, center=(0.5, 0.5, 0.5)) -> np.ndarray:
+    """Rigid-body velocity of `plate` at phase t (time in periods): the velocity of its centre,
+    its angular velocity (about y) and the centre.  Nine numbers, the layout
+    ibm_boundary_velocity_rigid takes per mesh."""
+    w = 2.0 * math.pi
+    th0 = math.radians(pitch_deg)
+    c = np.asarray(center, dtype=np.float64) + np.array([0.0, 0.0, heave * math.sin(w * t)])
+    v0 = np.array([0.0, 0.0, heave * w * math.cos(w * t)])
+    omega = np.array([0.0, -th0 * w * math.sin(w * t), 0.0])
+    return np.concatenate([v0, omega, c])
+
+
 def random_spheres(count: int = 12, seed: int = 4, h: float = 1.0 / 1024, level: int = 4,
                    rmin: float = 0.03, rmax: float = 0.08) -> list:
     """Non-overlapping spheres by rejection sampling (surface gap >= 8 h)."""

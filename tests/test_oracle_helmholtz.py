@@ -1,0 +1,141 @@
+"""Pins of the advection-diffusion (Helmholtz) oracle with no-slip ghost rows.
+
+* No body, uniform grid: (I - alpha L) is diagonalised by the DCT-II per axis; the oracle's
+  solve matches scipy's closed form.
+* A body with a manufactured field (zero normal derivative at the walls) and its boundary
+  values at BI: second-order convergence; planted ghost-row mistakes (the Neumann row in
+  place of the Dirichlet one, the factor 2 dropped) do not converge.
+* A constant field with f = C and u_b = C satisfies every row exactly (closed bodies and
+  membranes), which the (1 + w_s) / (1 - w_s) split of the ghost rows needs: dropping
+  either factor breaks it on the rows with a moved self weight.
+* The rigid boundary velocity against central differences of the moving plate's vertices.
+"""
+import numpy as np
+import pytest
+import scipy.fft as fft
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import synth
+from oracle import classify as OC
+from oracle import helmholtz as OH
+from oracle import membrane as OM
+from oracle import system as SYS
+from oracle.grid import Grid
+
+ALPHA = 0.02
+
+
+def test_no_body_matches_dct():
+    n = 20
+    f = synth.faces_uniform(n)
+    grid = Grid(f, f, f)
+    ib = np.zeros(grid.shape, dtype=np.uint8)
+    G = OC.GhostTable(0)
+    rhs = synth.counter_normal(3, 0, np.arange(n ** 3)).reshape(grid.shape)
+    u = OH.solve_closed(grid, ib, G, ALPHA, rhs)
+    h = 1.0 / n
+    k = np.arange(n)
+    lam1 = (2.0 * np.cos(np.pi * k / n) - 2.0) / (h * h)
+    lam = lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :]
+    uh = fft.dctn(rhs, type=2, norm="ortho") / (1.0 - ALPHA * lam)
+    exact = fft.idctn(uh, type=2, norm="ortho")
+    assert np.max(np.abs(u - exact)) < 1e-12 * np.max(np.abs(exact))
+
+
+def _manufactured(n, mistake=None):
+    f = synth.faces_uniform(n)
+    grid = Grid(f, f, f)
+    mesh = synth.octa_sphere(4, (0.5, 0.5, 0.5), 0.27)
+    ib, G = OC.classify(grid, [mesh])
+    X = grid.centre(np.arange(n ** 3))
+
+    def ue(P):
+        return np.cos(np.pi * P[:, 0]) * np.cos(np.pi * P[:, 1]) * np.cos(np.pi * P[:, 2])
+
+    alpha = 0.05
+    rhs = ((1.0 + 3.0 * np.pi ** 2 * alpha) * ue(X)).reshape(grid.shape)
+    ub = ue(G.bi)
+    if mistake is None:
+        u = OH.solve_closed(grid, ib, G, alpha, rhs, ub)
+    else:
+        # planted, on the oracle's own assembly: the ghost rows of the pressure system
+        # (g - sum w v = 0, a Neumann row) or the boundary value not doubled
+        A, cells, is_fluid = SYS.assemble(grid, ib, G)
+        row = np.full(n ** 3, -1, dtype=np.int64)
+        row[cells] = np.arange(cells.size)
+        grow = row[G.cell]
+        sd = np.where(is_fluid, 1.0, 0.0)
+        ad = np.where(is_fluid, alpha, 0.0)
+        b = np.where(is_fluid, rhs.ravel()[cells], 0.0)
+        if mistake == "neumann":
+            sd[grow], ad[grow], b[grow] = 0.0, -1.0, 0.0
+        else:
+            sd[grow], ad[grow], b[grow] = 2.0, 1.0 - G.wself, ub
+        H = (sp.diags(sd) - sp.diags(ad) @ A).tocsc()
+        u = np.zeros(n ** 3)
+        u[cells] = spl.spsolve(H, b)
+    fl = ib.ravel() == 0
+    return float(np.max(np.abs(u.ravel()[fl] - ue(X)[fl])))
+
+
+def test_manufactured_second_order_and_planted_mistakes():
+    e1, e2 = _manufactured(16), _manufactured(32)
+    assert e2 < e1 / 3.0, (e1, e2)
+    for m in ("neumann", "no2"):
+        b1, b2 = _manufactured(16, m), _manufactured(32, m)
+        assert b2 > 5.0 * e2 and b2 > 0.5 * b1, (m, b1, b2)
+
+
+def test_constant_field_closed_body():
+    xf, yf, zf = synth.faces_tanh(26, 2.0), synth.faces_uniform(22), synth.faces_tanh(24, 1.5)
+    grid = Grid(xf, yf, zf)
+    ib, G = OC.classify(grid, [synth.ellipsoid(4, (0.21, 0.13, 0.12), 23.0, (0.49, 0.51, 0.5))])
+    assert np.sum(G.wself > 0.0) > 0
+    C = 1.7
+    H, cells, is_fluid, grow = OH.system_closed(grid, ib, G, ALPHA)
+    b = np.where(is_fluid, C, 0.0)
+    b[grow] = 2.0 * C
+    r = b - H @ np.full(cells.size, C)
+    assert np.max(np.abs(r)) < 1e-12 * C / grid.dx.min() ** 2
+    # planted: the (1 - w_s) factor dropped from the ghost rows
+    Gw = OC.GhostTable(len(G))
+    for k in vars(G):
+        setattr(Gw, k, getattr(G, k))
+    Gw.wself = np.zeros(len(G))
+    H2, *_ = OH.system_closed(grid, ib, Gw, ALPHA)
+    moved = grow[G.wself > 0.0]
+    H3 = H2.tolil()
+    for q, g in zip(moved, np.flatnonzero(G.wself > 0.0)):
+        H3[q, q] = 1.0 + G.wself[g]                 # (1 + w_s) kept, (1 - w_s) dropped
+    r3 = b - H3.tocsr() @ np.full(cells.size, C)
+    assert np.max(np.abs(r3[moved])) > 1e-3
+
+
+def test_constant_field_membrane():
+    grid = Grid(synth.faces_tanh(22, 2.0), synth.faces_uniform(20), synth.faces_uniform(23))
+    m = synth.plate(0.13, chord=0.5, span=0.35, nq_x=5, nq_y=5, heave=0.05, pitch_deg=25.0,
+                    center=(0.503, 0.491, 0.517))
+    _, G = OM.classify(grid, [m])
+    C = -0.8
+    u, g = OH.solve_membrane(grid, G, ALPHA, np.full(grid.shape, C), np.full(len(G), C))
+    assert np.max(np.abs(u - C)) < 1e-12 and np.max(np.abs(g - C)) < 1e-12
+
+
+def test_solution_has_small_relative_residual():
+    f = synth.faces_tanh(18, 2.0)
+    grid = Grid(f, f, f)
+    ib, G = OC.classify(grid, [synth.octa_sphere(3, (0.5, 0.5, 0.5), 0.22)])
+    rhs = synth.counter_normal(4, 0, np.arange(18 ** 3)).reshape(grid.shape)
+    ub = synth.counter_normal(5, 0, np.arange(len(G)))
+    u = OH.solve_closed(grid, ib, G, ALPHA, rhs, ub)
+    assert OH.relative_residual_closed(grid, ib, G, ALPHA, rhs, u, ub) < 1e-13
+
+
+def test_rigid_velocity_against_finite_differences():
+    t, dt = 0.3, 1e-5
+    m0, mp, mm = (synth.plate(s, nq_x=3, nq_y=2) for s in (t, t + dt, t - dt))
+    v = (mp.verts - mm.verts) / (2.0 * dt)
+    M = np.repeat(synth.plate_velocity(t)[None], m0.verts.shape[0], axis=0)
+    ub = OH.point_velocity(m0.verts, M)
+    assert np.allclose(ub, v, rtol=1e-7, atol=1e-7 * np.abs(v).max())
