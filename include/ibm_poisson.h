@@ -201,6 +201,55 @@ ibm_status ibm_neumann_rigid(ibm_tables *t, const double *motions, int32_t nmesh
 ibm_status ibm_tables_export_neumann(const ibm_tables *t, double *kappa_dev, int32_t *tri_dev,
                                      double *d_dev, void *stream);
 
+/* ibm_tables_export_self_weight: copy out wself_dev double[nghost], each ghost row's own
+ * interpolation weight w_s where it was moved to the left-hand side (0 otherwise; the stored
+ * weights are divided by 1 - w_s).  Synchronises `stream`. */
+ibm_status ibm_tables_export_self_weight(const ibm_tables *t, double *wself_dev, void *stream);
+
+/* Advection-diffusion (Helmholtz-type) velocity solve of the fractional step with no-slip
+ * ghost rows (paper Sec. "Governing Equations and Numerical Methods": the momentum equation's
+ * advection-diffusion step, solved with scheduled relaxed Jacobi; Sec. "GPU Porting" item 2:
+ * no-slip on the immersed surface).  One velocity component u solves
+ *   fluid row i:  (1 + alpha sum_d c_{i,d}) u_i - alpha sum_d c_{i,d} v_nb = f_i
+ *   ghost row G:  (1 + w_s) u_G + (1 - w_s) sum_k w_k v_k = 2 u_b,G
+ * with the pressure system's coefficients c (zero across the outer walls), neighbours v_nb
+ * as in poisson_solve, and the image-point rows of the tables (w_s: see
+ * ibm_tables_export_self_weight); the ghost row sets the value at BI, the midpoint of the
+ * ghost centre and its image point, to u_b.  alpha = dt nu / 2 for Crank-Nicolson diffusion.
+ * Iteration: cycles of srj_steps Jacobi sweeps with the relaxation factors 1 / (Chebyshev
+ * nodes of [1 - rho, 1 + rho]), rho = alpha S / (1 + alpha S), S the largest coefficient sum
+ * of a cell, the ghost rows re-evaluated after every sweep; precision 1 runs each cycle in
+ * FP32 on the correction equation inside FP64 iterative refinement.  Convergence:
+ * ||S r|| / ||S b|| <= tol over fluid and ghost rows, S = alpha s_G on ghost rows (s_G the
+ * row scale of the pressure system), 1 on fluid rows.
+ *   f_dev    double[ncell]   right-hand side on fluid cells (others ignored); not modified.
+ *   ub_dev   double[nghost]  boundary values per ghost entry in ghost order, or NULL (0).
+ *   u_dev    double[ncell]   in: initial guess on fluid and ghost cells; out: u on fluid
+ *                            cells, the ghost value on ghost cells, 0 on other solid cells
+ *                            (membranes: every cell is fluid; entry values are internal).
+ * Uses the tables' FP64 multigrid hierarchy for its layout (built on first use).  Returns
+ * IBM_ERR_NOT_CONVERGED after max_cycles cycles (u = last iterate), IBM_ERR_DIVERGED if the
+ * residual grows a millionfold; IBM_ERR_INVALID_ARG for NULL arrays, alpha < 0, tol <= 0 or
+ * options out of range.  Synchronises `stream` once per cycle to read the residual. */
+typedef struct {
+  int32_t precision;    /* 0: FP64 cycles; 1: FP32 cycles inside FP64 refinement          [1] */
+  int32_t srj_steps;    /* Jacobi sweeps (relaxation factors) per cycle, 1..64            [8] */
+  int32_t max_cycles;   /* cycles (precision 0) or refinement steps (precision 1)       [100] */
+} ibm_helmholtz_opts;
+
+void ibm_helmholtz_opts_default(ibm_helmholtz_opts *opts);
+ibm_status ibm_helmholtz_solve(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_dev,
+                               const double *ub_dev, double tol, double *u_dev,
+                               const ibm_helmholtz_opts *opts, ibm_solve_info *info, void *stream);
+
+/* Rigid-body boundary velocity of every ghost entry: u_b = v0 + omega x (BI - c) for the mesh
+ * holding the entry's closest triangle.  motions (host) double[nmesh * 9]: per mesh in
+ * classification order v0 (3), omega (3), c (3); nmesh must equal the classification's mesh
+ * count (at most 32; IBM_ERR_CAPACITY beyond).  ub_dev double[3][nghost] out (device),
+ * component-major.  Stream-ordered. */
+ibm_status ibm_boundary_velocity_rigid(ibm_tables *t, const double *motions, int32_t nmesh,
+                                       double *ub_dev, void *stream);
+
 /* Surface pressure and nodal pressure forces (paper Sec. "Force Formulations": the external
  * force on a structure node is one third of the traction times the area, summed over the
  * node's triangles; here the pressure part, -dp n A).  The shear part is not computed.

@@ -18,7 +18,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path
 # per-file extra flags: the classification and surface-force units keep every FP64 operation
 # separately rounded
 EXTRA = {"classify.cu": ["-fmad=false"], "forces.cu": ["-fmad=false"]}
-SOURCES = ["capi.cu", "classify.cu", "mg.cu", "noalloc.cu", "forces.cu"]
+SOURCES = ["capi.cu", "classify.cu", "mg.cu", "noalloc.cu", "forces.cu", "helmholtz.cu"]
 
 
 def nvcc() -> str:

@@ -29,6 +29,11 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
                        double *kernel_ms);
 ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st);
 ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st);
+ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_user, const double *ub,
+                                double tol, double *u_user, const ibm_helmholtz_opts *opts, ibm_solve_info *info,
+                                cudaStream_t st);
+ibm_status boundary_velocity_rigid_impl(ibm_tables *T, const double *motions, int nmesh, double *ub,
+                                        cudaStream_t st);
 ibm_status surface_forces_impl(ibm_tables *T, const ibm_mesh *meshes, int nmesh, const double *p,
                                const double *q_tri, const double *motions, double *p_side, uint8_t *flags,
                                double *f_node, cudaStream_t st);
@@ -116,7 +121,7 @@ ibm_status ibm_tables_destroy(ibm_tables *t) {
   cudaDeviceSynchronize();
   for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
   void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref, t->axis,
-                t->scratch, t->cut, t->cside, t->gside, t->gkeys, t->gkappa, t->gd, t->gtri, t->fbuf};
+                t->scratch, t->cut, t->cside, t->gside, t->gkeys, t->gkappa, t->gd, t->gtri, t->fbuf, t->gwself};
   for (void *p : ps) if (p) cudaFree(p);
   delete t;
   return IBM_OK;
@@ -132,6 +137,38 @@ ibm_status ibm_neumann_rigid(ibm_tables *t, const double *motions, int32_t nmesh
   if (!t) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(t->ctx->device));
   return ibm::neumann_rigid_impl(t, motions, nmesh, (cudaStream_t)stream);
+}
+
+ibm_status ibm_tables_export_self_weight(const ibm_tables *t, double *wself_dev, void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (t->nghost > 0 && wself_dev)
+    IBM_TRY(cudaMemcpyAsync(wself_dev, t->gwself, sizeof(double) * t->nghost, cudaMemcpyDeviceToDevice, st));
+  IBM_TRY(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
+void ibm_helmholtz_opts_default(ibm_helmholtz_opts *o) {
+  if (!o) return;
+  o->precision = 1;
+  o->srj_steps = 8;
+  o->max_cycles = 100;
+}
+
+ibm_status ibm_helmholtz_solve(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_dev, const double *ub_dev,
+                               double tol, double *u_dev, const ibm_helmholtz_opts *opts, ibm_solve_info *info,
+                               void *stream) {
+  if (!ctx || !t || t->ctx != ctx) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return ibm::helmholtz_solve_impl(ctx, t, alpha, f_dev, ub_dev, tol, u_dev, opts, info, (cudaStream_t)stream);
+}
+
+ibm_status ibm_boundary_velocity_rigid(ibm_tables *t, const double *motions, int32_t nmesh, double *ub_dev,
+                                       void *stream) {
+  if (!t) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(t->ctx->device));
+  return ibm::boundary_velocity_rigid_impl(t, motions, nmesh, ub_dev, (cudaStream_t)stream);
 }
 
 ibm_status ibm_surface_forces(ibm_tables *t, const ibm_mesh *meshes, int32_t nmesh, const double *p_dev,

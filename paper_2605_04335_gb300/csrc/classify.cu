@@ -463,6 +463,7 @@ struct GhostArgs {
   long long *ref;
   double *kappa;           // Neumann coefficient of each row
   int *tri;                // closest triangle of each ghost
+  double *wself;           // the row's own weight where moved to the left-hand side, else 0
 };
 
 __device__ __forceinline__ void base_t(const double *c, int n, double v, int &i0, double &t) {
@@ -694,6 +695,7 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_ghost_tables(GhostArgs a) {
   }
   int flags = 0;
   a.tri[g] = bidx;
+  a.wself[g] = (moved && !fallback) ? wself : 0.0;
   if (!fallback) a.kappa[g] = row_kappa(P, IP, moved, wself);
   if (fallback) {
     flags |= 1;
@@ -1075,6 +1077,7 @@ __global__ void __launch_bounds__(TABLE_THREADS) k_mem_tables(GhostArgs a, MemAr
     }
   }
   a.tri[g] = bidx;
+  a.wself[g] = (moved && !fallback) ? wself : 0.0;
   // the cells that use the entry: face-neighbours n of the cell cut from side gs (the
   // cell's own side bit of that link is the other side)
   const uint8_t cc = m.cut[lin], cs = m.side[lin];
@@ -1238,10 +1241,10 @@ cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
   if (ng <= T->gcap && T->gcell) return cudaSuccess;
   const long long cap = std::max<long long>(std::max<long long>(ng + ng / 4, 1024), T->gcap);
   void *ps[] = {T->gcell, T->gbi,   T->gip,  T->gw,     T->gscale, T->gbase, T->gflags,
-                T->gref,  T->gside, T->gkeys, T->gkappa, T->gd,     T->gtri};
+                T->gref,  T->gside, T->gkeys, T->gkappa, T->gd,     T->gtri,   T->gwself};
   for (void *q : ps) if (q) cudaFree(q);
   T->gcell = nullptr; T->gbi = T->gip = T->gw = T->gscale = nullptr; T->gbase = T->gflags = nullptr; T->gref = nullptr;
-  T->gside = nullptr; T->gkeys = nullptr; T->gkappa = T->gd = nullptr; T->gtri = nullptr;
+  T->gside = nullptr; T->gkeys = nullptr; T->gkappa = T->gd = nullptr; T->gtri = nullptr; T->gwself = nullptr;
   T->gcap = 0;
   cudaError_t e = cudaMalloc(&T->gcell, cap * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&T->gbi, cap * 3 * sizeof(double));
@@ -1256,6 +1259,7 @@ cudaError_t ensure_ghost_capacity(ibm_tables *T, long long ng) {
   if (e == cudaSuccess) e = cudaMalloc(&T->gkappa, cap * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&T->gd, cap * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&T->gtri, cap * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&T->gwself, cap * sizeof(double));
   if (e == cudaSuccess) T->gcap = cap;
   return e;
 }
@@ -1352,7 +1356,7 @@ ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
-    ga.kappa = T->gkappa; ga.tri = T->gtri;
+    ga.kappa = T->gkappa; ga.tri = T->gtri; ga.wself = T->gwself;
     MemArgs ma;
     ma.ncell = ncell; ma.keys = T->gkeys; ma.gside = T->gside; ma.cut = T->cut; ma.side = T->cside;
     ma.Xs = ds[0]; ma.Ys = ds[1]; ma.Zs = ds[2]; ma.ntri = ntri;
@@ -1538,7 +1542,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     ga.ng = ng; ga.gcell = T->gcell;
     ga.bi = T->gbi; ga.ip = T->gip; ga.w = T->gw; ga.scale = T->gscale;
     ga.base = T->gbase; ga.flags = T->gflags; ga.ref = T->gref;
-    ga.kappa = T->gkappa; ga.tri = T->gtri;
+    ga.kappa = T->gkappa; ga.tri = T->gtri; ga.wself = T->gwself;
     k_ghost_tables<<<nblk(32 * ng, TABLE_THREADS), TABLE_THREADS, 0, st>>>(ga);
     CTRY(cudaGetLastError());
   }

@@ -1,0 +1,473 @@
+// Advection-diffusion (Helmholtz-type) velocity solve of the fractional step, with no-slip
+// ghost rows, by scheduled relaxed Jacobi (SRJ): Sec. "Governing Equations and Numerical
+// Methods" (the momentum equation split into an advection-diffusion step solved with SRJ and
+// the pressure Poisson equation), Sec. "Results and Discussions" (the diagonally dominant
+// advection-diffusion system), Sec. "GPU Porting" item 2 (no-slip on the immersed surface).
+//
+// System (the paper gives no discretisation; reading): one velocity component u solves
+//   fluid row i:  D_i u_i - alpha sum_d c_{i,d} v_nb = f_i,  D_i = 1 + alpha sum_d c_{i,d}
+//                 (c: the pressure system's 7-point coefficients, zero across the walls;
+//                 v_nb the neighbour, the ghost cell or, across a cut membrane link, the
+//                 neighbour's entry on this cell's side)
+//   ghost row G:  (1 + w_s) u_G + (1 - w_s) sum_k w_k v_k = 2 u_b
+//                 (the boundary value at BI, the midpoint of the ghost centre and its image
+//                 point; w_k the image-point weights divided by 1 - w_s, w_s the row's own
+//                 weight moved to the left-hand side, 0 if none)
+// SRJ cycle: K Jacobi sweeps of the fluid rows with relaxation factors w_k = 1 / lambda_k,
+// lambda_k the Chebyshev nodes of [1 - rho, 1 + rho], rho = alpha S / (1 + alpha S) with S
+// the largest sum of a cell's coefficients: the fluid rows' Jacobi spectrum lies in that
+// interval (diagonal dominance).  After every sweep the ghost rows are re-evaluated from the
+// new fluid values (Jacobi among ghosts).  Precision 0 runs the cycles in FP64; precision 1
+// runs each cycle in FP32 on the correction equation H e = r inside FP64 iterative
+// refinement (r and the update in FP64).  Convergence: ||S r|| / ||S b|| over fluid and
+// ghost rows, S = alpha s_G on ghost rows (s_G the pressure system's row scale), 1 elsewhere.
+//
+// Layout: the finest level of the FP64 multigrid hierarchy of the tables (padded arrays,
+// mask, ghost sources, membrane entry slots and cut-cell lists) is shared with the pressure
+// solver; the velocity work arrays live in the hierarchy's own workspace.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "ibm_internal.cuh"
+
+namespace ibm {
+
+ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st);
+
+namespace {
+
+constexpr int HZ_BLOCKS = REDUCE_BLOCKS;   // fixed grid of the norm kernels: deterministic sums
+constexpr int HZ_THREADS = 256;
+constexpr int TX = 32, TY = 8, KCH = 16;   // sweep tile (x, y) and z-planes per block
+
+inline unsigned nb_of(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+struct HzView {
+  int nx, ny, nz;
+  long long sy, sz;
+  const uint8_t *mask;
+  const T *cxm, *cxp, *cym, *cyp, *czm, *czp;   // face coefficients per axis
+  const T *sdx, *sdy, *sdz;                     // their per-axis sums
+};
+
+// one Jacobi step of the fluid rows with relaxation w: un = u + w (f - H u) / D, each block a
+// 32 x 8 tile marching KCH planes in z with the z-neighbours in registers
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_hz_sweep(HzView<T> v, const T *u, T *un, const T *f, T alpha, T w) {
+  const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+  if (i >= v.nx || j >= v.ny) return;
+  const int k0 = blockIdx.z * KCH, k1 = min(v.nz, k0 + KCH);
+  long long id = ((long long)(k0 + 1) * (v.ny + 2) + (j + 1)) * v.sy + (i + OX);
+  const T cxm = v.cxm[i], cxp = v.cxp[i], cym = v.cym[j], cyp = v.cyp[j], sxy = v.sdx[i] + v.sdy[j];
+  T zm = u[id - v.sz], zc = u[id];
+  for (int k = k0; k < k1; ++k, id += v.sz) {
+    const T zp = u[id + v.sz];
+    if (v.mask[id] == 0) {
+      T s = cxm * u[id - 1];
+      s += cxp * u[id + 1];
+      s += cym * u[id - v.sy];
+      s += cyp * u[id + v.sy];
+      s += v.czm[k] * zm;
+      s += v.czp[k] * zp;
+      const T D = (T)1 + alpha * (sxy + v.sdz[k]);
+      const T res = f[id] - (D * zc - alpha * s);
+      un[id] = zc + w * res / D;
+    }
+    zm = zc;
+    zc = zp;
+  }
+}
+
+// the same step at the membrane cut cells (their links read the entries through cut_nb)
+template <typename T>
+__global__ void k_hz_sweep_cut(HzView<T> v, const long long *cut_id, const long long *cut_nb, const int *cut_ijk,
+                               const long long *cnt, const T *u, T *un, const T *f, T alpha, T w) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt[1];
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long id = cut_id[t];
+    const int i = cut_ijk[3 * t], j = cut_ijk[3 * t + 1], k = cut_ijk[3 * t + 2];
+    const T c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
+    T s = 0;
+    for (int d = 0; d < 6; ++d) s += c[d] * u[cut_nb[6 * t + d]];
+    const T D = (T)1 + alpha * ((v.sdx[i] + v.sdy[j]) + v.sdz[k]);
+    const T res = f[id] - (D * u[id] - alpha * s);
+    un[id] = u[id] + w * res / D;
+  }
+}
+
+// ghost rows from the new fluid values and the previous ghost values:
+// u_G = (b_G - (1 - w_s) sum w v) / (1 + w_s), b_G = f at the ghost's slot
+template <typename T>
+__global__ void k_hz_ghost(const long long *src, const long long *dst, const double *gw, const double *ws,
+                           long long ng, T *un, const T *u, const T *f) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  T s = 0;
+  for (int c = 0; c < 8; ++c) {
+    const long long q = src[8 * g + c];
+    if (q < 0) continue;
+    const T v = (q & GHOST_CORNER) ? u[q & ~GHOST_CORNER] : un[q];
+    s += (T)gw[8 * g + c] * v;
+  }
+  const T w = (T)ws[g];
+  un[dst[g]] = (f[dst[g]] - ((T)1 - w) * s) / ((T)1 + w);
+}
+
+// FP64 residual r = b - H u of the regular fluid rows; block partials of sum r^2 (and of
+// sum b^2 when bpart); r32 (if given) receives r in FP32
+__global__ void __launch_bounds__(HZ_THREADS) k_hz_resid(HzView<double> v, const double *u, const double *f,
+                                                         double alpha, float *r32, double *part, bool with_b) {
+  __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
+  double ar = 0.0, ab = 0.0;
+  const long long rows = (long long)v.ny * v.nz;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = (int)(row % v.ny), k = (int)(row / v.ny);
+    const long long base = ((long long)(k + 1) * (v.ny + 2) + (j + 1)) * v.sy + OX;
+    const double cym = v.cym[j], cyp = v.cyp[j], czm = v.czm[k], czp = v.czp[k], syz = v.sdy[j] + v.sdz[k];
+    for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
+      const long long id = base + i;
+      if (v.mask[id] != 0) continue;
+      double s = v.cxm[i] * u[id - 1];
+      s += v.cxp[i] * u[id + 1];
+      s += cym * u[id - v.sy];
+      s += cyp * u[id + v.sy];
+      s += czm * u[id - v.sz];
+      s += czp * u[id + v.sz];
+      const double D = 1.0 + alpha * (v.sdx[i] + syz);
+      const double r = f[id] - (D * u[id] - alpha * s);
+      if (r32) r32[id] = (float)r;
+      ar += r * r;
+      if (with_b) ab += f[id] * f[id];
+    }
+  }
+  sr[threadIdx.x] = ar;
+  sb[threadIdx.x] = ab;
+  __syncthreads();
+  for (int st = HZ_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { sr[threadIdx.x] += sr[threadIdx.x + st]; sb[threadIdx.x] += sb[threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = sr[0]; part[2 * blockIdx.x + 1] = sb[0]; }
+}
+
+// residual of the cut cells and of the ghost rows (scaled by alpha s_G), one block-partial
+// pair per block after the regular rows' partials
+__global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_rest(
+    HzView<double> v, const long long *cut_id, const long long *cut_nb, const int *cut_ijk, const long long *cnt,
+    const long long *src, const long long *dst, const double *gw, const double *ws, const double *gscale,
+    long long ng, const double *u, const double *f, double alpha, float *r32, double *part, bool with_b) {
+  __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
+  double ar = 0.0, ab = 0.0;
+  const long long ncut = cnt ? cnt[1] : 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncut + ng;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < ncut) {
+      const long long id = cut_id[t];
+      const int i = cut_ijk[3 * t], j = cut_ijk[3 * t + 1], k = cut_ijk[3 * t + 2];
+      const double c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
+      double s = 0.0;
+      for (int d = 0; d < 6; ++d) s += c[d] * u[cut_nb[6 * t + d]];
+      const double D = 1.0 + alpha * ((v.sdx[i] + v.sdy[j]) + v.sdz[k]);
+      const double r = f[id] - (D * u[id] - alpha * s);
+      if (r32) r32[id] = (float)r;
+      ar += r * r;
+      if (with_b) ab += f[id] * f[id];
+    } else {
+      const long long g = t - ncut;
+      double s = 0.0;
+      for (int c = 0; c < 8; ++c) {
+        const long long q = src[8 * g + c];
+        if (q >= 0) s += gw[8 * g + c] * u[q & ~GHOST_CORNER];
+      }
+      const long long id = dst[g];
+      const double r = f[id] - ((1.0 + ws[g]) * u[id] + (1.0 - ws[g]) * s);
+      if (r32) r32[id] = (float)r;
+      const double sc = alpha * gscale[g];
+      ar += (sc * r) * (sc * r);
+      if (with_b) ab += (sc * f[id]) * (sc * f[id]);
+    }
+  }
+  sr[threadIdx.x] = ar;
+  sb[threadIdx.x] = ab;
+  __syncthreads();
+  for (int st = HZ_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { sr[threadIdx.x] += sr[threadIdx.x + st]; sb[threadIdx.x] += sb[threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = sr[0]; part[2 * blockIdx.x + 1] = sb[0]; }
+}
+
+// out[0] = sum of the r^2 partials, out[1] = sum of the b^2 partials (fixed order)
+__global__ void k_hz_norms(const double *part, int nb, double *out) {
+  __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
+  double ar = 0.0, ab = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) { ar += part[2 * b]; ab += part[2 * b + 1]; }
+  sr[threadIdx.x] = ar;
+  sb[threadIdx.x] = ab;
+  __syncthreads();
+  for (int st = HZ_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { sr[threadIdx.x] += sr[threadIdx.x + st]; sb[threadIdx.x] += sb[threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = sr[0]; out[1] = sb[0]; }
+}
+
+// user layout -> padded: f on fluid rows (0 elsewhere), u on fluid and ghost cells
+__global__ void k_hz_pack(const double *f, const double *u, long long ncell, int nx, int ny, LevelGeom g,
+                          const uint8_t *mask, double *fp, double *up) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= ncell) return;
+  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  const long long id = pidx(g, i, j, k);
+  const uint8_t m = mask[id];
+  fp[id] = fluid_row(m) ? f[l] : 0.0;
+  up[id] = (fluid_row(m) || m == 3) ? u[l] : 0.0;
+}
+
+// ghost-row right-hand sides 2 u_b at the ghosts' slots
+__global__ void k_hz_ghost_rhs(const long long *dst, const double *ub, long long ng, double *fp) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < ng) fp[dst[g]] = ub ? 2.0 * ub[g] : 0.0;
+}
+
+__global__ void k_hz_unpack(const double *up, long long ncell, int nx, int ny, LevelGeom g, const uint8_t *mask,
+                            double *u) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= ncell) return;
+  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  const long long id = pidx(g, i, j, k);
+  const uint8_t m = mask[id];
+  u[l] = (fluid_row(m) || m == 3) ? up[id] : 0.0;
+}
+
+// u += e on every slot (e is zero off the active rows)
+__global__ void k_hz_update(double *u, const float *e, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    u[q] += (double)e[q];
+}
+
+__global__ void k_to_float(const double *a, long long n, float *b) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q < n) b[q] = (float)a[q];
+}
+
+// rigid boundary velocity of every ghost entry: u_b = v0 + omega x (BI - c) for the mesh of
+// its closest triangle; out[d * ng + g]
+constexpr int MAX_RIGID_V = 32;
+struct RigidVel {
+  int n;
+  int off[MAX_RIGID_V + 1];
+  double m[MAX_RIGID_V][9];   // v0 (3), omega (3), centre (3)
+};
+
+__global__ void k_rigid_velocity(const double *bi, const int *tri, long long ng, RigidVel M, double *out) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  int lo = 0, hi = M.n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (M.off[mid] <= tri[g]) lo = mid; else hi = mid;
+  }
+  const double *mm = M.m[lo], *om = mm + 3;
+  const double r[3] = {bi[3 * g] - mm[6], bi[3 * g + 1] - mm[7], bi[3 * g + 2] - mm[8]};
+  out[g] = mm[0] + (om[1] * r[2] - om[2] * r[1]);
+  out[ng + g] = mm[1] + (om[2] * r[0] - om[0] * r[2]);
+  out[2 * ng + g] = mm[2] + (om[0] * r[1] - om[1] * r[0]);
+}
+
+// the largest sum of one cell's face coefficients along one axis (host, from the faces)
+double axis_max_sum(const std::vector<double> &f) {
+  const int n = (int)f.size() - 1;
+  double best = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double ci = 0.5 * (f[i] + f[i + 1]), wi = f[i + 1] - f[i];
+    double s = 0.0;
+    if (i > 0) s += 1.0 / (wi * (ci - 0.5 * (f[i - 1] + f[i])));
+    if (i < n - 1) s += 1.0 / (wi * (0.5 * (f[i + 1] + f[i + 2]) - ci));
+    best = std::max(best, s);
+  }
+  return best;
+}
+
+struct HzWork {
+  double *u[2], *f;
+  float *e[2], *r32, *c32;
+  double *part, *norms;
+};
+
+}  // namespace
+
+ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_user, const double *ub,
+                                double tol, double *u_user, const ibm_helmholtz_opts *opts, ibm_solve_info *info,
+                                cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  ibm_helmholtz_opts o;
+  ibm_helmholtz_opts_default(&o);
+  if (opts) o = *opts;
+  if (!f_user || !u_user || !(alpha >= 0.0) || !std::isfinite(alpha) || !(tol > 0.0) || o.precision < 0 ||
+      o.precision > 1 || o.srj_steps < 1 || o.srj_steps > 64 || o.max_cycles < 1)
+    return IBM_ERR_INVALID_ARG;
+  ibm_status s = build_hierarchy(t, 0, st);
+  if (s != IBM_OK) return s;
+  Hierarchy *h = t->hier[0];
+  Level &L0 = h->lv[0];
+  const LevelGeom &G = L0.g;
+  const long long nslot = h->nslot, ncell = t->ncell, ng = t->nghost;
+  const int nx = G.nx, ny = G.ny, nz = G.nz, na = nx + ny + nz;
+  // workspace: u (2), f in FP64; e (2), r in FP32; FP32 coefficients; partials; norms
+  const long long want = nslot;
+  const size_t bytes = sizeof(double) * (3 * (size_t)want + 2 * (size_t)HZ_BLOCKS * 2 + 8) +
+                       sizeof(float) * (3 * (size_t)want + 3 * (size_t)na + 64);
+  if (!h->helm_buf || h->helm_n != want) {
+    if (h->helm_buf) { IBM_TRY(cudaStreamSynchronize(st)); cudaFree(h->helm_buf); }
+    h->helm_buf = nullptr;
+    h->helm_n = 0;
+    IBM_TRY(cudaMalloc(&h->helm_buf, bytes));
+    IBM_TRY(cudaMemsetAsync(h->helm_buf, 0, bytes, st));   // halos and inactive cells stay 0
+    h->helm_n = want;
+  }
+  HzWork W;
+  {
+    double *d = (double *)h->helm_buf;
+    W.u[0] = d; W.u[1] = d + want; W.f = d + 2 * want;
+    W.part = d + 3 * want;
+    W.norms = W.part + 2 * 2 * HZ_BLOCKS;
+    float *fl = (float *)(W.norms + 8);
+    W.e[0] = fl; W.e[1] = fl + want; W.r32 = fl + 2 * want; W.c32 = fl + 3 * want;
+  }
+  // views of the finest level: FP64 coefficients of the hierarchy, FP32 copies
+  const double *c64 = h->c64;
+  HzView<double> v64;
+  v64.nx = nx; v64.ny = ny; v64.nz = nz; v64.sy = G.sy; v64.sz = G.sz; v64.mask = L0.mask;
+  v64.cxm = c64; v64.cxp = c64 + nx; v64.cym = c64 + 2 * nx; v64.cyp = v64.cym + ny;
+  v64.czm = v64.cyp + ny; v64.czp = v64.czm + nz;
+  v64.sdx = c64 + 2 * na; v64.sdy = v64.sdx + nx; v64.sdz = v64.sdy + ny;
+  long long launches = 0;
+  HzView<float> v32;
+  if (o.precision == 1) {
+    k_to_float<<<nb_of(3 * na, 256), 256, 0, st>>>(c64, 3 * na, W.c32);
+    ++launches;
+    const float *c = W.c32;
+    v32.nx = nx; v32.ny = ny; v32.nz = nz; v32.sy = G.sy; v32.sz = G.sz; v32.mask = L0.mask;
+    v32.cxm = c; v32.cxp = c + nx; v32.cym = c + 2 * nx; v32.cyp = v32.cym + ny;
+    v32.czm = v32.cyp + ny; v32.czp = v32.czm + nz;
+    v32.sdx = c + 2 * na; v32.sdy = v32.sdx + nx; v32.sdz = v32.sdy + ny;
+  }
+  // pack f, u and the ghost rows' right-hand sides
+  k_hz_pack<<<nb_of(ncell, 256), 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, W.f, W.u[0]);
+  ++launches;
+  if (ng > 0) {
+    k_hz_ghost_rhs<<<nb_of(ng, 128), 128, 0, st>>>(h->gdst, ub, ng, W.f);
+    ++launches;
+  }
+  const bool cuts = t->membrane && h->cut_id;
+  const unsigned cut_blocks = cuts ? std::max(1u, std::min(nb_of(h->cutcap, 256), 1216u)) : 0;
+  // SRJ relaxation factors: 1 / Chebyshev nodes of [1 - rho, 1 + rho]
+  const double S = axis_max_sum(t->xf) + axis_max_sum(t->yf) + axis_max_sum(t->zf);
+  const double rho = alpha * S / (1.0 + alpha * S);
+  const int K = o.srj_steps;
+  std::vector<double> om(K);
+  for (int k = 0; k < K; ++k) om[k] = 1.0 / (1.0 + rho * std::cos(3.141592653589793 * (2.0 * k + 1.0) / (2.0 * K)));
+  const dim3 sweep_grid(nb_of(nx, TX), nb_of(ny, TY), nb_of(nz, KCH)), sweep_block(TX, TY);
+  const int rest_blocks = (int)std::max<long long>(1, std::min<long long>(HZ_BLOCKS, nb_of((cuts ? h->cutcap : 0) + ng, HZ_THREADS)));
+  // residual r = b - H u (FP64) with its norm, and the norm of b on the first call
+  auto residual = [&](const double *u, float *r32, bool with_b) -> ibm_status {
+    k_hz_resid<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, u, W.f, alpha, r32, W.part, with_b);
+    k_hz_resid_rest<<<rest_blocks, HZ_THREADS, 0, st>>>(v64, h->cut_id, h->cut_nb, h->cut_ijk, cuts ? h->d_cnt : nullptr,
+                                                        h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng, u, W.f,
+                                                        alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
+    k_hz_norms<<<1, HZ_THREADS, 0, st>>>(W.part, HZ_BLOCKS + rest_blocks, W.norms);
+    launches += 3;
+    IBM_TRY(cudaMemcpyAsync(ctx->hscal, W.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IBM_TRY(cudaStreamSynchronize(st));
+    return IBM_OK;
+  };
+  // one SRJ cycle of K relaxed Jacobi steps on (u, rhs); returns the index of the current buffer
+  auto srj_cycle = [&](auto *buf0, auto *buf1, const auto *rhs, auto view, int cur) -> int {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(buf0)>>;
+    T *b[2] = {buf0, buf1};
+    for (int k = 0; k < K; ++k) {
+      T *u = b[cur], *un = b[1 - cur];
+      k_hz_sweep<T><<<sweep_grid, sweep_block, 0, st>>>(view, u, un, rhs, (T)alpha, (T)om[k]);
+      ++launches;
+      if (cuts) {
+        k_hz_sweep_cut<T><<<cut_blocks, 256, 0, st>>>(view, h->cut_id, h->cut_nb, h->cut_ijk, h->d_cnt, u, un, rhs,
+                                                     (T)alpha, (T)om[k]);
+        ++launches;
+      }
+      if (ng > 0) {
+        k_hz_ghost<T><<<nb_of(ng, 128), 128, 0, st>>>(h->gsrc, h->gdst, t->gw, t->gwself, ng, un, u, rhs);
+        ++launches;
+      }
+      cur = 1 - cur;
+    }
+    return cur;
+  };
+  ibm_status ret = IBM_OK;
+  int cycles = 0, hist = 0;
+  double rel = 0.0;
+  if ((s = residual(W.u[0], o.precision == 1 ? W.r32 : nullptr, true)) != IBM_OK) return s;
+  const double bnorm = std::sqrt(ctx->hscal[1]);
+  double r0 = std::sqrt(ctx->hscal[0]);
+  int cur = 0;
+  if (bnorm == 0.0) {
+    IBM_TRY(cudaMemsetAsync(W.u[0], 0, sizeof(double) * want, st));
+    rel = 0.0;
+  } else {
+    rel = r0 / bnorm;
+    while (rel > tol) {
+      if (cycles >= o.max_cycles) { ret = IBM_ERR_NOT_CONVERGED; break; }
+      if (o.precision == 0) {
+        cur = srj_cycle(W.u[0], W.u[1], (const double *)W.f, v64, cur);
+        if ((s = residual(W.u[cur], nullptr, false)) != IBM_OK) return s;
+      } else {
+        IBM_TRY(cudaMemsetAsync(W.e[0], 0, sizeof(float) * want, st));
+        const int ec = srj_cycle(W.e[0], W.e[1], (const float *)W.r32, v32, 0);
+        k_hz_update<<<1216, 256, 0, st>>>(W.u[cur], W.e[ec], want);
+        ++launches;
+        if ((s = residual(W.u[cur], W.r32, false)) != IBM_OK) return s;
+      }
+      ++cycles;
+      const double rn = std::sqrt(ctx->hscal[0]);
+      rel = rn / bnorm;
+      if (info && info->resid_history && hist < info->history_cap) info->resid_history[hist++] = rel;
+      if (!std::isfinite(rel) || rn > 1e6 * std::max(r0, bnorm)) { ret = IBM_ERR_DIVERGED; break; }
+    }
+  }
+  k_hz_unpack<<<nb_of(ncell, 256), 256, 0, st>>>(W.u[cur], ncell, nx, ny, G, L0.mask, u_user);
+  ++launches;
+  IBM_TRY(cudaGetLastError());
+  IBM_TRY(cudaStreamSynchronize(st));
+  ctx->launches += launches;
+  if (info) {
+    info->cycles = cycles;
+    info->history_len = hist;
+    info->rel_resid = rel;
+    info->lambda = 0.0;
+    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return ret;
+}
+
+ibm_status boundary_velocity_rigid_impl(ibm_tables *T, const double *motions, int nmesh, double *ub,
+                                        cudaStream_t st) {
+  if (nmesh < 1 || nmesh + 1 != (int)T->mesh_tri_off.size() || !motions || !ub) return IBM_ERR_INVALID_ARG;
+  if (nmesh > MAX_RIGID_V) return IBM_ERR_CAPACITY;
+  RigidVel M;
+  M.n = nmesh;
+  for (int m = 0; m <= nmesh; ++m) M.off[m] = T->mesh_tri_off[m];
+  for (int m = 0; m < nmesh; ++m)
+    for (int q = 0; q < 9; ++q) M.m[m][q] = motions[9 * m + q];
+  const long long ng = T->nghost;
+  if (ng > 0) {
+    k_rigid_velocity<<<nb_of(ng, 256), 256, 0, st>>>(T->gbi, T->gtri, ng, M, ub);
+    T->ctx->launches += 1;
+  }
+  IBM_TRY(cudaGetLastError());
+  return IBM_OK;
+}
+
+}  // namespace ibm

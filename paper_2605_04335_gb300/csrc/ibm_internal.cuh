@@ -49,6 +49,12 @@ __host__ __device__ inline long long pidx(const LevelGeom &g, int i, int j, int 
   return ((long long)(k + 1) * (g.ny + 2) + (j + 1)) * g.px + (i + OX);
 }
 
+constexpr long long GHOST_CORNER = 1LL << 62;   // flag on a ghost-row source that is itself a ghost
+// finest-level mask value of a fluid cell with a cut membrane link: a fluid row whose stencil
+// reads ghost entries, updated by the cut-cell kernels instead of the regular ones
+constexpr uint8_t MASK_CUT = 4;
+__host__ __device__ __forceinline__ bool fluid_row(uint8_t m) { return m == 0 || m == MASK_CUT; }
+
 // One multigrid level; arrays are device memory owned by the hierarchy.
 struct Level {
   LevelGeom g;
@@ -114,6 +120,8 @@ struct Hierarchy {
   uint8_t *par_flag = nullptr;              // level-1 scratch flags (kept zero between uses)
   void *bicg_buf = nullptr;                 // workspace of the paper's solver (BiCGStab + SRJ)
   long long bicg_n = 0;
+  void *helm_buf = nullptr;                 // workspace of the advection-diffusion solve
+  long long helm_n = 0;
   int gcr_m = 0;                            // Krylov directions allocated
   void *gcr_buf = nullptr;                  // 2 gcr_m arrays of nslot elements of T (Z then Q)
   void *gcr_state = nullptr;                // device state of the Krylov acceleration
@@ -170,6 +178,8 @@ struct ibm_tables {
   // ibm_neumann_rigid and cleared by every classification
   double *gkappa = nullptr, *gd = nullptr;
   int *gtri = nullptr;               // closest triangle of each ghost (global index)
+  double *gwself = nullptr;          // each row's own weight moved to the left-hand side (else 0):
+                                     // the Dirichlet rows of the velocity systems need it
   bool has_datum = false;
   std::vector<int> mesh_tri_off;     // first global triangle index of each mesh, and the total
   long long geom_version = 0;        // incremented by every classification of these tables

@@ -39,11 +39,6 @@ namespace {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-constexpr long long GHOST_CORNER = 1LL << 62;   // flag on a ghost-row source that is itself a ghost
-// finest-level mask value of a fluid cell with a cut membrane link: a fluid row whose stencil
-// reads ghost entries, updated by the cut-cell kernels instead of the regular ones
-constexpr uint8_t MASK_CUT = 4;
-__host__ __device__ __forceinline__ bool fluid_row(uint8_t m) { return m == 0 || m == MASK_CUT; }
 
 template <typename T>
 struct LV {          // kernel-side view of one level
@@ -2058,8 +2053,8 @@ void free_hierarchy(Hierarchy *h) {
   void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
                h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng,
                h->cut_id, h->cut_nb, h->cut_ijk, h->par_id, h->d_cnt, h->par_flag, h->scan_buf, h->gcr_buf,
-               h->gcr_state, h->gcr_part, h->bicg_buf};
-  ps.insert(ps.end(), q, q + 28);
+               h->gcr_state, h->gcr_part, h->bicg_buf, h->helm_buf};
+  ps.insert(ps.end(), q, q + sizeof(q) / sizeof(q[0]));
   std::sort(ps.begin(), ps.end());
   ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
   for (void *p : ps) if (p) cudaFree(p);

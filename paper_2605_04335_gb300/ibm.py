@@ -46,6 +46,10 @@ class ibm_solve_opts(C.Structure):
                 ("krylov", C.c_int32), ("method", C.c_int32), ("srj_steps", C.c_int32)]
 
 
+class ibm_helmholtz_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("srj_steps", C.c_int32), ("max_cycles", C.c_int32)]
+
+
 class ibm_solve_info(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("history_len", C.c_int32), ("rel_resid", C.c_double),
                 ("lambda_", C.c_double), ("ms_total", C.c_double), ("resid_history", C.c_void_p),
@@ -80,6 +84,10 @@ def load_library():
         "ibm_tables_export_neumann": (I32, [P, P, P, P, P]),
         "ibm_set_neumann": (I32, [P, P, P]),
         "ibm_neumann_rigid": (I32, [P, C.POINTER(C.c_double), I32, P]),
+        "ibm_tables_export_self_weight": (I32, [P, P, P]),
+        "ibm_helmholtz_opts_default": (None, [C.POINTER(ibm_helmholtz_opts)]),
+        "ibm_helmholtz_solve": (I32, [P, P, D, P, P, D, P, C.POINTER(ibm_helmholtz_opts), C.POINTER(ibm_solve_info), P]),
+        "ibm_boundary_velocity_rigid": (I32, [P, C.POINTER(C.c_double), I32, P, P]),
         "ibm_surface_forces": (I32, [P, C.POINTER(ibm_mesh), I32, P, P, C.POINTER(C.c_double), P, P, P, P]),
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
@@ -236,6 +244,40 @@ def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, strea
     return rep
 
 
+@dataclass
+class HelmholtzOpts:
+    precision: int = 1
+    srj_steps: int = 8
+    max_cycles: int = 100
+
+
+def ibm_helmholtz_solve(ctx, tables, alpha, f, u, ub=None, tol=1e-10, opts: HelmholtzOpts | None = None, stream=None,
+                        history_cap: int = 256, raise_on_error: bool = True):
+    """Advection-diffusion velocity solve in place: f, u CUDA float64 [nz, ny, nx]; ub the
+    boundary values per ghost entry (CUDA float64) or None.  Returns a dict report."""
+    lib = load_library()
+    o = opts or HelmholtzOpts()
+    co = ibm_helmholtz_opts(o.precision, o.srj_steps, o.max_cycles)
+    hist = np.zeros(max(1, history_cap))
+    info = ibm_solve_info(0, 0, 0.0, 0.0, 0.0, hist.ctypes.data, history_cap)
+    s = lib.ibm_helmholtz_solve(ctx, tables, float(alpha), _ptr(f), _ptr(ub), float(tol), _ptr(u), C.byref(co),
+                                C.byref(info), _stream(stream))
+    rep = {"status": STATUS.get(s, s), "cycles": info.cycles, "rel_resid": info.rel_resid, "ms_total": info.ms_total,
+           "history": hist[:info.history_len].copy()}
+    if raise_on_error and s != IBM_OK:
+        raise IbmError(s, "ibm_helmholtz_solve (%s)" % rep)
+    return rep
+
+
+def ibm_boundary_velocity_rigid(tables, motions, ub, stream=None):
+    """Rigid boundary velocity per ghost entry into ub (CUDA float64 (3, nghost)): motions
+    (nmesh x 9: v0, omega, centre)."""
+    m = np.ascontiguousarray(np.asarray(motions, dtype=np.float64).reshape(-1, 9))
+    _check(load_library().ibm_boundary_velocity_rigid(tables, m.ctypes.data_as(C.POINTER(C.c_double)),
+                                                      int(m.shape[0]), _ptr(ub), _stream(stream)),
+           "ibm_boundary_velocity_rigid")
+
+
 def ibm_smoother_sweeps(ctx, tables, precision: int, nsweeps: int, stream=None):
     _check(load_library().ibm_smoother_sweeps(ctx, tables, precision, nsweeps, _stream(stream)), "ibm_smoother_sweeps")
 
@@ -348,6 +390,9 @@ class Tables:
         out["d"] = torch.empty(ng, dtype=torch.float64, device=dev)
         _check(load_library().ibm_tables_export_neumann(self.h, _ptr(out["kappa"]), _ptr(out["tri"]), _ptr(out["d"]),
                                                         _stream(stream)), "ibm_tables_export_neumann")
+        out["wself"] = torch.empty(ng, dtype=torch.float64, device=dev)
+        _check(load_library().ibm_tables_export_self_weight(self.h, _ptr(out["wself"]), _stream(stream)),
+               "ibm_tables_export_self_weight")
         if self.membrane:
             out["cut"] = torch.empty(self.shape, dtype=torch.uint8, device=dev)
             out["cside"] = torch.empty(self.shape, dtype=torch.uint8, device=dev)
@@ -368,6 +413,17 @@ class Tables:
     def neumann_rigid(self, motions, stream=None):
         """Datum from rigid-body kinematics per mesh (a0, alpha, omega, centre)."""
         ibm_neumann_rigid(self.h, motions, stream)
+
+    def helmholtz_solve(self, alpha, f, u, ub=None, tol=1e-10, opts: HelmholtzOpts | None = None, stream=None, **kw):
+        """Advection-diffusion velocity solve (one component) on these tables, in place."""
+        return ibm_helmholtz_solve(self.ctx.h, self.h, alpha, f, u, ub, tol, opts, stream, **kw)
+
+    def boundary_velocity_rigid(self, motions, stream=None):
+        """(3, nghost) CUDA tensor of rigid boundary velocities (motions: nmesh x 9)."""
+        import torch
+        ub = torch.empty((3, max(self.nghost, 1)), dtype=torch.float64, device="cuda")
+        ibm_boundary_velocity_rigid(self.h, motions, ub, stream)
+        return ub[:, :self.nghost]
 
     def surface_forces(self, meshes, p, q=None, motions=None, stream=None) -> dict:
         """Side pressures (ntri, 2), flags (ntri,) and nodal forces (nvert, 3) of the meshes of

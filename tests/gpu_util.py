@@ -35,7 +35,8 @@ def assert_tables_equal(ex, ib, G, bitexact_fp=True):
     assert np.array_equal(ex["flags"], G.flags)
     assert np.array_equal(ex["ref"], G.ref)
     assert np.array_equal(ex["tri"].astype(np.int64), G.tri)
-    for k, o in (("bi", G.bi), ("ip", G.ip), ("w", G.w), ("scale", G.scale), ("kappa", G.kappa)):
+    for k, o in (("bi", G.bi), ("ip", G.ip), ("w", G.w), ("scale", G.scale), ("kappa", G.kappa),
+                 ("wself", G.wself)):
         if bitexact_fp:
             assert np.array_equal(ex[k], o), "%s: max diff %g" % (k, np.max(np.abs(ex[k] - o)) if o.size else 0)
         else:
