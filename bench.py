@@ -218,6 +218,59 @@ def bench_batched(pkg, ctx, torch, st, reps: int = 2):
     return out
 
 
+FP32_HZ_BYTES = 13   # Helmholtz Jacobi sweep, FP32 correction: e 4 + r 4 + mask 1 read, e 4 written
+FP64_HZ_BYTES = 25   # FP64: u 8 + f 8 + mask 1 read, u 8 written
+
+
+def bench_advection_diffusion(pkg, ctx, torch, st, n: int = 256, reps: int = 3):
+    """The fractional step's advection-diffusion solves on the headline grid and body: three
+    velocity components, (I - alpha L) u = f with no-slip ghost rows at the moving ellipsoid
+    (rigid boundary velocity), alpha = dt / (2 Re) with Re = 1000 and dt = 0.5 h_min (unit
+    velocity), each to 1e-10 by scheduled relaxed Jacobi; and the Jacobi sweep kernel alone."""
+    import math
+    import numpy as np
+    import synth
+    pr = synth.cfg2(n)
+    pose = moving_ellipsoid(synth)[0]
+    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pose, stream=st)
+    hmin = float(min(np.min(np.diff(pr.xf)), np.min(np.diff(pr.yf)), np.min(np.diff(pr.zf))))
+    alpha = 0.5 * hmin / (2.0 * 1000.0)
+    motion = np.array([[0.3, -0.1, 0.05, 0.0, 0.0, 2.0 * math.pi * 0.2, 0.5, 0.5, 0.5]])   # v0, omega, centre
+    ub = T.boundary_velocity_rigid(motion, stream=st)
+    fs = [torch.from_numpy(synth.smooth_field(pr.xf, pr.yf, pr.zf, 21 + c)).cuda() for c in range(3)]
+    us = [torch.zeros_like(f) for f in fs]
+    out = {"grid": [n] * 3, "alpha": alpha, "reynolds": 1000, "dt": 0.5 * hmin, "ghosts": T.nghost}
+    N = pr.ncells
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        opts = pkg.HelmholtzOpts(precision=prec)
+        ts, cyc = [], []
+        for r in range(reps + 1):
+            for u in us:
+                u.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            reps_c = [T.helmholtz_solve(alpha, fs[q], us[q], ub[q].contiguous(), TOL, opts, stream=st)
+                      for q in range(3)]
+            c.record(st)
+            c.synchronize()
+            if r > 0:
+                ts.append(a.elapsed_time(c))
+            cyc = [x["cycles"] for x in reps_c]
+        out["three_components_ms_" + name] = statistics.median(ts)
+        out["cycles_" + name] = cyc
+    out["mixed_speedup_vs_fp64"] = out["three_components_ms_fp64"] / out["three_components_ms_mixed"]
+    hbm, src = _peaks()
+    for name, prec, nbytes in (("fp32", 1, FP32_HZ_BYTES), ("fp64", 0, FP64_HZ_BYTES)):
+        ms = pkg.ibm_helmholtz_sweeps_timed(ctx.h, T.h, alpha, prec, 20, fs[0], us[0], st)
+        ach = nbytes * N / (ms * 1e-3) / 1e9
+        out["sweep_kernel_" + name] = {"ms": ms, "gcells_per_s": N / (ms * 1e-3) / 1e9, "achieved_gbs": ach,
+                                       "frac_of_hbm": ach / hbm, "algorithmic_bytes_per_cell": nbytes}
+    out["peak_source"] = src
+    T.close()
+    return out
+
+
 def bench_spheres_1024(pkg, ctx, torch, st):
     """1024^3 uniform grid with 12 random spheres (1.07e9 cells): classification, and the
     solve to 1e-10 in mode 2 and in FP64 once the hierarchy exists (ms), cycles, device
@@ -474,6 +527,8 @@ def run_ours(args):
             "e2e": {"value": ws * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(b_host.nbytes + mesh_bytes), "d2h_bytes_per_step": int(b_host.nbytes)},
             "gpu_launches": launches, "clocks": clk.summary()}
+    if not args.no_ad:
+        line["advection_diffusion"] = bench_advection_diffusion(pkg, ctx, torch, st, args.n)
     if not args.no_batched:
         line["batched_48"] = bench_batched(pkg, ctx, torch, st)
     if not args.no_membrane:
@@ -506,6 +561,7 @@ def main():
     ap.add_argument("--no-membrane", action="store_true")
     ap.add_argument("--no-paper-solver", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-ad", action="store_true")
     ap.add_argument("--membrane-n", type=int, default=512)
     ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")

@@ -242,6 +242,15 @@ ibm_status ibm_helmholtz_solve(ibm_ctx *ctx, ibm_tables *t, double alpha, const 
                                const double *ub_dev, double tol, double *u_dev,
                                const ibm_helmholtz_opts *opts, ibm_solve_info *info, void *stream);
 
+/* Measurement: nsweeps (1..4096) launches of the Helmholtz solve's fine-level Jacobi sweep
+ * kernel alone (precision 0: FP64 on u; 1: FP32 on the correction), after the solve's setup
+ * with f_dev and u_dev (as for ibm_helmholtz_solve; u_dev is not written), each launch
+ * bracketed by CUDA events on `stream`; *kernel_ms = the mean launch duration.  Synchronises
+ * `stream`. */
+ibm_status ibm_helmholtz_sweeps_timed(ibm_ctx *ctx, ibm_tables *t, double alpha, int32_t precision,
+                                      int32_t nsweeps, const double *f_dev, double *u_dev, void *stream,
+                                      double *kernel_ms);
+
 /* Rigid-body boundary velocity of every ghost entry: u_b = v0 + omega x (BI - c) for the mesh
  * holding the entry's closest triangle.  motions (host) double[nmesh * 9]: per mesh in
  * classification order v0 (3), omega (3), c (3); nmesh must equal the classification's mesh

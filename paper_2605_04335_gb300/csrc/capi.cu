@@ -31,9 +31,11 @@ ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st);
 ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st);
 ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_user, const double *ub,
                                 double tol, double *u_user, const ibm_helmholtz_opts *opts, ibm_solve_info *info,
-                                cudaStream_t st);
+                                cudaStream_t st, double *time_ms = nullptr, int n_timed = 0);
 ibm_status boundary_velocity_rigid_impl(ibm_tables *T, const double *motions, int nmesh, double *ub,
                                         cudaStream_t st);
+ibm_status helmholtz_sweeps_timed_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, int precision, int nsweeps,
+                                       const double *f_user, double *u_user, cudaStream_t st, double *ms);
 ibm_status surface_forces_impl(ibm_tables *T, const ibm_mesh *meshes, int nmesh, const double *p,
                                const double *q_tri, const double *motions, double *p_side, uint8_t *flags,
                                double *f_node, cudaStream_t st);
@@ -162,6 +164,14 @@ ibm_status ibm_helmholtz_solve(ibm_ctx *ctx, ibm_tables *t, double alpha, const 
   if (!ctx || !t || t->ctx != ctx) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::helmholtz_solve_impl(ctx, t, alpha, f_dev, ub_dev, tol, u_dev, opts, info, (cudaStream_t)stream);
+}
+
+ibm_status ibm_helmholtz_sweeps_timed(ibm_ctx *ctx, ibm_tables *t, double alpha, int32_t precision, int32_t nsweeps,
+                                      const double *f_dev, double *u_dev, void *stream, double *kernel_ms) {
+  if (!ctx || !t || t->ctx != ctx) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return ibm::helmholtz_sweeps_timed_impl(ctx, t, alpha, precision, nsweeps, f_dev, u_dev, (cudaStream_t)stream,
+                                          kernel_ms);
 }
 
 ibm_status ibm_boundary_velocity_rigid(ibm_tables *t, const double *motions, int32_t nmesh, double *ub_dev,

@@ -16,8 +16,9 @@
 // SRJ cycle: K Jacobi sweeps of the fluid rows with relaxation factors w_k = 1 / lambda_k,
 // lambda_k the Chebyshev nodes of [1 - rho, 1 + rho], rho = alpha S / (1 + alpha S) with S
 // the largest sum of a cell's coefficients: the fluid rows' Jacobi spectrum lies in that
-// interval (diagonal dominance).  After every sweep the ghost rows are re-evaluated from the
-// new fluid values (Jacobi among ghosts).  Precision 0 runs the cycles in FP64; precision 1
+// interval (diagonal dominance); the step divides by D through an FP32 reciprocal (it scales
+// the step only, so the fixed point is unchanged).  After every sweep the ghost rows are
+// re-evaluated from the new fluid values (Jacobi among ghosts).  Precision 0 runs the cycles in FP64; precision 1
 // runs each cycle in FP32 on the correction equation H e = r inside FP64 iterative
 // refinement (r and the update in FP64).  Convergence: ||S r|| / ||S b|| over fluid and
 // ghost rows, S = alpha s_G on ghost rows (s_G the pressure system's row scale), 1 elsewhere.
@@ -49,52 +50,69 @@ struct HzView {
   int nx, ny, nz;
   long long sy, sz;
   const uint8_t *mask;
-  const T *cxm, *cxp, *cym, *cyp, *czm, *czp;   // face coefficients per axis
-  const T *sdx, *sdy, *sdz;                     // their per-axis sums
+  const T *cxm, *cxp, *cym, *cyp, *czm, *czp;   // alpha x the face coefficients, per axis
+  const T *sdx, *sdy, *sdz;                     // alpha x their per-axis sums
 };
 
+// relaxation divisor: 1 / D as an FP32 reciprocal (it scales the Jacobi step only, so the
+// iteration's fixed point does not depend on its rounding)
+template <typename T> __device__ __forceinline__ T relax_rcp(T D);
+template <> __device__ __forceinline__ float relax_rcp<float>(float D) { return __frcp_rn(D); }
+template <> __device__ __forceinline__ double relax_rcp<double>(double D) { return (double)__frcp_rn((float)D); }
+
 // one Jacobi step of the fluid rows with relaxation w: un = u + w (f - H u) / D, each block a
-// 32 x 8 tile marching KCH planes in z with the z-neighbours in registers
+// 32 x 8 tile marching KCH planes in z with the z-neighbours in registers; the next plane's
+// value, mask and right-hand side are loaded one plane ahead
 template <typename T>
-__global__ void __launch_bounds__(TX *TY) k_hz_sweep(HzView<T> v, const T *u, T *un, const T *f, T alpha, T w) {
+__global__ void __launch_bounds__(TX *TY) k_hz_sweep(HzView<T> v, const T *u, T *un, const T *f, T w) {
   const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
   if (i >= v.nx || j >= v.ny) return;
   const int k0 = blockIdx.z * KCH, k1 = min(v.nz, k0 + KCH);
-  long long id = ((long long)(k0 + 1) * (v.ny + 2) + (j + 1)) * v.sy + (i + OX);
-  const T cxm = v.cxm[i], cxp = v.cxp[i], cym = v.cym[j], cyp = v.cyp[j], sxy = v.sdx[i] + v.sdy[j];
-  T zm = u[id - v.sz], zc = u[id];
-  for (int k = k0; k < k1; ++k, id += v.sz) {
-    const T zp = u[id + v.sz];
-    if (v.mask[id] == 0) {
-      T s = cxm * u[id - 1];
-      s += cxp * u[id + 1];
-      s += cym * u[id - v.sy];
-      s += cyp * u[id + v.sy];
-      s += v.czm[k] * zm;
-      s += v.czp[k] * zp;
-      const T D = (T)1 + alpha * (sxy + v.sdz[k]);
-      const T res = f[id] - (D * zc - alpha * s);
-      un[id] = zc + w * res / D;
+  const long long sy = v.sy, sz = v.sz;
+  long long id = ((long long)(k0 + 1) * (v.ny + 2) + (j + 1)) * sy + (i + OX);
+  const T cxm = v.cxm[i], cxp = v.cxp[i], cym = v.cym[j], cyp = v.cyp[j], dxy = (T)1 + (v.sdx[i] + v.sdy[j]);
+  T zm = u[id - sz], zc = u[id], zp = u[id + sz], fc = f[id];
+  uint8_t m = v.mask[id];
+  for (int k = k0; k < k1; ++k, id += sz) {
+    T zpp = 0, fn = 0;
+    uint8_t mn = 1;
+    if (k + 1 < k1) {   // planes k + 2 and k + 3 of the padded array exist when k + 1 < nz
+      zpp = u[id + 2 * sz];
+      fn = f[id + sz];
+      mn = v.mask[id + sz];
     }
+    const T xl = u[id - 1], xr = u[id + 1], yl = u[id - sy], yr = u[id + sy];
+    T s = cxm * xl;
+    s = fma(cxp, xr, s);
+    s = fma(cym, yl, s);
+    s = fma(cyp, yr, s);
+    s = fma(v.czm[k], zm, s);
+    s = fma(v.czp[k], zp, s);
+    const T D = dxy + v.sdz[k];
+    const T res = fma(-D, zc, fc) + s;
+    if (m == 0) un[id] = fma(w * relax_rcp(D), res, zc);
     zm = zc;
     zc = zp;
+    zp = zpp;
+    fc = fn;
+    m = mn;
   }
 }
 
 // the same step at the membrane cut cells (their links read the entries through cut_nb)
 template <typename T>
 __global__ void k_hz_sweep_cut(HzView<T> v, const long long *cut_id, const long long *cut_nb, const int *cut_ijk,
-                               const long long *cnt, const T *u, T *un, const T *f, T alpha, T w) {
+                               const long long *cnt, const T *u, T *un, const T *f, T w) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt[1];
        t += (long long)gridDim.x * blockDim.x) {
     const long long id = cut_id[t];
     const int i = cut_ijk[3 * t], j = cut_ijk[3 * t + 1], k = cut_ijk[3 * t + 2];
     const T c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
     T s = 0;
-    for (int d = 0; d < 6; ++d) s += c[d] * u[cut_nb[6 * t + d]];
-    const T D = (T)1 + alpha * ((v.sdx[i] + v.sdy[j]) + v.sdz[k]);
-    const T res = f[id] - (D * u[id] - alpha * s);
-    un[id] = u[id] + w * res / D;
+    for (int d = 0; d < 6; ++d) s = fma(c[d], u[cut_nb[6 * t + d]], s);
+    const T D = ((T)1 + (v.sdx[i] + v.sdy[j])) + v.sdz[k];
+    const T res = fma(-D, u[id], f[id]) + s;
+    un[id] = fma(w * relax_rcp(D), res, u[id]);
   }
 }
 
@@ -116,10 +134,10 @@ __global__ void k_hz_ghost(const long long *src, const long long *dst, const dou
   un[dst[g]] = (f[dst[g]] - ((T)1 - w) * s) / ((T)1 + w);
 }
 
-// FP64 residual r = b - H u of the regular fluid rows; block partials of sum r^2 (and of
-// sum b^2 when bpart); r32 (if given) receives r in FP32
+// FP64 residual r = b - H u of the regular fluid rows (coefficients pre-scaled by alpha);
+// block partials of sum r^2 (and of sum b^2 when with_b); r32 (if given) receives r in FP32
 __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid(HzView<double> v, const double *u, const double *f,
-                                                         double alpha, float *r32, double *part, bool with_b) {
+                                                         float *r32, double *part, bool with_b) {
   __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
   double ar = 0.0, ab = 0.0;
   const long long rows = (long long)v.ny * v.nz;
@@ -130,14 +148,14 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid(HzView<double> v, const
     for (int i = threadIdx.x; i < v.nx; i += blockDim.x) {
       const long long id = base + i;
       if (v.mask[id] != 0) continue;
-      double s = v.cxm[i] * u[id - 1];
-      s += v.cxp[i] * u[id + 1];
-      s += cym * u[id - v.sy];
-      s += cyp * u[id + v.sy];
-      s += czm * u[id - v.sz];
-      s += czp * u[id + v.sz];
-      const double D = 1.0 + alpha * (v.sdx[i] + syz);
-      const double r = f[id] - (D * u[id] - alpha * s);
+      double acc = v.cxm[i] * u[id - 1];
+      acc = fma(v.cxp[i], u[id + 1], acc);
+      acc = fma(cym, u[id - v.sy], acc);
+      acc = fma(cyp, u[id + v.sy], acc);
+      acc = fma(czm, u[id - v.sz], acc);
+      acc = fma(czp, u[id + v.sz], acc);
+      const double D = 1.0 + (v.sdx[i] + syz);
+      const double r = fma(-D, u[id], f[id]) + acc;
       if (r32) r32[id] = (float)r;
       ar += r * r;
       if (with_b) ab += f[id] * f[id];
@@ -168,10 +186,10 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_rest(
       const long long id = cut_id[t];
       const int i = cut_ijk[3 * t], j = cut_ijk[3 * t + 1], k = cut_ijk[3 * t + 2];
       const double c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
-      double s = 0.0;
-      for (int d = 0; d < 6; ++d) s += c[d] * u[cut_nb[6 * t + d]];
-      const double D = 1.0 + alpha * ((v.sdx[i] + v.sdy[j]) + v.sdz[k]);
-      const double r = f[id] - (D * u[id] - alpha * s);
+      double acc = 0.0;
+      for (int d = 0; d < 6; ++d) acc = fma(c[d], u[cut_nb[6 * t + d]], acc);
+      const double D = 1.0 + ((v.sdx[i] + v.sdy[j]) + v.sdz[k]);
+      const double r = fma(-D, u[id], f[id]) + acc;
       if (r32) r32[id] = (float)r;
       ar += r * r;
       if (with_b) ab += f[id] * f[id];
@@ -249,9 +267,13 @@ __global__ void k_hz_update(double *u, const float *e, long long n) {
     u[q] += (double)e[q];
 }
 
-__global__ void k_to_float(const double *a, long long n, float *b) {
+// alpha x the FP64 coefficients and their sums, in FP64 and FP32
+__global__ void k_scale_coefs(const double *c, long long n, double alpha, double *a64, float *a32) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q < n) b[q] = (float)a[q];
+  if (q >= n) return;
+  const double x = alpha * c[q];
+  a64[q] = x;
+  a32[q] = (float)x;
 }
 
 // rigid boundary velocity of every ghost entry: u_b = v0 + omega x (BI - c) for the mesh of
@@ -293,16 +315,18 @@ double axis_max_sum(const std::vector<double> &f) {
 }
 
 struct HzWork {
-  double *u[2], *f;
-  float *e[2], *r32, *c32;
+  double *u[2], *f, *ac64;   // ac: alpha x coefficients and sums
+  float *e[2], *r32, *ac32;
   double *part, *norms;
 };
 
 }  // namespace
 
+// time_ms non-null: after the setup, time n_timed launches of the sweep kernel alone (CUDA
+// events on st around each launch; mean in *time_ms) instead of solving
 ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_user, const double *ub,
                                 double tol, double *u_user, const ibm_helmholtz_opts *opts, ibm_solve_info *info,
-                                cudaStream_t st) {
+                                cudaStream_t st, double *time_ms = nullptr, int n_timed = 0) {
   const auto t0 = std::chrono::steady_clock::now();
   ibm_helmholtz_opts o;
   ibm_helmholtz_opts_default(&o);
@@ -319,15 +343,15 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   const int nx = G.nx, ny = G.ny, nz = G.nz, na = nx + ny + nz;
   // workspace: u (2), f in FP64; e (2), r in FP32; FP32 coefficients; partials; norms
   const long long want = nslot;
-  const size_t bytes = sizeof(double) * (3 * (size_t)want + 2 * (size_t)HZ_BLOCKS * 2 + 8) +
+  const size_t bytes = sizeof(double) * (3 * (size_t)want + 2 * (size_t)HZ_BLOCKS * 2 + 8 + 3 * (size_t)na) +
                        sizeof(float) * (3 * (size_t)want + 3 * (size_t)na + 64);
-  if (!h->helm_buf || h->helm_n != want) {
+  if (!h->helm_buf || h->helm_n != want + na) {
     if (h->helm_buf) { IBM_TRY(cudaStreamSynchronize(st)); cudaFree(h->helm_buf); }
     h->helm_buf = nullptr;
     h->helm_n = 0;
     IBM_TRY(cudaMalloc(&h->helm_buf, bytes));
     IBM_TRY(cudaMemsetAsync(h->helm_buf, 0, bytes, st));   // halos and inactive cells stay 0
-    h->helm_n = want;
+    h->helm_n = want + na;
   }
   HzWork W;
   {
@@ -335,22 +359,25 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     W.u[0] = d; W.u[1] = d + want; W.f = d + 2 * want;
     W.part = d + 3 * want;
     W.norms = W.part + 2 * 2 * HZ_BLOCKS;
-    float *fl = (float *)(W.norms + 8);
-    W.e[0] = fl; W.e[1] = fl + want; W.r32 = fl + 2 * want; W.c32 = fl + 3 * want;
+    W.ac64 = W.norms + 8;
+    float *fl = (float *)(W.ac64 + 3 * na);
+    W.e[0] = fl; W.e[1] = fl + want; W.r32 = fl + 2 * want; W.ac32 = fl + 3 * want;
   }
-  // views of the finest level: FP64 coefficients of the hierarchy, FP32 copies
-  const double *c64 = h->c64;
-  HzView<double> v64;
-  v64.nx = nx; v64.ny = ny; v64.nz = nz; v64.sy = G.sy; v64.sz = G.sz; v64.mask = L0.mask;
-  v64.cxm = c64; v64.cxp = c64 + nx; v64.cym = c64 + 2 * nx; v64.cyp = v64.cym + ny;
-  v64.czm = v64.cyp + ny; v64.czp = v64.czm + nz;
-  v64.sdx = c64 + 2 * na; v64.sdy = v64.sdx + nx; v64.sdz = v64.sdy + ny;
+  // views of the finest level: alpha x the hierarchy's FP64 coefficients, and FP32 copies
   long long launches = 0;
+  k_scale_coefs<<<nb_of(3 * na, 256), 256, 0, st>>>(h->c64, 3 * na, alpha, W.ac64, W.ac32);
+  ++launches;
+  HzView<double> v64;
+  {
+    const double *c = W.ac64;
+    v64.nx = nx; v64.ny = ny; v64.nz = nz; v64.sy = G.sy; v64.sz = G.sz; v64.mask = L0.mask;
+    v64.cxm = c; v64.cxp = c + nx; v64.cym = c + 2 * nx; v64.cyp = v64.cym + ny;
+    v64.czm = v64.cyp + ny; v64.czp = v64.czm + nz;
+    v64.sdx = c + 2 * na; v64.sdy = v64.sdx + nx; v64.sdz = v64.sdy + ny;
+  }
   HzView<float> v32;
-  if (o.precision == 1) {
-    k_to_float<<<nb_of(3 * na, 256), 256, 0, st>>>(c64, 3 * na, W.c32);
-    ++launches;
-    const float *c = W.c32;
+  {
+    const float *c = W.ac32;
     v32.nx = nx; v32.ny = ny; v32.nz = nz; v32.sy = G.sy; v32.sz = G.sz; v32.mask = L0.mask;
     v32.cxm = c; v32.cxp = c + nx; v32.cym = c + 2 * nx; v32.cyp = v32.cym + ny;
     v32.czm = v32.cyp + ny; v32.czp = v32.czm + nz;
@@ -375,7 +402,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   const int rest_blocks = (int)std::max<long long>(1, std::min<long long>(HZ_BLOCKS, nb_of((cuts ? h->cutcap : 0) + ng, HZ_THREADS)));
   // residual r = b - H u (FP64) with its norm, and the norm of b on the first call
   auto residual = [&](const double *u, float *r32, bool with_b) -> ibm_status {
-    k_hz_resid<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, u, W.f, alpha, r32, W.part, with_b);
+    k_hz_resid<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, u, W.f, r32, W.part, with_b);
     k_hz_resid_rest<<<rest_blocks, HZ_THREADS, 0, st>>>(v64, h->cut_id, h->cut_nb, h->cut_ijk, cuts ? h->d_cnt : nullptr,
                                                         h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng, u, W.f,
                                                         alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
@@ -391,11 +418,11 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     T *b[2] = {buf0, buf1};
     for (int k = 0; k < K; ++k) {
       T *u = b[cur], *un = b[1 - cur];
-      k_hz_sweep<T><<<sweep_grid, sweep_block, 0, st>>>(view, u, un, rhs, (T)alpha, (T)om[k]);
+      k_hz_sweep<T><<<sweep_grid, sweep_block, 0, st>>>(view, u, un, rhs, (T)om[k]);
       ++launches;
       if (cuts) {
         k_hz_sweep_cut<T><<<cut_blocks, 256, 0, st>>>(view, h->cut_id, h->cut_nb, h->cut_ijk, h->d_cnt, u, un, rhs,
-                                                     (T)alpha, (T)om[k]);
+                                                     (T)om[k]);
         ++launches;
       }
       if (ng > 0) {
@@ -406,6 +433,31 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     }
     return cur;
   };
+  if (time_ms) {   // the sweep kernel alone, on the packed field (FP32: the correction arrays)
+    std::vector<cudaEvent_t> ev(2 * (size_t)n_timed);
+    for (auto &e : ev) IBM_TRY(cudaEventCreate(&e));
+    for (int q = 0; q < n_timed; ++q) {
+      IBM_TRY(cudaEventRecord(ev[2 * q], st));
+      if (o.precision == 0)
+        k_hz_sweep<double><<<sweep_grid, sweep_block, 0, st>>>(v64, W.u[q & 1], W.u[1 - (q & 1)], W.f, om[0]);
+      else
+        k_hz_sweep<float><<<sweep_grid, sweep_block, 0, st>>>(v32, W.e[q & 1], W.e[1 - (q & 1)], W.r32,
+                                                              (float)om[0]);
+      IBM_TRY(cudaEventRecord(ev[2 * q + 1], st));
+    }
+    IBM_TRY(cudaGetLastError());
+    IBM_TRY(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (int q = 0; q < n_timed; ++q) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
+      tot += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    *time_ms = tot / std::max(1, n_timed);
+    ctx->launches += launches + n_timed;
+    return IBM_OK;
+  }
   ibm_status ret = IBM_OK;
   int cycles = 0, hist = 0;
   double rel = 0.0;
@@ -450,6 +502,15 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return ret;
+}
+
+ibm_status helmholtz_sweeps_timed_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, int precision, int nsweeps,
+                                       const double *f_user, double *u_user, cudaStream_t st, double *ms) {
+  if (!ms || nsweeps < 1 || nsweeps > 4096) return IBM_ERR_INVALID_ARG;
+  ibm_helmholtz_opts o;
+  ibm_helmholtz_opts_default(&o);
+  o.precision = precision;
+  return helmholtz_solve_impl(ctx, t, alpha, f_user, nullptr, 1.0, u_user, &o, nullptr, st, ms, nsweeps);
 }
 
 ibm_status boundary_velocity_rigid_impl(ibm_tables *T, const double *motions, int nmesh, double *ub,

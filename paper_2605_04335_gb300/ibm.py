@@ -88,6 +88,7 @@ def load_library():
         "ibm_helmholtz_opts_default": (None, [C.POINTER(ibm_helmholtz_opts)]),
         "ibm_helmholtz_solve": (I32, [P, P, D, P, P, D, P, C.POINTER(ibm_helmholtz_opts), C.POINTER(ibm_solve_info), P]),
         "ibm_boundary_velocity_rigid": (I32, [P, C.POINTER(C.c_double), I32, P, P]),
+        "ibm_helmholtz_sweeps_timed": (I32, [P, P, D, I32, I32, P, P, P, C.POINTER(C.c_double)]),
         "ibm_surface_forces": (I32, [P, C.POINTER(ibm_mesh), I32, P, P, C.POINTER(C.c_double), P, P, P, P]),
         "ibm_solve_opts_default": (None, [C.POINTER(ibm_solve_opts)]),
         "poisson_solve": (I32, [P, P, P, D, P, C.POINTER(ibm_solve_opts), C.POINTER(ibm_solve_info), P]),
@@ -267,6 +268,15 @@ def ibm_helmholtz_solve(ctx, tables, alpha, f, u, ub=None, tol=1e-10, opts: Helm
     if raise_on_error and s != IBM_OK:
         raise IbmError(s, "ibm_helmholtz_solve (%s)" % rep)
     return rep
+
+
+def ibm_helmholtz_sweeps_timed(ctx, tables, alpha, precision, nsweeps, f, u, stream=None) -> float:
+    """Mean duration (ms) of one launch of the Helmholtz sweep kernel, CUDA events on `stream`."""
+    ms = C.c_double()
+    _check(load_library().ibm_helmholtz_sweeps_timed(ctx, tables, float(alpha), int(precision), int(nsweeps), _ptr(f),
+                                                     _ptr(u), _stream(stream), C.byref(ms)),
+           "ibm_helmholtz_sweeps_timed")
+    return float(ms.value)
 
 
 def ibm_boundary_velocity_rigid(tables, motions, ub, stream=None):
