@@ -218,8 +218,8 @@ ibm_status ibm_tables_export_self_weight(const ibm_tables *t, double *wself_dev,
  * ghost centre and its image point, to u_b.  alpha = dt nu / 2 for Crank-Nicolson diffusion.
  * Iteration: cycles of srj_steps Jacobi sweeps with the relaxation factors 1 / (Chebyshev
  * nodes of [1 - rho, 1 + rho]), rho = alpha S / (1 + alpha S), S the largest coefficient sum
- * of a cell, the ghost rows re-evaluated after every sweep; precision 1 runs each cycle in
- * FP32 on the correction equation inside FP64 iterative refinement.  Convergence:
+ * of a cell, the ghost rows re-evaluated after every sweep; precisions 1 and 2 run each cycle
+ * in FP32 on the correction equation inside iterative refinement.  Convergence:
  * ||S r|| / ||S b|| <= tol over fluid and ghost rows, S = alpha s_G on ghost rows (s_G the
  * row scale of the pressure system), 1 on fluid rows.
  *   f_dev    double[ncell]   right-hand side on fluid cells (others ignored); not modified.
@@ -232,7 +232,10 @@ ibm_status ibm_tables_export_self_weight(const ibm_tables *t, double *wself_dev,
  * residual grows a millionfold; IBM_ERR_INVALID_ARG for NULL arrays, alpha < 0, tol <= 0 or
  * options out of range.  Synchronises `stream` once per cycle to read the residual. */
 typedef struct {
-  int32_t precision;    /* 0: FP64 cycles; 1: FP32 cycles inside FP64 refinement          [1] */
+  int32_t precision;    /* 0: FP64 cycles; 1: FP32 cycles inside FP64 refinement; 2: as 1
+                           with the refinement loop (u, f, residual, update) in
+                           double-FP32 pairs and error-free transformations on the FP32
+                           pipe, as precision 2 of poisson_solve                      [2] */
   int32_t srj_steps;    /* Jacobi sweeps (relaxation factors) per cycle, 1..64            [8] */
   int32_t max_cycles;   /* cycles (precision 0) or refinement steps (precision 1)       [100] */
 } ibm_helmholtz_opts;

@@ -153,7 +153,7 @@ ibm_status ibm_tables_export_self_weight(const ibm_tables *t, double *wself_dev,
 
 void ibm_helmholtz_opts_default(ibm_helmholtz_opts *o) {
   if (!o) return;
-  o->precision = 1;
+  o->precision = 2;
   o->srj_steps = 8;
   o->max_cycles = 100;
 }

@@ -18,10 +18,11 @@
 // the largest sum of a cell's coefficients: the fluid rows' Jacobi spectrum lies in that
 // interval (diagonal dominance); the step divides by D through an FP32 reciprocal (it scales
 // the step only, so the fixed point is unchanged).  After every sweep the ghost rows are
-// re-evaluated from the new fluid values (Jacobi among ghosts).  Precision 0 runs the cycles in FP64; precision 1
-// runs each cycle in FP32 on the correction equation H e = r inside FP64 iterative
-// refinement (r and the update in FP64).  Convergence: ||S r|| / ||S b|| over fluid and
-// ghost rows, S = alpha s_G on ghost rows (s_G the pressure system's row scale), 1 elsewhere.
+// re-evaluated from the new fluid values (Jacobi among ghosts).  Precision 0 runs the cycles
+// in FP64; precisions 1 and 2 run each cycle in FP32 on the correction equation H e = r
+// inside iterative refinement, whose residual and update are FP64 (1) or double-FP32 pairs
+// with error-free transformations on the FP32 pipe (2).  Convergence: ||S r|| / ||S b|| over
+// fluid and ghost rows, S = alpha s_G on ghost rows (s_G the pressure system's row scale), 1 elsewhere.
 //
 // Layout: the finest level of the FP64 multigrid hierarchy of the tables (padded arrays,
 // mask, ghost sources, membrane entry slots and cut-cell lists) is shared with the pressure
@@ -31,6 +32,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "ibm_internal.cuh"
 
 namespace ibm {
@@ -173,10 +175,23 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid(HzView<double> v, const
 
 // residual of the cut cells and of the ghost rows (scaled by alpha s_G), one block-partial
 // pair per block after the regular rows' partials
+// values of the refinement loop's u and f: FP64 arrays, or double-FP32 pairs (hi + lo)
+struct Fp64Vals {
+  const double *u, *f;
+  __device__ double U(long long q) const { return u[q]; }
+  __device__ double F(long long q) const { return f[q]; }
+};
+struct DfVals {
+  const float *uh, *ul, *fh, *fl;
+  __device__ double U(long long q) const { return dfl::join(uh[q], ul[q]); }
+  __device__ double F(long long q) const { return dfl::join(fh[q], fl[q]); }
+};
+
+template <typename Vals>
 __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_rest(
     HzView<double> v, const long long *cut_id, const long long *cut_nb, const int *cut_ijk, const long long *cnt,
     const long long *src, const long long *dst, const double *gw, const double *ws, const double *gscale,
-    long long ng, const double *u, const double *f, double alpha, float *r32, double *part, bool with_b) {
+    long long ng, Vals x, double alpha, float *r32, double *part, bool with_b) {
   __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
   double ar = 0.0, ab = 0.0;
   const long long ncut = cnt ? cnt[1] : 0;
@@ -187,25 +202,27 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_rest(
       const int i = cut_ijk[3 * t], j = cut_ijk[3 * t + 1], k = cut_ijk[3 * t + 2];
       const double c[6] = {v.cxm[i], v.cxp[i], v.cym[j], v.cyp[j], v.czm[k], v.czp[k]};
       double acc = 0.0;
-      for (int d = 0; d < 6; ++d) acc = fma(c[d], u[cut_nb[6 * t + d]], acc);
+      for (int d = 0; d < 6; ++d) acc = fma(c[d], x.U(cut_nb[6 * t + d]), acc);
       const double D = 1.0 + ((v.sdx[i] + v.sdy[j]) + v.sdz[k]);
-      const double r = fma(-D, u[id], f[id]) + acc;
+      const double fi = x.F(id);
+      const double r = fma(-D, x.U(id), fi) + acc;
       if (r32) r32[id] = (float)r;
       ar += r * r;
-      if (with_b) ab += f[id] * f[id];
+      if (with_b) ab += fi * fi;
     } else {
       const long long g = t - ncut;
       double s = 0.0;
       for (int c = 0; c < 8; ++c) {
         const long long q = src[8 * g + c];
-        if (q >= 0) s += gw[8 * g + c] * u[q & ~GHOST_CORNER];
+        if (q >= 0) s += gw[8 * g + c] * x.U(q & ~GHOST_CORNER);
       }
       const long long id = dst[g];
-      const double r = f[id] - ((1.0 + ws[g]) * u[id] + (1.0 - ws[g]) * s);
+      const double fi = x.F(id);
+      const double r = fi - ((1.0 + ws[g]) * x.U(id) + (1.0 - ws[g]) * s);
       if (r32) r32[id] = (float)r;
       const double sc = alpha * gscale[g];
       ar += (sc * r) * (sc * r);
-      if (with_b) ab += (sc * f[id]) * (sc * f[id]);
+      if (with_b) ab += (sc * fi) * (sc * fi);
     }
   }
   sr[threadIdx.x] = ar;
@@ -231,6 +248,110 @@ __global__ void k_hz_norms(const double *part, int nb, double *out) {
     __syncthreads();
   }
   if (threadIdx.x == 0) { out[0] = sr[0]; out[1] = sb[0]; }
+}
+
+// double-FP32 residual of the regular fluid rows (precision 2): u, f and alpha x the
+// coefficients as hi + lo float pairs, r = f - D u + sum c v by error-free transformations
+// on the FP32 pipe (the residual error is a few units of 2^-48 x sum |c| |v|); r32 receives
+// r; block partials of sum r^2 (and sum f^2 when with_b)
+struct HzDf {
+  const float *ch, *cl;   // alpha x coefficients and sums (layout of HzView), hi and lo parts
+};
+
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  float s, e;
+  dfl::two_sum(ah, bh, s, e);
+  e += al + bl;
+  dfl::fast_two_sum(s, e, sh, sl);
+}
+
+__global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_df(HzView<double> v, HzDf c, const float *uh,
+                                                            const float *ul, const float *fh, const float *fl,
+                                                            float *r32, double *part, bool with_b) {
+  __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
+  const int nx = v.nx, ny = v.ny, nz = v.nz, na = nx + ny + nz;
+  const long long sy = v.sy, sz = v.sz;
+  // coefficient offsets in the layout cxm cxp cym cyp czm czp (2 na) then sdx sdy sdz (na)
+  const float *cxmh = c.ch, *cxml = c.cl, *cxph = c.ch + nx, *cxpl = c.cl + nx;
+  const float *cyh = c.ch + 2 * nx, *cyl = c.cl + 2 * nx, *czh = c.ch + 2 * nx + 2 * ny, *czl = c.cl + 2 * nx + 2 * ny;
+  const float *sdh = c.ch + 2 * na, *sdl = c.cl + 2 * na;
+  float ar = 0.f, ab = 0.f;
+  double dr = 0.0, db = 0.0;
+  const long long rows = (long long)ny * nz;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = (int)(row % ny), k = (int)(row / ny);
+    const long long base = ((long long)(k + 1) * (ny + 2) + (j + 1)) * sy + OX;
+    const float cymh = cyh[j], cyml = cyl[j], cyph = cyh[ny + j], cypl = cyl[ny + j];
+    const float czmh = czh[k], czml = czl[k], czph = czh[nz + k], czpl = czl[nz + k];
+    float dyzh, dyzl, t1h, t1l;
+    df_add(1.0f, 0.0f, sdh[nx + j], sdl[nx + j], t1h, t1l);
+    df_add(t1h, t1l, sdh[nx + ny + k], sdl[nx + ny + k], dyzh, dyzl);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const long long id = base + i;
+      if (v.mask[id] != 0) continue;
+      float Dh, Dl;
+      df_add(dyzh, dyzl, sdh[i], sdl[i], Dh, Dl);
+      float acc_h = fh[id], acc_l = fl[id];
+      dfl::acc_prod(-Dh, -Dl, uh[id], ul[id], acc_h, acc_l);
+      dfl::acc_prod(cxmh[i], cxml[i], uh[id - 1], ul[id - 1], acc_h, acc_l);
+      dfl::acc_prod(cxph[i], cxpl[i], uh[id + 1], ul[id + 1], acc_h, acc_l);
+      dfl::acc_prod(cymh, cyml, uh[id - sy], ul[id - sy], acc_h, acc_l);
+      dfl::acc_prod(cyph, cypl, uh[id + sy], ul[id + sy], acc_h, acc_l);
+      dfl::acc_prod(czmh, czml, uh[id - sz], ul[id - sz], acc_h, acc_l);
+      dfl::acc_prod(czph, czpl, uh[id + sz], ul[id + sz], acc_h, acc_l);
+      const float r = acc_h + acc_l;
+      if (r32) r32[id] = r;
+      ar = fmaf(r, r, ar);
+      if (with_b) { const float b = fh[id] + fl[id]; ab = fmaf(b, b, ab); }
+    }
+    dr += (double)ar;   // per row: the float sums stay short
+    db += (double)ab;
+    ar = ab = 0.f;
+  }
+  sr[threadIdx.x] = dr;
+  sb[threadIdx.x] = db;
+  __syncthreads();
+  for (int st = HZ_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) { sr[threadIdx.x] += sr[threadIdx.x + st]; sb[threadIdx.x] += sb[threadIdx.x + st]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = sr[0]; part[2 * blockIdx.x + 1] = sb[0]; }
+}
+
+// (uh, ul) += e on every slot (double-FP32 update)
+__global__ void k_hz_update_df(float *uh, float *ul, const float *e, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    float s, t;
+    dfl::two_sum(uh[q], e[q], s, t);
+    t += ul[q];
+    dfl::fast_two_sum(s, t, uh[q], ul[q]);
+  }
+}
+
+__global__ void k_hz_pack_df(const double *f, const double *u, long long ncell, int nx, int ny, LevelGeom g,
+                             const uint8_t *mask, float *fh, float *fl, float *uh, float *ul) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= ncell) return;
+  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  const long long id = pidx(g, i, j, k);
+  const uint8_t m = mask[id];
+  dfl::split(fluid_row(m) ? f[l] : 0.0, fh[id], fl[id]);
+  dfl::split((fluid_row(m) || m == 3) ? u[l] : 0.0, uh[id], ul[id]);
+}
+
+__global__ void k_hz_ghost_rhs_df(const long long *dst, const double *ub, long long ng, float *fh, float *fl) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < ng) dfl::split(ub ? 2.0 * ub[g] : 0.0, fh[dst[g]], fl[dst[g]]);
+}
+
+__global__ void k_hz_unpack_df(const float *uh, const float *ul, long long ncell, int nx, int ny, LevelGeom g,
+                               const uint8_t *mask, double *u) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= ncell) return;
+  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  const long long id = pidx(g, i, j, k);
+  const uint8_t m = mask[id];
+  u[l] = (fluid_row(m) || m == 3) ? dfl::join(uh[id], ul[id]) : 0.0;
 }
 
 // user layout -> padded: f on fluid rows (0 elsewhere), u on fluid and ghost cells
@@ -267,13 +388,14 @@ __global__ void k_hz_update(double *u, const float *e, long long n) {
     u[q] += (double)e[q];
 }
 
-// alpha x the FP64 coefficients and their sums, in FP64 and FP32
-__global__ void k_scale_coefs(const double *c, long long n, double alpha, double *a64, float *a32) {
+// alpha x the FP64 coefficients and their sums, in FP64 and as a double-FP32 pair (a32 the
+// high part, the FP32 coefficients of the correction sweeps)
+__global__ void k_scale_coefs(const double *c, long long n, double alpha, double *a64, float *a32, float *a32lo) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= n) return;
   const double x = alpha * c[q];
   a64[q] = x;
-  a32[q] = (float)x;
+  dfl::split(x, a32[q], a32lo[q]);
 }
 
 // rigid boundary velocity of every ghost entry: u_b = v0 + omega x (BI - c) for the mesh of
@@ -316,7 +438,7 @@ double axis_max_sum(const std::vector<double> &f) {
 
 struct HzWork {
   double *u[2], *f, *ac64;   // ac: alpha x coefficients and sums
-  float *e[2], *r32, *ac32;
+  float *e[2], *r32, *ac32, *ac32lo;
   double *part, *norms;
 };
 
@@ -332,7 +454,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   ibm_helmholtz_opts_default(&o);
   if (opts) o = *opts;
   if (!f_user || !u_user || !(alpha >= 0.0) || !std::isfinite(alpha) || !(tol > 0.0) || o.precision < 0 ||
-      o.precision > 1 || o.srj_steps < 1 || o.srj_steps > 64 || o.max_cycles < 1)
+      o.precision > 2 || o.srj_steps < 1 || o.srj_steps > 64 || o.max_cycles < 1)
     return IBM_ERR_INVALID_ARG;
   ibm_status s = build_hierarchy(t, 0, st);
   if (s != IBM_OK) return s;
@@ -344,7 +466,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   // workspace: u (2), f in FP64; e (2), r in FP32; FP32 coefficients; partials; norms
   const long long want = nslot;
   const size_t bytes = sizeof(double) * (3 * (size_t)want + 2 * (size_t)HZ_BLOCKS * 2 + 8 + 3 * (size_t)na) +
-                       sizeof(float) * (3 * (size_t)want + 3 * (size_t)na + 64);
+                       sizeof(float) * (3 * (size_t)want + 6 * (size_t)na + 64);
   if (!h->helm_buf || h->helm_n != want + na) {
     if (h->helm_buf) { IBM_TRY(cudaStreamSynchronize(st)); cudaFree(h->helm_buf); }
     h->helm_buf = nullptr;
@@ -352,6 +474,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     IBM_TRY(cudaMalloc(&h->helm_buf, bytes));
     IBM_TRY(cudaMemsetAsync(h->helm_buf, 0, bytes, st));   // halos and inactive cells stay 0
     h->helm_n = want + na;
+    h->helm_layout = -1;
   }
   HzWork W;
   {
@@ -362,10 +485,11 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     W.ac64 = W.norms + 8;
     float *fl = (float *)(W.ac64 + 3 * na);
     W.e[0] = fl; W.e[1] = fl + want; W.r32 = fl + 2 * want; W.ac32 = fl + 3 * want;
+    W.ac32lo = W.ac32 + 3 * na;
   }
   // views of the finest level: alpha x the hierarchy's FP64 coefficients, and FP32 copies
   long long launches = 0;
-  k_scale_coefs<<<nb_of(3 * na, 256), 256, 0, st>>>(h->c64, 3 * na, alpha, W.ac64, W.ac32);
+  k_scale_coefs<<<nb_of(3 * na, 256), 256, 0, st>>>(h->c64, 3 * na, alpha, W.ac64, W.ac32, W.ac32lo);
   ++launches;
   HzView<double> v64;
   {
@@ -384,10 +508,23 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     v32.sdx = c + 2 * na; v32.sdy = v32.sdx + nx; v32.sdz = v32.sdy + ny;
   }
   // pack f, u and the ghost rows' right-hand sides
-  k_hz_pack<<<nb_of(ncell, 256), 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, W.f, W.u[0]);
+  // precision 2: u and f as double-FP32 pairs in the same bytes (hi parts, then lo parts).
+  // The packs write the cells only; halo and padding slots must read 0 in either view, so
+  // the arrays are cleared whenever the layout changes.
+  const bool df = o.precision == 2;
+  float *uh = (float *)W.u[0], *ul = uh + want, *fh = (float *)W.f, *fl = fh + want;
+  if (h->helm_layout != (df ? 1 : 0)) {
+    IBM_TRY(cudaMemsetAsync(W.u[0], 0, sizeof(double) * 3 * (size_t)want, st));   // u[0], u[1], f
+    h->helm_layout = df ? 1 : 0;
+  }
+  if (df)
+    k_hz_pack_df<<<nb_of(ncell, 256), 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, fh, fl, uh, ul);
+  else
+    k_hz_pack<<<nb_of(ncell, 256), 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, W.f, W.u[0]);
   ++launches;
   if (ng > 0) {
-    k_hz_ghost_rhs<<<nb_of(ng, 128), 128, 0, st>>>(h->gdst, ub, ng, W.f);
+    if (df) k_hz_ghost_rhs_df<<<nb_of(ng, 128), 128, 0, st>>>(h->gdst, ub, ng, fh, fl);
+    else k_hz_ghost_rhs<<<nb_of(ng, 128), 128, 0, st>>>(h->gdst, ub, ng, W.f);
     ++launches;
   }
   const bool cuts = t->membrane && h->cut_id;
@@ -402,10 +539,19 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   const int rest_blocks = (int)std::max<long long>(1, std::min<long long>(HZ_BLOCKS, nb_of((cuts ? h->cutcap : 0) + ng, HZ_THREADS)));
   // residual r = b - H u (FP64) with its norm, and the norm of b on the first call
   auto residual = [&](const double *u, float *r32, bool with_b) -> ibm_status {
-    k_hz_resid<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, u, W.f, r32, W.part, with_b);
-    k_hz_resid_rest<<<rest_blocks, HZ_THREADS, 0, st>>>(v64, h->cut_id, h->cut_nb, h->cut_ijk, cuts ? h->d_cnt : nullptr,
-                                                        h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng, u, W.f,
-                                                        alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
+    const long long *cnt = cuts ? h->d_cnt : nullptr;
+    if (df) {
+      const float *xh = (const float *)u, *xl = xh + want;
+      k_hz_resid_df<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, HzDf{W.ac32, W.ac32lo}, xh, xl, fh, fl, r32, W.part, with_b);
+      k_hz_resid_rest<DfVals><<<rest_blocks, HZ_THREADS, 0, st>>>(
+          v64, h->cut_id, h->cut_nb, h->cut_ijk, cnt, h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng,
+          DfVals{xh, xl, fh, fl}, alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
+    } else {
+      k_hz_resid<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, u, W.f, r32, W.part, with_b);
+      k_hz_resid_rest<Fp64Vals><<<rest_blocks, HZ_THREADS, 0, st>>>(
+          v64, h->cut_id, h->cut_nb, h->cut_ijk, cnt, h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng,
+          Fp64Vals{u, W.f}, alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
+    }
     k_hz_norms<<<1, HZ_THREADS, 0, st>>>(W.part, HZ_BLOCKS + rest_blocks, W.norms);
     launches += 3;
     IBM_TRY(cudaMemcpyAsync(ctx->hscal, W.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -461,11 +607,14 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   ibm_status ret = IBM_OK;
   int cycles = 0, hist = 0;
   double rel = 0.0;
-  if ((s = residual(W.u[0], o.precision == 1 ? W.r32 : nullptr, true)) != IBM_OK) return s;
+  if ((s = residual(W.u[0], o.precision >= 1 ? W.r32 : nullptr, true)) != IBM_OK) return s;
   const double bnorm = std::sqrt(ctx->hscal[1]);
   double r0 = std::sqrt(ctx->hscal[0]);
   int cur = 0;
-  if (bnorm == 0.0) {
+  if (!std::isfinite(bnorm) || !std::isfinite(r0)) {
+    ret = IBM_ERR_DIVERGED;
+    rel = r0 / bnorm;
+  } else if (bnorm == 0.0) {
     IBM_TRY(cudaMemsetAsync(W.u[0], 0, sizeof(double) * want, st));
     rel = 0.0;
   } else {
@@ -478,7 +627,8 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
       } else {
         IBM_TRY(cudaMemsetAsync(W.e[0], 0, sizeof(float) * want, st));
         const int ec = srj_cycle(W.e[0], W.e[1], (const float *)W.r32, v32, 0);
-        k_hz_update<<<1216, 256, 0, st>>>(W.u[cur], W.e[ec], want);
+        if (df) k_hz_update_df<<<1216, 256, 0, st>>>(uh, ul, W.e[ec], want);
+        else k_hz_update<<<1216, 256, 0, st>>>(W.u[cur], W.e[ec], want);
         ++launches;
         if ((s = residual(W.u[cur], W.r32, false)) != IBM_OK) return s;
       }
@@ -489,7 +639,8 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
       if (!std::isfinite(rel) || rn > 1e6 * std::max(r0, bnorm)) { ret = IBM_ERR_DIVERGED; break; }
     }
   }
-  k_hz_unpack<<<nb_of(ncell, 256), 256, 0, st>>>(W.u[cur], ncell, nx, ny, G, L0.mask, u_user);
+  if (df) k_hz_unpack_df<<<nb_of(ncell, 256), 256, 0, st>>>(uh, ul, ncell, nx, ny, G, L0.mask, u_user);
+  else k_hz_unpack<<<nb_of(ncell, 256), 256, 0, st>>>(W.u[cur], ncell, nx, ny, G, L0.mask, u_user);
   ++launches;
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaStreamSynchronize(st));

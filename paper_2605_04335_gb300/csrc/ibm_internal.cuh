@@ -122,6 +122,7 @@ struct Hierarchy {
   long long bicg_n = 0;
   void *helm_buf = nullptr;                 // workspace of the advection-diffusion solve
   long long helm_n = 0;
+  int helm_layout = -1;                     // its u and f arrays hold FP64 (0) or FP32 pairs (1)
   int gcr_m = 0;                            // Krylov directions allocated
   void *gcr_buf = nullptr;                  // 2 gcr_m arrays of nslot elements of T (Z then Q)
   void *gcr_state = nullptr;                // device state of the Krylov acceleration

@@ -247,7 +247,7 @@ def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, strea
 
 @dataclass
 class HelmholtzOpts:
-    precision: int = 1
+    precision: int = 2
     srj_steps: int = 8
     max_cycles: int = 100
 

@@ -1,5 +1,5 @@
 """Advection-diffusion (Helmholtz) velocity solve on the GPU against the oracle: closed bodies
-and membranes, both precisions, after reclassification; the rigid boundary velocity bit for
+and membranes, every precision mode, after reclassification; the rigid boundary velocity bit for
 bit; the 256^3 stretched-grid case by sampled rows; argument errors."""
 import numpy as np
 import pytest
@@ -50,7 +50,7 @@ def test_closed_body_matches_oracle(ctx, aS):
     T = pkg.Tables(c, xf, yf, zf, meshes)
     act = ib != 1                                  # fluid and ghost cells
     fd, ubd = torch.from_numpy(f).cuda(), torch.from_numpy(ub).cuda()
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         u = torch.zeros_like(fd)
         rep = T.helmholtz_solve(alpha, fd, u, ubd, TOL, pkg.HelmholtzOpts(precision=prec))
         ug = u.cpu().numpy()
@@ -79,7 +79,7 @@ def test_membrane_with_rigid_velocity(ctx):
     fd = torch.from_numpy(f).cuda()
     for comp in range(3):
         u_o, _ = OH.solve_membrane(grid, G, alpha, f, ub_o[:, comp])
-        for prec in (0, 1):
+        for prec in (0, 1, 2):
             u = torch.zeros_like(fd)
             rep = T.helmholtz_solve(alpha, fd, u, ub[comp].contiguous(), TOL, pkg.HelmholtzOpts(precision=prec))
             assert rep["status"] == "IBM_OK"
@@ -121,7 +121,7 @@ def test_stretched_256_sampled_rows(ctx):
     fd = torch.from_numpy(f).cuda()
     T = pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes)
     alpha = 0.5 / 1000 * 0.5 / 256                 # dt nu / 2 with dt = 0.5 h, nu = 1 / 1000
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         u = torch.zeros_like(fd)
         rep = T.helmholtz_solve(alpha, fd, u, None, TOL, pkg.HelmholtzOpts(precision=prec))
         assert rep["status"] == "IBM_OK", rep
