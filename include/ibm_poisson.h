@@ -229,8 +229,8 @@ ibm_status ibm_tables_export_self_weight(const ibm_tables *t, double *wself_dev,
  *                            (membranes: every cell is fluid; entry values are internal).
  * Uses the tables' FP64 multigrid hierarchy for its layout (built on first use).  Returns
  * IBM_ERR_NOT_CONVERGED after max_cycles cycles (u = last iterate), IBM_ERR_DIVERGED if the
- * residual grows a millionfold; IBM_ERR_INVALID_ARG for NULL arrays, alpha < 0, tol <= 0 or
- * options out of range.  Synchronises `stream` once per cycle to read the residual. */
+ * residual grows a millionfold or is not finite; IBM_ERR_INVALID_ARG for NULL arrays,
+ * alpha < 0, tol <= 0 or options out of range; IBM_ERR_CAPACITY for ny or nz above 65535.  Synchronises `stream` once per cycle to read the residual. */
 typedef struct {
   int32_t precision;    /* 0: FP64 cycles; 1: FP32 cycles inside FP64 refinement; 2: as 1
                            with the refinement loop (u, f, residual, update) in

@@ -330,9 +330,10 @@ __global__ void k_hz_update_df(float *uh, float *ul, const float *e, long long n
 
 __global__ void k_hz_pack_df(const double *f, const double *u, long long ncell, int nx, int ny, LevelGeom g,
                              const uint8_t *mask, float *fh, float *fl, float *uh, float *ul) {
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= ncell) return;
-  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  // grid: (x blocks, ny, nz); no divisions
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= nx) return;
+  const long long l = ((long long)k * ny + j) * nx + i;
   const long long id = pidx(g, i, j, k);
   const uint8_t m = mask[id];
   dfl::split(fluid_row(m) ? f[l] : 0.0, fh[id], fl[id]);
@@ -346,9 +347,10 @@ __global__ void k_hz_ghost_rhs_df(const long long *dst, const double *ub, long l
 
 __global__ void k_hz_unpack_df(const float *uh, const float *ul, long long ncell, int nx, int ny, LevelGeom g,
                                const uint8_t *mask, double *u) {
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= ncell) return;
-  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  // grid: (x blocks, ny, nz); no divisions
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= nx) return;
+  const long long l = ((long long)k * ny + j) * nx + i;
   const long long id = pidx(g, i, j, k);
   const uint8_t m = mask[id];
   u[l] = (fluid_row(m) || m == 3) ? dfl::join(uh[id], ul[id]) : 0.0;
@@ -357,9 +359,10 @@ __global__ void k_hz_unpack_df(const float *uh, const float *ul, long long ncell
 // user layout -> padded: f on fluid rows (0 elsewhere), u on fluid and ghost cells
 __global__ void k_hz_pack(const double *f, const double *u, long long ncell, int nx, int ny, LevelGeom g,
                           const uint8_t *mask, double *fp, double *up) {
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= ncell) return;
-  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  // grid: (x blocks, ny, nz); no divisions
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= nx) return;
+  const long long l = ((long long)k * ny + j) * nx + i;
   const long long id = pidx(g, i, j, k);
   const uint8_t m = mask[id];
   fp[id] = fluid_row(m) ? f[l] : 0.0;
@@ -374,9 +377,10 @@ __global__ void k_hz_ghost_rhs(const long long *dst, const double *ub, long long
 
 __global__ void k_hz_unpack(const double *up, long long ncell, int nx, int ny, LevelGeom g, const uint8_t *mask,
                             double *u) {
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= ncell) return;
-  const int i = (int)(l % nx), j = (int)((l / nx) % ny), k = (int)(l / ((long long)nx * ny));
+  // grid: (x blocks, ny, nz); no divisions
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= nx) return;
+  const long long l = ((long long)k * ny + j) * nx + i;
   const long long id = pidx(g, i, j, k);
   const uint8_t m = mask[id];
   u[l] = (fluid_row(m) || m == 3) ? up[id] : 0.0;
@@ -456,6 +460,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   if (!f_user || !u_user || !(alpha >= 0.0) || !std::isfinite(alpha) || !(tol > 0.0) || o.precision < 0 ||
       o.precision > 2 || o.srj_steps < 1 || o.srj_steps > 64 || o.max_cycles < 1)
     return IBM_ERR_INVALID_ARG;
+  if (t->ny > 65535 || t->nz > 65535) return IBM_ERR_CAPACITY;   // launch grid rows and planes
   ibm_status s = build_hierarchy(t, 0, st);
   if (s != IBM_OK) return s;
   Hierarchy *h = t->hier[0];
@@ -512,15 +517,16 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   // The packs write the cells only; halo and padding slots must read 0 in either view, so
   // the arrays are cleared whenever the layout changes.
   const bool df = o.precision == 2;
+  const dim3 cell_grid(nb_of(nx, 256), ny, nz);   // pack / unpack: one thread per cell of a row
   float *uh = (float *)W.u[0], *ul = uh + want, *fh = (float *)W.f, *fl = fh + want;
   if (h->helm_layout != (df ? 1 : 0)) {
     IBM_TRY(cudaMemsetAsync(W.u[0], 0, sizeof(double) * 3 * (size_t)want, st));   // u[0], u[1], f
     h->helm_layout = df ? 1 : 0;
   }
   if (df)
-    k_hz_pack_df<<<nb_of(ncell, 256), 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, fh, fl, uh, ul);
+    k_hz_pack_df<<<cell_grid, 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, fh, fl, uh, ul);
   else
-    k_hz_pack<<<nb_of(ncell, 256), 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, W.f, W.u[0]);
+    k_hz_pack<<<cell_grid, 256, 0, st>>>(f_user, u_user, ncell, nx, ny, G, L0.mask, W.f, W.u[0]);
   ++launches;
   if (ng > 0) {
     if (df) k_hz_ghost_rhs_df<<<nb_of(ng, 128), 128, 0, st>>>(h->gdst, ub, ng, fh, fl);
@@ -639,8 +645,8 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
       if (!std::isfinite(rel) || rn > 1e6 * std::max(r0, bnorm)) { ret = IBM_ERR_DIVERGED; break; }
     }
   }
-  if (df) k_hz_unpack_df<<<nb_of(ncell, 256), 256, 0, st>>>(uh, ul, ncell, nx, ny, G, L0.mask, u_user);
-  else k_hz_unpack<<<nb_of(ncell, 256), 256, 0, st>>>(W.u[cur], ncell, nx, ny, G, L0.mask, u_user);
+  if (df) k_hz_unpack_df<<<cell_grid, 256, 0, st>>>(uh, ul, ncell, nx, ny, G, L0.mask, u_user);
+  else k_hz_unpack<<<cell_grid, 256, 0, st>>>(W.u[cur], ncell, nx, ny, G, L0.mask, u_user);
   ++launches;
   IBM_TRY(cudaGetLastError());
   IBM_TRY(cudaStreamSynchronize(st));
