@@ -109,6 +109,19 @@ def _dist():
     return ws, rank, local
 
 
+def whole_job(t_ms_local: float, cells_per_rank: int, ws: int, device=None):
+    """Replicas: the step time is the slowest rank's (max over ranks), and the whole-job value
+    counts every rank's cells: ws x cells / max time (Gcell/s).  With ws > 1 the process group
+    must be initialised (NCCL on GPUs; any backend whose device holds the tensor)."""
+    t_ms = float(t_ms_local)
+    if ws > 1:
+        import torch
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    return t_ms, ws * cells_per_rank / (t_ms * 1e-3) / 1e9
+
+
 def _cpu_sample(n: int):
     """Oracle classify + solve of the workload's geometry on an n^3 grid (host cores)."""
     import numpy as np
@@ -408,12 +421,7 @@ def run_ours(args):
         e1.record(st)
         barrier()
     launches = pkg.ibm_ctx_launch_count(ctx.h) - l0
-    t_ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = ws * N / (t_ms * 1e-3) / 1e9
+    t_ms, value = whole_job(e0.elapsed_time(e1) / args.steps, N, ws, dev)
 
     # classification alone (iblank, ghosts, image points): fresh tables, and reclassification
     # of existing tables (the step's form), median of a few calls each
