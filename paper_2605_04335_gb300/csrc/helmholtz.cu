@@ -235,11 +235,16 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_rest(
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = sr[0]; part[2 * blockIdx.x + 1] = sb[0]; }
 }
 
-// out[0] = sum of the r^2 partials, out[1] = sum of the b^2 partials (fixed order)
-__global__ void k_hz_norms(const double *part, int nb, double *out) {
+// out[0] = sum of the r^2 partials, out[1] = sum of the b^2 partials (fixed order): nreg
+// pairs of the regular rows at part, nrest pairs of the other rows at part + 2 HZ_BLOCKS
+__global__ void k_hz_norms(const double *part, int nreg, int nrest, double *out) {
   __shared__ double sr[HZ_THREADS], sb[HZ_THREADS];
   double ar = 0.0, ab = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) { ar += part[2 * b]; ab += part[2 * b + 1]; }
+  for (int b = threadIdx.x; b < nreg + nrest; b += blockDim.x) {
+    const int q = b < nreg ? b : HZ_BLOCKS + (b - nreg);
+    ar += part[2 * q];
+    ab += part[2 * q + 1];
+  }
   sr[threadIdx.x] = ar;
   sb[threadIdx.x] = ab;
   __syncthreads();
@@ -275,10 +280,13 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_df(HzView<double> v, Hz
   const float *cxmh = c.ch, *cxml = c.cl, *cxph = c.ch + nx, *cxpl = c.cl + nx;
   const float *cyh = c.ch + 2 * nx, *cyl = c.cl + 2 * nx, *czh = c.ch + 2 * nx + 2 * ny, *czl = c.cl + 2 * nx + 2 * ny;
   const float *sdh = c.ch + 2 * na, *sdl = c.cl + 2 * na;
-  float ar = 0.f, ab = 0.f;
   double dr = 0.0, db = 0.0;
-  const long long rows = (long long)ny * nz;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+  // one warp per row, each lane four consecutive cells (16-byte loads: rows start at OX = 4 of
+  // a 16-float pitch, so every group is aligned); the halo and padding masks are non-zero
+  const int lane = threadIdx.x & 31;
+  const long long rows = (long long)ny * nz, wstep = (long long)gridDim.x * (HZ_THREADS / 32);
+  const int ngroups = (nx + 3) / 4;
+  for (long long row = blockIdx.x * (long long)(HZ_THREADS / 32) + (threadIdx.x >> 5); row < rows; row += wstep) {
     const int j = (int)(row % ny), k = (int)(row / ny);
     const long long base = ((long long)(k + 1) * (ny + 2) + (j + 1)) * sy + OX;
     const float cymh = cyh[j], cyml = cyl[j], cyph = cyh[ny + j], cypl = cyl[ny + j];
@@ -286,27 +294,54 @@ __global__ void __launch_bounds__(HZ_THREADS) k_hz_resid_df(HzView<double> v, Hz
     float dyzh, dyzl, t1h, t1l;
     df_add(1.0f, 0.0f, sdh[nx + j], sdl[nx + j], t1h, t1l);
     df_add(t1h, t1l, sdh[nx + ny + k], sdl[nx + ny + k], dyzh, dyzl);
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const long long id = base + i;
-      if (v.mask[id] != 0) continue;
-      float Dh, Dl;
-      df_add(dyzh, dyzl, sdh[i], sdl[i], Dh, Dl);
-      float acc_h = fh[id], acc_l = fl[id];
-      dfl::acc_prod(-Dh, -Dl, uh[id], ul[id], acc_h, acc_l);
-      dfl::acc_prod(cxmh[i], cxml[i], uh[id - 1], ul[id - 1], acc_h, acc_l);
-      dfl::acc_prod(cxph[i], cxpl[i], uh[id + 1], ul[id + 1], acc_h, acc_l);
-      dfl::acc_prod(cymh, cyml, uh[id - sy], ul[id - sy], acc_h, acc_l);
-      dfl::acc_prod(cyph, cypl, uh[id + sy], ul[id + sy], acc_h, acc_l);
-      dfl::acc_prod(czmh, czml, uh[id - sz], ul[id - sz], acc_h, acc_l);
-      dfl::acc_prod(czph, czpl, uh[id + sz], ul[id + sz], acc_h, acc_l);
-      const float r = acc_h + acc_l;
-      if (r32) r32[id] = r;
-      ar = fmaf(r, r, ar);
-      if (with_b) { const float b = fh[id] + fl[id]; ab = fmaf(b, b, ab); }
+    float ar = 0.f, ab = 0.f;
+    for (int g = lane; g < ngroups; g += 32) {
+      const long long id = base + 4 * g;
+      const uchar4 m4 = *reinterpret_cast<const uchar4 *>(v.mask + id);
+      const uint8_t mk[4] = {m4.x, m4.y, m4.z, m4.w};
+      if (mk[0] && mk[1] && mk[2] && mk[3]) continue;
+      const float4 ch4 = *reinterpret_cast<const float4 *>(uh + id), cl4 = *reinterpret_cast<const float4 *>(ul + id);
+      const float4 f4h = *reinterpret_cast<const float4 *>(fh + id), f4l = *reinterpret_cast<const float4 *>(fl + id);
+      const float Ch[6] = {uh[id - 1], ch4.x, ch4.y, ch4.z, ch4.w, uh[id + 4]};
+      const float Cl[6] = {ul[id - 1], cl4.x, cl4.y, cl4.z, cl4.w, ul[id + 4]};
+      const float Fh[4] = {f4h.x, f4h.y, f4h.z, f4h.w}, Fl[4] = {f4l.x, f4l.y, f4l.z, f4l.w};
+      float R[4];
+      // neighbours in y and z, one pair of 16-byte loads each, consumed one at a time
+      float acc_h[4], acc_l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { acc_h[q] = Fh[q]; acc_l[q] = Fl[q]; }
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) {
+        const long long off = nb == 0 ? -sy : (nb == 1 ? sy : (nb == 2 ? -sz : sz));
+        const float4 h4 = *reinterpret_cast<const float4 *>(uh + id + off);
+        const float4 l4 = *reinterpret_cast<const float4 *>(ul + id + off);
+        const float H[4] = {h4.x, h4.y, h4.z, h4.w}, L[4] = {l4.x, l4.y, l4.z, l4.w};
+        const float cH = nb == 0 ? cymh : (nb == 1 ? cyph : (nb == 2 ? czmh : czph));
+        const float cL = nb == 0 ? cyml : (nb == 1 ? cypl : (nb == 2 ? czml : czpl));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dfl::acc_prod(cH, cL, H[q], L[q], acc_h[q], acc_l[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = min(4 * g + q, nx - 1);
+        float Dh, Dl;
+        df_add(dyzh, dyzl, sdh[i], sdl[i], Dh, Dl);
+        dfl::acc_prod(-Dh, -Dl, Ch[q + 1], Cl[q + 1], acc_h[q], acc_l[q]);
+        dfl::acc_prod(cxmh[i], cxml[i], Ch[q], Cl[q], acc_h[q], acc_l[q]);
+        dfl::acc_prod(cxph[i], cxpl[i], Ch[q + 2], Cl[q + 2], acc_h[q], acc_l[q]);
+        R[q] = acc_h[q] + acc_l[q];
+        if (mk[q] == 0) {
+          ar = fmaf(R[q], R[q], ar);
+          if (with_b) { const float b = Fh[q] + Fl[q]; ab = fmaf(b, b, ab); }
+        }
+      }
+      if (r32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (mk[q] == 0) r32[id + q] = R[q];
     }
-    dr += (double)ar;   // per row: the float sums stay short
-    db += (double)ab;
-    ar = ab = 0.f;
+    dr += dfl::widen(ar);   // per row: the float sums of a lane's few groups
+    if (with_b) db += dfl::widen(ab);
   }
   sr[threadIdx.x] = dr;
   sb[threadIdx.x] = db;
@@ -470,8 +505,9 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   const int nx = G.nx, ny = G.ny, nz = G.nz, na = nx + ny + nz;
   // workspace: u (2), f in FP64; e (2), r in FP32; FP32 coefficients; partials; norms
   const long long want = nslot;
-  const size_t bytes = sizeof(double) * (3 * (size_t)want + 2 * (size_t)HZ_BLOCKS * 2 + 8 + 3 * (size_t)na) +
-                       sizeof(float) * (3 * (size_t)want + 6 * (size_t)na + 64);
+  const size_t na3 = ((3 * (size_t)na + 31) / 32) * 32;   // keeps the FP32 arrays 256-byte aligned
+  const size_t bytes = sizeof(double) * (3 * (size_t)want + 2 * (size_t)HZ_BLOCKS * 2 + 8 + na3) +
+                       sizeof(float) * (3 * (size_t)want + 2 * na3 + 64);
   if (!h->helm_buf || h->helm_n != want + na) {
     if (h->helm_buf) { IBM_TRY(cudaStreamSynchronize(st)); cudaFree(h->helm_buf); }
     h->helm_buf = nullptr;
@@ -488,9 +524,9 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     W.part = d + 3 * want;
     W.norms = W.part + 2 * 2 * HZ_BLOCKS;
     W.ac64 = W.norms + 8;
-    float *fl = (float *)(W.ac64 + 3 * na);
+    float *fl = (float *)(W.ac64 + na3);
     W.e[0] = fl; W.e[1] = fl + want; W.r32 = fl + 2 * want; W.ac32 = fl + 3 * want;
-    W.ac32lo = W.ac32 + 3 * na;
+    W.ac32lo = W.ac32 + na3;
   }
   // views of the finest level: alpha x the hierarchy's FP64 coefficients, and FP32 copies
   long long launches = 0;
@@ -543,12 +579,14 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
   for (int k = 0; k < K; ++k) om[k] = 1.0 / (1.0 + rho * std::cos(3.141592653589793 * (2.0 * k + 1.0) / (2.0 * K)));
   const dim3 sweep_grid(nb_of(nx, TX), nb_of(ny, TY), nb_of(nz, KCH)), sweep_block(TX, TY);
   const int rest_blocks = (int)std::max<long long>(1, std::min<long long>(HZ_BLOCKS, nb_of((cuts ? h->cutcap : 0) + ng, HZ_THREADS)));
+  // the double-FP32 residual keeps 80 registers: three resident blocks per SM, one wave
+  const int df_blocks = std::max(1, std::min(HZ_BLOCKS, 3 * std::max(1, ctx->sm_count)));
   // residual r = b - H u (FP64) with its norm, and the norm of b on the first call
   auto residual = [&](const double *u, float *r32, bool with_b) -> ibm_status {
     const long long *cnt = cuts ? h->d_cnt : nullptr;
     if (df) {
       const float *xh = (const float *)u, *xl = xh + want;
-      k_hz_resid_df<<<HZ_BLOCKS, HZ_THREADS, 0, st>>>(v64, HzDf{W.ac32, W.ac32lo}, xh, xl, fh, fl, r32, W.part, with_b);
+      k_hz_resid_df<<<df_blocks, HZ_THREADS, 0, st>>>(v64, HzDf{W.ac32, W.ac32lo}, xh, xl, fh, fl, r32, W.part, with_b);
       k_hz_resid_rest<DfVals><<<rest_blocks, HZ_THREADS, 0, st>>>(
           v64, h->cut_id, h->cut_nb, h->cut_ijk, cnt, h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng,
           DfVals{xh, xl, fh, fl}, alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
@@ -558,7 +596,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
           v64, h->cut_id, h->cut_nb, h->cut_ijk, cnt, h->gsrc, h->gdst, t->gw, t->gwself, t->gscale, ng,
           Fp64Vals{u, W.f}, alpha, r32, W.part + 2 * HZ_BLOCKS, with_b);
     }
-    k_hz_norms<<<1, HZ_THREADS, 0, st>>>(W.part, HZ_BLOCKS + rest_blocks, W.norms);
+    k_hz_norms<<<1, HZ_THREADS, 0, st>>>(W.part, df ? df_blocks : HZ_BLOCKS, rest_blocks, W.norms);
     launches += 3;
     IBM_TRY(cudaMemcpyAsync(ctx->hscal, W.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IBM_TRY(cudaStreamSynchronize(st));
