@@ -1147,7 +1147,7 @@ __global__ void k_split_df(const double *src, int n, float *h, float *l) {
 
 // r = b - lambda - A p on fluid rows with pairs of floats (see dfloat.cuh); FP32 copy of r
 // (0 on other cells); block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}] as
-// k_residual64.  ph == nullptr: residual of p = 0.
+// k_residual64, for b < REDUCE_BLOCKS whatever the grid.  ph == nullptr: residual of p = 0.
 __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const float *ph, const float *pl,
                                                                const float *bh, const float *bl,
                                                                const double *lambda, float *r32, double *partials) {
@@ -1178,38 +1178,48 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const 
         float BH[4], BL[4];
         Vec4<float>::ld(bh + id, BH);
         Vec4<float>::ld(bl + id, BL);
-        float PH[4], PL[4], YMH[4], YML[4], YPH[4], YPL[4], ZMH[4], ZML[4], ZPH[4], ZPL[4];
-        float xlh = 0.f, xll = 0.f, xrh = 0.f, xrl = 0.f;
+        // per cell the terms accumulate in the order b - lambda, diagonal, x-, x+, y-, y+, z-,
+        // z+; the y and z neighbour rows are loaded one pair at a time (fewer live registers)
+        float sh[4], sl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dfl::two_sum(BH[u], -lh, sh[u], sl[u]);
+          sl[u] += BL[u] - ll;
+        }
         if (ph) {
-          Vec4<float>::ld(ph + id, PH);          Vec4<float>::ld(pl + id, PL);
-          Vec4<float>::ld(ph + id - v.sy, YMH);  Vec4<float>::ld(pl + id - v.sy, YML);
-          Vec4<float>::ld(ph + id + v.sy, YPH);  Vec4<float>::ld(pl + id + v.sy, YPL);
-          Vec4<float>::ld(ph + id - v.sz, ZMH);  Vec4<float>::ld(pl + id - v.sz, ZML);
-          Vec4<float>::ld(ph + id + v.sz, ZPH);  Vec4<float>::ld(pl + id + v.sz, ZPL);
-          xlh = ph[id - 1]; xll = pl[id - 1]; xrh = ph[id + 4]; xrl = pl[id + 4];
+          float PH[4], PL[4];
+          Vec4<float>::ld(ph + id, PH);
+          Vec4<float>::ld(pl + id, PL);
+          const float xlh = ph[id - 1], xll = pl[id - 1], xrh = ph[id + 4], xrl = pl[id + 4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = min(4 * g + u, nx - 1);   // coefficients of cells past nx: any valid index
+            float dh, dl;   // diagonal sdx_i + sdy_j + sdz_k
+            dfl::two_sum(H[2 * n + i], syh, dh, dl);
+            dl += L[2 * n + i] + syl;
+            dfl::acc_prod(dh, dl, PH[u], PL[u], sh[u], sl[u]);
+            const float lfh = u == 0 ? xlh : PH[u - 1], lfl = u == 0 ? xll : PL[u - 1];
+            const float rgh = u == 3 ? xrh : PH[u + 1], rgl = u == 3 ? xrl : PL[u + 1];
+            dfl::acc_prod(-H[i], -L[i], lfh, lfl, sh[u], sl[u]);
+            dfl::acc_prod(-H[nx + i], -L[nx + i], rgh, rgl, sh[u], sl[u]);
+          }
+#pragma unroll
+          for (int nb = 0; nb < 4; ++nb) {
+            const long long off = nb == 0 ? -v.sy : (nb == 1 ? v.sy : (nb == 2 ? -v.sz : v.sz));
+            const float ch = nb == 0 ? cymh : (nb == 1 ? cyph : (nb == 2 ? czmh : czph));
+            const float cl = nb == 0 ? cyml : (nb == 1 ? cypl : (nb == 2 ? czml : czpl));
+            float NH[4], NL[4];
+            Vec4<float>::ld(ph + id + off, NH);
+            Vec4<float>::ld(pl + id + off, NL);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dfl::acc_prod(-ch, -cl, NH[u], NL[u], sh[u], sl[u]);
+          }
         }
         float rf[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = min(4 * g + u, nx - 1);   // coefficients of cells past nx: any valid index
-          float sh, sl;
-          dfl::two_sum(BH[u], -lh, sh, sl);
-          sl += BL[u] - ll;
-          if (ph) {
-            float dh, dl;   // diagonal sdx_i + sdy_j + sdz_k
-            dfl::two_sum(H[2 * n + i], syh, dh, dl);
-            dl += L[2 * n + i] + syl;
-            dfl::acc_prod(dh, dl, PH[u], PL[u], sh, sl);
-            const float lfh = u == 0 ? xlh : PH[u - 1], lfl = u == 0 ? xll : PL[u - 1];
-            const float rgh = u == 3 ? xrh : PH[u + 1], rgl = u == 3 ? xrl : PL[u + 1];
-            dfl::acc_prod(-H[i], -L[i], lfh, lfl, sh, sl);
-            dfl::acc_prod(-H[nx + i], -L[nx + i], rgh, rgl, sh, sl);
-            dfl::acc_prod(-cymh, -cyml, YMH[u], YML[u], sh, sl);
-            dfl::acc_prod(-cyph, -cypl, YPH[u], YPL[u], sh, sl);
-            dfl::acc_prod(-czmh, -czml, ZMH[u], ZML[u], sh, sl);
-            dfl::acc_prod(-czph, -czpl, ZPH[u], ZPL[u], sh, sl);
-          }
-          rf[u] = fl[u] ? sh + sl : 0.f;
+          const int i = min(4 * g + u, nx - 1);
+          rf[u] = fl[u] ? sh[u] + sl[u] : 0.f;
           a0 = fmaf(H[3 * n + i] * dydz, rf[u], a0);
           a1 += rf[u];
           a2 = fmaf(rf[u], rf[u], a2);
@@ -1225,6 +1235,10 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const 
     }
   A0 += a0; A1 += a1; A2 += a2;
   block_partials3(A0, A1, A2, partials);
+  // launched as one wave of fewer than REDUCE_BLOCKS blocks: the other slots read zero
+  if (threadIdx.x == 0)
+    for (int b = blockIdx.x + gridDim.x; b < REDUCE_BLOCKS; b += gridDim.x)
+      for (int q = 0; q < 3; ++q) partials[3 * b + q] = 0.0;
 }
 
 // ghost rows r_G = sum w v - g in FP64 from the split values; block partials of (s_G r_G)^2
@@ -2605,8 +2619,10 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
   const long long ntot = h->nslot;   // hi/lo split point of the outer arrays
   double *part = S.part;
   float *ph = with_p ? hi_of(h->p64) : nullptr, *pl = lo_of(h->p64, ntot);
-  k_residual_df<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(fine_view_df(h), ph, pl, hi_of(h->b64),
-                                                           lo_of(h->b64, ntot), S.scal + S_LAMBDA, r32, part);
+  // 80 registers: three resident blocks per SM, so one wave of 3 x SMs blocks
+  const int rdf_blocks = std::min(REDUCE_BLOCKS, 3 * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152));
+  k_residual_df<<<rdf_blocks, REDUCE_THREADS, 0, S.st>>>(fine_view_df(h), ph, pl, hi_of(h->b64),
+                                                         lo_of(h->b64, ntot), S.scal + S_LAMBDA, r32, part);
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
