@@ -37,7 +37,7 @@ FP32_SWEEP_BYTES = 13.0    # read e 4 + rhs 4 + mask 1, write e 4 per cell and f
 FP64_SWEEP_BYTES = 25.0    # read p 8 + b 8 + mask 1, write p 8
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_zmarch launch on the 256^3 grid,
 # from one ncu --set full capture of the current kernel
-SWEEP_TRAFFIC_BYTES = 180149760 + 40821248
+SWEEP_TRAFFIC_BYTES = 180176640 + 40386048   # dram read + write of one launch, ncu --set full (profiles/)
 
 
 def _peaks():
