@@ -285,6 +285,53 @@ def bench_advection_diffusion(pkg, ctx, torch, st, n: int = 256, reps: int = 3):
     return out
 
 
+def bench_paper_shape(pkg, ctx, torch, st, reps: int = 3):
+    """The paper's weak-scaling subdomain shape, 301 x 385 x 129 cells, stretched, around the
+    ellipsoid: classification, the pressure solve to 1e-10 in each precision mode, and the three
+    advection-diffusion solves (mode 2), ms (median)."""
+    import numpy as np
+    import synth
+    pr = synth.cfg_paper_shape()
+    rhs = torch.from_numpy(pr.rhs()).cuda()
+    p = torch.zeros_like(rhs)
+    out = {"grid": [len(pr.xf) - 1, len(pr.yf) - 1, len(pr.zf) - 1], "cells": pr.ncells}
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            r = fn()
+            c.record(st)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        return statistics.median(ts[1:]), r
+
+    out["classify_ms"], T = timed(lambda: pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st))
+    out["ghosts"] = T.nghost
+    for name, prec in (("mixed_df", 2), ("mixed", 1), ("fp64", 0)):
+        def solve():
+            p.zero_()
+            return T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)
+        out["solve_ms_" + name], rep = timed(solve)
+        out["cycles_" + name] = rep["cycles"]
+    out["gcells_per_s_mixed_df"] = pr.ncells / (out["solve_ms_mixed_df"] * 1e-3) / 1e9
+    hmin = float(min(np.min(np.diff(pr.xf)), np.min(np.diff(pr.yf)), np.min(np.diff(pr.zf))))
+    alpha = 0.5 * hmin / (2.0 * 1000.0)
+    fs = [torch.from_numpy(synth.smooth_field(pr.xf, pr.yf, pr.zf, 31 + q)).cuda() for q in range(3)]
+    us = [torch.zeros_like(f) for f in fs]
+
+    def ad():
+        for u in us:
+            u.zero_()
+        return [T.helmholtz_solve(alpha, fs[q], us[q], None, TOL, stream=st) for q in range(3)]
+    out["advection_diffusion_ms"], reps_ad = timed(ad)
+    out["advection_diffusion_cycles"] = [r["cycles"] for r in reps_ad]
+    T.close()
+    return out
+
+
 def bench_spheres_1024(pkg, ctx, torch, st):
     """1024^3 uniform grid with 12 random spheres (1.07e9 cells): classification, and the
     solve to 1e-10 in mode 2 and in FP64 once the hierarchy exists (ms), cycles, device
@@ -542,6 +589,8 @@ def run_ours(args):
         line["batched_48"] = bench_batched(pkg, ctx, torch, st)
     if not args.no_membrane:
         line["membrane_plate"] = bench_membrane(pkg, ctx, torch, st, args.membrane_n)
+    if not args.no_paper_shape:
+        line["paper_shape_301x385x129"] = bench_paper_shape(pkg, ctx, torch, st)
     if not args.no_large:
         line["spheres_1024"] = bench_spheres_1024(pkg, ctx, torch, st)
     if not args.no_cpu:
@@ -571,6 +620,7 @@ def main():
     ap.add_argument("--no-paper-solver", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-ad", action="store_true")
+    ap.add_argument("--no-paper-shape", action="store_true")
     ap.add_argument("--membrane-n", type=int, default=512)
     ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")

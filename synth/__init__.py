@@ -331,6 +331,16 @@ def cfg2(n: int = 256, ratio: float = 2.0) -> Problem:
                    [ellipsoid(5, (0.2, 0.08, 0.08), 20.0, (0.5, 0.5, 0.5))], 2)
 
 
+def cfg_paper_shape(ratio: float = 2.0) -> Problem:
+    """The paper's weak-scaling subdomain shape, 301 x 385 x 129 cells (about 15M). The box's
+    extents are proportional to the cell counts, [0, 301/385] x [0, 1] x [0, 129/385], so the
+    cells are as isotropic as the paper's grid near the body; the same tanh stretching on every
+    axis; the 8192-triangle ellipsoid of cfg2 at the box centre; right-hand side seed 6."""
+    sx, sz = 301.0 / 385.0, 129.0 / 385.0
+    return Problem("ellipsoid_301x385x129_stretched", sx * faces_tanh(301, ratio), faces_tanh(385, ratio),
+                   sz * faces_tanh(129, ratio), [ellipsoid(5, (0.2, 0.08, 0.08), 20.0, (0.5 * sx, 0.5, 0.5 * sz))], 6)
+
+
 def cfg3(n: int = 512, phase: int = 0, nphase: int = 8, ratio: float = 2.0) -> Problem:
     f = faces_tanh(n, ratio)
     return Problem("plate512_stretched_phase%d" % phase, f, f.copy(), f.copy(),

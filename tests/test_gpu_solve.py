@@ -98,6 +98,31 @@ def test_cfg2_full_256_residual_property(ctx):
     T.close()
 
 
+def test_paper_shape_301x385x129_residual_property(ctx):
+    """The paper's weak-scaling subdomain shape (odd, ragged against every tile size): the
+    oracle's residual of the GPU's p in every precision mode, and the modes against each
+    other."""
+    pkg, c = ctx
+    pr = synth.cfg_paper_shape()
+    g = Grid(pr.xf, pr.yf, pr.zf)
+    ib, G = OC.classify(g, pr.meshes)
+    b = pr.rhs()
+    T = pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes)
+    ex = T.export()
+    assert np.array_equal(ex["iblank"].cpu().numpy(), ib)
+    assert np.array_equal(ex["cell"].cpu().numpy(), G.cell)
+    ps = {}
+    for prec in (0, 1, 2):
+        p, rep = _solve_gpu(pkg, T, b, prec)
+        assert rep["status"] == "IBM_OK"
+        assert OSys.relative_residual(g, ib, G, b, p) <= 1.05 * TOL
+        ps[prec] = p
+    fl = ib == 0
+    for prec in (1, 2):
+        assert np.linalg.norm((ps[0] - ps[prec])[fl]) / np.linalg.norm(ps[0][fl]) <= PARITY
+    T.close()
+
+
 def test_warm_start_and_not_converged(ctx):
     pkg, c = ctx
     f = synth.faces_uniform(20)
