@@ -336,7 +336,8 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
 
 /* Autotuner: times complete solves of the given problem (rhs_dev, tol) with candidate
  * smoother schedules -- over-relaxation 1.2/1.3/1.4, sweeps (1,1)/(2,1)/(2,2) and, for
- * precision 1 or 2, 1/2/3 FP32 V-cycles per refinement step -- and returns the fastest in *best
+ * precision 1 or 2, 1/2/3 FP32 V-cycles per refinement step; Krylov acceleration none or
+ * GCR(2), and GCR(8) on membrane tables -- and returns the fastest in *best
  * (its time in *best_ms, optional).  p_work_dev (double[ncell], device) is overwritten.
  * Use the result for poisson_solve / poisson_solve_batched of similar problems. */
 ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, const double *rhs_dev,
