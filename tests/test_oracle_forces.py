@@ -164,3 +164,19 @@ def test_rigid_datum_against_second_differences():
     acc = (cp - 2.0 * c0 + cm) / (dt * dt)
     q = OF.rigid_q(c0, n, [0, T.shape[0]], synth.plate_motion(t))
     assert np.allclose(q, -np.einsum("ij,ij->i", acc, n), rtol=1e-5, atol=1e-5 * np.abs(acc).max())
+
+
+def test_zero_area_triangle_is_flagged_and_carries_no_force():
+    """A degenerate (zero-area) triangle appended to a membrane: flag bit 2, side pressures 0,
+    and every nodal force equal to the mesh without it."""
+    grid = Grid(synth.faces_tanh(24, 2.0), synth.faces_uniform(22), synth.faces_uniform(23))
+    mesh = _tilted_plate()
+    V = np.concatenate([mesh.verts, mesh.verts[:1] + 0.01])
+    T = np.concatenate([mesh.tris, [[0, 0, V.shape[0] - 1]]]).astype(np.int32)
+    deg = synth.Mesh(V, T, 0)
+    p = synth.smooth_field(grid.xf, grid.yf, grid.zf, 4)
+    ps, flags, F = OF.surface_forces(grid, None, [mesh], p)
+    ps2, flags2, F2 = OF.surface_forces(grid, None, [deg], p)
+    assert flags2[-1] == OF.FLAG_ZERO_AREA and np.all(ps2[-1] == 0.0)
+    assert np.array_equal(flags2[:-1], flags) and np.array_equal(ps2[:-1], ps)
+    assert np.array_equal(F2[:-1], F) and np.all(F2[-1] == 0.0)

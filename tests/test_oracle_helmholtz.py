@@ -139,3 +139,20 @@ def test_rigid_velocity_against_finite_differences():
     M = np.repeat(synth.plate_velocity(t)[None], m0.verts.shape[0], axis=0)
     ub = OH.point_velocity(m0.verts, M)
     assert np.allclose(ub, v, rtol=1e-7, atol=1e-7 * np.abs(v).max())
+
+
+def test_alpha_zero_is_the_identity_on_fluid_rows():
+    """alpha = 0: the fluid rows decouple, u = f there; the ghost rows still hold the boundary
+    condition (1 + w_s) u_G + (1 - w_s) sum w v = 2 u_b."""
+    f = synth.faces_tanh(16, 2.0)
+    grid = Grid(f, f, f)
+    ib, G = OC.classify(grid, [synth.octa_sphere(3, (0.5, 0.5, 0.5), 0.25)])
+    rhs = synth.counter_normal(8, 0, np.arange(16 ** 3)).reshape(grid.shape)
+    ub = synth.counter_normal(9, 0, np.arange(len(G)))
+    u = OH.solve_closed(grid, ib, G, 0.0, rhs, ub)
+    fl = ib == 0
+    assert np.array_equal(u[fl], rhs[fl])
+    uf = u.ravel()
+    s = np.sum(np.where(G.ref >= 0, G.w * uf[np.maximum(G.ref, 0)], 0.0), axis=1)
+    lhs = (1.0 + G.wself) * uf[G.cell] + (1.0 - G.wself) * s
+    assert np.max(np.abs(lhs - 2.0 * ub)) < 1e-12
