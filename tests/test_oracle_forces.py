@@ -180,3 +180,27 @@ def test_zero_area_triangle_is_flagged_and_carries_no_force():
     assert flags2[-1] == OF.FLAG_ZERO_AREA and np.all(ps2[-1] == 0.0)
     assert np.array_equal(flags2[:-1], flags) and np.array_equal(ps2[:-1], ps)
     assert np.array_equal(F2[:-1], F) and np.all(F2[-1] == 0.0)
+
+
+def test_tilted_plate_linear_fields_each_side():
+    """A tilted plate with p = a1 + g1.x above and a2 + g2.x below its plane (common normal
+    derivative q = g.n): every probe box lies on its own side, so both side pressures equal the
+    fields at the centroids (the plane test, the probe offset and the datum together)."""
+    grid = Grid(synth.faces_tanh(30, 2.0), synth.faces_uniform(27), synth.faces_tanh(29, 1.5))
+    mesh = _tilted_plate()
+    V, T = mesh.verts, mesh.tris.astype(np.int64)
+    N, a2, n, c = OF.triangle_geometry(V, T)
+    nhat = n[0]
+    P0 = V.mean(axis=0)
+    q0 = 0.6
+    t1, t2 = np.cross(nhat, [1.0, 0.0, 0.0]), np.cross(nhat, [0.0, 1.0, 0.0])
+    g1 = q0 * nhat + 0.8 * t1 - 0.3 * t2
+    g2 = q0 * nhat - 0.5 * t1 + 1.1 * t2
+    X = _cells(grid)
+    above = (X - P0) @ nhat > 0.0
+    p = np.where(above, 1.5 + X @ g1, -0.25 + X @ g2).reshape(grid.shape)
+    ps, flags, F = OF.surface_forces(grid, None, [mesh], p, q=n @ g1)
+    assert np.all(flags == 0)
+    assert np.allclose(n @ g1, n @ g2, atol=1e-14)
+    assert np.max(np.abs(ps[:, 0] - (1.5 + c @ g1))) < 1e-12
+    assert np.max(np.abs(ps[:, 1] - (-0.25 + c @ g2))) < 1e-12
