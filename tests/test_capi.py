@@ -44,3 +44,29 @@ def test_ctx_create_rejects_bad_device_without_gpu():
     h = ctypes.c_void_p()
     s = lib.ibm_ctx_create(ctypes.byref(h), -1)
     assert s != 0
+
+
+def test_null_handles_are_rejected_before_any_device_call():
+    """Every entry point that takes tables or a context returns IBM_ERR_INVALID_ARG for a NULL
+    handle, on the host, without touching a device."""
+    import paper_2605_04335_gb300 as pkg
+    lib = pkg.load_library()
+    INVALID = 1
+    assert lib.ibm_surface_forces(None, None, 0, None, None, None, None, None, None, None) == INVALID
+    assert lib.ibm_boundary_velocity_rigid(None, None, 0, None, None) == INVALID
+    assert lib.ibm_tables_export_self_weight(None, None, None) == INVALID
+    assert lib.ibm_helmholtz_solve(None, None, 0.1, None, None, 1e-10, None, None, None, None) == INVALID
+    ms = ctypes.c_double()
+    assert lib.ibm_helmholtz_sweeps_timed(None, None, 0.1, 2, 1, None, None, None, ctypes.byref(ms)) == INVALID
+    assert lib.ibm_set_neumann(None, None, None) == INVALID
+    assert lib.ibm_neumann_rigid(None, None, 0, None) == INVALID
+
+
+def test_helmholtz_option_defaults():
+    import paper_2605_04335_gb300 as pkg
+    from paper_2605_04335_gb300.ibm import ibm_helmholtz_opts
+    o = ibm_helmholtz_opts()
+    pkg.load_library().ibm_helmholtz_opts_default(ctypes.byref(o))
+    assert (o.precision, o.srj_steps, o.max_cycles) == (2, 8, 100)
+    d = pkg.HelmholtzOpts()
+    assert (d.precision, d.srj_steps, d.max_cycles) == (2, 8, 100)
