@@ -89,28 +89,55 @@ def inside_mesh(grid: Grid, verts: np.ndarray, tris: np.ndarray) -> np.ndarray:
     return out
 
 
+class MeshNotClosed(ValueError):
+    """A closed mesh is crossed an odd number of times by some grid column."""
+
+
 def inside_mesh_box(grid: Grid, verts: np.ndarray, tris: np.ndarray):
+    """(box, inside) of ``column_parity``: the inside test of the cells that can be inside."""
+    box, inside, _ = column_parity(grid, verts, tris)
+    return box, inside
+
+
+def odd_columns(grid: Grid, verts: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """(j, i) pairs of the grid columns (vertical lines through the cell centres) that the
+    surface crosses an odd number of times.  A watertight surface separates space into an
+    inside and an outside, so every line enters and leaves it alike: the count is even on
+    every column.  An odd count means a hole in the surface on that line."""
+    box, _, odd = column_parity(grid, verts, tris)
+    if box is None:
+        return np.zeros((0, 2), dtype=np.int64)
+    _, j0, i0 = box
+    jj, ii = np.nonzero(odd)
+    return np.stack([jj + j0, ii + i0], axis=1).astype(np.int64)
+
+
+def column_parity(grid: Grid, verts: np.ndarray, tris: np.ndarray):
     """The inside test on the cells that can be inside: columns whose centre lies in the
     mesh's xy box, planes from the mesh's lowest centre up to the top of the grid (cells
-    outside that region have no crossing below them, so their parity is even).  Returns
-    ((k0, j0, i0), boolean [nz-k0][nj][ni]) or (None, None).
+    outside that region have no crossing below them, so their parity is even).
 
     Every (triangle, column) pair of a triangle's xy box is tested at once: integer edge
     functions (exact in int64), the top-left rule, then the crossing height N / D.  N needs
     up to 82 bits, so its floor is taken from a float64 estimate whose error is far below
     one lattice unit, and pairs whose estimate lies within 1e-6 of an integer are redone
     in exact Python integers.
+
+    Returns ((k0, j0, i0), boolean inside [nz-k0][nj][ni], boolean odd [nj][ni]) or
+    (None, None, None); odd marks the columns with an odd total number of crossings (the
+    slot above the top centre included).  A mesh above every centre gives k0 = nz (no
+    inside cell), its columns still counted.
     """
     Xc, Yc, Zc = snap(grid.xc), snap(grid.yc), snap(grid.zc)
     V = snap(verts)
     nz, ny, nx = grid.shape
     if V.size == 0:
-        return None, None
+        return None, None, None
     bi0, bi1 = _closed_range(Xc, int(V[:, 0].min()), int(V[:, 0].max()))
     bj0, bj1 = _closed_range(Yc, int(V[:, 1].min()), int(V[:, 1].max()))
     bk0 = int(np.searchsorted(Zc, int(V[:, 2].min()), "left"))
-    if bi0 >= bi1 or bj0 >= bj1 or bk0 >= nz:
-        return None, None
+    if bi0 >= bi1 or bj0 >= bj1:
+        return None, None, None
     # local sub-box: columns [bj0, bj1) x [bi0, bi1), planes [bk0, nz)
     Xc, Yc, Zc = Xc[bi0:bi1], Yc[bj0:bj1], Zc[bk0:]
     nz, ny, nx = Zc.size, Yc.size, Xc.size
@@ -168,7 +195,8 @@ def inside_mesh_box(grid: Grid, verts: np.ndarray, tris: np.ndarray):
     on &= Zc[np.maximum(ks - 1, 0)] == q
     onsurf[ks[on] - 1, jj[on], ii[on]] = True
     parity = np.bitwise_xor.accumulate(toggles[:nz], axis=0).astype(bool)
-    return (bk0, bj0, bi0), parity & ~onsurf
+    odd = np.bitwise_xor.reduce(toggles, axis=0).astype(bool)
+    return (bk0, bj0, bi0), parity & ~onsurf, odd
 
 
 def _mark_vertical(A, B, C, QX, QY, Zc, onsurf, i0, j0):
@@ -199,12 +227,16 @@ def _mark_vertical(A, B, C, QX, QY, Zc, onsurf, i0, j0):
 
 
 def iblank_closed(grid: Grid, meshes) -> np.ndarray:
-    """uint8 [k][j][i]: 0 fluid, 1 solid (inside any closed mesh); ghost bit added by ``mark_ghosts``."""
+    """uint8 [k][j][i]: 0 fluid, 1 solid (inside any closed mesh); ghost bit added by ``mark_ghosts``.
+    Raises MeshNotClosed when a closed mesh has an odd crossing count on some column."""
     solid = np.zeros(grid.shape, dtype=bool)
     for m in meshes:
         if int(m.closed):
-            box, sub = inside_mesh_box(grid, m.verts, m.tris)
-            if box is not None:
+            box, sub, odd = column_parity(grid, m.verts, m.tris)
+            if odd is not None and np.any(odd):
+                raise MeshNotClosed("closed mesh crossed an odd number of times by %d grid column(s)"
+                                    % int(np.count_nonzero(odd)))
+            if box is not None and sub.shape[0] > 0:
                 k0, j0, i0 = box
                 solid[k0:, j0:j0 + sub.shape[1], i0:i0 + sub.shape[2]] |= sub
     return solid.astype(np.uint8)

@@ -160,6 +160,12 @@ def box_mesh(lo, hi) -> Mesh:
     return Mesh(V, T, 1)
 
 
+def overlapping_bodies(zc: float = 0.47) -> list:
+    """A box [0.1, 0.9]^2 x [0.1, zc] and a 512-triangle sphere (radius 0.23) centred on its top
+    face: two closed bodies whose surfaces cut through each other (the solid is their union)."""
+    return [box_mesh((0.1, 0.1, 0.1), (0.9, 0.9, zc)), octa_sphere(3, (0.5, 0.5, zc), 0.23)]
+
+
 def plate(t: float, chord: float = 0.4, span: float = 0.2, nq_x: int = 100, nq_y: int = 100,
           heave: float = 0.1, pitch_deg: float = 30.0, center=(0.5, 0.5, 0.5)) -> Mesh:
     """Zero-thickness flapping plate (membrane) at phase t.
@@ -347,9 +353,11 @@ def cfg3(n: int = 512, phase: int = 0, nphase: int = 8, ratio: float = 2.0) -> P
                    [plate(phase / nphase)], 3, {"phase": phase})
 
 
-def cfg4(n: int = 1024) -> Problem:
+def cfg4(n: int = 1024, placement_n: int = 1024) -> Problem:
+    """12 random spheres (placed for a placement_n^3 grid: surface gaps >= 8 / placement_n) on an
+    n^3 uniform grid; the default keeps the 1024^3 workload's spheres at every n."""
     f = faces_uniform(n)
-    return Problem("spheres12_1024_uniform", f, f.copy(), f.copy(), random_spheres(12, 4, 1.0 / n), 4)
+    return Problem("spheres12_%d_uniform" % n, f, f.copy(), f.copy(), random_spheres(12, 4, 1.0 / placement_n), 4)
 
 
 def cfg5(count: int = 48, seed: int = 5, lo: int = 64, hi: int = 192) -> list:

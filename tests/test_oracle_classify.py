@@ -293,3 +293,58 @@ def test_closest_points_mesh_pruning_equals_full_scan():
     tf = np.argmin(d2, axis=1)
     assert np.array_equal(t, tf)
     assert np.array_equal(q, Q[np.arange(P.shape[0]), tf])
+
+
+# ----------------------------------------------------------------------------- watertightness
+
+def _centres_strictly_inside_projection(grid, a, b, c, margin):
+    """Columns (j, i) whose centre lies inside the xy-projection of triangle abc by more than
+    `margin` from every edge (floats; the caller checks that no centre lies within the
+    margin, so the answer is not a tie)."""
+    X, Y = np.meshgrid(grid.xc, grid.yc, indexing="xy")
+    out, near = set(), False
+    area = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+    sgn = 1.0 if area > 0 else -1.0
+    for p, q in ((a, b), (b, c), (c, a)):
+        L = math.hypot(q[0] - p[0], q[1] - p[1])
+        d = sgn * ((q[0] - p[0]) * (Y - p[1]) - (q[1] - p[1]) * (X - p[0])) / L
+        near |= bool(np.any(np.abs(d) <= margin))
+        if p is a:
+            ok = d > margin
+        else:
+            ok &= d > margin
+    for j, i in zip(*np.nonzero(ok)):
+        out.add((int(j), int(i)))
+    return out, near
+
+
+def test_watertight_meshes_have_no_odd_column_and_a_hole_gives_exactly_its_columns():
+    """Jordan: a watertight surface crosses every vertical line an even number of times, so
+    no column is odd -- also for a body poking above the top cell centre (its crossings
+    above the last centre count).  Deleting one triangle of the upper half leaves a hole:
+    exactly the columns through the inside of its xy-projection become odd, and the inside
+    test refuses the mesh."""
+    f = synth.faces_tanh(24, 1.5)
+    g = Grid(f, synth.faces_uniform(22), f)
+    whole = synth.octa_sphere(2, (0.5, 0.5, 0.5), 0.36)
+    top = synth.octa_sphere(3, (0.47, 0.52, 0.93), 0.2)        # reaches z = 1.13 > the top centre
+    for m in (whole, top):
+        assert C.odd_columns(g, m.verts, m.tris).shape[0] == 0
+        C.iblank_closed(g, [m])
+    V = whole.verts
+    cz = V[whole.tris].mean(axis=1)[:, 2]
+    tested = 0
+    for t in np.argsort(-cz):
+        a, b, c = (V[whole.tris[t, q]] for q in range(3))
+        expect, near = _centres_strictly_inside_projection(g, a, b, c, 1e-7)
+        if near or len(expect) < 2:
+            continue
+        leaky = synth.Mesh(V, np.delete(whole.tris, t, axis=0), 1)
+        got = {(int(j), int(i)) for j, i in C.odd_columns(g, leaky.verts, leaky.tris)}
+        assert got == expect, (t, sorted(got ^ expect))
+        with pytest.raises(C.MeshNotClosed):
+            C.iblank_closed(g, [leaky])
+        tested += 1
+        if tested == 3:
+            break
+    assert tested == 3
