@@ -42,7 +42,9 @@ typedef enum {
   IBM_ERR_DIVERGED = 6,      /* residual became non-finite or grew by > 1e6          */
   IBM_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                   */
   IBM_ERR_NOT_IMPLEMENTED = 8,
-  IBM_ERR_CAPACITY = 9       /* a fixed-size internal buffer is too small            */
+  IBM_ERR_CAPACITY = 9,      /* a fixed-size internal buffer is too small            */
+  IBM_ERR_MESH_NOT_CLOSED = 10 /* a closed mesh is crossed an odd number of times by a
+                                  grid column (a hole in the surface on that line)     */
 } ibm_status;
 
 typedef struct ibm_ctx ibm_ctx;       /* opaque: device, scratch, reduction buffers      */
@@ -116,8 +118,10 @@ const char *ibm_status_str(ibm_status s);
 /* Text of the last CUDA error seen by this host thread (empty if none). */
 const char *ibm_last_cuda_error(void);
 
-/* Create a context on CUDA device `device` (allocates reduction scratch). */
-ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device);
+/* Create a context on CUDA device `device` (allocates reduction scratch).
+ * tune_cache_path (host string, nullable): a JSON file where ibm_autotune keeps the schedules
+ * it found (created on the first tuning; see ibm_autotune). */
+ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device, const char *tune_cache_path);
 ibm_status ibm_ctx_destroy(ibm_ctx *ctx);
 
 /* Iblanking and ghost-cell tables (paper Sec. "GPU Porting", items 1 and 2).
@@ -131,7 +135,11 @@ ibm_status ibm_ctx_destroy(ibm_ctx *ctx);
  * sign of orient3d of the crossing triangle and centre i; entries are ordered by cell, then
  * side; the IP's corners count only on the entry's side (exact segment tests), blocked
  * corners through the same-side entry of that cell.  nmesh may be 0 (no body).  On
- * success *out owns device memory until ibm_tables_destroy. */
+ * success *out owns device memory until ibm_tables_destroy.  A closed mesh that some grid
+ * column (the vertical line through cell centres (x_i, y_j)) crosses an odd number of times
+ * has a hole on that line: the call returns IBM_ERR_MESH_NOT_CLOSED and *out is not set
+ * (holes that no column passes through leave the classification unchanged and are not
+ * reported). */
 ibm_status ibm_classify(ibm_ctx *ctx, const ibm_grid *grid, const ibm_mesh *meshes,
                         int32_t nmesh, ibm_tables **out, void *stream);
 ibm_status ibm_tables_destroy(ibm_tables *t);
@@ -312,7 +320,10 @@ void ibm_solve_opts_default(ibm_solve_opts *opts);
  *   rhs_dev  double[ncell]  b on fluid cells (other cells ignored); not modified.
  *   p_dev    double[ncell]  in: initial guess on fluid and ghost cells; out: p on fluid
  *                           cells, g on ghost cells, 0 on other solid cells.
- * Returns IBM_ERR_NOT_CONVERGED (p = last iterate) if max_cycles is reached. */
+ * Returns IBM_ERR_NOT_CONVERGED (p = last iterate) if max_cycles is reached;
+ * IBM_ERR_DIVERGED before any cycle when rhs or the initial guess holds a NaN or an Inf on
+ * a fluid row (or in a value a ghost row reads), and during the iteration when the residual
+ * becomes non-finite or grows a millionfold. */
 ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol,
                          double *p_dev, const ibm_solve_opts *opts, ibm_solve_info *info,
                          void *stream);
@@ -339,7 +350,13 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
  * precision 1 or 2, 1/2/3 FP32 V-cycles per refinement step; Krylov acceleration none or
  * GCR(2), and GCR(8) on membrane tables -- and returns the fastest in *best
  * (its time in *best_ms, optional).  p_work_dev (double[ncell], device) is overwritten.
- * Use the result for poisson_solve / poisson_solve_batched of similar problems. */
+ * Use the result for poisson_solve / poisson_solve_batched of similar problems.
+ * With a tune cache (ibm_ctx_create), the cache is read first: an entry for the same grid
+ * (cell counts and a hash of the face coordinates), precision and body kind (closed or
+ * membrane) is returned as it is, with its recorded time, and nothing is launched.  Otherwise
+ * the search runs and its result is added to the file (one JSON object per line, rewritten
+ * through a temporary file and a rename); IBM_ERR_INVALID_ARG if the file cannot be
+ * written (*best is filled all the same). */
 ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, const double *rhs_dev,
                         double *p_work_dev, double tol, ibm_solve_opts *best, double *best_ms,
                         void *stream);
@@ -367,23 +384,31 @@ ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
  * start-up -- e.g. a flow solver that owns a fixed device arena, where cudaMalloc/cudaFree
  * would synchronise the whole device (breaking compute/communication overlap) or could
  * fail in the middle of a time-step loop.  It needs no context and no tables object: the
- * caller passes the grid (host faces), the classification as exported by
+ * caller passes the grid (host faces), the classification of CLOSED bodies as exported by
  * ibm_tables_export (iblank, ghost cells, interpolation sources, weights, row scales), the
- * right-hand side and the pressure (user layout, ghost values at ghost cells, as
+ * optional ghost-row data d = kappa q as ibm_tables_export_neumann writes it (NULL: zero),
+ * the right-hand side and the pressure (user layout, ghost values at ghost cells, as
  * poisson_solve returns it), all on the current CUDA device.
  *   result (host, 3 doubles): ||S P r|| / ||S P b||, ||S P r||, ||S P b||, with the same
- *   definitions as poisson_solve.
+ *   definitions as poisson_solve: fluid rows r = b - A p, the volume-weighted fluid mean
+ *   removed (P), ghost rows r_G = d_G - (g_G - sum w v) scaled by the row scale (S).  The
+ *   means are taken in a first pass and the squared deviations in a second, so a right-hand
+ *   side with a large fluid mean does not cancel the result away.
+ * Membrane tables are rejected with IBM_ERR_INVALID_ARG: any ghost row whose cell is not a
+ * closed body's ghost cell (iblank 3), or whose cell or source index is outside the
+ * nx*ny*nz cells, sets an error word in the scratch; p is never read at such an index.
  * Scratch: one fixed device array of about 0.2 MB inside this library, held by every GPU
  * that loads it until the process exits.  Grids with more than 2048 cells along any axis
- * are rejected with IBM_ERR_CAPACITY.  The first call on a device looks up that array's
- * device address (make it before any stream capture).  Every call reuses the same array:
+ * are rejected with IBM_ERR_CAPACITY.  The first call on a device (and the first after a
+ * new CUDA context replaces the device's old one) looks up that array's device address:
+ * make that first call before any stream capture.  Every call reuses the same array:
  * calls that overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Synchronises `stream` before returning. */
 ibm_status ibm_residual_norm_noalloc(const ibm_grid *grid, const uint8_t *iblank_dev, int64_t nghost,
                                      const int64_t *ghost_cell_dev, const int64_t *ghost_ref_dev,
                                      const double *ghost_w_dev, const double *ghost_scale_dev,
-                                     const double *rhs_dev, const double *p_dev, double *result,
-                                     void *stream);
+                                     const double *ghost_d_dev, const double *rhs_dev, const double *p_dev,
+                                     double *result, void *stream);
 
 #ifdef __cplusplus
 }

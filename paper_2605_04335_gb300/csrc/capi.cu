@@ -1,7 +1,12 @@
 // extern "C" entry points of libibmpoisson (declared and documented in include/ibm_poisson.h).
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
 
 #include "ibm_internal.cuh"
 
@@ -43,6 +48,93 @@ ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const 
                               double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
                               cudaStream_t st);
 
+// ---------------------------------------------------------------------- tune cache
+//
+// A JSON file of autotuned schedules, one entry per line:
+//   {"ibm_tune_cache": 1, "entries": [
+//   {"key": "...", "omega": 1.3, "nu1": 2, "nu2": 2, "inner_cycles": 2, "krylov": 0, "ms": 8.1},
+//   ...
+//   ]}
+// Key: the grid (cell counts and a 64-bit FNV-1a hash of the face coordinates' bytes), the
+// precision mode and whether the tables hold membranes.  The body's position is not part of
+// it, so one entry serves every time step of a moving body.
+
+struct TuneEntry {
+  std::string key;
+  double omega = 1.3, ms = 0.0;
+  int nu1 = 2, nu2 = 2, inner = 2, krylov = -1;
+};
+
+static std::string tune_key(const ibm_tables *t, int precision) {
+  uint64_t h = 1469598103934665603ULL;
+  auto mix = [&](const std::vector<double> &v) {
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(v.data());
+    for (size_t q = 0; q < v.size() * sizeof(double); ++q) { h ^= b[q]; h *= 1099511628211ULL; }
+  };
+  mix(t->xf); mix(t->yf); mix(t->zf);
+  char buf[128];
+  std::snprintf(buf, sizeof buf, "grid=%dx%dx%d faces=%016llx precision=%d membrane=%d", t->nx, t->ny, t->nz,
+                (unsigned long long)h, precision, t->membrane ? 1 : 0);
+  return buf;
+}
+
+// value of "name": in one entry line (number), false if absent
+static bool json_num(const std::string &line, const char *name, double *v) {
+  const std::string pat = std::string("\"") + name + "\":";
+  size_t q = line.find(pat);
+  if (q == std::string::npos) return false;
+  const char *p = line.c_str() + q + pat.size();
+  char *end = nullptr;
+  *v = std::strtod(p, &end);
+  return end != p;
+}
+
+// entries of the cache file (a missing or unreadable file reads as empty; lines that do not
+// parse are skipped)
+static std::vector<TuneEntry> tune_read(const std::string &path) {
+  std::vector<TuneEntry> out;
+  std::ifstream f(path);
+  std::string line;
+  while (f && std::getline(f, line)) {
+    size_t a = line.find("{\"key\": \"");
+    if (a == std::string::npos) continue;
+    a += 9;
+    size_t b = line.find('"', a);
+    if (b == std::string::npos) continue;
+    TuneEntry e;
+    e.key = line.substr(a, b - a);
+    double nu1, nu2, inner, kry;
+    if (!json_num(line, "omega", &e.omega) || !json_num(line, "nu1", &nu1) || !json_num(line, "nu2", &nu2) ||
+        !json_num(line, "inner_cycles", &inner) || !json_num(line, "krylov", &kry) || !json_num(line, "ms", &e.ms))
+      continue;
+    e.nu1 = (int)nu1; e.nu2 = (int)nu2; e.inner = (int)inner; e.krylov = (int)kry;
+    out.push_back(e);
+  }
+  return out;
+}
+
+// the whole file, rewritten through a temporary file and a rename
+static bool tune_write(const std::string &path, const std::vector<TuneEntry> &es) {
+  const std::string tmp = path + ".tmp";
+  {
+    std::ofstream f(tmp, std::ios::trunc);
+    if (!f) return false;
+    f << "{\"ibm_tune_cache\": 1, \"entries\": [\n";
+    char buf[512];
+    for (size_t q = 0; q < es.size(); ++q) {
+      const TuneEntry &e = es[q];
+      std::snprintf(buf, sizeof buf,
+                    "{\"key\": \"%s\", \"omega\": %.17g, \"nu1\": %d, \"nu2\": %d, \"inner_cycles\": %d, "
+                    "\"krylov\": %d, \"ms\": %.6g}%s\n",
+                    e.key.c_str(), e.omega, e.nu1, e.nu2, e.inner, e.krylov, e.ms, q + 1 < es.size() ? "," : "");
+      f << buf;
+    }
+    f << "]}\n";
+    if (!f) return false;
+  }
+  return std::rename(tmp.c_str(), path.c_str()) == 0;
+}
+
 }  // namespace ibm
 
 extern "C" {
@@ -59,13 +151,14 @@ const char *ibm_status_str(ibm_status s) {
     case IBM_ERR_TIMEOUT: return "device wait timed out";
     case IBM_ERR_NOT_IMPLEMENTED: return "not implemented";
     case IBM_ERR_CAPACITY: return "capacity exceeded";
+    case IBM_ERR_MESH_NOT_CLOSED: return "closed mesh not watertight";
   }
   return "unknown status";
 }
 
 const char *ibm_last_cuda_error(void) { return ibm::g_last_error.c_str(); }
 
-ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device) {
+ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device, const char *tune_cache_path) {
   if (!out) return IBM_ERR_INVALID_ARG;
   *out = nullptr;
   int n = 0;
@@ -74,7 +167,9 @@ ibm_status ibm_ctx_create(ibm_ctx **out, int32_t device) {
   IBM_TRY(cudaSetDevice(device));
   ibm_ctx *c = new ibm_ctx();
   c->device = device;
+  if (tune_cache_path) c->tune_cache = tune_cache_path;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (c->sm_count > 0) c->wave = 8 * c->sm_count;
   cudaError_t e = cudaMalloc((void **)&c->partials, sizeof(double) * ibm::REDUCE_BLOCKS * 8);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->scal, sizeof(double) * ibm::NSCAL);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hscal, sizeof(double) * ibm::NSCAL);
@@ -339,6 +434,19 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
     return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  std::string key;
+  if (!ctx->tune_cache.empty()) {
+    key = ibm::tune_key(t, precision);
+    for (const ibm::TuneEntry &e : ibm::tune_read(ctx->tune_cache))
+      if (e.key == key) {
+        ibm_solve_opts_default(best);
+        best->precision = precision;
+        best->omega = e.omega; best->nu1 = e.nu1; best->nu2 = e.nu2; best->inner_cycles = e.inner;
+        best->krylov = e.krylov;
+        if (best_ms) *best_ms = e.ms;
+        return IBM_OK;
+      }
+  }
   const double omegas[3] = {1.2, 1.3, 1.4};
   const int nus[3][2] = {{1, 1}, {2, 1}, {2, 2}};
   const int inners_mixed[3] = {1, 2, 3}, inner_fp64[1] = {1};
@@ -382,6 +490,14 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
   cudaEventDestroy(e1);
   if (best_t >= 1e29) return last != IBM_OK ? last : IBM_ERR_NOT_CONVERGED;
   if (best_ms) *best_ms = best_t;
+  if (!key.empty()) {
+    std::vector<ibm::TuneEntry> es = ibm::tune_read(ctx->tune_cache);
+    ibm::TuneEntry e;
+    e.key = key; e.omega = best->omega; e.nu1 = best->nu1; e.nu2 = best->nu2; e.inner = best->inner_cycles;
+    e.krylov = best->krylov; e.ms = best_t;
+    es.push_back(e);
+    if (!ibm::tune_write(ctx->tune_cache, es)) return IBM_ERR_INVALID_ARG;
+  }
   return IBM_OK;
 }
 

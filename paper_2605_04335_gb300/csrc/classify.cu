@@ -215,16 +215,20 @@ __global__ void k_tri_pairs(const Tri *tris, const long long *off, int ntri, lon
 }
 
 // per column: prefix parity of the toggles; solid where odd and not on the surface.
-// Clears the column's bit words for the next mesh.
+// Clears the column's bit words for the next mesh.  A watertight surface crosses every
+// vertical line an even number of times (each crossing counted once by the top-left rule),
+// so an odd total over the column -- the parity of all its toggle bits, the slot above the
+// top centre included -- marks a surface with a hole on that line: *leak is set.
 __global__ void k_parity(unsigned *toggles, unsigned *onsurf, int words, int nx, int ny, int nz, int i0, int i1,
-                         int j0, int j1, uint8_t *iblank) {
+                         int j0, int j1, uint8_t *iblank, unsigned *leak) {
   int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
   int j = j0 + blockIdx.y;
   if (i >= i1 || j >= j1) return;
   long long col = (long long)j * nx + i;
-  unsigned par = 0;
+  unsigned par = 0, total = 0;
   for (int w = 0; w < words; ++w) {
     unsigned tg = toggles[col * words + w], os = onsurf[col * words + w];
+    total ^= (unsigned)__popc(tg) & 1u;
     if (tg == 0 && os == 0 && par == 0) continue;
     toggles[col * words + w] = 0u;
     onsurf[col * words + w] = 0u;
@@ -235,6 +239,7 @@ __global__ void k_parity(unsigned *toggles, unsigned *onsurf, int words, int nx,
       if (par && !((os >> b) & 1u)) iblank[((long long)k * ny + j) * nx + i] = 1;
     }
   }
+  if (total) atomicOr(leak, 1u);
 }
 
 // -------------------------------------------------------------------------- ghost marking
@@ -1322,11 +1327,11 @@ ibm_status membrane_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     MTRY(cudaMemcpyAsync(&total, off + 3 * ntri, sizeof(long long), cudaMemcpyDeviceToHost, st));
     MTRY(cudaStreamSynchronize(st));
     if (total > 0) {
-      const unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 8LL * 152 * 4);
+      const unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 4LL * ctx->wave);
       k_mem_pairs<<<blocks, 256, 0, st>>>(recs, off, 3 * ntri, total, ntri, ax, ncell, linktri);
     }
   }
-  k_mem_cut<<<1216, 256, 0, st>>>(linktri, ncell, ax, tv, T->cut, T->cside);
+  k_mem_cut<<<ctx->wave, 256, 0, st>>>(linktri, ncell, ax, tv, T->cut, T->cside);
   MTRY(cudaGetLastError());
   // ghost entries in (cell, side) order
   const long long chunk = (long long)GM_THREADS * GM_PER;
@@ -1450,6 +1455,9 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     }
   }
   const int words = (nz + 1 + 31) / 32;
+  unsigned *leak = nullptr;   // set by k_parity: some column crosses a closed mesh an odd number of times
+  CTRY(S.get(&leak, 1));
+  CTRY(cudaMemsetAsync(leak, 0, sizeof(unsigned), st));
   if (tottris > 0) {
     unsigned *tog = nullptr, *ons = nullptr;
     CTRY(S.get(&tog, (size_t)nx * ny * words));
@@ -1469,7 +1477,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
       CTRY(cudaMemcpyAsync(&total, off + nt, sizeof(long long), cudaMemcpyDeviceToHost, st));
       CTRY(cudaStreamSynchronize(st));
       if (total > 0) {
-        unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 8LL * 152 * 4);
+        unsigned blocks = (unsigned)std::min<long long>(nblk(total, 256), 4LL * ctx->wave);
         k_tri_pairs<<<blocks, 256, 0, st>>>(tr, off, nt, total, ds[0], ds[1], ds[2], nx, ny, nz, words, tog, ons);
       }
       // columns of the mesh's xy box
@@ -1487,7 +1495,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
       i1 = std::min(nx, i1 + 1); j1 = std::min(ny, j1 + 1);
       if (i1 > i0 && j1 > j0) {
         dim3 gp(nblk(i1 - i0, 128), j1 - j0);
-        k_parity<<<gp, 128, 0, st>>>(tog, ons, words, nx, ny, nz, i0, i1, j0, j1, T->iblank);
+        k_parity<<<gp, 128, 0, st>>>(tog, ons, words, nx, ny, nz, i0, i1, j0, j1, T->iblank, leak);
       }
       CTRY(cudaGetLastError());
     }
@@ -1513,7 +1521,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
       k_ghost_scatter<<<nb, GM_THREADS, 0, st>>>(T->iblank, nx, ny, nz, ncell, bo, T->gcell);
       k_ghost_bits<<<nblk(ng, 256), 256, 0, st>>>(T->iblank, T->gcell, ng);
     }
-    k_count_cells<<<1216, 256, 0, st>>>(T->iblank, ncell, cellcnt);
+    k_count_cells<<<ctx->wave, 256, 0, st>>>(T->iblank, ncell, cellcnt);
     CTRY(cudaGetLastError());
   }
   const long long ng = T->nghost;
@@ -1547,7 +1555,9 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
     CTRY(cudaGetLastError());
   }
   unsigned long long hc[2];
+  unsigned hleak = 0;
   CTRY(cudaMemcpyAsync(hc, cellcnt, 16, cudaMemcpyDeviceToHost, st));
+  CTRY(cudaMemcpyAsync(&hleak, leak, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CTRY(cudaStreamSynchronize(st));
   T->nfluid = (long long)hc[0];
   T->nsolid = (long long)hc[1];
@@ -1555,6 +1565,7 @@ ibm_status classify_into(ibm_tables *T, const ibm_mesh *meshes, int nmesh, long 
   T->geom_version += 1;
   ctx->launches += 2 + 2 * (long long)nmesh * 3 + 5 + (T->nghost > 0 ? 5 + (long long)nmesh : 0);
 #undef CTRY
+  if (hleak) return IBM_ERR_MESH_NOT_CLOSED;
   return T->nfluid == 0 ? IBM_ERR_NO_FLUID : IBM_OK;
 }
 

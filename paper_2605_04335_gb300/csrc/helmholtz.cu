@@ -570,7 +570,7 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
     ++launches;
   }
   const bool cuts = t->membrane && h->cut_id;
-  const unsigned cut_blocks = cuts ? std::max(1u, std::min(nb_of(h->cutcap, 256), 1216u)) : 0;
+  const unsigned cut_blocks = cuts ? std::max(1u, std::min(nb_of(h->cutcap, 256), (unsigned)ctx->wave)) : 0;
   // SRJ relaxation factors: 1 / Chebyshev nodes of [1 - rho, 1 + rho]
   const double S = axis_max_sum(t->xf) + axis_max_sum(t->yf) + axis_max_sum(t->zf);
   const double rho = alpha * S / (1.0 + alpha * S);
@@ -671,8 +671,8 @@ ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const
       } else {
         IBM_TRY(cudaMemsetAsync(W.e[0], 0, sizeof(float) * want, st));
         const int ec = srj_cycle(W.e[0], W.e[1], (const float *)W.r32, v32, 0);
-        if (df) k_hz_update_df<<<1216, 256, 0, st>>>(uh, ul, W.e[ec], want);
-        else k_hz_update<<<1216, 256, 0, st>>>(W.u[cur], W.e[ec], want);
+        if (df) k_hz_update_df<<<ctx->wave, 256, 0, st>>>(uh, ul, W.e[ec], want);
+        else k_hz_update<<<ctx->wave, 256, 0, st>>>(W.u[cur], W.e[ec], want);
         ++launches;
         if ((s = residual(W.u[cur], W.r32, false)) != IBM_OK) return s;
       }

@@ -15,7 +15,9 @@ namespace ibm {
 // Padded cell arrays: one halo layer in every direction; element i = 0 of a row sits at
 // offset OX so rows start 32-byte aligned for float and double.
 constexpr int OX = 4;
-constexpr int REDUCE_BLOCKS = 608;   // 4 x 152 SMs: fixed grid -> deterministic reductions
+// Fixed reduction width: block partials are summed in a fixed order, so every reduction (and
+// with it every result) is the same on any device, whatever its SM count.
+constexpr int REDUCE_BLOCKS = 608;
 constexpr int REDUCE_THREADS = 256;
 constexpr int NSCAL = 32;            // device scalars per context
 
@@ -144,8 +146,11 @@ struct ibm_ctx {
   double *scal = nullptr;       // NSCAL device scalars
   double *hscal = nullptr;      // pinned host mirror of scal
   int sm_count = 0;
+  int wave = 1216;              // 256-thread blocks of one full wave: 8 per SM x sm_count
+                                // (launch shape of the grid-stride element-wise kernels)
   long long launches = 0;       // kernels launched by this context (all calls)
   int *errflag = nullptr;       // device flag: a bounded device-side wait gave up
+  std::string tune_cache;       // autotuner cache file (empty: none)
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture CUDA graphs
   // batched solves: the streams the problems' step graphs run on, fork/join events, and
   // per-problem scalars (device and pinned host) and block partials

@@ -31,8 +31,7 @@
 namespace ibm {
 
 constexpr int MAX_COARSE = 128;
-constexpr int PACK_BLOCKS = 1216;   // 8 x 152 SMs: grid of the row-group copy kernels
-constexpr int RESTRICT_BLOCKS = 1216;   // restriction blocks (at most; one partial sum each)
+constexpr int RESTRICT_BLOCKS = 1216;   // restriction blocks (at most; one partial sum each; fixed width)
 constexpr size_t GJ_SMEM_MAX = 160 * 1024;   // coarsest Gauss-Jordan in shared memory up to this size
 
 namespace {
@@ -1033,7 +1032,8 @@ __global__ void k_finalize_resid(const double *partials, int nb, const double *g
     double mu = sv / scal[S_FLUIDVOL];
     double n2 = s2 - 2.0 * mu * s1 + scal[S_NF] * mu * mu;
     scal[S_MU] = mu;
-    scal[S_NORM2] = (n2 > 0.0 ? n2 : 0.0) + sg;
+    // clamp the rounding below zero only: a NaN (from a non-finite b or p) must stay NaN
+    scal[S_NORM2] = (n2 < 0.0 ? 0.0 : n2) + sg;
     if (update_lambda) scal[S_LAMBDA] += mu;
   }
 }
@@ -1426,7 +1426,8 @@ __global__ void k_unpack_gauge_df(const float *ph, const float *pl, const uint8_
 // ntot + e for entry e).
 
 constexpr int CUT_THREADS = 256, CUT_PER = 16;   // compaction: cells per thread, contiguous
-constexpr int CUT_BLOCKS = 152;                  // grid of the cut-cell kernels (grid-stride)
+constexpr int CUT_BLOCKS = 152;                  // grid of the cut-cell kernels (grid-stride; fixed
+                                                 // reduction width)
 
 // exclusive scan of n int64 counts in one block; out has n+1 entries
 __global__ void k_scan1(const long long *in, long long *out, int n) {
@@ -2698,7 +2699,7 @@ void gcr_step(Solver &S, T *e, const T *r, int m) {
   k_gcr_dots<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, bs>>>(v0, wf, r, gs, Qb, ntot, p1);
   if (ng > 0) k_gcr_dots_ghost<T><<<GCR_GBLOCKS, 256, 0, bs>>>(h->gdst, S.t->gscale, h->d_ng, r, gs, Qb, ntot, p2);
   k_gcr_coef<<<1, 256, 0, bs>>>(p1, REDUCE_BLOCKS, p2, ng > 0 ? GCR_GBLOCKS : 0, gs);
-  k_gcr_update<T><<<1216, 256, 0, bs>>>(e, Zb, Qb, ntot, gs, S.dfo ? nullptr : h->p64,
+  k_gcr_update<T><<<S.ctx->wave, 256, 0, bs>>>(e, Zb, Qb, ntot, gs, S.dfo ? nullptr : h->p64,
                                         S.dfo ? hi_of(h->p64) : nullptr, S.dfo ? lo_of(h->p64, ntot) : nullptr);
   k_gcr_advance<<<1, 32, 0, bs>>>(gs, m);
   S.ctx->launches += 6 + (cuts ? 1 : 0) + (ng > 0 ? 2 : 0);
@@ -2781,6 +2782,7 @@ struct Run {
   double *r64 = nullptr;
   double *hs = nullptr;              // host copy of the scalars (NSCAL)
   double denom = 1.0, rel = 0.0, rel0 = 0.0;
+  bool finite_b = true;              // ||S P b|| is finite (no NaN or Inf on a fluid row of b)
   int cycles = 0, hl = 0;
   bool active = true;
   ibm_status result = IBM_ERR_NOT_CONVERGED;
@@ -2802,11 +2804,11 @@ ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, con
   R.S.batched = batched;
   R.ntot = h->nslot;   // level-0 elements: padded cells and membrane entry slots
   if (R.S.dfo) {
-    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, R.ntot), nullptr);
-    k_pack_df<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, R.ntot), L0.mask);
+    k_pack_df<<<R.ctx->wave, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, R.ntot), nullptr);
+    k_pack_df<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, R.ntot), L0.mask);
   } else {
-    k_pack<<<PACK_BLOCKS, 256, 0, st>>>(rhs, L0.g, h->b64, nullptr);
-    k_pack<<<PACK_BLOCKS, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask);
+    k_pack<<<R.ctx->wave, 256, 0, st>>>(rhs, L0.g, h->b64, nullptr);
+    k_pack<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask);
   }
   ctx->launches += 2;
   for (int q = 0; q < NSCAL; ++q) hs[q] = 0.0;
@@ -2822,6 +2824,7 @@ ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, con
 // the initial residual
 ibm_status run_begin(Run &R, cudaStream_t st) {
   const double bnorm = std::sqrt(R.hs[S_NORM2]);
+  R.finite_b = std::isfinite(bnorm);
   R.denom = bnorm > 0 ? bnorm : 1.0;
   Hierarchy *h = R.h;
   ibm_tables *t = R.t;
@@ -2869,9 +2872,12 @@ ibm_status run_begin(Run &R, cudaStream_t st) {
 }
 
 // after the initial residual's read-back
+// after the initial residual's read-back; a non-finite right-hand side or initial guess
+// (NaN or Inf on a fluid row, or in a ghost value it feeds) stops the solve before any cycle
 void run_initial(Run &R, double tol) {
   R.rel = R.rel0 = std::sqrt(R.hs[S_NORM2]) / R.denom;
-  if (R.rel <= tol) { R.result = IBM_OK; R.active = false; }
+  if (!R.finite_b || !std::isfinite(R.rel)) { R.result = IBM_ERR_DIVERGED; R.active = false; }
+  else if (R.rel <= tol) { R.result = IBM_OK; R.active = false; }
 }
 
 // one refinement step: V-cycle (FP64) or FP32 V-cycle(s) + outer update (mixed), then the
@@ -2903,11 +2909,11 @@ void run_step(Run &R, cudaStream_t bs) {
       gcr_step<float>(S, e32, R.r32, R.gcr_m);
     } else {
       if (S.dfo)
-        k_update_df<<<1216, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
+        k_update_df<<<R.ctx->wave, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
                                           reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
                                           reinterpret_cast<const float4 *>(e32), ntot / 4);
       else
-        k_update_p<<<1216, 256, 0, bs>>>(h->p64, e32, ntot);
+        k_update_p<<<R.ctx->wave, 256, 0, bs>>>(h->p64, e32, ntot);
       R.ctx->launches += 1;
     }
     outer_residual(S, true, R.r32, true);
@@ -2942,9 +2948,9 @@ void run_finish(Run &R, double *p_user, cudaStream_t st) {
     k_gauge_sum<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, st>>>(fine_view64(h), h->p64, part);
   k_gauge_finalize<<<1, 256, 0, st>>>(part, REDUCE_BLOCKS, scal);
   if (R.S.dfo)
-    k_unpack_gauge_df<<<PACK_BLOCKS, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, scal, p_user);
+    k_unpack_gauge_df<<<R.ctx->wave, 256, 0, st>>>(hi_of(h->p64), lo_of(h->p64, ntot), L0.mask, L0.g, scal, p_user);
   else
-    k_unpack_gauge<<<PACK_BLOCKS, 256, 0, st>>>(h->p64, L0.mask, L0.g, scal, p_user);
+    k_unpack_gauge<<<R.ctx->wave, 256, 0, st>>>(h->p64, L0.mask, L0.g, scal, p_user);
   R.ctx->launches += 3;
 }
 
@@ -3317,7 +3323,7 @@ void bc_dots(Solver &S, Bicg &B, const double *x0, const double *y0, const doubl
 // y := P y (volume-weighted fluid mean removed)
 void bc_project(Solver &S, Bicg &B, double *y, cudaStream_t bs) {
   bc_dots(S, B, y, nullptr, nullptr, nullptr, B.vw, 3, bs);
-  k_bc_project<<<1216, 256, 0, bs>>>(y, B.vw, B.st, S.h->nslot);
+  k_bc_project<<<S.ctx->wave, 256, 0, bs>>>(y, B.vw, B.st, S.h->nslot);
   S.ctx->launches += 1;
 }
 
@@ -3329,10 +3335,10 @@ void bc_precond(Solver &S, Bicg &B, const double *x, double *y, int K, cudaStrea
     const double lo = 2.0 / ((double)K * K), hi = 2.0;
     const double w = 2.0 / ((hi + lo) - (hi - lo) * node);
     if (k == 0) {
-      k_bc_jacobi<<<1216, 256, 0, bs>>>(y, x, nullptr, B.dinv, w, n);
+      k_bc_jacobi<<<S.ctx->wave, 256, 0, bs>>>(y, x, nullptr, B.dinv, w, n);
     } else {
       bc_apply(S, B, y, B.w, bs);
-      k_bc_jacobi<<<1216, 256, 0, bs>>>(y, x, B.w, B.dinv, w, n);
+      k_bc_jacobi<<<S.ctx->wave, 256, 0, bs>>>(y, x, B.w, B.dinv, w, n);
     }
     S.ctx->launches += 1;
   }
@@ -3375,7 +3381,7 @@ ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, d
   Level &L0 = h->lv[0];
   const LV<double> v0 = view<double>(L0);
   IBM_TRY(cudaMemcpyAsync(B.bt, h->b64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  k_bc_cells<<<1216, 256, 0, st>>>(v0, B.aw, B.vw, B.dinv);
+  k_bc_cells<<<ctx->wave, 256, 0, st>>>(v0, B.aw, B.vw, B.dinv);
   if (t->nghost > 0)
     k_bc_ghosts<<<nblk(h->gcap, 256), 256, 0, st>>>(h->gdst, t->gscale, h->d_ng, B.aw, B.dinv, B.bt,
                                                      t->has_datum ? t->gd : nullptr);
@@ -3386,7 +3392,7 @@ ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, d
   IBM_TRY(cudaMemcpyAsync(B.st, &init, sizeof(BicgState), cudaMemcpyHostToDevice, st));
   bc_dots(S, B, B.aw, nullptr, nullptr, nullptr, B.vw, 5, st);             // sum of fluid volumes
   bc_apply(S, B, B.x, B.y, st);
-  k_bc_resid<<<1216, 256, 0, st>>>(B.bt, B.y, B.aw, n, B.r);
+  k_bc_resid<<<ctx->wave, 256, 0, st>>>(B.bt, B.y, B.aw, n, B.r);
   ctx->launches += 1;
   bc_project(S, B, B.r, st);
   IBM_TRY(cudaMemcpyAsync(B.rh, B.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -3401,17 +3407,17 @@ ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, d
   auto iterate = [&](cudaStream_t bs) {
     S.st = bs;
     bc_dots(S, B, B.rh, B.r, nullptr, nullptr, B.aw, 0, bs);                 // rho, beta
-    k_bc_update<<<1216, 256, 0, bs>>>(0, B.st, n, B.p, B.r, B.v, nullptr, nullptr, nullptr, nullptr);
+    k_bc_update<<<S.ctx->wave, 256, 0, bs>>>(0, B.st, n, B.p, B.r, B.v, nullptr, nullptr, nullptr, nullptr);
     bc_precond(S, B, B.p, B.y, K, bs);                                        // y = K p
     bc_apply(S, B, B.y, B.v, bs);                                             // v = P A y
     bc_project(S, B, B.v, bs);
     bc_dots(S, B, B.rh, B.v, nullptr, nullptr, B.aw, 1, bs);                 // alpha
-    k_bc_update<<<1216, 256, 0, bs>>>(1, B.st, n, B.s, B.r, B.v, nullptr, nullptr, nullptr, nullptr);
+    k_bc_update<<<S.ctx->wave, 256, 0, bs>>>(1, B.st, n, B.s, B.r, B.v, nullptr, nullptr, nullptr, nullptr);
     bc_precond(S, B, B.s, B.z, K, bs);                                        // z = K s
     bc_apply(S, B, B.z, B.t, bs);                                             // t = P A z
     bc_project(S, B, B.t, bs);
     bc_dots(S, B, B.t, B.s, B.t, B.t, B.aw, 2, bs);                          // omega
-    k_bc_update<<<1216, 256, 0, bs>>>(2, B.st, n, B.r, B.s, nullptr, B.x, B.y, B.z, B.t);
+    k_bc_update<<<S.ctx->wave, 256, 0, bs>>>(2, B.st, n, B.r, B.s, nullptr, B.x, B.y, B.z, B.t);
     bc_dots(S, B, B.r, B.r, nullptr, nullptr, B.aw, 4, bs);                  // |r|^2
     ctx->launches += 3;
     S.st = st;
@@ -3452,7 +3458,7 @@ ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, d
   if (ge) cudaGraphExecDestroy(ge);
   // lambda: the volume-weighted fluid mean of the final unprojected residual
   bc_apply(S, B, B.x, B.y, st);
-  k_bc_resid<<<1216, 256, 0, st>>>(B.bt, B.y, B.aw, n, B.r);
+  k_bc_resid<<<ctx->wave, 256, 0, st>>>(B.bt, B.y, B.aw, n, B.r);
   bc_dots(S, B, B.r, nullptr, nullptr, nullptr, B.vw, 3, st);
   ctx->launches += 1;
   IBM_TRY(cudaMemcpyAsync(&hst, B.st, sizeof(BicgState), cudaMemcpyDeviceToHost, st));

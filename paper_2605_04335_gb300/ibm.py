@@ -18,7 +18,7 @@ IBM_OK = 0
 IBM_ERR_NOT_CONVERGED = 5
 STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID_ARG", 2: "IBM_ERR_OOM", 3: "IBM_ERR_CUDA", 4: "IBM_ERR_NO_FLUID",
           5: "IBM_ERR_NOT_CONVERGED", 6: "IBM_ERR_DIVERGED", 7: "IBM_ERR_TIMEOUT", 8: "IBM_ERR_NOT_IMPLEMENTED",
-          9: "IBM_ERR_CAPACITY"}
+          9: "IBM_ERR_CAPACITY", 10: "IBM_ERR_MESH_NOT_CLOSED"}
 
 
 class IbmError(RuntimeError):
@@ -73,7 +73,7 @@ def load_library():
     sig = {
         "ibm_status_str": (C.c_char_p, [I32]),
         "ibm_last_cuda_error": (C.c_char_p, []),
-        "ibm_ctx_create": (I32, [C.POINTER(P), I32]),
+        "ibm_ctx_create": (I32, [C.POINTER(P), I32, C.c_char_p]),
         "ibm_ctx_destroy": (I32, [P]),
         "ibm_classify": (I32, [P, C.POINTER(ibm_grid), C.POINTER(ibm_mesh), I32, C.POINTER(P), P]),
         "ibm_reclassify": (I32, [P, P, C.POINTER(ibm_mesh), I32, P]),
@@ -95,7 +95,7 @@ def load_library():
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
         "ibm_smoother_sweeps_timed": (I32, [P, P, I32, I32, P, C.POINTER(C.c_double)]),
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
-        "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P,
+        "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P, P,
                                             C.POINTER(C.c_double), P]),
         "poisson_solve_batched": (I32, [P, I32, P, P, D, P, C.POINTER(ibm_solve_opts), P, P]),
         "ibm_autotune": (I32, [P, P, I32, P, P, D, C.POINTER(ibm_solve_opts), C.POINTER(C.c_double), P]),
@@ -128,10 +128,12 @@ def _ptr(t):
 
 # ----------------------------------------------------------------------------- C-named calls
 
-def ibm_ctx_create(device: int = 0):
+def ibm_ctx_create(device: int = 0, tune_cache: str | None = None):
+    """Context on `device`; tune_cache: path of the autotuner's JSON cache file, or None."""
     lib = load_library()
     h = C.c_void_p()
-    _check(lib.ibm_ctx_create(C.byref(h), device), "ibm_ctx_create")
+    path = None if tune_cache is None else os.fsencode(tune_cache)
+    _check(lib.ibm_ctx_create(C.byref(h), device, path), "ibm_ctx_create")
     return h
 
 
@@ -306,16 +308,17 @@ def ibm_ctx_launch_count(ctx) -> int:
     return int(v.value)
 
 
-def ibm_residual_norm_noalloc(xf, yf, zf, iblank, cell, ref, w, scale, rhs, p, stream=None):
+def ibm_residual_norm_noalloc(xf, yf, zf, iblank, cell, ref, w, scale, rhs, p, d=None, stream=None):
     """Relative projected residual of p, computed by the library without allocating device
     memory (for callers that cannot allocate after start-up).  Device arrays are torch CUDA
-    tensors in the layout ibm_tables_export produces.  Returns (rel, ||SPr||, ||SPb||)."""
+    tensors in the layout ibm_tables_export produces (closed bodies only); d the ghost rows'
+    data as export()["d"] gives it, or None.  Returns (rel, ||SPr||, ||SPb||)."""
     f = [np.ascontiguousarray(a, dtype=np.float64) for a in (xf, yf, zf)]
     g = ibm_grid(f[0].size - 1, f[1].size - 1, f[2].size - 1, f[0].ctypes.data, f[1].ctypes.data, f[2].ctypes.data)
     out = (C.c_double * 3)()
     ng = int(cell.numel()) if cell is not None else 0
     _check(load_library().ibm_residual_norm_noalloc(C.byref(g), _ptr(iblank), ng, _ptr(cell), _ptr(ref), _ptr(w),
-                                                    _ptr(scale), _ptr(rhs), _ptr(p), out, _stream(stream)),
+                                                    _ptr(scale), _ptr(d), _ptr(rhs), _ptr(p), out, _stream(stream)),
            "ibm_residual_norm_noalloc")
     return float(out[0]), float(out[1]), float(out[2])
 
@@ -356,8 +359,8 @@ def ibm_autotune(ctx, tables, precision: int, rhs, p_work, tol: float = 1e-10, s
 # ----------------------------------------------------------------------------- conveniences
 
 class Context:
-    def __init__(self, device: int = 0):
-        self.h = ibm_ctx_create(device)
+    def __init__(self, device: int = 0, tune_cache: str | None = None):
+        self.h = ibm_ctx_create(device, tune_cache)
 
     def close(self):
         if self.h is not None:

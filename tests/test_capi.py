@@ -42,7 +42,7 @@ def test_ctx_create_rejects_bad_device_without_gpu():
     import paper_2605_04335_gb300 as pkg
     lib = pkg.load_library()
     h = ctypes.c_void_p()
-    s = lib.ibm_ctx_create(ctypes.byref(h), -1)
+    s = lib.ibm_ctx_create(ctypes.byref(h), -1, None)
     assert s != 0
 
 
