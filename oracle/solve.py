@@ -107,15 +107,18 @@ class BoxSolver:
         self.inv = np.where(small, 0.0, 1.0 / np.where(small, 1.0, tot))
 
     def solve(self, r: np.ndarray) -> np.ndarray:
+        """Each axis transform is one matrix contraction along that axis (np.tensordot, a
+        BLAS matrix product): forward transforms z, y, x, the scaling by the inverse
+        eigenvalue sums, then the inverse transforms."""
         x = r.reshape(self.shape)
-        x = np.einsum("ak,kji->aji", self.ops[0][2], x)
-        x = np.einsum("bj,aji->abi", self.ops[1][2], x)
-        x = np.einsum("ci,abi->abc", self.ops[2][2], x)
+        x = np.tensordot(self.ops[0][2], x, axes=([1], [0]))                     # z
+        x = np.tensordot(self.ops[1][2], x, axes=([1], [1])).transpose(1, 0, 2)  # y
+        x = np.tensordot(x, self.ops[2][2], axes=([2], [1]))                     # x
         x = x * self.inv
-        x = np.einsum("ka,abc->kbc", self.ops[0][1], x)
-        x = np.einsum("jb,kbc->kjc", self.ops[1][1], x)
-        x = np.einsum("ic,kjc->kji", self.ops[2][1], x)
-        return x
+        x = np.tensordot(self.ops[0][1], x, axes=([1], [0]))
+        x = np.tensordot(self.ops[1][1], x, axes=([1], [1])).transpose(1, 0, 2)
+        x = np.tensordot(x, self.ops[2][1], axes=([2], [1]))
+        return np.ascontiguousarray(x)
 
 
 def solve_gmres(grid: Grid, iblank: np.ndarray, G: GhostTable, b: np.ndarray,
