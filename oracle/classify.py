@@ -33,9 +33,16 @@ separately rounded operations (no fused multiply-add) and IEEE division, so
 results are reproducible bit for bit by any implementation that keeps this
 order.
 
+* Watertightness: a closed surface crosses every vertical line an even number
+  of times; a grid column with an odd count (crossings above the top centre
+  included) marks a hole and the mesh is refused (``MeshNotClosed``).
+
 Parity status: the inside test is pinned by exact rational winding numbers and
 analytic sphere bounds; closest points by brute force and closed forms (plane
-reflection); weights by linear-field reproduction (tests/test_oracle_classify.py).
+reflection); weights by linear-field reproduction; the watertightness rule by a
+sphere with one triangle deleted (tests/test_oracle_classify.py); the fallback
+rows by the rule recomputed cell by cell on two overlapping bodies
+(tests/test_oracle_fallback.py).
 """
 from __future__ import annotations
 
