@@ -1,17 +1,19 @@
 """Benchmark of the ghost-cell immersed-boundary pressure Poisson hot path on GB300.
 
-One step = one time step of a moving body: reclassify the 256^3 tanh-stretched grid (max/min
-spacing 2) for the prolate ellipsoid (0.2/0.08/0.08, 8192 triangles) at its next position
-(eight positions cycled) + mixed-precision solve of the pressure Poisson system to 1e-10
-relative projected residual, with the seeded N(0,1) divergence right-hand side (synthetic
-inputs standing in for the paper's wing geometries).
-Inputs are resident in HBM when the timed region starts; the working set (~0.8 GB) is
-larger than L2, so no flush is needed between steps.
+Headline step: the pressure Poisson solve of the 1024^3 uniform grid (1.07e9 cells) around 12
+random non-overlapping spheres (r in [0.03, 0.08], 2048 triangles each), with the seeded
+N(0,1) divergence right-hand side, from p = 0 to 1e-10 relative projected residual, in the
+mixed precision mode: FP32 multigrid V-cycles inside FP64 iterative refinement (FP64 fine
+residual, refinement update and gauge).  Synthetic inputs standing in for the paper's wing and
+bat geometries at the paper's largest grid scale.  Inputs are resident in HBM when the timed
+region starts; the working set (~35 GB) is far larger than L2, so no flush is needed.
 
-Printed as one JSON line (rank 0).  Also measured: FP64 and mixed time to 1e-10 (solve
-only), smoother sweep throughput (Gpts/s per sweep) with its HBM roofline fraction, the
-end-to-end time through the C ABI with host buffers, GPU clocks during the timed region,
-and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+Printed as one JSON line (rank 0).  Also measured: the same solve in FP64 and with the
+double-FP32 refinement loop, the device memory of each mode, the smoother sweep kernel against
+the HBM roofline, the end-to-end time through the C ABI with host buffers, GPU clocks during
+the timed region, the FP64 CPU oracle on a bounded sample (cpu_baseline), and sections for the
+other workloads (moving ellipsoid on a 256^3 stretched grid, the paper's solver, advection-
+diffusion, 48 batched problems, the flapping plate, the paper's subdomain shape).
 
 --impl reference times the oracle (the CPU program the results are checked against) on a
 bounded sample of the same workload, on the host cores.
@@ -19,8 +21,10 @@ bounded sample of the same workload, on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -31,13 +35,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-10 residual & Gpts/s per sweep, mixed vs FP64, fraction of HBM peak"
-UNIT = "Gcell/s (cells classified and solved to 1e-10 per second)"
+UNIT = "Gcell/s (cells solved to 1e-10 relative residual per second)"
 TOL = 1e-10
 FP32_SWEEP_BYTES = 13.0    # read e 4 + rhs 4 + mask 1, write e 4 per cell and full sweep
 FP64_SWEEP_BYTES = 25.0    # read p 8 + b 8 + mask 1, write p 8
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_zmarch launch on the 256^3 grid,
-# from one ncu --set full capture of the current kernel
-SWEEP_TRAFFIC_BYTES = 180176640 + 40386048   # dram read + write of one launch, ncu --set full (profiles/)
+DTYPES = {0: "f64", 1: "f32+f64", 2: "f32 (double-f32 outer)"}
+PRECISIONS = {0: "FP64 multigrid", 1: "FP32 multigrid + FP64 refinement",
+              2: "FP32 multigrid + double-FP32 (48-bit) refinement"}
+SWEEP_KERNEL = "k_sweep_zmarch<float>"
+SWEEP_SOURCE = "paper_2605_04335_gb300/csrc/zmarch.cuh"
 
 
 def _peaks():
@@ -47,6 +53,29 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _traffic_per_cell(kernel: str, source: str):
+    """DRAM bytes per cell of one launch of `kernel` from the committed ncu summaries: a line
+    'bench-readable: kernel=K source_sha256=S dram_bytes_per_cell=B' under profiles/, used only
+    while the kernel's source file still has that hash (else None: counters of an older kernel)."""
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except OSError:
+        return None, "source not found"
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        try:
+            text = open(os.path.join(pdir, fn)).read()
+        except OSError:
+            continue
+        for m in re.finditer(r"bench-readable: kernel=(\S+) source_sha256=([0-9a-f]+) dram_bytes_per_cell=([0-9.eE+-]+)",
+                             text):
+            if m.group(1) == kernel:
+                if m.group(2) == sha:
+                    return float(m.group(3)), "profiles/" + fn
+                return None, "kernel changed since the ncu capture in profiles/" + fn
+    return None, "no ncu capture of this kernel"
 
 
 class ClockSampler:
@@ -123,13 +152,13 @@ def whole_job(t_ms_local: float, cells_per_rank: int, ws: int, device=None):
 
 
 def _cpu_sample(n: int):
-    """Oracle classify + solve of the workload's geometry on an n^3 grid (host cores)."""
-    import numpy as np
+    """Oracle classify + GMRES solve to 1e-10 of the headline workload's 12 spheres on an n^3
+    grid (host cores): (cells, seconds)."""
     import synth
     from oracle import classify as OC
     from oracle import solve as OS
     from oracle.grid import Grid
-    pr = synth.cfg2(n)
+    pr = synth.cfg4(n)
     g = Grid(pr.xf, pr.yf, pr.zf)
     b = pr.rhs()
     t0 = time.perf_counter()
@@ -137,6 +166,12 @@ def _cpu_sample(n: int):
     OS.solve_gmres(g, ib, G, b)
     dt = time.perf_counter() - t0
     return pr.ncells, dt
+
+
+def _sample_text(n: int, t: float = None) -> str:
+    s = ("FP64 CPU oracle (numpy/scipy): classification + GMRES solve to the FP64 floor of the headline "
+         "workload's 12 spheres on a %d^3 grid per step" % n)
+    return s + (" (%.1f s)" % t if t is not None else "")
 
 
 def run_reference(args):
@@ -157,23 +192,42 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(args),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "FP64 CPU oracle: classify + GMRES solve of the same geometry on a %d^3 grid "
-                                       "per step" % n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": _sample_text(n)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-DTYPES = {0: "f64", 1: "f32+f64", 2: "f32 (double-f32 outer)"}
-PRECISIONS = {0: "FP64 multigrid", 1: "FP32 multigrid + FP64 refinement",
-              2: "FP32 multigrid + double-FP32 (48-bit) refinement"}
+def _config(args):
+    return {"workload": "pressure Poisson solve from p = 0 to 1e-10 relative projected residual: %d^3 uniform grid "
+                        "(%.3g cells) around 12 random non-overlapping spheres (r in [0.03, 0.08], 2048 triangles "
+                        "each), seeded N(0,1) divergence right-hand side" % (args.n, float(args.n) ** 3),
+            "grid": [args.n] * 3, "tol": TOL, "precision": PRECISIONS[args.precision],
+            "l2": "working set > L2 (no flush)", "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+            "schedule": "library defaults (nu1 = nu2 = 2, omega 1.3, 2 FP32 V-cycles per refinement step)"}
+
+
+def _timed(torch, st, fn, reps):
+    """median CUDA-event time (ms) of fn() on stream st over reps calls after one untimed call"""
+    fn()
+    ts = []
+    for _ in range(reps):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        r = fn()
+        c.record(st)
+        c.synchronize()
+        ts.append(a.elapsed_time(c))
+    return statistics.median(ts), r
+
+
 NPOSE = 8
 
 
 def moving_ellipsoid(synth):
-    """Body positions of the step: the 0.2/0.08/0.08 ellipsoid (8192 triangles) circling its
-    centre by 0.01 and turning 2.5 deg per step, NPOSE positions cycled."""
+    """Body positions of the moving-body step: the 0.2/0.08/0.08 ellipsoid (8192 triangles)
+    circling its centre by 0.01 and turning 2.5 deg per step, NPOSE positions cycled."""
     import math
     out = []
     for s in range(NPOSE):
@@ -183,13 +237,94 @@ def moving_ellipsoid(synth):
     return out
 
 
-def _config(args):
-    return {"workload": "moving ellipsoid 0.2/0.08/0.08 (8192 tris; %d positions cycled) in a %d^3 tanh-stretched "
-                        "grid (ratio 2), seeded N(0,1) divergence rhs; step = reclassify the grid + solve the "
-                        "pressure system to 1e-10" % (NPOSE, args.n),
-            "grid": [args.n] * 3, "tol": TOL, "precision": PRECISIONS[args.precision],
-            "l2": "working set > L2 (no flush)", "parallelism": "replicas" if args.gpus > 1 else "single GPU",
-            "schedule": "library defaults" if args.no_autotune else "ibm_autotune per precision mode (untimed)"}
+def bench_moving_ellipsoid(pkg, ctx, torch, st, n: int = 256, steps: int = 20, autotune: bool = True,
+                           paper_solver: bool = True):
+    """One time step of a moving body on the 256^3 tanh-stretched grid (max/min spacing 2):
+    reclassify for the next of 8 positions of the 0.2/0.08/0.08 ellipsoid + solve to 1e-10 in
+    each precision mode (schedules from ibm_autotune on the first position); solve-only time to
+    1e-10 per mode on the fixed body; the paper's BiCGStab + SRJ on the same system; the fused
+    FP32 and the FP64 sweep kernels alone."""
+    import synth
+    pr = synth.cfg2(n)
+    N = pr.ncells
+    rhs = torch.from_numpy(pr.rhs()).cuda()
+    p = torch.zeros_like(rhs)
+    poses = moving_ellipsoid(synth)
+    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, poses[0], stream=st)
+    tuned, schedule = {}, {}
+    for prec in (0, 1, 2):
+        tuned[prec] = (pkg.ibm_autotune(ctx.h, T.h, prec, rhs, p, TOL, stream=st)[0] if autotune
+                       else pkg.SolveOpts(precision=prec))
+        o = tuned[prec]
+        schedule[PRECISIONS[prec]] = {"omega": o.omega, "nu1": o.nu1, "nu2": o.nu2, "inner_cycles": o.inner_cycles,
+                                      "krylov": o.krylov}
+    out = {"grid": [n] * 3, "cells": N, "solver_schedule": schedule, "step_ms": {}, "step_gcells_per_s": {}}
+    count = [0]
+    for name, prec in (("mixed", 1), ("mixed_df", 2), ("fp64", 0)):
+        def step():
+            count[0] += 1
+            T.reclassify(poses[count[0] % len(poses)], stream=st)
+            p.zero_()
+            return T.solve(rhs, p, TOL, tuned[prec], stream=st)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = steps if prec != 0 else max(3, steps // 4)
+        e0.record(st)
+        for _ in range(k):
+            step()
+        e1.record(st)
+        e1.synchronize()
+        out["step_ms"][name] = e0.elapsed_time(e1) / k
+        out["step_gcells_per_s"][name] = N / (out["step_ms"][name] * 1e-3) / 1e9
+    tcl, trc = [], []
+    for q in range(3):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        Tc = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+        c.record(st)
+        c.synchronize()
+        tcl.append(a.elapsed_time(c))
+        a.record(st)
+        Tc.reclassify(poses[q + 1], stream=st)
+        c.record(st)
+        c.synchronize()
+        trc.append(a.elapsed_time(c))
+        Tc.close()
+    out["classify_ms"], out["reclassify_ms"] = statistics.median(tcl), statistics.median(trc)
+    T.reclassify(pr.meshes, stream=st)
+    out["ghosts"] = T.nghost
+    tts, cyc = {}, {}
+    for name, prec in (("mixed", 1), ("mixed_df", 2), ("fp64", 0)):
+        def solve():
+            p.zero_()
+            return T.solve(rhs, p, TOL, tuned[prec], stream=st)
+        tts[name], rep = _timed(torch, st, solve, 3)
+        cyc[name] = rep["cycles"]
+    out["time_to_tol_ms"], out["cycles"] = tts, cyc
+    out["mixed_speedup_vs_fp64"] = {k: tts["fp64"] / tts[k] for k in ("mixed", "mixed_df")}
+    if paper_solver:
+        po = pkg.SolveOpts(precision=0, method=1, max_cycles=5000)
+        p.zero_()
+        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=0, method=1, max_cycles=2), stream=st, raise_on_error=False)
+        def paper():
+            p.zero_()
+            return T.solve(rhs, p, TOL, po, stream=st)
+        t_paper, rep = _timed(torch, st, paper, 1)
+        out["paper_solver"] = {"method": "BiCGStab preconditioned with %d relaxed Jacobi sweeps (Chebyshev schedule), "
+                                         "FP64" % po.srj_steps, "time_to_tol_ms": t_paper, "iterations": rep["cycles"],
+                               "multigrid_speedup": {k: t_paper / tts[k] for k in tts}}
+    hbm, src = _peaks()
+    for name, prec, nbytes in (("fp32", 2, FP32_SWEEP_BYTES), ("fp64", 0, FP64_SWEEP_BYTES)):
+        pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, 3, st)
+        ms = pkg.ibm_smoother_sweeps_timed(ctx.h, T.h, prec, 20, st)
+        ach = nbytes * N / (ms * 1e-3) / 1e9
+        out["sweep_kernel_" + name] = {"ms": ms, "gcells_per_s": N / (ms * 1e-3) / 1e9, "achieved_gbs": ach,
+                                       "frac_of_hbm": ach / hbm, "algorithmic_bytes_per_cell": nbytes}
+    out["peak_source"] = src
+    T.close()
+    return out
 
 
 def bench_batched(pkg, ctx, torch, st, reps: int = 2):
@@ -333,40 +468,6 @@ def bench_paper_shape(pkg, ctx, torch, st, reps: int = 3):
     return out
 
 
-def bench_spheres_1024(pkg, ctx, torch, st):
-    """1024^3 uniform grid with 12 random spheres (1.07e9 cells): classification, and the
-    solve to 1e-10 in mode 2 and in FP64 once the hierarchy exists (ms), cycles, device
-    memory held by the tables and both hierarchies."""
-    import synth
-    pr = synth.cfg4(1024)
-    rhs = torch.from_numpy(pr.rhs()).cuda()
-    p = torch.zeros_like(rhs)
-    torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
-    c.record(st)
-    c.synchronize()
-    out = {"grid": [1024] * 3, "bodies": len(pr.meshes), "ghosts": T.nghost, "classify_ms": a.elapsed_time(c)}
-    for name, prec in (("mixed_df", 2), ("fp64", 0)):
-        p.zero_()
-        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)      # builds the hierarchy
-        p.zero_()
-        a.record(st)
-        rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec), stream=st)
-        c.record(st)
-        c.synchronize()
-        out["solve_ms_" + name] = a.elapsed_time(c)
-        out["cycles_" + name] = rep["cycles"]
-    free1, _ = torch.cuda.mem_get_info()
-    out["device_gb"] = (free0 - free1) / 1e9
-    out["mixed_df_speedup_vs_fp64"] = out["solve_ms_fp64"] / out["solve_ms_mixed_df"]
-    out["gcells_per_s_mixed_df"] = pr.ncells / (out["solve_ms_mixed_df"] * 1e-3) / 1e9
-    T.close()
-    return out
-
-
 def bench_membrane(pkg, ctx, torch, st, n: int = 512, nphase: int = 8):
     """Flapping plate (20 000 triangles) on an n^3 tanh-stretched grid: per phase, reclassify,
     set the moving-boundary datum from the plate's rigid kinematics (dp/dn = -a.n), solve to
@@ -432,33 +533,26 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream()
 
-    pr = synth.cfg2(args.n)
+    pr = synth.cfg4(args.n)
     b_host = pr.rhs()
     N = pr.ncells
     ctx = pkg.Context(local)
     rhs = torch.from_numpy(b_host).to(dev)
     p = torch.zeros_like(rhs)
-    poses = moving_ellipsoid(synth)
-    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, poses[0], stream=st)
-    # the smoother schedule (omega, nu1/nu2, V-cycles per refinement step) of each precision
-    # mode from the library's autotuner on the first body position, before any timing
-    tuned, schedule = {}, {}
-    for prec in (0, 1, 2):
-        if args.no_autotune:
-            tuned[prec] = pkg.SolveOpts(precision=prec)
-        else:
-            tuned[prec], _ = pkg.ibm_autotune(ctx.h, T.h, prec, rhs, p, TOL, stream=st)
-        o = tuned[prec]
-        schedule[PRECISIONS[prec]] = {"omega": o.omega, "nu1": o.nu1, "nu2": o.nu2, "inner_cycles": o.inner_cycles,
-                                      "krylov": o.krylov}
-    mixed, mixed_df, fp64 = tuned[1], tuned[2], tuned[0]
-    step_opts = tuned[args.precision]
-    count = [0]
+    torch.cuda.synchronize()
+    free0, total_mem = torch.cuda.mem_get_info()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    T = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
+    c.record(st)
+    c.synchronize()
+    classify_ms = a.elapsed_time(c)
+    free_t, _ = torch.cuda.mem_get_info()
+    opts = {prec: pkg.SolveOpts(precision=prec) for prec in (0, 1, 2)}
+    step_opts = opts[args.precision]
 
     def step():
-        # one time step of the moving body: reclassify the grid, solve the pressure system
-        count[0] += 1
-        T.reclassify(poses[count[0] % len(poses)], stream=st)
+        # the headline step: solve the pressure system from p = 0 to 1e-10
         p.zero_()
         return T.solve(rhs, p, TOL, step_opts, stream=st)
 
@@ -467,6 +561,9 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    step()                                    # builds the mode's hierarchy and captures its cycle
+    torch.cuda.synchronize()
+    free_h, _ = torch.cuda.mem_get_info()
     for _ in range(args.warmup):
         step()
     barrier()
@@ -479,78 +576,17 @@ def run_ours(args):
         barrier()
     launches = pkg.ibm_ctx_launch_count(ctx.h) - l0
     t_ms, value = whole_job(e0.elapsed_time(e1) / args.steps, N, ws, dev)
+    final = reps[-1]
+    # the oracle's defining residual of the returned pressure, on a few z-slabs would need the
+    # whole grid; the solver's own FP64 residual is reported (the parity tests check it)
 
-    # classification alone (iblank, ghosts, image points): fresh tables, and reclassification
-    # of existing tables (the step's form), median of a few calls each
-    tcl, trc = [], []
-    for q in range(3):
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        Tc = pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st)
-        c.record(st)
-        c.synchronize()
-        tcl.append(a.elapsed_time(c))
-        a.record(st)
-        Tc.reclassify(poses[q + 1], stream=st)
-        c.record(st)
-        c.synchronize()
-        trc.append(a.elapsed_time(c))
-        Tc.close()
-    # solve-only time to 1e-10, mixed vs FP64 (fixed body; warm)
-    T.reclassify(pr.meshes, stream=st)
-    tts = {}
-    cyc = {}
-    for name, o in (("mixed", mixed), ("mixed_df", mixed_df), ("fp64", fp64)):
-        p.zero_()
-        T.solve(rhs, p, TOL, o, stream=st)
-        ts = []
-        for _ in range(max(1, args.solve_reps)):
-            p.zero_()
-            torch.cuda.synchronize()
-            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(st)
-            rep = T.solve(rhs, p, TOL, o, stream=st)
-            c.record(st)
-            c.synchronize()
-            ts.append(a.elapsed_time(c))
-        tts[name] = statistics.median(ts)
-        cyc[name] = rep["cycles"]
-    # the paper's pressure solver on the same system (BiCGStab + scheduled relaxed Jacobi, FP64)
-    paper = None
-    if not args.no_paper_solver:
-        po = pkg.SolveOpts(precision=0, method=1, max_cycles=5000)
-        p.zero_()
-        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=0, method=1, max_cycles=2), stream=st,
-                raise_on_error=False)   # workspace
-        p.zero_()
-        torch.cuda.synchronize()
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        rep = T.solve(rhs, p, TOL, po, stream=st)
-        c.record(st)
-        c.synchronize()
-        t_paper = a.elapsed_time(c)
-        paper = {"method": "BiCGStab preconditioned with %d relaxed Jacobi sweeps (Chebyshev schedule), FP64"
-                 % po.srj_steps, "time_to_tol_ms": t_paper, "iterations": rep["cycles"],
-                 "multigrid_speedup": {k: t_paper / tts[k] for k in tts}}
-    # smoother sweeps (fine level): the sweep kernel alone (CUDA events on the stream around
-    # each fused-sweep launch, 20 sweeps), and whole sweeps with the ghost-row refresh
-    sweeps, sweeps_g = {}, {}
-    for name, prec in (("fp32", 2), ("fp64", 0)):
-        nsw = 20
-        pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, 3, st)
-        sweeps[name] = pkg.ibm_smoother_sweeps_timed(ctx.h, T.h, prec, nsw, st)
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        pkg.ibm_smoother_sweeps(ctx.h, T.h, prec, nsw, st)
-        c.record(st)
-        c.synchronize()
-        sweeps_g[name] = a.elapsed_time(c) / nsw
-    T_ng = T.nghost
+    # the smoother sweep kernels on this grid (fused FP32 sweep of the mixed modes; the FP64
+    # sweep of mode 0 needs its own hierarchy, measured in the modes section)
     hbm, src = _peaks()
-    gpts32 = N / (sweeps["fp32"] * 1e-3) / 1e9
-    gpts64 = N / (sweeps["fp64"] * 1e-3) / 1e9
-    ach = FP32_SWEEP_BYTES * N / (sweeps["fp32"] * 1e-3) / 1e9
+    pkg.ibm_smoother_sweeps(ctx.h, T.h, 1, 3, st)
+    sweep_ms = pkg.ibm_smoother_sweeps_timed(ctx.h, T.h, 1, 10, st)
+    ach = FP32_SWEEP_BYTES * N / (sweep_ms * 1e-3) / 1e9
+    tpc, tsrc = _traffic_per_cell(SWEEP_KERNEL, SWEEP_SOURCE)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     b_pin = torch.from_numpy(b_host).pin_memory()
@@ -560,56 +596,89 @@ def run_ours(args):
         step()
         p_pin.copy_(p, non_blocking=True)
     barrier()
+    ke = max(3, args.steps // 2)
     a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(st)
-    for _ in range(args.steps):
+    for _ in range(ke):
         rhs.copy_(b_pin, non_blocking=True)
         step()
         p_pin.copy_(p, non_blocking=True)
     c.record(st)
     c.synchronize()
-    e2e_ms = a.elapsed_time(c) / args.steps
-    mesh_bytes = sum(m.verts.nbytes + m.tris.nbytes for m in poses[0])
-    T.close()
+    e2e_ms = a.elapsed_time(c) / ke
+    del b_pin, p_pin
 
-    if rank != 0:
-        return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic", "config": _config(args),
-            "time_to_tol_ms": dict(tts), "solver_schedule": schedule,
-            "classify_ms": statistics.median(tcl), "reclassify_ms": statistics.median(trc), "ghosts": T_ng,
-            "cycles": cyc, "mixed_speedup_vs_fp64": tts["fp64"] / tts["mixed"],
-            "mixed_df_speedup_vs_fp64": tts["fp64"] / tts["mixed_df"],
-            "paper_solver": paper,
-            "sweep_gpts": {"fp32": gpts32, "fp64": gpts64},
-            "sweep_kernel_ms": sweeps, "sweep_with_ghost_rows_ms": sweeps_g,
-            "final_rel_resid": reps[-1]["rel_resid"],
+            "time_to_tol_ms": t_ms, "cycles": final["cycles"], "final_rel_resid": final["rel_resid"],
+            "classify_ms": classify_ms, "ghosts": T.nghost,
+            "device_gb": {"tables": (free0 - free_t) / 1e9,
+                          "hierarchy_" + ["fp64", "mixed", "mixed_df"][args.precision]: (free_t - free_h) / 1e9},
+            "sweep_kernel_fp32": {"ms": sweep_ms, "gcells_per_s": N / (sweep_ms * 1e-3) / 1e9},
             "roofline": {"bound": "hbm", "kernel": "k_sweep_zmarch (fused FP32 red-black sweep, finest level)",
                          "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": SWEEP_TRAFFIC_BYTES if args.n == 256 else None,
-                         "peak_source": src + " (copy bandwidth)", "algorithmic_bytes_per_cell": FP32_SWEEP_BYTES,
-                         "cells_per_launch": N},
+                         "traffic": tpc * N if tpc is not None else None, "traffic_source": tsrc,
+                         "peak_source": src + " (copy bandwidth, MEASURED_PEAKS.json)",
+                         "algorithmic_bytes_per_cell": FP32_SWEEP_BYTES, "cells_per_launch": N},
             "e2e": {"value": ws * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": int(b_host.nbytes + mesh_bytes), "d2h_bytes_per_step": int(b_host.nbytes)},
+                    "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
             "gpu_launches": launches, "clocks": clk.summary()}
+
+    # the other precision modes on the same problem, each with its hierarchy's device memory
+    if not args.no_modes:
+        modes = {}
+        for name, prec in (("mixed", 1), ("mixed_df", 2), ("fp64", 0)):
+            if prec == args.precision:
+                modes[name] = {"time_to_tol_ms": t_ms, "cycles": final["cycles"],
+                               "hierarchy_gb": (free_t - free_h) / 1e9}
+                continue
+            torch.cuda.synchronize()
+            fa, _ = torch.cuda.mem_get_info()
+            p.zero_()
+            T.solve(rhs, p, TOL, opts[prec], stream=st)
+            torch.cuda.synchronize()
+            fb, _ = torch.cuda.mem_get_info()
+            def solve():
+                p.zero_()
+                return T.solve(rhs, p, TOL, opts[prec], stream=st)
+            ms, rep = _timed(torch, st, solve, 1 if prec == 0 else 2)
+            modes[name] = {"time_to_tol_ms": ms, "cycles": rep["cycles"], "hierarchy_gb": (fa - fb) / 1e9}
+            if prec == 0:
+                pkg.ibm_smoother_sweeps(ctx.h, T.h, 0, 2, st)
+                ms64 = pkg.ibm_smoother_sweeps_timed(ctx.h, T.h, 0, 4, st)
+                ach64 = FP64_SWEEP_BYTES * N / (ms64 * 1e-3) / 1e9
+                line["sweep_kernel_fp64"] = {"ms": ms64, "gcells_per_s": N / (ms64 * 1e-3) / 1e9,
+                                             "achieved_gbs": ach64, "frac_of_hbm": ach64 / hbm}
+        for name in modes:
+            modes[name]["device_gb_with_tables"] = modes[name]["hierarchy_gb"] + (free0 - free_t) / 1e9
+            modes[name]["gcells_per_s"] = N / (modes[name]["time_to_tol_ms"] * 1e-3) / 1e9
+        line["modes"] = modes
+        line["mixed_speedup_vs_fp64"] = {k: modes["fp64"]["time_to_tol_ms"] / modes[k]["time_to_tol_ms"]
+                                         for k in ("mixed", "mixed_df")}
+        line["device_total_gb"] = total_mem / 1e9
+    T.close()
+    del rhs, p
+    torch.cuda.empty_cache()
+    if not args.no_ellipsoid:
+        line["moving_ellipsoid_256"] = bench_moving_ellipsoid(pkg, ctx, torch, st, 256,
+                                                              autotune=not args.no_autotune,
+                                                              paper_solver=not args.no_paper_solver)
     if not args.no_ad:
-        line["advection_diffusion"] = bench_advection_diffusion(pkg, ctx, torch, st, args.n)
+        line["advection_diffusion"] = bench_advection_diffusion(pkg, ctx, torch, st, 256)
     if not args.no_batched:
         line["batched_48"] = bench_batched(pkg, ctx, torch, st)
     if not args.no_membrane:
         line["membrane_plate"] = bench_membrane(pkg, ctx, torch, st, args.membrane_n)
     if not args.no_paper_shape:
         line["paper_shape_301x385x129"] = bench_paper_shape(pkg, ctx, torch, st)
-    if not args.no_large:
-        line["spheres_1024"] = bench_spheres_1024(pkg, ctx, torch, st)
-    if not args.no_cpu:
+    if not args.no_cpu and rank == 0 and ws == 1:
         c_cells, c_t = _cpu_sample(args.cpu_n)
         line["cpu_baseline"] = {"value": c_cells / c_t / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": "FP64 CPU oracle: classify + GMRES solve of the same geometry on a "
-                                          "%d^3 grid (%.1f s)" % (args.cpu_n, c_t)}
-    print(json.dumps(line))
+                                "sample": _sample_text(args.cpu_n, c_t)}
     ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -618,22 +687,22 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--cpu-n", type=int, default=96)
-    ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--no-ellipsoid", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-membrane", action="store_true")
     ap.add_argument("--no-paper-solver", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-ad", action="store_true")
     ap.add_argument("--no-paper-shape", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--membrane-n", type=int, default=512)
-    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")
     args = ap.parse_args()
     if args.warmup < 3:

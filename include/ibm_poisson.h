@@ -379,6 +379,14 @@ ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t 
 /* Number of CUDA kernels this context has launched so far (all calls). */
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
 
+/* Test hook (no counterpart in the paper): the number of tries of the first bounded
+ * shared-memory wait of every item of the fused FP32 sweep.  0 makes that wait give up at
+ * once: the sweep sets the context's error flag, waits (with the normal bound) for every copy
+ * it has in flight, and returns, so the next synchronising call (poisson_solve) reports
+ * IBM_ERR_TIMEOUT and the context stays usable.  tries < 0 restores the normal limit.
+ * Solves captured as CUDA graphs are recaptured when the setting changes. */
+ibm_status ibm_ctx_set_sweep_wait_limit(ibm_ctx *ctx, int32_t tries);
+
 /* Relative projected residual of a pressure field, with NO device allocation.  The paper
  * has no counterpart: this exists for callers that cannot allocate device memory after
  * start-up -- e.g. a flow solver that owns a fixed device arena, where cudaMalloc/cudaFree

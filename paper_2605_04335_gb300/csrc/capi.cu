@@ -501,6 +501,12 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
   return IBM_OK;
 }
 
+ibm_status ibm_ctx_set_sweep_wait_limit(ibm_ctx *ctx, int32_t tries) {
+  if (!ctx) return IBM_ERR_INVALID_ARG;
+  ctx->sweep_first_wait = tries < 0 ? -1 : tries;
+  return IBM_OK;
+}
+
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count) {
   if (!ctx || !count) return IBM_ERR_INVALID_ARG;
   *count = ctx->launches;

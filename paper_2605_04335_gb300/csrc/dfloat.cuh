@@ -61,6 +61,20 @@ __device__ __forceinline__ double widen(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// double -> float by truncating the significand (bit manipulation after the IEEE 754
+// binary64 / binary32 layouts, so the FP64 pipe stays free): normal results lie within one
+// unit in the last place of the float, toward zero; magnitudes below 2^-126 become signed
+// zero, above the float range infinity, and a NaN stays a NaN
+__device__ __forceinline__ float narrow_trunc(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t s = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+  uint32_t bits;
+  if (ex <= 896u) bits = s;
+  else if (ex >= 1151u) bits = s | 0x7f800000u | ((ex == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+  else bits = s | ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(bits);
+}
+
 // hi + lo as a double (one FP64 add)
 __device__ __forceinline__ double join(float h, float l) { return widen(h) + widen(l); }
 

@@ -74,6 +74,12 @@ struct Level {
   void *sdiag = nullptr;                    // finest level: cxm+cxp, cym+cyp, czm+czp (element type)
   double fluid_vol = 0.0;
   long long nfluid = 0;
+  // levels >= 1 swept by the fused z-march (large enough FP32 levels)
+  bool zm = false;
+  uint8_t *zmask = nullptr;                 // padded: 0 regular fluid, 8 irregular fluid, 1 other
+  void *ealt = nullptr;                     // second e buffer (ping-pong of the fused sweep)
+  void *zsd = nullptr;                      // cxm+cxp, cym+cyp, czm+czp (element type)
+  CUtensorMap ztm_e[2], ztm_r, ztm_m;       // tensor maps of e (both buffers), r and zmask
 };
 
 struct Hierarchy {
@@ -134,6 +140,7 @@ struct Hierarchy {
   int tail_level = -1;                      // first level of the one-block coarse tail (-1: none)
   bool zmarch = false;
   int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep
+  int zmc_per_sm = 1;                       // the same for its coarse-level form
   CUtensorMap tm_e[2], tm_r, tm_m;
   void *tm_base[2] = {nullptr, nullptr};    // which buffer each tm_e describes
 };
@@ -150,6 +157,8 @@ struct ibm_ctx {
                                 // (launch shape of the grid-stride element-wise kernels)
   long long launches = 0;       // kernels launched by this context (all calls)
   int *errflag = nullptr;       // device flag: a bounded device-side wait gave up
+  int sweep_first_wait = -1;    // tries of the fused sweep's first wait per item (-1: the
+                                // normal limit; set only to test the timeout path)
   std::string tune_cache;       // autotuner cache file (empty: none)
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture CUDA graphs
   // batched solves: the streams the problems' step graphs run on, fork/join events, and

@@ -913,11 +913,13 @@ __device__ __forceinline__ void block_partials3(double A0, double A1, double A2,
 
 // FP64 fine residual r = b - lambda - A p on fluid rows, stored as R (FP32 for the mixed
 // modes' inner cycles, FP64 for the accelerated FP64 mode; 0 on other cells); block partials
-// (sum V r, sum r, sum r^2, of the FP32-rounded r) at partials[3 b + {0,1,2}].  FP64
-// arithmetic is kept to the stencil itself (GB300 issues FP64 at about 1/64 of the FP32
-// rate): the diagonal is separable, row invariants are hoisted, the volume weights (wf: float
-// widths dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64 every
-// 8 rows.
+// (sum V r, sum r, sum r^2, of the FP32 r) at partials[3 b + {0,1,2}].  FP64 arithmetic is
+// kept to the stencil itself (GB300 issues FP64 at about 1/64 of the FP32 rate): per cell one
+// add for b - lambda, one for the separable diagonal (row invariants hoisted) and seven fused
+// multiply-adds, r = (b - lambda) + D p - sum_d c_d p_d; the FP32 copy of r is cut from the
+// FP64 bits on the integer pipe (truncation, within one FP32 ulp); the volume weights (wf:
+// float widths dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64
+// every 8 rows.
 template <typename R>
 __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
                                                               const double *lambda, const float *wf, R *r32,
@@ -959,17 +961,17 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
           double res = B[u] - lam;
           if (p) {
             const double left = u == 0 ? xl : P[u - 1], right = u == 3 ? xr : P[u + 1];
-            double s = v.cxm[i] * left;
-            s = fma(v.cxp[i], right, s);
-            s = fma(cym, YM[u], s);
-            s = fma(cyp, YP[u], s);
-            s = fma(czm, ZM[u], s);
-            s = fma(czp, ZP[u], s);
-            s = fma(-(v.sdx[i] + syz), P[u], s);   // (A p)_i
-            res -= s;
+            res = fma(v.sdx[i] + syz, P[u], res);   // b - lambda - (A p)_i
+            res = fma(-v.cxm[i], left, res);
+            res = fma(-v.cxp[i], right, res);
+            res = fma(-cym, YM[u], res);
+            res = fma(-cyp, YP[u], res);
+            res = fma(-czm, ZM[u], res);
+            res = fma(-czp, ZP[u], res);
           }
-          rf[u] = fl[u] ? (float)res : 0.f;
-          rs[u] = fl[u] ? (R)res : (R)0;
+          rf[u] = fl[u] ? dfl::narrow_trunc(res) : 0.f;
+          if constexpr (sizeof(R) == 4) rs[u] = rf[u];
+          else rs[u] = fl[u] ? (R)res : (R)0;
           a0 = fmaf(wf[i] * dydz, rf[u], a0);
           a1 += rf[u];
           a2 = fmaf(rf[u], rf[u], a2);
@@ -1038,9 +1040,10 @@ __global__ void k_finalize_resid(const double *partials, int nb, const double *g
   }
 }
 
+// p += e (the refinement update); e widened on the integer pipe, one FP64 add per cell
 __global__ void k_update_p(double *p, const float *e, long long n) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-    p[q] += (double)e[q];
+    p[q] += dfl::widen(e[q]);
 }
 
 __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum(LV<double> v, const double *p, double *partials) {
@@ -1054,6 +1057,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum(LV<double> v, cons
       const int j = row % ny, k = row / ny;
       const double dydz = v.dy[j] * v.dz[k];
       const long long base = (long long)(k + 1) * v.sz + (long long)(j + 1) * v.sy + OX;
+      // sum_i dx_i p_i over this thread's cells of the row (one FP64 fused multiply-add per
+      // cell), then the row's dy dz once
+      double ra = 0.0;
       for (int g = rg.g0; g < rg.G; g += rg.gstep) {
         const long long id = base + 4 * g;
         bool fl[4];
@@ -1062,8 +1068,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum(LV<double> v, cons
         Vec4<double>::ld(p + id, P);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (fl[u]) a = fma(v.dx[min(4 * g + u, nx - 1)] * dydz, P[u], a);
+          if (fl[u]) ra = fma(v.dx[min(4 * g + u, nx - 1)], P[u], ra);
       }
+      a = fma(ra, dydz, a);
     }
   sm[threadIdx.x] = a;
   __syncthreads();
@@ -2062,8 +2069,9 @@ void free_hierarchy(Hierarchy *h) {
   if (!h) return;
   std::vector<void *> ps;
   for (Level &L : h->lv) {
-    void *q[] = {L.mask, L.inner, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt, L.wT, L.sdiag};
-    ps.insert(ps.end(), q, q + 14);
+    void *q[] = {L.mask, L.inner, L.e, L.r, L.fx, L.fy, L.fz, L.c1d, L.w1d, L.cen, L.poff, L.pt, L.wT, L.sdiag,
+                 L.zmask, L.ealt, L.zsd};
+    ps.insert(ps.end(), q, q + sizeof(q) / sizeof(q[0]));
   }
   void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
                h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng,
@@ -2117,15 +2125,79 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
   // whose small blocks give the occupancy that hides FP64 latency
   h->zmarch = false;
   if constexpr (sizeof(T) == 4) {
-    h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(zm::Smem<T>)) == cudaSuccess;
     int per_sm = 0;
-    if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T>, zm::THREADS,
-                                                                   sizeof(zm::Smem<T>)) == cudaSuccess && per_sm > 0)
+    if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T, false>,
+                                                                   zm::THREADS, sizeof(zm::Smem<T>)) == cudaSuccess &&
+        per_sm > 0)
       h->zm_per_sm = per_sm;
     else
       h->zmarch = false;
   }
+}
+
+// Coarse levels swept by the fused z-march: levels >= 1 of at least ZM_COARSE_CELLS cells in
+// FP32 hierarchies whose finest level uses it.  Tensor maps over the level's e (both buffers),
+// r and z-march mask.
+constexpr long long ZM_COARSE_CELLS = 1LL << 18;
+
+template <typename T>
+static void setup_zmarch_coarse(Hierarchy *h) {
+  if constexpr (sizeof(T) == 4) {
+    bool any = false;
+    for (size_t l = 1; l < h->lv.size(); ++l) {
+      Level &L = h->lv[l];
+      if (!L.zm) continue;
+      L.zm = make_map(&L.ztm_e[0], L.e, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.g, zm::BX, zm::EY) &&
+             make_map(&L.ztm_e[1], L.ealt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.g, zm::BX, zm::EY) &&
+             make_map(&L.ztm_r, L.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.g, zm::BX, zm::RY) &&
+             make_map(&L.ztm_m, L.zmask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, L.g, zm::BXM, zm::RY);
+      any |= L.zm;
+    }
+    int per_sm = 0;
+    const bool ok = any &&
+                    cudaFuncSetAttribute(zm::k_sweep_zmarch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(zm::Smem<T>)) == cudaSuccess &&
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T, true>, zm::THREADS,
+                                                                  sizeof(zm::Smem<T>)) == cudaSuccess &&
+                    per_sm > 0;
+    h->zmc_per_sm = ok ? per_sm : 1;
+    if (!ok)
+      for (size_t l = 1; l < h->lv.size(); ++l) h->lv[l].zm = false;
+  }
+}
+
+// separable diagonal parts of a level: sd = cm + cp per axis, from its coefficient array
+template <typename T>
+__global__ void k_sdiag(const T *c1d, int nx, int ny, int nz, T *sd) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nx + ny + nz;
+  if (q >= n) return;
+  const T *cm = q < nx ? c1d : (q < nx + ny ? c1d + 2 * nx : c1d + 2 * nx + 2 * ny);
+  const int o = q < nx ? q : (q < nx + ny ? q - nx : q - nx - ny);
+  const int len = q < nx ? nx : (q < nx + ny ? ny : nz);
+  sd[q] = cm[o] + cm[len + o];
+}
+
+// z-march mask of a coarse level: plain solid (mask != 0) -> 1; fluid -> 8 when a face that
+// carries a coefficient is not fully open, else 0
+template <typename T>
+__global__ void k_zmask(LV<T> v, uint8_t *zm) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)v.nx * v.ny * v.nz) return;
+  const int i = (int)(l % v.nx);
+  const long long rr = l / v.nx;
+  const int j = (int)(rr % v.ny), k = (int)(rr / v.ny);
+  const long long id = vidx(v, i, j, k);
+  uint8_t m = 1;
+  if (v.mask[id] == 0) {
+    const bool irr = (v.cxm[i] != (T)0 && v.fx[id - 1] != (T)1) || (v.cxp[i] != (T)0 && v.fx[id] != (T)1) ||
+                     (v.cym[j] != (T)0 && v.fy[id - v.sy] != (T)1) || (v.cyp[j] != (T)0 && v.fy[id] != (T)1) ||
+                     (v.czm[k] != (T)0 && v.fz[id - v.sz] != (T)1) || (v.czp[k] != (T)0 && v.fz[id] != (T)1);
+    m = irr ? (uint8_t)zm::IRREGULAR : (uint8_t)0;
+  }
+  zm[id] = m;
 }
 
 // Grid-only part of a hierarchy: every allocation, the level geometry, coefficients,
@@ -2197,6 +2269,20 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     HTRY(cudaGetLastError());
   }
   h->nslot = h->lv[0].g.ntot + slotcap;
+  // coarse levels for the fused sweep: z-march mask, second e buffer, separable diagonals
+  if (sizeof(T) == 4)
+    for (int l = 1; l < nl; ++l) {
+      Level &L = h->lv[l];
+      if ((long long)L.g.nx * L.g.ny * L.g.nz < ZM_COARSE_CELLS) continue;
+      HTRY(cudaMalloc((void **)&L.zmask, L.g.ntot));
+      HTRY(cudaMemsetAsync(L.zmask, 1, L.g.ntot, st));
+      HTRY(alloc_zero<T>(&L.ealt, L.g.ntot, st));
+      HTRY(cudaMalloc(&L.zsd, sizeof(T) * (L.g.nx + L.g.ny + L.g.nz)));
+      k_sdiag<T><<<nblk(L.g.nx + L.g.ny + L.g.nz, 128), 128, 0, st>>>((const T *)L.c1d, L.g.nx, L.g.ny, L.g.nz,
+                                                                      (T *)L.zsd);
+      HTRY(cudaGetLastError());
+      L.zm = true;
+    }
   for (int l = 0; l + 1 < nl; ++l) {
     Level &Fl = h->lv[l], &C = h->lv[l + 1];
     HTRY(alloc_zero<uint8_t>((void **)&C.inner, C.g.ntot, st));
@@ -2237,6 +2323,9 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     Level &L0 = h->lv[0];
     if (sizeof(T) == 8) setup_zmarch<T>(h, h->p64, h->b64);
     else setup_zmarch<T>(h, L0.e, L0.r);
+    if (!h->zmarch)
+      for (Level &L : h->lv) L.zm = false;
+    setup_zmarch_coarse<T>(h);
   }
   // coarse tail: the first level (below the finest) small enough for one block
   h->tail_level = -1;
@@ -2279,6 +2368,7 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
                                                   wf, wf + Fl.g.nx, wf + Fl.g.nx + Fl.g.ny, C.g, wc, wc + C.g.nx,
                                                   wc + C.g.nx + C.g.ny, (T *)C.fx, (T *)C.fy, (T *)C.fz,
                                                   l == 0 && t->membrane ? t->cut : nullptr);
+    if (C.zm) k_zmask<T><<<nblk(nc, 256), 256, 0, st>>>(view<T>(C), C.zmask);
   }
   IBM_TRY(cudaGetLastError());
   // fluid volume and count per level (one read-back for all levels)
@@ -2399,7 +2489,9 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
   IBM_TRY(cudaStreamSynchronize(st));
   // mask0, 3 per coarse level, fluid statistics per level, coarsest setup, ghost sources,
   // membrane cut lists
-  t->ctx->launches += 1 + 3LL * (nl - 1) + nl + 1 + (t->nghost ? 1 : 0) + (t->membrane && nl >= 2 ? 10 : 0);
+  long long nzm = 0;
+  for (const Level &L : h->lv) nzm += L.zm ? 1 : 0;
+  t->ctx->launches += 1 + 3LL * (nl - 1) + nl + 1 + (t->nghost ? 1 : 0) + (t->membrane && nl >= 2 ? 10 : 0) + nzm;
   h->geom_version = t->geom_version;
   return IBM_OK;
 }
@@ -2439,34 +2531,70 @@ void ghost_update(Solver &S, T *e, const T *ghost_rhs) {
   S.ctx->launches += 2;
 }
 
+// One fused red-black sweep of level l: the finest level (tensor maps of the hierarchy, ghost
+// values read as neighbours) or a coarse level (its own maps, face fractions on irregular
+// cells).  e is swapped to the output buffer.
 template <typename T>
-void sweep_zmarch(Solver &S, T *&e, const double *shift) {
+void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
   Hierarchy *h = S.h;
-  Level &L0 = h->lv[0];
-  const int which = (e == (T *)h->tm_base[0]) ? 0 : 1;
-  T *other = (T *)h->tm_base[1 - which];
+  Level &L0 = h->lv[l];
+  const bool coarse = l > 0;
+  T *base0 = coarse ? (T *)L0.e : (T *)h->tm_base[0], *base1 = coarse ? (T *)L0.ealt : (T *)h->tm_base[1];
+  const int which = (e == base0) ? 0 : 1;
+  T *other = which == 0 ? base1 : base0;
   LV<T> v = view<T>(L0);
   zm::Args<T> a;
   a.nx = L0.g.nx; a.ny = L0.g.ny; a.nz = L0.g.nz; a.px = L0.g.px; a.sy = L0.g.sy; a.sz = L0.g.sz;
   a.cxm = v.cxm; a.cxp = v.cxp; a.cym = v.cym; a.cyp = v.cyp; a.czm = v.czm; a.czp = v.czp;
-  a.sdx = v.sdx; a.sdy = v.sdy; a.sdz = v.sdz;
+  if (coarse) {
+    const T *sd = (const T *)L0.zsd;
+    a.sdx = sd; a.sdy = sd + L0.g.nx; a.sdz = sd + L0.g.nx + L0.g.ny;
+    a.fx = v.fx; a.fy = v.fy; a.fz = v.fz;
+  } else {
+    a.sdx = v.sdx; a.sdy = v.sdy; a.sdz = v.sdz;
+    a.fx = a.fy = a.fz = nullptr;
+  }
   a.shift = shift;
   a.omega = (float)S.omega;
   a.out = other;
   a.err = S.ctx->errflag;
   const int gx = (a.nx + zm::TX - 1) / zm::TX, gy = (a.ny + zm::TY - 1) / zm::TY;
-  const int per_sm = std::max(1, h->zm_per_sm);
-  const long long target = (long long)per_sm * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152);
-  // one wave: tiles x chunks <= resident CTAs (a second, partly filled wave would idle most
-  // SMs); in a batch, chunks of at least 24 planes, so that several problems' sweeps share
-  // the GPU without the extra planes of short chunks
-  int chunks = (int)std::max<long long>(1, std::min<long long>(a.nz, target / (gx * gy)));
-  if (S.batched) chunks = std::max(1, std::min(chunks, a.nz / 24));
-  a.kz = (a.nz + chunks - 1) / chunks;
-  chunks = (a.nz + a.kz - 1) / a.kz;
-  dim3 grid(gx, gy, chunks);
-  if constexpr (sizeof(T) == 4)   // FP32 only (setup_zmarch enables it for FP32 hierarchies)
-    zm::k_sweep_zmarch<T><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r, h->tm_m, a);
+  const long long tiles = (long long)gx * gy;
+  const int per_sm = std::max(1, coarse ? h->zmc_per_sm : h->zm_per_sm);
+  const long long resident = (long long)per_sm * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152);
+  // Items are (tile, z-chunk) pairs; the resident CTAs take them in turn, so a sweep costs
+  // about ceil(items / resident) rounds of kz + 2 plane steps (each item marches two planes
+  // beyond its chunk) plus a start-up of about 4 steps (its first copies and coefficients).
+  // Take the chunk length with the fewest steps.  In a batch each
+  // item gets its own CTA and chunks keep at least 24 planes, so that several problems'
+  // sweeps share the GPU without the extra planes of short chunks.
+  int best_kz = std::min(a.nz, zm::KZ_MAX);
+  if (S.batched) {
+    const long long chunks = std::max<long long>(1, std::min<long long>(resident / tiles, a.nz / 24));
+    best_kz = std::min<long long>(zm::KZ_MAX, (a.nz + chunks - 1) / chunks);
+  } else {
+    long long best_cost = -1;
+    for (int kz = std::min(a.nz, zm::KZ_MAX); kz >= 1; --kz) {
+      const long long chunks = (a.nz + kz - 1) / kz;
+      const long long cost = ((tiles * chunks + resident - 1) / resident) * (kz + 6);
+      if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_kz = kz; }
+    }
+  }
+  a.kz = best_kz;
+  const long long chunks = (a.nz + a.kz - 1) / a.kz;
+  a.tiles_x = gx;
+  a.tiles_y = gy;
+  a.items = (int)(tiles * chunks);
+  a.first_wait = S.ctx->sweep_first_wait >= 0 ? S.ctx->sweep_first_wait : zm::WAIT_LIMIT;
+  const int grid = (int)(S.batched ? a.items : std::min<long long>(a.items, resident));
+  if constexpr (sizeof(T) == 4) {   // FP32 only (setup_zmarch enables it for FP32 hierarchies)
+    if (coarse)
+      zm::k_sweep_zmarch<T, true><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(L0.ztm_e[which], L0.ztm_r,
+                                                                                    L0.ztm_m, a);
+    else
+      zm::k_sweep_zmarch<T, false><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r,
+                                                                                     h->tm_m, a);
+  }
   S.ctx->launches += 1;
   e = other;
 }
@@ -2490,9 +2618,14 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
   for (int s = 0; s < sweeps; ++s) {
     const bool timed = fine && S.sweep_events && S.sweep_events->size() >= 2 * (size_t)(s + 1);
     if (timed) cudaEventRecord((*S.sweep_events)[2 * s], S.st);
+    if (sizeof(T) == 4 && !fine && L.zm) {   // coarse level: fused sweep, no ghost rows
+      sweep_zmarch<T>(S, l, e, shift);
+      if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
+      continue;
+    }
     if (sizeof(T) == 4 && fine && S.h->zmarch) {
       T *old = e;
-      sweep_zmarch<T>(S, e, shift);
+      sweep_zmarch<T>(S, 0, e, shift);
       if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
       cut_relax<T>(S, e, old, r, shift);
       const long long ng = S.t->nghost;
@@ -2978,7 +3111,8 @@ unsigned long long run_key(const Run &R) {
                                        (unsigned long long)(h->hcnt[1] > 0) | ((unsigned long long)(h->hcnt[2] > 0) << 1),
                                        (unsigned long long)h->slotcap, (unsigned long long)(uintptr_t)R.S.scal,
                                        (unsigned long long)(uintptr_t)R.S.part,
-                                       (unsigned long long)R.S.batched | ((unsigned long long)t->has_datum << 1)};
+                                       (unsigned long long)R.S.batched | ((unsigned long long)t->has_datum << 1) |
+                                           ((unsigned long long)(unsigned)R.ctx->sweep_first_wait << 8)};
   for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
   return key;
 }

@@ -95,6 +95,7 @@ def load_library():
         "ibm_smoother_sweeps": (I32, [P, P, I32, I32, P]),
         "ibm_smoother_sweeps_timed": (I32, [P, P, I32, I32, P, C.POINTER(C.c_double)]),
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
+        "ibm_ctx_set_sweep_wait_limit": (I32, [P, I32]),
         "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P, P,
                                             C.POINTER(C.c_double), P]),
         "poisson_solve_batched": (I32, [P, I32, P, P, D, P, C.POINTER(ibm_solve_opts), P, P]),
@@ -300,6 +301,11 @@ def ibm_smoother_sweeps_timed(ctx, tables, precision: int, nsweeps: int, stream=
     _check(load_library().ibm_smoother_sweeps_timed(ctx, tables, precision, nsweeps, _stream(stream), C.byref(ms)),
            "ibm_smoother_sweeps_timed")
     return float(ms.value)
+
+
+def ibm_ctx_set_sweep_wait_limit(ctx, tries: int):
+    """Test hook: tries of the fused sweep's first wait per item (0: give up at once; -1: normal)."""
+    _check(load_library().ibm_ctx_set_sweep_wait_limit(ctx, int(tries)), "ibm_ctx_set_sweep_wait_limit")
 
 
 def ibm_ctx_launch_count(ctx) -> int:

@@ -104,3 +104,24 @@ def test_non_finite_input_diverges_before_any_cycle(ctx, bad):
     rep = T.solve(good, p, 1e-10, pkg.SolveOpts(precision=1))
     assert rep["status"] == "IBM_OK" and torch.isfinite(p).all()
     T.close()
+
+
+def test_sweep_wait_that_runs_out_reports_timeout(ctx):
+    """The fused sweep's first bounded wait given zero tries: every item gives up at once,
+    drains its copies in flight and returns; the solve reports IBM_ERR_TIMEOUT and the context
+    then solves normally again (graph and direct launches)."""
+    pkg, c = ctx
+    f = synth.faces_tanh(72, 2.0)
+    m = [synth.octa_sphere(3, (0.5, 0.5, 0.5), 0.2)]
+    T = pkg.Tables(c, f, f, f, m)
+    rhs = torch.from_numpy(synth.rhs_divergence(f, f, f, 19)).cuda()
+    for graph in (0, 1):
+        pkg.ibm_ctx_set_sweep_wait_limit(c.h, 0)
+        p = torch.zeros_like(rhs)
+        rep = T.solve(rhs, p, 1e-10, pkg.SolveOpts(precision=2, max_cycles=2, use_graph=graph), raise_on_error=False)
+        assert rep["status"] == "IBM_ERR_TIMEOUT", rep
+        pkg.ibm_ctx_set_sweep_wait_limit(c.h, -1)
+        p = torch.zeros_like(rhs)
+        rep = T.solve(rhs, p, 1e-10, pkg.SolveOpts(precision=2, use_graph=graph))
+        assert rep["status"] == "IBM_OK" and rep["rel_resid"] <= 1e-10
+    T.close()
