@@ -376,6 +376,25 @@ ibm_status ibm_smoother_sweeps(ibm_ctx *ctx, const ibm_tables *t, int32_t precis
 ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t precision,
                                      int32_t nsweeps, void *stream, double *kernel_ms);
 
+/* Test hook: the finest level's smoother applied to caller data.  e_dev and r_dev
+ * (double[ncell], [k][j][i], device, read only) are loaded into the finest level of the
+ * hierarchy of the given precision (built when missing), rounded to its type (FP32 for
+ * precision 1 and 2), and nsweeps sweeps with over-relaxation omega run exactly as inside a
+ * V-cycle: each fluid cell of one colour, red ((i + j + k) even) then black, takes
+ *   e_i += omega ((A e)_i - (r_i - mu)) / D_i,   D_i = -A_ii
+ * (A the fluid rows of the pressure operator, Sec. "Governing Equations and Numerical
+ * Methods"; a row's neighbours include ghost values), the cut cells of membranes follow, and
+ * the ghost rows are refreshed, Jacobi among ghosts: e_G = sum_k w_k e_k + r_G.  e_out_dev
+ * (double[ncell], device, caller-owned) receives the finest level's e; other cells keep
+ * their loaded values.  The solver's work arrays are overwritten (each solve initialises
+ * them again).  Waits for the stream.  IBM_ERR_INVALID_ARG for a null pointer, omega outside
+ * (0, 2), nsweeps < 0 or a non-finite mu; IBM_ERR_TIMEOUT if a bounded wait of the fused
+ * sweep gave up.  The paper has no counterpart: it checks the smoother against a direct
+ * restatement of Gauss-Seidel. */
+ibm_status ibm_smoother_apply(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps,
+                              double omega, const double *e_dev, const double *r_dev, double mu,
+                              double *e_out_dev, void *stream);
+
 /* Number of CUDA kernels this context has launched so far (all calls). */
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
 

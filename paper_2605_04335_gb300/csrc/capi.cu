@@ -32,6 +32,8 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
                       const ibm_solve_opts *opts, ibm_solve_info *info, cudaStream_t st);
 ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st,
                        double *kernel_ms);
+ibm_status smoother_apply_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, double omega,
+                               const double *e_in, const double *r_in, double mu, double *e_out, cudaStream_t st);
 ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st);
 ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st);
 ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_user, const double *ub,
@@ -392,6 +394,16 @@ ibm_status ibm_smoother_sweeps_timed(ibm_ctx *ctx, const ibm_tables *t, int32_t 
     return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::sweeps_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, (cudaStream_t)stream, kernel_ms);
+}
+
+ibm_status ibm_smoother_apply(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, int32_t nsweeps, double omega,
+                              const double *e_dev, const double *r_dev, double mu, double *e_out_dev, void *stream) {
+  if (!ctx || !t || t->ctx != ctx || precision < 0 || precision > 2 || nsweeps < 0 || !(omega > 0.0 && omega < 2.0) ||
+      !e_dev || !r_dev || !e_out_dev || !std::isfinite(mu))
+    return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return ibm::smoother_apply_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, omega, e_dev, r_dev, mu,
+                                  e_out_dev, (cudaStream_t)stream);
 }
 
 static bool valid_opts(const ibm_solve_opts &o) {

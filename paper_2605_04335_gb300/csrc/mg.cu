@@ -3608,6 +3608,27 @@ ibm_status solve_bicgstab_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, d
   return result;
 }
 
+// user [k][j][i] doubles <-> a padded level array of type T (padding cells untouched)
+template <typename T>
+__global__ void k_load_level(const double *src, LevelGeom g, T *dst) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < n; l += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(l % g.nx);
+    const long long r = l / g.nx;
+    dst[pidx(g, i, (int)(r % g.ny), (int)(r / g.ny))] = (T)src[l];
+  }
+}
+
+template <typename T>
+__global__ void k_store_level(const T *src, LevelGeom g, double *dst) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < n; l += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(l % g.nx);
+    const long long r = l / g.nx;
+    dst[l] = (double)src[pidx(g, i, (int)(r % g.ny), (int)(r / g.ny))];
+  }
+}
+
 ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, cudaStream_t st,
                        double *kernel_ms) {
   ibm_status s = build_hierarchy(t, precision, st);
@@ -3643,6 +3664,36 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
   destroy();
   if (ce != cudaSuccess) return check(ce, "smoother sweeps");
   return IBM_OK;
+}
+
+// the finest level's smoother on caller data: e and r loaded (rounded to the hierarchy's
+// type), the shift mu in a context scalar, nsweeps sweeps as inside a V-cycle with the ghost
+// rows' right-hand side r, e read back
+ibm_status smoother_apply_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, double omega,
+                               const double *e_in, const double *r_in, double mu, double *e_out, cudaStream_t st) {
+  ibm_status s = build_hierarchy(t, precision, st);
+  if (s != IBM_OK) return s;
+  Hierarchy *h = t->hier[precision];
+  Solver S{ctx, t, h, st, 1, 1, omega, h->dncoarse};
+  S.scal = ctx->scal;
+  S.part = ctx->partials;
+  Level &L0 = h->lv[0];
+  IBM_TRY(cudaMemcpyAsync(ctx->scal + S_MU, &mu, sizeof(double), cudaMemcpyHostToDevice, st));
+  if (precision == 0) {
+    k_load_level<double><<<ctx->wave, 256, 0, st>>>(e_in, L0.g, h->p64);
+    k_load_level<double><<<ctx->wave, 256, 0, st>>>(r_in, L0.g, h->b64);
+    smooth_level<double>(S, 0, h->p64, h->b64, ctx->scal + S_MU, true, h->b64, nsweeps);
+    k_store_level<double><<<ctx->wave, 256, 0, st>>>(h->p64, L0.g, e_out);
+  } else {
+    float *&e = reinterpret_cast<float *&>(L0.e);
+    k_load_level<float><<<ctx->wave, 256, 0, st>>>(e_in, L0.g, e);
+    k_load_level<float><<<ctx->wave, 256, 0, st>>>(r_in, L0.g, (float *)L0.r);
+    smooth_level<float>(S, 0, e, (const float *)L0.r, ctx->scal + S_MU, true, (const float *)L0.r, nsweeps);
+    k_store_level<float><<<ctx->wave, 256, 0, st>>>(e, L0.g, e_out);
+  }
+  ctx->launches += 3;
+  IBM_TRY(cudaGetLastError());
+  return read_errflag(ctx, IBM_OK, st);
 }
 
 }  // namespace ibm

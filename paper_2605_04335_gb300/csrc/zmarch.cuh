@@ -11,18 +11,19 @@
 // result is exactly one red half-sweep followed by one black half-sweep (deterministic,
 // independent of the tiling).
 //
-// Warps 0..7 own the tile: each thread keeps two strips of 4 consecutive x-cells (rows y and
-// y + SR) in registers for planes q-2 .. q+1 (the rhs and mask are read from shared memory
-// by each pass).  Red
+// Warps 0..6 own the tile, one row per warp and strip set: each thread keeps two strips of 4
+// consecutive x-cells (rows y and y + SR) in registers for planes q-2 .. q+1 (the rhs and
+// mask are read from shared memory by each pass).  Red
 // results go back to the plane's buffer (their y-neighbours in other warps read them in the
 // next step) and stay in the registers (the strip's black update two steps later reads its
 // z-1 neighbours there); black results go only to registers and global memory.
 // x-neighbours across strips move by warp shuffle; the two edge lanes of a row read the
-// ring from shared memory at a per-lane address, so the update is branch-free.  Warp 0 also
-// updates the ring's 32 row strips and warp 1 its 32 column cells (coefficients from a
-// shared table), warp 2 issues the copies.  A red update reads only black cells and a black
-// update only red ones, so the in-place writes never change a value another thread reads in
-// the same step: one barrier per step suffices.
+// ring from shared memory at a per-lane address, so the update is branch-free.  Warp 7 owns
+// the ring -- its two rows of 32 strips and its 14 red column cells per plane (coefficients
+// from a shared table) -- and issues the copies; its work per step is below a tile warp's,
+// so no warp of the tile waits for it at the barrier.  A red update reads only black cells and
+// a black update only red ones, so the in-place writes never change a value another thread
+// reads in the same step: one barrier per step suffices.
 //
 // Coarse levels (COARSE = true) carry face fractions (the area fraction of open fine faces)
 // in their coefficients.  Their mask here is the z-march mask: 0 for a regular fluid cell
@@ -43,23 +44,27 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 namespace ibm {
 namespace zm {
 
-constexpr int TX = 64;          // tile width (cells); multiple of 16
-constexpr int SR = 16;          // rows of one strip set (a multiple of 4)
+constexpr int TX = 128;         // tile width (cells): 32 lanes x 4 cells
+constexpr int SR = 7;           // rows of one strip set: one per tile warp
 constexpr int NS = 2;           // interior strips per thread: rows y and y + SR
 constexpr int TY = SR * NS;     // tile height
 constexpr int BX = TX + 8;      // staged width of e and rhs: x in [-4, TX + 4)
 constexpr int BXM = TX + 16;    // staged width of the mask (an 8-bit box row must be 16-byte multiple)
 constexpr int EY = TY + 4;      // e rows: y in [-2, TY + 2)
 constexpr int RY = TY + 2;      // rhs / mask rows: y in [-1, TY + 1)
-constexpr int THREADS = (TX / 4) * SR;   // 8 warps; NS interior strips per thread
+constexpr int TILE_WARPS = SR;                 // one row of strips each
+constexpr int RING_WARP = TILE_WARPS;          // the ring and the copies
+constexpr int THREADS = (TILE_WARPS + 1) * 32;
 constexpr int MIN_CTAS = 2;
-constexpr int ROW_WARP = 0, COL_WARP = 1, ISSUER = 64;   // ring rows, ring columns, copies
-static_assert(TX == 64 && TY == 32 && THREADS == 256, "warp 0's lanes cover 2 x 16 ring strips, warp 1's 2 x 16 cells");
-static_assert(SR % 4 == 0 && NS == 2, "strips at rows y and y + SR share the colour parity");
+constexpr int COL_LANES = TY;                  // ring warp lanes with a column cell (pairs of rows)
+static_assert(TX == 128 && THREADS == 256 && TY % 2 == 0 && COL_LANES <= 32,
+              "a warp's 32 lanes cover one row of the tile; the ring warp's lanes its column cells");
+static_assert(NS == 2 && SR % 2 == 1, "strip 1 lies an odd number of rows below strip 0: the other colour");
 constexpr int WAIT_LIMIT = 1 << 22;
 constexpr int KZ_MAX = 256;     // planes per item at most (the z-coefficient table)
 
@@ -81,7 +86,7 @@ struct Smem {
   alignas(128) T r[NR][RSZ];
   alignas(128) uint8_t m[NR][MSZ];
   alignas(16) float4 zc[KZ_MAX + 4];   // czm, czp, czm + czp of planes k0 - 2 .. k1 + 1
-  alignas(16) float cc[32][16];       // ring lanes' coefficients (warp 0: strip row; warp 1: column)
+  alignas(16) float cc[32][20];       // ring warp lanes' coefficients (ring rows, column cell)
   alignas(8) uint64_t bar_e[NE];
   alignas(8) uint64_t bar_r[NR];
 };
@@ -177,6 +182,9 @@ __device__ __forceinline__ float relax_frac(const Args<T> &a, long long id, floa
   return D > 0.f ? relax1(c, w, ea, n, s, zm, zp, c0, c1, c2, c3, c4, c5, D, rsh, om) : c;
 }
 
+using U0 = std::integral_constant<int, 0>;   // a strip's colour: u of its first cell to relax
+using U1 = std::integral_constant<int, 1>;
+
 // x coefficients of a strip's four cells
 struct XCoef {
   float4 m, p, s;   // cxm, cxp, cxm + cxp
@@ -192,7 +200,7 @@ __device__ __forceinline__ void relax_strip(float4 &C, float west, float east, c
                                             const float4 &Zm, const float4 &Zp, const float4 &R, unsigned mm,
                                             const XCoef &X, float cym, float cyp, float syz, float czm, float czp,
                                             float sh, float om, const Args<T> &a, long long gid) {
-  float *c0 = UA == 0 ? &C.x : &C.y, *c1 = UA == 0 ? &C.z : &C.w;
+  const float c0 = UA == 0 ? C.x : C.y, c1 = UA == 0 ? C.z : C.w;
   const float w0 = UA == 0 ? west : C.x, e0 = UA == 0 ? C.y : C.z;
   const float w1 = UA == 0 ? C.y : C.z, e1 = UA == 0 ? C.w : east;
   const float n0 = UA == 0 ? N.x : N.y, n1 = UA == 0 ? N.z : N.w, s0 = UA == 0 ? S.x : S.y, s1 = UA == 0 ? S.z : S.w;
@@ -202,23 +210,30 @@ __device__ __forceinline__ void relax_strip(float4 &C, float west, float east, c
   const float xm0 = UA == 0 ? X.m.x : X.m.y, xm1 = UA == 0 ? X.m.z : X.m.w;
   const float xp0 = UA == 0 ? X.p.x : X.p.y, xp1 = UA == 0 ? X.p.z : X.p.w;
   const float xs0 = UA == 0 ? X.s.x : X.s.y, xs1 = UA == 0 ? X.s.z : X.s.w;
-  float v0 = relax1(*c0, w0, e0, n0, s0, zm0, zp0, xm0, xp0, cym, cyp, czm, czp, xs0 + syz, r0, om);
-  float v1 = relax1(*c1, w1, e1, n1, s1, zm1, zp1, xm1, xp1, cym, cyp, czm, czp, xs1 + syz, r1, om);
+  float v0 = relax1(c0, w0, e0, n0, s0, zm0, zp0, xm0, xp0, cym, cyp, czm, czp, xs0 + syz, r0, om);
+  float v1 = relax1(c1, w1, e1, n1, s1, zm1, zp1, xm1, xp1, cym, cyp, czm, czp, xs1 + syz, r1, om);
   unsigned b0 = (mm >> (8 * UA)) & 0xffu, b1 = (mm >> (8 * (UA + 2))) & 0xffu;
   if constexpr (COARSE) {
     if (__any_sync(0xffffffffu, b0 == IRREGULAR || b1 == IRREGULAR)) {
       if (b0 == IRREGULAR) {
-        v0 = relax_frac(a, gid + UA, *c0, w0, e0, n0, s0, zm0, zp0, xm0, xp0, cym, cyp, czm, czp, r0, om);
+        v0 = relax_frac(a, gid + UA, c0, w0, e0, n0, s0, zm0, zp0, xm0, xp0, cym, cyp, czm, czp, r0, om);
         b0 = 0u;
       }
       if (b1 == IRREGULAR) {
-        v1 = relax_frac(a, gid + UA + 2, *c1, w1, e1, n1, s1, zm1, zp1, xm1, xp1, cym, cyp, czm, czp, r1, om);
+        v1 = relax_frac(a, gid + UA + 2, c1, w1, e1, n1, s1, zm1, zp1, xm1, xp1, cym, cyp, czm, czp, r1, om);
         b1 = 0u;
       }
     }
   }
-  *c0 = b0 ? *c0 : v0;
-  *c1 = b1 ? *c1 : v1;
+  v0 = b0 ? c0 : v0;
+  v1 = b1 ? c1 : v1;
+  if constexpr (UA == 0) {
+    C.x = v0;
+    C.z = v1;
+  } else {
+    C.y = v0;
+    C.w = v1;
+  }
 }
 
 template <typename T>
@@ -256,8 +271,9 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
   static_assert(sizeof(T) == 4, "the fused sweep runs in FP32");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<float> &s = *reinterpret_cast<Smem<float> *>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, l16 = lane & 15;
-  const bool issuer = tid == ISSUER;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool ring = warp == RING_WARP;
+  const bool issuer = ring && lane == 0;
   if (tid == 0) {
     for (int b = 0; b < NE; ++b) mbar_init(&s.bar_e[b], 1);
     for (int b = 0; b < NR; ++b) mbar_init(&s.bar_r[b], 1);
@@ -271,14 +287,15 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
   // also keeps which slots have a copy in flight that it has not yet seen land
   unsigned pe = 0, pr = 0, pend_e = 0, pend_r = 0;
   bool bad = false;
-  // this thread's strips: warp w takes rows r and r + 2 (lanes 0-15 and 16-31),
-  // r = 4 (w / 2) + (w mod 2), so a warp's strips share one colour parity; strip t lies SR t
-  // rows below strip 0.  Warp 0 lanes also own the ring strip at row -1 (lanes 0-15) or TY
-  // (16-31), same x; warp 1 lanes the column cell x = -1 (lanes 0-15) or TX (16-31), the red
-  // one of rows 2 l16 and 2 l16 + 1.
-  const int xs = 4 * l16;
-  const int ys = 4 * (warp >> 1) + (warp & 1) + 2 * (lane >> 4);
+  // this thread's strips: tile warp w takes row w (strip 0) and row w + SR (strip 1), lane l
+  // the cells 4 l .. 4 l + 3, so the lanes of a warp share each strip's colour parity.  The
+  // ring warp's lanes take the ring strips at x = 4 l of rows -1 and TY, and lanes
+  // l < COL_LANES the column cell x = -1 (l < TY / 2) or TX (the rest), the red one of the
+  // pair of rows 2 (l mod TY / 2), 2 (l mod TY / 2) + 1.
+  const int xs = 4 * lane;
+  const int ys = ring ? 0 : warp;
   const int ie0 = (ys + 2) * BX + (xs + 4), ir0 = (ys + 1) * BX + (xs + 4), im0 = (ys + 1) * BXM + (xs + 4);
+  const int eoff = lane == 0 ? -1 : 4;   // edge lanes: the ring cell beside the strip
   const int first_wait = a.first_wait;
   const int tiles = a.tiles_x * a.tiles_y;
 
@@ -300,24 +317,25 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
       cyp[t] = jok ? a.cyp[gj] : 0.f;
       sy[t] = jok ? a.sdy[gj] : 0.f;
     }
-    // warp 0: its ring strip's row coefficients and invalid bytes (slots 0-3 of the table)
-    if (warp == ROW_WARP) {
-      const int gj = y0 + (lane < 16 ? -1 : TY);
-      const bool jok = gj >= 0 && gj < a.ny;
-      float *cc = s.cc[lane];
-      cc[0] = jok ? a.cym[gj] : 0.f;
-      cc[1] = jok ? a.cyp[gj] : 0.f;
-      cc[2] = jok ? a.sdy[gj] : 0.f;
-      reinterpret_cast<unsigned *>(cc)[3] = invalid_bytes(x0 + xs, a.nx, jok);
-    }
-    // warp 1: its column cell's coefficients (x fixed, the two rows of its pair): cxm, cxp,
-    // sdx, then cym, cyp, sdy of rows 2 l16 and 2 l16 + 1, then which rows are in the grid
-    // (slots 4-13 of the table)
-    if (warp == COL_WARP) {
-      const int cgi = x0 + (lane < 16 ? -1 : TX), gj0 = y0 + 2 * l16;
-      const bool cxok = cgi >= 0 && cgi < a.nx;
+    // ring warp: its ring strips' row coefficients and invalid bytes (slots 0-3: row -1,
+    // 4-7: row TY), then its column cell's (slots 8-17): cxm, cxp, sdx, then cym, cyp, sdy of
+    // the pair's two rows, then which rows are in the grid
+    if (ring) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gj = y0 + (h == 0 ? -1 : TY);
+        const bool jok = gj >= 0 && gj < a.ny;
+        float *cc = s.cc[lane] + 4 * h;
+        cc[0] = jok ? a.cym[gj] : 0.f;
+        cc[1] = jok ? a.cyp[gj] : 0.f;
+        cc[2] = jok ? a.sdy[gj] : 0.f;
+        reinterpret_cast<unsigned *>(cc)[3] = invalid_bytes(x0 + xs, a.nx, jok);
+      }
+      const int pr_ = lane % (TY / 2);
+      const int cgi = x0 + (lane < TY / 2 ? -1 : TX), gj0 = y0 + 2 * pr_;
+      const bool cxok = lane < COL_LANES && cgi >= 0 && cgi < a.nx;
       const bool ok0 = cxok && gj0 < a.ny, ok1 = cxok && gj0 + 1 < a.ny;
-      float *cc = s.cc[lane] + 4;
+      float *cc = s.cc[lane] + 8;
       cc[0] = cxok ? a.cxm[cgi] : 0.f;
       cc[1] = cxok ? a.cxp[cgi] : 0.f;
       cc[2] = cxok ? a.sdx[cgi] : 0.f;
@@ -408,110 +426,124 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
       const float4 zq = s.zc[q - (k0 - 2)], zb = s.zc[q - 1 - (k0 - 2)];
       const float zmr = zq.x, zpr = zq.y, szr = zq.z, zmb = zb.x, zpb = zb.y, szb = zb.z;
       const bool red = q >= 0 && q < a.nz;
-      const bool parq = ((y0 + ys + q) & 1) == 0;   // x0 + xs is even: UA = (y0 + ys + q) & 1
+      // x0 + xs is even: strip t relaxes u = (y0 + ys + SR t + q) & 1 (SR is odd, so strip 1 has
+      // the other colour of strip 0)
+      const bool parq = ((y0 + ys + q) & 1) == 0;
       float4 U[NS];   // the strips in plane q+1
 #pragma unroll
-      for (int t = 0; t < NS; ++t) {
+      for (int t = 0; t < NS; ++t) U[t] = ld4(Pp + ie0 + SR * t * BX);
+      // red cells of strip t of plane q (ua: its colour's u, a compile-time constant):
+      // x-edges from the adjacent lanes, or the ring at the edges
+      auto red_strip = [&](auto ua, const int t) {
         const int ie = ie0 + SR * t * BX;
-        U[t] = ld4(Pp + ie);
-        if (red) {
-          // red cells of plane q: x-edges from the adjacent lanes, or the ring at the edges
-          const float ep = P[ie + (l16 == 0 ? -1 : 4)];
-          float w = __shfl_up_sync(0xffffffffu, C0[t].w, 1, 16);
-          float e = __shfl_down_sync(0xffffffffu, C0[t].x, 1, 16);
-          w = l16 == 0 ? ep : w;
-          e = l16 == 15 ? ep : e;
-          const float4 N = ld4(P + ie - BX), S = ld4(P + ie + BX);
-          const float4 Rr = ld4(R + ir0 + SR * t * BX);
-          const unsigned mm = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM) | inval[t];
-          const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
-          if (parq)
-            relax_strip<0, COARSE>(C0[t], w, e, N, S, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t], sy[t] + szr, zmr, zpr,
-                                   sh, om, a, gid);
+        const float ep = P[ie + eoff];
+        float w = __shfl_up_sync(0xffffffffu, C0[t].w, 1);
+        float e = __shfl_down_sync(0xffffffffu, C0[t].x, 1);
+        w = lane == 0 ? ep : w;
+        e = lane == 31 ? ep : e;
+        const float4 N = ld4(P + ie - BX), S = ld4(P + ie + BX);
+        const float4 Rr = ld4(R + ir0 + SR * t * BX);
+        const unsigned mm = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM) | inval[t];
+        const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
+        relax_strip<decltype(ua)::value, COARSE>(C0[t], w, e, N, S, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t],
+                                                 sy[t] + szr, zmr, zpr, sh, om, a, gid);
+        st4(P + ie, C0[t]);
+      };
+      if (!ring && red) {
+        if (parq) {
+          red_strip(U0{}, 0);
+          red_strip(U1{}, 1);
+        } else {
+          red_strip(U1{}, 0);
+          red_strip(U0{}, 1);
+        }
+      }
+      if (ring && red) {
+        // ring row strips (rows -1 and TY, this lane's x): red cells of plane q, in place
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float *cc = s.cc[lane] + 4 * h;
+          const int yr = h == 0 ? -1 : TY;
+          const int iq0 = (yr + 2) * BX + (xs + 4), irq0 = (yr + 1) * BX + (xs + 4), imq0 = (yr + 1) * BXM + (xs + 4);
+          float4 C = ld4(P + iq0);
+          const float4 N = ld4(P + iq0 - BX), S = ld4(P + iq0 + BX), Zm = ld4(Pm + iq0), Zp = ld4(Pp + iq0);
+          const float4 Rr = ld4(R + irq0);
+          const unsigned mm = *reinterpret_cast<const unsigned *>(M + imq0) | reinterpret_cast<const unsigned *>(cc)[3];
+          const float ep = P[iq0 + eoff];
+          float w = __shfl_up_sync(0xffffffffu, C.w, 1);
+          float e = __shfl_down_sync(0xffffffffu, C.x, 1);
+          w = lane == 0 ? ep : w;
+          e = lane == 31 ? ep : e;
+          const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + yr + 1) * a.sy + (x0 + xs + 4);
+          if (((y0 + yr + q) & 1) == 0)
+            relax_strip<0, COARSE>(C, w, e, N, S, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om, a,
+                                   gid);
           else
-            relax_strip<1, COARSE>(C0[t], w, e, N, S, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t], sy[t] + szr, zmr, zpr,
-                                   sh, om, a, gid);
-          st4(P + ie, C0[t]);
+            relax_strip<1, COARSE>(C, w, e, N, S, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om, a,
+                                   gid);
+          st4(P + iq0, C);
         }
-      }
-      if (red && warp == ROW_WARP) {
-        // ring row strip (row -1 / TY, this lane's x): red cells of plane q, in place
-        const float *cc = s.cc[lane];
-        const int yr = lane < 16 ? -1 : TY;
-        const int iq0 = (yr + 2) * BX + (xs + 4), irq0 = (yr + 1) * BX + (xs + 4), imq0 = (yr + 1) * BXM + (xs + 4);
-        float4 C = ld4(P + iq0);
-        const float4 N = ld4(P + iq0 - BX), S = ld4(P + iq0 + BX), Zm = ld4(Pm + iq0), Zp = ld4(Pp + iq0);
-        const float4 Rr = ld4(R + irq0);
-        const unsigned mm = *reinterpret_cast<const unsigned *>(M + imq0) | reinterpret_cast<const unsigned *>(cc)[3];
-        const float ep = P[iq0 + (l16 == 0 ? -1 : 4)];
-        float w = __shfl_up_sync(0xffffffffu, C.w, 1, 16);
-        float e = __shfl_down_sync(0xffffffffu, C.x, 1, 16);
-        w = l16 == 0 ? ep : w;
-        e = l16 == 15 ? ep : e;
-        const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + yr + 1) * a.sy + (x0 + xs + 4);
-        if (((y0 + yr + q) & 1) == 0)
-          relax_strip<0, COARSE>(C, w, e, N, S, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om, a, gid);
-        else
-          relax_strip<1, COARSE>(C, w, e, N, S, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om, a, gid);
-        st4(P + iq0, C);
-      }
-      if (red && warp == COL_WARP) {
-        // ring column cell (x = -1 or TX): the red one of rows (2 l16, 2 l16 + 1)
-        const int cxl = lane < 16 ? -1 : TX;
-        const int h = (x0 + cxl + y0 + 2 * l16 + q) & 1, cy = 2 * l16 + h;
-        const int ic = (cy + 2) * BX + (cxl + 4);
-        const int icr = (cy + 1) * BX + (cxl + 4), icm = (cy + 1) * BXM + (cxl + 4);
-        const float *cf = s.cc[lane] + 4;
-        const float cc0 = P[ic], cw = P[ic - 1], ce = P[ic + 1], cn = P[ic - BX], cs = P[ic + BX], czmv = Pm[ic],
-                    czpv = Pp[ic], crs = R[icr] - sh;
-        float v = relax1(cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr,
-                         cf[2] + (cf[7 + h] + szr), crs, om);
-        unsigned mb = M[icm];
-        if constexpr (COARSE) {
-          if (mb == IRREGULAR) {
-            const long long id = (long long)(q + 1) * a.sz + (long long)(y0 + cy + 1) * a.sy + (x0 + cxl + 4);
-            v = relax_frac(a, id, cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr, crs,
-                           om);
-            mb = 0u;
+        // ring column cell (x = -1 or TX): the red one of the lane's pair of rows
+        if (lane < COL_LANES) {
+          const int pr_ = lane % (TY / 2);
+          const int cxl = lane < TY / 2 ? -1 : TX;
+          const int h = (x0 + cxl + y0 + 2 * pr_ + q) & 1, cy = 2 * pr_ + h;
+          const int ic = (cy + 2) * BX + (cxl + 4);
+          const int icr = (cy + 1) * BX + (cxl + 4), icm = (cy + 1) * BXM + (cxl + 4);
+          const float *cf = s.cc[lane] + 8;
+          const float cc0 = P[ic], cw = P[ic - 1], ce = P[ic + 1], cn = P[ic - BX], cs = P[ic + BX], czmv = Pm[ic],
+                      czpv = Pp[ic], crs = R[icr] - sh;
+          float v = relax1(cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr,
+                           cf[2] + (cf[7 + h] + szr), crs, om);
+          unsigned mb = M[icm];
+          if constexpr (COARSE) {
+            if (mb == IRREGULAR) {
+              const long long id = (long long)(q + 1) * a.sz + (long long)(y0 + cy + 1) * a.sy + (x0 + cxl + 4);
+              v = relax_frac(a, id, cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr,
+                             crs, om);
+              mb = 0u;
+            }
           }
+          if (((reinterpret_cast<const int *>(cf)[9] >> h) & 1) && mb == 0u) P[ic] = v;
         }
-        if (((reinterpret_cast<const int *>(cf)[9] >> h) & 1) && mb == 0u) P[ic] = v;
       }
       // black cells of plane q-1: neighbours all red, updated by now (in-plane ones in
       // shared memory, the z-neighbours in Cm2 and C0); store the strips from registers
       const int kb = q - 1;
-      if (kb >= k0 && kb < k1) {
-        float *const dk = dst0 + (long long)(kb + 1) * a.sz;
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-          const int ie = ie0 + SR * t * BX;
-          const float ep = Pm[ie + (l16 == 0 ? -1 : 4)];
-          float w = __shfl_up_sync(0xffffffffu, Cm1[t].w, 1, 16);
-          float e = __shfl_down_sync(0xffffffffu, Cm1[t].x, 1, 16);
-          w = l16 == 0 ? ep : w;
-          e = l16 == 15 ? ep : e;
-          const float4 N = ld4(Pm + ie - BX), S = ld4(Pm + ie + BX);
-          const float4 Rr = ld4(Rm + ir0 + SR * t * BX);
-          const unsigned mm = *reinterpret_cast<const unsigned *>(Mm + im0 + SR * t * BXM) | inval[t];
-          const long long gid = (long long)q * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
-          // black cells of plane q-1 sit at the same u as the red cells of plane q
-          if (parq)
-            relax_strip<0, COARSE>(Cm1[t], w, e, N, S, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t], sy[t] + szb, zmb,
-                                   zpb, sh, om, a, gid);
-          else
-            relax_strip<1, COARSE>(Cm1[t], w, e, N, S, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t], sy[t] + szb, zmb,
-                                   zpb, sh, om, a, gid);
-          if ((inval[t] & 0xffu) == 0u) {   // the strip's row is in the grid
-            float *dst = dk + (long long)(SR * t) * a.px;
-            if (inval[t] == 0u) {
-              st4(dst, Cm1[t]);
-            } else {
-              if (!(inval[t] & 0xff00u)) dst[1] = Cm1[t].y;
-              if (!(inval[t] & 0xff0000u)) dst[2] = Cm1[t].z;
-              if (!(inval[t] & 0xff000000u)) dst[3] = Cm1[t].w;
-              dst[0] = Cm1[t].x;
-            }
+      // black cells of strip t of plane q-1 (they sit at the same u as the red cells of plane q)
+      auto black_strip = [&](auto ua, const int t, float *const dk) {
+        const int ie = ie0 + SR * t * BX;
+        const float ep = Pm[ie + eoff];
+        float w = __shfl_up_sync(0xffffffffu, Cm1[t].w, 1);
+        float e = __shfl_down_sync(0xffffffffu, Cm1[t].x, 1);
+        w = lane == 0 ? ep : w;
+        e = lane == 31 ? ep : e;
+        const float4 N = ld4(Pm + ie - BX), S = ld4(Pm + ie + BX);
+        const float4 Rr = ld4(Rm + ir0 + SR * t * BX);
+        const unsigned mm = *reinterpret_cast<const unsigned *>(Mm + im0 + SR * t * BXM) | inval[t];
+        const long long gid = (long long)q * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
+        relax_strip<decltype(ua)::value, COARSE>(Cm1[t], w, e, N, S, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t],
+                                                 sy[t] + szb, zmb, zpb, sh, om, a, gid);
+        if ((inval[t] & 0xffu) == 0u) {   // the strip's row is in the grid
+          float *dst = dk + (long long)(SR * t) * a.px;
+          if (inval[t] == 0u) {
+            st4(dst, Cm1[t]);
+          } else {
+            if (!(inval[t] & 0xff00u)) dst[1] = Cm1[t].y;
+            if (!(inval[t] & 0xff0000u)) dst[2] = Cm1[t].z;
+            if (!(inval[t] & 0xff000000u)) dst[3] = Cm1[t].w;
+            dst[0] = Cm1[t].x;
           }
+        }
+      };
+      if (!ring && kb >= k0 && kb < k1) {
+        float *const dk = dst0 + (long long)(kb + 1) * a.sz;
+        if (parq) {
+          black_strip(U0{}, 0, dk);
+          black_strip(U1{}, 1, dk);
+        } else {
+          black_strip(U1{}, 0, dk);
+          black_strip(U0{}, 1, dk);
         }
       }
 #pragma unroll

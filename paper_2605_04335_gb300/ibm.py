@@ -96,6 +96,7 @@ def load_library():
         "ibm_smoother_sweeps_timed": (I32, [P, P, I32, I32, P, C.POINTER(C.c_double)]),
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
         "ibm_ctx_set_sweep_wait_limit": (I32, [P, I32]),
+        "ibm_smoother_apply": (I32, [P, P, I32, I32, D, P, P, D, P, P]),
         "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P, P,
                                             C.POINTER(C.c_double), P]),
         "poisson_solve_batched": (I32, [P, I32, P, P, D, P, C.POINTER(ibm_solve_opts), P, P]),
@@ -306,6 +307,17 @@ def ibm_smoother_sweeps_timed(ctx, tables, precision: int, nsweeps: int, stream=
 def ibm_ctx_set_sweep_wait_limit(ctx, tries: int):
     """Test hook: tries of the fused sweep's first wait per item (0: give up at once; -1: normal)."""
     _check(load_library().ibm_ctx_set_sweep_wait_limit(ctx, int(tries)), "ibm_ctx_set_sweep_wait_limit")
+
+
+def ibm_smoother_apply(ctx, tables, precision: int, nsweeps: int, omega: float, e, r, mu: float, stream=None):
+    """Test hook: nsweeps finest-level smoother sweeps on caller data (e, r: float64 CUDA
+    tensors of the grid's [k][j][i] shape); returns the resulting e as a new tensor."""
+    e = e.contiguous()
+    r = r.contiguous()
+    out = e.new_empty(e.shape)
+    _check(load_library().ibm_smoother_apply(ctx, tables, int(precision), int(nsweeps), float(omega), _ptr(e), _ptr(r),
+                                             float(mu), _ptr(out), _stream(stream)), "ibm_smoother_apply")
+    return out
 
 
 def ibm_ctx_launch_count(ctx) -> int:

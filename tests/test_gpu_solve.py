@@ -84,16 +84,16 @@ def test_ragged_stretched_ellipsoid(ctx):
 
 def test_multi_tile_stretched_ellipsoid(ctx):
     """160 x 96 x 80 tanh-stretched cells around the 256^3 case's ellipsoid: the fused sweep's
-    64 x 32 tiles number 3 x 3 (ragged in y) with z-chunks, so its inter-tile rings and the
-    one-wave grid are compared element by element with the oracle in every mode."""
+    128 x 14 tiles number 2 x 7 (ragged in x and y) with z-chunks, so its inter-tile rings and
+    the one-wave grid are compared element by element with the oracle in every mode."""
     xf, yf, zf = synth.faces_tanh(160, 2.0), synth.faces_tanh(96, 2.0), synth.faces_tanh(80, 2.0)
     _parity(ctx, xf, yf, zf, [synth.ellipsoid(5, (0.2, 0.08, 0.08), 20.0, (0.5, 0.5, 0.5))], 2)
 
 
 def test_multi_tile_mean_carrying_rhs(ctx):
-    """b + 3 (a large fluid mean, absorbed by lambda) on a 130 x 70 x 66 grid (ragged in every
+    """b + 3 (a large fluid mean, absorbed by lambda) on a 130 x 68 x 66 grid (ragged in every
     tile direction): same pressure as for b, lambda shifted by 3."""
-    xf, yf, zf = synth.faces_tanh(130, 1.5), synth.faces_uniform(70), synth.faces_tanh(66, 2.0)
+    xf, yf, zf = synth.faces_tanh(130, 1.5), synth.faces_uniform(68), synth.faces_tanh(66, 2.0)
     b = synth.rhs_divergence(xf, yf, zf, 12) + 3.0
     _parity(ctx, xf, yf, zf, [synth.octa_sphere(4, (0.47, 0.52, 0.5), 0.21)], 12, b=b)
 
