@@ -395,6 +395,13 @@ ibm_status ibm_smoother_apply(ibm_ctx *ctx, const ibm_tables *t, int32_t precisi
                               double omega, const double *e_dev, const double *r_dev, double mu,
                               double *e_out_dev, void *stream);
 
+/* Measurement: the device's FP64 fused multiply-add rate (FMAs per second, *dfma_per_s),
+ * from a kernel of independent dependent chains filling every SM, best of three timed
+ * launches after one warm-up.  The paper has no counterpart; it is the roofline denominator
+ * of the FP64 smoother, whose work is FP64 arithmetic rather than memory traffic.  Waits for
+ * the stream. */
+ibm_status ibm_measure_fp64_rate(ibm_ctx *ctx, double *dfma_per_s, void *stream);
+
 /* Number of CUDA kernels this context has launched so far (all calls). */
 ibm_status ibm_ctx_launch_count(const ibm_ctx *ctx, int64_t *count);
 

@@ -8,7 +8,8 @@ missing: there is no CPU fallback.
 from .ibm import (IbmError, Context, Tables, SolveOpts, ibm_ctx_create, ibm_ctx_destroy, ibm_classify,
                   ibm_tables_counts, ibm_tables_export, ibm_tables_destroy, poisson_solve, load_library,
                   library_path, ibm_smoother_sweeps, ibm_smoother_sweeps_timed, ibm_ctx_launch_count,
-                  ibm_ctx_set_sweep_wait_limit, ibm_smoother_apply, ibm_residual_norm_noalloc, poisson_solve_batched,
+                  ibm_ctx_set_sweep_wait_limit, ibm_smoother_apply, ibm_measure_fp64_rate,
+                  ibm_residual_norm_noalloc, poisson_solve_batched,
                   ibm_autotune, ibm_reclassify,
                   ibm_set_neumann, ibm_neumann_rigid, ibm_surface_forces, HelmholtzOpts,
                   ibm_helmholtz_solve, ibm_boundary_velocity_rigid, ibm_helmholtz_sweeps_timed)
@@ -16,7 +17,7 @@ from .ibm import (IbmError, Context, Tables, SolveOpts, ibm_ctx_create, ibm_ctx_
 __all__ = ["IbmError", "Context", "Tables", "SolveOpts", "ibm_ctx_create", "ibm_ctx_destroy", "ibm_classify",
            "ibm_tables_counts", "ibm_tables_export", "ibm_tables_destroy", "poisson_solve", "load_library",
            "library_path", "ibm_smoother_sweeps", "ibm_smoother_sweeps_timed", "ibm_ctx_launch_count",
-           "ibm_ctx_set_sweep_wait_limit", "ibm_smoother_apply",
+           "ibm_ctx_set_sweep_wait_limit", "ibm_smoother_apply", "ibm_measure_fp64_rate",
            "ibm_residual_norm_noalloc", "poisson_solve_batched", "ibm_autotune", "ibm_reclassify",
            "ibm_set_neumann", "ibm_neumann_rigid", "ibm_surface_forces", "HelmholtzOpts",
            "ibm_helmholtz_solve", "ibm_boundary_velocity_rigid", "ibm_helmholtz_sweeps_timed"]

@@ -34,6 +34,7 @@ ibm_status sweeps_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, 
                        double *kernel_ms);
 ibm_status smoother_apply_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int nsweeps, double omega,
                                const double *e_in, const double *r_in, double mu, double *e_out, cudaStream_t st);
+ibm_status measure_fp64_impl(ibm_ctx *ctx, double *dfma_per_s, cudaStream_t st);
 ibm_status neumann_set_impl(ibm_tables *T, const double *q, cudaStream_t st);
 ibm_status neumann_rigid_impl(ibm_tables *T, const double *motions, int nmesh, cudaStream_t st);
 ibm_status helmholtz_solve_impl(ibm_ctx *ctx, ibm_tables *t, double alpha, const double *f_user, const double *ub,
@@ -404,6 +405,12 @@ ibm_status ibm_smoother_apply(ibm_ctx *ctx, const ibm_tables *t, int32_t precisi
   IBM_TRY(cudaSetDevice(ctx->device));
   return ibm::smoother_apply_impl(ctx, const_cast<ibm_tables *>(t), precision, nsweeps, omega, e_dev, r_dev, mu,
                                   e_out_dev, (cudaStream_t)stream);
+}
+
+ibm_status ibm_measure_fp64_rate(ibm_ctx *ctx, double *dfma_per_s, void *stream) {
+  if (!ctx || !dfma_per_s) return IBM_ERR_INVALID_ARG;
+  IBM_TRY(cudaSetDevice(ctx->device));
+  return ibm::measure_fp64_impl(ctx, dfma_per_s, (cudaStream_t)stream);
 }
 
 static bool valid_opts(const ibm_solve_opts &o) {

@@ -143,6 +143,7 @@ struct Hierarchy {
   int zmc_per_sm = 1;                       // the same for its coarse-level form
   CUtensorMap tm_e[2], tm_r, tm_m;
   void *tm_base[2] = {nullptr, nullptr};    // which buffer each tm_e describes
+  const void *tm_rbase = nullptr;           // the right-hand side tm_r describes
 };
 
 }  // namespace ibm

@@ -388,7 +388,7 @@ __global__ void k_ghost_eval(const long long *src, const long long *dst, const W
 // unchanged), so no thread reads a value another thread writes (Jacobi among ghosts)
 template <typename T, typename W>
 __global__ void k_ghost_pp(const long long *src, const long long *dst, const W *w, long long ng,
-                           const long long *ngp, T *enew, const T *eold, const T *rhs) {
+                           const long long *ngp, T *enew, const T *eold, const T *rhs, const double *gd) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= (ngp ? *ngp : ng)) return;
   T s = (T)0;
@@ -399,6 +399,7 @@ __global__ void k_ghost_pp(const long long *src, const long long *dst, const W *
     s += (T)w[8 * g + c] * v;
   }
   if (rhs) s += rhs[dst[g]];
+  if (gd) s += (T)gd[g];     // the row's Neumann datum
   enew[dst[g]] = s;
 }
 
@@ -2121,20 +2122,17 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
             make_map(&h->tm_m, L0.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, L0.g, zm::BXM, zm::RY);
   h->tm_base[0] = e0;
   h->tm_base[1] = h->e_alt;
-  // the FP64 smoother is bound by the FP64 pipe, not by memory: it keeps the two-pass kernel,
-  // whose small blocks give the occupancy that hides FP64 latency
-  h->zmarch = false;
-  if constexpr (sizeof(T) == 4) {
-    h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sizeof(zm::Smem<T>)) == cudaSuccess;
-    int per_sm = 0;
-    if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T, false>,
-                                                                   zm::THREADS, sizeof(zm::Smem<T>)) == cudaSuccess &&
-        per_sm > 0)
-      h->zm_per_sm = per_sm;
-    else
-      h->zmarch = false;
-  }
+  h->tm_rbase = r0;
+  // FP32: two CTAs per SM; FP64 (bound by the FP64 pipe): one, with the same tiles
+  h->zmarch = ok && cudaFuncSetAttribute(zm::k_sweep_zmarch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(zm::Smem<T>)) == cudaSuccess;
+  int per_sm = 0;
+  if (h->zmarch && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T, false>, zm::THREADS,
+                                                                 sizeof(zm::Smem<T>)) == cudaSuccess &&
+      per_sm > 0)
+    h->zm_per_sm = per_sm;
+  else
+    h->zmarch = false;
 }
 
 // Coarse levels swept by the fused z-march: levels >= 1 of at least ZM_COARSE_CELLS cells in
@@ -2587,14 +2585,14 @@ void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
   a.items = (int)(tiles * chunks);
   a.first_wait = S.ctx->sweep_first_wait >= 0 ? S.ctx->sweep_first_wait : zm::WAIT_LIMIT;
   const int grid = (int)(S.batched ? a.items : std::min<long long>(a.items, resident));
-  if constexpr (sizeof(T) == 4) {   // FP32 only (setup_zmarch enables it for FP32 hierarchies)
+  if constexpr (sizeof(T) == 4) {   // coarse levels: FP32 hierarchies only
     if (coarse)
       zm::k_sweep_zmarch<T, true><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(L0.ztm_e[which], L0.ztm_r,
                                                                                     L0.ztm_m, a);
-    else
-      zm::k_sweep_zmarch<T, false><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r,
-                                                                                     h->tm_m, a);
   }
+  if (!coarse)
+    zm::k_sweep_zmarch<T, false><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(h->tm_e[which], h->tm_r, h->tm_m,
+                                                                                   a);
   S.ctx->launches += 1;
   e = other;
 }
@@ -2623,7 +2621,9 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
       if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
       continue;
     }
-    if (sizeof(T) == 4 && fine && S.h->zmarch) {
+    // the finest level's fused sweep, when e and r are the arrays its tensor maps cover (in
+    // FP64 the solution and right-hand side of the V-cycle on p)
+    if (fine && S.h->zmarch && (e == S.h->tm_base[0] || e == S.h->tm_base[1]) && (const void *)r == S.h->tm_rbase) {
       T *old = e;
       sweep_zmarch<T>(S, 0, e, shift);
       if (timed) cudaEventRecord((*S.sweep_events)[2 * s + 1], S.st);
@@ -2632,10 +2632,10 @@ void smooth_level(Solver &S, int l, T *&e, const T *r, const double *shift, bool
       if (ng > 0) {
         if (sizeof(T) == 8)
           k_ghost_pp<T, double><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.t->gw, S.h->gcap,
-                                                                        S.h->d_ng, e, old, ghost_rhs);
+                                                                        S.h->d_ng, e, old, ghost_rhs, S.gd);
         else
           k_ghost_pp<T, float><<<nblk(S.h->gcap, 128), 128, 0, S.st>>>(S.h->gsrc, S.h->gdst, S.h->gw32, S.h->gcap,
-                                                                       S.h->d_ng, e, old, ghost_rhs);
+                                                                       S.h->d_ng, e, old, ghost_rhs, S.gd);
         S.ctx->launches += 1;
       }
       continue;
@@ -3694,6 +3694,50 @@ ibm_status smoother_apply_impl(ibm_ctx *ctx, ibm_tables *t, int precision, int n
   ctx->launches += 3;
   IBM_TRY(cudaGetLastError());
   return read_errflag(ctx, IBM_OK, st);
+}
+
+// FP64 fused multiply-add throughput: CHAINS independent dependent chains per thread, every
+// SM filled with resident blocks; the roofline denominator of the FP64 smoother
+namespace {
+constexpr int FMA_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_dfma_rate(int iters, double b, double c, double *sink) {
+  double x[FMA_CHAINS];
+#pragma unroll
+  for (int q = 0; q < FMA_CHAINS; ++q) x[q] = 1.0 + 1e-3 * (threadIdx.x + q);
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < FMA_CHAINS; ++q) x[q] = fma(x[q], b, c);
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < FMA_CHAINS; ++q) acc += x[q];
+  if (acc == 12345.678) sink[0] = acc;   // never true; keeps the chains live
+}
+}  // namespace
+
+ibm_status measure_fp64_impl(ibm_ctx *ctx, double *dfma_per_s, cudaStream_t st) {
+  int per_sm = 0;
+  IBM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma_rate, 256, 0));
+  const int blocks = std::max(1, per_sm) * std::max(1, ctx->sm_count);
+  const int iters = 4096;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  IBM_TRY(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && ce == cudaSuccess; ++rep) {   // the first launch warms up
+    cudaEventRecord(e0, st);
+    k_dfma_rate<<<blocks, 256, 0, st>>>(iters, 0.9999999, 1e-7, ctx->partials);
+    cudaEventRecord(e1, st);
+    ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  ctx->launches += 4;
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return check(ce, "fp64 rate");
+  *dfma_per_s = (double)blocks * 256 * FMA_CHAINS * iters / (best * 1e-3);
+  return IBM_OK;
 }
 
 }  // namespace ibm

@@ -1,5 +1,7 @@
 // Fused two-colour red-black Gauss-Seidel sweep on the finest level: z-march with
-// TMA-staged planes in shared memory, persistent CTAs over (x-y tile, z-chunk) items.
+// TMA-staged planes in shared memory, persistent CTAs over (x-y tile, z-chunk) items.  FP32
+// (the mixed solves' multigrid, two CTAs per SM) and FP64 (the FP64 solve's smoother on p,
+// one CTA per SM: its buffers take 190 KB of shared memory) share the code.
 //
 // One item is an x-y tile (TX x TY) and a z-range [k0, k1).  Step q of its march
 //   1. updates the red cells of plane q on the tile, and the one-cell ring that the tile's
@@ -46,6 +48,8 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "dfloat.cuh"
+
 namespace ibm {
 namespace zm {
 
@@ -75,18 +79,34 @@ constexpr int NE = 3 + DP;
 constexpr int NR = 2 + DP;
 
 constexpr int pad128(int bytes) { return (bytes + 127) / 128 * 128; }
-constexpr int ESZ = pad128(EY * BX * 4) / 4;   // floats per e buffer
-constexpr int RSZ = pad128(RY * BX * 4) / 4;   // floats per rhs buffer
+template <typename T> constexpr int esz() { return pad128(EY * BX * (int)sizeof(T)) / (int)sizeof(T); }  // per e buffer
+template <typename T> constexpr int rsz() { return pad128(RY * BX * (int)sizeof(T)) / (int)sizeof(T); }  // per rhs buffer
 constexpr int MSZ = pad128(RY * BXM);          // bytes per mask buffer
+
+// four consecutive cells of a strip (16 bytes in FP32, 32 in FP64)
+struct alignas(32) dbl4 {
+  double x, y, z, w;
+};
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = dbl4; };
+template <typename T> using vec4 = typename V4<T>::type;
+
+// z coefficients of one plane
+template <typename T>
+struct ZC {
+  T m, p, s, pad;   // czm, czp, czm + czp
+};
 
 // every TMA destination starts on a 128-byte boundary
 template <typename T>
 struct Smem {
-  alignas(128) T e[NE][ESZ];
-  alignas(128) T r[NR][RSZ];
+  alignas(128) T e[NE][esz<T>()];
+  alignas(128) T r[NR][rsz<T>()];
   alignas(128) uint8_t m[NR][MSZ];
-  alignas(16) float4 zc[KZ_MAX + 4];   // czm, czp, czm + czp of planes k0 - 2 .. k1 + 1
-  alignas(16) float cc[32][20];       // ring warp lanes' coefficients (ring rows, column cell)
+  alignas(32) ZC<T> zc[KZ_MAX + 4];   // planes k0 - 2 .. k1 + 1
+  alignas(16) T cc[32][16];           // ring warp lanes' coefficients (ring rows, column cell)
+  alignas(16) unsigned ccu[32][4];    // ... their invalid-cell bytes and row flags
   alignas(8) uint64_t bar_e[NE];
   alignas(8) uint64_t bar_r[NR];
 };
@@ -146,8 +166,16 @@ struct Args {
   int *err;
 };
 
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void st4(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
+template <typename T>
+__device__ __forceinline__ vec4<T> ld4(const T *p) { return *reinterpret_cast<const vec4<T> *>(p); }
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const vec4<T> &v) { *reinterpret_cast<vec4<T> *>(p) = v; }
+template <typename T>
+__device__ __forceinline__ vec4<T> make4(T a, T b, T c, T d) {
+  vec4<T> v;
+  v.x = a; v.y = b; v.z = c; v.w = d;
+  return v;
+}
 
 // One cell: e + omega (sum_d c_d e_d - D e - (rhs - sh)) / D.  The residual is formed in FP32
 // in a fixed order; the relaxation factor omega / D uses an approximate reciprocal (it does
@@ -164,6 +192,23 @@ __device__ __forceinline__ float relax1(float c, float w, float ea, float n, flo
   acc = fmaf(czm, zm, acc);
   acc = fmaf(czp, zp, acc);
   return fmaf(acc, __fdividef(om, D), c);
+}
+
+// The same cell in FP64 (the FP64 solve's smoother): the residual in FP64 in the same order; the
+// relaxation factor omega / D in FP32 from D rounded toward zero, widened exactly (both
+// conversions by bit manipulation, off the FP64 pipe).  As in FP32, the factor does not move
+// the fixed point.
+__device__ __forceinline__ double relax1(double c, double w, double ea, double n, double s, double zm, double zp,
+                                        double cxm, double cxp, double cym, double cyp, double czm, double czp,
+                                        double D, double rsh, float om) {
+  double acc = fma(-D, c, -rsh);
+  acc = fma(cxm, w, acc);
+  acc = fma(cxp, ea, acc);
+  acc = fma(cym, n, acc);
+  acc = fma(cyp, s, acc);
+  acc = fma(czm, zm, acc);
+  acc = fma(czp, zp, acc);
+  return fma(acc, dfl::widen(__fdividef(om, dfl::narrow_trunc(D))), c);
 }
 
 // z-march mask byte of an irregular coarse cell
@@ -186,8 +231,9 @@ using U0 = std::integral_constant<int, 0>;   // a strip's colour: u of its first
 using U1 = std::integral_constant<int, 1>;
 
 // x coefficients of a strip's four cells
+template <typename T>
 struct XCoef {
-  float4 m, p, s;   // cxm, cxp, cxm + cxp
+  vec4<T> m, p, s;   // cxm, cxp, cxm + cxp
 };
 
 // Relax the cells u = UA and UA + 2 of strip C (a warp's strips share UA): west/east are the
@@ -196,22 +242,22 @@ struct XCoef {
 // levels; invalid cells carry 0xff); gid the padded index of the strip's first cell (coarse
 // levels' fractions).  Called by all 32 lanes of a warp.
 template <int UA, bool COARSE, typename T>
-__device__ __forceinline__ void relax_strip(float4 &C, float west, float east, const float4 &N, const float4 &S,
-                                            const float4 &Zm, const float4 &Zp, const float4 &R, unsigned mm,
-                                            const XCoef &X, float cym, float cyp, float syz, float czm, float czp,
-                                            float sh, float om, const Args<T> &a, long long gid) {
-  const float c0 = UA == 0 ? C.x : C.y, c1 = UA == 0 ? C.z : C.w;
-  const float w0 = UA == 0 ? west : C.x, e0 = UA == 0 ? C.y : C.z;
-  const float w1 = UA == 0 ? C.y : C.z, e1 = UA == 0 ? C.w : east;
-  const float n0 = UA == 0 ? N.x : N.y, n1 = UA == 0 ? N.z : N.w, s0 = UA == 0 ? S.x : S.y, s1 = UA == 0 ? S.z : S.w;
-  const float zm0 = UA == 0 ? Zm.x : Zm.y, zm1 = UA == 0 ? Zm.z : Zm.w;
-  const float zp0 = UA == 0 ? Zp.x : Zp.y, zp1 = UA == 0 ? Zp.z : Zp.w;
-  const float r0 = (UA == 0 ? R.x : R.y) - sh, r1 = (UA == 0 ? R.z : R.w) - sh;
-  const float xm0 = UA == 0 ? X.m.x : X.m.y, xm1 = UA == 0 ? X.m.z : X.m.w;
-  const float xp0 = UA == 0 ? X.p.x : X.p.y, xp1 = UA == 0 ? X.p.z : X.p.w;
-  const float xs0 = UA == 0 ? X.s.x : X.s.y, xs1 = UA == 0 ? X.s.z : X.s.w;
-  float v0 = relax1(c0, w0, e0, n0, s0, zm0, zp0, xm0, xp0, cym, cyp, czm, czp, xs0 + syz, r0, om);
-  float v1 = relax1(c1, w1, e1, n1, s1, zm1, zp1, xm1, xp1, cym, cyp, czm, czp, xs1 + syz, r1, om);
+__device__ __forceinline__ void relax_strip(vec4<T> &C, T west, T east, const vec4<T> &N, const vec4<T> &S,
+                                            const vec4<T> &Zm, const vec4<T> &Zp, const vec4<T> &R, unsigned mm,
+                                            const XCoef<T> &X, T cym, T cyp, T syz, T czm, T czp, T sh, float om,
+                                            const Args<T> &a, long long gid) {
+  const T c0 = UA == 0 ? C.x : C.y, c1 = UA == 0 ? C.z : C.w;
+  const T w0 = UA == 0 ? west : C.x, e0 = UA == 0 ? C.y : C.z;
+  const T w1 = UA == 0 ? C.y : C.z, e1 = UA == 0 ? C.w : east;
+  const T n0 = UA == 0 ? N.x : N.y, n1 = UA == 0 ? N.z : N.w, s0 = UA == 0 ? S.x : S.y, s1 = UA == 0 ? S.z : S.w;
+  const T zm0 = UA == 0 ? Zm.x : Zm.y, zm1 = UA == 0 ? Zm.z : Zm.w;
+  const T zp0 = UA == 0 ? Zp.x : Zp.y, zp1 = UA == 0 ? Zp.z : Zp.w;
+  const T r0 = (UA == 0 ? R.x : R.y) - sh, r1 = (UA == 0 ? R.z : R.w) - sh;
+  const T xm0 = UA == 0 ? X.m.x : X.m.y, xm1 = UA == 0 ? X.m.z : X.m.w;
+  const T xp0 = UA == 0 ? X.p.x : X.p.y, xp1 = UA == 0 ? X.p.z : X.p.w;
+  const T xs0 = UA == 0 ? X.s.x : X.s.y, xs1 = UA == 0 ? X.s.z : X.s.w;
+  T v0 = relax1(c0, w0, e0, n0, s0, zm0, zp0, xm0, xp0, cym, cyp, czm, czp, xs0 + syz, r0, om);
+  T v1 = relax1(c1, w1, e1, n1, s1, zm1, zp1, xm1, xp1, cym, cyp, czm, czp, xs1 + syz, r1, om);
   unsigned b0 = (mm >> (8 * UA)) & 0xffu, b1 = (mm >> (8 * (UA + 2))) & 0xffu;
   if constexpr (COARSE) {
     if (__any_sync(0xffffffffu, b0 == IRREGULAR || b1 == IRREGULAR)) {
@@ -237,20 +283,20 @@ __device__ __forceinline__ void relax_strip(float4 &C, float west, float east, c
 }
 
 template <typename T>
-__device__ __forceinline__ XCoef load_x(const Args<T> &a, int gi0) {
-  XCoef X;
-  float m[4], p[4], s[4];
+__device__ __forceinline__ XCoef<T> load_x(const Args<T> &a, int gi0) {
+  XCoef<T> X;
+  T m[4], p[4], s[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int gi = gi0 + u;
     const bool ok = gi >= 0 && gi < a.nx;
-    m[u] = ok ? a.cxm[gi] : 0.f;
-    p[u] = ok ? a.cxp[gi] : 0.f;
-    s[u] = ok ? a.sdx[gi] : 0.f;
+    m[u] = ok ? a.cxm[gi] : (T)0;
+    p[u] = ok ? a.cxp[gi] : (T)0;
+    s[u] = ok ? a.sdx[gi] : (T)0;
   }
-  X.m = make_float4(m[0], m[1], m[2], m[3]);
-  X.p = make_float4(p[0], p[1], p[2], p[3]);
-  X.s = make_float4(s[0], s[1], s[2], s[3]);
+  X.m = make4<T>(m[0], m[1], m[2], m[3]);
+  X.p = make4<T>(p[0], p[1], p[2], p[3]);
+  X.s = make4<T>(s[0], s[1], s[2], s[3]);
   return X;
 }
 
@@ -263,14 +309,18 @@ __device__ __forceinline__ unsigned invalid_bytes(int gi0, int nx, bool jok) {
   return v;
 }
 
+// resident CTAs per SM: two in FP32; one in FP64, whose buffers take most of the shared memory
+template <typename T>
+constexpr int min_ctas() { return sizeof(T) == 4 ? MIN_CTAS : 1; }
+
 template <typename T, bool COARSE>
-__global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
-                                                                    const __grid_constant__ CUtensorMap tm_r,
-                                                                    const __grid_constant__ CUtensorMap tm_m,
-                                                                    Args<T> a) {
-  static_assert(sizeof(T) == 4, "the fused sweep runs in FP32");
+__global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
+                                                                         const __grid_constant__ CUtensorMap tm_r,
+                                                                         const __grid_constant__ CUtensorMap tm_m,
+                                                                         Args<T> a) {
+  static_assert(sizeof(T) == 4 || !COARSE, "coarse levels are swept in FP32");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem<float> &s = *reinterpret_cast<Smem<float> *>(smem_raw);
+  Smem<T> &s = *reinterpret_cast<Smem<T> *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ring = warp == RING_WARP;
   const bool issuer = ring && lane == 0;
@@ -280,9 +330,9 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
     fence_mbar_init();
   }
   __syncthreads();
-  const unsigned ebytes = EY * BX * 4, rbytes = RY * BX * 4 + RY * BXM;
+  const unsigned ebytes = EY * BX * sizeof(T), rbytes = RY * BX * sizeof(T) + RY * BXM;
   const float om = a.omega;
-  const float sh = a.shift ? (float)(*a.shift) : 0.f;
+  const T sh = a.shift ? (T)(*a.shift) : (T)0;
   // per slot: parity of its next completion (toggled when a wait sees it land); the issuer
   // also keeps which slots have a copy in flight that it has not yet seen land
   unsigned pe = 0, pr = 0, pend_e = 0, pend_r = 0;
@@ -305,53 +355,57 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
     const int k0 = bz * a.kz, k1 = min(a.nz, k0 + a.kz);
     if (k0 >= k1) continue;
     // coefficients of this thread's strips (registers for the item's whole march)
-    const XCoef X = load_x(a, x0 + xs);
-    float cym[NS], cyp[NS], sy[NS];
+    const XCoef<T> X = load_x(a, x0 + xs);
+    T cym[NS], cyp[NS], sy[NS];
     unsigned inval[NS];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
       const int gj = y0 + ys + SR * t;
       const bool jok = gj < a.ny;
       inval[t] = invalid_bytes(x0 + xs, a.nx, jok);
-      cym[t] = jok ? a.cym[gj] : 0.f;
-      cyp[t] = jok ? a.cyp[gj] : 0.f;
-      sy[t] = jok ? a.sdy[gj] : 0.f;
+      cym[t] = jok ? a.cym[gj] : (T)0;
+      cyp[t] = jok ? a.cyp[gj] : (T)0;
+      sy[t] = jok ? a.sdy[gj] : (T)0;
     }
-    // ring warp: its ring strips' row coefficients and invalid bytes (slots 0-3: row -1,
-    // 4-7: row TY), then its column cell's (slots 8-17): cxm, cxp, sdx, then cym, cyp, sdy of
-    // the pair's two rows, then which rows are in the grid
+    // ring warp: its ring strips' row coefficients (slots 0-2: row -1, 3-5: row TY; cym, cyp,
+    // sdy) and invalid bytes (ccu 0, 1), then its column cell's (slots 6-14): cxm, cxp, sdx,
+    // then cym, cyp, sdy of the pair's two rows, and which rows are in the grid (ccu 2)
     if (ring) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int gj = y0 + (h == 0 ? -1 : TY);
         const bool jok = gj >= 0 && gj < a.ny;
-        float *cc = s.cc[lane] + 4 * h;
-        cc[0] = jok ? a.cym[gj] : 0.f;
-        cc[1] = jok ? a.cyp[gj] : 0.f;
-        cc[2] = jok ? a.sdy[gj] : 0.f;
-        reinterpret_cast<unsigned *>(cc)[3] = invalid_bytes(x0 + xs, a.nx, jok);
+        T *cc = s.cc[lane] + 3 * h;
+        cc[0] = jok ? a.cym[gj] : (T)0;
+        cc[1] = jok ? a.cyp[gj] : (T)0;
+        cc[2] = jok ? a.sdy[gj] : (T)0;
+        s.ccu[lane][h] = invalid_bytes(x0 + xs, a.nx, jok);
       }
       const int pr_ = lane % (TY / 2);
       const int cgi = x0 + (lane < TY / 2 ? -1 : TX), gj0 = y0 + 2 * pr_;
       const bool cxok = lane < COL_LANES && cgi >= 0 && cgi < a.nx;
       const bool ok0 = cxok && gj0 < a.ny, ok1 = cxok && gj0 + 1 < a.ny;
-      float *cc = s.cc[lane] + 8;
-      cc[0] = cxok ? a.cxm[cgi] : 0.f;
-      cc[1] = cxok ? a.cxp[cgi] : 0.f;
-      cc[2] = cxok ? a.sdx[cgi] : 0.f;
-      cc[3] = ok0 ? a.cym[gj0] : 0.f;
-      cc[4] = ok1 ? a.cym[gj0 + 1] : 0.f;
-      cc[5] = ok0 ? a.cyp[gj0] : 0.f;
-      cc[6] = ok1 ? a.cyp[gj0 + 1] : 0.f;
-      cc[7] = ok0 ? a.sdy[gj0] : 0.f;
-      cc[8] = ok1 ? a.sdy[gj0 + 1] : 0.f;
-      reinterpret_cast<int *>(cc)[9] = (ok0 ? 1 : 0) | (ok1 ? 2 : 0);
+      T *cc = s.cc[lane] + 6;
+      cc[0] = cxok ? a.cxm[cgi] : (T)0;
+      cc[1] = cxok ? a.cxp[cgi] : (T)0;
+      cc[2] = cxok ? a.sdx[cgi] : (T)0;
+      cc[3] = ok0 ? a.cym[gj0] : (T)0;
+      cc[4] = ok1 ? a.cym[gj0 + 1] : (T)0;
+      cc[5] = ok0 ? a.cyp[gj0] : (T)0;
+      cc[6] = ok1 ? a.cyp[gj0 + 1] : (T)0;
+      cc[7] = ok0 ? a.sdy[gj0] : (T)0;
+      cc[8] = ok1 ? a.sdy[gj0 + 1] : (T)0;
+      s.ccu[lane][2] = (ok0 ? 1u : 0u) | (ok1 ? 2u : 0u);
     }
     // the item's z coefficients, read from shared memory by every step (planes k0 - 2 .. k1 + 1)
     for (int pl = k0 - 2 + tid; pl <= k1 + 1; pl += THREADS) {
       const bool ok = pl >= 0 && pl < a.nz;
-      const float m = ok ? a.czm[pl] : 0.f, p = ok ? a.czp[pl] : 0.f, z = ok ? a.sdz[pl] : 0.f;
-      s.zc[pl - (k0 - 2)] = make_float4(m, p, z, 0.f);
+      ZC<T> z;
+      z.m = ok ? a.czm[pl] : (T)0;
+      z.p = ok ? a.czp[pl] : (T)0;
+      z.s = ok ? a.sdz[pl] : (T)0;
+      z.pad = (T)0;
+      s.zc[pl - (k0 - 2)] = z;
     }
     // slots: plane p lives in e slot (p + 2 NE) mod NE and rhs/mask slot (p + 2 NR) mod NR
     auto wrap_e = [](int x) { return x >= NE ? x - NE : x; };
@@ -394,14 +448,14 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
     wait_e(sq, WAIT_LIMIT);
     // registers: each strip in planes q-2 (Cm2; its red cells are final once plane q-2's red
     // pass is done), q-1 (Cm1) and q (C0)
-    float4 Cm2[NS], Cm1[NS], C0[NS];
+    vec4<T> Cm2[NS], Cm1[NS], C0[NS];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
       Cm1[t] = ld4(s.e[se0] + ie0 + SR * t * BX);
       C0[t] = ld4(s.e[sq] + ie0 + SR * t * BX);
       Cm2[t] = Cm1[t];
     }
-    float *const dst0 = a.out + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
+    T *const dst0 = a.out + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
     // unrolled by 3: the strips' register rotation (planes q-2, q-1, q) becomes renaming
 #pragma unroll 3
     for (int q = k0 - 1; q <= k1; ++q) {
@@ -417,32 +471,32 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
         if (q + 1 + DP <= k1 + 1) load_e(q + 1 + DP, wrap_e(sp1 + DP));
         if (q + DP <= k1) load_r(q + DP, wrap_r(rq + DP));
       }
-      float *P = s.e[sq], *Pm = s.e[sm1];
-      const float *Pp = s.e[sp1];
+      T *P = s.e[sq], *Pm = s.e[sm1];
+      const T *Pp = s.e[sp1];
       const int rqm = rq == 0 ? NR - 1 : rq - 1;   // rhs/mask slot of plane q-1
-      const float *R = s.r[rq], *Rm = s.r[rqm];
+      const T *R = s.r[rq], *Rm = s.r[rqm];
       const uint8_t *M = s.m[rq], *Mm = s.m[rqm];
       // z coefficients of planes q (red pass) and q-1 (black pass)
-      const float4 zq = s.zc[q - (k0 - 2)], zb = s.zc[q - 1 - (k0 - 2)];
-      const float zmr = zq.x, zpr = zq.y, szr = zq.z, zmb = zb.x, zpb = zb.y, szb = zb.z;
+      const ZC<T> zq = s.zc[q - (k0 - 2)], zb = s.zc[q - 1 - (k0 - 2)];
+      const T zmr = zq.m, zpr = zq.p, szr = zq.s, zmb = zb.m, zpb = zb.p, szb = zb.s;
       const bool red = q >= 0 && q < a.nz;
       // x0 + xs is even: strip t relaxes u = (y0 + ys + SR t + q) & 1 (SR is odd, so strip 1 has
       // the other colour of strip 0)
       const bool parq = ((y0 + ys + q) & 1) == 0;
-      float4 U[NS];   // the strips in plane q+1
+      vec4<T> U[NS];   // the strips in plane q+1
 #pragma unroll
       for (int t = 0; t < NS; ++t) U[t] = ld4(Pp + ie0 + SR * t * BX);
       // red cells of strip t of plane q (ua: its colour's u, a compile-time constant):
       // x-edges from the adjacent lanes, or the ring at the edges
       auto red_strip = [&](auto ua, const int t) {
         const int ie = ie0 + SR * t * BX;
-        const float ep = P[ie + eoff];
-        float w = __shfl_up_sync(0xffffffffu, C0[t].w, 1);
-        float e = __shfl_down_sync(0xffffffffu, C0[t].x, 1);
+        const T ep = P[ie + eoff];
+        T w = __shfl_up_sync(0xffffffffu, C0[t].w, 1);
+        T e = __shfl_down_sync(0xffffffffu, C0[t].x, 1);
         w = lane == 0 ? ep : w;
         e = lane == 31 ? ep : e;
-        const float4 N = ld4(P + ie - BX), S = ld4(P + ie + BX);
-        const float4 Rr = ld4(R + ir0 + SR * t * BX);
+        const vec4<T> N = ld4(P + ie - BX), S = ld4(P + ie + BX);
+        const vec4<T> Rr = ld4(R + ir0 + SR * t * BX);
         const unsigned mm = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM) | inval[t];
         const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
         relax_strip<decltype(ua)::value, COARSE>(C0[t], w, e, N, S, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t],
@@ -462,16 +516,16 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
         // ring row strips (rows -1 and TY, this lane's x): red cells of plane q, in place
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float *cc = s.cc[lane] + 4 * h;
+          const T *cc = s.cc[lane] + 3 * h;
           const int yr = h == 0 ? -1 : TY;
           const int iq0 = (yr + 2) * BX + (xs + 4), irq0 = (yr + 1) * BX + (xs + 4), imq0 = (yr + 1) * BXM + (xs + 4);
-          float4 C = ld4(P + iq0);
-          const float4 N = ld4(P + iq0 - BX), S = ld4(P + iq0 + BX), Zm = ld4(Pm + iq0), Zp = ld4(Pp + iq0);
-          const float4 Rr = ld4(R + irq0);
-          const unsigned mm = *reinterpret_cast<const unsigned *>(M + imq0) | reinterpret_cast<const unsigned *>(cc)[3];
-          const float ep = P[iq0 + eoff];
-          float w = __shfl_up_sync(0xffffffffu, C.w, 1);
-          float e = __shfl_down_sync(0xffffffffu, C.x, 1);
+          vec4<T> C = ld4(P + iq0);
+          const vec4<T> N = ld4(P + iq0 - BX), S = ld4(P + iq0 + BX), Zm = ld4(Pm + iq0), Zp = ld4(Pp + iq0);
+          const vec4<T> Rr = ld4(R + irq0);
+          const unsigned mm = *reinterpret_cast<const unsigned *>(M + imq0) | s.ccu[lane][h];
+          const T ep = P[iq0 + eoff];
+          T w = __shfl_up_sync(0xffffffffu, C.w, 1);
+          T e = __shfl_down_sync(0xffffffffu, C.x, 1);
           w = lane == 0 ? ep : w;
           e = lane == 31 ? ep : e;
           const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + yr + 1) * a.sy + (x0 + xs + 4);
@@ -490,11 +544,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
           const int h = (x0 + cxl + y0 + 2 * pr_ + q) & 1, cy = 2 * pr_ + h;
           const int ic = (cy + 2) * BX + (cxl + 4);
           const int icr = (cy + 1) * BX + (cxl + 4), icm = (cy + 1) * BXM + (cxl + 4);
-          const float *cf = s.cc[lane] + 8;
-          const float cc0 = P[ic], cw = P[ic - 1], ce = P[ic + 1], cn = P[ic - BX], cs = P[ic + BX], czmv = Pm[ic],
-                      czpv = Pp[ic], crs = R[icr] - sh;
-          float v = relax1(cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr,
-                           cf[2] + (cf[7 + h] + szr), crs, om);
+          const T *cf = s.cc[lane] + 6;
+          const T cc0 = P[ic], cw = P[ic - 1], ce = P[ic + 1], cn = P[ic - BX], cs = P[ic + BX], czmv = Pm[ic],
+                  czpv = Pp[ic], crs = R[icr] - sh;
+          T v = relax1(cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr,
+                       cf[2] + (cf[7 + h] + szr), crs, om);
           unsigned mb = M[icm];
           if constexpr (COARSE) {
             if (mb == IRREGULAR) {
@@ -504,28 +558,28 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
               mb = 0u;
             }
           }
-          if (((reinterpret_cast<const int *>(cf)[9] >> h) & 1) && mb == 0u) P[ic] = v;
+          if (((s.ccu[lane][2] >> h) & 1u) && mb == 0u) P[ic] = v;
         }
       }
       // black cells of plane q-1: neighbours all red, updated by now (in-plane ones in
       // shared memory, the z-neighbours in Cm2 and C0); store the strips from registers
       const int kb = q - 1;
       // black cells of strip t of plane q-1 (they sit at the same u as the red cells of plane q)
-      auto black_strip = [&](auto ua, const int t, float *const dk) {
+      auto black_strip = [&](auto ua, const int t, T *const dk) {
         const int ie = ie0 + SR * t * BX;
-        const float ep = Pm[ie + eoff];
-        float w = __shfl_up_sync(0xffffffffu, Cm1[t].w, 1);
-        float e = __shfl_down_sync(0xffffffffu, Cm1[t].x, 1);
+        const T ep = Pm[ie + eoff];
+        T w = __shfl_up_sync(0xffffffffu, Cm1[t].w, 1);
+        T e = __shfl_down_sync(0xffffffffu, Cm1[t].x, 1);
         w = lane == 0 ? ep : w;
         e = lane == 31 ? ep : e;
-        const float4 N = ld4(Pm + ie - BX), S = ld4(Pm + ie + BX);
-        const float4 Rr = ld4(Rm + ir0 + SR * t * BX);
+        const vec4<T> N = ld4(Pm + ie - BX), S = ld4(Pm + ie + BX);
+        const vec4<T> Rr = ld4(Rm + ir0 + SR * t * BX);
         const unsigned mm = *reinterpret_cast<const unsigned *>(Mm + im0 + SR * t * BXM) | inval[t];
         const long long gid = (long long)q * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
         relax_strip<decltype(ua)::value, COARSE>(Cm1[t], w, e, N, S, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t],
                                                  sy[t] + szb, zmb, zpb, sh, om, a, gid);
         if ((inval[t] & 0xffu) == 0u) {   // the strip's row is in the grid
-          float *dst = dk + (long long)(SR * t) * a.px;
+          T *dst = dk + (long long)(SR * t) * a.px;
           if (inval[t] == 0u) {
             st4(dst, Cm1[t]);
           } else {
@@ -537,7 +591,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_sweep_zmarch(const __grid
         }
       };
       if (!ring && kb >= k0 && kb < k1) {
-        float *const dk = dst0 + (long long)(kb + 1) * a.sz;
+        T *const dk = dst0 + (long long)(kb + 1) * a.sz;
         if (parq) {
           black_strip(U0{}, 0, dk);
           black_strip(U1{}, 1, dk);

@@ -97,6 +97,7 @@ def load_library():
         "ibm_ctx_launch_count": (I32, [P, C.POINTER(I64)]),
         "ibm_ctx_set_sweep_wait_limit": (I32, [P, I32]),
         "ibm_smoother_apply": (I32, [P, P, I32, I32, D, P, P, D, P, P]),
+        "ibm_measure_fp64_rate": (I32, [P, C.POINTER(C.c_double), P]),
         "ibm_residual_norm_noalloc": (I32, [C.POINTER(ibm_grid), P, I64, P, P, P, P, P, P, P,
                                             C.POINTER(C.c_double), P]),
         "poisson_solve_batched": (I32, [P, I32, P, P, D, P, C.POINTER(ibm_solve_opts), P, P]),
@@ -318,6 +319,13 @@ def ibm_smoother_apply(ctx, tables, precision: int, nsweeps: int, omega: float, 
     _check(load_library().ibm_smoother_apply(ctx, tables, int(precision), int(nsweeps), float(omega), _ptr(e), _ptr(r),
                                              float(mu), _ptr(out), _stream(stream)), "ibm_smoother_apply")
     return out
+
+
+def ibm_measure_fp64_rate(ctx, stream=None) -> float:
+    """FP64 fused multiply-adds per second of the device (a throughput kernel, best of three)."""
+    v = C.c_double()
+    _check(load_library().ibm_measure_fp64_rate(ctx, C.byref(v), _stream(stream)), "ibm_measure_fp64_rate")
+    return float(v.value)
 
 
 def ibm_ctx_launch_count(ctx) -> int:
