@@ -240,6 +240,37 @@ def moving_ellipsoid(synth):
     return out
 
 
+def bench_coarse_bf16(pkg, ctx, torch, T, rhs, p, st, N, mixed):
+    """Mode 1 with the z-march coarse levels' e and r stored in BF16, against the same solve
+    with FP32 storage: cycles, time to 1e-10, the extra hierarchy's device memory, and the
+    pressure's largest difference (relative to its largest value) from the FP32-storage one."""
+    ob = pkg.SolveOpts(precision=1, coarse_bf16=1)
+    of = pkg.SolveOpts(precision=1)
+    p.zero_()
+    T.solve(rhs, p, TOL, of, stream=st)
+    torch.cuda.synchronize()
+    ref = p.clone()
+    torch.cuda.synchronize()
+    fa, _ = torch.cuda.mem_get_info()
+    p.zero_()
+    T.solve(rhs, p, TOL, ob, stream=st)
+    torch.cuda.synchronize()
+    fb, _ = torch.cuda.mem_get_info()
+
+    def solve():
+        p.zero_()
+        return T.solve(rhs, p, TOL, ob, stream=st)
+    ms, rep = _timed(torch, st, solve, 2)
+    diff = float((p - ref).abs().max() / ref.abs().max())
+    del ref
+    torch.cuda.empty_cache()
+    return {"storage": "e and r of the z-march coarse levels (levels >= 1, >= 2^18 cells) in BF16, FP32 arithmetic",
+            "time_to_tol_ms": ms, "cycles": rep["cycles"], "final_rel_resid": rep["rel_resid"],
+            "hierarchy_gb": (fa - fb) / 1e9, "gcells_per_s": N / (ms * 1e-3) / 1e9,
+            "vs_fp32_storage": {"time_ratio": ms / mixed["time_to_tol_ms"], "cycles_fp32": mixed["cycles"],
+                                "hierarchy_gb_fp32": mixed["hierarchy_gb"], "max_rel_diff_p": diff}}
+
+
 def bench_moving_ellipsoid(pkg, ctx, torch, st, n: int = 256, steps: int = 20, autotune: bool = True,
                            paper_solver: bool = True):
     """One time step of a moving body on the 256^3 tanh-stretched grid (max/min spacing 2):
@@ -666,6 +697,7 @@ def run_ours(args):
         line["modes"] = modes
         line["mixed_speedup_vs_fp64"] = {k: modes["fp64"]["time_to_tol_ms"] / modes[k]["time_to_tol_ms"]
                                          for k in ("mixed", "mixed_df")}
+        line["coarse_bf16"] = bench_coarse_bf16(pkg, ctx, torch, T, rhs, p, st, N, modes["mixed"])
         line["device_total_gb"] = total_mem / 1e9
     T.close()
     del rhs, p

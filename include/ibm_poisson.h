@@ -100,6 +100,12 @@ typedef struct {
                            relaxation factors 1 / Chebyshev nodes of [2/K^2, 2] (K =
                            srj_steps); max_cycles counts BiCGStab iterations.            [0] */
   int32_t srj_steps;    /* Jacobi sweeps per preconditioner application, 1..64            [8] */
+  int32_t coarse_bf16;  /* 1: the coarse levels swept by the fused z-march (levels >= 1 of at
+                           least 2^18 cells) store their error and right-hand side in BF16,
+                           arithmetic in FP32 (loads widen exactly, stores round to nearest
+                           even); precision 1 or 2, closed bodies (IBM_ERR_INVALID_ARG
+                           otherwise).  A storage experiment of this library; the paper runs
+                           FP64 throughout.  The hierarchy is kept beside the FP32 one.     [0] */
 } ibm_solve_opts;
 
 /* Solve report.  resid_history (host, optional) receives the relative residual after

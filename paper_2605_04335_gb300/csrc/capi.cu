@@ -219,7 +219,7 @@ ibm_status ibm_tables_destroy(ibm_tables *t) {
   if (!t) return IBM_ERR_INVALID_ARG;
   if (t->ctx) cudaSetDevice(t->ctx->device);
   cudaDeviceSynchronize();
-  for (int q = 0; q < 3; ++q) ibm::free_hierarchy(t->hier[q]);
+  for (int q = 0; q < 5; ++q) ibm::free_hierarchy(t->hier[q]);
   void *ps[] = {t->iblank, t->gcell, t->gbi, t->gip, t->gw, t->gscale, t->gbase, t->gflags, t->gref, t->axis,
                 t->scratch, t->cut, t->cside, t->gside, t->gkeys, t->gkappa, t->gd, t->gtri, t->fbuf, t->gwself};
   for (void *p : ps) if (p) cudaFree(p);
@@ -363,6 +363,7 @@ void ibm_solve_opts_default(ibm_solve_opts *o) {
   o->krylov = -1;
   o->method = 0;
   o->srj_steps = 8;
+  o->coarse_bf16 = 0;
 }
 
 ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol, double *p_dev,
@@ -373,7 +374,8 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
   if (opts) o = *opts;
   if (!(o.precision >= 0 && o.precision <= 2) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0) || o.krylov < -1 || o.krylov > 8 || o.method < 0 ||
-      o.method > 1 || o.srj_steps < 1 || o.srj_steps > 64 || (o.method == 1 && o.precision != 0))
+      o.method > 1 || o.srj_steps < 1 || o.srj_steps > 64 || (o.method == 1 && o.precision != 0) ||
+      o.coarse_bf16 < 0 || o.coarse_bf16 > 1 || (o.coarse_bf16 && (o.precision == 0 || t->membrane)))
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
@@ -416,7 +418,8 @@ ibm_status ibm_measure_fp64_rate(ibm_ctx *ctx, double *dfma_per_s, void *stream)
 static bool valid_opts(const ibm_solve_opts &o) {
   return o.precision >= 0 && o.precision <= 2 && o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 &&
          o.max_cycles >= 0 && o.inner_cycles >= 1 && o.omega > 0.0 && o.omega < 2.0 && o.krylov >= -1 &&
-         o.krylov <= 8 && o.method == 0;   // batched: the multigrid solver
+         o.krylov <= 8 && o.method == 0 &&   // batched: the multigrid solver
+         (o.coarse_bf16 == 0 || (o.coarse_bf16 == 1 && o.precision != 0));
 }
 
 ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,
@@ -425,6 +428,7 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
   if (!ctx || n < 0 || (n > 0 && (!tables || !rhs_dev || !p_dev)) || !(tol >= 0.0)) return IBM_ERR_INVALID_ARG;
   for (int p = 0; p < n; ++p) {
     if (!tables[p] || tables[p]->ctx != ctx || !rhs_dev[p] || !p_dev[p]) return IBM_ERR_INVALID_ARG;
+    if (opts && opts->coarse_bf16 && tables[p]->membrane) return IBM_ERR_INVALID_ARG;
     for (int q = 0; q < p; ++q)
       if (tables[q] == tables[p]) return IBM_ERR_INVALID_ARG;   // each problem owns its work arrays
     if (infos && infos[p].history_cap > 0 && !infos[p].resid_history) return IBM_ERR_INVALID_ARG;

@@ -29,6 +29,7 @@ enum Scal {
   S_FLUIDVOL = 3, // sum of fluid volumes (fine)
   S_NF = 4,       // number of fluid cells (fine)
   S_MEANP = 5,    // fluid mean of p (gauge)
+  S_PNZ = 6,      // the packed initial p has a nonzero value (an integer flag in the slot's bits)
   S_LEVEL_SHIFT = 8  // S_LEVEL_SHIFT + l: projection shift of coarse level l
 };
 
@@ -80,6 +81,8 @@ struct Level {
   void *ealt = nullptr;                     // second e buffer (ping-pong of the fused sweep)
   void *zsd = nullptr;                      // cxm+cxp, cym+cyp, czm+czp (element type)
   CUtensorMap ztm_e[2], ztm_r, ztm_m;       // tensor maps of e (both buffers), r and zmask
+  bool bf16 = false;                        // e, r and ealt stored in BF16 (a z-march level of a
+                                            // hierarchy built with BF16 coarse storage)
 };
 
 struct Hierarchy {
@@ -141,6 +144,7 @@ struct Hierarchy {
   bool zmarch = false;
   int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep
   int zmc_per_sm = 1;                       // the same for its coarse-level form
+  bool coarse_bf16 = false;                 // z-march coarse levels store e and r in BF16
   CUtensorMap tm_e[2], tm_r, tm_m;
   void *tm_base[2] = {nullptr, nullptr};    // which buffer each tm_e describes
   const void *tm_rbase = nullptr;           // the right-hand side tm_r describes
@@ -205,7 +209,8 @@ struct ibm_tables {
   char *fbuf = nullptr;              // surface-force working set (meshes, incidence, shares)
   size_t fcap = 0;
   // solver hierarchies by precision mode (lazy)
-  ibm::Hierarchy *hier[3] = {nullptr, nullptr, nullptr};
+  // one hierarchy per precision (0, 1, 2), then precisions 1 and 2 with BF16 coarse storage
+  ibm::Hierarchy *hier[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace ibm {

@@ -430,9 +430,9 @@ template <> struct Pair<double> {
 // coarse cell (the 2x2x2 children of e, r and mask and their 24 face neighbours) is issued
 // before the arithmetic; children past an odd fine extent are halo cells (mask 1) whose
 // outward neighbours are not read.
-template <typename T>
-__global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const T *e, const T *r, const double *shift, LV<T> cv,
-                                                   T *rc, T *ec, double *partials) {
+template <typename T, typename SF = T, typename SC = T>
+__global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const SF *e, const SF *r, const double *shift, LV<T> cv,
+                                                   SC *rc, SC *ec, double *partials) {
   __shared__ double sm[128];
   double acc_all = 0.0;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -470,25 +470,25 @@ __global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const T *e, const T 
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           const long long q = fb + d * f.sz + b * f.sy;
-          Pair<T>::ld(e + q, E[d][b]);
-          Pair<T>::ld(r + q, R[d][b]);
+          ld2(e + q, E[d][b]);
+          ld2(r + q, R[d][b]);
           M[d][b] = *reinterpret_cast<const uchar2 *>(f.mask + q);
-          XM[d][b] = e[q - 1];
-          XP[d][b] = vx1 ? e[q + 2] : (T)0;
+          XM[d][b] = ld1(e + q - 1);
+          XP[d][b] = vx1 ? ld1(e + q + 2) : (T)0;
         }
 #pragma unroll
       for (int d = 0; d < 2; ++d)
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-          YM[d][a] = e[fb + d * f.sz - f.sy + a];
-          YP[d][a] = vy1 ? e[fb + d * f.sz + 2 * f.sy + a] : (T)0;
+          YM[d][a] = ld1(e + fb + d * f.sz - f.sy + a);
+          YP[d][a] = vy1 ? ld1(e + fb + d * f.sz + 2 * f.sy + a) : (T)0;
         }
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-          ZM[b][a] = e[fb - f.sz + b * f.sy + a];
-          ZP[b][a] = vz1 ? e[fb + 2 * f.sz + b * f.sy + a] : (T)0;
+          ZM[b][a] = ld1(e + fb - f.sz + b * f.sy + a);
+          ZP[b][a] = vz1 ? ld1(e + fb + 2 * f.sz + b * f.sy + a) : (T)0;
         }
       const bool cfl = cv.mask[ic] == 0;
       T acc = (T)0;
@@ -515,8 +515,8 @@ __global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const T *e, const T 
             if (m == 0) acc += (wxf[a] * wyf[b]) * wzf[d] * res;
           }
       const T vc = (cv.wx[I] * cv.wy[J]) * cv.wz[K];
-      rc[ic] = cfl ? acc / vc : (T)0;
-      ec[ic] = (T)0;
+      st1(rc + ic, cfl ? acc / vc : (T)0);
+      st1(ec + ic, (T)0);
       if (cfl) acc_all += (double)acc;
     }
   sm[threadIdx.x] = acc_all;
@@ -559,8 +559,8 @@ __global__ void k_finalize_shift(const double *partials, int nb, const double *f
 // (inner flag), else summed the same way over the fluid indicator.  Children that are not
 // fluid rows are left unchanged.  The children's e and masks are loaded with the coarse
 // block, before any arithmetic.
-template <typename T>
-__global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const uint8_t *inner, LV<T> f, T *ef,
+template <typename T, typename SC = T, typename SF = T>
+__global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef,
                                                   const int8_t *offx, const int8_t *offy, const int8_t *offz,
                                                   const float *tx, const float *ty, const float *tz) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const u
       for (int b = 0; b < 2; ++b) {
         fr[d][b] = vidx(f, 2 * I, 2 * J + b, 2 * K + d);
         fm[d][b] = *reinterpret_cast<const uchar2 *>(f.mask + fr[d][b]);
-        Pair<T>::ld(ef + fr[d][b], fe[d][b]);
+        ld2(ef + fr[d][b], fe[d][b]);
       }
     const long long c0 = vidx(cv, I, J, K);
     const bool inr = inner[c0] != 0;
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const u
 #pragma unroll
       for (int y = 0; y < 3; ++y)
 #pragma unroll
-        for (int x = 0; x < 3; ++x) e[z][y][x] = ec[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)];
+        for (int x = 0; x < 3; ++x) e[z][y][x] = ld1(ec + c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1));
     // contract x, then y, then z
     auto contract = [&](const T (&v)[3][3][3], T (&out)[2][2][2]) {
       T vx[2][3][3];
@@ -657,9 +657,9 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const T *ec, const u
       for (int b = 0; b < 2; ++b) {
         const bool u0 = fluid_row(fm[d][b].x) && den[d][b][0] > (T)0,
                    u1 = fluid_row(fm[d][b].y) && den[d][b][1] > (T)0;
-        T *rowp = ef + fr[d][b];
-        if (u0) rowp[0] = fe[d][b][0] + num[d][b][0] / den[d][b][0];
-        if (u1) rowp[1] = fe[d][b][1] + num[d][b][1] / den[d][b][1];
+        SF *rowp = ef + fr[d][b];
+        if (u0) st1(rowp, fe[d][b][0] + num[d][b][0] / den[d][b][0]);
+        if (u1) st1(rowp + 1, fe[d][b][1] + num[d][b][1] / den[d][b][1]);
       }
   }
 }
@@ -924,8 +924,11 @@ __device__ __forceinline__ void block_partials3(double A0, double A1, double A2,
 template <typename R>
 __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
                                                               const double *lambda, const float *wf, R *r32,
-                                                              double *partials) {
+                                                              double *partials, const unsigned *p_nonzero) {
   const double lam = *lambda;
+  // p_nonzero (optional): zero when every packed value of p is zero, so A p = 0 exactly and
+  // the FP64 stencil is skipped (a cold start); one test for the whole launch
+  const bool use_p = p != nullptr && (p_nonzero == nullptr || *p_nonzero != 0u);
   const int nx = v.nx, ny = v.ny;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   double A0 = 0.0, A1 = 0.0, A2 = 0.0;
@@ -945,7 +948,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
         ld_mask4(v.mask + id, fl);
         double B[4], P[4], YM[4], YP[4], ZM[4], ZP[4], xl = 0.0, xr = 0.0;
         Vec4<double>::ld(b + id, B);
-        if (p) {
+        if (use_p) {
           Vec4<double>::ld(p + id, P);
           Vec4<double>::ld(p + id - v.sy, YM);
           Vec4<double>::ld(p + id + v.sy, YP);
@@ -960,7 +963,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
         for (int u = 0; u < 4; ++u) {
           const int i = min(4 * g + u, nx - 1);   // coefficients of cells past nx: any valid index
           double res = B[u] - lam;
-          if (p) {
+          if (use_p) {
             const double left = u == 0 ? xl : P[u - 1], right = u == 3 ? xr : P[u + 1];
             res = fma(v.sdx[i] + syz, P[u], res);   // b - lambda - (A p)_i
             res = fma(-v.cxm[i], left, res);
@@ -1089,10 +1092,11 @@ __global__ void k_gauge_finalize(const double *partials, int nb, double *scal) {
 
 // pack a user [k][j][i] array into a padded array (cells past nx in the last group get 0);
 // cells with mask == 1 (plain solid) are set to zero when mask is given
-__global__ void k_pack(const double *src, LevelGeom g, double *dst, const uint8_t *mask) {
+__global__ void k_pack(const double *src, LevelGeom g, double *dst, const uint8_t *mask, unsigned *nonzero) {
   const RowGroups rg(g.nx);
   const int rows = g.ny * g.nz;
   if (!rg.active()) return;
+  unsigned long long seen = 0;   // bits of the packed values (nonzero: some value is not +-0)
   for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
     const int j = row % g.ny, k = row / g.ny;
     const long long q0 = (long long)row * g.nx;
@@ -1108,8 +1112,13 @@ __global__ void k_pack(const double *src, LevelGeom g, double *dst, const uint8_
 #pragma unroll
       for (int u = 0; u < 4; ++u) V[u] = (4 * gr + u < g.nx && fl[u]) ? src[q0 + 4 * gr + u] : 0.0;
       Vec4<double>::st(dst + id, V);
+      if (nonzero)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) seen |= (unsigned long long)__double_as_longlong(V[u]) << 1;   // sign dropped
     }
   }
+  if (nonzero && __any_sync(__activemask(), seen != 0ull) && (threadIdx.x & 31) == __ffs(__activemask()) - 1)
+    atomicOr(nonzero, 1u);
 }
 
 // unpack with the gauge applied: dst = p - mean on active cells, 0 on plain solid cells
@@ -2140,30 +2149,46 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
 // r and z-march mask.
 constexpr long long ZM_COARSE_CELLS = 1LL << 18;
 
+// With BF16 coarse storage those levels' e and r maps are BF16 (the kernel's BF16 form); a
+// BF16 level must be swept by it (no other coarse kernel reads BF16): false if it cannot be.
 template <typename T>
-static void setup_zmarch_coarse(Hierarchy *h) {
+static bool setup_zmarch_coarse(Hierarchy *h) {
   if constexpr (sizeof(T) == 4) {
-    bool any = false;
+    bool any = false, anyb = false;
     for (size_t l = 1; l < h->lv.size(); ++l) {
       Level &L = h->lv[l];
       if (!L.zm) continue;
-      L.zm = make_map(&L.ztm_e[0], L.e, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.g, zm::BX, zm::EY) &&
-             make_map(&L.ztm_e[1], L.ealt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.g, zm::BX, zm::EY) &&
-             make_map(&L.ztm_r, L.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.g, zm::BX, zm::RY) &&
+      const CUtensorMapDataType dt = L.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+      const int el = L.bf16 ? 2 : 4;
+      L.zm = make_map(&L.ztm_e[0], L.e, dt, el, L.g, zm::BX, zm::EY) &&
+             make_map(&L.ztm_e[1], L.ealt, dt, el, L.g, zm::BX, zm::EY) &&
+             make_map(&L.ztm_r, L.r, dt, el, L.g, zm::BX, zm::RY) &&
              make_map(&L.ztm_m, L.zmask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, L.g, zm::BXM, zm::RY);
       any |= L.zm;
+      anyb |= L.zm && L.bf16;
     }
-    int per_sm = 0;
-    const bool ok = any &&
-                    cudaFuncSetAttribute(zm::k_sweep_zmarch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(zm::Smem<T>)) == cudaSuccess &&
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T, true>, zm::THREADS,
-                                                                  sizeof(zm::Smem<T>)) == cudaSuccess &&
-                    per_sm > 0;
+    int per_sm = 0, per_smb = 0;
+    bool ok = any &&
+              cudaFuncSetAttribute(zm::k_sweep_zmarch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(zm::Smem<T>)) == cudaSuccess &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zm::k_sweep_zmarch<T, true>, zm::THREADS,
+                                                            sizeof(zm::Smem<T>)) == cudaSuccess &&
+              per_sm > 0;
+    if (ok && anyb) {
+      ok = cudaFuncSetAttribute(zm::k_sweep_zmarch<T, true, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(zm::Smem<T, bf16>)) == cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_smb, zm::k_sweep_zmarch<T, true, bf16>, zm::THREADS,
+                                                         sizeof(zm::Smem<T, bf16>)) == cudaSuccess &&
+           per_smb > 0;
+      per_sm = std::min(per_sm, per_smb);
+    }
     h->zmc_per_sm = ok ? per_sm : 1;
     if (!ok)
       for (size_t l = 1; l < h->lv.size(); ++l) h->lv[l].zm = false;
+    for (size_t l = 1; l < h->lv.size(); ++l)
+      if (h->lv[l].bf16 && !h->lv[l].zm) return false;
   }
+  return true;
 }
 
 // separable diagonal parts of a level: sd = cm + cp per axis, from its coefficient array
@@ -2201,9 +2226,10 @@ __global__ void k_zmask(LV<T> v, uint8_t *zm) {
 // Grid-only part of a hierarchy: every allocation, the level geometry, coefficients,
 // prolongation tables and the fused-sweep tensor maps.  Nothing here depends on the bodies.
 template <typename T>
-static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) {
+static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out, bool coarse_bf16) {
   Hierarchy *h = new Hierarchy();
   h->elem = sizeof(T);
+  h->coarse_bf16 = sizeof(T) == 4 && coarse_bf16;
   // membranes: one slot per ghost entry after the finest level's padded cells (capacity
   // rounded to 16 elements, so the level-0 arrays stay a multiple of 16 long)
   const long long slotcap = t->membrane ? (std::max<long long>(t->gcap, 1024) + 15) / 16 * 16 : 0;
@@ -2245,10 +2271,17 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
     HTRY(cudaMalloc((void **)&L.mask, L.g.ntot));
     HTRY(cudaMemsetAsync(L.mask, 1, L.g.ntot, st));
-    // the finest level's arrays end with one slot per membrane ghost entry
+    // the finest level's arrays end with one slot per membrane ghost entry; coarse levels
+    // that the fused sweep takes store e and r in BF16 when asked
     const long long nel = l == 0 ? L.g.ntot + slotcap : L.g.ntot;
-    HTRY(alloc_zero<T>(&L.e, nel, st));
-    HTRY(alloc_zero<T>(&L.r, nel, st));
+    L.bf16 = h->coarse_bf16 && l >= 1 && (long long)nx * ny * nz >= ZM_COARSE_CELLS;
+    if (L.bf16) {
+      HTRY(alloc_zero<bf16>(&L.e, nel, st));
+      HTRY(alloc_zero<bf16>(&L.r, nel, st));
+    } else {
+      HTRY(alloc_zero<T>(&L.e, nel, st));
+      HTRY(alloc_zero<T>(&L.r, nel, st));
+    }
     HTRY(cudaMalloc(&L.c1d, sizeof(T) * 2 * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.w1d, sizeof(double) * (nx + ny + nz)));
     HTRY(cudaMalloc((void **)&L.cen, sizeof(double) * (nx + ny + nz)));
@@ -2274,7 +2307,8 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
       if ((long long)L.g.nx * L.g.ny * L.g.nz < ZM_COARSE_CELLS) continue;
       HTRY(cudaMalloc((void **)&L.zmask, L.g.ntot));
       HTRY(cudaMemsetAsync(L.zmask, 1, L.g.ntot, st));
-      HTRY(alloc_zero<T>(&L.ealt, L.g.ntot, st));
+      if (L.bf16) HTRY(alloc_zero<bf16>(&L.ealt, L.g.ntot, st));
+      else HTRY(alloc_zero<T>(&L.ealt, L.g.ntot, st));
       HTRY(cudaMalloc(&L.zsd, sizeof(T) * (L.g.nx + L.g.ny + L.g.nz)));
       k_sdiag<T><<<nblk(L.g.nx + L.g.ny + L.g.nz, 128), 128, 0, st>>>((const T *)L.c1d, L.g.nx, L.g.ny, L.g.nz,
                                                                       (T *)L.zsd);
@@ -2323,7 +2357,11 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out) 
     else setup_zmarch<T>(h, L0.e, L0.r);
     if (!h->zmarch)
       for (Level &L : h->lv) L.zm = false;
-    setup_zmarch_coarse<T>(h);
+    if (!setup_zmarch_coarse<T>(h)) {
+      free_faces();
+      free_hierarchy(h);
+      return IBM_ERR_CUDA;
+    }
   }
   // coarse tail: the first level (below the finest) small enough for one block
   h->tail_level = -1;
@@ -2586,7 +2624,10 @@ void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
   a.first_wait = S.ctx->sweep_first_wait >= 0 ? S.ctx->sweep_first_wait : zm::WAIT_LIMIT;
   const int grid = (int)(S.batched ? a.items : std::min<long long>(a.items, resident));
   if constexpr (sizeof(T) == 4) {   // coarse levels: FP32 hierarchies only
-    if (coarse)
+    if (coarse && L0.bf16)
+      zm::k_sweep_zmarch<T, true, bf16><<<grid, zm::THREADS, sizeof(zm::Smem<T, bf16>), S.st>>>(
+          L0.ztm_e[which], L0.ztm_r, L0.ztm_m, a);
+    else if (coarse)
       zm::k_sweep_zmarch<T, true><<<grid, zm::THREADS, sizeof(zm::Smem<T>), S.st>>>(L0.ztm_e[which], L0.ztm_r,
                                                                                     L0.ztm_m, a);
   }
@@ -2691,7 +2732,21 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   T *ec = (T *)C.e, *rc = (T *)C.r;
   const int gx = (int)nblk(C.g.nx, 128),
             gy = std::max(1, std::min(C.g.ny * C.g.nz, std::min(RESTRICT_BLOCKS, h->grid_blocks[0]) / gx));
-  k_restrict8<T><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), e, r, shift, view<T>(C), rc, ec, S.part);
+  // storage of the two levels (BF16 on coarse levels of a BF16-storage hierarchy)
+  auto restrict_into = [&](auto sf, auto sc) {
+    using SF = decltype(sf);
+    using SC = decltype(sc);
+    k_restrict8<T, SF, SC><<<dim3(gx, gy), 128, 0, S.st>>>(view<T>(F), (const SF *)e, (const SF *)r, shift, view<T>(C),
+                                                           (SC *)rc, (SC *)ec, S.part);
+  };
+  if constexpr (sizeof(T) == 4) {
+    if (F.bf16 && C.bf16) restrict_into(bf16{}, bf16{});
+    else if (F.bf16) restrict_into(bf16{}, T{});
+    else if (C.bf16) restrict_into(T{}, bf16{});
+    else restrict_into(T{}, T{});
+  } else {
+    restrict_into(T{}, T{});
+  }
   int nparts = gx * gy;
   if (l == 0 && h->hcnt[2] > 0) {   // membranes: the cut cells' share, partials after the regular ones
     k_cut_restrict<T><<<CUT_BLOCKS, 256, 0, S.st>>>(h->par_id, h->d_cnt, h->cut_id, h->cut_nb, view<T>(F), e, r,
@@ -2705,8 +2760,20 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   const int pgx = (int)nblk(C.g.nx, 128);
   dim3 gp(pgx, std::max(1, std::min(C.g.ny * C.g.nz, h->grid_blocks[1] / pgx)));
   const int nxf = F.g.nx, nyf = F.g.ny;
-  k_prolong8<T><<<gp, 128, 0, S.st>>>(view<T>(C), ec, C.inner, view<T>(F), e, F.poff, F.poff + nxf, F.poff + nxf + nyf,
-                                      F.pt, F.pt + nxf, F.pt + nxf + nyf);
+  auto prolong_from = [&](auto sc, auto sf) {
+    using SC = decltype(sc);
+    using SF = decltype(sf);
+    k_prolong8<T, SC, SF><<<gp, 128, 0, S.st>>>(view<T>(C), (const SC *)ec, C.inner, view<T>(F), (SF *)e, F.poff,
+                                                F.poff + nxf, F.poff + nxf + nyf, F.pt, F.pt + nxf, F.pt + nxf + nyf);
+  };
+  if constexpr (sizeof(T) == 4) {
+    if (C.bf16 && F.bf16) prolong_from(bf16{}, bf16{});
+    else if (C.bf16) prolong_from(bf16{}, T{});
+    else if (F.bf16) prolong_from(T{}, bf16{});
+    else prolong_from(T{}, T{});
+  } else {
+    prolong_from(T{}, T{});
+  }
   S.ctx->launches += 3;   // restrict, finalize shift, prolong
   // the corrected fluid values make the ghost rows stale: refresh them before post-smoothing
   if (fine) ghost_update<T>(S, e, ghost_rhs);
@@ -2744,11 +2811,12 @@ inline float *hi_of(double *a) { return reinterpret_cast<float *>(a); }
 inline float *lo_of(double *a, long long ntot) { return reinterpret_cast<float *>(a) + ntot; }
 
 template <typename R>
-void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda);
+void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda, const unsigned *p_nonzero = nullptr);
 
-// the outer residual, its norms and the lambda update; with_p == false: residual of p = 0
-void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
-  if (!S.dfo) return fine_residual<float>(S, with_p ? S.h->p64 : nullptr, r32, update_lambda);
+// the outer residual, its norms and the lambda update; with_p == false: residual of p = 0;
+// p_nonzero (FP64 residual only): a device flag, zero when p is all zero
+void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda, const unsigned *p_nonzero = nullptr) {
+  if (!S.dfo) return fine_residual<float>(S, with_p ? S.h->p64 : nullptr, r32, update_lambda, p_nonzero);
   Hierarchy *h = S.h;
   const long long ntot = h->nslot;   // hi/lo split point of the outer arrays
   double *part = S.part;
@@ -2777,12 +2845,12 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda) {
 }
 
 template <typename R>
-void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda) {
+void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda, const unsigned *p_nonzero) {
   LV<double> v = fine_view64(S.h);
   double *part = S.part;
   const int n = v.nx + v.ny + v.nz;
   k_residual64<R><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.scal + S_LAMBDA, S.h->cdf + 3 * n,
-                                                          r32, part);
+                                                          r32, part, p_nonzero);
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
@@ -2840,15 +2908,20 @@ void gcr_step(Solver &S, T *e, const T *r, int m) {
 
 }  // namespace
 
-ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
-  Hierarchy *h = t->hier[precision];
+// the hierarchy slot of a precision and coarse storage (BF16 only for the FP32 multigrid)
+int hier_slot(int precision, bool coarse_bf16) { return coarse_bf16 && precision > 0 ? precision + 2 : precision; }
+
+ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st, bool coarse_bf16) {
+  const int slot = hier_slot(precision, coarse_bf16);
+  Hierarchy *h = t->hier[slot];
   if (h && h->geom_version == t->geom_version) return IBM_OK;
   if (h && t->membrane && t->nghost > h->slotcap) {   // more membrane entries than slots: rebuild
     free_hierarchy(h);
-    t->hier[precision] = h = nullptr;
+    t->hier[slot] = h = nullptr;
   }
   if (h) return precision == 0 ? refresh_geometry_t<double>(t, h, st) : refresh_geometry_t<float>(t, h, st);
-  ibm_status s = precision == 0 ? build_grid_t<double>(t, st, &h) : build_grid_t<float>(t, st, &h);
+  ibm_status s = precision == 0 ? build_grid_t<double>(t, st, &h, false)
+                                : build_grid_t<float>(t, st, &h, coarse_bf16);
   if (s != IBM_OK) return s;
   // FP64 fine coefficients
   Level &L0 = h->lv[0];
@@ -2894,8 +2967,12 @@ ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
     free_hierarchy(h);
     return s;
   }
-  t->hier[precision] = h;
+  t->hier[slot] = h;
   return IBM_OK;
+}
+
+ibm_status build_hierarchy(ibm_tables *t, int precision, cudaStream_t st) {
+  return build_hierarchy(t, precision, st, false);
 }
 
 namespace {
@@ -2926,9 +3003,10 @@ ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, con
                      const ibm_solve_opts *opts, double *scal, double *part, double *hs, bool batched,
                      cudaStream_t st) {
   R.ctx = ctx; R.t = t; R.opts = opts; R.prec = opts->precision; R.hs = hs;
-  ibm_status s = build_hierarchy(t, R.prec, st);
+  const bool cb = opts->coarse_bf16 != 0;
+  ibm_status s = build_hierarchy(t, R.prec, st, cb);
   if (s != IBM_OK) return s;
-  Hierarchy *h = R.h = t->hier[R.prec];
+  Hierarchy *h = R.h = t->hier[hier_slot(R.prec, cb)];
   Level &L0 = h->lv[0];
   R.S = Solver{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
   R.S.dfo = R.prec == 2;
@@ -2936,18 +3014,19 @@ ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, con
   R.S.part = part;
   R.S.batched = batched;
   R.ntot = h->nslot;   // level-0 elements: padded cells and membrane entry slots
-  if (R.S.dfo) {
-    k_pack_df<<<R.ctx->wave, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, R.ntot), nullptr);
-    k_pack_df<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, R.ntot), L0.mask);
-  } else {
-    k_pack<<<R.ctx->wave, 256, 0, st>>>(rhs, L0.g, h->b64, nullptr);
-    k_pack<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask);
-  }
-  ctx->launches += 2;
+  // the scalars first: the packing of p records in S_PNZ whether any value is nonzero
   for (int q = 0; q < NSCAL; ++q) hs[q] = 0.0;
   hs[S_FLUIDVOL] = L0.fluid_vol;
   hs[S_NF] = (double)L0.nfluid;
   IBM_TRY(cudaMemcpyAsync(scal, hs, sizeof(double) * NSCAL, cudaMemcpyHostToDevice, st));
+  if (R.S.dfo) {
+    k_pack_df<<<R.ctx->wave, 256, 0, st>>>(rhs, L0.g, hi_of(h->b64), lo_of(h->b64, R.ntot), nullptr);
+    k_pack_df<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, hi_of(h->p64), lo_of(h->p64, R.ntot), L0.mask);
+  } else {
+    k_pack<<<R.ctx->wave, 256, 0, st>>>(rhs, L0.g, h->b64, nullptr, nullptr);
+    k_pack<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask, reinterpret_cast<unsigned *>(scal + S_PNZ));
+  }
+  ctx->launches += 2;
   outer_residual(R.S, false, nullptr, false);
   IBM_TRY(cudaGetLastError());
   return IBM_OK;
@@ -2998,8 +3077,10 @@ ibm_status run_begin(Run &R, cudaStream_t st) {
   // the V-cycle on p itself (precision 0 without GCR) updates ghost rows with their datum;
   // correction forms carry it in the residual
   R.S.gd = R.prec == 0 && R.gcr_m == 0 && t->has_datum ? t->gd : nullptr;
-  if (R.r64) fine_residual<double>(R.S, h->p64, R.r64, true);
-  else outer_residual(R.S, true, R.r32, true);
+  // a zero initial guess (as packed) gives A p = 0 unless ghost rows carry a datum
+  const unsigned *pnz = t->has_datum ? nullptr : reinterpret_cast<const unsigned *>(R.S.scal + S_PNZ);
+  if (R.r64) fine_residual<double>(R.S, h->p64, R.r64, true, pnz);
+  else outer_residual(R.S, true, R.r32, true, pnz);
   IBM_TRY(cudaGetLastError());
   return IBM_OK;
 }

@@ -49,6 +49,7 @@
 #include <type_traits>
 
 #include "dfloat.cuh"
+#include "storage.cuh"
 
 namespace ibm {
 namespace zm {
@@ -98,11 +99,11 @@ struct ZC {
   T m, p, s, pad;   // czm, czp, czm + czp
 };
 
-// every TMA destination starts on a 128-byte boundary
-template <typename T>
+// every TMA destination starts on a 128-byte boundary; e and r staged in their storage type S
+template <typename T, typename S = T>
 struct Smem {
-  alignas(128) T e[NE][esz<T>()];
-  alignas(128) T r[NR][rsz<T>()];
+  alignas(128) S e[NE][esz<S>()];
+  alignas(128) S r[NR][rsz<S>()];
   alignas(128) uint8_t m[NR][MSZ];
   alignas(32) ZC<T> zc[KZ_MAX + 4];   // planes k0 - 2 .. k1 + 1
   alignas(16) T cc[32][16];           // ring warp lanes' coefficients (ring rows, column cell)
@@ -162,7 +163,7 @@ struct Args {
   const T *fx, *fy, *fz;  // coarse levels: face fractions (padded level arrays); else unused
   const double *shift;
   float omega;
-  T *out;
+  void *out;              // the output e, of the storage type
   int *err;
 };
 
@@ -170,6 +171,25 @@ template <typename T>
 __device__ __forceinline__ vec4<T> ld4(const T *p) { return *reinterpret_cast<const vec4<T> *>(p); }
 template <typename T>
 __device__ __forceinline__ void st4(T *p, const vec4<T> &v) { *reinterpret_cast<vec4<T> *>(p) = v; }
+// a strip in its storage type <-> the arithmetic type
+__device__ __forceinline__ float4 lds4(const float *p) { return ld4<float>(p); }
+__device__ __forceinline__ dbl4 lds4(const double *p) { return ld4<double>(p); }
+__device__ __forceinline__ float4 lds4(const bf16 *p) {
+  const uint2 u = *reinterpret_cast<const uint2 *>(p);
+  return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+}
+__device__ __forceinline__ void sts4(float *p, const float4 &v) { st4<float>(p, v); }
+__device__ __forceinline__ void sts4(double *p, const dbl4 &v) { st4<double>(p, v); }
+__device__ __forceinline__ void sts4(bf16 *p, const float4 &v) {
+  *reinterpret_cast<uint2 *>(p) = make_uint2(bf16_pack(v.x, v.y), bf16_pack(v.z, v.w));
+}
+// a strip's values as they read back after a store of type S
+template <typename S, typename V>
+__device__ __forceinline__ V stored4(V v) {
+  v.x = as_stored<S>(v.x); v.y = as_stored<S>(v.y); v.z = as_stored<S>(v.z); v.w = as_stored<S>(v.w);
+  return v;
+}
+
 template <typename T>
 __device__ __forceinline__ vec4<T> make4(T a, T b, T c, T d) {
   vec4<T> v;
@@ -313,14 +333,15 @@ __device__ __forceinline__ unsigned invalid_bytes(int gi0, int nx, bool jok) {
 template <typename T>
 constexpr int min_ctas() { return sizeof(T) == 4 ? MIN_CTAS : 1; }
 
-template <typename T, bool COARSE>
+template <typename T, bool COARSE, typename S = T>
 __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const __grid_constant__ CUtensorMap tm_e,
                                                                          const __grid_constant__ CUtensorMap tm_r,
                                                                          const __grid_constant__ CUtensorMap tm_m,
                                                                          Args<T> a) {
   static_assert(sizeof(T) == 4 || !COARSE, "coarse levels are swept in FP32");
+  static_assert(std::is_same<typename Arith<S>::type, T>::value, "storage of the arithmetic type, or BF16 for FP32");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem<T> &s = *reinterpret_cast<Smem<T> *>(smem_raw);
+  Smem<T, S> &s = *reinterpret_cast<Smem<T, S> *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ring = warp == RING_WARP;
   const bool issuer = ring && lane == 0;
@@ -330,7 +351,7 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
     fence_mbar_init();
   }
   __syncthreads();
-  const unsigned ebytes = EY * BX * sizeof(T), rbytes = RY * BX * sizeof(T) + RY * BXM;
+  const unsigned ebytes = EY * BX * sizeof(S), rbytes = RY * BX * sizeof(S) + RY * BXM;
   const float om = a.omega;
   const T sh = a.shift ? (T)(*a.shift) : (T)0;
   // per slot: parity of its next completion (toggled when a wait sees it land); the issuer
@@ -451,11 +472,11 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
     vec4<T> Cm2[NS], Cm1[NS], C0[NS];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
-      Cm1[t] = ld4(s.e[se0] + ie0 + SR * t * BX);
-      C0[t] = ld4(s.e[sq] + ie0 + SR * t * BX);
+      Cm1[t] = lds4(s.e[se0] + ie0 + SR * t * BX);
+      C0[t] = lds4(s.e[sq] + ie0 + SR * t * BX);
       Cm2[t] = Cm1[t];
     }
-    T *const dst0 = a.out + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
+    S *const dst0 = static_cast<S *>(a.out) + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
     // unrolled by 3: the strips' register rotation (planes q-2, q-1, q) becomes renaming
 #pragma unroll 3
     for (int q = k0 - 1; q <= k1; ++q) {
@@ -471,10 +492,10 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
         if (q + 1 + DP <= k1 + 1) load_e(q + 1 + DP, wrap_e(sp1 + DP));
         if (q + DP <= k1) load_r(q + DP, wrap_r(rq + DP));
       }
-      T *P = s.e[sq], *Pm = s.e[sm1];
-      const T *Pp = s.e[sp1];
+      S *P = s.e[sq], *Pm = s.e[sm1];
+      const S *Pp = s.e[sp1];
       const int rqm = rq == 0 ? NR - 1 : rq - 1;   // rhs/mask slot of plane q-1
-      const T *R = s.r[rq], *Rm = s.r[rqm];
+      const S *R = s.r[rq], *Rm = s.r[rqm];
       const uint8_t *M = s.m[rq], *Mm = s.m[rqm];
       // z coefficients of planes q (red pass) and q-1 (black pass)
       const ZC<T> zq = s.zc[q - (k0 - 2)], zb = s.zc[q - 1 - (k0 - 2)];
@@ -485,23 +506,24 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
       const bool parq = ((y0 + ys + q) & 1) == 0;
       vec4<T> U[NS];   // the strips in plane q+1
 #pragma unroll
-      for (int t = 0; t < NS; ++t) U[t] = ld4(Pp + ie0 + SR * t * BX);
+      for (int t = 0; t < NS; ++t) U[t] = lds4(Pp + ie0 + SR * t * BX);
       // red cells of strip t of plane q (ua: its colour's u, a compile-time constant):
       // x-edges from the adjacent lanes, or the ring at the edges
       auto red_strip = [&](auto ua, const int t) {
         const int ie = ie0 + SR * t * BX;
-        const T ep = P[ie + eoff];
+        const T ep = ld1(P + ie + eoff);
         T w = __shfl_up_sync(0xffffffffu, C0[t].w, 1);
         T e = __shfl_down_sync(0xffffffffu, C0[t].x, 1);
         w = lane == 0 ? ep : w;
         e = lane == 31 ? ep : e;
-        const vec4<T> N = ld4(P + ie - BX), S = ld4(P + ie + BX);
-        const vec4<T> Rr = ld4(R + ir0 + SR * t * BX);
+        const vec4<T> N = lds4(P + ie - BX), So = lds4(P + ie + BX);
+        const vec4<T> Rr = lds4(R + ir0 + SR * t * BX);
         const unsigned mm = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM) | inval[t];
         const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
-        relax_strip<decltype(ua)::value, COARSE>(C0[t], w, e, N, S, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t],
+        relax_strip<decltype(ua)::value, COARSE>(C0[t], w, e, N, So, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t],
                                                  sy[t] + szr, zmr, zpr, sh, om, a, gid);
-        st4(P + ie, C0[t]);
+        C0[t] = stored4<S>(C0[t]);   // the registers hold what every reader of the buffer sees
+        sts4(P + ie, C0[t]);
       };
       if (!ring && red) {
         if (parq) {
@@ -519,23 +541,23 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
           const T *cc = s.cc[lane] + 3 * h;
           const int yr = h == 0 ? -1 : TY;
           const int iq0 = (yr + 2) * BX + (xs + 4), irq0 = (yr + 1) * BX + (xs + 4), imq0 = (yr + 1) * BXM + (xs + 4);
-          vec4<T> C = ld4(P + iq0);
-          const vec4<T> N = ld4(P + iq0 - BX), S = ld4(P + iq0 + BX), Zm = ld4(Pm + iq0), Zp = ld4(Pp + iq0);
-          const vec4<T> Rr = ld4(R + irq0);
+          vec4<T> C = lds4(P + iq0);
+          const vec4<T> N = lds4(P + iq0 - BX), So = lds4(P + iq0 + BX), Zm = lds4(Pm + iq0), Zp = lds4(Pp + iq0);
+          const vec4<T> Rr = lds4(R + irq0);
           const unsigned mm = *reinterpret_cast<const unsigned *>(M + imq0) | s.ccu[lane][h];
-          const T ep = P[iq0 + eoff];
+          const T ep = ld1(P + iq0 + eoff);
           T w = __shfl_up_sync(0xffffffffu, C.w, 1);
           T e = __shfl_down_sync(0xffffffffu, C.x, 1);
           w = lane == 0 ? ep : w;
           e = lane == 31 ? ep : e;
           const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + yr + 1) * a.sy + (x0 + xs + 4);
           if (((y0 + yr + q) & 1) == 0)
-            relax_strip<0, COARSE>(C, w, e, N, S, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om, a,
-                                   gid);
+            relax_strip<0, COARSE>(C, w, e, N, So, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om,
+                                   a, gid);
           else
-            relax_strip<1, COARSE>(C, w, e, N, S, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om, a,
-                                   gid);
-          st4(P + iq0, C);
+            relax_strip<1, COARSE>(C, w, e, N, So, Zm, Zp, Rr, mm, X, cc[0], cc[1], cc[2] + szr, zmr, zpr, sh, om,
+                                   a, gid);
+          sts4(P + iq0, C);
         }
         // ring column cell (x = -1 or TX): the red one of the lane's pair of rows
         if (lane < COL_LANES) {
@@ -545,8 +567,8 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
           const int ic = (cy + 2) * BX + (cxl + 4);
           const int icr = (cy + 1) * BX + (cxl + 4), icm = (cy + 1) * BXM + (cxl + 4);
           const T *cf = s.cc[lane] + 6;
-          const T cc0 = P[ic], cw = P[ic - 1], ce = P[ic + 1], cn = P[ic - BX], cs = P[ic + BX], czmv = Pm[ic],
-                  czpv = Pp[ic], crs = R[icr] - sh;
+          const T cc0 = ld1(P + ic), cw = ld1(P + ic - 1), ce = ld1(P + ic + 1), cn = ld1(P + ic - BX),
+                  cs = ld1(P + ic + BX), czmv = ld1(Pm + ic), czpv = ld1(Pp + ic), crs = ld1(R + icr) - sh;
           T v = relax1(cc0, cw, ce, cn, cs, czmv, czpv, cf[0], cf[1], cf[3 + h], cf[5 + h], zmr, zpr,
                        cf[2] + (cf[7 + h] + szr), crs, om);
           unsigned mb = M[icm];
@@ -558,40 +580,40 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
               mb = 0u;
             }
           }
-          if (((s.ccu[lane][2] >> h) & 1u) && mb == 0u) P[ic] = v;
+          if (((s.ccu[lane][2] >> h) & 1u) && mb == 0u) st1(P + ic, v);
         }
       }
       // black cells of plane q-1: neighbours all red, updated by now (in-plane ones in
       // shared memory, the z-neighbours in Cm2 and C0); store the strips from registers
       const int kb = q - 1;
       // black cells of strip t of plane q-1 (they sit at the same u as the red cells of plane q)
-      auto black_strip = [&](auto ua, const int t, T *const dk) {
+      auto black_strip = [&](auto ua, const int t, S *const dk) {
         const int ie = ie0 + SR * t * BX;
-        const T ep = Pm[ie + eoff];
+        const T ep = ld1(Pm + ie + eoff);
         T w = __shfl_up_sync(0xffffffffu, Cm1[t].w, 1);
         T e = __shfl_down_sync(0xffffffffu, Cm1[t].x, 1);
         w = lane == 0 ? ep : w;
         e = lane == 31 ? ep : e;
-        const vec4<T> N = ld4(Pm + ie - BX), S = ld4(Pm + ie + BX);
-        const vec4<T> Rr = ld4(Rm + ir0 + SR * t * BX);
+        const vec4<T> N = lds4(Pm + ie - BX), So = lds4(Pm + ie + BX);
+        const vec4<T> Rr = lds4(Rm + ir0 + SR * t * BX);
         const unsigned mm = *reinterpret_cast<const unsigned *>(Mm + im0 + SR * t * BXM) | inval[t];
         const long long gid = (long long)q * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
-        relax_strip<decltype(ua)::value, COARSE>(Cm1[t], w, e, N, S, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t],
+        relax_strip<decltype(ua)::value, COARSE>(Cm1[t], w, e, N, So, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t],
                                                  sy[t] + szb, zmb, zpb, sh, om, a, gid);
         if ((inval[t] & 0xffu) == 0u) {   // the strip's row is in the grid
-          T *dst = dk + (long long)(SR * t) * a.px;
+          S *dst = dk + (long long)(SR * t) * a.px;
           if (inval[t] == 0u) {
-            st4(dst, Cm1[t]);
+            sts4(dst, Cm1[t]);
           } else {
-            if (!(inval[t] & 0xff00u)) dst[1] = Cm1[t].y;
-            if (!(inval[t] & 0xff0000u)) dst[2] = Cm1[t].z;
-            if (!(inval[t] & 0xff000000u)) dst[3] = Cm1[t].w;
-            dst[0] = Cm1[t].x;
+            if (!(inval[t] & 0xff00u)) st1(dst + 1, Cm1[t].y);
+            if (!(inval[t] & 0xff0000u)) st1(dst + 2, Cm1[t].z);
+            if (!(inval[t] & 0xff000000u)) st1(dst + 3, Cm1[t].w);
+            st1(dst, Cm1[t].x);
           }
         }
       };
       if (!ring && kb >= k0 && kb < k1) {
-        T *const dk = dst0 + (long long)(kb + 1) * a.sz;
+        S *const dk = dst0 + (long long)(kb + 1) * a.sz;
         if (parq) {
           black_strip(U0{}, 0, dk);
           black_strip(U1{}, 1, dk);

@@ -43,7 +43,8 @@ class ibm_mesh(C.Structure):
 class ibm_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32), ("max_cycles", C.c_int32),
                 ("inner_cycles", C.c_int32), ("use_graph", C.c_int32), ("omega", C.c_double),
-                ("krylov", C.c_int32), ("method", C.c_int32), ("srj_steps", C.c_int32)]
+                ("krylov", C.c_int32), ("method", C.c_int32), ("srj_steps", C.c_int32),
+                ("coarse_bf16", C.c_int32)]
 
 
 class ibm_helmholtz_opts(C.Structure):
@@ -232,6 +233,12 @@ class SolveOpts:
     krylov: int = -1
     method: int = 0
     srj_steps: int = 8
+    coarse_bf16: int = 0
+
+
+def _c_opts(o: SolveOpts) -> ibm_solve_opts:
+    return ibm_solve_opts(o.precision, o.nu1, o.nu2, o.max_cycles, o.inner_cycles, o.use_graph, o.omega, o.krylov,
+                          o.method, o.srj_steps, o.coarse_bf16)
 
 
 def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, stream=None, history_cap: int = 256,
@@ -239,7 +246,7 @@ def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, strea
     """Solve in place: rhs, p are CUDA float64 tensors [nz, ny, nx].  Returns a dict report."""
     lib = load_library()
     o = opts or SolveOpts()
-    co = ibm_solve_opts(o.precision, o.nu1, o.nu2, o.max_cycles, o.inner_cycles, o.use_graph, o.omega, o.krylov, o.method, o.srj_steps)
+    co = _c_opts(o)
     hist = np.zeros(max(1, history_cap))
     info = ibm_solve_info(0, 0, 0.0, 0.0, 0.0, hist.ctypes.data, history_cap)
     s = lib.poisson_solve(ctx, tables, _ptr(rhs), float(tol), _ptr(p), C.byref(co), C.byref(info), _stream(stream))
@@ -356,7 +363,7 @@ def poisson_solve_batched(ctx, tables, rhs_list, tol, p_list, opts: "SolveOpts |
     lib = load_library()
     n = len(tables)
     o = opts or SolveOpts()
-    co = ibm_solve_opts(o.precision, o.nu1, o.nu2, o.max_cycles, o.inner_cycles, o.use_graph, o.omega, o.krylov, o.method, o.srj_steps)
+    co = _c_opts(o)
     T = (C.c_void_p * max(1, n))(*[t.value if hasattr(t, "value") else t for t in tables])
     R = (C.c_void_p * max(1, n))(*[r.data_ptr() for r in rhs_list])
     Pp = (C.c_void_p * max(1, n))(*[x.data_ptr() for x in p_list])
@@ -379,7 +386,7 @@ def ibm_autotune(ctx, tables, precision: int, rhs, p_work, tol: float = 1e-10, s
     _check(load_library().ibm_autotune(ctx, tables, precision, _ptr(rhs), _ptr(p_work), float(tol), C.byref(best),
                                        C.byref(ms), _stream(stream)), "ibm_autotune")
     return SolveOpts(best.precision, best.nu1, best.nu2, best.max_cycles, best.inner_cycles, best.use_graph,
-                     best.omega, best.krylov, best.method, best.srj_steps), float(ms.value)
+                     best.omega, best.krylov, best.method, best.srj_steps, best.coarse_bf16), float(ms.value)
 
 
 # ----------------------------------------------------------------------------- conveniences

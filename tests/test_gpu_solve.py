@@ -41,7 +41,7 @@ def _lambda_tol(b, fl):
     return 1e-8 * float(np.sqrt(np.mean((bf - bf.mean()) ** 2)))
 
 
-def _parity(ctx, xf, yf, zf, meshes, seed, oracle="gmres", modes=(0, 1, 2), b=None):
+def _parity(ctx, xf, yf, zf, meshes, seed, oracle="gmres", modes=(0, 1, 2), b=None, **kw):
     pkg, c = ctx
     g = Grid(xf, yf, zf)
     ib, G = OC.classify(g, meshes)
@@ -51,8 +51,10 @@ def _parity(ctx, xf, yf, zf, meshes, seed, oracle="gmres", modes=(0, 1, 2), b=No
     T = pkg.Tables(c, xf, yf, zf, meshes)
     fl = ib == 0
     out = {}
-    for prec in modes:
-        p, rep = _solve_gpu(pkg, T, b, prec)
+    for mode in modes:
+        # a mode is a precision, or (precision, extra solve options)
+        prec, extra = (mode, {}) if isinstance(mode, int) else mode
+        p, rep = _solve_gpu(pkg, T, b, prec, **kw, **extra)
         assert rep["status"] == "IBM_OK" and rep["rel_resid"] <= TOL
         # the residual the oracle computes for the GPU's p, on the oracle's own tables
         assert OSys.relative_residual(g, ib, G, b, p) <= 1.05 * TOL
@@ -62,7 +64,7 @@ def _parity(ctx, xf, yf, zf, meshes, seed, oracle="gmres", modes=(0, 1, 2), b=No
             gerr = np.max(np.abs(p.ravel()[G.cell] - p_o.ravel()[G.cell])) / np.max(np.abs(p_o[fl]))
             assert gerr <= 10 * PARITY
         assert abs(rep["lambda"] - lam_o) <= _lambda_tol(b, fl), (prec, rep["lambda"], lam_o)
-        out[prec] = (err, rep)
+        out[prec if not extra else (prec, tuple(sorted(extra.items())))] = (err, rep)
     T.close()
     return out
 
@@ -98,15 +100,33 @@ def test_multi_tile_mean_carrying_rhs(ctx):
     _parity(ctx, xf, yf, zf, [synth.octa_sphere(4, (0.47, 0.52, 0.5), 0.21)], 12, b=b)
 
 
+def test_coarse_bf16_storage(ctx):
+    """BF16 storage of the z-march coarse levels' e and r (modes 1 and 2): 160 x 130 x 112
+    stretched cells, so level 1 (80 x 65 x 56) has more than 2^18 cells and is stored in BF16,
+    with ragged tiles on it; the refined pressure meets the same bar against the oracle."""
+    xf, yf, zf = synth.faces_tanh(160, 1.5), synth.faces_uniform(130), synth.faces_tanh(112, 1.5)
+    out = _parity(ctx, xf, yf, zf, [synth.ellipsoid(5, (0.2, 0.1, 0.08), 30.0, (0.48, 0.5, 0.5))], 14, modes=(1, 2),
+                  coarse_bf16=1)
+    pkg, c = ctx
+    T = pkg.Tables(c, xf, yf, zf, [synth.ellipsoid(5, (0.2, 0.1, 0.08), 30.0, (0.48, 0.5, 0.5))])
+    rhs = torch.from_numpy(synth.rhs_divergence(xf, yf, zf, 14)).cuda()
+    p = torch.zeros_like(rhs)
+    with pytest.raises(pkg.IbmError):   # FP64 multigrid has no BF16 form
+        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=0, coarse_bf16=1))
+    T.close()
+    assert all(rep["cycles"] <= 12 for _, rep in out.values()), out
+
+
 def test_no_body_ragged(ctx):
     _parity(ctx, synth.faces_uniform(33), synth.faces_tanh(24, 2.0), synth.faces_uniform(20), [], 3)
 
 
 def test_cfg2_full_256_elementwise(ctx):
-    """The full 256^3 stretched grid around the ellipsoid: every mode against the oracle's
-    GMRES solution element by element (1e-8 relative L2 over fluid cells after the gauge)."""
+    """The full 256^3 stretched grid around the ellipsoid: every mode, and mode 1 with BF16
+    coarse storage, against the oracle's GMRES solution element by element (1e-8 relative L2
+    over fluid cells after the gauge)."""
     pr = synth.cfg2(256)
-    _parity(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, pr.seed)
+    _parity(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, pr.seed, modes=(0, 1, 2, (1, {"coarse_bf16": 1})))
 
 
 def test_cfg2_full_256_residual_property(ctx):
