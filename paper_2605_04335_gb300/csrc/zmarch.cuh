@@ -477,8 +477,10 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
       Cm2[t] = Cm1[t];
     }
     S *const dst0 = static_cast<S *>(a.out) + (long long)(y0 + ys + 1) * a.px + (x0 + xs + 4);
-    // unrolled by 3: the strips' register rotation (planes q-2, q-1, q) becomes renaming
-#pragma unroll 3
+    // not unrolled: with the coarse levels' irregular-cell path, three copies of the step
+    // overflow the instruction cache (measured: most stalls waiting for instructions), and the
+    // strips' rotation by register moves costs the FP32 kernel nothing measurable
+#pragma unroll 1
     for (int q = k0 - 1; q <= k1; ++q) {
       const int sp1 = wrap_e(sq + 1), sm1 = sq == 0 ? NE - 1 : sq - 1;
       wait_e(sp1, WAIT_LIMIT);
