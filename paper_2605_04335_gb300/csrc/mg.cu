@@ -431,7 +431,7 @@ template <> struct Pair<double> {
 // before the arithmetic; children past an odd fine extent are halo cells (mask 1) whose
 // outward neighbours are not read.
 template <typename T, typename SF = T, typename SC = T>
-__global__ void __launch_bounds__(128) k_restrict8(LV<T> f, const SF *e, const SF *r, const double *shift, LV<T> cv,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_restrict8(LV<T> f, const SF *e, const SF *r, const double *shift, LV<T> cv,
                                                    SC *rc, SC *ec, double *partials) {
   __shared__ double sm[128];
   double acc_all = 0.0;
@@ -549,6 +549,11 @@ __global__ void k_finalize_shift(const double *partials, int nb, const double *f
   if (threadIdx.x == 0) *shift = *fluid_vol > 0 ? s / *fluid_vol : 0.0;
 }
 
+// a fused multiply-add in the element type
+template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+
 // Prolongation e_f += P e_c, one thread per coarse cell (I,J,K) and its 2x2x2 children,
 // coarse rows strided over blockIdx.y.  Along each axis a child takes weight 1-t on its
 // parent and t on the parent's neighbour on the child's side (off = -1 or +1; t = 0 without
@@ -560,7 +565,7 @@ __global__ void k_finalize_shift(const double *partials, int nb, const double *f
 // fluid rows are left unchanged.  The children's e and masks are loaded with the coarse
 // block, before any arithmetic.
 template <typename T, typename SC = T, typename SF = T>
-__global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef,
                                                   const int8_t *offx, const int8_t *offy, const int8_t *offz,
                                                   const float *tx, const float *ty, const float *tz) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -605,7 +610,13 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const SC *ec, const 
       for (int y = 0; y < 3; ++y)
 #pragma unroll
         for (int x = 0; x < 3; ++x) e[z][y][x] = ld1(ec + c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1));
-    // contract x, then y, then z
+    // contract x, then y, then z.  The first child of a coarse cell lies left of its centre
+    // and the second right (the coarse faces are every other fine face), so child 0 weighs
+    // columns 0 and 1 and child 1 columns 1 and 2: two terms per child, the third weight being
+    // zero (w2 = 0 for child 0, w0 = 0 for child 1).
+    auto two = [](const float (&w)[2][3], int a, T v0, T v1, T v2) {
+      return a == 0 ? fma_t<T>((T)w[0][1], v1, (T)w[0][0] * v0) : fma_t<T>((T)w[1][2], v2, (T)w[1][1] * v1);
+    };
     auto contract = [&](const T (&v)[3][3][3], T (&out)[2][2][2]) {
       T vx[2][3][3];
 #pragma unroll
@@ -613,23 +624,20 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const SC *ec, const 
 #pragma unroll
         for (int z = 0; z < 3; ++z)
 #pragma unroll
-          for (int y = 0; y < 3; ++y)
-            vx[a][z][y] = (T)wx[a][0] * v[z][y][0] + (T)wx[a][1] * v[z][y][1] + (T)wx[a][2] * v[z][y][2];
+          for (int y = 0; y < 3; ++y) vx[a][z][y] = two(wx, a, v[z][y][0], v[z][y][1], v[z][y][2]);
       T vxy[2][2][3];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-          for (int z = 0; z < 3; ++z)
-            vxy[a][b][z] = (T)wy[b][0] * vx[a][z][0] + (T)wy[b][1] * vx[a][z][1] + (T)wy[b][2] * vx[a][z][2];
+          for (int z = 0; z < 3; ++z) vxy[a][b][z] = two(wy, b, vx[a][z][0], vx[a][z][1], vx[a][z][2]);
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-          for (int d = 0; d < 2; ++d)
-            out[d][b][a] = (T)wz[d][0] * vxy[a][b][0] + (T)wz[d][1] * vxy[a][b][1] + (T)wz[d][2] * vxy[a][b][2];
+          for (int d = 0; d < 2; ++d) out[d][b][a] = two(wz, d, vxy[a][b][0], vxy[a][b][1], vxy[a][b][2]);
     };
     T num[2][2][2], den[2][2][2];
     contract(e, num);
@@ -658,8 +666,9 @@ __global__ void __launch_bounds__(128) k_prolong8(LV<T> cv, const SC *ec, const 
         const bool u0 = fluid_row(fm[d][b].x) && den[d][b][0] > (T)0,
                    u1 = fluid_row(fm[d][b].y) && den[d][b][1] > (T)0;
         SF *rowp = ef + fr[d][b];
-        if (u0) st1(rowp, fe[d][b][0] + num[d][b][0] / den[d][b][0]);
-        if (u1) st1(rowp + 1, fe[d][b][1] + num[d][b][1] / den[d][b][1]);
+        // a fully fluid block has den = 1 exactly: its correction is num itself
+        if (u0) st1(rowp, fe[d][b][0] + (inr ? num[d][b][0] : num[d][b][0] / den[d][b][0]));
+        if (u1) st1(rowp + 1, fe[d][b][1] + (inr ? num[d][b][1] : num[d][b][1] / den[d][b][1]));
       }
   }
 }
@@ -1764,9 +1773,6 @@ struct GcrState {           // device memory
   double mu;                // volume-weighted fluid mean of A z
 };
 
-template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c);
-template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
 
 // q = A z on every row of the finest level (regular fluid rows here; 0 on other cells), with
 // block partials of sum V q over regular fluid rows at part[b]
