@@ -116,7 +116,7 @@ struct Hierarchy {
   // finest level ping-pong for the fused z-march sweep: the second buffer of the
   // level-0 unknown (p64 in FP64 mode, lv[0].e in mixed mode) and TMA tensor maps
   void *e_alt = nullptr;
-  int grid_blocks[2] = {1216, 1216};        // resident blocks of the restriction / prolongation
+  int grid_blocks[1] = {1216};              // resident blocks of the restriction
   long long slotcap = 0;                    // membranes: ghost-entry slots after the finest cells
   long long nslot = 0;                      // elements of the finest arrays (cells + slots); in
                                             // double-FP32 mode the hi/lo split point of p and b

@@ -31,6 +31,7 @@
 namespace ibm {
 
 constexpr int MAX_COARSE = 128;
+constexpr int PROLONG_KC = 32;          // coarse planes per thread of the prolongation's z-march
 constexpr int RESTRICT_BLOCKS = 1216;   // restriction blocks (at most; one partial sum each; fixed width)
 constexpr size_t GJ_SMEM_MAX = 160 * 1024;   // coarsest Gauss-Jordan in shared memory up to this size
 
@@ -554,23 +555,24 @@ template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c);
 template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
 template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
 
-// Prolongation e_f += P e_c, one thread per coarse cell (I,J,K) and its 2x2x2 children,
-// coarse rows strided over blockIdx.y.  Along each axis a child takes weight 1-t on its
-// parent and t on the parent's neighbour on the child's side (off = -1 or +1; t = 0 without
-// one), so each child reads the 3x3x3 coarse block around (I,J,K).  Coarse e is zero on
-// every non-fluid coarse cell (zeroed by the restriction, written only on fluid rows), so
-// the weighted sum needs no mask and is contracted axis by axis; the renormalising
-// denominator (sum of the weights of the fluid corners) is 1 where the whole block is fluid
-// (inner flag), else summed the same way over the fluid indicator.  Children that are not
-// fluid rows are left unchanged.  The children's e and masks are loaded with the coarse
-// block, before any arithmetic.
+// Prolongation e_f += P e_c as a z-march: one thread per coarse column (I,J) and a chunk of kc
+// coarse planes, each coarse cell with its 2x2x2 children.  Along each axis a child takes
+// weight 1-t on its parent and t on the parent's neighbour on the child's side (off = -1 or
+// +1; t = 0 without one).  Coarse e is zero on every non-fluid coarse cell (zeroed by the
+// restriction, written only on fluid rows), so the weighted sum needs no mask and is contracted
+// axis by axis: each coarse plane's 3x3 neighbourhood of the column is contracted in x, then y,
+// once (2x2 values, the last three planes kept in registers), and each child plane in z.  The
+// renormalising denominator (sum of the weights of the fluid corners) is 1 where the whole
+// 3x3x3 block is fluid (inner flag), else summed the same way over the fluid indicator.
+// Children that are not fluid rows are left unchanged; rows past the fine extent (odd sizes)
+// are halo rows (mask 1), never updated.
 template <typename T, typename SC = T, typename SF = T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef,
-                                                  const int8_t *offx, const int8_t *offy, const int8_t *offz,
-                                                  const float *tx, const float *ty, const float *tz) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= cv.nx) return;
-  float wx[2][3], wy[2][3], wz[2][3];
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4)
+    k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef, const int8_t *offx,
+               const int8_t *offy, const int8_t *offz, const float *tx, const float *ty, const float *tz, int kc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
+  const int K0 = blockIdx.z * kc, K1 = min(cv.nz, K0 + kc);
+  if (I >= cv.nx || K0 >= K1) return;
   auto axis = [](int c0, int nf, const int8_t *off, const float *t, float w[2][3]) {
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
@@ -582,14 +584,42 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_prolong8(LV<T> 
       w[a][2] = o > 0 ? tt : 0.f;
     }
   };
+  float wx[2][3], wy[2][3];
   axis(2 * I, f.nx, offx, tx, wx);
-  const int crows = cv.ny * cv.nz;
-  for (int row = blockIdx.y; row < crows; row += gridDim.y) {
-    const int J = row % cv.ny, K = row / cv.ny;
-    axis(2 * J, f.ny, offy, ty, wy);
-    axis(2 * K, f.nz, offz, tz, wz);
-    // children rows (d = z child, b = y child) at x = 2I; rows past the fine extent (odd
-    // sizes) are halo rows: mask 1, never updated
+  axis(2 * J, f.ny, offy, ty, wy);
+  // The first child of a coarse cell lies left of its centre and the second right (the coarse
+  // faces are every other fine face), so child 0 weighs columns 0 and 1 and child 1 columns 1
+  // and 2: two terms per child, the third weight being zero.
+  auto two = [](const float (&w)[2][3], int a, T v0, T v1, T v2) {
+    return a == 0 ? fma_t<T>((T)w[0][1], v1, (T)w[0][0] * v0) : fma_t<T>((T)w[1][2], v2, (T)w[1][1] * v1);
+  };
+  // x then y contraction of a 3x3 neighbourhood: o[a][b] for children a (x) and b (y)
+  auto contract_xy = [&](const T (&v)[3][3], T (&o)[2][2]) {
+    T vx[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) vx[a][y] = two(wx, a, v[y][0], v[y][1], v[y][2]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) o[a][b] = two(wy, b, vx[a][0], vx[a][1], vx[a][2]);
+  };
+  auto plane = [&](int Kp, T (&o)[2][2]) {
+    const long long c = vidx(cv, I, J, Kp);
+    T v[3][3];
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) v[y][x] = ld1(ec + c + (y - 1) * cv.sy + (x - 1));
+    contract_xy(v, o);
+  };
+  T pm[2][2], p0[2][2], pp[2][2];   // coarse planes K-1, K, K+1 contracted in x and y
+  plane(K0 - 1, pm);
+  plane(K0, p0);
+#pragma unroll 1
+  for (int K = K0; K < K1; ++K) {
+    // children rows (d = z child, b = y child) at x = 2I
     long long fr[2][2];
     uchar2 fm[2][2];
     T fe[2][2][2];
@@ -603,61 +633,36 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_prolong8(LV<T> 
       }
     const long long c0 = vidx(cv, I, J, K);
     const bool inr = inner[c0] != 0;
-    T e[3][3][3];
-#pragma unroll
-    for (int z = 0; z < 3; ++z)
-#pragma unroll
-      for (int y = 0; y < 3; ++y)
-#pragma unroll
-        for (int x = 0; x < 3; ++x) e[z][y][x] = ld1(ec + c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1));
-    // contract x, then y, then z.  The first child of a coarse cell lies left of its centre
-    // and the second right (the coarse faces are every other fine face), so child 0 weighs
-    // columns 0 and 1 and child 1 columns 1 and 2: two terms per child, the third weight being
-    // zero (w2 = 0 for child 0, w0 = 0 for child 1).
-    auto two = [](const float (&w)[2][3], int a, T v0, T v1, T v2) {
-      return a == 0 ? fma_t<T>((T)w[0][1], v1, (T)w[0][0] * v0) : fma_t<T>((T)w[1][2], v2, (T)w[1][1] * v1);
-    };
-    auto contract = [&](const T (&v)[3][3][3], T (&out)[2][2][2]) {
-      T vx[2][3][3];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int z = 0; z < 3; ++z)
-#pragma unroll
-          for (int y = 0; y < 3; ++y) vx[a][z][y] = two(wx, a, v[z][y][0], v[z][y][1], v[z][y][2]);
-      T vxy[2][2][3];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-          for (int z = 0; z < 3; ++z) vxy[a][b][z] = two(wy, b, vx[a][z][0], vx[a][z][1], vx[a][z][2]);
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-          for (int d = 0; d < 2; ++d) out[d][b][a] = two(wz, d, vxy[a][b][0], vxy[a][b][1], vxy[a][b][2]);
-    };
+    plane(K + 1, pp);
+    float wz[2][3];
+    axis(2 * K, f.nz, offz, tz, wz);
     T num[2][2][2], den[2][2][2];
-    contract(e, num);
-    if (inr) {
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          num[d][b][a] = two(wz, d, pm[a][b], p0[a][b], pp[a][b]);
+          den[d][b][a] = (T)1;
+        }
+    if (!inr) {
+      T m[3][2][2];   // the fluid indicator's planes K-1, K, K+1, contracted in x and y
+#pragma unroll
+      for (int z = 0; z < 3; ++z) {
+        T v[3][3];
+#pragma unroll
+        for (int y = 0; y < 3; ++y)
+#pragma unroll
+          for (int x = 0; x < 3; ++x) v[y][x] = cv.mask[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)] == 0 ? (T)1 : (T)0;
+        contract_xy(v, m[z]);
+      }
 #pragma unroll
       for (int d = 0; d < 2; ++d)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-          for (int a = 0; a < 2; ++a) den[d][b][a] = (T)1;
-    } else {
-      T m[3][3][3];
-#pragma unroll
-      for (int z = 0; z < 3; ++z)
-#pragma unroll
-        for (int y = 0; y < 3; ++y)
-#pragma unroll
-          for (int x = 0; x < 3; ++x)
-            m[z][y][x] = cv.mask[c0 + (z - 1) * cv.sz + (y - 1) * cv.sy + (x - 1)] == 0 ? (T)1 : (T)0;
-      contract(m, den);
+          for (int a = 0; a < 2; ++a) den[d][b][a] = two(wz, d, m[0][a][b], m[1][a][b], m[2][a][b]);
     }
 #pragma unroll
     for (int d = 0; d < 2; ++d)
@@ -669,6 +674,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_prolong8(LV<T> 
         // a fully fluid block has den = 1 exactly: its correction is num itself
         if (u0) st1(rowp, fe[d][b][0] + (inr ? num[d][b][0] : num[d][b][0] / den[d][b][0]));
         if (u1) st1(rowp + 1, fe[d][b][1] + (inr ? num[d][b][1] : num[d][b][1] / den[d][b][1]));
+      }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        pm[a][b] = p0[a][b];
+        p0[a][b] = pp[a][b];
       }
   }
 }
@@ -2375,13 +2387,11 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out, 
     const Level &L = h->lv[l];
     if ((long long)L.g.nx * L.g.ny * L.g.nz <= TAIL_CELLS && nl - l <= TAIL_MAX_LEVELS) { h->tail_level = l; break; }
   }
-  // one wave of the row-strided restriction and prolongation kernels
+  // one wave of the row-strided restriction
   {
-    int sms = t->ctx->sm_count > 0 ? t->ctx->sm_count : 152, pr = 0, pp = 0;
+    int sms = t->ctx->sm_count > 0 ? t->ctx->sm_count : 152, pr = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pr, k_restrict8<T>, 128, 0) != cudaSuccess || pr < 1) pr = 4;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pp, k_prolong8<T>, 128, 0) != cudaSuccess || pp < 1) pp = 8;
     h->grid_blocks[0] = pr * sms;
-    h->grid_blocks[1] = pp * sms;
   }
 #undef HTRY
   *out = h;
@@ -2763,14 +2773,18 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   double *cshift = S.scal + S_LEVEL_SHIFT + (l + 1);
   k_finalize_shift<<<1, 256, 0, S.st>>>(S.part, nparts, h->d_fvol + (l + 1), cshift);
   vcycle<T>(S, l + 1, ec, rc, cshift, nullptr);
-  const int pgx = (int)nblk(C.g.nx, 128);
-  dim3 gp(pgx, std::max(1, std::min(C.g.ny * C.g.nz, h->grid_blocks[1] / pgx)));
+  // coarse columns (x: 128 per block, y: one per block) and chunks of kc planes: up to
+  // PROLONG_KC, shorter on small levels so that a launch still has about two waves of blocks
+  const long long pcols = nblk(C.g.nx, 128) * (long long)C.g.ny;
+  const int kc = (int)std::max(1LL, std::min<long long>(PROLONG_KC, pcols * C.g.nz / (16LL * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152))));
+  dim3 gp((unsigned)nblk(C.g.nx, 128), (unsigned)C.g.ny, (unsigned)((C.g.nz + kc - 1) / kc));
   const int nxf = F.g.nx, nyf = F.g.ny;
   auto prolong_from = [&](auto sc, auto sf) {
     using SC = decltype(sc);
     using SF = decltype(sf);
     k_prolong8<T, SC, SF><<<gp, 128, 0, S.st>>>(view<T>(C), (const SC *)ec, C.inner, view<T>(F), (SF *)e, F.poff,
-                                                F.poff + nxf, F.poff + nxf + nyf, F.pt, F.pt + nxf, F.pt + nxf + nyf);
+                                                F.poff + nxf, F.poff + nxf + nyf, F.pt, F.pt + nxf, F.pt + nxf + nyf,
+                                                kc);
   };
   if constexpr (sizeof(T) == 4) {
     if (C.bf16 && F.bf16) prolong_from(bf16{}, bf16{});
