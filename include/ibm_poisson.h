@@ -106,6 +106,11 @@ typedef struct {
                            even); precision 1 or 2, closed bodies (IBM_ERR_INVALID_ARG
                            otherwise).  A storage experiment of this library; the paper runs
                            FP64 throughout.  The hierarchy is kept beside the FP32 one.     [0] */
+  int32_t sweep_chunk;  /* planes per z-chunk of the finest level's fused sweep (the z extent
+                           of its tiles; each x-y tile is 128 x 14 cells); 0: chosen by the
+                           sweep's cost model (the fewest plane steps for one wave of resident
+                           blocks), else 1..256 (IBM_ERR_INVALID_ARG outside).  Searched by
+                           ibm_autotune.                                                  [0] */
 } ibm_solve_opts;
 
 /* Solve report.  resid_history (host, optional) receives the relative residual after
@@ -354,8 +359,9 @@ ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *cons
 /* Autotuner: times complete solves of the given problem (rhs_dev, tol) with candidate
  * smoother schedules -- over-relaxation 1.2/1.3/1.4, sweeps (1,1)/(2,1)/(2,2) and, for
  * precision 1 or 2, 1/2/3 FP32 V-cycles per refinement step; Krylov acceleration none or
- * GCR(2), and GCR(8) on membrane tables -- and returns the fastest in *best
- * (its time in *best_ms, optional).  p_work_dev (double[ncell], device) is overwritten.
+ * GCR(2), and GCR(8) on membrane tables -- then, for the fastest, the z extent of the fused
+ * sweep's tiles (sweep_chunk: the cost model's choice, 128, 64, 32 planes), and returns the
+ * fastest in *best (its time in *best_ms, optional).  p_work_dev (double[ncell], device) is overwritten.
  * Use the result for poisson_solve / poisson_solve_batched of similar problems.
  * With a tune cache (ibm_ctx_create), the cache is read first: an entry for the same grid
  * (cell counts and a hash of the face coordinates), precision and body kind (closed or

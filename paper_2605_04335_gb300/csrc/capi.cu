@@ -65,7 +65,7 @@ ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const 
 struct TuneEntry {
   std::string key;
   double omega = 1.3, ms = 0.0;
-  int nu1 = 2, nu2 = 2, inner = 2, krylov = -1;
+  int nu1 = 2, nu2 = 2, inner = 2, krylov = -1, chunk = 0;
 };
 
 static std::string tune_key(const ibm_tables *t, int precision) {
@@ -111,6 +111,8 @@ static std::vector<TuneEntry> tune_read(const std::string &path) {
         !json_num(line, "inner_cycles", &inner) || !json_num(line, "krylov", &kry) || !json_num(line, "ms", &e.ms))
       continue;
     e.nu1 = (int)nu1; e.nu2 = (int)nu2; e.inner = (int)inner; e.krylov = (int)kry;
+    double chunk = 0;
+    if (json_num(line, "sweep_chunk", &chunk)) e.chunk = (int)chunk;
     out.push_back(e);
   }
   return out;
@@ -128,8 +130,9 @@ static bool tune_write(const std::string &path, const std::vector<TuneEntry> &es
       const TuneEntry &e = es[q];
       std::snprintf(buf, sizeof buf,
                     "{\"key\": \"%s\", \"omega\": %.17g, \"nu1\": %d, \"nu2\": %d, \"inner_cycles\": %d, "
-                    "\"krylov\": %d, \"ms\": %.6g}%s\n",
-                    e.key.c_str(), e.omega, e.nu1, e.nu2, e.inner, e.krylov, e.ms, q + 1 < es.size() ? "," : "");
+                    "\"krylov\": %d, \"sweep_chunk\": %d, \"ms\": %.6g}%s\n",
+                    e.key.c_str(), e.omega, e.nu1, e.nu2, e.inner, e.krylov, e.chunk, e.ms,
+                    q + 1 < es.size() ? "," : "");
       f << buf;
     }
     f << "]}\n";
@@ -364,6 +367,7 @@ void ibm_solve_opts_default(ibm_solve_opts *o) {
   o->method = 0;
   o->srj_steps = 8;
   o->coarse_bf16 = 0;
+  o->sweep_chunk = 0;
 }
 
 ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol, double *p_dev,
@@ -375,7 +379,8 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
   if (!(o.precision >= 0 && o.precision <= 2) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.max_cycles < 0 ||
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0) || o.krylov < -1 || o.krylov > 8 || o.method < 0 ||
       o.method > 1 || o.srj_steps < 1 || o.srj_steps > 64 || (o.method == 1 && o.precision != 0) ||
-      o.coarse_bf16 < 0 || o.coarse_bf16 > 1 || (o.coarse_bf16 && (o.precision == 0 || t->membrane)))
+      o.coarse_bf16 < 0 || o.coarse_bf16 > 1 || (o.coarse_bf16 && (o.precision == 0 || t->membrane)) ||
+      o.sweep_chunk < 0 || o.sweep_chunk > 256)
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
@@ -419,7 +424,8 @@ static bool valid_opts(const ibm_solve_opts &o) {
   return o.precision >= 0 && o.precision <= 2 && o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 &&
          o.max_cycles >= 0 && o.inner_cycles >= 1 && o.omega > 0.0 && o.omega < 2.0 && o.krylov >= -1 &&
          o.krylov <= 8 && o.method == 0 &&   // batched: the multigrid solver
-         (o.coarse_bf16 == 0 || (o.coarse_bf16 == 1 && o.precision != 0));
+         (o.coarse_bf16 == 0 || (o.coarse_bf16 == 1 && o.precision != 0)) && o.sweep_chunk >= 0 &&
+         o.sweep_chunk <= 256;
 }
 
 ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,
@@ -466,6 +472,7 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
         best->precision = precision;
         best->omega = e.omega; best->nu1 = e.nu1; best->nu2 = e.nu2; best->inner_cycles = e.inner;
         best->krylov = e.krylov;
+        best->sweep_chunk = e.chunk;
         if (best_ms) *best_ms = e.ms;
         return IBM_OK;
       }
@@ -509,6 +516,28 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
           }
           if (ms_best < best_t) { best_t = ms_best; *best = cand; }
         }
+  // the tiles' z extent for the best schedule: the cost model's chunking, then fixed chunks
+  if (best_t < 1e29) {
+    const int chunks[3] = {128, 64, 32};
+    cand = *best;
+    for (int c : chunks) {
+      cand.sweep_chunk = c;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaMemsetAsync(p_work_dev, 0, bytes, st);
+        cudaEventRecord(e0, st);
+        ibm_solve_info info{};
+        ibm_status s = ibm::solve_impl(ctx, const_cast<ibm_tables *>(t), rhs_dev, tol, p_work_dev, &cand, &info, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        if (s != IBM_OK) { ms_best = 1e30f; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_best = std::min(ms_best, ms);
+      }
+      if (ms_best < best_t) { best_t = ms_best; *best = cand; }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best_t >= 1e29) return last != IBM_OK ? last : IBM_ERR_NOT_CONVERGED;
@@ -517,7 +546,7 @@ ibm_status ibm_autotune(ibm_ctx *ctx, const ibm_tables *t, int32_t precision, co
     std::vector<ibm::TuneEntry> es = ibm::tune_read(ctx->tune_cache);
     ibm::TuneEntry e;
     e.key = key; e.omega = best->omega; e.nu1 = best->nu1; e.nu2 = best->nu2; e.inner = best->inner_cycles;
-    e.krylov = best->krylov; e.ms = best_t;
+    e.krylov = best->krylov; e.chunk = best->sweep_chunk; e.ms = best_t;
     es.push_back(e);
     if (!ibm::tune_write(ctx->tune_cache, es)) return IBM_ERR_INVALID_ARG;
   }

@@ -2562,6 +2562,7 @@ struct Solver {
   bool dfo = false;   // double-FP32 outer loop (precision mode 2)
   double *scal = nullptr, *part = nullptr;   // this solve's device scalars and block partials
   bool batched = false;                      // one of several problems advancing together
+  int sweep_chunk = 0;                       // planes per z-chunk of the fine fused sweep (0: model)
   const double *gd = nullptr;                // Neumann datum added by the level-0 ghost updates
                                              // (the V-cycle on p itself: precision 0 without GCR)
   // measurement only: events recorded on the stream around each fine-level sweep kernel
@@ -2621,7 +2622,9 @@ void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
   // item gets its own CTA and chunks keep at least 24 planes, so that several problems'
   // sweeps share the GPU without the extra planes of short chunks.
   int best_kz = std::min(a.nz, zm::KZ_MAX);
-  if (S.batched) {
+  if (!coarse && S.sweep_chunk > 0) {
+    best_kz = std::min(std::min(a.nz, zm::KZ_MAX), S.sweep_chunk);
+  } else if (S.batched) {
     const long long chunks = std::max<long long>(1, std::min<long long>(resident / tiles, a.nz / 24));
     best_kz = std::min<long long>(zm::KZ_MAX, (a.nz + chunks - 1) / chunks);
   } else {
@@ -3030,6 +3033,7 @@ ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, con
   Level &L0 = h->lv[0];
   R.S = Solver{ctx, t, h, st, opts->nu1, opts->nu2, opts->omega, h->dncoarse};
   R.S.dfo = R.prec == 2;
+  R.S.sweep_chunk = opts->sweep_chunk;
   R.S.scal = scal;
   R.S.part = part;
   R.S.batched = batched;
@@ -3213,7 +3217,8 @@ unsigned long long run_key(const Run &R) {
                                        (unsigned long long)h->slotcap, (unsigned long long)(uintptr_t)R.S.scal,
                                        (unsigned long long)(uintptr_t)R.S.part,
                                        (unsigned long long)R.S.batched | ((unsigned long long)t->has_datum << 1) |
-                                           ((unsigned long long)(unsigned)R.ctx->sweep_first_wait << 8)};
+                                           ((unsigned long long)(unsigned)R.ctx->sweep_first_wait << 8) |
+                                           ((unsigned long long)(unsigned)o->sweep_chunk << 40)};
   for (unsigned long long v : ptrs) key = (key ^ v) * 0x100000001b3ULL;
   return key;
 }

@@ -117,6 +117,29 @@ def test_coarse_bf16_storage(ctx):
     assert all(rep["cycles"] <= 12 for _, rep in out.values()), out
 
 
+def test_sweep_chunk_gives_the_same_bits(ctx):
+    """The z extent of the fused sweep's tiles (sweep_chunk: the cost model's, 8, 13 planes;
+    13 leaves a ragged last chunk) changes which CTA computes which plane, not the arithmetic:
+    the solves' pressures are equal bit for bit, in both mixed modes, and solve the system."""
+    pkg, c = ctx
+    xf, yf, zf = synth.faces_tanh(150, 1.5), synth.faces_uniform(40), synth.faces_tanh(58, 2.0)
+    meshes = [synth.octa_sphere(4, (0.52, 0.48, 0.5), 0.2)]
+    T = pkg.Tables(c, xf, yf, zf, meshes)
+    rhs = torch.from_numpy(synth.rhs_divergence(xf, yf, zf, 17)).cuda()
+    for prec in (1, 2):
+        out = []
+        for chunk in (0, 8, 13):
+            p = torch.zeros_like(rhs)
+            rep = T.solve(rhs, p, TOL, pkg.SolveOpts(precision=prec, sweep_chunk=chunk))
+            assert rep["status"] == "IBM_OK" and rep["rel_resid"] <= TOL, (prec, chunk, rep)
+            out.append((p, rep["cycles"]))
+        assert all(torch.equal(out[0][0], q) and out[0][1] == k for q, k in out[1:]), prec
+    p = torch.zeros_like(rhs)
+    with pytest.raises(pkg.IbmError):
+        T.solve(rhs, p, TOL, pkg.SolveOpts(precision=1, sweep_chunk=300))
+    T.close()
+
+
 def test_no_body_ragged(ctx):
     _parity(ctx, synth.faces_uniform(33), synth.faces_tanh(24, 2.0), synth.faces_uniform(20), [], 3)
 

@@ -31,16 +31,17 @@ def test_tune_cache_round_trip(tmp_path):
     assert len(doc["entries"]) == 1
     e = doc["entries"][0]
     assert "precision=2" in e["key"] and "grid=24x24x24" in e["key"]
-    assert (e["omega"], e["nu1"], e["nu2"], e["inner_cycles"], e["krylov"]) == \
-        (o1.omega, o1.nu1, o1.nu2, o1.inner_cycles, o1.krylov)
+    assert (e["omega"], e["nu1"], e["nu2"], e["inner_cycles"], e["krylov"], e["sweep_chunk"]) == \
+        (o1.omega, o1.nu1, o1.nu2, o1.inner_cycles, o1.krylov, o1.sweep_chunk)
+    assert o1.sweep_chunk in (0, 128, 64, 32)
     # a new context on the same file: the entry comes back, no kernel is launched
     with pkg.Context(0, tune_cache=path) as c2:
         T = pkg.Tables(c2, xf, yf, zf, meshes)
         l0 = pkg.ibm_ctx_launch_count(c2.h)
         o2, ms2 = pkg.ibm_autotune(c2.h, T.h, 2, rhs, p, 1e-10)
         assert pkg.ibm_ctx_launch_count(c2.h) == l0
-        assert (o2.omega, o2.nu1, o2.nu2, o2.inner_cycles, o2.krylov, o2.precision) == \
-            (o1.omega, o1.nu1, o1.nu2, o1.inner_cycles, o1.krylov, 2)
+        assert (o2.omega, o2.nu1, o2.nu2, o2.inner_cycles, o2.krylov, o2.sweep_chunk, o2.precision) == \
+            (o1.omega, o1.nu1, o1.nu2, o1.inner_cycles, o1.krylov, o1.sweep_chunk, 2)
         assert abs(ms2 - ms1) <= 1e-5 * ms1
         # the cached schedule solves the problem
         rep = T.solve(rhs, p, 1e-10, o2)
