@@ -575,7 +575,7 @@ def run_ours(args):
     pr = synth.cfg4(args.n)
     b_host = pr.rhs()
     N = pr.ncells
-    ctx = pkg.Context(local)
+    ctx = pkg.Context(local, tune_cache=args.tune_cache)
     rhs = torch.from_numpy(b_host).to(dev)
     p = torch.zeros_like(rhs)
     torch.cuda.synchronize()
@@ -757,6 +757,8 @@ def main():
     ap.add_argument("--no-ad", action="store_true")
     ap.add_argument("--no-paper-shape", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON tune cache for ibm_autotune: a schedule found once is reused (no tuning launches)")
     ap.add_argument("--membrane-n", type=int, default=512)
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="solver mode of the step: 0 FP64, 1 FP32 MG + FP64 refinement, 2 FP32 MG + double-FP32")
