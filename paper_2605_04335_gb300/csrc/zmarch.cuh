@@ -511,29 +511,55 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
       for (int t = 0; t < NS; ++t) U[t] = lds4(Pp + ie0 + SR * t * BX);
       // red cells of strip t of plane q (ua: its colour's u, a compile-time constant):
       // x-edges from the adjacent lanes, or the ring at the edges
-      auto red_strip = [&](auto ua, const int t) {
+      // In FP32 a pass gathers both strips' inputs (x-edges, the rows above and below, rhs,
+      // mask) before relaxing either, so the shared-memory loads of the two strips overlap (the
+      // kernel's main stall is their latency); the FP64 form, bound by the FP64 pipe and short
+      // of registers, takes one strip at a time.
+      struct In {
+        T w, e;
+        vec4<T> N, So, Rr;
+        unsigned mm;
+      };
+      auto red_load = [&](const int t) {
         const int ie = ie0 + SR * t * BX;
+        In in;
         const T ep = ld1(P + ie + eoff);
         T w = __shfl_up_sync(0xffffffffu, C0[t].w, 1);
         T e = __shfl_down_sync(0xffffffffu, C0[t].x, 1);
-        w = lane == 0 ? ep : w;
-        e = lane == 31 ? ep : e;
-        const vec4<T> N = lds4(P + ie - BX), So = lds4(P + ie + BX);
-        const vec4<T> Rr = lds4(R + ir0 + SR * t * BX);
-        const unsigned mm = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM) | inval[t];
+        in.w = lane == 0 ? ep : w;
+        in.e = lane == 31 ? ep : e;
+        in.N = lds4(P + ie - BX);
+        in.So = lds4(P + ie + BX);
+        in.Rr = lds4(R + ir0 + SR * t * BX);
+        in.mm = *reinterpret_cast<const unsigned *>(M + im0 + SR * t * BXM) | inval[t];
+        return in;
+      };
+      auto red_do = [&](auto ua, const int t, const In &in) {
+        const int ie = ie0 + SR * t * BX;
         const long long gid = (long long)(q + 1) * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
-        relax_strip<decltype(ua)::value, COARSE>(C0[t], w, e, N, So, Cm1[t], U[t], Rr, mm, X, cym[t], cyp[t],
-                                                 sy[t] + szr, zmr, zpr, sh, om, a, gid);
+        relax_strip<decltype(ua)::value, COARSE>(C0[t], in.w, in.e, in.N, in.So, Cm1[t], U[t], in.Rr, in.mm, X, cym[t],
+                                                 cyp[t], sy[t] + szr, zmr, zpr, sh, om, a, gid);
         C0[t] = stored4<S>(C0[t]);   // the registers hold what every reader of the buffer sees
         sts4(P + ie, C0[t]);
       };
       if (!ring && red) {
-        if (parq) {
-          red_strip(U0{}, 0);
-          red_strip(U1{}, 1);
+        if constexpr (sizeof(T) == 4) {
+          const In i0 = red_load(0), i1 = red_load(1);
+          if (parq) {
+            red_do(U0{}, 0, i0);
+            red_do(U1{}, 1, i1);
+          } else {
+            red_do(U1{}, 0, i0);
+            red_do(U0{}, 1, i1);
+          }
         } else {
-          red_strip(U1{}, 0);
-          red_strip(U0{}, 1);
+          if (parq) {
+            red_do(U0{}, 0, red_load(0));
+            red_do(U1{}, 1, red_load(1));
+          } else {
+            red_do(U1{}, 0, red_load(0));
+            red_do(U0{}, 1, red_load(1));
+          }
         }
       }
       if (ring && red) {
@@ -589,19 +615,24 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
       // shared memory, the z-neighbours in Cm2 and C0); store the strips from registers
       const int kb = q - 1;
       // black cells of strip t of plane q-1 (they sit at the same u as the red cells of plane q)
-      auto black_strip = [&](auto ua, const int t, S *const dk) {
+      auto black_load = [&](const int t) {
         const int ie = ie0 + SR * t * BX;
+        In in;
         const T ep = ld1(Pm + ie + eoff);
         T w = __shfl_up_sync(0xffffffffu, Cm1[t].w, 1);
         T e = __shfl_down_sync(0xffffffffu, Cm1[t].x, 1);
-        w = lane == 0 ? ep : w;
-        e = lane == 31 ? ep : e;
-        const vec4<T> N = lds4(Pm + ie - BX), So = lds4(Pm + ie + BX);
-        const vec4<T> Rr = lds4(Rm + ir0 + SR * t * BX);
-        const unsigned mm = *reinterpret_cast<const unsigned *>(Mm + im0 + SR * t * BXM) | inval[t];
+        in.w = lane == 0 ? ep : w;
+        in.e = lane == 31 ? ep : e;
+        in.N = lds4(Pm + ie - BX);
+        in.So = lds4(Pm + ie + BX);
+        in.Rr = lds4(Rm + ir0 + SR * t * BX);
+        in.mm = *reinterpret_cast<const unsigned *>(Mm + im0 + SR * t * BXM) | inval[t];
+        return in;
+      };
+      auto black_do = [&](auto ua, const int t, const In &in, S *const dk) {
         const long long gid = (long long)q * a.sz + (long long)(y0 + ys + SR * t + 1) * a.sy + (x0 + xs + 4);
-        relax_strip<decltype(ua)::value, COARSE>(Cm1[t], w, e, N, So, Cm2[t], C0[t], Rr, mm, X, cym[t], cyp[t],
-                                                 sy[t] + szb, zmb, zpb, sh, om, a, gid);
+        relax_strip<decltype(ua)::value, COARSE>(Cm1[t], in.w, in.e, in.N, in.So, Cm2[t], C0[t], in.Rr, in.mm, X,
+                                                 cym[t], cyp[t], sy[t] + szb, zmb, zpb, sh, om, a, gid);
         if ((inval[t] & 0xffu) == 0u) {   // the strip's row is in the grid
           S *dst = dk + (long long)(SR * t) * a.px;
           if (inval[t] == 0u) {
@@ -616,12 +647,23 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
       };
       if (!ring && kb >= k0 && kb < k1) {
         S *const dk = dst0 + (long long)(kb + 1) * a.sz;
-        if (parq) {
-          black_strip(U0{}, 0, dk);
-          black_strip(U1{}, 1, dk);
+        if constexpr (sizeof(T) == 4) {
+          const In i0 = black_load(0), i1 = black_load(1);
+          if (parq) {
+            black_do(U0{}, 0, i0, dk);
+            black_do(U1{}, 1, i1, dk);
+          } else {
+            black_do(U1{}, 0, i0, dk);
+            black_do(U0{}, 1, i1, dk);
+          }
         } else {
-          black_strip(U1{}, 0, dk);
-          black_strip(U0{}, 1, dk);
+          if (parq) {
+            black_do(U0{}, 0, black_load(0), dk);
+            black_do(U1{}, 1, black_load(1), dk);
+          } else {
+            black_do(U1{}, 0, black_load(0), dk);
+            black_do(U0{}, 1, black_load(1), dk);
+          }
         }
       }
 #pragma unroll
