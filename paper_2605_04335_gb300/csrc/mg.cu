@@ -3051,7 +3051,10 @@ ibm_status run_start(Run &R, ibm_ctx *ctx, ibm_tables *t, const double *rhs, con
     k_pack<<<R.ctx->wave, 256, 0, st>>>(p_user, L0.g, h->p64, L0.mask, reinterpret_cast<unsigned *>(scal + S_PNZ));
   }
   ctx->launches += 2;
-  outer_residual(R.S, false, nullptr, false);
+  // the residual of p = 0 (its norm is ||S P b||); in mode 1 on closed bodies it also writes the
+  // FP32 right-hand side b - lambda, which is the initial residual when the guess is zero
+  R.r32 = R.prec != 0 ? (float *)L0.r : nullptr;
+  outer_residual(R.S, false, R.prec == 1 && !t->membrane ? R.r32 : nullptr, false);
   IBM_TRY(cudaGetLastError());
   return IBM_OK;
 }
@@ -3096,15 +3099,25 @@ ibm_status run_begin(Run &R, cudaStream_t st) {
                          sizeof(double) * (REDUCE_BLOCKS + CUT_BLOCKS + GCR_NV * (REDUCE_BLOCKS + GCR_GBLOCKS))));
     IBM_TRY(cudaMemsetAsync(h->gcr_state, 0, sizeof(GcrState), st));
   }
-  R.r32 = R.prec != 0 ? (float *)L0.r : nullptr;
   R.r64 = R.prec == 0 && R.gcr_m > 0 ? (double *)L0.r : nullptr;
   // the V-cycle on p itself (precision 0 without GCR) updates ghost rows with their datum;
   // correction forms carry it in the residual
   R.S.gd = R.prec == 0 && R.gcr_m == 0 && t->has_datum ? t->gd : nullptr;
   // a zero initial guess (as packed) gives A p = 0 unless ghost rows carry a datum
   const unsigned *pnz = t->has_datum ? nullptr : reinterpret_cast<const unsigned *>(R.S.scal + S_PNZ);
-  if (R.r64) fine_residual<double>(R.S, h->p64, R.r64, true, pnz);
-  else outer_residual(R.S, true, R.r32, true, pnz);
+  uint64_t pnz_bits = 0;
+  std::memcpy(&pnz_bits, &R.hs[S_PNZ], sizeof pnz_bits);
+  if (R.prec == 1 && !t->membrane && !t->has_datum && pnz_bits == 0) {
+    // mode 1, zero guess: the residual of p = 0 already computed its partial sums and wrote
+    // r = b - lambda (lambda still 0), and its ghost rows are zero; finalising those sums with
+    // the lambda update gives the initial residual's scalars bit for bit
+    k_finalize_resid<<<1, 256, 0, st>>>(R.S.part, REDUCE_BLOCKS, nullptr, 0, R.S.scal, 1, nullptr, 0);
+    ctx->launches += 1;
+  } else if (R.r64) {
+    fine_residual<double>(R.S, h->p64, R.r64, true, pnz);
+  } else {
+    outer_residual(R.S, true, R.r32, true, pnz);
+  }
   IBM_TRY(cudaGetLastError());
   return IBM_OK;
 }
