@@ -145,6 +145,7 @@ struct Hierarchy {
   int zm_per_sm = 1;                        // resident CTAs per SM of the fused sweep
   int zmc_per_sm = 1;                       // the same for its coarse-level form
   bool coarse_bf16 = false;                 // z-march coarse levels store e and r in BF16
+  int *zcount = nullptr;                    // per level: the coarse sweep's item counter
   CUtensorMap tm_e[2], tm_r, tm_m;
   void *tm_base[2] = {nullptr, nullptr};    // which buffer each tm_e describes
   const void *tm_rbase = nullptr;           // the right-hand side tm_r describes

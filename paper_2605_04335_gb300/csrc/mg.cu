@@ -2102,6 +2102,7 @@ void free_hierarchy(Hierarchy *h) {
     ps.insert(ps.end(), q, q + sizeof(q) / sizeof(q[0]));
   }
   void *q[] = {h->p64, h->b64, h->minv, h->gj, h->cidx, h->dncoarse, h->c64, h->cdf, h->gsrc, h->gdst, h->gw64,
+               h->zcount,
                h->gw32, h->gtmp, h->e_alt, h->tm_base[0], h->tm_base[1], h->d_fvol, h->d_ng,
                h->cut_id, h->cut_nb, h->cut_ijk, h->par_id, h->d_cnt, h->par_flag, h->scan_buf, h->gcr_buf,
                h->gcr_state, h->gcr_part, h->bicg_buf, h->helm_buf};
@@ -2166,6 +2167,7 @@ static void setup_zmarch(Hierarchy *h, void *e0, void *r0) {
 // FP32 hierarchies whose finest level uses it.  Tensor maps over the level's e (both buffers),
 // r and z-march mask.
 constexpr long long ZM_COARSE_CELLS = 1LL << 18;
+constexpr int ZM_COARSE_KZ = 64;   // planes per chunk of a coarse level's dynamic schedule at most
 
 // With BF16 coarse storage those levels' e and r maps are BF16 (the kernel's BF16 form); a
 // BF16 level must be swept by it (no other coarse kernel reads BF16): false if it cannot be.
@@ -2318,6 +2320,7 @@ static ibm_status build_grid_t(ibm_tables *t, cudaStream_t st, Hierarchy **out, 
     HTRY(cudaGetLastError());
   }
   h->nslot = h->lv[0].g.ntot + slotcap;
+  HTRY(alloc_zero<int>((void **)&h->zcount, nl, st));
   // coarse levels for the fused sweep: z-march mask, second e buffer, separable diagonals
   if (sizeof(T) == 4)
     for (int l = 1; l < nl; ++l) {
@@ -2622,6 +2625,10 @@ void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
   // item gets its own CTA and chunks keep at least 24 planes, so that several problems'
   // sweeps share the GPU without the extra planes of short chunks.
   int best_kz = std::min(a.nz, zm::KZ_MAX);
+  // Coarse levels take their items from a counter (dynamic schedule): tiles crossing a body
+  // cost more (their irregular cells wait on face-fraction loads), and chunks of at most
+  // ZM_COARSE_KZ planes spread them over the CTAs.
+  const bool dynamic = coarse && !S.batched;
   if (!coarse && S.sweep_chunk > 0) {
     best_kz = std::min(std::min(a.nz, zm::KZ_MAX), S.sweep_chunk);
   } else if (S.batched) {
@@ -2634,6 +2641,7 @@ void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
       const long long cost = ((tiles * chunks + resident - 1) / resident) * (kz + 6);
       if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_kz = kz; }
     }
+    if (dynamic) best_kz = std::min(best_kz, ZM_COARSE_KZ);
   }
   a.kz = best_kz;
   const long long chunks = (a.nz + a.kz - 1) / a.kz;
@@ -2641,6 +2649,11 @@ void sweep_zmarch(Solver &S, int l, T *&e, const double *shift) {
   a.tiles_y = gy;
   a.items = (int)(tiles * chunks);
   a.first_wait = S.ctx->sweep_first_wait >= 0 ? S.ctx->sweep_first_wait : zm::WAIT_LIMIT;
+  a.counter = nullptr;
+  if (dynamic) {
+    a.counter = h->zcount + l;
+    cudaMemsetAsync(a.counter, 0, sizeof(int), S.st);
+  }
   const int grid = (int)(S.batched ? a.items : std::min<long long>(a.items, resident));
   if constexpr (sizeof(T) == 4) {   // coarse levels: FP32 hierarchies only
     if (coarse && L0.bf16)

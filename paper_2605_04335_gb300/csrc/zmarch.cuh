@@ -110,6 +110,7 @@ struct Smem {
   alignas(16) unsigned ccu[32][4];    // ... their invalid-cell bytes and row flags
   alignas(8) uint64_t bar_e[NE];
   alignas(8) uint64_t bar_r[NR];
+  int next;                           // the CTA's next item (dynamic schedule)
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -157,6 +158,8 @@ struct Args {
   int kz;                 // planes per item
   int tiles_x, tiles_y;   // item i: tile (i mod tiles_x, (i / tiles_x) mod tiles_y), chunk i / tiles
   int items;
+  int *counter;           // dynamic schedule: items after the first gridDim.x are taken from this
+                          // counter (zeroed before the launch); null: item i + k gridDim.x
   int first_wait;         // tries of each item's first wait (WAIT_LIMIT; less only to test the
                           // error path)
   const T *cxm, *cxp, *cym, *cyp, *czm, *czp, *sdx, *sdy, *sdz;
@@ -370,11 +373,19 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
   const int first_wait = a.first_wait;
   const int tiles = a.tiles_x * a.tiles_y;
 
-  for (int item = blockIdx.x; item < a.items; item += gridDim.x) {
+  for (int item = blockIdx.x; item < a.items;) {
+    // the next item: fetched by one thread now, read by all after this item's barriers
+    if (a.counter && tid == 0) s.next = (int)gridDim.x + atomicAdd(a.counter, 1);
     const int bx = item % a.tiles_x, by = (item / a.tiles_x) % a.tiles_y, bz = item / tiles;
     const int x0 = bx * TX, y0 = by * TY;
     const int k0 = bz * a.kz, k1 = min(a.nz, k0 + a.kz);
-    if (k0 >= k1) continue;
+    if (k0 >= k1) {   // an empty chunk (not produced by the host's chunking)
+      __syncthreads();
+      const int nxt = a.counter ? s.next : item + (int)gridDim.x;
+      __syncthreads();
+      item = nxt;
+      continue;
+    }
     // coefficients of this thread's strips (registers for the item's whole march)
     const XCoef<T> X = load_x(a, x0 + xs);
     T cym[NS], cyp[NS], sy[NS];
@@ -687,7 +698,9 @@ __global__ void __launch_bounds__(THREADS, min_ctas<T>()) k_sweep_zmarch(const _
       __syncthreads();
       return;
     }
+    const int nxt = a.counter ? s.next : item + (int)gridDim.x;
     __syncthreads();   // the next item's prologue refills buffers this item's last step read
+    item = nxt;
   }
 }
 
