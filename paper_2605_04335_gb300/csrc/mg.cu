@@ -942,14 +942,15 @@ __device__ __forceinline__ void block_partials3(double A0, double A1, double A2,
 // FP64 bits on the integer pipe (truncation, within one FP32 ulp); the volume weights (wf:
 // float widths dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64
 // every 8 rows.
-template <typename R>
+// WP = false: the residual of p = 0 (no stencil; fewer registers, a fuller machine).
+template <typename R, bool WP = true>
 __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
                                                               const double *lambda, const float *wf, R *r32,
                                                               double *partials, const unsigned *p_nonzero) {
   const double lam = *lambda;
   // p_nonzero (optional): zero when every packed value of p is zero, so A p = 0 exactly and
   // the FP64 stencil is skipped (a cold start); one test for the whole launch
-  const bool use_p = p != nullptr && (p_nonzero == nullptr || *p_nonzero != 0u);
+  const bool use_p = WP && p != nullptr && (p_nonzero == nullptr || *p_nonzero != 0u);
   const int nx = v.nx, ny = v.ny;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   double A0 = 0.0, A1 = 0.0, A2 = 0.0;
@@ -2885,8 +2886,12 @@ void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda, const
   LV<double> v = fine_view64(S.h);
   double *part = S.part;
   const int n = v.nx + v.ny + v.nz;
-  k_residual64<R><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.scal + S_LAMBDA, S.h->cdf + 3 * n,
-                                                          r32, part, p_nonzero);
+  if (p)
+    k_residual64<R, true><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.scal + S_LAMBDA,
+                                                                    S.h->cdf + 3 * n, r32, part, p_nonzero);
+  else
+    k_residual64<R, false><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.scal + S_LAMBDA,
+                                                                     S.h->cdf + 3 * n, r32, part, nullptr);
   const long long ng = S.t->nghost;
   const int ngb = 152;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
