@@ -18,6 +18,9 @@ constexpr int OX = 4;
 // Fixed reduction width: block partials are summed in a fixed order, so every reduction (and
 // with it every result) is the same on any device, whatever its SM count.
 constexpr int REDUCE_BLOCKS = 608;
+// a second fixed width (grid-stride kernels over ghost rows, fluid statistics, cut-cell flags):
+// the same partial-sum layout, hence the same bits, on any number of SMs
+constexpr int FIXED_BLOCKS = 152;
 constexpr int REDUCE_THREADS = 256;
 constexpr int NSCAL = 32;            // device scalars per context
 

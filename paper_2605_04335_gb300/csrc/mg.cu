@@ -1774,7 +1774,7 @@ __global__ void __launch_bounds__(256) k_cut_restrict(const long long *par_id, c
 // Q_i of nslot elements of T each (Z at zb + i nslot, Q at qb + i nslot).
 constexpr int GCR_MAX = 8;
 constexpr int GCR_BLOCKS = 608;
-constexpr int GCR_GBLOCKS = 152;
+constexpr int GCR_GBLOCKS = FIXED_BLOCKS;
 constexpr int GCR_NV = 2 * GCR_MAX + 3;   // partial sums per block: <q,Q_i>, <r,Q_i>, <q,q>, <r,q>, sum V q
 
 struct GcrState {           // device memory
@@ -2429,20 +2429,23 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
   IBM_TRY(cudaGetLastError());
   // fluid volume and count per level (one read-back for all levels)
   {
-    double *part = t->ctx->partials;   // 2 x 152 doubles per level fit in the context's scratch
-    static_assert(2 * 152 * 16 <= REDUCE_BLOCKS * 8, "fluid statistics scratch");
+    double *part = t->ctx->partials;   // 2 x FIXED_BLOCKS doubles per level fit in the scratch
+    static_assert(2 * FIXED_BLOCKS * 16 <= REDUCE_BLOCKS * 8, "fluid statistics scratch");
     if (nl > 16) return IBM_ERR_CAPACITY;
     for (int l = 0; l < nl; ++l) {
       Level &L = h->lv[l];
-      k_fluid_stats<<<152, STATS_THREADS, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx, L.w1d + L.g.nx + L.g.ny,
-                                                   part + 2 * 152 * l);
+      k_fluid_stats<<<FIXED_BLOCKS, STATS_THREADS, 0, st>>>(L.mask, L.g, L.w1d, L.w1d + L.g.nx,
+                                                            L.w1d + L.g.nx + L.g.ny, part + 2 * FIXED_BLOCKS * l);
     }
-    std::vector<double> hv(2 * 152 * nl), fv(nl);
+    std::vector<double> hv(2 * FIXED_BLOCKS * nl), fv(nl);
     IBM_TRY(cudaMemcpyAsync(hv.data(), part, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
     IBM_TRY(cudaStreamSynchronize(st));
     for (int l = 0; l < nl; ++l) {
       double v = 0.0, c = 0.0;
-      for (int b = 0; b < 152; ++b) { v += hv[2 * 152 * l + 2 * b]; c += hv[2 * 152 * l + 2 * b + 1]; }
+      for (int b = 0; b < FIXED_BLOCKS; ++b) {
+        v += hv[2 * FIXED_BLOCKS * l + 2 * b];
+        c += hv[2 * FIXED_BLOCKS * l + 2 * b + 1];
+      }
       h->lv[l].fluid_vol = v;
       h->lv[l].nfluid = (long long)c;
       fv[l] = v;
@@ -2524,7 +2527,7 @@ static ibm_status refresh_geometry_t(ibm_tables *t, Hierarchy *h, cudaStream_t s
     h->hcnt[1] = ncut;
     IBM_TRY(cudaMemcpyAsync(h->d_cnt, h->hcnt, sizeof(long long) * 2, cudaMemcpyHostToDevice, st));
     if (!h->par_flag) IBM_TRY(alloc_zero<uint8_t>((void **)&h->par_flag, L1.g.ntot, st));
-    k_par_flag<<<152, 256, 0, st>>>(h->cut_id, h->cut_ijk, h->d_cnt, L1.g, h->par_flag);
+    k_par_flag<<<FIXED_BLOCKS, 256, 0, st>>>(h->cut_id, h->cut_ijk, h->d_cnt, L1.g, h->par_flag);
     k_par_count<<<nbp, CUT_THREADS, 0, st>>>(h->par_flag, L1.g.ntot, bc);
     k_scan1<<<1, 1024, 0, st>>>(bc, bo[0], (int)nbp);
     long long npar = 0;
@@ -2793,7 +2796,8 @@ void vcycle(Solver &S, int l, T *&e, const T *r, const double *shift, const T *g
   // coarse columns (x: 128 per block, y: one per block) and chunks of kc planes: up to
   // PROLONG_KC, shorter on small levels so that a launch still has about two waves of blocks
   const long long pcols = nblk(C.g.nx, 128) * (long long)C.g.ny;
-  const int kc = (int)std::max(1LL, std::min<long long>(PROLONG_KC, pcols * C.g.nz / (16LL * (S.ctx->sm_count > 0 ? S.ctx->sm_count : 152))));
+  const long long sms = S.ctx->sm_count > 0 ? S.ctx->sm_count : 152;
+  const int kc = (int)std::max(1LL, std::min<long long>(PROLONG_KC, pcols * C.g.nz / (16LL * sms)));
   dim3 gp((unsigned)nblk(C.g.nx, 128), (unsigned)C.g.ny, (unsigned)((C.g.nz + kc - 1) / kc));
   const int nxf = F.g.nx, nyf = F.g.ny;
   auto prolong_from = [&](auto sc, auto sf) {
@@ -2863,7 +2867,7 @@ void outer_residual(Solver &S, bool with_p, float *r32, bool update_lambda, cons
   k_residual_df<<<rdf_blocks, REDUCE_THREADS, 0, S.st>>>(fine_view_df(h), ph, pl, hi_of(h->b64),
                                                          lo_of(h->b64, ntot), S.scal + S_LAMBDA, r32, part);
   const long long ng = S.t->nghost;
-  const int ngb = 152;
+  const int ngb = FIXED_BLOCKS;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
   const bool cuts = h->hcnt[1] > 0;
   if (cuts) {
@@ -2893,7 +2897,7 @@ void fine_residual(Solver &S, const double *p, R *r32, bool update_lambda, const
     k_residual64<R, false><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, S.st>>>(v, p, S.h->b64, S.scal + S_LAMBDA,
                                                                      S.h->cdf + 3 * n, r32, part, nullptr);
   const long long ng = S.t->nghost;
-  const int ngb = 152;
+  const int ngb = FIXED_BLOCKS;
   double *gpart = part + 3 * REDUCE_BLOCKS, *cpart = gpart + ngb;
   const bool cuts = S.h->hcnt[1] > 0;
   if (cuts) {
