@@ -206,13 +206,12 @@ def _schedule(o) -> str:
             % (o.nu1, o.nu2, o.omega, o.inner_cycles, o.krylov, o.sweep_chunk or "by the cost model"))
 
 
-def _config(args, schedule: str | None = None):
+def _config(args):
     return {"workload": "pressure Poisson solve from p = 0 to 1e-10 relative projected residual: %d^3 uniform grid "
                         "(%.3g cells) around 12 random non-overlapping spheres (r in [0.03, 0.08], 2048 triangles "
                         "each), seeded N(0,1) divergence right-hand side" % (args.n, float(args.n) ** 3),
             "grid": [args.n] * 3, "tol": TOL, "precision": PRECISIONS[args.precision],
-            "l2": "working set > L2 (no flush)", "parallelism": "replicas" if args.gpus > 1 else "single GPU",
-            "schedule": schedule or "library defaults (nu1 = nu2 = 2, omega 1.3, 2 FP32 V-cycles per refinement step)"}
+            "l2": "working set > L2 (no flush)", "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
 def _timed(torch, st, fn, reps):
@@ -657,7 +656,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": _config(args, schedule),
+            "config": _config(args),
+            "schedule": schedule or "library defaults (nu1 = nu2 = 2, omega 1.3, 2 FP32 V-cycles per refinement step)",
             "time_to_tol_ms": t_ms, "cycles": final["cycles"], "final_rel_resid": final["rel_resid"],
             "classify_ms": classify_ms, "ghosts": T.nghost,
             "device_gb": {"tables": (free0 - free_t) / 1e9,
