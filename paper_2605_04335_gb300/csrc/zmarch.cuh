@@ -1,7 +1,9 @@
-// Fused two-colour red-black Gauss-Seidel sweep on the finest level: z-march with
+// Fused two-colour red-black Gauss-Seidel sweep of one multigrid level: z-march with
 // TMA-staged planes in shared memory, persistent CTAs over (x-y tile, z-chunk) items.  FP32
 // (the mixed solves' multigrid, two CTAs per SM) and FP64 (the FP64 solve's smoother on p,
-// one CTA per SM: its buffers take 190 KB of shared memory) share the code.
+// one CTA per SM: its buffers take 190 KB of shared memory) share the code, for the finest
+// level and (FP32) the coarse levels of at least 2^18 cells; a coarse level may store its e
+// and r in BF16 (S = bf16: staged as BF16, widened exactly on load, rounded on store).
 //
 // One item is an x-y tile (TX x TY) and a z-range [k0, k1).  Step q of its march
 //   1. updates the red cells of plane q on the tile, and the one-cell ring that the tile's
@@ -32,7 +34,8 @@
 // (every face with a coefficient fully open, so the rediscretised coefficients and the
 // separable diagonal apply), 8 for an irregular fluid cell (near a body; its update reads the
 // six fractions from global memory and forms the diagonal as their weighted sum), anything
-// else for a cell that is not updated.
+// else for a cell that is not updated.  Tiles crossing a body therefore cost more, and coarse
+// launches hand their items out from a counter (dynamic schedule) rather than in a fixed order.
 //
 // Planes of e (halo 2 in x and y), the right-hand side and the mask (halo 1) arrive by
 // cp.async.bulk.tensor into rings of shared-memory buffers DP steps ahead of their use,
