@@ -367,8 +367,8 @@ def bench_moving_ellipsoid(pkg, ctx, torch, st, n: int = 256, steps: int = 20, a
 
 def bench_batched(pkg, ctx, torch, st, reps: int = 2):
     """48 independent uneven problems (edges U{64..192}, sphere or ellipsoid each): batched
-    solves in each precision mode and 48 sequential solves in the mixed modes, to 1e-10
-    (ms, median)."""
+    solves in each precision mode (the mixed modes in lockstep and, for comparison, on the
+    stream pool) and 48 sequential solves in the mixed modes, to 1e-10 (ms, median)."""
     import synth
     probs = synth.cfg5(48)
     tabs = [pkg.Tables(ctx, pr.xf, pr.yf, pr.zf, pr.meshes, stream=st) for pr in probs]
@@ -390,16 +390,22 @@ def bench_batched(pkg, ctx, torch, st, reps: int = 2):
             ts.append(a.elapsed_time(c))
         return statistics.median(ts[1:])
 
-    out = {"problems": len(probs), "cells": cells}
+    out = {"problems": len(probs), "cells": cells,
+           "schedule": "mixed modes: lockstep (one launch per V-cycle stage over every problem); "
+                       "FP64: per-problem step graphs on the stream pool"}
     for name, prec in (("mixed", 1), ("mixed_df", 2), ("fp64", 0)):
         out["batched_%s_ms" % name] = timed(lambda: pkg.poisson_solve_batched(
             ctx.h, [t.h for t in tabs], rhs, TOL, ps, pkg.SolveOpts(precision=prec), stream=st))
     for name, prec in (("mixed", 1), ("mixed_df", 2)):
+        out["stream_pool_%s_ms" % name] = timed(lambda: pkg.poisson_solve_batched(
+            ctx.h, [t.h for t in tabs], rhs, TOL, ps, pkg.SolveOpts(precision=prec, batch_schedule=1), stream=st))
         out["sequential_%s_ms" % name] = timed(lambda: [t.solve(r, x, TOL, pkg.SolveOpts(precision=prec), stream=st)
                                                        for t, r, x in zip(tabs, rhs, ps)])
     out["batched_mixed_gcells_per_s"] = cells / (out["batched_mixed_ms"] * 1e-3) / 1e9
     out["batched_speedup_vs_sequential"] = {k: out["sequential_%s_ms" % k] / out["batched_%s_ms" % k]
                                             for k in ("mixed", "mixed_df")}
+    out["lockstep_speedup_vs_stream_pool"] = {k: out["stream_pool_%s_ms" % k] / out["batched_%s_ms" % k]
+                                              for k in ("mixed", "mixed_df")}
     for t in tabs:
         t.close()
     return out

@@ -111,6 +111,14 @@ typedef struct {
                            sweep's cost model (the fewest plane steps for one wave of resident
                            blocks), else 1..256 (IBM_ERR_INVALID_ARG outside).  Searched by
                            ibm_autotune.                                                  [0] */
+  int32_t batch_schedule; /* poisson_solve_batched only: 0 = lockstep when every problem allows
+                           it (precision 1 or 2, closed bodies, krylov 0 or automatic, FP32
+                           coarse storage): each V-cycle stage is one launch over all problems
+                           still iterating, else the stream pool; 1 = the stream pool: each
+                           problem's step as its own CUDA graph, the problems' graphs running
+                           concurrently on the context's streams.  Both give every problem the
+                           result of its own poisson_solve.  IBM_ERR_INVALID_ARG outside 0..1.
+                                                                                           [0] */
 } ibm_solve_opts;
 
 /* Solve report.  resid_history (host, optional) receives the relative residual after

@@ -204,6 +204,8 @@ ibm_status ibm_ctx_destroy(ibm_ctx *c) {
   if (c->bscal) cudaFree(c->bscal);
   if (c->bhscal) cudaFreeHost(c->bhscal);
   if (c->bpart) cudaFree(c->bpart);
+  if (c->lk_count) cudaFree(c->lk_count);
+  if (c->lk_tail) cudaFree(c->lk_tail);
   delete c;
   return IBM_OK;
 }
@@ -368,6 +370,7 @@ void ibm_solve_opts_default(ibm_solve_opts *o) {
   o->srj_steps = 8;
   o->coarse_bf16 = 0;
   o->sweep_chunk = 0;
+  o->batch_schedule = 0;
 }
 
 ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_dev, double tol, double *p_dev,
@@ -380,7 +383,7 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
       o.inner_cycles < 1 || !(o.omega > 0.0 && o.omega < 2.0) || o.krylov < -1 || o.krylov > 8 || o.method < 0 ||
       o.method > 1 || o.srj_steps < 1 || o.srj_steps > 64 || (o.method == 1 && o.precision != 0) ||
       o.coarse_bf16 < 0 || o.coarse_bf16 > 1 || (o.coarse_bf16 && (o.precision == 0 || t->membrane)) ||
-      o.sweep_chunk < 0 || o.sweep_chunk > 256)
+      o.sweep_chunk < 0 || o.sweep_chunk > 256 || o.batch_schedule < 0 || o.batch_schedule > 1)
     return IBM_ERR_INVALID_ARG;
   if (info && info->history_cap > 0 && !info->resid_history) return IBM_ERR_INVALID_ARG;
   IBM_TRY(cudaSetDevice(ctx->device));
@@ -425,7 +428,7 @@ static bool valid_opts(const ibm_solve_opts &o) {
          o.max_cycles >= 0 && o.inner_cycles >= 1 && o.omega > 0.0 && o.omega < 2.0 && o.krylov >= -1 &&
          o.krylov <= 8 && o.method == 0 &&   // batched: the multigrid solver
          (o.coarse_bf16 == 0 || (o.coarse_bf16 == 1 && o.precision != 0)) && o.sweep_chunk >= 0 &&
-         o.sweep_chunk <= 256;
+         o.sweep_chunk <= 256 && o.batch_schedule >= 0 && o.batch_schedule <= 1;
 }
 
 ibm_status poisson_solve_batched(ibm_ctx *ctx, int32_t n, const ibm_tables *const *tables,

@@ -177,6 +177,11 @@ struct ibm_ctx {
   cudaEvent_t bevent[NBSTREAM + 1] = {};
   double *bscal = nullptr, *bhscal = nullptr, *bpart = nullptr;
   int bcap = 0;                        // problems the batch buffers hold
+  // lockstep batches: dynamic-schedule counters of one step's batched sweeps, and the
+  // problems' coarse-tail arguments (device copies)
+  int *lk_count = nullptr;
+  void *lk_tail = nullptr;
+  int lk_tail_cap = 0;
 };
 
 struct ibm_tables {

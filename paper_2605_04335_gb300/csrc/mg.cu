@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -69,6 +70,18 @@ LV<T> view(const Level &L) {
   return v;
 }
 
+// Arithmetic shared by several kernels leaves the compiler one way to contract it: no addition
+// has two unrounded products as operands (one of them is rounded on its own by mul_rn, never
+// fused).  Left open, which product of such a sum gets fused into a multiply-add may differ
+// between two kernels that inline the same body, so the single-problem kernels and the
+// batched launches would round differently.
+template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ long long vidx(const LV<T> &v, int i, int j, int k) {
   return ((long long)(k + 1) * (v.ny + 2) + (j + 1)) * v.px + (i + OX);
@@ -79,15 +92,17 @@ template <typename T>
 __device__ __forceinline__ void coefs(const LV<T> &v, int i, int j, int k, long long id, T c[6]) {
   c[0] = v.cxm[i]; c[1] = v.cxp[i]; c[2] = v.cym[j]; c[3] = v.cyp[j]; c[4] = v.czm[k]; c[5] = v.czp[k];
   if (v.fx) {
-    c[0] *= v.fx[id - 1]; c[1] *= v.fx[id];
-    c[2] *= v.fy[id - v.sy]; c[3] *= v.fy[id];
-    c[4] *= v.fz[id - v.sz]; c[5] *= v.fz[id];
+    c[0] = mul_rn(c[0], v.fx[id - 1]); c[1] = mul_rn(c[1], v.fx[id]);
+    c[2] = mul_rn(c[2], v.fy[id - v.sy]); c[3] = mul_rn(c[3], v.fy[id]);
+    c[4] = mul_rn(c[4], v.fz[id - v.sz]); c[5] = mul_rn(c[5], v.fz[id]);
   }
 }
 
+// sum_d c_d e_d over the six neighbours, in this order; the first product rounded on its own,
+// so each later addition has one product, fused into it
 template <typename T>
 __device__ __forceinline__ T stencil_sum(const LV<T> &v, const T *e, long long id, const T c[6]) {
-  return c[0] * e[id - 1] + c[1] * e[id + 1] + c[2] * e[id - v.sy] + c[3] * e[id + v.sy] +
+  return mul_rn(c[0], e[id - 1]) + c[1] * e[id + 1] + c[2] * e[id - v.sy] + c[3] * e[id + v.sy] +
          c[4] * e[id - v.sz] + c[5] * e[id + v.sz];
 }
 
@@ -350,10 +365,30 @@ __global__ void __launch_bounds__(STATS_THREADS) k_fluid_stats(const uint8_t *ma
 // ------------------------------------------------------------------ solve kernels
 
 // one colour of red-black Gauss-Seidel on fluid rows: e_i += omega (sum - D e_i - rhs) / D
-template <typename T>
-__global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colour, T omega) {
-  int ti = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y, k = blockIdx.z;
+// Kernel bodies take their block coordinates from a grid policy: HwGrid (the launch's own
+// blockIdx and gridDim, read where they are used) for the single-problem kernels, VGrid (the
+// block's coordinates within its problem's grid) for batched launches over several problems.
+struct HwGrid {
+  __device__ __forceinline__ int bx() const { return (int)blockIdx.x; }
+  __device__ __forceinline__ int by() const { return (int)blockIdx.y; }
+  __device__ __forceinline__ int bz() const { return (int)blockIdx.z; }
+  __device__ __forceinline__ int gx() const { return (int)gridDim.x; }
+  __device__ __forceinline__ int gy() const { return (int)gridDim.y; }
+};
+struct VGrid {
+  int x, y, z, nx, ny;
+  __device__ __forceinline__ int bx() const { return x; }
+  __device__ __forceinline__ int by() const { return y; }
+  __device__ __forceinline__ int bz() const { return z; }
+  __device__ __forceinline__ int gx() const { return nx; }
+  __device__ __forceinline__ int gy() const { return ny; }
+};
+
+template <typename T, class G>
+__device__ __forceinline__ void rbgs_body(const LV<T> &v, T *e, const T *r, const double *shift, int colour, T omega,
+                                          const G &gr) {
+  int ti = gr.bx() * blockDim.x + threadIdx.x;
+  int j = gr.by(), k = gr.bz();
   int i = 2 * ti + ((j + k + colour) & 1);
   if (i >= v.nx) return;
   long long id = vidx(v, i, j, k);
@@ -368,11 +403,17 @@ __global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colou
   e[id] += (T)__fdividef((float)omega * (float)res, (float)D);
 }
 
+template <typename T>
+__global__ void k_rbgs(LV<T> v, T *e, const T *r, const double *shift, int colour, T omega) {
+  rbgs_body(v, e, r, shift, colour, omega, HwGrid{});
+}
+
 // ghost rows (Jacobi): gnew = sum_k w_k e[src_k] (+ rhs at the ghost cell)
-template <typename T, typename W>
-__global__ void k_ghost_eval(const long long *src, const long long *dst, const W *w, long long ng,
-                             const long long *ngp, const T *e, const T *rhs, T *gtmp, const double *gd = nullptr) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+template <typename T, typename W, class G>
+__device__ __forceinline__ void ghost_eval_body(const long long *src, const long long *dst, const W *w, long long ng,
+                                                const long long *ngp, const T *e, const T *rhs, T *gtmp,
+                                                const double *gd, const G &gr) {
+  long long g = gr.bx() * (long long)blockDim.x + threadIdx.x;
   if (g >= (ngp ? *ngp : ng)) return;
   T s = (T)0;
   for (int c = 0; c < 8; ++c) {
@@ -384,13 +425,20 @@ __global__ void k_ghost_eval(const long long *src, const long long *dst, const W
   gtmp[g] = s;
 }
 
+template <typename T, typename W>
+__global__ void k_ghost_eval(const long long *src, const long long *dst, const W *w, long long ng,
+                             const long long *ngp, const T *e, const T *rhs, T *gtmp, const double *gd = nullptr) {
+  ghost_eval_body(src, dst, w, ng, ngp, e, rhs, gtmp, gd, HwGrid{});
+}
+
 // ghost rows right after a ping-pong sweep, in one launch: fluid sources from the new
 // array, ghost sources from the previous one (whose ghost values the sweep copied
 // unchanged), so no thread reads a value another thread writes (Jacobi among ghosts)
-template <typename T, typename W>
-__global__ void k_ghost_pp(const long long *src, const long long *dst, const W *w, long long ng,
-                           const long long *ngp, T *enew, const T *eold, const T *rhs, const double *gd) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+template <typename T, typename W, class G>
+__device__ __forceinline__ void ghost_pp_body(const long long *src, const long long *dst, const W *w, long long ng,
+                                              const long long *ngp, T *enew, const T *eold, const T *rhs,
+                                              const double *gd, const G &gr) {
+  long long g = gr.bx() * (long long)blockDim.x + threadIdx.x;
   if (g >= (ngp ? *ngp : ng)) return;
   T s = (T)0;
   for (int c = 0; c < 8; ++c) {
@@ -404,10 +452,22 @@ __global__ void k_ghost_pp(const long long *src, const long long *dst, const W *
   enew[dst[g]] = s;
 }
 
+template <typename T, typename W>
+__global__ void k_ghost_pp(const long long *src, const long long *dst, const W *w, long long ng,
+                           const long long *ngp, T *enew, const T *eold, const T *rhs, const double *gd) {
+  ghost_pp_body(src, dst, w, ng, ngp, enew, eold, rhs, gd, HwGrid{});
+}
+
+template <typename T, class G>
+__device__ __forceinline__ void ghost_store_body(const long long *dst, long long ng, const long long *ngp,
+                                                 const T *gtmp, T *e, const G &gr) {
+  long long g = gr.bx() * (long long)blockDim.x + threadIdx.x;
+  if (g < (ngp ? *ngp : ng)) e[dst[g]] = gtmp[g];
+}
+
 template <typename T>
 __global__ void k_ghost_store(const long long *dst, long long ng, const long long *ngp, const T *gtmp, T *e) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g < (ngp ? *ngp : ng)) e[dst[g]] = gtmp[g];
+  ghost_store_body(dst, ng, ngp, gtmp, e, HwGrid{});
 }
 
 template <typename T> struct Pair;
@@ -427,16 +487,16 @@ template <> struct Pair<double> {
 // Restriction of the level-f residual to level c, one thread per coarse cell (I,J,K) with
 // coarse rows strided over blockIdx.y: rc = sum over the fluid children of V_f r_f / V_c,
 // with r_f = r - shift - (A e)_f; ec = 0 (the coarse correction starts from zero); block
-// partials of sum V_c rc at partials[blockIdx.y * gridDim.x + blockIdx.x].  Every load of a
+// partials of sum V_c rc at partials[by * gx + bx] (block (bx, by) of a gx x gy grid).  Every load of a
 // coarse cell (the 2x2x2 children of e, r and mask and their 24 face neighbours) is issued
 // before the arithmetic; children past an odd fine extent are halo cells (mask 1) whose
 // outward neighbours are not read.
-template <typename T, typename SF = T, typename SC = T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_restrict8(LV<T> f, const SF *e, const SF *r, const double *shift, LV<T> cv,
-                                                   SC *rc, SC *ec, double *partials) {
+template <typename T, typename SF, typename SC, class G>
+__device__ __forceinline__ void restrict8_body(const LV<T> &f, const SF *e, const SF *r, const double *shift,
+                                               const LV<T> &cv, SC *rc, SC *ec, double *partials, const G &gr) {
   __shared__ double sm[128];
   double acc_all = 0.0;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = gr.bx() * blockDim.x + threadIdx.x;
   const T sh = shift ? (T)(*shift) : (T)0;
   const int crows = cv.ny * cv.nz;
   // the children's 1D coefficients: x parts fixed per thread, y and z parts per row
@@ -449,7 +509,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_restrict8(LV<T>
     sdx[a] = f.sdx ? f.sdx[i] : (T)0;
   }
   if (I < cv.nx)
-    for (int row = blockIdx.y; row < crows; row += gridDim.y) {
+    for (int row = gr.by(); row < crows; row += gr.gy()) {
       const int J = row % cv.ny, K = row / cv.ny;
       const long long ic = vidx(cv, I, J, K);
       const int j0 = 2 * J, k0 = 2 * K;
@@ -503,15 +563,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_restrict8(LV<T>
             const long long id = fb + d * f.sz + b * f.sy + a;
             T c[6] = {cxm[a], cxp[a], cym[b], cyp[b], czm[d], czp[d]};
             if (f.fx) {
-              c[0] *= f.fx[id - 1]; c[1] *= f.fx[id];
-              c[2] *= f.fy[id - f.sy]; c[3] *= f.fy[id];
-              c[4] *= f.fz[id - f.sz]; c[5] *= f.fz[id];
+              c[0] = mul_rn(c[0], f.fx[id - 1]); c[1] = mul_rn(c[1], f.fx[id]);
+              c[2] = mul_rn(c[2], f.fy[id - f.sy]); c[3] = mul_rn(c[3], f.fy[id]);
+              c[4] = mul_rn(c[4], f.fz[id - f.sz]); c[5] = mul_rn(c[5], f.fz[id]);
             }
             const T D = f.sdx ? (sdx[a] + sdy[b]) + sdz[d] : ((c[0] + c[1]) + (c[2] + c[3])) + (c[4] + c[5]);
             const T xm = a ? E[d][b][0] : XM[d][b], xp = a ? XP[d][b] : E[d][b][1];
             const T ym = b ? E[d][0][a] : YM[d][a], yp = b ? YP[d][a] : E[d][1][a];
             const T zm = d ? E[0][b][a] : ZM[b][a], zp = d ? ZP[b][a] : E[1][b][a];
-            const T s = c[0] * xm + c[1] * xp + c[2] * ym + c[3] * yp + c[4] * zm + c[5] * zp;
+            // the first product rounded on its own: every sum then has one product, fused into it
+            const T s = mul_rn(c[0], xm) + c[1] * xp + c[2] * ym + c[3] * yp + c[4] * zm + c[5] * zp;
             const T res = (R[d][b][a] - sh) - (s - D * E[d][b][a]);
             if (m == 0) acc += (wxf[a] * wyf[b]) * wzf[d] * res;
           }
@@ -526,7 +587,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_restrict8(LV<T>
     if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sm[0];
+  if (threadIdx.x == 0) partials[gr.by() * gr.gx() + gr.bx()] = sm[0];
+}
+
+template <typename T, typename SF = T, typename SC = T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_restrict8(LV<T> f, const SF *e, const SF *r, const double *shift, LV<T> cv,
+                                                   SC *rc, SC *ec, double *partials) {
+  restrict8_body<T, SF, SC>(f, e, r, shift, cv, rc, ec, partials, HwGrid{});
 }
 
 // deterministic sum of nb partials (stride `stride`, offset `off`) in one block
@@ -545,15 +612,16 @@ __device__ double block_sum_partials(const double *p, int nb, int stride, int of
   return out;
 }
 
-__global__ void k_finalize_shift(const double *partials, int nb, const double *fluid_vol, double *shift) {
+__device__ __forceinline__ void finalize_shift_body(const double *partials, int nb, const double *fluid_vol,
+                                                    double *shift) {
   double s = block_sum_partials(partials, nb, 1, 0);
   if (threadIdx.x == 0) *shift = *fluid_vol > 0 ? s / *fluid_vol : 0.0;
 }
 
-// a fused multiply-add in the element type
-template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c);
-template <> __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <> __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+__global__ void k_finalize_shift(const double *partials, int nb, const double *fluid_vol, double *shift) {
+  finalize_shift_body(partials, nb, fluid_vol, shift);
+}
+
 
 // Prolongation e_f += P e_c as a z-march: one thread per coarse column (I,J) and a chunk of kc
 // coarse planes, each coarse cell with its 2x2x2 children.  Along each axis a child takes
@@ -566,12 +634,13 @@ template <> __device__ __forceinline__ double fma_t<double>(double a, double b, 
 // 3x3x3 block is fluid (inner flag), else summed the same way over the fluid indicator.
 // Children that are not fluid rows are left unchanged; rows past the fine extent (odd sizes)
 // are halo rows (mask 1), never updated.
-template <typename T, typename SC = T, typename SF = T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4)
-    k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef, const int8_t *offx,
-               const int8_t *offy, const int8_t *offz, const float *tx, const float *ty, const float *tz, int kc) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
-  const int K0 = blockIdx.z * kc, K1 = min(cv.nz, K0 + kc);
+template <typename T, typename SC, typename SF, class G>
+__device__ __forceinline__ void prolong8_body(const LV<T> &cv, const SC *ec, const uint8_t *inner, const LV<T> &f,
+                                              SF *ef, const int8_t *offx, const int8_t *offy, const int8_t *offz,
+                                              const float *tx, const float *ty, const float *tz, int kc,
+                                              const G &gr) {
+  const int I = gr.bx() * blockDim.x + threadIdx.x, J = gr.by();
+  const int K0 = gr.bz() * kc, K1 = min(cv.nz, K0 + kc);
   if (I >= cv.nx || K0 >= K1) return;
   auto axis = [](int c0, int nf, const int8_t *off, const float *t, float w[2][3]) {
 #pragma unroll
@@ -683,6 +752,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4)
         p0[a][b] = pp[a][b];
       }
   }
+}
+
+template <typename T, typename SC = T, typename SF = T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4)
+    k_prolong8(LV<T> cv, const SC *ec, const uint8_t *inner, LV<T> f, SF *ef, const int8_t *offx,
+               const int8_t *offy, const int8_t *offz, const float *tx, const float *ty, const float *tz, int kc) {
+  prolong8_body<T, SC, SF>(cv, ec, inner, f, ef, offx, offy, offz, tx, ty, tz, kc, HwGrid{});
 }
 
 // ------------------------------------------------------------------ coarse tail
@@ -809,7 +885,7 @@ __device__ void tail_prolong(const LV<T> &cv, const T *ec, const LV<T> &f, T *ef
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail(TailArgs<T> A) {
+__device__ __forceinline__ void tail_body(const TailArgs<T> &A) {
   __shared__ double shift_s[TAIL_MAX_LEVELS];
   __shared__ T rs[MAX_COARSE + 1];
   if (threadIdx.x == 0) shift_s[0] = *A.shift0;
@@ -856,9 +932,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(TailArgs<T> A) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const __grid_constant__ TailArgs<T> A) {
+  tail_body(A);
+}
+
 // bordered coarsest solve: [e; lambda] = Minv [r; 0]
 template <typename T>
-__global__ void k_coarsest(const T *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
+__device__ __forceinline__ void coarsest_body(const T *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
   __shared__ T rs[MAX_COARSE + 1];
   const int n = *ncount, m = n + 1;
   for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = r[cidx[q]];
@@ -868,6 +949,11 @@ __global__ void k_coarsest(const T *Minv, const int *cidx, const int *ncount, co
     for (int c = 0; c < n; ++c) s += Minv[q * m + c] * rs[c];
     e[cidx[q]] = s;
   }
+}
+
+template <typename T>
+__global__ void k_coarsest(const T *Minv, const int *cidx, const int *ncount, const T *r, T *e) {
+  coarsest_body(Minv, cidx, ncount, r, e);
 }
 
 // Fine-level cell kernels work on groups of four consecutive x-cells of a row (j,k): every
@@ -3153,6 +3239,24 @@ void run_initial(Run &R, double tol) {
   else if (R.rel <= tol) { R.result = IBM_OK; R.active = false; }
 }
 
+// the mixed modes' outer update without Krylov acceleration, on stream bs: p += e (the FP32
+// correction in the finest level's e), then the new residual with its norms
+void run_outer(Run &R, cudaStream_t bs) {
+  Solver &S = R.S;
+  Hierarchy *h = R.h;
+  const long long ntot = R.ntot;
+  S.st = bs;
+  const float *e32 = (const float *)h->lv[0].e;
+  if (S.dfo)
+    k_update_df<<<R.ctx->wave, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
+                                             reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
+                                             reinterpret_cast<const float4 *>(e32), ntot / 4);
+  else
+    k_update_p<<<R.ctx->wave, 256, 0, bs>>>(h->p64, e32, ntot);
+  R.ctx->launches += 1;
+  outer_residual(S, true, R.r32, true);
+}
+
 // one refinement step: V-cycle (FP64) or FP32 V-cycle(s) + outer update (mixed), then the
 // fine residual with its norms, on stream bs
 void run_step(Run &R, cudaStream_t bs) {
@@ -3180,16 +3284,10 @@ void run_step(Run &R, cudaStream_t bs) {
     }
     if (R.gcr_m > 0) {
       gcr_step<float>(S, e32, R.r32, R.gcr_m);
+      outer_residual(S, true, R.r32, true);
     } else {
-      if (S.dfo)
-        k_update_df<<<R.ctx->wave, 256, 0, bs>>>(reinterpret_cast<float4 *>(hi_of(h->p64)),
-                                          reinterpret_cast<float4 *>(lo_of(h->p64, ntot)),
-                                          reinterpret_cast<const float4 *>(e32), ntot / 4);
-      else
-        k_update_p<<<R.ctx->wave, 256, 0, bs>>>(h->p64, e32, ntot);
-      R.ctx->launches += 1;
+      run_outer(R, bs);
     }
-    outer_residual(S, true, R.r32, true);
   }
 }
 
@@ -3295,6 +3393,535 @@ ibm_status run_launch(Run &R, bool graph, cudaStream_t st) {
   return IBM_OK;
 }
 
+// ------------------------------------------------------------------ lockstep batched solves
+//
+// Problems of a batch advance through each refinement step together, one launch per V-cycle
+// stage (a level's sweep, restriction, shift, prolongation, ghost update, coarse tail) over the
+// blocks of every problem in that stage: each block runs the single-problem kernel's body on
+// its problem's arguments, so every problem gets the bits its own solve would get.  The
+// arguments travel as kernel parameters, up to BATCH_MAX problems per launch; problem q owns
+// blocks b0[q] .. b0[q + 1] - 1 of the launch (its own grid, laid out x fastest).  Problems
+// that need other forms (FP64 multigrid, membranes, Krylov acceleration, BF16 coarse storage)
+// run on the stream pool instead.
+
+constexpr int BMAX = zm::BATCH_MAX;
+constexpr int LK_COUNTERS = 1024;   // dynamic-schedule counters of one step's batched sweeps
+
+template <class P>
+struct BL {
+  P p[BMAX];
+  int b0[BMAX + 1];
+  int n;
+};
+
+// the problem that owns block b: the last q with b0[q] <= b
+template <class P>
+__device__ __forceinline__ int bl_owner(const BL<P> &L, int b) {
+  int q = 0, hi = L.n - 1;
+  while (q < hi) {
+    const int mid = (q + hi + 1) >> 1;
+    if (L.b0[mid] <= b) q = mid;
+    else hi = mid - 1;
+  }
+  return q;
+}
+
+__device__ __forceinline__ VGrid vgrid(int lb, int gx, int gy) {
+  VGrid g;
+  g.x = lb % gx;
+  g.y = (lb / gx) % gy;
+  g.z = lb / (gx * gy);
+  g.nx = gx;
+  g.ny = gy;
+  return g;
+}
+
+struct PRbgs {
+  LV<float> v;
+  float *e;
+  const float *r;
+  const double *shift;
+  int gx, gy;
+};
+struct PGhost {
+  const long long *src, *dst;
+  const float *w;
+  long long ng;
+  const long long *ngp;
+  float *e, *gtmp;
+  const float *eold, *rhs;
+};
+struct PRestrict {
+  LV<float> f, c;
+  const float *e, *r;
+  const double *shift;
+  float *rc, *ec;
+  double *part;
+  int gx, gy;
+};
+struct PShift {
+  const double *part, *fvol;
+  double *shift;
+  int nb;
+};
+struct PProlong {
+  LV<float> c, f;
+  const float *ec;
+  const uint8_t *inner;
+  float *ef;
+  const int8_t *offx, *offy, *offz;
+  const float *tx, *ty, *tz;
+  int kc, gx, gy;
+};
+struct PCoarsest {
+  const float *minv, *r;
+  const int *cidx, *ncount;
+  float *e;
+};
+struct PZero {
+  float *p;
+  long long n;
+  int gx;
+};
+static_assert(sizeof(BL<PProlong>) <= 32764 && sizeof(BL<PRestrict>) <= 32764, "kernel parameters of at most 32764 bytes");
+
+#define BL_BLOCK(L)                           \
+  const int q = bl_owner(L, (int)blockIdx.x); \
+  const auto &p = L.p[q];                     \
+  const int lb = (int)blockIdx.x - L.b0[q];
+
+__global__ void kb_rbgs(const __grid_constant__ BL<PRbgs> L, int colour, float omega) {
+  BL_BLOCK(L)
+  rbgs_body<float>(p.v, p.e, p.r, p.shift, colour, omega, vgrid(lb, p.gx, p.gy));
+}
+__global__ void kb_ghost_pp(const __grid_constant__ BL<PGhost> L) {
+  BL_BLOCK(L)
+  ghost_pp_body<float, float>(p.src, p.dst, p.w, p.ng, p.ngp, p.e, p.eold, p.rhs, nullptr, vgrid(lb, 1 << 30, 1));
+}
+__global__ void kb_ghost_eval(const __grid_constant__ BL<PGhost> L) {
+  BL_BLOCK(L)
+  ghost_eval_body<float, float>(p.src, p.dst, p.w, p.ng, p.ngp, p.e, p.rhs, p.gtmp, nullptr, vgrid(lb, 1 << 30, 1));
+}
+__global__ void kb_ghost_store(const __grid_constant__ BL<PGhost> L) {
+  BL_BLOCK(L)
+  ghost_store_body<float>(p.dst, p.ng, p.ngp, p.gtmp, p.e, vgrid(lb, 1 << 30, 1));
+}
+__global__ void __launch_bounds__(128, 5) kb_restrict8(const __grid_constant__ BL<PRestrict> L) {
+  BL_BLOCK(L)
+  restrict8_body<float, float, float>(p.f, p.e, p.r, p.shift, p.c, p.rc, p.ec, p.part, vgrid(lb, p.gx, p.gy));
+}
+__global__ void kb_finalize_shift(const __grid_constant__ BL<PShift> L) {
+  BL_BLOCK(L)
+  (void)lb;
+  finalize_shift_body(p.part, p.nb, p.fvol, p.shift);
+}
+__global__ void __launch_bounds__(128, 8) kb_prolong8(const __grid_constant__ BL<PProlong> L) {
+  BL_BLOCK(L)
+  prolong8_body<float, float, float>(p.c, p.ec, p.inner, p.f, p.ef, p.offx, p.offy, p.offz, p.tx, p.ty, p.tz, p.kc,
+                                     vgrid(lb, p.gx, p.gy));
+}
+__global__ void kb_coarsest(const __grid_constant__ BL<PCoarsest> L) {
+  BL_BLOCK(L)
+  (void)lb;
+  coarsest_body<float>(p.minv, p.cidx, p.ncount, p.r, p.e);
+}
+__global__ void kb_zero(const __grid_constant__ BL<PZero> L) {
+  BL_BLOCK(L)
+  const long long n4 = p.n / 4, step = (long long)p.gx * blockDim.x;
+  float4 *p4 = reinterpret_cast<float4 *>(p.p);
+  for (long long i = lb * (long long)blockDim.x + threadIdx.x; i < n4; i += step) p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = 4 * n4 + lb * (long long)blockDim.x + threadIdx.x; i < p.n; i += step) p.p[i] = 0.f;
+}
+// the coarse tails: block q runs problem idx[q]'s tail, its arguments copied to shared memory
+__global__ void __launch_bounds__(TAIL_THREADS) kb_tail(const TailArgs<float> *A, const __grid_constant__ BL<int> L) {
+  __shared__ TailArgs<float> As;
+  const int q = bl_owner(L, (int)blockIdx.x);
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(A + L.p[q]);
+  unsigned long long *dst = reinterpret_cast<unsigned long long *>(&As);
+  for (int w = threadIdx.x; w < (int)(sizeof(TailArgs<float>) / 8); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  tail_body<float>(As);
+}
+#undef BL_BLOCK
+static_assert(sizeof(TailArgs<float>) % 8 == 0, "tail arguments are copied as 8-byte words");
+
+// one batched launch per group of at most BMAX problems: blocks(i) is problem i's block count
+// (problems with none are left out), fill(i) its arguments
+template <class P, class Blocks, class Fill, class Launch>
+void bl_launch(const std::vector<int> &grp, Blocks blocks, Fill fill, Launch launch) {
+  std::unique_ptr<BL<P>> L(new BL<P>());
+  size_t g = 0;
+  while (g < grp.size()) {
+    int n = 0, b = 0;
+    for (; g < grp.size() && n < BMAX; ++g) {
+      const int nb = blocks(grp[g]);
+      if (nb <= 0) continue;
+      L->p[n] = fill(grp[g]);
+      L->b0[n] = b;
+      b += nb;
+      ++n;
+    }
+    if (n == 0) continue;
+    L->b0[n] = b;
+    L->n = n;
+    launch(*L, b);
+  }
+}
+
+struct Lock {
+  ibm_ctx *ctx = nullptr;
+  cudaStream_t st = nullptr;
+  std::vector<Run> *R = nullptr;
+  std::vector<std::vector<float *>> E;   // E[l][i]: the buffer holding problem i's e on level l
+  int nu1 = 0, nu2 = 0;
+  float omega = 1.f;
+  int zm_resident = 0, zmc_resident = 0;
+  int ncount = 0;                        // counters taken this step
+  std::unique_ptr<zm::Batch<float>> zb{new zm::Batch<float>()};
+};
+
+Hierarchy *lk_h(Lock &K, int i) { return (*K.R)[i].h; }
+float *lk_r(Lock &K, int i, int l) { return l == 0 ? (*K.R)[i].r32 : (float *)lk_h(K, i)->lv[l].r; }
+const double *lk_shift(Lock &K, int i, int l) {
+  double *scal = (*K.R)[i].S.scal;
+  return l == 0 ? scal + S_MU : scal + S_LEVEL_SHIFT + l;
+}
+
+// one fused sweep of level l of every problem in grp (all swept by the z-march on that level)
+void lk_zmarch(Lock &K, int l, const std::vector<int> &grp) {
+  const bool coarse = l > 0;
+  const long long resident = coarse ? K.zmc_resident : K.zm_resident;
+  // one chunk length for the launch: the fewest rounds x steps over every problem's items, as
+  // for a single problem (coarse levels: chunks of at most ZM_COARSE_KZ planes)
+  int nzmax = 1;
+  for (int i : grp) nzmax = std::max(nzmax, lk_h(K, i)->lv[l].g.nz);
+  int best_kz = std::min(nzmax, zm::KZ_MAX);
+  long long best_cost = -1;
+  for (int kz = std::min(nzmax, zm::KZ_MAX); kz >= 1; --kz) {
+    long long items = 0;
+    for (int i : grp) {
+      const LevelGeom &g = lk_h(K, i)->lv[l].g;
+      items += (long long)((g.nx + zm::TX - 1) / zm::TX) * ((g.ny + zm::TY - 1) / zm::TY) * ((g.nz + kz - 1) / kz);
+    }
+    const long long cost = ((items + resident - 1) / resident) * (kz + 6);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_kz = kz; }
+  }
+  if (coarse) best_kz = std::min(best_kz, ZM_COARSE_KZ);
+  zm::Batch<float> &B = *K.zb;
+  size_t g = 0;
+  while (g < grp.size()) {
+    int n = 0, items = 0;
+    for (; g < grp.size() && n < BMAX; ++g, ++n) {
+      const int i = grp[g];
+      Hierarchy *h = lk_h(K, i);
+      Level &L = h->lv[l];
+      float *base0 = coarse ? (float *)L.e : (float *)h->tm_base[0], *base1 = coarse ? (float *)L.ealt : (float *)h->tm_base[1];
+      const int which = K.E[l][i] == base0 ? 0 : 1;
+      float *other = which == 0 ? base1 : base0;
+      const LV<float> v = view<float>(L);
+      zm::Args<float> &a = B.a[n];
+      a = zm::Args<float>{};
+      a.nx = L.g.nx; a.ny = L.g.ny; a.nz = L.g.nz; a.px = L.g.px; a.sy = L.g.sy; a.sz = L.g.sz;
+      a.cxm = v.cxm; a.cxp = v.cxp; a.cym = v.cym; a.cyp = v.cyp; a.czm = v.czm; a.czp = v.czp;
+      if (coarse) {
+        const float *sd = (const float *)L.zsd;
+        a.sdx = sd; a.sdy = sd + L.g.nx; a.sdz = sd + L.g.nx + L.g.ny;
+        a.fx = v.fx; a.fy = v.fy; a.fz = v.fz;
+        B.tm[n][0] = L.ztm_e[which]; B.tm[n][1] = L.ztm_r; B.tm[n][2] = L.ztm_m;
+      } else {
+        a.sdx = v.sdx; a.sdy = v.sdy; a.sdz = v.sdz;
+        a.fx = a.fy = a.fz = nullptr;
+        B.tm[n][0] = h->tm_e[which]; B.tm[n][1] = h->tm_r; B.tm[n][2] = h->tm_m;
+      }
+      a.shift = lk_shift(K, i, l);
+      a.omega = K.omega;
+      a.out = other;
+      a.err = K.ctx->errflag;
+      a.kz = std::min(best_kz, a.nz);
+      a.tiles_x = (a.nx + zm::TX - 1) / zm::TX;
+      a.tiles_y = (a.ny + zm::TY - 1) / zm::TY;
+      a.items = a.tiles_x * a.tiles_y * ((a.nz + a.kz - 1) / a.kz);
+      a.first_wait = K.ctx->sweep_first_wait >= 0 ? K.ctx->sweep_first_wait : zm::WAIT_LIMIT;
+      a.counter = nullptr;
+      B.item0[n] = items;
+      items += a.items;
+      K.E[l][i] = other;
+    }
+    B.item0[n] = items;
+    B.n = n;
+    B.err = K.ctx->errflag;
+    B.counter = K.ncount < LK_COUNTERS ? K.ctx->lk_count + K.ncount++ : nullptr;
+    const int grid = (int)std::min<long long>(items, resident);
+    if (coarse)
+      zm::k_sweep_zmarch_batch<float, true><<<grid, zm::THREADS, sizeof(zm::Smem<float>), K.st>>>(B);
+    else
+      zm::k_sweep_zmarch_batch<float, false><<<grid, zm::THREADS, sizeof(zm::Smem<float>), K.st>>>(B);
+    K.ctx->launches += 1;
+  }
+}
+
+PGhost lk_ghost(Lock &K, int i, float *e, const float *eold) {
+  Hierarchy *h = lk_h(K, i);
+  PGhost p;
+  p.src = h->gsrc; p.dst = h->gdst; p.w = h->gw32; p.ng = h->gcap; p.ngp = h->d_ng;
+  p.e = e; p.eold = eold; p.rhs = (*K.R)[i].r32; p.gtmp = (float *)h->gtmp;
+  return p;
+}
+int lk_ghost_blocks(Lock &K, int i) {
+  return (*K.R)[i].t->nghost > 0 ? (int)nblk(lk_h(K, i)->gcap, 128) : 0;
+}
+
+void lk_smooth(Lock &K, int l, const std::vector<int> &grp, int sweeps) {
+  for (int s = 0; s < sweeps; ++s) {
+    if (l == 0) {
+      std::vector<float *> old(K.E[0]);
+      lk_zmarch(K, 0, grp);
+      bl_launch<PGhost>(grp, [&](int i) { return lk_ghost_blocks(K, i); },
+                        [&](int i) { return lk_ghost(K, i, K.E[0][i], old[i]); },
+                        [&](const BL<PGhost> &L, int b) { kb_ghost_pp<<<b, 128, 0, K.st>>>(L); K.ctx->launches += 1; });
+      continue;
+    }
+    std::vector<int> zg, rg;
+    for (int i : grp) (lk_h(K, i)->lv[l].zm ? zg : rg).push_back(i);
+    if (!zg.empty()) lk_zmarch(K, l, zg);
+    for (int colour = 0; colour < 2; ++colour)
+      bl_launch<PRbgs>(rg,
+                       [&](int i) {
+                         const LevelGeom &g = lk_h(K, i)->lv[l].g;
+                         return (int)nblk((g.nx + 1) / 2, 128) * g.ny * g.nz;
+                       },
+                       [&](int i) {
+                         const Level &L = lk_h(K, i)->lv[l];
+                         PRbgs p;
+                         p.v = view<float>(L); p.e = K.E[l][i]; p.r = lk_r(K, i, l); p.shift = lk_shift(K, i, l);
+                         p.gx = (int)nblk((L.g.nx + 1) / 2, 128); p.gy = L.g.ny;
+                         return p;
+                       },
+                       [&](const BL<PRbgs> &L, int b) {
+                         kb_rbgs<<<b, 128, 0, K.st>>>(L, colour, K.omega);
+                         K.ctx->launches += 1;
+                       });
+  }
+}
+
+// the restriction's grid of level l -> l + 1, as the single-problem V-cycle takes it
+void lk_restrict_grid(Hierarchy *h, int l, int &gx, int &gy) {
+  const Level &C = h->lv[l + 1];
+  gx = (int)nblk(C.g.nx, 128);
+  gy = std::max(1, std::min(C.g.ny * C.g.nz, std::min(RESTRICT_BLOCKS, h->grid_blocks[0]) / gx));
+}
+
+void lk_vcycle(Lock &K, int l, const std::vector<int> &grp) {
+  std::vector<int> tail, coarsest, mid;
+  for (int i : grp) {
+    Hierarchy *h = lk_h(K, i);
+    const int nl = (int)h->lv.size();
+    if (l > 0 && l == h->tail_level && nl - l >= 2) tail.push_back(i);
+    else if (l == nl - 1) coarsest.push_back(i);
+    else mid.push_back(i);
+  }
+  if (!tail.empty()) {
+    bl_launch<int>(tail, [](int) { return 1; }, [](int i) { return i; },
+                   [&](const BL<int> &L, int b) {
+                     kb_tail<<<b, TAIL_THREADS, 0, K.st>>>((const TailArgs<float> *)K.ctx->lk_tail, L);
+                     K.ctx->launches += 1;
+                   });
+  }
+  if (!coarsest.empty()) {
+    bl_launch<PCoarsest>(coarsest, [](int) { return 1; },
+                         [&](int i) {
+                           Hierarchy *h = lk_h(K, i);
+                           PCoarsest p;
+                           p.minv = (const float *)h->minv; p.cidx = h->cidx; p.ncount = h->dncoarse;
+                           p.r = lk_r(K, i, l); p.e = K.E[l][i];
+                           return p;
+                         },
+                         [&](const BL<PCoarsest> &L, int b) {
+                           kb_coarsest<<<b, 128, 0, K.st>>>(L);
+                           K.ctx->launches += 1;
+                         });
+  }
+  if (mid.empty()) return;
+  lk_smooth(K, l, mid, K.nu1);
+  bl_launch<PRestrict>(mid,
+                       [&](int i) {
+                         int gx, gy;
+                         lk_restrict_grid(lk_h(K, i), l, gx, gy);
+                         return gx * gy;
+                       },
+                       [&](int i) {
+                         Hierarchy *h = lk_h(K, i);
+                         PRestrict p;
+                         p.f = view<float>(h->lv[l]); p.c = view<float>(h->lv[l + 1]);
+                         p.e = K.E[l][i]; p.r = lk_r(K, i, l); p.shift = lk_shift(K, i, l);
+                         p.rc = (float *)h->lv[l + 1].r; p.ec = (float *)h->lv[l + 1].e;
+                         p.part = (*K.R)[i].S.part;
+                         lk_restrict_grid(h, l, p.gx, p.gy);
+                         return p;
+                       },
+                       [&](const BL<PRestrict> &L, int b) {
+                         kb_restrict8<<<b, 128, 0, K.st>>>(L);
+                         K.ctx->launches += 1;
+                       });
+  bl_launch<PShift>(mid, [](int) { return 1; },
+                    [&](int i) {
+                      Hierarchy *h = lk_h(K, i);
+                      int gx, gy;
+                      lk_restrict_grid(h, l, gx, gy);
+                      PShift p;
+                      p.part = (*K.R)[i].S.part; p.nb = gx * gy; p.fvol = h->d_fvol + (l + 1);
+                      p.shift = (*K.R)[i].S.scal + S_LEVEL_SHIFT + (l + 1);
+                      return p;
+                    },
+                    [&](const BL<PShift> &L, int b) {
+                      kb_finalize_shift<<<b, 256, 0, K.st>>>(L);
+                      K.ctx->launches += 1;
+                    });
+  for (int i : mid) K.E[l + 1][i] = (float *)lk_h(K, i)->lv[l + 1].e;
+  lk_vcycle(K, l + 1, mid);
+  const long long sms = K.ctx->sm_count > 0 ? K.ctx->sm_count : 152;
+  auto kc_of = [&](const LevelGeom &C) {
+    const long long pcols = nblk(C.nx, 128) * (long long)C.ny;
+    return (int)std::max(1LL, std::min<long long>(PROLONG_KC, pcols * C.nz / (16LL * sms)));
+  };
+  bl_launch<PProlong>(mid,
+                      [&](int i) {
+                        const LevelGeom &C = lk_h(K, i)->lv[l + 1].g;
+                        const int kc = kc_of(C);
+                        return (int)nblk(C.nx, 128) * C.ny * ((C.nz + kc - 1) / kc);
+                      },
+                      [&](int i) {
+                        Hierarchy *h = lk_h(K, i);
+                        const Level &C = h->lv[l + 1], &F = h->lv[l];
+                        const int nxf = F.g.nx, nyf = F.g.ny;
+                        PProlong p;
+                        p.c = view<float>(C); p.f = view<float>(F);
+                        p.ec = K.E[l + 1][i]; p.inner = C.inner; p.ef = K.E[l][i];
+                        p.offx = F.poff; p.offy = F.poff + nxf; p.offz = F.poff + nxf + nyf;
+                        p.tx = F.pt; p.ty = F.pt + nxf; p.tz = F.pt + nxf + nyf;
+                        p.kc = kc_of(C.g);
+                        p.gx = (int)nblk(C.g.nx, 128); p.gy = C.g.ny;
+                        return p;
+                      },
+                      [&](const BL<PProlong> &L, int b) {
+                        kb_prolong8<<<b, 128, 0, K.st>>>(L);
+                        K.ctx->launches += 1;
+                      });
+  if (l == 0) {   // the corrected fluid values make the ghost rows stale
+    bl_launch<PGhost>(mid, [&](int i) { return lk_ghost_blocks(K, i); },
+                      [&](int i) { return lk_ghost(K, i, K.E[0][i], nullptr); },
+                      [&](const BL<PGhost> &L, int b) { kb_ghost_eval<<<b, 128, 0, K.st>>>(L); K.ctx->launches += 1; });
+    bl_launch<PGhost>(mid, [&](int i) { return lk_ghost_blocks(K, i); },
+                      [&](int i) { return lk_ghost(K, i, K.E[0][i], nullptr); },
+                      [&](const BL<PGhost> &L, int b) { kb_ghost_store<<<b, 128, 0, K.st>>>(L); K.ctx->launches += 1; });
+  }
+  lk_smooth(K, l, mid, K.nu2);
+}
+
+// can the batch advance in lockstep: mixed precision, closed bodies, no Krylov acceleration,
+// FP32 coarse storage, and every finest level swept by the fused z-march on its own e and r
+bool lockstep_ok(const std::vector<Run> &R, const ibm_solve_opts *opts) {
+  if (opts->batch_schedule != 0 || opts->precision == 0 || opts->coarse_bf16) return false;
+  for (const Run &r : R) {
+    const Hierarchy *h = r.h;
+    if (r.t->membrane || r.gcr_m > 0 || h->hcnt[1] > 0 || h->hcnt[2] > 0 || !h->zmarch || h->elem != 4) return false;
+    const void *e0 = h->lv[0].e;
+    if ((e0 != h->tm_base[0] && e0 != h->tm_base[1]) || (const void *)r.r32 != h->tm_rbase) return false;
+    if ((int)h->lv.size() > 1 && h->lv[1].bf16) return false;
+  }
+  return true;
+}
+
+// the context's lockstep buffers: step counters and the problems' coarse-tail arguments
+ibm_status lockstep_setup(Lock &K, std::vector<Run> &R) {
+  ibm_ctx *ctx = K.ctx;
+  const int n = (int)R.size();
+  if (!ctx->lk_count) IBM_TRY(cudaMalloc((void **)&ctx->lk_count, sizeof(int) * LK_COUNTERS));
+  if (ctx->lk_tail_cap < n) {
+    if (ctx->lk_tail) cudaFree(ctx->lk_tail);
+    ctx->lk_tail = nullptr;
+    ctx->lk_tail_cap = 0;
+    IBM_TRY(cudaMalloc((void **)&ctx->lk_tail, sizeof(TailArgs<float>) * n));
+    ctx->lk_tail_cap = n;
+  }
+  std::vector<TailArgs<float>> ta(n);
+  size_t nl_max = 1;
+  for (int i = 0; i < n; ++i) {
+    Hierarchy *h = R[i].h;
+    nl_max = std::max(nl_max, h->lv.size());
+    const int nl = (int)h->lv.size(), l = h->tail_level;
+    TailArgs<float> &A = ta[i];
+    A = TailArgs<float>{};
+    if (l > 0 && nl - l >= 2) {
+      A.nl = nl - l;
+      for (int q = 0; q < A.nl; ++q) {
+        Level &L = h->lv[l + q];
+        A.lv[q].v = view<float>(L);
+        A.lv[q].e = (float *)L.e;
+        A.lv[q].r = (float *)L.r;
+        A.lv[q].poff = L.poff;
+        A.lv[q].pt = L.pt;
+      }
+      A.shift0 = R[i].S.scal + S_LEVEL_SHIFT + l;
+      A.fvol = h->d_fvol + l;
+      A.minv = (const float *)h->minv;
+      A.cidx = h->cidx;
+      A.ncoarse = h->dncoarse;
+      A.nu1 = K.nu1;
+      A.nu2 = K.nu2;
+      A.omega = K.omega;
+    }
+  }
+  IBM_TRY(cudaMemcpyAsync(ctx->lk_tail, ta.data(), sizeof(TailArgs<float>) * n, cudaMemcpyHostToDevice, K.st));
+  K.E.assign(nl_max, std::vector<float *>(n, nullptr));
+  for (int i = 0; i < n; ++i) K.E[0][i] = (float *)R[i].h->lv[0].e;
+  const size_t smem = sizeof(zm::Smem<float>);
+  int pf = 0, pc = 0;
+  IBM_TRY(cudaFuncSetAttribute(zm::k_sweep_zmarch_batch<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  IBM_TRY(cudaFuncSetAttribute(zm::k_sweep_zmarch_batch<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  IBM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, zm::k_sweep_zmarch_batch<float, false>, zm::THREADS, smem));
+  IBM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, zm::k_sweep_zmarch_batch<float, true>, zm::THREADS, smem));
+  if (pf < 1 || pc < 1) return IBM_ERR_CUDA;
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+  K.zm_resident = pf * sms;
+  K.zmc_resident = pc * sms;
+  return IBM_OK;
+}
+
+// one refinement step of the problems in act: their FP32 V-cycles in lockstep on the caller's
+// stream, then each problem's outer update and residual on the stream pool
+ibm_status lockstep_step(Lock &K, const std::vector<int> &act, int inner) {
+  ibm_ctx *ctx = K.ctx;
+  std::vector<Run> &R = *K.R;
+  IBM_TRY(cudaMemsetAsync(ctx->lk_count, 0, sizeof(int) * LK_COUNTERS, K.st));
+  K.ncount = 0;
+  for (int q = 0; q < std::max(1, inner); ++q) {
+    if (q == 0)
+      bl_launch<PZero>(act, [&](int i) { return (int)std::min<long long>(nblk(R[i].ntot / 4, 256), 1024); },
+                       [&](int i) {
+                         PZero p;
+                         p.p = K.E[0][i]; p.n = R[i].ntot;
+                         p.gx = (int)std::min<long long>(nblk(R[i].ntot / 4, 256), 1024);
+                         return p;
+                       },
+                       [&](const BL<PZero> &L, int b) { kb_zero<<<b, 256, 0, K.st>>>(L); ctx->launches += 1; });
+    lk_vcycle(K, 0, act);
+  }
+  for (int i : act) R[i].h->lv[0].e = K.E[0][i];
+  const int ns = std::min((int)act.size(), (int)ibm_ctx::NBSTREAM);
+  IBM_TRY(cudaEventRecord(ctx->bevent[ibm_ctx::NBSTREAM], K.st));
+  for (int s = 0; s < ns; ++s) IBM_TRY(cudaStreamWaitEvent(ctx->bstream[s], ctx->bevent[ibm_ctx::NBSTREAM], 0));
+  for (size_t j = 0; j < act.size(); ++j) run_outer(R[act[j]], ctx->bstream[j % ns]);
+  for (int s = 0; s < ns; ++s) {
+    IBM_TRY(cudaEventRecord(ctx->bevent[s], ctx->bstream[s]));
+    IBM_TRY(cudaStreamWaitEvent(K.st, ctx->bevent[s], 0));
+  }
+  IBM_TRY(cudaGetLastError());
+  return IBM_OK;
+}
+
 // after the solve: the time-out flag of bounded device waits
 ibm_status read_errflag(ibm_ctx *ctx, ibm_status result, cudaStream_t st) {
   int herr = 0;
@@ -3349,12 +3976,15 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
   return result;
 }
 
-// Batched solves: every problem runs the single-problem refinement step with its own
-// scalars and partials, captured once as its hierarchy's CUDA graph.  Each step launches
-// the graphs of the problems still iterating on the context's pool of streams (problem p
-// on stream p mod NBSTREAM), forked from and joined back into the caller's stream, so the
-// small problems' latency-bound coarse levels overlap and their fine-level kernels share
-// the GPU; converged problems drop out.  One read-back per step serves every problem.
+// Batched solves: every problem keeps its own scalars and partials.  In lockstep (mixed
+// precision on closed bodies, the default when every problem allows it) each step's V-cycles
+// run as one launch per stage over all problems still iterating, and their outer updates and
+// residuals on the context's pool of streams.  Otherwise each problem runs the single-problem
+// refinement step, captured once as its hierarchy's CUDA graph, and each step launches the
+// graphs of the problems still iterating on the stream pool (problem p on stream p mod
+// NBSTREAM), forked from and joined back into the caller's stream, so the small problems'
+// latency-bound coarse levels overlap.  Converged problems drop out; one read-back per step
+// serves every problem.
 ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const double *const *rhs, double tol,
                               double *const *p_user, const ibm_solve_opts *opts, ibm_solve_info *infos,
                               cudaStream_t st) {
@@ -3392,23 +4022,45 @@ ibm_status solve_batched_impl(ibm_ctx *ctx, int n, ibm_tables *const *ts, const 
     if ((s = run_begin(R[p], st)) != IBM_OK) return s;
   if ((s = readback()) != IBM_OK) return s;
   int active = 0;
-  std::vector<char> graph(n);
   for (int p = 0; p < n; ++p) {
     run_initial(R[p], tol);
     active += R[p].active;
-    graph[p] = run_graphable(R[p]);
-    if (graph[p] && (s = run_capture(R[p])) != IBM_OK) return s;
+  }
+  const bool lock = lockstep_ok(R, opts);
+  Lock K;
+  std::vector<char> graph(n, 0);
+  if (lock) {
+    K.ctx = ctx;
+    K.st = st;
+    K.R = &R;
+    K.nu1 = opts->nu1;
+    K.nu2 = opts->nu2;
+    K.omega = (float)opts->omega;
+    if ((s = lockstep_setup(K, R)) != IBM_OK) return s;
+  } else {
+    for (int p = 0; p < n; ++p) {
+      graph[p] = run_graphable(R[p]);
+      if (graph[p] && (s = run_capture(R[p])) != IBM_OK) return s;
+    }
   }
   const int ns = std::min(n, (int)ibm_ctx::NBSTREAM);
   int it = 0;
+  std::vector<int> act;
   while (active > 0 && it < opts->max_cycles) {
-    IBM_TRY(cudaEventRecord(ctx->bevent[ibm_ctx::NBSTREAM], st));
-    for (int q = 0; q < ns; ++q) IBM_TRY(cudaStreamWaitEvent(ctx->bstream[q], ctx->bevent[ibm_ctx::NBSTREAM], 0));
-    for (int p = 0; p < n; ++p)
-      if (R[p].active && (s = run_launch(R[p], graph[p], ctx->bstream[p % ns])) != IBM_OK) return s;
-    for (int q = 0; q < ns; ++q) {
-      IBM_TRY(cudaEventRecord(ctx->bevent[q], ctx->bstream[q]));
-      IBM_TRY(cudaStreamWaitEvent(st, ctx->bevent[q], 0));
+    if (lock) {
+      act.clear();
+      for (int p = 0; p < n; ++p)
+        if (R[p].active) act.push_back(p);
+      if ((s = lockstep_step(K, act, opts->inner_cycles)) != IBM_OK) return s;
+    } else {
+      IBM_TRY(cudaEventRecord(ctx->bevent[ibm_ctx::NBSTREAM], st));
+      for (int q = 0; q < ns; ++q) IBM_TRY(cudaStreamWaitEvent(ctx->bstream[q], ctx->bevent[ibm_ctx::NBSTREAM], 0));
+      for (int p = 0; p < n; ++p)
+        if (R[p].active && (s = run_launch(R[p], graph[p], ctx->bstream[p % ns])) != IBM_OK) return s;
+      for (int q = 0; q < ns; ++q) {
+        IBM_TRY(cudaEventRecord(ctx->bevent[q], ctx->bstream[q]));
+        IBM_TRY(cudaStreamWaitEvent(st, ctx->bevent[q], 0));
+      }
     }
     IBM_TRY(cudaGetLastError());
     if ((s = readback()) != IBM_OK) return s;

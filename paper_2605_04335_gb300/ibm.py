@@ -44,7 +44,7 @@ class ibm_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32), ("max_cycles", C.c_int32),
                 ("inner_cycles", C.c_int32), ("use_graph", C.c_int32), ("omega", C.c_double),
                 ("krylov", C.c_int32), ("method", C.c_int32), ("srj_steps", C.c_int32),
-                ("coarse_bf16", C.c_int32), ("sweep_chunk", C.c_int32)]
+                ("coarse_bf16", C.c_int32), ("sweep_chunk", C.c_int32), ("batch_schedule", C.c_int32)]
 
 
 class ibm_helmholtz_opts(C.Structure):
@@ -235,11 +235,12 @@ class SolveOpts:
     srj_steps: int = 8
     coarse_bf16: int = 0
     sweep_chunk: int = 0
+    batch_schedule: int = 0
 
 
 def _c_opts(o: SolveOpts) -> ibm_solve_opts:
     return ibm_solve_opts(o.precision, o.nu1, o.nu2, o.max_cycles, o.inner_cycles, o.use_graph, o.omega, o.krylov,
-                          o.method, o.srj_steps, o.coarse_bf16, o.sweep_chunk)
+                          o.method, o.srj_steps, o.coarse_bf16, o.sweep_chunk, o.batch_schedule)
 
 
 def poisson_solve(ctx, tables, rhs, tol, p, opts: SolveOpts | None = None, stream=None, history_cap: int = 256,
@@ -387,7 +388,8 @@ def ibm_autotune(ctx, tables, precision: int, rhs, p_work, tol: float = 1e-10, s
     _check(load_library().ibm_autotune(ctx, tables, precision, _ptr(rhs), _ptr(p_work), float(tol), C.byref(best),
                                        C.byref(ms), _stream(stream)), "ibm_autotune")
     return SolveOpts(best.precision, best.nu1, best.nu2, best.max_cycles, best.inner_cycles, best.use_graph,
-                     best.omega, best.krylov, best.method, best.srj_steps, best.coarse_bf16, best.sweep_chunk), float(ms.value)
+                     best.omega, best.krylov, best.method, best.srj_steps, best.coarse_bf16, best.sweep_chunk,
+                     best.batch_schedule), float(ms.value)
 
 
 # ----------------------------------------------------------------------------- conveniences

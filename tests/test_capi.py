@@ -70,3 +70,31 @@ def test_helmholtz_option_defaults():
     assert (o.precision, o.srj_steps, o.max_cycles) == (2, 8, 100)
     d = pkg.HelmholtzOpts()
     assert (d.precision, d.srj_steps, d.max_cycles) == (2, 8, 100)
+
+
+def _struct_fields(name):
+    """Field names of a typedef'd struct in include/ibm_poisson.h, in declaration order."""
+    src = open(os.path.join(ROOT, "include", "ibm_poisson.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct(?: %s)? \{([^{}]*)\} %s;" % (name, name), src, flags=re.S).group(1)
+    names = []
+    for decl in body.split(";"):
+        words = decl.split(None, 1)   # type, then one or more comma-separated names
+        if len(words) == 2:
+            names += [w.strip(" *\n") for w in words[1].split(",")]
+    return names
+
+
+def test_solve_options_binding_matches_the_header():
+    """The ctypes mirror of ibm_solve_opts has the header's fields in the header's order, and
+    the C defaults are the binding's defaults."""
+    import dataclasses
+    import paper_2605_04335_gb300 as pkg
+    from paper_2605_04335_gb300.ibm import ibm_solve_opts
+    assert [f[0] for f in ibm_solve_opts._fields_] == _struct_fields("ibm_solve_opts")
+    o = ibm_solve_opts()
+    pkg.load_library().ibm_solve_opts_default(ctypes.byref(o))
+    d = pkg.SolveOpts()
+    for f in dataclasses.fields(d):
+        assert getattr(o, f.name) == pytest.approx(getattr(d, f.name)), f.name
+    assert o.batch_schedule == 0

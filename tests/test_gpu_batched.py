@@ -1,5 +1,6 @@
-"""Batched solves of uneven problems (one launch per V-cycle stage) vs the oracle and the
-single-problem path; the autotuner returns a schedule that converges."""
+"""Batched solves of uneven problems (lockstep: one launch per V-cycle stage over every
+problem; or the stream pool) vs the oracle and the single-problem path; the autotuner returns
+a schedule that converges."""
 import numpy as np
 import pytest
 
@@ -53,6 +54,67 @@ def test_batched_matches_oracle_and_single(ctx, prec):
         tabs[q].solve(rhs[q], p1, TOL, pkg.SolveOpts(precision=prec))
         assert np.linalg.norm((p1.cpu().numpy() - pb)[fl]) / np.linalg.norm(pb[fl]) <= PARITY
     assert len(set(cyc)) >= 1
+    for t in tabs:
+        t.close()
+
+
+def _wide_problem():
+    """136 x 40 x 24 cubic cells: two 128-cell tiles of the fused sweep in x."""
+    h = 1.0 / 40
+    return synth.Problem("wide", np.arange(137) * h, np.arange(41) * h, np.arange(25) * h,
+                         [synth.octa_sphere(3, (1.2, 0.5, 0.3), 0.12)], 4242)
+
+
+def _solve_all(pkg, c, tabs, rhs, opts):
+    ps = [torch.zeros_like(r) for r in rhs]
+    status, reps = pkg.poisson_solve_batched(c.h, [t.h for t in tabs], rhs, TOL, ps, opts)
+    assert status == "IBM_OK"
+    return [x.cpu().numpy() for x in ps], reps
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_lockstep_gives_each_problem_its_own_solve(ctx, prec):
+    """The lockstep schedule (one launch per V-cycle stage over every problem, the default for
+    mixed precision on closed bodies) runs each block on the single-problem kernels' bodies:
+    every problem's pressure, cycle count and lambda equal its own poisson_solve's, and the
+    stream-pool schedule's, bit for bit.  The batch mixes level counts (edges 20-44) and a
+    problem two sweep tiles wide."""
+    pkg, c = ctx
+    probs = _batch(5, 11, 20, 44) + [_wide_problem()]
+    tabs = [pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes) for pr in probs]
+    rhs = [torch.from_numpy(pr.rhs()).cuda() for pr in probs]
+    pl, rl = _solve_all(pkg, c, tabs, rhs, pkg.SolveOpts(precision=prec))
+    pp, rp = _solve_all(pkg, c, tabs, rhs, pkg.SolveOpts(precision=prec, batch_schedule=1))
+    for q in range(len(probs)):
+        p1 = torch.zeros_like(rhs[q])
+        r1 = tabs[q].solve(rhs[q], p1, TOL, pkg.SolveOpts(precision=prec))
+        assert rl[q]["rel_resid"] <= TOL
+        assert rl[q]["cycles"] == r1["cycles"] == rp[q]["cycles"]
+        assert rl[q]["lambda"] == r1["lambda"] == rp[q]["lambda"]
+        assert np.array_equal(pl[q], p1.cpu().numpy()), probs[q].name
+        assert np.array_equal(pl[q], pp[q]), probs[q].name
+    for t in tabs:
+        t.close()
+
+
+def test_lockstep_splits_launches_of_more_than_48_problems(ctx):
+    """50 problems: each stage takes two launches (48 + 2 problems); every problem still gets
+    its own solve's bits."""
+    pkg, c = ctx
+    probs = _batch(50, 21, 12, 20)
+    tabs = [pkg.Tables(c, pr.xf, pr.yf, pr.zf, pr.meshes) for pr in probs]
+    rhs = [torch.from_numpy(pr.rhs()).cuda() for pr in probs]
+    pl, rl = _solve_all(pkg, c, tabs, rhs, pkg.SolveOpts(precision=1))
+    for q in range(len(probs)):
+        assert rl[q]["rel_resid"] <= TOL
+    for q in (0, 1, 47, 48, 49):
+        p1 = torch.zeros_like(rhs[q])
+        r1 = tabs[q].solve(rhs[q], p1, TOL, pkg.SolveOpts(precision=1))
+        assert rl[q]["cycles"] == r1["cycles"]
+        assert np.array_equal(pl[q], p1.cpu().numpy()), q
+    with pytest.raises(pkg.IbmError):
+        pkg.poisson_solve_batched(c.h, [tabs[0].h], [rhs[0]], TOL, [torch.zeros_like(rhs[0])],
+                                  pkg.SolveOpts(precision=1, batch_schedule=2))
     for t in tabs:
         t.close()
 
