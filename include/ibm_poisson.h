@@ -349,12 +349,14 @@ ibm_status poisson_solve(ibm_ctx *ctx, const ibm_tables *t, const double *rhs_de
 
 /* Batched pressure Poisson solves: n independent problems (each its own classified grid, of
  * any size; closed bodies or membranes; every precision mode and Krylov setting) advanced
- * together.  Each problem runs the single-problem refinement step with its own device
- * scalars and partial sums, captured once as a CUDA graph; every step launches the graphs of
- * the problems still iterating on a small pool of streams owned by the context (forked from
- * and joined back into `stream`), so that the problems' kernels run concurrently, with one
- * read-back per step for all of them.  Same equations, options and outputs as
- * poisson_solve, per problem:
+ * together, each with its own device scalars and partial sums, with one read-back per step
+ * for all of them.  Schedule (opts->batch_schedule): lockstep, where each V-cycle stage and
+ * each kernel of the outer step is one launch over every problem still iterating (mixed
+ * precision, closed bodies, no Krylov acceleration, FP32 coarse storage); or each problem's
+ * step captured once as a CUDA graph, the graphs of the problems still iterating launched on
+ * a small pool of streams owned by the context (forked from and joined back into `stream`).
+ * Either way each problem gets the bits of its own poisson_solve.  Same equations, options
+ * and outputs as poisson_solve, per problem:
  *   tables[p], rhs_dev[p], p_dev[p] as in poisson_solve (p_dev[p] is in/out);
  *   infos (optional, n entries) receives each problem's report; ms_total is the batch's.
  * The tables must be distinct (each problem owns its work arrays); the context's batch

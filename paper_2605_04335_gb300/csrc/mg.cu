@@ -971,6 +971,8 @@ struct RowGroups {
   __device__ bool active() const { return rsub < rpi; }
   __device__ int first_row() const { return blockIdx.x * rpi + rsub; }
   __device__ int row_step() const { return gridDim.x * rpi; }
+  template <class G> __device__ int first_row(const G &gr) const { return gr.bx() * rpi + rsub; }
+  template <class G> __device__ int row_step(const G &gr) const { return gr.gx() * rpi; }
 };
 
 template <typename T> struct Vec4;
@@ -1005,8 +1007,9 @@ __device__ __forceinline__ void ld_fluid4(const uint8_t *m, bool fl[4]) {
   fl[0] = fluid_row(q.x); fl[1] = fluid_row(q.y); fl[2] = fluid_row(q.z); fl[3] = fluid_row(q.w);
 }
 
-// block reduction of three doubles into partials[3 b + q]
-__device__ __forceinline__ void block_partials3(double A0, double A1, double A2, double *partials) {
+// block reduction of three doubles into partials[3 b + q] (b: the block's index in its grid)
+__device__ __forceinline__ void block_partials3(double A0, double A1, double A2, double *partials,
+                                                int b = (int)blockIdx.x) {
   __shared__ double sm[3][REDUCE_THREADS];
   sm[0][threadIdx.x] = A0; sm[1][threadIdx.x] = A1; sm[2][threadIdx.x] = A2;
   __syncthreads();
@@ -1016,7 +1019,7 @@ __device__ __forceinline__ void block_partials3(double A0, double A1, double A2,
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sm[q][0];
+    for (int q = 0; q < 3; ++q) partials[3 * b + q] = sm[q][0];
 }
 
 // FP64 fine residual r = b - lambda - A p on fluid rows, stored as R (FP32 for the mixed
@@ -1029,10 +1032,10 @@ __device__ __forceinline__ void block_partials3(double A0, double A1, double A2,
 // float widths dx dy dz) and the norm/mean partial sums are FP32 per thread, folded into FP64
 // every 8 rows.
 // WP = false: the residual of p = 0 (no stencil; fewer registers, a fuller machine).
-template <typename R, bool WP = true>
-__global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
-                                                              const double *lambda, const float *wf, R *r32,
-                                                              double *partials, const unsigned *p_nonzero) {
+template <typename R, bool WP, class G>
+__device__ __forceinline__ void residual64_body(const LV<double> &v, const double *p, const double *b,
+                                                const double *lambda, const float *wf, R *r32, double *partials,
+                                                const unsigned *p_nonzero, const G &gr) {
   const double lam = *lambda;
   // p_nonzero (optional): zero when every packed value of p is zero, so A p = 0 exactly and
   // the FP64 stencil is skipped (a cold start); one test for the whole launch
@@ -1044,7 +1047,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
   const RowGroups rg(nx);
   const int rows = ny * v.nz;
   if (rg.active())
-    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+    for (int row = rg.first_row(gr); row < rows; row += rg.row_step(gr)) {
       const int j = row % ny, k = row / ny;
       const double cym = v.cym[j], cyp = v.cyp[j], czm = v.czm[k], czp = v.czp[k];
       const double syz = v.sdy[j] + v.sdz[k];
@@ -1097,17 +1100,25 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, con
       }
     }
   A0 += a0; A1 += a1; A2 += a2;
-  block_partials3(A0, A1, A2, partials);
+  block_partials3(A0, A1, A2, partials, gr.bx());
+}
+
+template <typename R, bool WP = true>
+__global__ void __launch_bounds__(REDUCE_THREADS) k_residual64(LV<double> v, const double *p, const double *b,
+                                                              const double *lambda, const float *wf, R *r32,
+                                                              double *partials, const unsigned *p_nonzero) {
+  residual64_body<R, WP>(v, p, b, lambda, wf, r32, partials, p_nonzero, HwGrid{});
 }
 
 // ghost rows r_G = sum w v - g; block partials of (s_G r_G)^2 at gpart[b]
-template <typename R>
-__global__ void k_ghost_resid64(const long long *src, const long long *dst, const double *w, const double *scale,
-                                const long long *ngp, const double *p, R *r32, double *gpart, const double *gd) {
+template <typename R, class G>
+__device__ __forceinline__ void ghost_resid64_body(const long long *src, const long long *dst, const double *w,
+                                                   const double *scale, const long long *ngp, const double *p, R *r32,
+                                                   double *gpart, const double *gd, const G &gr) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
   const long long ng = *ngp;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+  for (long long g = gr.bx() * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gr.gx() * blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < 8; ++c) {
       long long q = src[8 * g + c];
@@ -1125,14 +1136,20 @@ __global__ void k_ghost_resid64(const long long *src, const long long *dst, cons
     if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) gpart[blockIdx.x] = sm[0];
+  if (threadIdx.x == 0) gpart[gr.bx()] = sm[0];
+}
+
+template <typename R>
+__global__ void k_ghost_resid64(const long long *src, const long long *dst, const double *w, const double *scale,
+                                const long long *ngp, const double *p, R *r32, double *gpart, const double *gd) {
+  ghost_resid64_body<R>(src, dst, w, scale, ngp, p, r32, gpart, gd, HwGrid{});
 }
 
 // mu = sum V r / V_F; ||S P r||^2 = sum r^2 - 2 mu sum r + N_F mu^2 + sum (s r_G)^2;
 // lambda += mu when update_lambda
 // (cpart, ncb: block partials of the membrane cut cells, same layout as partials; ncb may be 0)
-__global__ void k_finalize_resid(const double *partials, int nb, const double *gpart, int ngb, double *scal,
-                                 int update_lambda, const double *cpart, int ncb) {
+__device__ __forceinline__ void finalize_resid_body(const double *partials, int nb, const double *gpart, int ngb,
+                                                    double *scal, int update_lambda, const double *cpart, int ncb) {
   double sv = block_sum_partials(partials, nb, 3, 0);
   double s1 = block_sum_partials(partials, nb, 3, 1);
   double s2 = block_sum_partials(partials, nb, 3, 2);
@@ -1152,11 +1169,19 @@ __global__ void k_finalize_resid(const double *partials, int nb, const double *g
   }
 }
 
+__global__ void k_finalize_resid(const double *partials, int nb, const double *gpart, int ngb, double *scal,
+                                 int update_lambda, const double *cpart, int ncb) {
+  finalize_resid_body(partials, nb, gpart, ngb, scal, update_lambda, cpart, ncb);
+}
+
 // p += e (the refinement update); e widened on the integer pipe, one FP64 add per cell
-__global__ void k_update_p(double *p, const float *e, long long n) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+template <class G>
+__device__ __forceinline__ void update_p_body(double *p, const float *e, long long n, const G &gr) {
+  for (long long q = gr.bx() * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gr.gx() * blockDim.x)
     p[q] += dfl::widen(e[q]);
 }
+
+__global__ void k_update_p(double *p, const float *e, long long n) { update_p_body(p, e, n, HwGrid{}); }
 
 __global__ void __launch_bounds__(REDUCE_THREADS) k_gauge_sum(LV<double> v, const double *p, double *partials) {
   __shared__ double sm[REDUCE_THREADS];
@@ -1273,9 +1298,10 @@ __global__ void k_split_df(const double *src, int n, float *h, float *l) {
 // r = b - lambda - A p on fluid rows with pairs of floats (see dfloat.cuh); FP32 copy of r
 // (0 on other cells); block partials (sum V r, sum r, sum r^2) at partials[3 b + {0,1,2}] as
 // k_residual64, for b < REDUCE_BLOCKS whatever the grid.  ph == nullptr: residual of p = 0.
-__global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const float *ph, const float *pl,
-                                                               const float *bh, const float *bl,
-                                                               const double *lambda, float *r32, double *partials) {
+template <class G>
+__device__ __forceinline__ void residual_df_body(const DfView &v, const float *ph, const float *pl, const float *bh,
+                                                 const float *bl, const double *lambda, float *r32, double *partials,
+                                                 const G &gr) {
   float lh, ll;
   dfl::split(*lambda, lh, ll);
   const int nx = v.nx, ny = v.ny, nz = v.nz, n = nx + ny + nz;
@@ -1286,7 +1312,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const 
   const RowGroups rg(nx);
   const int rows = ny * nz;
   if (rg.active())
-    for (int row = rg.first_row(); row < rows; row += rg.row_step()) {
+    for (int row = rg.first_row(gr); row < rows; row += rg.row_step(gr)) {
       const int j = row % ny, k = row / ny;
       const float cymh = H[2 * nx + j], cyml = L[2 * nx + j], cyph = H[2 * nx + ny + j], cypl = L[2 * nx + ny + j];
       const float czmh = H[2 * nx + 2 * ny + k], czml = L[2 * nx + 2 * ny + k];
@@ -1359,21 +1385,29 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const 
       }
     }
   A0 += a0; A1 += a1; A2 += a2;
-  block_partials3(A0, A1, A2, partials);
+  block_partials3(A0, A1, A2, partials, gr.bx());
   // launched as one wave of fewer than REDUCE_BLOCKS blocks: the other slots read zero
   if (threadIdx.x == 0)
-    for (int b = blockIdx.x + gridDim.x; b < REDUCE_BLOCKS; b += gridDim.x)
+    for (int b = gr.bx() + gr.gx(); b < REDUCE_BLOCKS; b += gr.gx())
       for (int q = 0; q < 3; ++q) partials[3 * b + q] = 0.0;
 }
 
+__global__ void __launch_bounds__(REDUCE_THREADS) k_residual_df(DfView v, const float *ph, const float *pl,
+                                                               const float *bh, const float *bl,
+                                                               const double *lambda, float *r32, double *partials) {
+  residual_df_body(v, ph, pl, bh, bl, lambda, r32, partials, HwGrid{});
+}
+
 // ghost rows r_G = sum w v - g in FP64 from the split values; block partials of (s_G r_G)^2
-__global__ void k_ghost_resid_df(const long long *src, const long long *dst, const double *w, const double *scale,
-                                 const long long *ngp, const float *ph, const float *pl, float *r32, double *gpart,
-                                 const double *gd) {
+template <class G>
+__device__ __forceinline__ void ghost_resid_df_body(const long long *src, const long long *dst, const double *w,
+                                                    const double *scale, const long long *ngp, const float *ph,
+                                                    const float *pl, float *r32, double *gpart, const double *gd,
+                                                    const G &gr) {
   __shared__ double sm[REDUCE_THREADS];
   double a = 0.0;
   const long long ng = *ngp;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+  for (long long g = gr.bx() * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gr.gx() * blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < 8; ++c) {
       long long q = src[8 * g + c];
@@ -1395,7 +1429,13 @@ __global__ void k_ghost_resid_df(const long long *src, const long long *dst, con
     if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) gpart[blockIdx.x] = sm[0];
+  if (threadIdx.x == 0) gpart[gr.bx()] = sm[0];
+}
+
+__global__ void k_ghost_resid_df(const long long *src, const long long *dst, const double *w, const double *scale,
+                                 const long long *ngp, const float *ph, const float *pl, float *r32, double *gpart,
+                                 const double *gd) {
+  ghost_resid_df_body(src, dst, w, scale, ngp, ph, pl, r32, gpart, gd, HwGrid{});
 }
 
 // ghost values g = sum w v from the split values (into gtmp), then stored split (Jacobi)
@@ -1421,8 +1461,9 @@ __global__ void k_ghost_store_df(const long long *dst, long long ng, const doubl
 }
 
 // p += e (FP32 correction) on every padded cell, four at a time (n4 = ntot / 4)
-__global__ void k_update_df(float4 *ph, float4 *pl, const float4 *e, long long n4) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+template <class G>
+__device__ __forceinline__ void update_df_body(float4 *ph, float4 *pl, const float4 *e, long long n4, const G &gr) {
+  for (long long q = gr.bx() * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gr.gx() * blockDim.x) {
     float4 h = ph[q], l = pl[q];
     const float4 x = e[q];
     float *hv = &h.x, *lv = &l.x;
@@ -1437,6 +1478,10 @@ __global__ void k_update_df(float4 *ph, float4 *pl, const float4 *e, long long n
     ph[q] = h;
     pl[q] = l;
   }
+}
+
+__global__ void k_update_df(float4 *ph, float4 *pl, const float4 *e, long long n4) {
+  update_df_body(ph, pl, e, n4, HwGrid{});
 }
 
 // pack a user [k][j][i] array into split padded arrays (cells past nx in the last group
@@ -3396,8 +3441,9 @@ ibm_status run_launch(Run &R, bool graph, cudaStream_t st) {
 // ------------------------------------------------------------------ lockstep batched solves
 //
 // Problems of a batch advance through each refinement step together, one launch per V-cycle
-// stage (a level's sweep, restriction, shift, prolongation, ghost update, coarse tail) over the
-// blocks of every problem in that stage: each block runs the single-problem kernel's body on
+// stage (a level's sweep, restriction, shift, prolongation, ghost update, coarse tail) and per
+// kernel of the outer step (update, residual, ghost rows, norms) over the blocks of every
+// problem in that stage: each block runs the single-problem kernel's body on
 // its problem's arguments, so every problem gets the bits its own solve would get.  The
 // arguments travel as kernel parameters, up to BATCH_MAX problems per launch; problem q owns
 // blocks b0[q] .. b0[q + 1] - 1 of the launch (its own grid, laid out x fastest).  Problems
@@ -3541,6 +3587,66 @@ __global__ void __launch_bounds__(TAIL_THREADS) kb_tail(const TailArgs<float> *A
   for (int w = threadIdx.x; w < (int)(sizeof(TailArgs<float>) / 8); w += blockDim.x) dst[w] = src[w];
   __syncthreads();
   tail_body<float>(As);
+}
+// the outer step: p += e, the fine residual with its ghost rows and norms (lambda updated)
+struct PUpdate {
+  double *p;
+  const float *e;
+  float4 *ph, *pl;    // double-FP32 p (hi, lo), four floats at a time
+  long long n;        // elements of p (FP64), or groups of four (double-FP32)
+  int gx;
+};
+struct PRes {
+  LV<double> v;       // FP64 view (mode 1)
+  DfView vd;          // double-FP32 view (mode 2)
+  const double *p, *b, *lambda;
+  const float *wf, *ph, *pl, *bh, *bl;
+  float *r32;
+  double *part;
+  int gx;
+};
+struct PGres {
+  const long long *src, *dst, *ngp;
+  const double *w, *scale, *p, *gd;
+  const float *ph, *pl;
+  float *r32;
+  double *gpart;
+};
+struct PFin {
+  const double *part, *gpart;
+  double *scal;
+  int ngb;
+};
+static_assert(sizeof(BL<PRes>) <= 32764, "kernel parameters of at most 32764 bytes");
+
+__global__ void kb_update_p(const __grid_constant__ BL<PUpdate> L) {
+  BL_BLOCK(L)
+  update_p_body(p.p, p.e, p.n, vgrid(lb, p.gx, 1));
+}
+__global__ void kb_update_df(const __grid_constant__ BL<PUpdate> L) {
+  BL_BLOCK(L)
+  update_df_body(p.ph, p.pl, reinterpret_cast<const float4 *>(p.e), p.n, vgrid(lb, p.gx, 1));
+}
+__global__ void __launch_bounds__(REDUCE_THREADS) kb_residual64(const __grid_constant__ BL<PRes> L) {
+  BL_BLOCK(L)
+  residual64_body<float, true>(p.v, p.p, p.b, p.lambda, p.wf, p.r32, p.part, nullptr, vgrid(lb, p.gx, 1));
+}
+__global__ void __launch_bounds__(REDUCE_THREADS) kb_residual_df(const __grid_constant__ BL<PRes> L) {
+  BL_BLOCK(L)
+  residual_df_body(p.vd, p.ph, p.pl, p.bh, p.bl, p.lambda, p.r32, p.part, vgrid(lb, p.gx, 1));
+}
+__global__ void kb_ghost_resid64(const __grid_constant__ BL<PGres> L) {
+  BL_BLOCK(L)
+  ghost_resid64_body<float>(p.src, p.dst, p.w, p.scale, p.ngp, p.p, p.r32, p.gpart, p.gd, vgrid(lb, FIXED_BLOCKS, 1));
+}
+__global__ void kb_ghost_resid_df(const __grid_constant__ BL<PGres> L) {
+  BL_BLOCK(L)
+  ghost_resid_df_body(p.src, p.dst, p.w, p.scale, p.ngp, p.ph, p.pl, p.r32, p.gpart, p.gd, vgrid(lb, FIXED_BLOCKS, 1));
+}
+__global__ void kb_finalize_resid(const __grid_constant__ BL<PFin> L) {
+  BL_BLOCK(L)
+  (void)lb;
+  finalize_resid_body(p.part, REDUCE_BLOCKS, p.gpart, p.ngb, p.scal, 1, nullptr, 0);
 }
 #undef BL_BLOCK
 static_assert(sizeof(TailArgs<float>) % 8 == 0, "tail arguments are copied as 8-byte words");
@@ -3818,6 +3924,98 @@ void lk_vcycle(Lock &K, int l, const std::vector<int> &grp) {
   lk_smooth(K, l, mid, K.nu2);
 }
 
+// the outer step of every problem in act, as the single-problem run_outer takes it: p += e,
+// then the fine residual (FP64 in mode 1, double-FP32 in mode 2), its ghost rows and norms,
+// with lambda updated; one launch per kernel over all problems
+void lk_outer(Lock &K, const std::vector<int> &act) {
+  std::vector<Run> &R = *K.R;
+  ibm_ctx *ctx = K.ctx;
+  const bool dfo = R[act[0]].S.dfo;
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+  const int rdf_blocks = std::min(REDUCE_BLOCKS, 3 * sms);   // as outer_residual's double-FP32 launch
+  auto ublocks = [&](int i) {
+    return (int)std::min<long long>(nblk(dfo ? R[i].ntot / 4 : R[i].ntot, 256), ctx->wave);
+  };
+  bl_launch<PUpdate>(act, ublocks,
+                     [&](int i) {
+                       Hierarchy *h = R[i].h;
+                       PUpdate p{};
+                       p.e = (const float *)h->lv[0].e;
+                       if (dfo) {
+                         p.ph = reinterpret_cast<float4 *>(hi_of(h->p64));
+                         p.pl = reinterpret_cast<float4 *>(lo_of(h->p64, R[i].ntot));
+                         p.n = R[i].ntot / 4;
+                       } else {
+                         p.p = h->p64;
+                         p.n = R[i].ntot;
+                       }
+                       p.gx = ublocks(i);
+                       return p;
+                     },
+                     [&](const BL<PUpdate> &L, int b) {
+                       if (dfo) kb_update_df<<<b, 256, 0, K.st>>>(L);
+                       else kb_update_p<<<b, 256, 0, K.st>>>(L);
+                       ctx->launches += 1;
+                     });
+  bl_launch<PRes>(act, [&](int) { return dfo ? rdf_blocks : REDUCE_BLOCKS; },
+                  [&](int i) {
+                    Hierarchy *h = R[i].h;
+                    const long long ntot = R[i].ntot;
+                    PRes p{};
+                    if (dfo) {
+                      p.vd = fine_view_df(h);
+                      p.ph = hi_of(h->p64); p.pl = lo_of(h->p64, ntot);
+                      p.bh = hi_of(h->b64); p.bl = lo_of(h->b64, ntot);
+                      p.gx = rdf_blocks;
+                    } else {
+                      p.v = fine_view64(h);
+                      p.p = h->p64; p.b = h->b64;
+                      p.wf = h->cdf + 3 * (p.v.nx + p.v.ny + p.v.nz);
+                      p.gx = REDUCE_BLOCKS;
+                    }
+                    p.lambda = R[i].S.scal + S_LAMBDA;
+                    p.r32 = R[i].r32;
+                    p.part = R[i].S.part;
+                    return p;
+                  },
+                  [&](const BL<PRes> &L, int b) {
+                    if (dfo) kb_residual_df<<<b, REDUCE_THREADS, 0, K.st>>>(L);
+                    else kb_residual64<<<b, REDUCE_THREADS, 0, K.st>>>(L);
+                    ctx->launches += 1;
+                  });
+  bl_launch<PGres>(act, [&](int i) { return R[i].t->nghost > 0 ? FIXED_BLOCKS : 0; },
+                   [&](int i) {
+                     Hierarchy *h = R[i].h;
+                     const ibm_tables *t = R[i].t;
+                     PGres p{};
+                     p.src = h->gsrc; p.dst = h->gdst; p.ngp = h->d_ng;
+                     p.w = t->gw; p.scale = t->gscale; p.gd = t->has_datum ? t->gd : nullptr;
+                     if (dfo) { p.ph = hi_of(h->p64); p.pl = lo_of(h->p64, R[i].ntot); }
+                     else p.p = h->p64;
+                     p.r32 = R[i].r32;
+                     p.gpart = R[i].S.part + 3 * REDUCE_BLOCKS;
+                     return p;
+                   },
+                   [&](const BL<PGres> &L, int b) {
+                     if (dfo) kb_ghost_resid_df<<<b, REDUCE_THREADS, 0, K.st>>>(L);
+                     else kb_ghost_resid64<<<b, REDUCE_THREADS, 0, K.st>>>(L);
+                     ctx->launches += 1;
+                   });
+  bl_launch<PFin>(act, [](int) { return 1; },
+                  [&](int i) {
+                    PFin p{};
+                    p.part = R[i].S.part;
+                    p.gpart = R[i].S.part + 3 * REDUCE_BLOCKS;
+                    p.scal = R[i].S.scal;
+                    p.ngb = R[i].t->nghost > 0 ? FIXED_BLOCKS : 0;
+                    return p;
+                  },
+                  [&](const BL<PFin> &L, int b) {
+                    kb_finalize_resid<<<b, 256, 0, K.st>>>(L);
+                    ctx->launches += 1;
+                  });
+}
+
 // can the batch advance in lockstep: mixed precision, closed bodies, no Krylov acceleration,
 // FP32 coarse storage, and every finest level swept by the fused z-march on its own e and r
 bool lockstep_ok(const std::vector<Run> &R, const ibm_solve_opts *opts) {
@@ -3890,8 +4088,8 @@ ibm_status lockstep_setup(Lock &K, std::vector<Run> &R) {
   return IBM_OK;
 }
 
-// one refinement step of the problems in act: their FP32 V-cycles in lockstep on the caller's
-// stream, then each problem's outer update and residual on the stream pool
+// one refinement step of the problems in act, in lockstep on the caller's stream: their FP32
+// V-cycles, then their outer updates and residuals
 ibm_status lockstep_step(Lock &K, const std::vector<int> &act, int inner) {
   ibm_ctx *ctx = K.ctx;
   std::vector<Run> &R = *K.R;
@@ -3910,14 +4108,7 @@ ibm_status lockstep_step(Lock &K, const std::vector<int> &act, int inner) {
     lk_vcycle(K, 0, act);
   }
   for (int i : act) R[i].h->lv[0].e = K.E[0][i];
-  const int ns = std::min((int)act.size(), (int)ibm_ctx::NBSTREAM);
-  IBM_TRY(cudaEventRecord(ctx->bevent[ibm_ctx::NBSTREAM], K.st));
-  for (int s = 0; s < ns; ++s) IBM_TRY(cudaStreamWaitEvent(ctx->bstream[s], ctx->bevent[ibm_ctx::NBSTREAM], 0));
-  for (size_t j = 0; j < act.size(); ++j) run_outer(R[act[j]], ctx->bstream[j % ns]);
-  for (int s = 0; s < ns; ++s) {
-    IBM_TRY(cudaEventRecord(ctx->bevent[s], ctx->bstream[s]));
-    IBM_TRY(cudaStreamWaitEvent(K.st, ctx->bevent[s], 0));
-  }
+  lk_outer(K, act);
   IBM_TRY(cudaGetLastError());
   return IBM_OK;
 }
@@ -3977,9 +4168,9 @@ ibm_status solve_impl(ibm_ctx *ctx, ibm_tables *t, const double *rhs, double tol
 }
 
 // Batched solves: every problem keeps its own scalars and partials.  In lockstep (mixed
-// precision on closed bodies, the default when every problem allows it) each step's V-cycles
-// run as one launch per stage over all problems still iterating, and their outer updates and
-// residuals on the context's pool of streams.  Otherwise each problem runs the single-problem
+// precision on closed bodies, the default when every problem allows it) each step's V-cycles,
+// outer updates and residuals run as one launch per stage over all problems still iterating.
+// Otherwise each problem runs the single-problem
 // refinement step, captured once as its hierarchy's CUDA graph, and each step launches the
 // graphs of the problems still iterating on the stream pool (problem p on stream p mod
 // NBSTREAM), forked from and joined back into the caller's stream, so the small problems'
