@@ -4019,7 +4019,7 @@ void lk_outer(Lock &K, const std::vector<int> &act) {
 // can the batch advance in lockstep: mixed precision, closed bodies, no Krylov acceleration,
 // FP32 coarse storage, and every finest level swept by the fused z-march on its own e and r
 bool lockstep_ok(const std::vector<Run> &R, const ibm_solve_opts *opts) {
-  if (opts->batch_schedule != 0 || opts->precision == 0 || opts->coarse_bf16) return false;
+  if (R.empty() || opts->batch_schedule != 0 || opts->precision == 0 || opts->coarse_bf16) return false;
   for (const Run &r : R) {
     const Hierarchy *h = r.h;
     if (r.t->membrane || r.gcr_m > 0 || h->hcnt[1] > 0 || h->hcnt[2] > 0 || !h->zmarch || h->elem != 4) return false;
